@@ -1,0 +1,223 @@
+"""CPU oracle for dedispersion and the boxcar single-pulse search.
+
+TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+benchmark's CPU-baseline leg may import this package.  The product path (the
+CUDA library and its Python binding) never imports, links or runs it, and the
+two share no code: only the seeded input generators feed both.
+
+The arithmetic lives in ``oracle.c`` (plain C, FP64 where floating point is
+involved); this module is ctypes marshalling around it.  Each wrapper cites
+the passage of the paper its C function writes out:
+
+* ``delay_table``   -- dispersion delay law, Ch.1 Eq.1;
+* ``dedisperse``    -- brute-force shift-and-sum, Sec.3.2;
+* ``window_stats``  -- median / MAD noise estimate, Sec.3.3;
+* ``boxcar``, ``sps`` -- boxcar single-pulse search above a threshold, Sec.2.1.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+
+class Cand(C.Structure):
+    _fields_ = [("dm_idx", C.c_int32), ("w_idx", C.c_int32),
+                ("t", C.c_int64), ("snr", C.c_double)]
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        L = C.CDLL(path)
+        P = C.c_void_p
+        L.orc_delay_table.restype = C.c_int32
+        L.orc_delay_table.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double,
+                                      P, C.c_int, P]
+        L.orc_delay_exact.restype = C.c_double
+        L.orc_delay_exact.argtypes = [C.c_int, C.c_double, C.c_double, C.c_double,
+                                      C.c_double, C.c_int]
+        L.orc_unpack_u8.restype = None
+        L.orc_unpack_u8.argtypes = [P, C.c_int64, C.c_int, P]
+        L.orc_unpack_u16.restype = None
+        L.orc_unpack_u16.argtypes = [P, C.c_int64, C.c_int, P]
+        L.orc_dedisperse.restype = C.c_int
+        L.orc_dedisperse.argtypes = [P, C.c_int, C.c_int64, C.c_int, P, C.c_int,
+                                     C.c_int64, P]
+        L.orc_dedisperse_at.restype = C.c_int64
+        L.orc_dedisperse_at.argtypes = [P, C.c_int, C.c_int64, C.c_int, P, C.c_int64]
+        L.orc_num_windows.restype = C.c_int64
+        L.orc_num_windows.argtypes = [C.c_int64, C.c_int64]
+        L.orc_window_bounds.restype = None
+        L.orc_window_bounds.argtypes = [C.c_int64, C.c_int64, C.c_int64, P, P]
+        L.orc_median_mad.restype = None
+        L.orc_median_mad.argtypes = [P, C.c_int64, P, P]
+        L.orc_window_stats.restype = None
+        L.orc_window_stats.argtypes = [P, C.c_int64, C.c_int64, P, P]
+        L.orc_boxcar.restype = C.c_int
+        L.orc_boxcar.argtypes = [P, C.c_int64, C.c_int, P]
+        L.orc_snr.restype = C.c_double
+        L.orc_snr.argtypes = [C.c_int64, C.c_int, C.c_int64, C.c_int64]
+        L.orc_best_at.restype = C.c_int
+        L.orc_best_at.argtypes = [P, C.c_int64, C.c_int64, P, C.c_int, C.c_int64,
+                                  C.POINTER(C.c_double)]
+        L.orc_sps.restype = C.c_int64
+        L.orc_sps.argtypes = [P, C.c_int, C.c_int64, P, C.c_int, C.c_int64,
+                              C.c_double, P, C.c_int64]
+        _lib = L
+    return _lib
+
+
+def _ptr(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def set_threads(n: int) -> None:
+    """Number of OpenMP threads the DM loop of ``dedisperse`` may use."""
+    os.environ["OMP_NUM_THREADS"] = str(int(n))
+
+
+def delay_table(nchan, f_top, chan_bw, tsamp, dm_list):
+    """Integer delay table d[k][c] and the largest delay D (Ch.1 Eq.1)."""
+    dm = np.ascontiguousarray(dm_list, dtype=np.float64)
+    d = np.empty((dm.size, nchan), dtype=np.int32)
+    D = lib().orc_delay_table(int(nchan), float(f_top), float(chan_bw),
+                              float(tsamp), _ptr(dm), int(dm.size), _ptr(d))
+    if D < 0:
+        raise ValueError("invalid delay-table arguments")
+    return d, int(D)
+
+
+def delay_exact(nchan, f_top, chan_bw, tsamp, dm, c):
+    """Unrounded delay in samples for one (DM, channel)."""
+    return lib().orc_delay_exact(int(nchan), float(f_top), float(chan_bw),
+                                 float(tsamp), float(dm), int(c))
+
+
+def unpack(x):
+    """Time-major [nin][nchan] spectra -> channel-major [nchan][nin]."""
+    x = np.ascontiguousarray(x)
+    nin, nchan = x.shape
+    out = np.empty((nchan, nin), dtype=x.dtype)
+    if x.dtype == np.uint8:
+        lib().orc_unpack_u8(_ptr(x), nin, nchan, _ptr(out))
+    elif x.dtype == np.uint16:
+        lib().orc_unpack_u16(_ptr(x), nin, nchan, _ptr(out))
+    else:
+        raise TypeError("uint8 or uint16 spectra expected")
+    return out
+
+
+def _nbits(x):
+    if x.dtype == np.uint8:
+        return 8
+    if x.dtype == np.uint16:
+        return 16
+    raise TypeError("uint8 or uint16 spectra expected")
+
+
+def dedisperse(x, d):
+    """Brute-force dedispersion of time-major spectra x[nin][nchan] (Sec.3.2).
+
+    Returns int32 out[ndm][nout], nout = nin - max(d)."""
+    x = np.ascontiguousarray(x)
+    d = np.ascontiguousarray(d, dtype=np.int32)
+    nin, nchan = x.shape
+    ndm = d.shape[0]
+    nout = nin - int(d.max())
+    if nout <= 0:
+        raise ValueError("input shorter than the largest delay")
+    out = np.empty((ndm, nout), dtype=np.int32)
+    rc = lib().orc_dedisperse(_ptr(x), _nbits(x), nin, nchan, _ptr(d), ndm, nout,
+                              _ptr(out))
+    if rc != 0:
+        raise ValueError("dedispersion sum out of int32 range")
+    return out
+
+
+def dedisperse_at(x, d, k, t):
+    """One dedispersed sample out[k][t] (same definition as ``dedisperse``)."""
+    x = np.ascontiguousarray(x)
+    nin, nchan = x.shape
+    row = np.ascontiguousarray(d[k], dtype=np.int32)
+    v = lib().orc_dedisperse_at(_ptr(x), _nbits(x), nin, nchan, _ptr(row), int(t))
+    if v == np.iinfo(np.int64).min:
+        raise IndexError("sample outside the input")
+    return int(v)
+
+
+def num_windows(n, L):
+    return int(lib().orc_num_windows(int(n), int(L)))
+
+
+def window_bounds(n, L, j):
+    lo, hi = C.c_int64(), C.c_int64()
+    lib().orc_window_bounds(int(n), int(L), int(j), C.byref(lo), C.byref(hi))
+    return lo.value, hi.value
+
+
+def median_mad(x):
+    """(2*median, 4*MAD) of a 1-D int32 array, exact (Sec.3.3)."""
+    x = np.ascontiguousarray(x, dtype=np.int32)
+    m2, mad4 = C.c_int64(), C.c_int64()
+    lib().orc_median_mad(_ptr(x), x.size, C.byref(m2), C.byref(mad4))
+    return m2.value, mad4.value
+
+
+def window_stats(x, L):
+    """Per-window (2*median, 4*MAD) arrays of one int32 series."""
+    x = np.ascontiguousarray(x, dtype=np.int32)
+    nwin = num_windows(x.size, L)
+    m2 = np.empty(nwin, dtype=np.int64)
+    mad4 = np.empty(nwin, dtype=np.int64)
+    lib().orc_window_stats(_ptr(x), x.size, int(L), _ptr(m2), _ptr(mad4))
+    return m2, mad4
+
+
+def boxcar(x, w):
+    """B_w(t) = sum_{i<w} x[t+i] for t <= n-w, by direct summation (int64)."""
+    x = np.ascontiguousarray(x, dtype=np.int32)
+    n = x.size
+    out = np.empty(max(n - w + 1, 0), dtype=np.int64)
+    if out.size and lib().orc_boxcar(_ptr(x), n, int(w), _ptr(out)) != 0:
+        raise OverflowError("boxcar sum leaves int32")
+    return out
+
+
+def snr(B, w, m2, mad4):
+    return lib().orc_snr(int(B), int(w), int(m2), int(mad4))
+
+
+def best_at(x, L, widths, t):
+    """(best width index, best S/N) at one sample of one series."""
+    x = np.ascontiguousarray(x, dtype=np.int32)
+    ws = np.ascontiguousarray(widths, dtype=np.int32)
+    s = C.c_double()
+    wi = lib().orc_best_at(_ptr(x), x.size, int(L), _ptr(ws), ws.size, int(t),
+                           C.byref(s))
+    return wi, s.value
+
+
+CAND_DTYPE = np.dtype([("dm_idx", np.int32), ("w_idx", np.int32),
+                       ("t", np.int64), ("snr", np.float64)])
+
+
+def sps(series, widths, L, thr, cap=None):
+    """Boxcar single-pulse search over series[ndm][n] (Sec.2.1).
+
+    Returns (candidates sorted by (dm_idx, t), true count)."""
+    series = np.ascontiguousarray(series, dtype=np.int32)
+    if series.ndim == 1:
+        series = series[None, :]
+    ndm, n = series.shape
+    ws = np.ascontiguousarray(widths, dtype=np.int32)
+    if cap is None:
+        cap = 1 << 20
+    out = np.zeros(cap, dtype=CAND_DTYPE)
+    cnt = lib().orc_sps(_ptr(series), ndm, n, _ptr(ws), ws.size, int(L),
+                        float(thr), _ptr(out), int(cap))
+    return out[:min(cnt, cap)].copy(), int(cnt)

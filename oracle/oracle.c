@@ -1,0 +1,313 @@
+/*
+ * oracle.c -- plain, slow CPU oracle for brute-force incoherent dedispersion
+ * and the boxcar single-pulse search.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing on the product path may call, link or
+ * load this file: only the test suite, the smoke check and the CPU-baseline
+ * leg of the benchmark use it.  It shares no source with the CUDA library.
+ *
+ * Every function writes out a definition directly, in the order the method
+ * states it, with no blocking, fusion or reordering:
+ *   - delay table:       dispersion delay law, Ch.1 Eq.1 (constant
+ *                        4148.808 s MHz^2, i.e. 4.14881 ms GHz^2), rounded to
+ *                        the nearest sample with ties away from zero;
+ *   - dedispersion:      brute-force shift-and-sum over channels, Sec.3.2
+ *                        ("brute-force dedispersion is O(m x N)");
+ *   - window statistics: median and median absolute deviation, Sec.3.3
+ *                        (median preferred for robustness to outliers);
+ *   - boxcar S/N search: time-domain boxcar filtering above a user threshold,
+ *                        Sec.2.1.
+ * Readings where the paper is silent (channel frequencies, output length,
+ * boxcar alignment, window layout, even-count median, MAD = 0) are listed at
+ * each function.
+ *
+ * Floating point is IEEE double; build with -ffp-contract=off so no fused
+ * multiply-add changes the rounding of the delay expression.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_K_DISP 4148.808          /* s MHz^2 per (pc cm^-3), Ch.1 Eq.1 */
+#define ORC_MAD_TO_SIGMA 1.482602218505602
+
+/* ------------------------------------------------------------------------ */
+/* Delay table (Ch.1 Eq.1).                                                 */
+/* Reading: channel c is centred at f_c = f_top + c*chan_bw (first channel   */
+/* at f_top); the reference frequency f_ref is the highest channel          */
+/* frequency, so every delay is >= 0 for DM >= 0.                            */
+/* d[k][c] = round_half_away(K * DM_k * (f_c^-2 - f_ref^-2) / tsamp).        */
+/* Returns the largest delay D, or -1 on a bad argument.                    */
+/* ------------------------------------------------------------------------ */
+int32_t orc_delay_table(int nchan, double f_top, double chan_bw, double tsamp,
+                        const double *dm, int ndm, int32_t *d)
+{
+    if (nchan <= 0 || ndm <= 0 || !(tsamp > 0.0) || chan_bw == 0.0) return -1;
+    double f_last = f_top + (double)(nchan - 1) * chan_bw;
+    double fr = f_top > f_last ? f_top : f_last;
+    int32_t dmax = 0;
+    for (int k = 0; k < ndm; ++k) {
+        if (!(dm[k] >= 0.0) || !isfinite(dm[k])) return -1;
+        for (int c = 0; c < nchan; ++c) {
+            double f = f_top + c * chan_bw;
+            double x = ORC_K_DISP * dm[k] * (1.0 / (f * f) - 1.0 / (fr * fr)) / tsamp;
+            double r = round(x);               /* C round(): half away from zero */
+            if (r > 2147483647.0) return -1;
+            d[(int64_t)k * nchan + c] = (int32_t)r;
+            if ((int32_t)r > dmax) dmax = (int32_t)r;
+        }
+    }
+    return dmax;
+}
+
+/* Unrounded delay x = K*DM*(f^-2 - f_ref^-2)/tsamp, so a test can list the  */
+/* entries that sit within a hair of a .5 tie.                               */
+double orc_delay_exact(int nchan, double f_top, double chan_bw, double tsamp,
+                       double dm, int c)
+{
+    double f_last = f_top + (double)(nchan - 1) * chan_bw;
+    double fr = f_top > f_last ? f_top : f_last;
+    double f = f_top + c * chan_bw;
+    return ORC_K_DISP * dm * (1.0 / (f * f) - 1.0 / (fr * fr)) / tsamp;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Unpack: time-major spectra [nin][nchan] (the layout of a block of         */
+/* spectra, Sec.2.2) to channel-major rows [nchan][nin].  A plain transpose. */
+/* ------------------------------------------------------------------------ */
+void orc_unpack_u8(const uint8_t *in, int64_t nin, int nchan, uint8_t *out)
+{
+    for (int c = 0; c < nchan; ++c)
+        for (int64_t s = 0; s < nin; ++s)
+            out[(int64_t)c * nin + s] = in[s * nchan + c];
+}
+
+void orc_unpack_u16(const uint16_t *in, int64_t nin, int nchan, uint16_t *out)
+{
+    for (int c = 0; c < nchan; ++c)
+        for (int64_t s = 0; s < nin; ++s)
+            out[(int64_t)c * nin + s] = in[s * nchan + c];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Brute-force dedispersion (Sec.3.2).                                       */
+/* out[k][t] = sum_c in[t + d[k][c]][c], t in [0, nout), nout = nin - D.      */
+/* The input is read in its time-major layout in[sample][chan].  Sums are    */
+/* accumulated in int64 and must fit int32 (they do: 4096*65535 < 2^31).     */
+/* The loop over DM trials may run on several cores (each trial is           */
+/* independent); the arithmetic is the same triple loop either way.          */
+/* ------------------------------------------------------------------------ */
+static int64_t sample_at(const void *in, int nbits, int nchan, int64_t s, int c)
+{
+    if (nbits == 8) return ((const uint8_t *)in)[s * nchan + c];
+    return ((const uint16_t *)in)[s * nchan + c];
+}
+
+int orc_dedisperse(const void *in, int nbits, int64_t nin, int nchan,
+                   const int32_t *d, int ndm, int64_t nout, int32_t *out)
+{
+    if (nbits != 8 && nbits != 16) return -1;
+    int bad = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : bad)
+    for (int k = 0; k < ndm; ++k) {
+        const int32_t *dk = d + (int64_t)k * nchan;
+        for (int64_t t = 0; t < nout; ++t) {
+            int64_t acc = 0;
+            for (int c = 0; c < nchan; ++c) {
+                int64_t s = t + dk[c];
+                if (s < 0 || s >= nin) { bad = 1; continue; }
+                acc += sample_at(in, nbits, nchan, s, c);
+            }
+            if (acc > INT32_MAX) bad = 1;
+            out[(int64_t)k * nout + t] = (int32_t)acc;
+        }
+    }
+    return bad ? -1 : 0;
+}
+
+/* One output sample out[k][t], for sampled checks at sizes where the full   */
+/* triple loop would take too long.  Same definition as above.               */
+int64_t orc_dedisperse_at(const void *in, int nbits, int64_t nin, int nchan,
+                          const int32_t *dk, int64_t t)
+{
+    int64_t acc = 0;
+    for (int c = 0; c < nchan; ++c) {
+        int64_t s = t + dk[c];
+        if (s < 0 || s >= nin) return INT64_MIN;
+        acc += sample_at(in, nbits, nchan, s, c);
+    }
+    return acc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Window statistics (Sec.3.3: median-based noise estimate; MAD as the       */
+/* robust spread).                                                           */
+/* Readings: windows j = [jL, (j+1)L) for j < nwin-1 with                    */
+/* nwin = max(1, floor(n/L)); the last window runs to n.  L = 0 means one    */
+/* window over the whole series.  Median of an even count = mean of the two  */
+/* middle order statistics, kept exact as m2 = 2*median.  MAD = median of    */
+/* |x - median|, kept exact as mad4 = 4*MAD (u_i = |2x_i - m2|,              */
+/* mad4 = 2*median(u)).  The order statistics come from a full sort (qsort). */
+/* ------------------------------------------------------------------------ */
+static int cmp_i64(const void *a, const void *b)
+{
+    int64_t x = *(const int64_t *)a, y = *(const int64_t *)b;
+    return (x > y) - (x < y);
+}
+
+int64_t orc_num_windows(int64_t n, int64_t L)
+{
+    if (L <= 0) return 1;
+    int64_t w = n / L;
+    return w < 1 ? 1 : w;
+}
+
+void orc_window_bounds(int64_t n, int64_t L, int64_t j, int64_t *lo, int64_t *hi)
+{
+    int64_t nwin = orc_num_windows(n, L);
+    if (L <= 0) { *lo = 0; *hi = n; return; }
+    *lo = j * L;
+    *hi = (j == nwin - 1) ? n : (j + 1) * L;
+}
+
+/* m2 = 2*median and mad4 = 4*MAD of x[0..n). */
+void orc_median_mad(const int32_t *x, int64_t n, int64_t *m2, int64_t *mad4)
+{
+    int64_t *v = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    for (int64_t i = 0; i < n; ++i) v[i] = x[i];
+    qsort(v, (size_t)n, sizeof(int64_t), cmp_i64);
+    int64_t med2 = (n & 1) ? 2 * v[n / 2] : v[n / 2 - 1] + v[n / 2];
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t u = 2 * (int64_t)x[i] - med2;
+        v[i] = u < 0 ? -u : u;
+    }
+    qsort(v, (size_t)n, sizeof(int64_t), cmp_i64);
+    int64_t umed2 = (n & 1) ? 2 * v[n / 2] : v[n / 2 - 1] + v[n / 2];
+    free(v);
+    *m2 = med2;
+    *mad4 = umed2;
+}
+
+void orc_window_stats(const int32_t *x, int64_t n, int64_t L,
+                      int64_t *m2, int64_t *mad4)
+{
+    int64_t nwin = orc_num_windows(n, L);
+    for (int64_t j = 0; j < nwin; ++j) {
+        int64_t lo, hi;
+        orc_window_bounds(n, L, j, &lo, &hi);
+        orc_median_mad(x + lo, hi - lo, &m2[j], &mad4[j]);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Boxcar (Sec.2.1).  Reading: left-aligned windows, B_w(t) = sum_{i<w}      */
+/* x[t+i], defined for t <= n - w only.  Direct summation in int64.          */
+/* Returns -1 if a sum leaves int32.                                         */
+/* ------------------------------------------------------------------------ */
+int orc_boxcar(const int32_t *x, int64_t n, int w, int64_t *out)
+{
+    for (int64_t t = 0; t + w <= n; ++t) {
+        int64_t acc = 0;
+        for (int i = 0; i < w; ++i) acc += x[t + i];
+        out[t] = acc;
+        if (acc > INT32_MAX || acc < INT32_MIN) return -1;
+    }
+    return 0;
+}
+
+/* S/N of B_w(t) against the statistics of the window holding t:             */
+/* snr = (B_w - w*median) / (sigma*sqrt(w)), sigma = 1.4826*MAD, in FP64.     */
+/* Reading: MAD = 0 gives S/N = 0 (no candidate from that window).            */
+double orc_snr(int64_t B, int w, int64_t m2, int64_t mad4)
+{
+    if (mad4 == 0) return 0.0;
+    double sigma = ORC_MAD_TO_SIGMA * ((double)mad4 / 4.0);
+    double num = (double)B - (double)w * ((double)m2 / 2.0);
+    return num / (sigma * sqrt((double)w));
+}
+
+typedef struct {
+    int32_t dm_idx;
+    int32_t w_idx;
+    int64_t t;
+    double snr;
+} orc_cand;
+
+static int cmp_cand(const void *a, const void *b)
+{
+    const orc_cand *x = (const orc_cand *)a, *y = (const orc_cand *)b;
+    if (x->dm_idx != y->dm_idx) return (x->dm_idx > y->dm_idx) - (x->dm_idx < y->dm_idx);
+    return (x->t > y->t) - (x->t < y->t);
+}
+
+/* Best width and S/N at one (series, t): widths scanned in the order given;   */
+/* the first width reaching the maximum wins (ties go to the earlier width).  */
+/* Only widths with t + w <= n take part.  Returns -1 if none does.           */
+int orc_best_at(const int32_t *x, int64_t n, int64_t L, const int *widths,
+                int nw, int64_t t, double *snr_out)
+{
+    int64_t j = (L <= 0) ? 0 : t / L;
+    int64_t nwin = orc_num_windows(n, L);
+    if (j > nwin - 1) j = nwin - 1;
+    int64_t lo, hi, m2, mad4;
+    orc_window_bounds(n, L, j, &lo, &hi);
+    orc_median_mad(x + lo, hi - lo, &m2, &mad4);
+    int best = -1;
+    double bsnr = 0.0;
+    for (int wi = 0; wi < nw; ++wi) {
+        int w = widths[wi];
+        if (t + w > n) continue;
+        int64_t B = 0;
+        for (int i = 0; i < w; ++i) B += x[t + i];
+        double s = orc_snr(B, w, m2, mad4);
+        if (best < 0 || s > bsnr) { best = wi; bsnr = s; }
+    }
+    *snr_out = bsnr;
+    return best;
+}
+
+/* Single-pulse search over series[ndm][n]: per window the statistics, per    */
+/* (k, t) the best width, and one candidate per (k, t) whose best S/N is      */
+/* >= thr (reading: no peak merging).  Candidates come back sorted by (k, t). */
+/* Returns the true count; at most cap records are written.                   */
+int64_t orc_sps(const int32_t *series, int ndm, int64_t n, const int *widths,
+                int nw, int64_t L, double thr, orc_cand *out, int64_t cap)
+{
+    int64_t nwin = orc_num_windows(n, L);
+    int64_t count = 0;
+    int64_t *m2 = (int64_t *)malloc((size_t)nwin * sizeof(int64_t));
+    int64_t *mad4 = (int64_t *)malloc((size_t)nwin * sizeof(int64_t));
+    for (int k = 0; k < ndm; ++k) {
+        const int32_t *x = series + (int64_t)k * n;
+        orc_window_stats(x, n, L, m2, mad4);
+        for (int64_t t = 0; t < n; ++t) {
+            int64_t j = (L <= 0) ? 0 : t / L;
+            if (j > nwin - 1) j = nwin - 1;
+            int best = -1;
+            double bsnr = 0.0;
+            for (int wi = 0; wi < nw; ++wi) {
+                int w = widths[wi];
+                if (t + w > n) continue;
+                int64_t B = 0;
+                for (int i = 0; i < w; ++i) B += x[t + i];
+                double s = orc_snr(B, w, m2[j], mad4[j]);
+                if (best < 0 || s > bsnr) { best = wi; bsnr = s; }
+            }
+            if (best >= 0 && bsnr >= thr) {
+                if (count < cap) {
+                    out[count].dm_idx = k;
+                    out[count].w_idx = best;
+                    out[count].t = t;
+                    out[count].snr = bsnr;
+                }
+                ++count;
+            }
+        }
+    }
+    free(m2);
+    free(mad4);
+    int64_t nout = count < cap ? count : cap;
+    qsort(out, (size_t)nout, sizeof(orc_cand), cmp_cand);
+    return count;
+}
