@@ -1,0 +1,409 @@
+#!/usr/bin/env python
+"""Benchmark of the dedispersion + single-pulse-search path on B300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = one pass of the whole path over one beam block: unpack
+(time-major -> channel-major), brute-force dedispersion of every DM trial,
+the fused median/MAD + boxcar S/N + candidate-compaction kernel, and the
+candidate fetch (device -> host, sorted).  Workload: one full-size beam,
+4096 channels over 300-500 MHz at 81.92 us, a 262144-sample block plus the
+89989-sample maximum-delay overlap, 1024 DM trials over 0-250 pc cm^-3,
+boxcar widths 1..256, median/MAD windows of 8192 samples, threshold 7
+(seeded synthetic 8-bit noise with 20 injected dispersed pulses).
+
+Metric: dedispersion channel*sample*DM adds per second, N_c * N_out * N_dm
+per step divided by the step time (whole job, all ranks).  The input block
+(1.44 GB) is larger than L2, so no flush is needed between steps.
+
+For N > 1 (torchrun, one rank per GPU) every rank processes its own beam:
+weak scaling with no data-path collective; the barrier and the max-over-
+ranks of the timings use the process group only.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "dedispersion chan·sample·DM adds/s"
+UNIT = "adds/s"
+SM_COUNT_B300 = 148
+ADDS_PER_SM_CLK = 128  # one byte operand per add through the 128 B/clk shared-memory port
+
+
+def workload():
+    from paper_2605_03531_b300 import synth
+    return synth.config2()
+
+
+def workload_config(cfg, nout):
+    return {"workload": "single full-size beam: 4096 ch x 81.92 us, 300-500 MHz, "
+                        "262144-sample block + max-delay overlap, 1024 DMs 0-250, "
+                        "widths 1-256, L=8192, thr 7",
+            "nchan": cfg.nchan, "nsamp_out": nout, "ndm": cfg.ndm,
+            "widths": [int(w) for w in cfg.widths], "norm_window": cfg.norm_window,
+            "threshold": cfg.threshold, "input_bits": 8,
+            "l2": "inputs larger than L2 (1.44 GB block per step)"}
+
+
+# ----------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.lines = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index),
+                 f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                text=True)
+        except OSError:
+            self.proc = None
+            return
+        threading.Thread(target=self._read, daemon=True).start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown",
+                 "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------- distributed
+def dist_setup(n_gpus):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------- oracle CPU
+def oracle_sample_rate(x_host, d, widths, L, target_s, min_t=8):
+    """Time the oracle (dedispersion + search) on all DM trials x the first T
+    output samples, T sized to about target_s seconds; returns adds/s,
+    T, elapsed seconds."""
+    import oracle
+    cal_t = min_t
+    D = int(d.max())
+
+    def run(T):
+        xs = np.ascontiguousarray(x_host[:T + D])
+        t0 = time.perf_counter()
+        series = oracle.dedisperse(xs, d)
+        oracle.sps(series, widths, L, 7.0, cap=1 << 16)
+        return time.perf_counter() - t0
+
+    avail = x_host.shape[0] - D
+    el = run(cal_t)
+    T = int(max(min_t, min(avail, cal_t * target_s / max(el, 1e-3))))
+    el = run(T)
+    adds = d.shape[0] * d.shape[1] * T
+    return adds / el, T, el
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+# ----------------------------------------------------------------- arms
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and rank != 0:
+        return 0
+    cores = cpu_cores()
+    os.environ["OMP_NUM_THREADS"] = str(cores)
+    import oracle
+    from paper_2605_03531_b300 import synth
+    cfg = workload()
+    d, D = oracle.delay_table(cfg.nchan, cfg.f_top, cfg.chan_bw, cfg.tsamp,
+                              cfg.dm_list())
+    budget = max(1.0, min(10.0, 150.0 / max(1, args.steps + args.warmup)))
+    # one bounded slice of the block, regenerated on the host
+    xfull = synth.noise_u8(32768 + D, cfg.nchan, cfg.seed).numpy()
+    rate0, T, _ = oracle_sample_rate(xfull, d, cfg.widths, cfg.norm_window,
+                                     target_s=budget)
+    x = np.ascontiguousarray(xfull[:T + D])
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        series = oracle.dedisperse(x, d)
+        oracle.sps(series, cfg.widths, cfg.norm_window, cfg.threshold, cap=1 << 16)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    step_s = sum(times) / len(times)
+    adds = cfg.ndm * cfg.nchan * T
+    value = adds / step_s
+    sample = (f"all {cfg.ndm} DM trials x first {T} output samples x "
+              f"{cfg.nchan} channels of the block per step (dedispersion + search)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": step_s * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic",
+            "config": workload_config(cfg, cfg.nsamp_out),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def traffic_record(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        rec = json.load(open(path))[kernel]
+    except (OSError, KeyError, ValueError):
+        return None
+    src = os.path.join(ROOT, "paper_2605_03531_b300", "csrc", rec["source"])
+    try:
+        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    if h != rec.get("source_sha256"):
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def run_ours(args):
+    import torch
+    from paper_2605_03531_b300 import Plan, build, synth
+    build.build()
+    world, rank, local = dist_setup(args.gpus)
+    dev = torch.device("cuda", local if world > 1 else 0)
+    cfg = workload()
+    if world > 1:
+        cfg.seed = cfg.seed + 1000 * rank   # each rank its own beam
+    plan = Plan(cfg.nchan, cfg.f_top, cfg.chan_bw, cfg.tsamp, cfg.dm_list(),
+                cfg.widths, nbits=8, norm_window=cfg.norm_window,
+                cand_capacity=1 << 20)
+    D = plan.max_delay
+    nout = cfg.nsamp_out
+    nin = nout + D
+    x = synth.noise_u8(nin, cfg.nchan, cfg.seed, device=dev)
+    synth.inject_pulses(x, cfg.pulses, cfg.f_top, cfg.chan_bw, cfg.tsamp, cfg.seed)
+    pitch = plan.cm_pitch(nout)
+    cm = torch.empty((cfg.nchan, pitch), dtype=torch.uint8, device=dev)
+    series = torch.empty((cfg.ndm, nout), dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    adds = cfg.nchan * nout * cfg.ndm
+
+    def step(ev=None):
+        if ev is not None:
+            ev[0].record(stream)
+        plan.unpack(x, pitch, out=cm, stream=stream)
+        if ev is not None:
+            ev[1].record(stream)
+        plan.dedisperse_cm(cm, pitch, nout, out=series, stream=stream)
+        if ev is not None:
+            ev[2].record(stream)
+        plan.single_pulse_search(series, cfg.threshold, stream=stream)
+        if ev is not None:
+            ev[3].record(stream)
+        return plan.fetch()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)]
+           for _ in range(args.steps)]
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    idx = dev.index if dev.index is not None else 0
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    smi_index = vis.split(",")[idx] if vis and vis.split(",")[idx].isdigit() else idx
+    clocks = ClockSampler(smi_index)
+    clocks.start()
+    time.sleep(0.5)
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    start.record(stream)
+    ncand = 0
+    for i in range(args.steps):
+        _, ncand = step(evs[i])
+    end.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    ck = clocks.stop()
+    ms_total = start.elapsed_time(end)
+    ms_total = max_over_ranks(ms_total, world)
+    ms_step = ms_total / args.steps
+    k_unpack = statistics.mean(e[0].elapsed_time(e[1]) for e in evs)
+    k_dedisp = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
+    k_sps = statistics.mean(e[2].elapsed_time(e[3]) for e in evs)
+    value = world * adds / (ms_step * 1e-3)
+
+    # ---- end to end through the public call with host buffers
+    xh = torch.empty((nin, cfg.nchan), dtype=torch.uint8, pin_memory=True)
+    xh.copy_(x.cpu())
+    xd2 = torch.empty_like(x)
+    series2 = torch.empty_like(series)
+
+    def e2e_step():
+        xd2.copy_(xh, non_blocking=True)
+        plan.dedisperse(xd2, out=series2, stream=stream)
+        plan.single_pulse_search(series2, cfg.threshold, stream=stream)
+        return plan.fetch()
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    t0 = time.perf_counter()
+    nc2 = 0
+    for _ in range(args.steps):
+        _, nc2 = e2e_step()
+    torch.cuda.synchronize(dev)
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world) / args.steps
+    e2e = {"value": world * adds / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": int(nin * cfg.nchan),
+           "d2h_bytes_per_step": int(4 + 16 * nc2), "ms_per_step": e2e_s * 1e3}
+
+    sm_mhz = ck["sm_mhz"] if ck else None
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    clk = sm_mhz or peaks.get("sm_max_mhz", 2032.0)
+    peak = SM_COUNT_B300 * ADDS_PER_SM_CLK * clk * 1e6 / 1e12
+    achieved = adds / (k_dedisp * 1e-3) / 1e12
+    traffic = traffic_record("dedisp")
+    hbm_peak = peaks.get("hbm_gbs", 6400.0)
+    sps_bytes = 4.0 * cfg.ndm * nout + 16 * ncand
+    unpack_bytes = 2.0 * nin * cfg.nchan
+    result = None
+    if rank == 0:
+        result = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int32", "data": "synthetic",
+            "config": workload_config(cfg, nout),
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
+                         "unit": "Tadd/s", "frac": achieved / peak,
+                         "traffic": traffic,
+                         "kernel": "dedisp_kernel",
+                         "peak_basis": f"{SM_COUNT_B300} SMs x {ADDS_PER_SM_CLK} "
+                                       f"adds/clk x {clk:.0f} MHz "
+                                       "(median SM clock sampled in the timed region)"},
+            "kernels": {
+                "unpack_ms": k_unpack, "dedisp_ms": k_dedisp, "sps_ms": k_sps,
+                "unpack_hbm_frac": unpack_bytes / (k_unpack * 1e-3) / 1e9 / hbm_peak,
+                "sps_hbm_frac": sps_bytes / (k_sps * 1e-3) / 1e9 / hbm_peak,
+                "hbm_peak_gbs": hbm_peak},
+            "candidates_per_step": int(ncand),
+            "e2e": e2e,
+            "gpu_launches": 3 * args.steps,
+            "clocks": ck,
+        }
+    if rank == 0 and not args.no_cpu_baseline:
+        cores = cpu_cores()
+        os.environ["OMP_NUM_THREADS"] = str(cores)
+        d = plan.delays()
+        xs = x[:min(nin, 65536 + D)].cpu().numpy()
+        rate, T, el = oracle_sample_rate(xs, d, cfg.widths, cfg.norm_window,
+                                         target_s=args.cpu_seconds)
+        result["cpu_baseline"] = {
+            "value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"all {cfg.ndm} DM trials x first {T} output samples x "
+                      f"{cfg.nchan} channels (dedispersion + search), "
+                      f"{el:.1f} s"}
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

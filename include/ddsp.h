@@ -1,0 +1,204 @@
+/*
+ * ddsp.h -- C ABI of the B300 (sm_103a) brute-force dedispersion and boxcar
+ * single-pulse search library (libddsp.so).
+ *
+ * The method is the hot path of a radio transient / pulsar search:
+ *   1. the dispersion delay of every (trial DM, channel) pair from the cold-
+ *      plasma law of Ch.1 Eq.1, dt = 4148.808 s MHz^2 * DM * (f^-2 - f_ref^-2),
+ *      rounded to the nearest sample (ties away from zero);
+ *   2. brute-force incoherent dedispersion (Sec.3.2): every trial is the sum
+ *      over channels of the channel's samples shifted by its delay;
+ *   3. the single-pulse search (Sec.2.1): time-domain boxcar filtering of
+ *      every dedispersed series, normalised by a robust median / MAD noise
+ *      estimate (Sec.3.3), keeping the samples whose S/N reaches a user
+ *      threshold.
+ *
+ * Conventions shared by every call
+ *   - All pointers named d_* are DEVICE pointers owned by the caller (for
+ *     example the data_ptr() of a CUDA tensor); all others are host pointers
+ *     owned by the caller.  The plan owns its own workspaces.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls that
+ *     take a stream are asynchronous and stream-ordered: they return once the
+ *     work is enqueued.  ddsp_candidates_fetch and the *_get_* calls
+ *     synchronise.
+ *   - Every call returns DDSP_OK (0) or a negative DDSP_E_* code; no C++
+ *     exception crosses this boundary.  A plan is not thread-safe: use one
+ *     plan per host thread / stream.
+ *   - Frequencies are in MHz, times in seconds, DMs in pc cm^-3.
+ */
+#ifndef DDSP_H
+#define DDSP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *ddsp_stream_t; /* same type as cudaStream_t */
+typedef struct ddsp_plan ddsp_plan;        /* opaque; owned by the library */
+
+/* One single-pulse candidate (Sec.2.1): DM-trial index into the plan's DM
+ * list, output sample t (sample of arrival at the highest channel
+ * frequency), index of the best boxcar width into the plan's width list, and
+ * that width's S/N in FP32. */
+typedef struct {
+    uint32_t dm_idx;
+    uint32_t t;
+    uint32_t w_idx;
+    float snr;
+} ddsp_cand;
+
+enum {
+    DDSP_OK = 0,
+    DDSP_E_INVALID_ARG = -1, /* bad argument (see each call)                     */
+    DDSP_E_SHAPE = -2,       /* input too short / too long for the plan          */
+    DDSP_E_CUDA = -3,        /* a CUDA runtime call or kernel launch failed      */
+    DDSP_E_NOMEM = -4,       /* device or host allocation failed                 */
+    DDSP_E_TIMEOUT = -5,     /* a bounded device wait expired (kernel returned)  */
+    DDSP_E_TRUNCATED = -6,   /* more candidates than capacity; count still exact */
+    DDSP_E_RANGE = -7,       /* a series window spans >= 2^31 (MAD undefined)    */
+    DDSP_E_STATE = -8        /* call out of order (e.g. fetch before a search)   */
+};
+
+/*
+ * ddsp_plan_create -- validate the search parameters and build the plan.
+ *
+ *   nchan        channels (> 0); channel c is centred at f_top + c*chan_bw
+ *   f_top_mhz    frequency of channel 0 (> 0)
+ *   chan_bw_mhz  channel spacing, non-zero, either sign
+ *   tsamp_s      sampling time (> 0)
+ *   dm_list      ndm trial DMs (finite, >= 0), any order; host array, copied
+ *   widths       nwidths boxcar widths, each a power of two in [1, 1024],
+ *                strictly increasing; host array, copied
+ *   nbits        8 or 16: sample type of the filterbank (uint8 / uint16)
+ *   norm_window  L, samples per median/MAD window (0 = one window over the
+ *                whole series); windows are [jL,(j+1)L), the last one
+ *                extended to the end of the series
+ *   cand_capacity  candidate records kept per search (> 0)
+ *
+ * The delay table d[k][c] = round_half_away(4148.808*DM_k*(f_c^-2 -
+ * f_ref^-2)/tsamp) (Ch.1 Eq.1, f_ref the highest channel frequency) is built
+ * on the host in FP64 and copied to the device.  Returns DDSP_E_INVALID_ARG
+ * for any bad argument, DDSP_E_NOMEM / DDSP_E_CUDA on allocation failure.
+ * On success *out owns every plan resource until ddsp_plan_destroy.
+ */
+int ddsp_plan_create(ddsp_plan **out, int nchan, double f_top_mhz,
+                     double chan_bw_mhz, double tsamp_s, const double *dm_list,
+                     int ndm, const int *widths, int nwidths, int nbits,
+                     int64_t norm_window, size_t cand_capacity);
+
+/* The delay table alone, on the host, without a plan or a GPU: the same
+ * FP64 expression ddsp_plan_create uses (Ch.1 Eq.1).  host_out[ndm*nchan]
+ * receives d[k][c]; *max_delay (may be NULL) receives D.  Arguments are
+ * checked as in ddsp_plan_create. */
+int ddsp_delay_table(int nchan, double f_top_mhz, double chan_bw_mhz,
+                     double tsamp_s, const double *dm_list, int ndm,
+                     int32_t *host_out, int32_t *max_delay);
+
+/* Output samples per trial for nsamp_in input samples: N_out = N_in - D,
+ * D the largest delay of the plan.  DDSP_E_SHAPE if N_out <= 0. */
+int ddsp_plan_nsamp_out(const ddsp_plan *plan, int64_t nsamp_in, int64_t *nsamp_out);
+
+/* Largest delay D (samples) over the whole (DM, channel) grid. */
+int ddsp_plan_max_delay(const ddsp_plan *plan, int32_t *max_delay);
+
+/* Copy the plan's delay table into host_out[ndm*nchan], row k = DM trial k in
+ * the order given to ddsp_plan_create. */
+int ddsp_plan_get_delays(const ddsp_plan *plan, int32_t *host_out);
+
+/* Unpack (step 2 of the path): time-major spectra d_in[nsamp_in][nchan]
+ * (uint8 or uint16 as the plan's nbits, the block layout of Sec.2.2) into
+ * channel-major rows d_out[nchan][pitch] of the same type; samples
+ * nsamp_in..pitch-1 of every row are written as zero.  pitch >= nsamp_in and
+ * a multiple of 128; d_in and d_out 16-byte aligned. */
+int ddsp_unpack(ddsp_plan *plan, const void *d_in, int64_t nsamp_in,
+                void *d_out, int64_t pitch, ddsp_stream_t stream);
+
+/* Dedisperse (Sec.3.2): d_out[k][t] = sum_c in[t + d[k][c]][c] for every DM
+ * trial k (plan order) and t in [0, N_out), N_out = nsamp_in - D, exact in
+ * int32.  d_in: time-major spectra [nsamp_in][nchan] (uint8/uint16), 16-byte
+ * aligned.  d_out: int32 [ndm][N_out], rows contiguous.  Runs the unpack
+ * kernel into a plan-owned channel-major workspace (grown on demand with
+ * cudaMalloc, so the first call for a new size synchronises) and then the
+ * dedispersion kernel.  DDSP_E_SHAPE if N_out <= 0. */
+int ddsp_dedisperse(ddsp_plan *plan, const void *d_in, int64_t nsamp_in,
+                    int32_t *d_out, ddsp_stream_t stream);
+
+/* Dedisperse from channel-major rows already on the device (for example
+ * the output of ddsp_unpack, or a per-beam ring kept in that layout):
+ * d_cm[nchan][pitch] of the plan's sample type, 16-byte aligned; pitch a
+ * multiple of 128 and at least ddsp_plan_cm_pitch(nsamp_out); samples
+ * beyond nsamp_out + D of every row must be readable (they are read but do
+ * not reach any stored output).  d_out as in ddsp_dedisperse. */
+int ddsp_dedisperse_cm(ddsp_plan *plan, const void *d_cm, int64_t pitch,
+                       int64_t nsamp_out, int32_t *d_out, ddsp_stream_t stream);
+
+/* Smallest channel-major row pitch (samples) ddsp_dedisperse_cm accepts for
+ * nsamp_out output samples with the plan's current tile shape. */
+int ddsp_plan_cm_pitch(const ddsp_plan *plan, int64_t nsamp_out, int64_t *pitch);
+
+/* Single-pulse search (Sec.2.1 with the Sec.3.3 median noise estimate) over
+ * d_series[ndm][nsamp_out] (int32, e.g. the output of ddsp_dedisperse):
+ *   per (k, window j): m = median, MAD = median |x - m| (exact integers),
+ *     sigma = 1.482602218505602 * MAD;
+ *   per (k, t) and width w with t + w <= nsamp_out:
+ *     B_w(t) = sum_{i<w} x[t+i] (exact), S/N_w = (B_w - w*m)/(sigma*sqrt(w))
+ *     in FP32 (0 when MAD = 0), best = first width reaching the maximum;
+ *   a candidate is every (k, t) whose best S/N >= threshold (> 0).
+ * Candidates go to a plan-owned device buffer (capacity from plan creation);
+ * read them with ddsp_candidates_fetch.  Windows are processed on chip, so
+ * every window plus (max width - 1) samples must fit in 49152 samples;
+ * DDSP_E_SHAPE otherwise.  Boxcar sums must fit in int32. */
+int ddsp_single_pulse_search(ddsp_plan *plan, const int32_t *d_series,
+                             int64_t nsamp_out, float threshold,
+                             ddsp_stream_t stream);
+
+/* Same search without the threshold, for checking: per (k, t) writes the
+ * best width index (-1 where no width fits), its FP32 S/N and its boxcar sum
+ * B to d_best_w / d_best_snr / d_best_sum, each [ndm][nsamp_out]. */
+int ddsp_single_pulse_search_dense(ddsp_plan *plan, const int32_t *d_series,
+                                   int64_t nsamp_out, int32_t *d_best_w,
+                                   float *d_best_snr, int32_t *d_best_sum,
+                                   ddsp_stream_t stream);
+
+/* Copy the per-(DM, window) statistics of the last search to the host:
+ * m2[k*nwin + j] = 2*median, mad4[k*nwin + j] = 4*MAD (both exact).  *nwin
+ * receives the window count.  Synchronises the last search's stream.
+ * host arrays may be NULL to query *nwin only. */
+int ddsp_plan_get_stats(ddsp_plan *plan, int64_t *m2, int64_t *mad4,
+                        int64_t cap, int64_t *nwin);
+
+/* Wait for the last search, copy up to min(cap, capacity) candidates to
+ * host_buf sorted by (dm_idx, t), and set *n_total to the true number found.
+ * Returns DDSP_E_TRUNCATED when *n_total exceeds what was copied (the copied
+ * records are then the first ones the device stored, sorted),
+ * DDSP_E_TIMEOUT / DDSP_E_RANGE if a kernel reported one, DDSP_E_STATE if no
+ * search ran. */
+int ddsp_candidates_fetch(ddsp_plan *plan, ddsp_cand *host_buf, size_t cap,
+                          size_t *n_total);
+
+/* Synchronise `stream` and report any error a kernel of this plan recorded
+ * on the device (DDSP_E_TIMEOUT, DDSP_E_RANGE), then clear it. */
+int ddsp_plan_check(ddsp_plan *plan, ddsp_stream_t stream);
+
+/* Release every resource of the plan (NULL is ignored). */
+void ddsp_plan_destroy(ddsp_plan *plan);
+
+/* Static, human-readable text for a DDSP_* code. */
+const char *ddsp_error_string(int code);
+
+/* Tile shape of the dedispersion kernel: dm_tile DM trials x time_tile
+ * samples per block, chan_chunk channels staged per pipeline stage.  A
+ * value of 0 lets the library choose.  Returns DDSP_E_INVALID_ARG for a
+ * shape the kernel does not implement or that does not fit on chip. */
+int ddsp_plan_set_tile(ddsp_plan *plan, int dm_tile, int chan_chunk);
+int ddsp_plan_get_tile(const ddsp_plan *plan, int *dm_tile, int *time_tile,
+                       int *chan_chunk);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DDSP_H */

@@ -1,0 +1,227 @@
+"""B300-native brute-force dedispersion and boxcar single-pulse search.
+
+Python side of the C ABI in ``include/ddsp.h``: argument marshalling only.
+Every step of the path (unpack, dedispersion, window statistics, boxcar S/N,
+candidate compaction) runs in the CUDA kernels of ``libddsp.so``; PyTorch
+provides device memory and streams.  Importing this package does not load
+the library; the first ``Plan`` does, and fails loudly if it is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import DdspError, DdspCand
+
+__all__ = ["Plan", "DdspError", "CAND_DTYPE", "delay_table"]
+
+CAND_DTYPE = np.dtype([("dm_idx", np.uint32), ("t", np.uint32),
+                       ("w_idx", np.uint32), ("snr", np.float32)])
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _dev_ptr(t, dtype=None, what="tensor"):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{what} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{what} must be {dtype}, got {t.dtype}")
+    return C.c_void_p(t.data_ptr())
+
+
+def delay_table(nchan, f_top, chan_bw, tsamp, dm_list):
+    """(d[k][c] int32, D) from the library's host-side delay code."""
+    dms = np.ascontiguousarray(dm_list, dtype=np.float64)
+    d = np.empty((dms.size, int(nchan)), dtype=np.int32)
+    D = C.c_int32()
+    _lib.check(_lib.lib().ddsp_delay_table(
+        int(nchan), float(f_top), float(chan_bw), float(tsamp),
+        dms.ctypes.data_as(C.c_void_p), int(dms.size),
+        d.ctypes.data_as(C.c_void_p), C.byref(D)), "ddsp_delay_table")
+    return d, D.value
+
+
+class Plan:
+    """A dedispersion + single-pulse-search plan (``ddsp_plan_create``)."""
+
+    def __init__(self, nchan, f_top, chan_bw, tsamp, dm_list, widths,
+                 nbits=8, norm_window=8192, cand_capacity=1 << 20):
+        self._h = C.c_void_p()
+        L = _lib.lib()
+        dms = np.ascontiguousarray(dm_list, dtype=np.float64)
+        ws = np.ascontiguousarray(widths, dtype=np.int32)
+        _lib.check(L.ddsp_plan_create(
+            C.byref(self._h), int(nchan), float(f_top), float(chan_bw),
+            float(tsamp), dms.ctypes.data_as(C.c_void_p), int(dms.size),
+            ws.ctypes.data_as(C.c_void_p), int(ws.size), int(nbits),
+            int(norm_window), int(cand_capacity)), "ddsp_plan_create")
+        self.nchan, self.ndm, self.nbits = int(nchan), int(dms.size), int(nbits)
+        self.widths = [int(w) for w in ws]
+        self.norm_window = int(norm_window)
+        self.cand_capacity = int(cand_capacity)
+
+    # ---------------------------------------------------------------- info
+    @property
+    def max_delay(self) -> int:
+        D = C.c_int32()
+        _lib.check(_lib.lib().ddsp_plan_max_delay(self._h, C.byref(D)),
+                   "ddsp_plan_max_delay")
+        return D.value
+
+    def nsamp_out(self, nsamp_in) -> int:
+        n = C.c_int64()
+        _lib.check(_lib.lib().ddsp_plan_nsamp_out(self._h, int(nsamp_in),
+                                                  C.byref(n)),
+                   "ddsp_plan_nsamp_out")
+        return n.value
+
+    def delays(self) -> np.ndarray:
+        d = np.empty((self.ndm, self.nchan), dtype=np.int32)
+        _lib.check(_lib.lib().ddsp_plan_get_delays(
+            self._h, d.ctypes.data_as(C.c_void_p)), "ddsp_plan_get_delays")
+        return d
+
+    def set_tile(self, dm_tile=0, chan_chunk=0):
+        _lib.check(_lib.lib().ddsp_plan_set_tile(self._h, int(dm_tile),
+                                                 int(chan_chunk)),
+                   "ddsp_plan_set_tile")
+
+    def get_tile(self):
+        a, b, c = C.c_int(), C.c_int(), C.c_int()
+        _lib.check(_lib.lib().ddsp_plan_get_tile(self._h, C.byref(a),
+                                                 C.byref(b), C.byref(c)),
+                   "ddsp_plan_get_tile")
+        return a.value, b.value, c.value
+
+    # ---------------------------------------------------------------- path
+    def _in_dtype(self):
+        import torch
+        return torch.uint8 if self.nbits == 8 else torch.uint16
+
+    def unpack(self, x, pitch, out=None, stream=None):
+        import torch
+        nin = x.shape[0]
+        if out is None:
+            out = torch.empty((self.nchan, pitch), dtype=x.dtype, device=x.device)
+        _lib.check(_lib.lib().ddsp_unpack(
+            self._h, _dev_ptr(x, self._in_dtype(), "spectra"), int(nin),
+            _dev_ptr(out, self._in_dtype(), "out"), int(pitch),
+            _stream_handle(stream)), "ddsp_unpack")
+        return out
+
+    def dedisperse(self, x, out=None, stream=None):
+        """x: CUDA tensor [nsamp_in][nchan] (uint8/uint16) -> int32
+        [ndm][nsamp_out]."""
+        import torch
+        if x.dim() != 2 or x.shape[1] != self.nchan:
+            raise ValueError("spectra must be [nsamp_in][nchan]")
+        nin = x.shape[0]
+        nout = self.nsamp_out(nin)
+        if out is None:
+            out = torch.empty((self.ndm, nout), dtype=torch.int32, device=x.device)
+        elif tuple(out.shape) != (self.ndm, nout):
+            raise ValueError("out must be [ndm][nsamp_out]")
+        _lib.check(_lib.lib().ddsp_dedisperse(
+            self._h, _dev_ptr(x, self._in_dtype(), "spectra"), int(nin),
+            _dev_ptr(out, torch.int32, "out"), _stream_handle(stream)),
+            "ddsp_dedisperse")
+        return out
+
+    def cm_pitch(self, nsamp_out) -> int:
+        v = C.c_int64()
+        _lib.check(_lib.lib().ddsp_plan_cm_pitch(self._h, int(nsamp_out),
+                                                 C.byref(v)),
+                   "ddsp_plan_cm_pitch")
+        return v.value
+
+    def dedisperse_cm(self, cm, pitch, nsamp_out, out=None, stream=None):
+        """Dedisperse channel-major rows cm[nchan][pitch] already on the GPU."""
+        import torch
+        if out is None:
+            out = torch.empty((self.ndm, nsamp_out), dtype=torch.int32,
+                              device=cm.device)
+        _lib.check(_lib.lib().ddsp_dedisperse_cm(
+            self._h, _dev_ptr(cm, self._in_dtype(), "cm"), int(pitch),
+            int(nsamp_out), _dev_ptr(out, torch.int32, "out"),
+            _stream_handle(stream)), "ddsp_dedisperse_cm")
+        return out
+
+    def single_pulse_search(self, series, threshold, stream=None):
+        import torch
+        if series.dim() != 2 or series.shape[0] != self.ndm:
+            raise ValueError("series must be [ndm][nsamp_out]")
+        _lib.check(_lib.lib().ddsp_single_pulse_search(
+            self._h, _dev_ptr(series, torch.int32, "series"),
+            int(series.shape[1]), float(threshold), _stream_handle(stream)),
+            "ddsp_single_pulse_search")
+
+    def search_dense(self, series, stream=None):
+        """Per-sample best width index, FP32 S/N and boxcar sum."""
+        import torch
+        n = series.shape[1]
+        bw = torch.empty((self.ndm, n), dtype=torch.int32, device=series.device)
+        bs = torch.empty((self.ndm, n), dtype=torch.float32, device=series.device)
+        bsum = torch.empty((self.ndm, n), dtype=torch.int32, device=series.device)
+        _lib.check(_lib.lib().ddsp_single_pulse_search_dense(
+            self._h, _dev_ptr(series, torch.int32, "series"), int(n),
+            _dev_ptr(bw), _dev_ptr(bs), _dev_ptr(bsum), _stream_handle(stream)),
+            "ddsp_single_pulse_search_dense")
+        return bw, bs, bsum
+
+    def fetch(self, cap=None, allow_truncated=False):
+        """(candidates sorted by (dm_idx, t), true count)."""
+        if cap is None:
+            cap = self.cand_capacity
+        buf = np.zeros(cap, dtype=CAND_DTYPE)
+        n = C.c_size_t()
+        rc = _lib.lib().ddsp_candidates_fetch(
+            self._h, buf.ctypes.data_as(C.c_void_p), int(cap), C.byref(n))
+        if rc == _lib.DDSP_E_TRUNCATED and allow_truncated:
+            return buf[:min(cap, self.cand_capacity)], n.value
+        _lib.check(rc, "ddsp_candidates_fetch")
+        return buf[:n.value].copy(), n.value
+
+    def stats(self):
+        """Per-(DM, window) exact (2*median, 4*MAD) of the last search."""
+        nwin = C.c_int64()
+        L = _lib.lib()
+        _lib.check(L.ddsp_plan_get_stats(self._h, None, None, 0, C.byref(nwin)),
+                   "ddsp_plan_get_stats")
+        m2 = np.empty((self.ndm, nwin.value), dtype=np.int64)
+        mad4 = np.empty((self.ndm, nwin.value), dtype=np.int64)
+        _lib.check(L.ddsp_plan_get_stats(
+            self._h, m2.ctypes.data_as(C.c_void_p),
+            mad4.ctypes.data_as(C.c_void_p), m2.size, C.byref(nwin)),
+            "ddsp_plan_get_stats")
+        return m2, mad4
+
+    def check(self, stream=None):
+        _lib.check(_lib.lib().ddsp_plan_check(self._h, _stream_handle(stream)),
+                   "ddsp_plan_check")
+
+    def close(self):
+        if self._h:
+            _lib.lib().ddsp_plan_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

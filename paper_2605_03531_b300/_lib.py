@@ -1,0 +1,89 @@
+"""ctypes declarations of the C ABI in include/ddsp.h (libddsp.so).
+
+There is no fallback: if the compiled library is missing, ``lib()`` raises.
+Build it with ``python -m paper_2605_03531_b300.build``.
+"""
+import ctypes as C
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libddsp.so")
+
+DDSP_OK = 0
+DDSP_E_INVALID_ARG = -1
+DDSP_E_SHAPE = -2
+DDSP_E_CUDA = -3
+DDSP_E_NOMEM = -4
+DDSP_E_TIMEOUT = -5
+DDSP_E_TRUNCATED = -6
+DDSP_E_RANGE = -7
+DDSP_E_STATE = -8
+
+
+class DdspCand(C.Structure):
+    _fields_ = [("dm_idx", C.c_uint32), ("t", C.c_uint32),
+                ("w_idx", C.c_uint32), ("snr", C.c_float)]
+
+
+P = C.c_void_p
+I64 = C.c_int64
+I32 = C.c_int
+PI64 = C.POINTER(C.c_int64)
+
+# name -> (restype, argtypes); the same list the header declares
+SIGNATURES = {
+    "ddsp_plan_create": (I32, [C.POINTER(P), I32, C.c_double, C.c_double,
+                               C.c_double, P, I32, P, I32, I32, I64, C.c_size_t]),
+    "ddsp_delay_table": (I32, [I32, C.c_double, C.c_double, C.c_double, P,
+                               I32, P, C.POINTER(C.c_int32)]),
+    "ddsp_plan_nsamp_out": (I32, [P, I64, PI64]),
+    "ddsp_plan_max_delay": (I32, [P, C.POINTER(C.c_int32)]),
+    "ddsp_plan_get_delays": (I32, [P, P]),
+    "ddsp_unpack": (I32, [P, P, I64, P, I64, P]),
+    "ddsp_dedisperse": (I32, [P, P, I64, P, P]),
+    "ddsp_dedisperse_cm": (I32, [P, P, I64, I64, P, P]),
+    "ddsp_plan_cm_pitch": (I32, [P, I64, PI64]),
+    "ddsp_single_pulse_search": (I32, [P, P, I64, C.c_float, P]),
+    "ddsp_single_pulse_search_dense": (I32, [P, P, I64, P, P, P, P]),
+    "ddsp_plan_get_stats": (I32, [P, P, P, I64, PI64]),
+    "ddsp_candidates_fetch": (I32, [P, P, C.c_size_t, C.POINTER(C.c_size_t)]),
+    "ddsp_plan_check": (I32, [P, P]),
+    "ddsp_plan_destroy": (None, [P]),
+    "ddsp_error_string": (C.c_char_p, [I32]),
+    "ddsp_plan_set_tile": (I32, [P, I32, I32]),
+    "ddsp_plan_get_tile": (I32, [P, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                 C.POINTER(C.c_int)]),
+}
+
+_lib = None
+
+
+def lib():
+    """The loaded libddsp.so with every exported signature declared."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(
+                f"{LIB_PATH} is missing: build it with "
+                "`python -m paper_2605_03531_b300.build` (there is no CPU "
+                "fallback)")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+class DdspError(RuntimeError):
+    def __init__(self, code, call):
+        self.code = code
+        msg = lib().ddsp_error_string(code).decode()
+        super().__init__(f"{call} failed: {msg} ({code})")
+
+
+def check(code, call):
+    if code != DDSP_OK:
+        raise DdspError(code, call)
+    return code

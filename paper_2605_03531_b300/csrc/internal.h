@@ -1,0 +1,103 @@
+// internal.h -- plan layout and kernel launchers shared by the library's
+// translation units (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "ddsp.h"
+
+namespace ddsp {
+
+// Device-side error word values (plan->d_err).
+enum : int32_t { kErrNone = 0, kErrTimeout = 1, kErrRange = 2 };
+
+// Dedispersion kernel geometry: 8 warps per block, each thread owns
+// kDmPerThread DM trials x kElemPerThread interleaved elements.
+constexpr int kThreads = 256;
+constexpr int kDmPerThread = 4;
+constexpr int kElemPerThread = 4;
+
+struct DedispTile {
+  int wt = 0;          // warps along time
+  int wd = 0;          // warps along DM
+  int chan_chunk = 0;  // channels staged per pipeline stage
+  int dm_tile() const { return wd * kDmPerThread; }
+  // elements per row segment: 32 lanes x kElemPerThread x wt
+  int seg(int) const { return 32 * kElemPerThread * wt; }
+};
+
+struct DedispTables {
+  // per (DM tile g, channel c): window start (multiple of 16, samples
+  // relative to the block's first output sample), bytes to copy, and the
+  // element-byte offsets of the tile's DM trials.
+  int n_dm_tiles = 0;
+  int dm_tile = 0;
+  int span_max = 0;           // max over (g, c) of (dhi - wbase)
+  int32_t *d_wbase = nullptr; // [n_dm_tiles][nchan]
+  int32_t *d_relb = nullptr;  // [n_dm_tiles][nchan][dm_tile], bytes
+  int32_t *d_rowmap = nullptr;// [n_dm_tiles*dm_tile] output row (-1 = pad)
+};
+
+struct Plan {
+  int device = 0;
+  int nchan = 0, ndm = 0, nbits = 8, nwidths = 0;
+  double f_top = 0, chan_bw = 0, tsamp = 0;
+  std::vector<double> dms;
+  std::vector<int> widths;
+  int64_t norm_window = 0;
+  size_t cand_capacity = 0;
+
+  std::vector<int32_t> delays;  // [ndm][nchan], plan order
+  int32_t max_delay = 0;
+  std::vector<int> order;       // DM trials sorted by DM value
+
+  DedispTile tile;       // wt == 0: no staged tile fits, use the direct kernel
+  DedispTables tab;
+  int32_t *d_delays = nullptr;  // [ndm][nchan] device copy (direct kernel)
+
+  // channel-major workspace
+  void *d_cm = nullptr;
+  size_t cm_bytes = 0;
+
+  // search workspace
+  int64_t *d_m2 = nullptr, *d_mad4 = nullptr;
+  size_t stats_cap = 0;
+  int64_t last_nwin = 0;
+  ddsp_cand *d_cands = nullptr;
+  uint32_t *d_count = nullptr;
+  int32_t *d_err = nullptr;
+  int32_t *d_widths = nullptr;
+  bool searched = false;
+  cudaStream_t last_stream = nullptr;
+};
+
+// ---- launchers (each returns a cudaError_t from the launch) ------------
+cudaError_t launch_unpack(const void *d_in, int64_t nsamp_in, int nchan,
+                          int nbits, void *d_out, int64_t pitch,
+                          cudaStream_t s);
+
+cudaError_t launch_dedisperse(const Plan &p, const void *d_cm, int64_t pitch,
+                              int64_t nsamp_out, int32_t *d_out,
+                              cudaStream_t s);
+cudaError_t launch_dedisperse_direct(const Plan &p, const void *d_cm,
+                                     int64_t pitch, int64_t nsamp_out,
+                                     int32_t *d_out, cudaStream_t s);
+int dedisp_time_tile(const DedispTile &t, int nbits);
+
+size_t dedisp_smem_bytes(const DedispTile &t, int span_max, int nbits);
+
+cudaError_t launch_sps(const Plan &p, const int32_t *d_series,
+                       int64_t nsamp_out, float threshold, bool dense,
+                       int32_t *d_best_w, float *d_best_snr,
+                       int32_t *d_best_sum, cudaStream_t s);
+
+int64_t sps_max_window_samples();
+
+}  // namespace ddsp
+
+struct ddsp_plan {
+  ddsp::Plan p;
+};

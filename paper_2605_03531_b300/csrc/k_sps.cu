@@ -1,0 +1,391 @@
+// k_sps.cu -- boxcar single-pulse search (Sec.2.1) with the robust median /
+// MAD noise estimate of Sec.3.3, fused into one kernel: one block per
+// (DM trial k, normalisation window j).
+//
+//   1. load the window x[lo, hi) plus (w_max - 1) samples of look-ahead into
+//      shared memory (the series is read from HBM once);
+//   2. exact median and MAD of the window by histogram selection on integer
+//      keys: a 2048-bin shared histogram over the current key range narrows
+//      it by 2^11 per pass until the bin holding the wanted order statistic
+//      is one key wide (or the two middle order statistics fall in different
+//      bins: then max of the lower bin and min of the upper bin);
+//      m2 = 2*median, mad4 = 4*MAD are kept as exact integers;
+//   3. y = x - floor(median) and an inclusive prefix sum Q of y in uint32
+//      (modular, so every boxcar sum B_w(t) - w*floor(median) = Q[t+w]-Q[t]
+//      is exact), computed with warp-shuffle scans;
+//   4. per sample an integer screen against per-width thresholds derived
+//      from the S/N threshold with a small safety margin, then for the
+//      survivors the FP32 S/N of every width, the best one (first maximum),
+//      and candidate emission with one atomicAdd per warp (ballot + popc).
+// Memory traffic is 4 bytes per series sample read once (plus the look-ahead)
+// and 16 bytes per candidate: the kernel is bounded by HBM bandwidth.
+#include <math.h>
+
+#include "internal.h"
+
+namespace ddsp {
+namespace {
+
+constexpr int kSpsThreads = 512;
+constexpr int kWarps = kSpsThreads / 32;
+constexpr int kBins = 2048;
+constexpr int kMaxWidths = 11;  // 1 .. 1024
+constexpr int64_t kMaxWindowSamples = 49152;
+constexpr float kMadToSigma = 1.482602218505602f;
+
+struct SpsShared {
+  uint32_t hist[kBins];
+  uint32_t wred[kWarps][2];
+  int64_t bc[4];      // broadcast slots
+  float inv[kMaxWidths];
+  int32_t thr_by[kMaxWidths];
+  uint32_t wsum[kWarps];
+};
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t u = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += u;
+  }
+  return v;
+}
+
+// Block-wide min & max of a per-thread pair (int64).
+__device__ void block_minmax(int64_t &mn, int64_t &mx, SpsShared &sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    mn = min(mn, (int64_t)__shfl_xor_sync(0xffffffffu, (long long)mn, o));
+    mx = max(mx, (int64_t)__shfl_xor_sync(0xffffffffu, (long long)mx, o));
+  }
+  __shared__ int64_t red[kWarps][2];
+  if (lane == 0) {
+    red[warp][0] = mn;
+    red[warp][1] = mx;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int64_t a = red[0][0], b = red[0][1];
+    for (int w = 1; w < kWarps; ++w) {
+      a = min(a, red[w][0]);
+      b = max(b, red[w][1]);
+    }
+    sh.bc[0] = a;
+    sh.bc[1] = b;
+  }
+  __syncthreads();
+  mn = sh.bc[0];
+  mx = sh.bc[1];
+  __syncthreads();
+}
+
+// Exact order statistics of rank r1 and r2 = r1 or r1 + 1 (0-based) of n
+// uint32 keys produced by key(i), all <= kmax.  Returns them in k1, k2.
+template <typename KeyFn>
+__device__ void select2(KeyFn key, int n, int r1, int r2, uint32_t kmax,
+                        SpsShared &sh, uint32_t &k1, uint32_t &k2) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  uint32_t lo = 0;
+  uint64_t span = (uint64_t)kmax + 1;
+  int below = 0;
+  while (true) {
+    int s = 0;
+    while (((span - 1) >> s) >= (uint64_t)kBins) ++s;
+    const int nb = (int)((span - 1) >> s) + 1;
+    for (int b = tid; b < nb; b += kSpsThreads) sh.hist[b] = 0;
+    __syncthreads();
+    for (int i = tid; i < n; i += kSpsThreads) {
+      uint32_t k = key(i);
+      uint64_t d = (uint64_t)(k - lo);
+      if (k >= lo && d < span) atomicAdd(&sh.hist[d >> s], 1u);
+    }
+    __syncthreads();
+    // exclusive scan of the histogram: each thread owns 4 consecutive bins
+    uint32_t c[4], tsum = 0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int b = 4 * tid + q;
+      c[q] = (b < nb) ? sh.hist[b] : 0;
+      tsum += c[q];
+    }
+    uint32_t incl = warp_incl_scan(tsum, lane);
+    if (lane == 31) sh.wsum[warp] = incl;
+    __syncthreads();
+    uint32_t wpre = 0;
+    for (int w = 0; w < warp; ++w) wpre += sh.wsum[w];
+    uint32_t run = wpre + incl - tsum;  // keys of this window below bin 4*tid
+    const uint32_t q1 = (uint32_t)(r1 - below), q2 = (uint32_t)(r2 - below);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      int b = 4 * tid + q;
+      if (b < nb && c[q] > 0) {
+        if (q1 >= run && q1 < run + c[q]) {
+          sh.bc[0] = b;
+          sh.bc[2] = run;
+        }
+        if (q2 >= run && q2 < run + c[q]) {
+          sh.bc[1] = b;
+          sh.bc[3] = run;
+        }
+      }
+      run += c[q];
+    }
+    __syncthreads();
+    const int b1 = (int)sh.bc[0], b2 = (int)sh.bc[1];
+    const int run1 = (int)sh.bc[2];
+    __syncthreads();
+    if (s == 0) {
+      k1 = lo + (uint32_t)b1;
+      k2 = lo + (uint32_t)b2;
+      return;
+    }
+    if (b1 == b2) {
+      below += run1;
+      lo += (uint32_t)b1 << s;
+      uint64_t rest = span - ((uint64_t)b1 << s);
+      span = min((uint64_t)1 << s, rest);
+      continue;
+    }
+    // r2 = r1 + 1 sits in a later bin: k1 = max of bin b1, k2 = min of bin b2
+    uint32_t mx = 0, mn = 0xffffffffu;
+    for (int i = tid; i < n; i += kSpsThreads) {
+      uint32_t k = key(i);
+      uint64_t d = (uint64_t)(k - lo);
+      if (k >= lo && d < span) {
+        int b = (int)(d >> s);
+        if (b == b1) mx = max(mx, k);
+        if (b == b2) mn = min(mn, k);
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+    }
+    if (lane == 0) {
+      sh.wred[warp][0] = mx;
+      sh.wred[warp][1] = mn;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      uint32_t a = 0, b = 0xffffffffu;
+      for (int w = 0; w < kWarps; ++w) {
+        a = max(a, sh.wred[w][0]);
+        b = min(b, sh.wred[w][1]);
+      }
+      sh.bc[0] = a;
+      sh.bc[1] = b;
+    }
+    __syncthreads();
+    k1 = (uint32_t)sh.bc[0];
+    k2 = (uint32_t)sh.bc[1];
+    __syncthreads();
+    return;
+  }
+}
+
+template <bool DENSE>
+__global__ void __launch_bounds__(kSpsThreads)
+sps_kernel(const int32_t *__restrict__ series, int64_t n, int64_t L,
+           int64_t nwin, const int32_t *__restrict__ widths, int nw, float thr,
+           int64_t *__restrict__ m2_out, int64_t *__restrict__ mad4_out,
+           ddsp_cand *__restrict__ cands, uint32_t *__restrict__ count,
+           uint32_t cap, int32_t *__restrict__ best_w,
+           float *__restrict__ best_snr, int32_t *__restrict__ best_sum,
+           int32_t *__restrict__ err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SpsShared &sh = *reinterpret_cast<SpsShared *>(smem_raw);
+  int32_t *buf = reinterpret_cast<int32_t *>(smem_raw + sizeof(SpsShared));
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t j = blockIdx.x;
+  const int k = blockIdx.y;
+  const int64_t lo = (L <= 0) ? 0 : j * L;
+  const int64_t hi = (L <= 0 || j == nwin - 1) ? n : (j + 1) * L;
+  const int wmax = widths[nw - 1];
+  const int64_t ext = min(hi + wmax - 1, n);
+  const int len = (int)(hi - lo), elen = (int)(ext - lo);
+  const int32_t *x = series + (int64_t)k * n + lo;
+
+  // ---- 1. load (buf[0] is the zero prefix slot)
+  int64_t mn = INT64_MAX, mx = INT64_MIN;
+  for (int i = tid; i < elen; i += kSpsThreads) {
+    int32_t v = __ldg(x + i);
+    buf[1 + i] = v;
+    if (i < len) {
+      mn = min(mn, (int64_t)v);
+      mx = max(mx, (int64_t)v);
+    }
+  }
+  if (tid == 0) buf[0] = 0;
+  __syncthreads();
+  block_minmax(mn, mx, sh);
+
+  // ---- 2. median and MAD
+  int64_t M2 = 0, MAD4 = 0;
+  const bool range_ok = (mx - mn) < (int64_t)1 << 31;
+  if (range_ok) {
+    const int r1 = (len - 1) / 2, r2 = len / 2;
+    const int32_t base = (int32_t)mn;
+    uint32_t k1, k2;
+    select2([&](int i) { return (uint32_t)(buf[1 + i] - base); }, len, r1,
+            r2, (uint32_t)(mx - mn), sh, k1, k2);
+    M2 = 2 * mn + (int64_t)k1 + (int64_t)k2;
+    // |2x - M2| <= 2*(max - min) < 2^32
+    const int64_t m2c = M2;
+    uint64_t umax = (uint64_t)max(2 * mx - m2c, m2c - 2 * mn);
+    uint32_t u1, u2;
+    select2(
+        [&](int i) {
+          int64_t d = 2 * (int64_t)buf[1 + i] - m2c;
+          return (uint32_t)(d < 0 ? -d : d);
+        },
+        len, r1, r2, (uint32_t)umax, sh, u1, u2);
+    MAD4 = (int64_t)u1 + (int64_t)u2;
+  } else if (tid == 0) {
+    atomicExch(err, kErrRange);
+  }
+  if (tid == 0) {
+    m2_out[(int64_t)k * nwin + j] = M2;
+    mad4_out[(int64_t)k * nwin + j] = MAD4;
+  }
+
+  // per-width FP32 scale 1/(2 sigma sqrt(w)) and integer screen thresholds
+  // on B_y = sum(y) over the width: S/N >= thr  <=>  2 B_y - w*odd >= thr *
+  // 2 sigma sqrt(w); the screen keeps a 4e-6 relative margin below that so
+  // FP32 rounding cannot hide a candidate the FP32 S/N would accept.
+  const int32_t mfloor = (int32_t)(M2 >> 1);  // floor(median)
+  const int odd = (int)(M2 & 1);
+  if (tid < nw) {
+    const float w = (float)widths[tid];
+    const float two_sigma = kMadToSigma * (float)MAD4 * 0.5f;
+    const float denom = two_sigma * sqrtf(w);
+    sh.inv[tid] = MAD4 > 0 ? 1.0f / denom : 0.0f;
+    float tnum = thr * denom * (1.0f - 4e-6f);  // threshold on 2B_y - w*odd
+    float tby = 0.5f * (tnum + (float)(widths[tid] * odd));
+    int32_t tb;
+    if (MAD4 <= 0 || !(tby < 2.0e9f)) tb = INT32_MAX;
+    else if (tby <= -2.0e9f) tb = INT32_MIN;
+    else tb = (int32_t)floorf(tby);
+    sh.thr_by[tid] = tb;
+  }
+
+  // ---- 3. y = x - floor(median); inclusive prefix sum Q[1..elen] in place
+  {
+    const int chunk = ((elen + kWarps * 32 - 1) / (kWarps * 32)) * 32;
+    const int b0 = warp * chunk, b1 = min(elen, b0 + chunk);
+    uint32_t carry = 0;
+    for (int i = b0; i < b1; i += 32) {
+      int ii = i + lane;
+      uint32_t v = (ii < b1) ? (uint32_t)(buf[1 + ii] - mfloor) : 0u;
+      v = warp_incl_scan(v, lane) + carry;
+      if (ii < b1) buf[1 + ii] = (int32_t)v;
+      carry = __shfl_sync(0xffffffffu, v, 31);
+    }
+    if (lane == 0) sh.wsum[warp] = carry;
+    __syncthreads();
+    uint32_t off = 0;
+    for (int w = 0; w < warp; ++w) off += sh.wsum[w];
+    for (int i = b0 + lane; i < b1; i += 32) buf[1 + i] = (int32_t)((uint32_t)buf[1 + i] + off);
+    __syncthreads();
+  }
+  const uint32_t *Q = reinterpret_cast<const uint32_t *>(buf);
+
+  // ---- 4. boxcars, S/N, candidates
+  const int64_t nvalid_t = n - lo;  // t - lo + w <= n - lo
+  for (int i0 = 0; i0 < len; i0 += kSpsThreads) {
+    const int i = i0 + tid;
+    const bool in = i < len;
+    bool pass = false;
+    if (in && !DENSE) {
+      const uint32_t qi = Q[i];
+#pragma unroll 1
+      for (int wi = 0; wi < nw; ++wi) {
+        const int w = widths[wi];
+        if ((int64_t)i + w > nvalid_t) break;
+        int32_t by = (int32_t)(Q[i + w] - qi);
+        pass |= by >= sh.thr_by[wi];
+      }
+    }
+    if (DENSE || pass) {
+      int bw = -1;
+      float bs = 0.0f;
+      int32_t bsum = 0;
+      if (in) {
+        const uint32_t qi = Q[i];
+        for (int wi = 0; wi < nw; ++wi) {
+          const int w = widths[wi];
+          if ((int64_t)i + w > nvalid_t) break;
+          int32_t by = (int32_t)(Q[i + w] - qi);
+          int64_t num = 2 * (int64_t)by - (int64_t)w * odd;
+          float s = (float)num * sh.inv[wi];
+          if (bw < 0 || s > bs) {
+            bw = wi;
+            bs = s;
+            bsum = by + w * mfloor;
+          }
+        }
+      }
+      if (DENSE) {
+        if (in) {
+          const int64_t o = (int64_t)k * n + lo + i;
+          best_w[o] = bw;
+          best_snr[o] = bs;
+          best_sum[o] = bsum;
+        }
+      } else {
+        const bool cand = in && bw >= 0 && bs >= thr;
+        const uint32_t ball = __ballot_sync(__activemask(), cand);
+        if (cand) {
+          const int leader = __ffs(ball) - 1;
+          uint32_t base = 0;
+          if (lane == leader) base = atomicAdd(count, (uint32_t)__popc(ball));
+          base = __shfl_sync(ball, base, leader);
+          const uint32_t slot = base + __popc(ball & ((1u << lane) - 1u));
+          if (slot < cap) {
+            ddsp_cand c;
+            c.dm_idx = (uint32_t)k;
+            c.t = (uint32_t)(lo + i);
+            c.w_idx = (uint32_t)bw;
+            c.snr = bs;
+            cands[slot] = c;
+          }
+        }
+      }
+    }
+  }
+}
+
+}  // namespace
+
+int64_t sps_max_window_samples() { return kMaxWindowSamples; }
+
+cudaError_t launch_sps(const Plan &p, const int32_t *d_series,
+                       int64_t nsamp_out, float threshold, bool dense,
+                       int32_t *d_best_w, float *d_best_snr,
+                       int32_t *d_best_sum, cudaStream_t s) {
+  const int64_t L = p.norm_window;
+  int64_t nwin = (L <= 0) ? 1 : max((int64_t)1, nsamp_out / L);
+  int64_t maxlen = (L <= 0 || nwin == 1) ? nsamp_out
+                                         : max(L, nsamp_out - (nwin - 1) * L);
+  const int wmax = p.widths.back();
+  const size_t smem =
+      sizeof(SpsShared) + 4 * (size_t)(maxlen + wmax + 4);
+  static bool attr_set[2] = {false, false};
+  auto kern = dense ? sps_kernel<true> : sps_kernel<false>;
+  if (!attr_set[dense]) {
+    cudaError_t e = cudaFuncSetAttribute(
+        kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (e != cudaSuccess) return e;
+    attr_set[dense] = true;
+  }
+  dim3 grid((unsigned)nwin, (unsigned)p.ndm);
+  kern<<<grid, kSpsThreads, smem, s>>>(
+      d_series, nsamp_out, L, nwin, p.d_widths, p.nwidths, threshold, p.d_m2,
+      p.d_mad4, p.d_cands, p.d_count, (uint32_t)p.cand_capacity, d_best_w,
+      d_best_snr, d_best_sum, p.d_err);
+  return cudaGetLastError();
+}
+
+}  // namespace ddsp

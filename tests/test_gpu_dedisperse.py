@@ -1,0 +1,197 @@
+"""GPU parity of unpack + dedispersion against the CPU oracle (bit-exact).
+
+Covers every tile shape of the staged kernel and the direct kernel, ragged
+channel / sample / DM counts, unsorted DM lists, uint16 input, the
+256-channel configuration in full, and the 4096-channel 262144-sample
+configuration at full size on sampled outputs plus the DM = 0 invariant."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2605_03531_b300 import Plan, build, synth
+
+pytestmark = pytest.mark.gpu
+
+TILES = [(0, 0), (4, 1), (4, 2), (4, 8), (8, 4), (8, 8), (16, 8), (16, 16), (-1, 0)]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+
+
+def _plan(nchan, f_top, bw, ts, dms, nbits=8, widths=(1, 2, 4)):
+    return Plan(nchan, f_top, bw, ts, dms, list(widths), nbits=nbits,
+                norm_window=8192, cand_capacity=1 << 16)
+
+
+def to_dev(x):
+    """numpy uint8/uint16 array -> CUDA tensor of the same bits."""
+    if x.dtype == np.uint16:
+        return torch.from_numpy(x.view(np.int16)).cuda().view(torch.uint16)
+    return torch.from_numpy(x).cuda()
+
+
+def from_dev(t):
+    if t.dtype == torch.uint16:
+        return t.view(torch.int16).cpu().numpy().view(np.uint16)
+    return t.cpu().numpy()
+
+
+def _set_tile(plan, t):
+    try:
+        plan.set_tile(*t)
+        return True
+    except Exception:
+        return False  # shape does not fit on chip for this plan
+
+
+@pytest.mark.parametrize("nchan,nin,nbits", [(256, 1000, 8), (4096, 300, 8),
+                                             (37, 777, 8), (100, 129, 8),
+                                             (64, 500, 16), (33, 301, 16)])
+def test_unpack_byte_exact(nchan, nin, nbits):
+    rng = np.random.default_rng(nchan + nin)
+    dt = np.uint8 if nbits == 8 else np.uint16
+    x = rng.integers(0, np.iinfo(dt).max + 1, size=(nin, nchan)).astype(dt)
+    p = _plan(nchan, 500.0, -0.1, 1e-3, [0.0], nbits=nbits)
+    pitch = ((nin + 127) // 128) * 128 + 128
+    out = from_dev(p.unpack(to_dev(x), pitch))
+    ref = oracle.unpack(x)
+    assert np.array_equal(out[:, :nin], ref)
+    assert not out[:, nin:].any()
+
+
+def test_plan_delays_match_oracle():
+    cfg = synth.config2()
+    p = _plan(cfg.nchan, cfg.f_top, cfg.chan_bw, cfg.tsamp, cfg.dm_list())
+    d_ref, D = oracle.delay_table(cfg.nchan, cfg.f_top, cfg.chan_bw, cfg.tsamp,
+                                  cfg.dm_list())
+    assert p.max_delay == D == 89989
+    assert np.array_equal(p.delays(), d_ref)
+
+
+@pytest.fixture(scope="module")
+def c1():
+    cfg = synth.config1()
+    x = synth.filterbank(cfg, 16384)
+    d, D = oracle.delay_table(cfg.nchan, cfg.f_top, cfg.chan_bw, cfg.tsamp,
+                              cfg.dm_list())
+    ref = oracle.dedisperse(x.numpy(), d)
+    return cfg, x, ref
+
+
+@pytest.mark.parametrize("tile", TILES)
+def test_c1_bit_exact_every_tile(c1, tile):
+    cfg, x, ref = c1
+    p = _plan(cfg.nchan, cfg.f_top, cfg.chan_bw, cfg.tsamp, cfg.dm_list())
+    if not _set_tile(p, tile):
+        pytest.skip("tile does not fit")
+    out = p.dedisperse(x.cuda())
+    torch.cuda.synchronize()
+    assert out.shape == ref.shape == (256, 15158)
+    assert np.array_equal(out.cpu().numpy(), ref)
+
+
+SHAPES = [
+    # nchan, nin, dms, nbits, f_top, bw, tsamp
+    (37, 3000, np.linspace(0, 40, 5), 8, 450.0, -2.0, 1e-3),
+    (100, 5000, np.random.default_rng(1).uniform(0, 60, 33), 8, 500.0, -1.0, 1e-3),
+    (16, 777, [17.0], 8, 400.0, -4.0, 1e-3),
+    (64, 4100, np.linspace(0, 20, 20)[::-1], 16, 420.0, -1.5, 1e-3),
+    (48, 2000, np.random.default_rng(2).uniform(0, 30, 17), 16, 380.0, 1.0, 1e-3),
+    (300, 3333, np.linspace(3, 9, 9), 8, 700.0, -0.5, 5e-4),
+    (1, 600, np.linspace(0, 100, 7), 8, 300.0, -1.0, 1e-3),
+]
+
+
+@pytest.mark.parametrize("shape", range(len(SHAPES)))
+@pytest.mark.parametrize("tile", [(0, 0), (4, 2), (8, 8), (16, 4), (-1, 0)])
+def test_ragged_shapes_bit_exact(shape, tile):
+    nchan, nin, dms, nbits, f_top, bw, ts = SHAPES[shape]
+    rng = np.random.default_rng(shape)
+    dt = np.uint8 if nbits == 8 else np.uint16
+    hi = 256 if nbits == 8 else 65536
+    x = rng.integers(0, hi, size=(nin, nchan)).astype(dt)
+    p = _plan(nchan, f_top, bw, ts, dms, nbits=nbits)
+    if not _set_tile(p, tile):
+        pytest.skip("tile does not fit")
+    d = p.delays()
+    ref = oracle.dedisperse(x, d)
+    out = p.dedisperse(to_dev(x))
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy(), ref)
+
+
+def test_impulses_land_at_their_delays():
+    """I2 on the GPU: unit impulses reappear at t = s0 - d[k][c] only."""
+    nchan, nin = 96, 6000
+    dms = np.linspace(0, 150, 24)
+    p = _plan(nchan, 450.0, -1.0, 1e-3, dms)
+    d = p.delays()
+    D = p.max_delay
+    nout = nin - D
+    x = np.zeros((nin, nchan), dtype=np.uint8)
+    hits = [(0, 100), (95, nin - 1), (50, 3000), (7, D + 5)]
+    for c, s0 in hits:
+        x[s0, c] = 1
+    out = p.dedisperse(torch.from_numpy(x).cuda()).cpu().numpy()
+    expect = np.zeros((len(dms), nout), dtype=np.int64)
+    for c, s0 in hits:
+        for k in range(len(dms)):
+            t = s0 - d[k, c]
+            if 0 <= t < nout:
+                expect[k, t] += 1
+    assert np.array_equal(out, expect)
+
+
+def test_saturated_input_no_overflow():
+    """All-255 input over 4096 channels: the SWAR lanes widen correctly."""
+    nchan, nin = 4096, 3000
+    p = _plan(nchan, 500.0, -0.048828125, 81.92e-6, np.linspace(0, 2, 16))
+    x = torch.full((nin, nchan), 255, dtype=torch.uint8, device="cuda")
+    out = p.dedisperse(x)
+    assert (out == 255 * 4096).all().item()
+
+
+def test_full_size_4096ch_sampled():
+    """4096 ch x (262144 + 89989) samples x 1024 DMs, the launch the
+    benchmark times: sampled outputs against the oracle one by one, and the
+    DM = 0 trial equal to the channel sum over the whole block."""
+    cfg = synth.config2()
+    p = _plan(cfg.nchan, cfg.f_top, cfg.chan_bw, cfg.tsamp, cfg.dm_list(),
+              widths=cfg.widths)
+    D = p.max_delay
+    nin = cfg.nsamp_out + D
+    x = synth.noise_u8(nin, cfg.nchan, cfg.seed, device="cuda")
+    synth.inject_pulses(x, cfg.pulses, cfg.f_top, cfg.chan_bw, cfg.tsamp, cfg.seed)
+    out = p.dedisperse(x)
+    torch.cuda.synchronize()
+    nout = cfg.nsamp_out
+    chan_sum = x[:nout].to(torch.int32).sum(dim=1, dtype=torch.int32)
+    assert torch.equal(out[0], chan_sum)
+    xh = x.cpu().numpy()
+    d = p.delays()
+    rng = np.random.default_rng(7)
+    ks = np.concatenate([[0, cfg.ndm - 1, 511, 512], rng.integers(0, cfg.ndm, 600)])
+    ts = np.concatenate([[0, nout - 1, 2047, 2048], rng.integers(0, nout, 600)])
+    for pl in cfg.pulses[:5]:
+        k = int(np.argmin(np.abs(cfg.dm_list() - pl.dm)))
+        ks = np.append(ks, [k, k])
+        ts = np.append(ts, [int(pl.t0), int(pl.t0) + 1])
+    outh = out.cpu().numpy()
+    for k, t in zip(ks, ts):
+        assert outh[k, t] == oracle.dedisperse_at(xh, d, int(k), int(t)), (k, t)
+
+
+def test_injected_pulse_found_on_gpu(c1):
+    cfg, x, _ = c1
+    p = _plan(cfg.nchan, cfg.f_top, cfg.chan_bw, cfg.tsamp, cfg.dm_list(),
+              widths=cfg.widths)
+    series = p.dedisperse(x.cuda())
+    p.single_pulse_search(series, cfg.threshold)
+    cands, n = p.fetch()
+    assert n > 0
+    best = cands[np.argmax(cands["snr"])]
+    assert best["dm_idx"] == 100 and cfg.widths[best["w_idx"]] == 4
+    assert abs(int(best["t"]) - 8000) <= 1

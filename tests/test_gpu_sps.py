@@ -1,0 +1,220 @@
+"""GPU parity of the single-pulse search against the CPU oracle.
+
+* window statistics (2*median, 4*MAD): bit-exact;
+* per-sample best boxcar sum: bit-exact; best S/N: within 1e-5 relative of
+  the FP64 oracle; best width: equal unless two widths tie within 1e-5;
+* candidate lists: identical after removing events whose oracle S/N is
+  within 1e-4*thr of the threshold;
+* the 2048 x 1048576 stress configuration at full size: statistics and
+  candidates of sampled DM rows against the oracle run on those rows.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2605_03531_b300 import DdspError, Plan, build, synth
+
+pytestmark = pytest.mark.gpu
+
+SNR_RTOL = 1e-5
+THR_EXEMPT = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+
+
+def _plan(ndm, widths, L, cap=1 << 20):
+    # the delay parameters do not matter for the search on a given series
+    return Plan(16, 500.0, -1.0, 1e-3, np.zeros(ndm), widths, nbits=8,
+                norm_window=L, cand_capacity=cap)
+
+
+def oracle_dense(x, widths, L):
+    """Best width index and S/N at every (k, t) from the oracle (a search with
+    a threshold below every possible S/N returns every sample)."""
+    ndm, n = x.shape
+    c, cnt = oracle.sps(x, widths, L, -1e300, cap=ndm * n)
+    assert cnt == c.size
+    bw = np.full((ndm, n), -1, np.int64)
+    bs = np.zeros((ndm, n))
+    bw[c["dm_idx"], c["t"]] = c["w_idx"]
+    bs[c["dm_idx"], c["t"]] = c["snr"]
+    return bw, bs
+
+
+def check_dense(x, widths, L):
+    ndm, n = x.shape
+    p = _plan(ndm, widths, L)
+    xd = torch.from_numpy(x).cuda()
+    bw, bs, bsum = p.search_dense(xd)
+    torch.cuda.synchronize()
+    bw, bs, bsum = bw.cpu().numpy(), bs.cpu().numpy(), bsum.cpu().numpy()
+    # statistics, bit-exact
+    m2, mad4 = p.stats()
+    for k in range(ndm):
+        rm2, rmad4 = oracle.window_stats(x[k], L)
+        assert np.array_equal(m2[k], rm2) and np.array_equal(mad4[k], rmad4), k
+    rbw, rbs = oracle_dense(x, widths, L)
+    valid = rbw >= 0
+    assert np.array_equal(bw >= 0, valid)
+    # S/N of the GPU's chosen width vs the oracle's best S/N
+    err = np.abs(bs[valid] - rbs[valid])
+    assert (err <= SNR_RTOL * np.abs(rbs[valid]) + 1e-30).all(), err.max()
+    # width: equal, or the oracle's S/N at both widths agrees within 1e-5
+    diff = valid & (bw != rbw)
+    for k, t in zip(*np.nonzero(diff)):
+        w_gpu = widths[bw[k, t]]
+        B = int(x[k, t:t + w_gpu].astype(np.int64).sum())
+        j = min(t // L, max(1, n // L) - 1) if L else 0
+        rm2, rmad4 = oracle.window_stats(x[k], L)
+        s_gpu_w = oracle.snr(B, w_gpu, rm2[j], rmad4[j])
+        assert abs(s_gpu_w - rbs[k, t]) <= SNR_RTOL * abs(rbs[k, t]), (k, t)
+    # boxcar sum at the GPU's width, bit-exact
+    for k in range(ndm):
+        for wi, w in enumerate(widths):
+            sel = np.nonzero(bw[k] == wi)[0]
+            if sel.size:
+                ref = oracle.boxcar(x[k], w)[sel]
+                assert np.array_equal(bsum[k, sel].astype(np.int64), ref), (k, w)
+    return p
+
+
+@pytest.mark.parametrize("n,L,widths", [
+    (40000, 8192, [1, 2, 4, 8, 16, 32, 64, 128, 256, 512, 1024]),
+    (15158, 8192, [1, 2, 4, 8, 16, 32]),      # one window longer than L
+    (8192, 8192, [1, 2, 4]),
+    (5000, 0, [1, 4, 16]),                    # one window over the series
+    (9001, 1000, [2, 8, 64]),                 # ragged last window, odd widths set
+    (33, 8, [1, 2, 4, 8, 16, 32]),            # widths longer than windows
+])
+def test_dense_matches_oracle(n, L, widths):
+    x = synth.gaussian_series(4, n, seed=n + L).numpy()
+    check_dense(x, widths, L)
+
+
+def test_dense_on_dedispersed_series():
+    cfg = synth.config1()
+    x = synth.filterbank(cfg, 16384).numpy()
+    d, _ = oracle.delay_table(cfg.nchan, cfg.f_top, cfg.chan_bw, cfg.tsamp,
+                              cfg.dm_list())
+    ks = np.array([0, 1, 99, 100, 101, 255])
+    series = oracle.dedisperse(x, d[ks])
+    check_dense(series, cfg.widths, 8192)
+
+
+def _compare_candidates(got, n_got, ref, n_ref, thr, x, widths, L):
+    assert n_got == got.size and n_ref == ref.size
+    gk = {(int(c["dm_idx"]), int(c["t"])): c for c in got}
+    rk = {(int(c["dm_idx"]), int(c["t"])): c for c in ref}
+    for key in set(gk) | set(rk):
+        if key in gk and key in rk:
+            g, r = gk[key], rk[key]
+            assert abs(g["snr"] - r["snr"]) <= SNR_RTOL * abs(r["snr"]), key
+            if g["w_idx"] != r["w_idx"]:
+                k, t = key
+                wg = widths[g["w_idx"]]
+                B = int(x[k, t:t + wg].astype(np.int64).sum())
+                rm2, rmad4 = oracle.window_stats(x[k], L)
+                j = min(t // L, max(1, x.shape[1] // L) - 1) if L else 0
+                s = oracle.snr(B, wg, rm2[j], rmad4[j])
+                assert abs(s - r["snr"]) <= SNR_RTOL * abs(r["snr"]), key
+        else:
+            k, t = key
+            _, s = oracle.best_at(x[k], L, widths, t)
+            assert abs(s - thr) <= THR_EXEMPT * thr, (key, s)
+
+
+@pytest.mark.parametrize("thr", [5.0, 6.5, 9.0])
+def test_candidates_match_oracle(thr):
+    widths = [1, 2, 4, 8, 16, 32, 64, 128, 256, 512, 1024]
+    x = synth.gaussian_series(8, 1 << 16, seed=21).numpy()
+    p = _plan(8, widths, 8192)
+    p.single_pulse_search(torch.from_numpy(x).cuda(), thr)
+    got, n_got = p.fetch()
+    ref, n_ref = oracle.sps(x, widths, 8192, thr)
+    assert n_ref > 0
+    _compare_candidates(got, n_got, ref, n_ref, thr, x, widths, 8192)
+
+
+def test_candidates_c1_series():
+    cfg = synth.config1()
+    x = synth.filterbank(cfg, 16384).numpy()
+    d, _ = oracle.delay_table(cfg.nchan, cfg.f_top, cfg.chan_bw, cfg.tsamp,
+                              cfg.dm_list())
+    series = oracle.dedisperse(x, d)
+    p = _plan(cfg.ndm, cfg.widths, cfg.norm_window)
+    p.single_pulse_search(torch.from_numpy(series).cuda(), cfg.threshold)
+    got, n_got = p.fetch()
+    ref, n_ref = oracle.sps(series, cfg.widths, cfg.norm_window, cfg.threshold)
+    _compare_candidates(got, n_got, ref, n_ref, cfg.threshold, series,
+                        cfg.widths, cfg.norm_window)
+
+
+def test_mad_zero_gives_no_candidates():
+    x = np.full((3, 20000), 7, np.int32)
+    x[1, 5000] = 10 ** 6
+    x[2, ::2] = 9                      # two values: MAD 1
+    x[2, 100:104] = 400
+    p = _plan(3, [1, 2, 4], 8192)
+    p.single_pulse_search(torch.from_numpy(x).cuda(), 5.0)
+    got, n = p.fetch()
+    ref, n_ref = oracle.sps(x, [1, 2, 4], 8192, 5.0)
+    assert n == n_ref
+    assert set(got["dm_idx"].tolist()) <= {2}
+    m2, mad4 = p.stats()
+    assert (mad4[0] == 0).all() and (mad4[1] == 0).all()
+
+
+def test_truncation_reports_true_count():
+    widths = [1, 2, 4]
+    x = synth.gaussian_series(4, 1 << 15, seed=5).numpy()
+    ref, n_ref = oracle.sps(x, widths, 8192, 3.0)
+    assert n_ref > 50
+    p = _plan(4, widths, 8192, cap=16)
+    p.single_pulse_search(torch.from_numpy(x).cuda(), 3.0)
+    with pytest.raises(DdspError) as e:
+        p.fetch()
+    assert e.value.code == -6
+    got, n = p.fetch(allow_truncated=True)
+    assert n == n_ref and got.size == 16
+
+
+def test_argument_errors():
+    p = _plan(2, [1, 2], 8192)
+    x = torch.zeros((2, 1000), dtype=torch.int32, device="cuda")
+    with pytest.raises(DdspError):
+        p.single_pulse_search(x, 0.0)
+    with pytest.raises(DdspError):
+        p.single_pulse_search(x, float("nan"))
+    big = _plan(1, [1, 1024], 0)
+    with pytest.raises(DdspError) as e:
+        big.single_pulse_search(torch.zeros((1, 60000), dtype=torch.int32,
+                                            device="cuda"), 5.0)
+    assert e.value.code == -2
+
+
+def test_stress_config_full_size_sampled_rows():
+    """2048 x 1048576 int32 series, widths 1..1024, L = 8192, thr 6.5, in the
+    launch configuration the benchmark times; oracle on sampled rows."""
+    ndm, n, L, thr = 2048, 1 << 20, 8192, 6.5
+    widths = [1 << i for i in range(11)]
+    x = synth.gaussian_series(ndm, n, seed=4, device="cuda")
+    p = _plan(ndm, widths, L, cap=1 << 22)
+    p.single_pulse_search(x, thr)
+    got, n_got = p.fetch()
+    m2, mad4 = p.stats()
+    rows = [0, 1, 1023, 2047]
+    for k in rows:
+        xk = x[k].cpu().numpy()
+        rm2, rmad4 = oracle.window_stats(xk, L)
+        assert np.array_equal(m2[k], rm2) and np.array_equal(mad4[k], rmad4)
+        ref, n_ref = oracle.sps(xk, widths, L, thr)
+        mine = got[got["dm_idx"] == k].copy()
+        mine["dm_idx"] = 0
+        _compare_candidates(mine, mine.size, ref, n_ref, thr, xk[None, :],
+                            widths, L)
+    # the candidate density follows the 0.1% event rate
+    assert 0 < n_got < ndm * n * 0.01
