@@ -179,6 +179,18 @@ int ddsp_plan_get_stats(ddsp_plan *plan, int64_t *m2, int64_t *mad4,
 int ddsp_candidates_fetch(ddsp_plan *plan, ddsp_cand *host_buf, size_t cap,
                           size_t *n_total);
 
+/* Like ddsp_candidates_fetch, restricted to DM-trial indices in
+ * [dm_lo, dm_hi): the stored records are streamed to the host in bounded
+ * pieces and filtered there, so a caller can inspect a few DM rows of a very
+ * large candidate set without a host buffer for all of it.  *n_range gets
+ * the number of stored records in the range, *n_total the device count.
+ * DDSP_E_TRUNCATED if *n_range > cap or the device count exceeded the
+ * capacity (some records of the range may then be missing). */
+int ddsp_candidates_fetch_dm_range(ddsp_plan *plan, uint32_t dm_lo,
+                                   uint32_t dm_hi, ddsp_cand *host_buf,
+                                   size_t cap, size_t *n_range,
+                                   size_t *n_total);
+
 /* Synchronise `stream` and report any error a kernel of this plan recorded
  * on the device (DDSP_E_TIMEOUT, DDSP_E_RANGE), then clear it. */
 int ddsp_plan_check(ddsp_plan *plan, ddsp_stream_t stream);
@@ -189,13 +201,23 @@ void ddsp_plan_destroy(ddsp_plan *plan);
 /* Static, human-readable text for a DDSP_* code. */
 const char *ddsp_error_string(int code);
 
-/* Tile shape of the dedispersion kernel: dm_tile DM trials x time_tile
- * samples per block, chan_chunk channels staged per pipeline stage.  A
- * value of 0 lets the library choose.  Returns DDSP_E_INVALID_ARG for a
- * shape the kernel does not implement or that does not fit on chip. */
-int ddsp_plan_set_tile(ddsp_plan *plan, int dm_tile, int chan_chunk);
-int ddsp_plan_get_tile(const ddsp_plan *plan, int *dm_tile, int *time_tile,
-                       int *chan_chunk);
+/* Name and text of the last CUDA error this library saw on the calling
+ * host thread (empty if none); the storage is the library's. */
+const char *ddsp_last_error_detail(void);
+
+/* Tile shape of the dedispersion kernel.  A block of 8 warps computes
+ * dm_tile DM trials x time_tile output samples; each thread owns
+ * dm_per_thread (2 or 4) trials x 16 samples; chan_chunk channels (1..32)
+ * are staged per pipeline step with `stages` (2..4) raw-window buffers.
+ * dm_tile must be dm_per_thread x {1, 2, 4}; time_tile follows from it.
+ * dm_tile = 0 restores the library's choice, dm_tile = -1 selects the direct
+ * (unstaged) kernel.  DDSP_E_INVALID_ARG for a shape the kernel does not
+ * implement or whose staging does not fit on chip.  Synchronises. */
+int ddsp_plan_set_tile(ddsp_plan *plan, int dm_tile, int dm_per_thread,
+                       int chan_chunk, int stages);
+int ddsp_plan_get_tile(const ddsp_plan *plan, int *dm_tile,
+                       int *dm_per_thread, int *time_tile, int *chan_chunk,
+                       int *stages);
 
 #ifdef __cplusplus
 }

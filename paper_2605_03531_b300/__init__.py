@@ -91,17 +91,20 @@ class Plan:
             self._h, d.ctypes.data_as(C.c_void_p)), "ddsp_plan_get_delays")
         return d
 
-    def set_tile(self, dm_tile=0, chan_chunk=0):
-        _lib.check(_lib.lib().ddsp_plan_set_tile(self._h, int(dm_tile),
-                                                 int(chan_chunk)),
-                   "ddsp_plan_set_tile")
+    def set_tile(self, dm_tile=0, dm_per_thread=4, chan_chunk=8, stages=2):
+        """Pick the dedispersion tile shape (0: library's choice, -1: the
+        direct kernel); see ddsp_plan_set_tile."""
+        _lib.check(_lib.lib().ddsp_plan_set_tile(
+            self._h, int(dm_tile), int(dm_per_thread), int(chan_chunk),
+            int(stages)), "ddsp_plan_set_tile")
 
     def get_tile(self):
-        a, b, c = C.c_int(), C.c_int(), C.c_int()
-        _lib.check(_lib.lib().ddsp_plan_get_tile(self._h, C.byref(a),
-                                                 C.byref(b), C.byref(c)),
+        """dict(dm_tile, dm_per_thread, time_tile, chan_chunk, stages)."""
+        v = [C.c_int() for _ in range(5)]
+        _lib.check(_lib.lib().ddsp_plan_get_tile(self._h, *[C.byref(a) for a in v]),
                    "ddsp_plan_get_tile")
-        return a.value, b.value, c.value
+        keys = ("dm_tile", "dm_per_thread", "time_tile", "chan_chunk", "stages")
+        return dict(zip(keys, (a.value for a in v)))
 
     # ---------------------------------------------------------------- path
     def _in_dtype(self):
@@ -190,6 +193,16 @@ class Plan:
             return buf[:min(cap, self.cand_capacity)], n.value
         _lib.check(rc, "ddsp_candidates_fetch")
         return buf[:n.value].copy(), n.value
+
+    def fetch_dm_range(self, dm_lo, dm_hi, cap=1 << 22):
+        """(candidates with dm_lo <= dm_idx < dm_hi sorted, count in range,
+        device count)."""
+        buf = np.zeros(cap, dtype=CAND_DTYPE)
+        nr, nt = C.c_size_t(), C.c_size_t()
+        _lib.check(_lib.lib().ddsp_candidates_fetch_dm_range(
+            self._h, int(dm_lo), int(dm_hi), buf.ctypes.data_as(C.c_void_p),
+            int(cap), C.byref(nr), C.byref(nt)), "ddsp_candidates_fetch_dm_range")
+        return buf[:nr.value].copy(), nr.value, nt.value
 
     def stats(self):
         """Per-(DM, window) exact (2*median, 4*MAD) of the last search."""

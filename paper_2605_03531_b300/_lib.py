@@ -47,12 +47,15 @@ SIGNATURES = {
     "ddsp_single_pulse_search_dense": (I32, [P, P, I64, P, P, P, P]),
     "ddsp_plan_get_stats": (I32, [P, P, P, I64, PI64]),
     "ddsp_candidates_fetch": (I32, [P, P, C.c_size_t, C.POINTER(C.c_size_t)]),
+    "ddsp_candidates_fetch_dm_range": (I32, [P, C.c_uint32, C.c_uint32, P,
+                                             C.c_size_t, C.POINTER(C.c_size_t),
+                                             C.POINTER(C.c_size_t)]),
     "ddsp_plan_check": (I32, [P, P]),
     "ddsp_plan_destroy": (None, [P]),
     "ddsp_error_string": (C.c_char_p, [I32]),
-    "ddsp_plan_set_tile": (I32, [P, I32, I32]),
-    "ddsp_plan_get_tile": (I32, [P, C.POINTER(C.c_int), C.POINTER(C.c_int),
-                                 C.POINTER(C.c_int)]),
+    "ddsp_last_error_detail": (C.c_char_p, []),
+    "ddsp_plan_set_tile": (I32, [P, I32, I32, I32, I32]),
+    "ddsp_plan_get_tile": (I32, [P] + [C.POINTER(C.c_int)] * 5),
 }
 
 _lib = None
@@ -80,7 +83,9 @@ class DdspError(RuntimeError):
     def __init__(self, code, call):
         self.code = code
         msg = lib().ddsp_error_string(code).decode()
-        super().__init__(f"{call} failed: {msg} ({code})")
+        detail = lib().ddsp_last_error_detail().decode() if code == DDSP_E_CUDA else ""
+        super().__init__(f"{call} failed: {msg} ({code})"
+                         + (f" [{detail}]" if detail else ""))
 
 
 def check(code, call):

@@ -15,18 +15,17 @@ namespace ddsp {
 enum : int32_t { kErrNone = 0, kErrTimeout = 1, kErrRange = 2 };
 
 // Dedispersion kernel geometry: 8 warps per block, each thread owns
-// kDmPerThread DM trials x kElemPerThread interleaved elements.
+// rd DM trials x kElemPerThread interleaved elements.
 constexpr int kThreads = 256;
-constexpr int kDmPerThread = 4;
 constexpr int kElemPerThread = 4;
 
 struct DedispTile {
-  int wt = 0;          // warps along time
+  int wt = 0;          // warps along time (0: use the direct kernel)
   int wd = 0;          // warps along DM
-  int chan_chunk = 0;  // channels staged per pipeline stage
-  int dm_tile() const { return wd * kDmPerThread; }
-  // elements per row segment: 32 lanes x kElemPerThread x wt
-  int seg(int) const { return 32 * kElemPerThread * wt; }
+  int rd = 4;          // DM trials per thread (2 or 4)
+  int chan_chunk = 0;  // channels staged per pipeline step
+  int nbuf = 2;        // raw-window stages (bulk copies in flight + 1)
+  int dm_tile() const { return wd * rd; }
 };
 
 struct DedispTables {
@@ -36,7 +35,7 @@ struct DedispTables {
   int n_dm_tiles = 0;
   int dm_tile = 0;
   int span_max = 0;           // max over (g, c) of (dhi - wbase)
-  int32_t *d_wbase = nullptr; // [n_dm_tiles][nchan]
+  int32_t *d_desc = nullptr;  // [n_dm_tiles][nchan] {window start, bytes}
   int32_t *d_relb = nullptr;  // [n_dm_tiles][nchan][dm_tile], bytes
   int32_t *d_rowmap = nullptr;// [n_dm_tiles*dm_tile] output row (-1 = pad)
 };
@@ -86,6 +85,8 @@ cudaError_t launch_dedisperse_direct(const Plan &p, const void *d_cm,
                                      int64_t pitch, int64_t nsamp_out,
                                      int32_t *d_out, cudaStream_t s);
 int dedisp_time_tile(const DedispTile &t, int nbits);
+int dedisp_copy_bytes(const DedispTile &t, int span, int nbits);
+bool dedisp_tile_supported(const DedispTile &t);
 
 size_t dedisp_smem_bytes(const DedispTile &t, int span_max, int nbits);
 

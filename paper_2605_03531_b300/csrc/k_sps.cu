@@ -372,13 +372,14 @@ cudaError_t launch_sps(const Plan &p, const int32_t *d_series,
   const int wmax = p.widths.back();
   const size_t smem =
       sizeof(SpsShared) + 4 * (size_t)(maxlen + wmax + 4);
-  static bool attr_set[2] = {false, false};
+  static size_t attr_bytes[2] = {0, 0};
   auto kern = dense ? sps_kernel<true> : sps_kernel<false>;
-  if (!attr_set[dense]) {
+  if (smem > attr_bytes[dense]) {
+    // the opt-in limit covers static + dynamic shared memory together
     cudaError_t e = cudaFuncSetAttribute(
-        kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    attr_set[dense] = true;
+    attr_bytes[dense] = smem;
   }
   dim3 grid((unsigned)nwin, (unsigned)p.ndm);
   kern<<<grid, kSpsThreads, smem, s>>>(

@@ -4,6 +4,7 @@
 // every step of the path runs in the kernels of k_unpack.cu, k_dedisp.cu and
 // k_sps.cu.
 #include <math.h>
+#include <stdio.h>
 #include <string.h>
 
 #include <algorithm>
@@ -33,8 +34,12 @@ struct DeviceGuard {
   }
 };
 
+thread_local char g_detail[256] = "";
+
 int cuda_rc(cudaError_t e) {
   if (e == cudaSuccess) return DDSP_OK;
+  snprintf(g_detail, sizeof(g_detail), "%s: %s", cudaGetErrorName(e),
+           cudaGetErrorString(e));
   if (e == cudaErrorMemoryAllocation) return DDSP_E_NOMEM;
   return DDSP_E_CUDA;
 }
@@ -79,10 +84,10 @@ int span_for(const Plan &p, int dt) {
 }
 
 void free_tables(DedispTables &t) {
-  cudaFree(t.d_wbase);
+  cudaFree(t.d_desc);
   cudaFree(t.d_relb);
   cudaFree(t.d_rowmap);
-  t.d_wbase = t.d_relb = t.d_rowmap = nullptr;
+  t.d_desc = t.d_relb = t.d_rowmap = nullptr;
 }
 
 // Build and upload the staging tables for tile shape p.tile.
@@ -91,7 +96,7 @@ int build_tables(Plan &p) {
   if (p.tile.wt == 0) return DDSP_OK;  // direct kernel needs none
   const int dt = p.tile.dm_tile();
   const int ntiles = (p.ndm + dt - 1) / dt;
-  std::vector<int32_t> wbase((size_t)ntiles * p.nchan);
+  std::vector<int32_t> desc((size_t)ntiles * p.nchan * 2);
   std::vector<int32_t> relb((size_t)ntiles * p.nchan * dt);
   std::vector<int32_t> rowmap((size_t)ntiles * dt, -1);
   int span_max = 0;
@@ -103,46 +108,56 @@ int build_tables(Plan &p) {
       // delays are non-decreasing along the DM-sorted order
       const int32_t dlo = p.delays[(size_t)p.order[a] * p.nchan + c];
       const int32_t wb = dlo & ~15;
-      wbase[(size_t)g * p.nchan + c] = wb;
+      int span = 0;
       for (int r = 0; r < dt; ++r) {
         const int k = p.order[a + std::min(r, nvalid - 1)];
         const int32_t d = p.delays[(size_t)k * p.nchan + c];
         relb[((size_t)g * p.nchan + c) * dt + r] = 4 * (d - wb);
-        span_max = std::max(span_max, d - wb);
+        span = std::max(span, d - wb);
       }
+      span_max = std::max(span_max, span);
+      desc[((size_t)g * p.nchan + c) * 2] = wb;
+      desc[((size_t)g * p.nchan + c) * 2 + 1] =
+          dedisp_copy_bytes(p.tile, span, p.nbits);
     }
   }
   p.tab.n_dm_tiles = ntiles;
   p.tab.dm_tile = dt;
   p.tab.span_max = span_max;
   cudaError_t e;
-  if ((e = cudaMalloc(&p.tab.d_wbase, wbase.size() * 4)) != cudaSuccess ||
+  if ((e = cudaMalloc(&p.tab.d_desc, desc.size() * 4)) != cudaSuccess ||
       (e = cudaMalloc(&p.tab.d_relb, relb.size() * 4)) != cudaSuccess ||
       (e = cudaMalloc(&p.tab.d_rowmap, rowmap.size() * 4)) != cudaSuccess) {
     free_tables(p.tab);
     return cuda_rc(e);
   }
-  cudaMemcpy(p.tab.d_wbase, wbase.data(), wbase.size() * 4, cudaMemcpyHostToDevice);
+  cudaMemcpy(p.tab.d_desc, desc.data(), desc.size() * 4, cudaMemcpyHostToDevice);
   cudaMemcpy(p.tab.d_relb, relb.data(), relb.size() * 4, cudaMemcpyHostToDevice);
   e = cudaMemcpy(p.tab.d_rowmap, rowmap.data(), rowmap.size() * 4,
                  cudaMemcpyHostToDevice);
   return cuda_rc(e);
 }
 
-// Default tile: the largest DM tile whose staged windows fit with two
-// resident blocks per SM, else one block per SM, else the direct kernel.
+// Default tile: the first shape (in order of preference) whose staged
+// windows fit with two resident blocks per SM, else one block per SM, else
+// the direct kernel.
 DedispTile choose_tile(const Plan &p) {
-  struct Cand { int wt, wd, cc; };
-  const Cand prefs[] = {{4, 2, 8}, {2, 4, 8}, {8, 1, 8}, {4, 2, 4},
-                        {8, 1, 4}, {8, 1, 2}, {8, 1, 1}};
+  struct Cand { int wt, wd, rd, cc; };
+  const Cand prefs[] = {{4, 2, 4, 8}, {2, 4, 4, 8}, {4, 2, 4, 6},
+                        {8, 1, 4, 8}, {4, 2, 4, 4}, {8, 1, 4, 4},
+                        {8, 1, 4, 2}, {8, 1, 2, 2}, {8, 1, 2, 1}};
   for (size_t budget : {kSmemBudgetTwoBlocks, kSmemBudgetOneBlock}) {
     for (const Cand &c : prefs) {
       DedispTile t;
       t.wt = c.wt;
       t.wd = c.wd;
+      t.rd = c.rd;
       t.chan_chunk = c.cc;
       const int span = span_for(p, t.dm_tile());
-      if (dedisp_smem_bytes(t, span, p.nbits) <= budget) return t;
+      for (int nbuf : {3, 2}) {
+        t.nbuf = nbuf;
+        if (dedisp_smem_bytes(t, span, p.nbits) <= budget) return t;
+      }
     }
   }
   return DedispTile{};  // direct kernel
@@ -226,6 +241,8 @@ int read_err(Plan &p) {
 }  // namespace
 
 extern "C" {
+
+const char *ddsp_last_error_detail(void) { return g_detail; }
 
 const char *ddsp_error_string(int code) {
   switch (code) {
@@ -373,25 +390,26 @@ int ddsp_plan_get_delays(const ddsp_plan *h, int32_t *host_out) {
   return DDSP_OK;
 }
 
-int ddsp_plan_set_tile(ddsp_plan *h, int dm_tile, int chan_chunk) {
+int ddsp_plan_set_tile(ddsp_plan *h, int dm_tile, int dm_per_thread,
+                       int chan_chunk, int stages) {
   if (!h) return DDSP_E_INVALID_ARG;
   Plan &p = h->p;
   DeviceGuard g(p.device);
   DedispTile t;
-  if (dm_tile == 0 && chan_chunk == 0) {
+  if (dm_tile == 0) {
     t = choose_tile(p);
   } else if (dm_tile == -1) {
     t = DedispTile{};  // direct kernel
   } else {
-    switch (dm_tile) {
-      case 4: t.wt = 8; t.wd = 1; break;
-      case 8: t.wt = 4; t.wd = 2; break;
-      case 16: t.wt = 2; t.wd = 4; break;
-      default: return DDSP_E_INVALID_ARG;
-    }
-    if (chan_chunk < 1 || chan_chunk > 64 || (256 % chan_chunk) != 0)
-      return DDSP_E_INVALID_ARG;
+    t.rd = dm_per_thread;
+    if (t.rd != 2 && t.rd != 4) return DDSP_E_INVALID_ARG;
+    if (dm_tile % t.rd) return DDSP_E_INVALID_ARG;
+    t.wd = dm_tile / t.rd;
+    if (t.wd <= 0 || (kThreads / 32) % t.wd) return DDSP_E_INVALID_ARG;
+    t.wt = (kThreads / 32) / t.wd;
     t.chan_chunk = chan_chunk;
+    t.nbuf = stages;
+    if (!dedisp_tile_supported(t)) return DDSP_E_INVALID_ARG;
     const int span = span_for(p, t.dm_tile());
     if (dedisp_smem_bytes(t, span, p.nbits) > kSmemBudgetOneBlock)
       return DDSP_E_INVALID_ARG;
@@ -401,13 +419,16 @@ int ddsp_plan_set_tile(ddsp_plan *h, int dm_tile, int chan_chunk) {
   return build_tables(p);
 }
 
-int ddsp_plan_get_tile(const ddsp_plan *h, int *dm_tile, int *time_tile,
-                       int *chan_chunk) {
+int ddsp_plan_get_tile(const ddsp_plan *h, int *dm_tile, int *dm_per_thread,
+                       int *time_tile, int *chan_chunk, int *stages) {
   if (!h) return DDSP_E_INVALID_ARG;
   const Plan &p = h->p;
-  if (dm_tile) *dm_tile = p.tile.wt ? p.tile.dm_tile() : -1;
-  if (time_tile) *time_tile = p.tile.wt ? dedisp_time_tile(p.tile, p.nbits) : 0;
-  if (chan_chunk) *chan_chunk = p.tile.chan_chunk;
+  const bool staged = p.tile.wt > 0;
+  if (dm_tile) *dm_tile = staged ? p.tile.dm_tile() : -1;
+  if (dm_per_thread) *dm_per_thread = staged ? p.tile.rd : 0;
+  if (time_tile) *time_tile = staged ? dedisp_time_tile(p.tile, p.nbits) : 0;
+  if (chan_chunk) *chan_chunk = staged ? p.tile.chan_chunk : 0;
+  if (stages) *stages = staged ? p.tile.nbuf : 0;
   return DDSP_OK;
 }
 
@@ -551,6 +572,48 @@ int ddsp_candidates_fetch(ddsp_plan *h, ddsp_cand *host_buf, size_t cap,
   int rc = read_err(p);
   if (rc != DDSP_OK) return rc;
   return ncopy < cnt ? DDSP_E_TRUNCATED : DDSP_OK;
+}
+
+int ddsp_candidates_fetch_dm_range(ddsp_plan *h, uint32_t dm_lo,
+                                   uint32_t dm_hi, ddsp_cand *host_buf,
+                                   size_t cap, size_t *n_range,
+                                   size_t *n_total) {
+  if (!h || !n_range || !n_total || dm_hi < dm_lo || (cap > 0 && !host_buf))
+    return DDSP_E_INVALID_ARG;
+  Plan &p = h->p;
+  if (!p.searched) return DDSP_E_STATE;
+  DeviceGuard g(p.device);
+  cudaError_t e = cudaStreamSynchronize(p.last_stream);
+  if (e != cudaSuccess) return cuda_rc(e);
+  uint32_t cnt = 0;
+  e = cudaMemcpy(&cnt, p.d_count, 4, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_rc(e);
+  *n_total = cnt;
+  const size_t stored = std::min<size_t>(cnt, p.cand_capacity);
+  // stream the stored records through a bounded host buffer, keep the range
+  const size_t piece = (size_t)1 << 22;
+  std::vector<ddsp_cand> tmp(std::min(stored, piece));
+  size_t found = 0, kept = 0;
+  for (size_t off = 0; off < stored; off += piece) {
+    const size_t n = std::min(piece, stored - off);
+    e = cudaMemcpy(tmp.data(), p.d_cands + off, n * sizeof(ddsp_cand),
+                   cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_rc(e);
+    for (size_t i = 0; i < n; ++i) {
+      if (tmp[i].dm_idx >= dm_lo && tmp[i].dm_idx < dm_hi) {
+        if (kept < cap) host_buf[kept++] = tmp[i];
+        ++found;
+      }
+    }
+  }
+  std::sort(host_buf, host_buf + kept,
+            [](const ddsp_cand &a, const ddsp_cand &b) {
+              return a.dm_idx != b.dm_idx ? a.dm_idx < b.dm_idx : a.t < b.t;
+            });
+  *n_range = found;
+  int rc = read_err(p);
+  if (rc != DDSP_OK) return rc;
+  return (found > kept || stored < cnt) ? DDSP_E_TRUNCATED : DDSP_OK;
 }
 
 int ddsp_plan_check(ddsp_plan *h, ddsp_stream_t stream) {

@@ -13,7 +13,10 @@ from paper_2605_03531_b300 import Plan, build, synth
 
 pytestmark = pytest.mark.gpu
 
-TILES = [(0, 0), (4, 1), (4, 2), (4, 8), (8, 4), (8, 8), (16, 8), (16, 16), (-1, 0)]
+# (dm_tile, dm_per_thread, chan_chunk, stages); 0 = library's choice, -1 = direct
+TILES = [(0, 4, 8, 2), (4, 4, 1, 2), (4, 4, 8, 3), (8, 4, 8, 2), (8, 4, 6, 3),
+         (8, 4, 32, 4), (16, 4, 8, 2), (16, 4, 16, 3), (2, 2, 8, 2),
+         (4, 2, 5, 3), (8, 2, 8, 2), (-1, 4, 8, 2)]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -106,7 +109,8 @@ SHAPES = [
 
 
 @pytest.mark.parametrize("shape", range(len(SHAPES)))
-@pytest.mark.parametrize("tile", [(0, 0), (4, 2), (8, 8), (16, 4), (-1, 0)])
+@pytest.mark.parametrize("tile", [(0, 4, 8, 2), (4, 4, 3, 2), (8, 4, 8, 3),
+                                  (16, 4, 4, 2), (8, 2, 7, 3), (-1, 4, 8, 2)])
 def test_ragged_shapes_bit_exact(shape, tile):
     nchan, nin, dms, nbits, f_top, bw, ts = SHAPES[shape]
     rng = np.random.default_rng(shape)

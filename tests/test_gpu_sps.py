@@ -202,19 +202,19 @@ def test_stress_config_full_size_sampled_rows():
     ndm, n, L, thr = 2048, 1 << 20, 8192, 6.5
     widths = [1 << i for i in range(11)]
     x = synth.gaussian_series(ndm, n, seed=4, device="cuda")
-    p = _plan(ndm, widths, L, cap=1 << 22)
+    # no peak merging: the wide events light up ~1/3 of all samples
+    p = _plan(ndm, widths, L, cap=1 << 30)
     p.single_pulse_search(x, thr)
-    got, n_got = p.fetch()
     m2, mad4 = p.stats()
     rows = [0, 1, 1023, 2047]
+    n_total = None
     for k in rows:
         xk = x[k].cpu().numpy()
         rm2, rmad4 = oracle.window_stats(xk, L)
         assert np.array_equal(m2[k], rm2) and np.array_equal(mad4[k], rmad4)
-        ref, n_ref = oracle.sps(xk, widths, L, thr)
-        mine = got[got["dm_idx"] == k].copy()
+        ref, n_ref = oracle.sps(xk, widths, L, thr, cap=1 << 22)
+        mine, n_mine, n_total = p.fetch_dm_range(k, k + 1)
         mine["dm_idx"] = 0
-        _compare_candidates(mine, mine.size, ref, n_ref, thr, xk[None, :],
+        _compare_candidates(mine, n_mine, ref, n_ref, thr, xk[None, :],
                             widths, L)
-    # the candidate density follows the 0.1% event rate
-    assert 0 < n_got < ndm * n * 0.01
+    assert 0.1 * ndm * n < n_total < 0.6 * ndm * n
