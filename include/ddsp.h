@@ -207,17 +207,30 @@ const char *ddsp_last_error_detail(void);
 
 /* Tile shape of the dedispersion kernel.  A block of 8 warps computes
  * dm_tile DM trials x time_tile output samples; each thread owns
- * dm_per_thread (2 or 4) trials x 16 samples; chan_chunk channels (1..32)
+ * dm_per_thread (2, 4 or 8) trials x 16 samples; chan_chunk channels (1..32)
  * are staged per pipeline step with `stages` (2..4) raw-window buffers.
  * dm_tile must be dm_per_thread x {1, 2, 4}; time_tile follows from it.
- * dm_tile = 0 restores the library's choice, dm_tile = -1 selects the direct
- * (unstaged) kernel.  DDSP_E_INVALID_ARG for a shape the kernel does not
- * implement or whose staging does not fit on chip.  Synchronises. */
+ * flags: DDSP_TILE_SINGLE_ELEM_BUFFER (one relayout buffer, two barriers
+ * per chunk, less shared memory), DDSP_TILE_REGISTER_TOTALS (int32 totals
+ * kept in registers instead of being accumulated in the output array every
+ * <= 256 channels; uint8 plans accept it only together with
+ * DDSP_TILE_SINGLE_ELEM_BUFFER, uint16 plans always keep their totals in
+ * registers and accept 0 or DDSP_TILE_SINGLE_ELEM_BUFFER), or
+ * DDSP_TILE_WARP_SPECIALIZED alone (producer warps stage and relayout,
+ * consumer warps accumulate, no block-wide barrier in the main loop;
+ * dm_per_thread 4, or 8 for uint8).  Every variant computes the same exact
+ * sums.  dm_tile = 0 restores the library's choice, dm_tile = -1
+ * selects the direct (unstaged) kernel.  DDSP_E_INVALID_ARG for a shape the
+ * kernel does not implement or whose staging does not fit on chip.
+ * Synchronises. */
+#define DDSP_TILE_SINGLE_ELEM_BUFFER 1
+#define DDSP_TILE_REGISTER_TOTALS 4
+#define DDSP_TILE_WARP_SPECIALIZED 8
 int ddsp_plan_set_tile(ddsp_plan *plan, int dm_tile, int dm_per_thread,
-                       int chan_chunk, int stages);
+                       int chan_chunk, int stages, int flags);
 int ddsp_plan_get_tile(const ddsp_plan *plan, int *dm_tile,
                        int *dm_per_thread, int *time_tile, int *chan_chunk,
-                       int *stages);
+                       int *stages, int *flags);
 
 #ifdef __cplusplus
 }

@@ -91,19 +91,21 @@ class Plan:
             self._h, d.ctypes.data_as(C.c_void_p)), "ddsp_plan_get_delays")
         return d
 
-    def set_tile(self, dm_tile=0, dm_per_thread=4, chan_chunk=8, stages=2):
+    def set_tile(self, dm_tile=0, dm_per_thread=4, chan_chunk=8, stages=2,
+                 flags=0):
         """Pick the dedispersion tile shape (0: library's choice, -1: the
         direct kernel); see ddsp_plan_set_tile."""
         _lib.check(_lib.lib().ddsp_plan_set_tile(
             self._h, int(dm_tile), int(dm_per_thread), int(chan_chunk),
-            int(stages)), "ddsp_plan_set_tile")
+            int(stages), int(flags)), "ddsp_plan_set_tile")
 
     def get_tile(self):
-        """dict(dm_tile, dm_per_thread, time_tile, chan_chunk, stages)."""
-        v = [C.c_int() for _ in range(5)]
+        """dict(dm_tile, dm_per_thread, time_tile, chan_chunk, stages, flags)."""
+        v = [C.c_int() for _ in range(6)]
         _lib.check(_lib.lib().ddsp_plan_get_tile(self._h, *[C.byref(a) for a in v]),
                    "ddsp_plan_get_tile")
-        keys = ("dm_tile", "dm_per_thread", "time_tile", "chan_chunk", "stages")
+        keys = ("dm_tile", "dm_per_thread", "time_tile", "chan_chunk", "stages",
+                "flags")
         return dict(zip(keys, (a.value for a in v)))
 
     # ---------------------------------------------------------------- path

@@ -54,8 +54,8 @@ SIGNATURES = {
     "ddsp_plan_destroy": (None, [P]),
     "ddsp_error_string": (C.c_char_p, [I32]),
     "ddsp_last_error_detail": (C.c_char_p, []),
-    "ddsp_plan_set_tile": (I32, [P, I32, I32, I32, I32]),
-    "ddsp_plan_get_tile": (I32, [P] + [C.POINTER(C.c_int)] * 5),
+    "ddsp_plan_set_tile": (I32, [P, I32, I32, I32, I32, I32]),
+    "ddsp_plan_get_tile": (I32, [P] + [C.POINTER(C.c_int)] * 6),
 }
 
 _lib = None

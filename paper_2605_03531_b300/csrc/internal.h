@@ -19,12 +19,21 @@ enum : int32_t { kErrNone = 0, kErrTimeout = 1, kErrRange = 2 };
 constexpr int kThreads = 256;
 constexpr int kElemPerThread = 4;
 
+// DedispTile::flags
+enum : int {
+  kTileSingleElemBuffer = 1,  // one element buffer, two barriers per chunk
+  kTileRegisterTotals = 4,    // int32 totals in registers, not in the output
+  kTileWarpSpecialized = 8,   // producer / consumer warps (k_dedisp_ws.cu)
+};
+
 struct DedispTile {
   int wt = 0;          // warps along time (0: use the direct kernel)
   int wd = 0;          // warps along DM
-  int rd = 4;          // DM trials per thread (2 or 4)
+  int rd = 4;          // DM trials per thread (2 or 4; 4 or 8 when warp-
+                       // specialised)
   int chan_chunk = 0;  // channels staged per pipeline step
   int nbuf = 2;        // raw-window stages (bulk copies in flight + 1)
+  int flags = 0;       // kTile* variant switches
   int dm_tile() const { return wd * rd; }
 };
 
@@ -86,9 +95,15 @@ cudaError_t launch_dedisperse_direct(const Plan &p, const void *d_cm,
                                      int32_t *d_out, cudaStream_t s);
 int dedisp_time_tile(const DedispTile &t, int nbits);
 int dedisp_copy_bytes(const DedispTile &t, int span, int nbits);
-bool dedisp_tile_supported(const DedispTile &t);
+bool dedisp_tile_supported(const DedispTile &t, int nbits);
 
 size_t dedisp_smem_bytes(const DedispTile &t, int span_max, int nbits);
+size_t dedisp_ws_smem_bytes(int chan_chunk, int dm_tile, int rawmax,
+                            int elmax, int nbuf);
+cudaError_t launch_dedisperse_ws(const Plan &p, const void *d_cm,
+                                 int64_t pitch, int64_t nsamp_out,
+                                 int32_t *d_out, cudaStream_t s, int rawmax,
+                                 int elmax, size_t smem);
 
 cudaError_t launch_sps(const Plan &p, const int32_t *d_series,
                        int64_t nsamp_out, float threshold, bool dense,

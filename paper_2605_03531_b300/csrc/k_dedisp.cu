@@ -13,13 +13,13 @@
 //      i, i+S for uint16), S = TT/4.  A shifted read of element (i + delay)
 //      then yields four output times at once whatever the delay's alignment,
 //      so every 32-bit shared load feeds four adds (1 byte of shared traffic
-//      per add).  The element buffer is double-buffered: the relayout of
-//      chunk j+1 follows the accumulation of chunk j with one barrier;
+//      per add).  With two element buffers the relayout of chunk j+1
+//      follows the accumulation of chunk j with one barrier;
 //   3. every thread adds, for each of its RD DM trials and 4 elements, the
-//      element at offset (delay - wbase) into SWAR accumulators:
+//      element at offset (delay - wbase) into SWAR accumulators, two
+//      channels per step so the adds are 3-input:
 //         acc_even += w & 0x00FF00FF   (bytes 0 and 2 in 16-bit lanes)
-//         acc_odd  += w >> 8           (bytes 1..3 as b1 + 2^8 b2 + 2^16 b3,
-//                                       as mad.hi on the FMA pipe)
+//         acc_odd  += w >> 8           (bytes 1..3 as b1 + 2^8 b2 + 2^16 b3)
 //      Both stay exact for <= 256 channels (acc_odd <= 255*256*65793 <
 //      2^32); at least every 256 channels they are unpacked into int32:
 //         s0 = E & 0xFFFF, s2 = E >> 16, r = O - (s2 << 8),
@@ -80,41 +80,41 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity,
   }
 }
 
-// acc += w >> 8 on the FMA pipe: mad.hi(w, 2^24, acc).  `k24` is 2^24 held
-// in a register so the multiply is not turned back into an ALU shift.
-__device__ __forceinline__ uint32_t add_hi(uint32_t acc, uint32_t w,
-                                           uint32_t k24) {
-  uint32_t r;
-  asm("mad.hi.u32 %0, %1, %2, %3;" : "=r"(r) : "r"(w), "r"(k24), "r"(acc));
-  return r;
-}
-
 // Shared-memory layout of one block (bytes, all offsets 16-aligned):
 //   [0, 32)                          up to four mbarriers, one per stage
 //   rel_s[nbuf][cc*DT]               element-byte offsets of a staged chunk
 //   raw[nbuf][cc][rawmax]            raw channel windows (bulk-copy targets)
-//   elem[2][cc][elmax]               interleaved elements (uint32)
+//   elem[1|2][cc][elmax]             interleaved elements (uint32); with two
+//                                    buffers the relayout of chunk j+1
+//                                    follows the adds of chunk j with a
+//                                    single barrier per chunk
 struct SmemLayout {
   int rel_off, rel_stride, raw_off, elem_off, elem_stride, total;
   __host__ __device__ SmemLayout(int cc, int dt, int rawmax, int elmax,
-                                 int nbuf) {
+                                 int nbuf, int nelem) {
     rel_off = 32;
     rel_stride = ((cc * dt * 4 + 15) / 16) * 16;
     raw_off = rel_off + nbuf * rel_stride;
     elem_off = raw_off + nbuf * cc * rawmax;
     elem_stride = cc * elmax * 4;
-    total = elem_off + 2 * elem_stride;
+    total = elem_off + nelem * elem_stride;
   }
 };
 
-template <int WT, int WD, int RD, typename T>
-__global__ void __launch_bounds__(kThreads, RD == 4 ? 2 : 3)
+// Resident blocks per SM the register budget is set for: int32 totals held
+// in registers (RTOT) cost 16*RD registers more per thread.
+__host__ __device__ constexpr int dedisp_min_blocks(int rd, bool rtot) {
+  return rtot ? (rd == 4 ? 2 : 3) : (rd == 4 ? 3 : 4);
+}
+
+template <int WT, int WD, int RD, bool DBUF, bool RTOT, typename T>
+__global__ void __launch_bounds__(kThreads, dedisp_min_blocks(RD, RTOT))
 dedisp_kernel(const T *__restrict__ cm, int64_t pitch, int nchan,
               int64_t nsamp_out, const int2 *__restrict__ desc,
               const int32_t *__restrict__ relb,
               const int32_t *__restrict__ rowmap, int32_t *__restrict__ out,
-              int cc, int nbuf, int rawmax, int elmax, uint32_t k24,
-              int32_t *err, long long timeout_cycles) {
+              int cc, int nbuf, int rawmax, int elmax, int32_t *err,
+              long long timeout_cycles) {
   constexpr int SPE = 4 / sizeof(T);               // samples per element
   constexpr int E = kElemPerThread;
   constexpr int S = 32 * E * WT;                   // elements per segment
@@ -127,7 +127,7 @@ dedisp_kernel(const T *__restrict__ cm, int64_t pitch, int nchan,
   const int wt = warp % WT, wd = warp / WT;
   const int g = blockIdx.x;
   const int64_t T0 = (int64_t)blockIdx.y * TT;
-  const SmemLayout L(cc, DT, rawmax, elmax, nbuf);
+  const SmemLayout L(cc, DT, rawmax, elmax, nbuf, DBUF ? 2 : 1);
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem);
   unsigned char *rel_base = smem + L.rel_off;
   unsigned char *raw = smem + L.raw_off;
@@ -173,19 +173,20 @@ dedisp_kernel(const T *__restrict__ cm, int64_t pitch, int nchan,
                relbytes, &bar[st]);
   };
 
-  // Wait for chunk j's copies, then relayout it into element buffer j & 1,
-  // one warp per channel; only the elements the chunk's offsets can reach
-  // are built.  Returns false (uniformly) if the bounded wait expired.
+  // Wait (bounded) for chunk j's copies and relayout it into its element
+  // buffer, one warp per channel; only the elements the chunk's offsets can
+  // reach are built.  Returns false if this thread's wait expired (it then
+  // skips the relayout; the caller votes on the result at its barrier).
   auto stage_in = [&](int j) -> bool {
     const int st = j % nbuf;
     const int ncur = min(cc, nchan - j * cc);
-    bool ok = mbar_wait(&bar[st], (uint32_t)((j / nbuf) & 1), timeout_cycles);
-    if (__syncthreads_or(!ok)) return false;
+    if (!mbar_wait(&bar[st], (uint32_t)((j / nbuf) & 1), timeout_cycles))
+      return false;
     const int32_t *rel_s =
         reinterpret_cast<const int32_t *>(rel_base + st * L.rel_stride);
     const unsigned char *rb = raw + st * cc * rawmax;
-    uint32_t *eb =
-        reinterpret_cast<uint32_t *>(elem_base + (j & 1) * L.elem_stride);
+    uint32_t *eb = reinterpret_cast<uint32_t *>(
+        elem_base + (DBUF ? (j & 1) : 0) * L.elem_stride);
     for (int q = warp; q < ncur; q += kWarps) {
       const unsigned char *rq = rb + q * rawmax;
       uint32_t *eq = eb + q * elmax;
@@ -232,8 +233,13 @@ dedisp_kernel(const T *__restrict__ cm, int64_t pitch, int nchan,
     }
     load_desc(nbuf - 1);
   }
+  int last_issued = min(nbuf - 2, nchunks - 1);  // same value in every thread
 
-  // SWAR accumulators (uint8) or direct int32 sums (uint16).
+  // SWAR accumulators (uint8) and int32 totals.  With !RTOT (uint8 only)
+  // the totals live in the output array: the owning thread adds each
+  // <= 256-channel partial into its own outputs (the block's output tile
+  // stays in L2), which frees 16*RD registers for more resident warps.
+  constexpr bool kRegTot = RTOT || SPE != 4;
   uint32_t accE[RD][E];
   uint32_t accO[RD][E];
   int32_t tot[RD][E][SPE];
@@ -246,31 +252,45 @@ dedisp_kernel(const T *__restrict__ cm, int64_t pitch, int nchan,
 #pragma unroll
       for (int m = 0; m < SPE; ++m) tot[r][e][m] = 0;
     }
+  bool first_flush = true;
 
   const int i0 = 32 * E * wt + lane;  // first element of this thread
   int failed_at = -1;
   int since = 0;  // channels in the SWAR accumulators since the last widen
 
-  // prologue: chunk 0 into element buffer 0
-  if (!stage_in(0)) failed_at = 0;
-  __syncthreads();
+  // prologue (two element buffers): chunk 0 into element buffer 0
+  if (DBUF) {
+    const bool ok = stage_in(0);
+    if (__syncthreads_or(!ok)) failed_at = 0;
+  }
 
   for (int j = 0; j < nchunks && failed_at < 0; ++j) {
     const int st = j % nbuf;
     const int ncur = min(cc, nchan - j * cc);
     // refill the raw stage the previous relayout consumed
-    if (warp == 0 && j + nbuf - 1 < nchunks) {
-      issue(j + nbuf - 1);
-      load_desc(j + nbuf);
+    if (j + nbuf - 1 < nchunks) {
+      if (warp == 0) {
+        issue(j + nbuf - 1);
+        load_desc(j + nbuf);
+      }
+      last_issued = j + nbuf - 1;
+    }
+    if (!DBUF) {
+      const bool ok = stage_in(j);
+      if (__syncthreads_or(!ok)) {
+        failed_at = j;
+        break;
+      }
     }
     const int32_t *rel_s =
         reinterpret_cast<const int32_t *>(rel_base + st * L.rel_stride);
 
-    // ---- accumulate chunk j from element buffer j & 1
-    const unsigned char *ebase = elem_base + (j & 1) * L.elem_stride + 4 * i0;
-#pragma unroll 2
-    for (int q = 0; q < ncur; ++q) {
-      int rr[RD];
+    // ---- accumulate chunk j from its element buffer, two channels at a
+    // time: acc += (wa & M) + (wb & M) and acc += (wa >> 8) + (wb >> 8) map
+    // to 3-input adds, which halves the add instructions per word
+    const unsigned char *ebase =
+        elem_base + (DBUF ? (j & 1) : 0) * L.elem_stride + 4 * i0;
+    auto offsets = [&](int q, int (&rr)[RD]) {
       if constexpr (RD == 4) {
         const int4 ro =
             *reinterpret_cast<const int4 *>(rel_s + q * DT + RD * wd);
@@ -284,19 +304,48 @@ dedisp_kernel(const T *__restrict__ cm, int64_t pitch, int nchan,
         rr[0] = ro.x;
         rr[1] = ro.y;
       }
-      const unsigned char *eq = ebase + q * elmax * 4;
+    };
+    int q = 0;
+    for (; q + 1 < ncur; q += 2) {
+      int ra[RD], rb[RD];
+      offsets(q, ra);
+      offsets(q + 1, rb);
+      const unsigned char *ea = ebase + q * elmax * 4;
+      const unsigned char *eb = ea + elmax * 4;
 #pragma unroll
       for (int r = 0; r < RD; ++r) {
-        const unsigned char *p = eq + rr[r];
+        const unsigned char *pa = ea + ra[r];
+        const unsigned char *pb = eb + rb[r];
 #pragma unroll
         for (int e = 0; e < E; ++e) {
-          uint32_t w = *reinterpret_cast<const uint32_t *>(p + 128 * e);
+          const uint32_t wa = *reinterpret_cast<const uint32_t *>(pa + 128 * e);
+          const uint32_t wb = *reinterpret_cast<const uint32_t *>(pb + 128 * e);
           if constexpr (SPE == 4) {
-            accE[r][e] += w & 0x00FF00FFu;
-            accO[r][e] = add_hi(accO[r][e], w, k24);
+            accE[r][e] += (wa & 0x00FF00FFu) + (wb & 0x00FF00FFu);
+            accO[r][e] += (wa >> 8) + (wb >> 8);
           } else {
-            tot[r][e][0] += (int32_t)(w & 0xFFFFu);
-            tot[r][e][1] += (int32_t)(w >> 16);
+            tot[r][e][0] += (int32_t)((wa & 0xFFFFu) + (wb & 0xFFFFu));
+            tot[r][e][1] += (int32_t)((wa >> 16) + (wb >> 16));
+          }
+        }
+      }
+    }
+    if (q < ncur) {
+      int ra[RD];
+      offsets(q, ra);
+      const unsigned char *ea = ebase + q * elmax * 4;
+#pragma unroll
+      for (int r = 0; r < RD; ++r) {
+        const unsigned char *pa = ea + ra[r];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const uint32_t wa = *reinterpret_cast<const uint32_t *>(pa + 128 * e);
+          if constexpr (SPE == 4) {
+            accE[r][e] += wa & 0x00FF00FFu;
+            accO[r][e] += wa >> 8;
+          } else {
+            tot[r][e][0] += (int32_t)(wa & 0xFFFFu);
+            tot[r][e][1] += (int32_t)(wa >> 16);
           }
         }
       }
@@ -305,27 +354,57 @@ dedisp_kernel(const T *__restrict__ cm, int64_t pitch, int nchan,
     if constexpr (SPE == 4) {
       since += ncur;
       if (since + cc > 256 || j == nchunks - 1) {
+        if constexpr (kRegTot) {
 #pragma unroll
-        for (int r = 0; r < RD; ++r)
+          for (int r = 0; r < RD; ++r)
 #pragma unroll
-          for (int e = 0; e < E; ++e) {
-            uint32_t Ev = accE[r][e], O = accO[r][e];
-            uint32_t s2 = Ev >> 16;
-            uint32_t rem = O - (s2 << 8);
-            tot[r][e][0] += (int32_t)(Ev & 0xFFFFu);
-            tot[r][e][1] += (int32_t)(rem & 0xFFFFu);
-            tot[r][e][2] += (int32_t)s2;
-            tot[r][e][3] += (int32_t)(rem >> 16);
-            accE[r][e] = 0;
-            accO[r][e] = 0;
+            for (int e = 0; e < E; ++e) {
+              uint32_t Ev = accE[r][e], O = accO[r][e];
+              uint32_t s2 = Ev >> 16;
+              uint32_t rem = O - (s2 << 8);
+              tot[r][e][0] += (int32_t)(Ev & 0xFFFFu);
+              tot[r][e][1] += (int32_t)(rem & 0xFFFFu);
+              tot[r][e][2] += (int32_t)s2;
+              tot[r][e][3] += (int32_t)(rem >> 16);
+              accE[r][e] = 0;
+              accO[r][e] = 0;
+            }
+        } else {
+#pragma unroll
+          for (int r = 0; r < RD; ++r) {
+            const int row = __ldg(rowmap + g * DT + RD * wd + r);
+            int32_t *o = out + (int64_t)(row < 0 ? 0 : row) * nsamp_out;
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+              uint32_t Ev = accE[r][e], O = accO[r][e];
+              uint32_t s2 = Ev >> 16;
+              uint32_t rem = O - (s2 << 8);
+              int32_t part[4] = {(int32_t)(Ev & 0xFFFFu),
+                                 (int32_t)(rem & 0xFFFFu), (int32_t)s2,
+                                 (int32_t)(rem >> 16)};
+#pragma unroll
+              for (int m = 0; m < 4; ++m) {
+                const int64_t t = T0 + i0 + 32 * e + (int64_t)m * S;
+                if (row >= 0 && t < nsamp_out)
+                  o[t] = first_flush ? part[m] : o[t] + part[m];
+              }
+              accE[r][e] = 0;
+              accO[r][e] = 0;
+            }
           }
+          first_flush = false;
+        }
         since = 0;
       }
     }
 
-    // ---- relayout chunk j + 1 into the other element buffer
-    if (j + 1 < nchunks && !stage_in(j + 1)) failed_at = j + 1;
-    __syncthreads();
+    if (DBUF) {
+      // relayout chunk j + 1 into the other buffer; one barrier per chunk
+      const bool ok = (j + 1 < nchunks) ? stage_in(j + 1) : true;
+      if (__syncthreads_or(!ok)) failed_at = j + 1;
+    } else {
+      __syncthreads();  // the element buffer is rewritten next iteration
+    }
   }
 
   if (failed_at >= 0) {
@@ -333,34 +412,35 @@ dedisp_kernel(const T *__restrict__ cm, int64_t pitch, int nchan,
       atomicExch(err, kErrTimeout);
       // let the copies still in flight land before the block retires, again
       // with a bounded wait per chunk
-      const int last = min(failed_at + nbuf - 2, nchunks - 1);
-      for (int jj = failed_at; jj <= last; ++jj)
+      for (int jj = failed_at; jj <= last_issued; ++jj)
         mbar_wait(&bar[jj % nbuf], (uint32_t)((jj / nbuf) & 1), timeout_cycles);
     }
     return;
   }
 
-  // ---- store
+  // ---- store (without kRegTot the totals already sit in the output array)
+  if constexpr (kRegTot) {
 #pragma unroll
-  for (int r = 0; r < RD; ++r) {
-    const int row = rowmap[g * DT + RD * wd + r];
-    if (row < 0) continue;
-    int32_t *o = out + (int64_t)row * nsamp_out;
+    for (int r = 0; r < RD; ++r) {
+      const int row = rowmap[g * DT + RD * wd + r];
+      if (row < 0) continue;
+      int32_t *o = out + (int64_t)row * nsamp_out;
 #pragma unroll
-    for (int e = 0; e < E; ++e)
+      for (int e = 0; e < E; ++e)
 #pragma unroll
-      for (int m = 0; m < SPE; ++m) {
-        const int64_t t = T0 + i0 + 32 * e + (int64_t)m * S;
-        if (t < nsamp_out) o[t] = tot[r][e][m];
-      }
+        for (int m = 0; m < SPE; ++m) {
+          const int64_t t = T0 + i0 + 32 * e + (int64_t)m * S;
+          if (t < nsamp_out) o[t] = tot[r][e][m];
+        }
+    }
   }
 }
 
-template <int WT, int WD, int RD, typename T>
+template <int WT, int WD, int RD, bool DBUF, bool RTOT, typename T>
 cudaError_t launch_t(const Plan &p, const void *d_cm, int64_t pitch,
                      int64_t nsamp_out, int32_t *d_out, cudaStream_t s,
                      int rawmax, int elmax, size_t smem) {
-  auto kern = dedisp_kernel<WT, WD, RD, T>;
+  auto kern = dedisp_kernel<WT, WD, RD, DBUF, RTOT, T>;
   static size_t attr_bytes = 0;
   if (smem > attr_bytes) {
     cudaError_t e = cudaFuncSetAttribute(
@@ -377,7 +457,7 @@ cudaError_t launch_t(const Plan &p, const void *d_cm, int64_t pitch,
       static_cast<const T *>(d_cm), pitch, p.nchan, nsamp_out,
       reinterpret_cast<const int2 *>(p.tab.d_desc), p.tab.d_relb,
       p.tab.d_rowmap, d_out, p.tile.chan_chunk, p.tile.nbuf, rawmax, elmax,
-      1u << 24, p.d_err, timeout);
+      p.d_err, timeout);
   return cudaGetLastError();
 }
 
@@ -404,7 +484,11 @@ static void buffer_sizes(const DedispTile &t, int span_max, int nbits,
 size_t dedisp_smem_bytes(const DedispTile &t, int span_max, int nbits) {
   int rawmax, elmax;
   buffer_sizes(t, span_max, nbits, &rawmax, &elmax);
-  SmemLayout L(t.chan_chunk, t.dm_tile(), rawmax, elmax, t.nbuf);
+  if (t.flags & kTileWarpSpecialized)
+    return dedisp_ws_smem_bytes(t.chan_chunk, t.dm_tile(), rawmax, elmax,
+                                t.nbuf);
+  const bool dbuf = !(t.flags & kTileSingleElemBuffer);
+  SmemLayout L(t.chan_chunk, t.dm_tile(), rawmax, elmax, t.nbuf, dbuf ? 2 : 1);
   return (size_t)L.total;
 }
 
@@ -413,8 +497,23 @@ int dedisp_copy_bytes(const DedispTile &t, int span, int nbits) {
   return ((TT + span) * (nbits / 8) + 15) & ~15;
 }
 
-bool dedisp_tile_supported(const DedispTile &t) {
+bool dedisp_tile_supported(const DedispTile &t, int nbits) {
   if (t.wt * t.wd != kThreads / 32) return false;
+  // instantiated variants (the dispatch list in launch_dedisperse): int32
+  // totals in registers only with one element buffer; uint16 totals are
+  // always in registers (the flag is implied)
+  const int f = t.flags;
+  if (f & kTileWarpSpecialized) {
+    if (f != kTileWarpSpecialized) return false;
+    if (t.rd != 4 && !(t.rd == 8 && nbits == 8)) return false;
+    if (t.wd != 1 && t.wd != 2 && t.wd != 4) return false;
+    if (t.chan_chunk < 1 || t.chan_chunk > 32) return false;
+    return t.nbuf >= 2 && t.nbuf <= 4;
+  }
+  if (f & ~(kTileSingleElemBuffer | kTileRegisterTotals)) return false;
+  if (nbits == 8 && (f & kTileRegisterTotals) && !(f & kTileSingleElemBuffer))
+    return false;
+  if (nbits == 16 && (f & kTileRegisterTotals)) return false;
   if (t.rd != 2 && t.rd != 4) return false;
   if (t.wd != 1 && t.wd != 2 && t.wd != 4) return false;
   if (t.chan_chunk < 1 || t.chan_chunk > 32) return false;
@@ -431,22 +530,42 @@ cudaError_t launch_dedisperse(const Plan &p, const void *d_cm, int64_t pitch,
   int rawmax, elmax;
   buffer_sizes(p.tile, p.tab.span_max, p.nbits, &rawmax, &elmax);
   const size_t smem = dedisp_smem_bytes(p.tile, p.tab.span_max, p.nbits);
+  if (p.tile.flags & kTileWarpSpecialized)
+    return launch_dedisperse_ws(p, d_cm, pitch, nsamp_out, d_out, s, rawmax,
+                                elmax, smem);
   const int wt = p.tile.wt, wd = p.tile.wd, rd = p.tile.rd;
-#define DDSP_CASE(WT_, WD_, RD_)                                             \
-  if (wt == WT_ && wd == WD_ && rd == RD_)                                   \
-    return p.nbits == 8                                                      \
-               ? launch_t<WT_, WD_, RD_, uint8_t>(p, d_cm, pitch, nsamp_out, \
-                                                  d_out, s, rawmax, elmax,   \
-                                                  smem)                      \
-               : launch_t<WT_, WD_, RD_, uint16_t>(p, d_cm, pitch,           \
-                                                   nsamp_out, d_out, s,      \
-                                                   rawmax, elmax, smem);
-  DDSP_CASE(8, 1, 4)
-  DDSP_CASE(4, 2, 4)
-  DDSP_CASE(2, 4, 4)
-  DDSP_CASE(8, 1, 2)
-  DDSP_CASE(4, 2, 2)
-  DDSP_CASE(2, 4, 2)
+  const int f = p.tile.flags;
+  const bool dbuf = !(f & kTileSingleElemBuffer);
+  const bool rtot = (f & kTileRegisterTotals) != 0;
+#define DDSP_CASE(WT_, WD_, RD_, DB_, RT_, T_)                                \
+  if (wt == WT_ && wd == WD_ && rd == RD_ && dbuf == DB_ && rtot == RT_)      \
+    return launch_t<WT_, WD_, RD_, DB_, RT_, T_>(p, d_cm, pitch, nsamp_out,   \
+                                                 d_out, s, rawmax, elmax,     \
+                                                 smem);
+#define DDSP_SHAPE8(WT_, WD_, RD_)                                            \
+  DDSP_CASE(WT_, WD_, RD_, true, false, uint8_t)                              \
+  DDSP_CASE(WT_, WD_, RD_, false, false, uint8_t)                             \
+  DDSP_CASE(WT_, WD_, RD_, false, true, uint8_t)
+#define DDSP_SHAPE16(WT_, WD_, RD_)                                           \
+  DDSP_CASE(WT_, WD_, RD_, true, false, uint16_t)                             \
+  DDSP_CASE(WT_, WD_, RD_, false, false, uint16_t)
+  if (p.nbits == 8) {
+    DDSP_SHAPE8(8, 1, 4)
+    DDSP_SHAPE8(4, 2, 4)
+    DDSP_SHAPE8(2, 4, 4)
+    DDSP_SHAPE8(8, 1, 2)
+    DDSP_SHAPE8(4, 2, 2)
+    DDSP_SHAPE8(2, 4, 2)
+  } else {
+    DDSP_SHAPE16(8, 1, 4)
+    DDSP_SHAPE16(4, 2, 4)
+    DDSP_SHAPE16(2, 4, 4)
+    DDSP_SHAPE16(8, 1, 2)
+    DDSP_SHAPE16(4, 2, 2)
+    DDSP_SHAPE16(2, 4, 2)
+  }
+#undef DDSP_SHAPE16
+#undef DDSP_SHAPE8
 #undef DDSP_CASE
   return cudaErrorInvalidValue;
 }

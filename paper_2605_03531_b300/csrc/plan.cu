@@ -142,10 +142,16 @@ int build_tables(Plan &p) {
 // windows fit with two resident blocks per SM, else one block per SM, else
 // the direct kernel.
 DedispTile choose_tile(const Plan &p) {
-  struct Cand { int wt, wd, rd, cc; };
-  const Cand prefs[] = {{4, 2, 4, 8}, {2, 4, 4, 8}, {4, 2, 4, 6},
-                        {8, 1, 4, 8}, {4, 2, 4, 4}, {8, 1, 4, 4},
-                        {8, 1, 4, 2}, {8, 1, 2, 2}, {8, 1, 2, 1}};
+  // {wt, wd, rd, cc, flags}: the warp-specialised kernel first (fastest on
+  // the 4096-channel 1024-DM block), then the block-synchronous kernel with
+  // totals in registers, then smaller staging footprints
+  struct Cand { int wt, wd, rd, cc, flags; };
+  const Cand prefs[] = {
+      {4, 2, 8, 4, kTileWarpSpecialized}, {8, 1, 8, 4, kTileWarpSpecialized},
+      {4, 2, 4, 8, kTileSingleElemBuffer | kTileRegisterTotals},
+      {4, 2, 4, 6, kTileSingleElemBuffer}, {8, 1, 4, 4, kTileSingleElemBuffer},
+      {8, 1, 4, 2, kTileSingleElemBuffer}, {8, 1, 2, 2, kTileSingleElemBuffer},
+      {8, 1, 2, 1, kTileSingleElemBuffer}};
   for (size_t budget : {kSmemBudgetTwoBlocks, kSmemBudgetOneBlock}) {
     for (const Cand &c : prefs) {
       DedispTile t;
@@ -153,6 +159,8 @@ DedispTile choose_tile(const Plan &p) {
       t.wd = c.wd;
       t.rd = c.rd;
       t.chan_chunk = c.cc;
+      t.flags = c.flags;
+      if (!dedisp_tile_supported(t, p.nbits)) continue;
       const int span = span_for(p, t.dm_tile());
       for (int nbuf : {3, 2}) {
         t.nbuf = nbuf;
@@ -391,7 +399,7 @@ int ddsp_plan_get_delays(const ddsp_plan *h, int32_t *host_out) {
 }
 
 int ddsp_plan_set_tile(ddsp_plan *h, int dm_tile, int dm_per_thread,
-                       int chan_chunk, int stages) {
+                       int chan_chunk, int stages, int flags) {
   if (!h) return DDSP_E_INVALID_ARG;
   Plan &p = h->p;
   DeviceGuard g(p.device);
@@ -402,14 +410,18 @@ int ddsp_plan_set_tile(ddsp_plan *h, int dm_tile, int dm_per_thread,
     t = DedispTile{};  // direct kernel
   } else {
     t.rd = dm_per_thread;
-    if (t.rd != 2 && t.rd != 4) return DDSP_E_INVALID_ARG;
+    if (t.rd != 2 && t.rd != 4 && t.rd != 8) return DDSP_E_INVALID_ARG;
     if (dm_tile % t.rd) return DDSP_E_INVALID_ARG;
     t.wd = dm_tile / t.rd;
     if (t.wd <= 0 || (kThreads / 32) % t.wd) return DDSP_E_INVALID_ARG;
     t.wt = (kThreads / 32) / t.wd;
     t.chan_chunk = chan_chunk;
     t.nbuf = stages;
-    if (!dedisp_tile_supported(t)) return DDSP_E_INVALID_ARG;
+    if (flags & ~(kTileSingleElemBuffer | kTileRegisterTotals |
+                  kTileWarpSpecialized))
+      return DDSP_E_INVALID_ARG;
+    t.flags = flags;
+    if (!dedisp_tile_supported(t, p.nbits)) return DDSP_E_INVALID_ARG;
     const int span = span_for(p, t.dm_tile());
     if (dedisp_smem_bytes(t, span, p.nbits) > kSmemBudgetOneBlock)
       return DDSP_E_INVALID_ARG;
@@ -420,7 +432,8 @@ int ddsp_plan_set_tile(ddsp_plan *h, int dm_tile, int dm_per_thread,
 }
 
 int ddsp_plan_get_tile(const ddsp_plan *h, int *dm_tile, int *dm_per_thread,
-                       int *time_tile, int *chan_chunk, int *stages) {
+                       int *time_tile, int *chan_chunk, int *stages,
+                       int *flags) {
   if (!h) return DDSP_E_INVALID_ARG;
   const Plan &p = h->p;
   const bool staged = p.tile.wt > 0;
@@ -429,6 +442,7 @@ int ddsp_plan_get_tile(const ddsp_plan *h, int *dm_tile, int *dm_per_thread,
   if (time_tile) *time_tile = staged ? dedisp_time_tile(p.tile, p.nbits) : 0;
   if (chan_chunk) *chan_chunk = staged ? p.tile.chan_chunk : 0;
   if (stages) *stages = staged ? p.tile.nbuf : 0;
+  if (flags) *flags = staged ? p.tile.flags : 0;
   return DDSP_OK;
 }
 
