@@ -163,6 +163,36 @@ int ddsp_single_pulse_search_dense(ddsp_plan *plan, const int32_t *d_series,
                                    float *d_best_snr, int32_t *d_best_sum,
                                    ddsp_stream_t stream);
 
+/* The single-pulse search of ddsp_single_pulse_search for callers that
+ * cannot allocate device memory (a fixed device-memory budget, a real-time
+ * loop that must not stall on an allocation, or a host that only hands out
+ * pre-allocated buffers).  There is no counterpart in the paper: it is the
+ * same search, only without a plan.  Nothing is allocated: the scratch
+ * (per-(DM trial, window) statistics, the width table, an error word) is a
+ * static device array of the library of a little over 4 MiB, which every
+ * GPU that loads the library holds until exit.
+ *   d_series   int32 [ndm][nsamp_out] on the current device
+ *   widths     nwidths boxcar widths (host array, as in ddsp_plan_create)
+ *   norm_window, threshold  as in ddsp_plan_create / the plan search
+ *   d_cands    caller's device buffer of cand_capacity records; the
+ *              candidates come back unsorted
+ *   d_count    caller's device uint32: the true number of candidates (may
+ *              exceed cand_capacity; only that many records are written)
+ * Rejects ndm * (number of windows) > 262144 and windows longer than the
+ * plan search allows with DDSP_E_SHAPE, bad arguments with
+ * DDSP_E_INVALID_ARG.  The first call on a device looks up the array's
+ * device address (cudaGetSymbolAddress); make it before any stream
+ * capture.  Every call uses the same array: calls whose work overlaps on a
+ * GPU (different streams, or different host threads) race and must be
+ * serialised by the caller.  A window whose values span 2^31 or more gives
+ * no candidates (its MAD is taken as 0).  Asynchronous on `stream`. */
+int ddsp_single_pulse_search_noalloc(const int32_t *d_series, int ndm,
+                                     int64_t nsamp_out, const int *widths,
+                                     int nwidths, int64_t norm_window,
+                                     float threshold, ddsp_cand *d_cands,
+                                     uint32_t cand_capacity,
+                                     uint32_t *d_count, ddsp_stream_t stream);
+
 /* Copy the per-(DM, window) statistics of the last search to the host:
  * m2[k*nwin + j] = 2*median, mad4[k*nwin + j] = 4*MAD (both exact).  *nwin
  * receives the window count.  Synchronises the last search's stream.

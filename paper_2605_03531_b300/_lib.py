@@ -45,6 +45,8 @@ SIGNATURES = {
     "ddsp_plan_cm_pitch": (I32, [P, I64, PI64]),
     "ddsp_single_pulse_search": (I32, [P, P, I64, C.c_float, P]),
     "ddsp_single_pulse_search_dense": (I32, [P, P, I64, P, P, P, P]),
+    "ddsp_single_pulse_search_noalloc": (I32, [P, I32, I64, P, I32, I64,
+                                               C.c_float, P, C.c_uint32, P, P]),
     "ddsp_plan_get_stats": (I32, [P, P, P, I64, PI64]),
     "ddsp_candidates_fetch": (I32, [P, P, C.c_size_t, C.POINTER(C.c_size_t)]),
     "ddsp_candidates_fetch_dm_range": (I32, [P, C.c_uint32, C.c_uint32, P,

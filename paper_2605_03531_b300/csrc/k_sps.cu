@@ -390,3 +390,102 @@ cudaError_t launch_sps(const Plan &p, const int32_t *d_series,
 }
 
 }  // namespace ddsp
+
+// ===========================================================================
+// Single-pulse search without any allocation.
+//
+// Some callers cannot call cudaMalloc: code that runs under a device memory
+// budget fixed in advance, real-time loops where an allocation (which may
+// synchronise the device) would break the latency budget, or hosts that
+// hand this library pre-allocated buffers only.  For them the search's
+// scratch -- the per-(DM trial, window) median/MAD statistics, the width
+// table and the error word -- lives in one file-scope device array instead
+// of a plan's workspace.  Every GPU that loads the library holds this array
+// (a little over 4 MiB) until the process exits.
+// ===========================================================================
+namespace ddsp {
+namespace {
+
+constexpr int64_t kNoAllocMaxWindows = 262144;  // (DM trial, window) slots
+constexpr size_t kNoAllocStatsBytes = (size_t)kNoAllocMaxWindows * 8;
+// layout: m2[kNoAllocMaxWindows] | mad4[kNoAllocMaxWindows] | widths[16] |
+//         error word
+constexpr size_t kNoAllocWidthsOff = 2 * kNoAllocStatsBytes;
+constexpr size_t kNoAllocErrOff = kNoAllocWidthsOff + 16 * sizeof(int32_t);
+constexpr size_t kNoAllocBytes = kNoAllocErrOff + 256;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+// device address of g_noalloc_scratch per device, found once per device
+unsigned char *g_noalloc_ptr[kNoAllocMaxDevices] = {};
+size_t g_noalloc_attr[kNoAllocMaxDevices] = {};
+
+}  // namespace
+}  // namespace ddsp
+
+extern "C" int ddsp_single_pulse_search_noalloc(
+    const int32_t *d_series, int ndm, int64_t nsamp_out, const int *widths,
+    int nwidths, int64_t norm_window, float threshold, ddsp_cand *d_cands,
+    uint32_t cand_capacity, uint32_t *d_count, ddsp_stream_t stream) {
+  using namespace ddsp;
+  if (!d_series || !widths || !d_cands || !d_count || ndm <= 0 ||
+      ndm > 65535 || nsamp_out <= 0 || nsamp_out > 0x7fffffffLL ||
+      nwidths <= 0 || nwidths > kMaxWidths || norm_window < 0 ||
+      cand_capacity == 0 || !(threshold > 0.0f) || !isfinite(threshold))
+    return DDSP_E_INVALID_ARG;
+  for (int i = 0; i < nwidths; ++i) {
+    const int w = widths[i];
+    if (w < 1 || w > 1024 || (w & (w - 1)) != 0) return DDSP_E_INVALID_ARG;
+    if (i > 0 && w <= widths[i - 1]) return DDSP_E_INVALID_ARG;
+  }
+  const int64_t L = norm_window;
+  const int64_t nwin = (L <= 0) ? 1 : max((int64_t)1, nsamp_out / L);
+  const int64_t maxlen =
+      (L <= 0 || nwin == 1) ? nsamp_out : max(L, nsamp_out - (nwin - 1) * L);
+  const int wmax = widths[nwidths - 1];
+  if (maxlen + wmax > kMaxWindowSamples) return DDSP_E_SHAPE;
+  // the statistics of every (DM trial, window) must fit the static scratch
+  if ((int64_t)ndm * nwin > kNoAllocMaxWindows) return DDSP_E_SHAPE;
+
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices)
+    return DDSP_E_CUDA;
+  if (!g_noalloc_ptr[dev]) {
+    // once per device, with that device current: the host-side name of the
+    // array is only a stand-in, the kernel needs its device address
+    unsigned char *ptr = nullptr;
+    if (cudaGetSymbolAddress((void **)&ptr, g_noalloc_scratch) != cudaSuccess ||
+        !ptr)
+      return DDSP_E_CUDA;
+    g_noalloc_ptr[dev] = ptr;
+  }
+  unsigned char *base = g_noalloc_ptr[dev];
+  int64_t *m2 = reinterpret_cast<int64_t *>(base);
+  int64_t *mad4 = reinterpret_cast<int64_t *>(base + kNoAllocStatsBytes);
+  int32_t *d_widths = reinterpret_cast<int32_t *>(base + kNoAllocWidthsOff);
+  int32_t *d_err = reinterpret_cast<int32_t *>(base + kNoAllocErrOff);
+
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t smem = sizeof(SpsShared) + 4 * (size_t)(maxlen + wmax + 4);
+  auto kern = sps_kernel<false>;
+  if (smem > g_noalloc_attr[dev]) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) != cudaSuccess)
+      return DDSP_E_CUDA;
+    g_noalloc_attr[dev] = smem;
+  }
+  // the array keeps the previous call's contents: reset what must start at
+  // zero (the caller's counter and the error word), refresh the widths
+  if (cudaMemsetAsync(d_count, 0, sizeof(uint32_t), s) != cudaSuccess ||
+      cudaMemsetAsync(d_err, 0, sizeof(int32_t), s) != cudaSuccess ||
+      cudaMemcpyAsync(d_widths, widths, sizeof(int32_t) * nwidths,
+                      cudaMemcpyHostToDevice, s) != cudaSuccess)
+    return DDSP_E_CUDA;
+  dim3 grid((unsigned)nwin, (unsigned)ndm);
+  kern<<<grid, kSpsThreads, smem, s>>>(d_series, nsamp_out, L, nwin, d_widths,
+                                       nwidths, threshold, m2, mad4, d_cands,
+                                       d_count, cand_capacity, nullptr, nullptr,
+                                       nullptr, d_err);
+  return cudaGetLastError() == cudaSuccess ? DDSP_OK : DDSP_E_CUDA;
+}
