@@ -252,8 +252,11 @@ def run_ours(args):
                 cfg.widths, nbits=8, norm_window=cfg.norm_window,
                 cand_capacity=1 << 20)
     D = plan.max_delay
-    nout = cfg.nsamp_out
+    nout = args.nsamp_out or cfg.nsamp_out
     nin = nout + D
+    tile = plan.get_tile()
+    kname = ("dedisp_ws_kernel" if tile["flags"] & 8 else
+             "dedisp_kernel" if tile["dm_tile"] > 0 else "dedisp_direct_kernel")
     x = synth.noise_u8(nin, cfg.nchan, cfg.seed, device=dev)
     synth.inject_pulses(x, cfg.pulses, cfg.f_top, cfg.chan_bw, cfg.tsamp, cfg.seed)
     pitch = plan.cm_pitch(nout)
@@ -287,8 +290,9 @@ def run_ours(args):
     vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
     smi_index = vis.split(",")[idx] if vis and vis.split(",")[idx].isdigit() else idx
     clocks = ClockSampler(smi_index)
-    clocks.start()
-    time.sleep(0.5)
+    if not args.profile:
+        clocks.start()
+        time.sleep(0.5)
     barrier(world)
     torch.cuda.synchronize(dev)
     start.record(stream)
@@ -306,6 +310,14 @@ def run_ours(args):
     k_dedisp = statistics.mean(e[1].elapsed_time(e[2]) for e in evs)
     k_sps = statistics.mean(e[2].elapsed_time(e[3]) for e in evs)
     value = world * adds / (ms_step * 1e-3)
+
+    if args.profile:   # kernels only (for profiler captures)
+        if rank == 0:
+            print(json.dumps({"profile": True, "workload": "beam", "nsamp_out": nout,
+                              "ms_per_step": ms_step, "dedisp_ms": k_dedisp,
+                              "sps_ms": k_sps, "unpack_ms": k_unpack,
+                              "tile": tile}), flush=True)
+        return 0
 
     # ---- end to end through the public call with host buffers
     xh = torch.empty((nin, cfg.nchan), dtype=torch.uint8, pin_memory=True)
@@ -342,7 +354,7 @@ def run_ours(args):
     clk = sm_mhz or peaks.get("sm_max_mhz", 2032.0)
     peak = SM_COUNT_B300 * ADDS_PER_SM_CLK * clk * 1e6 / 1e12
     achieved = adds / (k_dedisp * 1e-3) / 1e12
-    traffic = traffic_record("dedisp")
+    traffic = traffic_record(kname) if nout == cfg.nsamp_out else None
     hbm_peak = peaks.get("hbm_gbs", 6400.0)
     sps_bytes = 4.0 * cfg.ndm * nout + 16 * ncand
     unpack_bytes = 2.0 * nin * cfg.nchan
@@ -357,7 +369,7 @@ def run_ours(args):
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
                          "unit": "Tadd/s", "frac": achieved / peak,
                          "traffic": traffic,
-                         "kernel": "dedisp_kernel",
+                         "kernel": kname, "tile": tile,
                          "peak_basis": f"{SM_COUNT_B300} SMs x {ADDS_PER_SM_CLK} "
                                        f"adds/clk x {clk:.0f} MHz "
                                        "(median SM clock sampled in the timed region)"},
@@ -391,17 +403,100 @@ def run_ours(args):
     return 0
 
 
+# ------------------------------------------------ search-only stress workload
+SPS_METRIC = "single-pulse search series samples/s"
+
+
+def run_sps(args):
+    """2048 DM trials x 1048576 int32 samples (seeded Gaussian, mean 524288,
+    sd 1024, 0.1% boxcar events of width 1..1024 and S/N 6..50), widths
+    1..1024, median/MAD windows of 8192, FP32 S/N, threshold 6.5.  A step is
+    the search kernel plus the read-back of the candidate count; the
+    candidate records (about a third of all samples: no peak merging) stay on
+    the device.  HBM-bound: 4 bytes per series sample read once plus 16 bytes
+    per candidate record written."""
+    import torch
+    from paper_2605_03531_b300 import Plan, build, synth
+    build.build()
+    world, rank, local = dist_setup(args.gpus)
+    dev = torch.device("cuda", local if world > 1 else 0)
+    ndm, n = args.ndm or 2048, args.nsamp or (1 << 20)
+    widths = [1 << i for i in range(11)]
+    L, thr = 8192, 6.5
+    x = synth.gaussian_series(ndm, n, seed=4 + 1000 * rank, device=dev)
+    cap = min(1 << 30, ndm * n)
+    plan = Plan(16, 500.0, -1.0, 1e-3, np.zeros(ndm), widths, nbits=8,
+                norm_window=L, cand_capacity=cap)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        plan.single_pulse_search(x, thr, stream=stream)
+        return plan.count()
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    ncand = 0
+    for _ in range(args.steps):
+        ncand = step()
+    end.record(stream)
+    torch.cuda.synchronize(dev)
+    ms = max_over_ranks(start.elapsed_time(end), world) / args.steps
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm = peaks.get("hbm_gbs", 6400.0)
+    nbytes = 4.0 * ndm * n + 16.0 * min(ncand, cap)
+    achieved = nbytes / (ms * 1e-3) / 1e9
+    if rank == 0:
+        print(json.dumps({
+            "metric": SPS_METRIC, "value": world * ndm * n / (ms * 1e-3),
+            "unit": "samples/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": f"single-pulse search stress: {ndm} DM trials x "
+                                   f"{n} int32 samples, widths 1-1024, L=8192, "
+                                   "thr 6.5", "ndm": ndm, "nsamp": n,
+                       "l2": "inputs larger than L2"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm,
+                         "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                         "kernel": "sps_kernel"},
+            "candidates_per_step": int(ncand), "gpu_launches": args.steps,
+            "profile": bool(args.profile)}), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=["beam", "sps"], default="beam",
+                    help="beam: the full path on one 4096-channel beam block "
+                         "(headline); sps: the search-only stress case")
+    ap.add_argument("--nsamp-out", type=int, default=0,
+                    help="beam: output samples per trial (0 = 262144)")
+    ap.add_argument("--ndm", type=int, default=0, help="sps: DM trials (0 = 2048)")
+    ap.add_argument("--nsamp", type=int, default=0,
+                    help="sps: samples per trial (0 = 1048576)")
+    ap.add_argument("--profile", action="store_true",
+                    help="kernels only: no clocks, end-to-end or CPU baseline "
+                         "(for profiler captures)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "sps":
+        return run_sps(args)
     return run_ours(args)
 
 

@@ -209,6 +209,10 @@ int ddsp_plan_get_stats(ddsp_plan *plan, int64_t *m2, int64_t *mad4,
 int ddsp_candidates_fetch(ddsp_plan *plan, ddsp_cand *host_buf, size_t cap,
                           size_t *n_total);
 
+/* Wait for the last search and report only the number of candidates it
+ * found (no records are copied).  Error codes as ddsp_candidates_fetch. */
+int ddsp_candidates_count(ddsp_plan *plan, size_t *n_total);
+
 /* Like ddsp_candidates_fetch, restricted to DM-trial indices in
  * [dm_lo, dm_hi): the stored records are streamed to the host in bounded
  * pieces and filtered there, so a caller can inspect a few DM rows of a very

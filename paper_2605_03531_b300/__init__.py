@@ -196,6 +196,13 @@ class Plan:
         _lib.check(rc, "ddsp_candidates_fetch")
         return buf[:n.value].copy(), n.value
 
+    def count(self):
+        """Number of candidates the last search found (no records copied)."""
+        n = C.c_size_t()
+        _lib.check(_lib.lib().ddsp_candidates_count(self._h, C.byref(n)),
+                   "ddsp_candidates_count")
+        return n.value
+
     def fetch_dm_range(self, dm_lo, dm_hi, cap=1 << 22):
         """(candidates with dm_lo <= dm_idx < dm_hi sorted, count in range,
         device count)."""

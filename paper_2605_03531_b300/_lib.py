@@ -49,6 +49,7 @@ SIGNATURES = {
                                                C.c_float, P, C.c_uint32, P, P]),
     "ddsp_plan_get_stats": (I32, [P, P, P, I64, PI64]),
     "ddsp_candidates_fetch": (I32, [P, P, C.c_size_t, C.POINTER(C.c_size_t)]),
+    "ddsp_candidates_count": (I32, [P, C.POINTER(C.c_size_t)]),
     "ddsp_candidates_fetch_dm_range": (I32, [P, C.c_uint32, C.c_uint32, P,
                                              C.c_size_t, C.POINTER(C.c_size_t),
                                              C.POINTER(C.c_size_t)]),

@@ -588,6 +588,20 @@ int ddsp_candidates_fetch(ddsp_plan *h, ddsp_cand *host_buf, size_t cap,
   return ncopy < cnt ? DDSP_E_TRUNCATED : DDSP_OK;
 }
 
+int ddsp_candidates_count(ddsp_plan *h, size_t *n_total) {
+  if (!h || !n_total) return DDSP_E_INVALID_ARG;
+  Plan &p = h->p;
+  if (!p.searched) return DDSP_E_STATE;
+  DeviceGuard g(p.device);
+  cudaError_t e = cudaStreamSynchronize(p.last_stream);
+  if (e != cudaSuccess) return cuda_rc(e);
+  uint32_t cnt = 0;
+  e = cudaMemcpy(&cnt, p.d_count, 4, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_rc(e);
+  *n_total = cnt;
+  return read_err(p);
+}
+
 int ddsp_candidates_fetch_dm_range(ddsp_plan *h, uint32_t dm_lo,
                                    uint32_t dm_hi, ddsp_cand *host_buf,
                                    size_t cap, size_t *n_range,
