@@ -235,6 +235,75 @@ void ddsp_plan_destroy(ddsp_plan *plan);
 /* Static, human-readable text for a DDSP_* code. */
 const char *ddsp_error_string(int code);
 
+/* ---------------------------------------------------------------------
+ * Batches: many beams of uneven shape (channel counts, block lengths, DM
+ * grids) searched together.  One step = a batched unpack launch, ONE
+ * persistent dedispersion launch whose blocks take (beam, DM tile, time
+ * tile) work items from a device queue, and a batched search launch; the
+ * step can be replayed from a captured CUDA graph.  Every beam's results are
+ * the same as its plan would give alone (same exact sums).
+ * --------------------------------------------------------------------- */
+typedef struct ddsp_batch ddsp_batch;
+
+/* Create a batch over `nbeams` plans (uint8, nchan a multiple of 16, all on
+ * the current device); nsamp_in[b] input samples per beam.  The batch owns
+ * each beam's channel-major input rows (filled by ddsp_batch_ingest from a
+ * time-major block, or written directly: see ddsp_batch_input).  Output
+ * series [ndm][nsamp_out] go to d_series[b] (caller-owned device buffers
+ * that must outlive the batch) or, where d_series or d_series[b] is NULL, to
+ * buffers the batch allocates (ddsp_batch_series); candidates go to each
+ * plan's own buffer (read them with ddsp_candidates_fetch on that plan
+ * after ddsp_batch_run).  The plans must outlive the batch.  Chooses a
+ * common tile shape that fits every beam.  DDSP_E_SHAPE if a block is
+ * shorter than its plan's largest delay. */
+int ddsp_batch_create(ddsp_batch **out, ddsp_plan *const *plans, int nbeams,
+                      const int64_t *nsamp_in, int32_t *const *d_series);
+void ddsp_batch_destroy(ddsp_batch *batch);
+
+/* Unpack (step 2 of the path) a beam's time-major block d_in[nsamp_in]
+ * [nchan] (16-byte aligned, the caller's) into the batch's channel-major
+ * rows of that beam.  Asynchronous on `stream`. */
+int ddsp_batch_ingest(ddsp_batch *batch, int beam, const void *d_in,
+                      ddsp_stream_t stream);
+
+/* Device pointer and row pitch (samples) of a beam's channel-major rows
+ * [nchan][pitch] (rows past nsamp_in must hold zeros or any readable
+ * bytes), and of its output series [ndm][nsamp_out]. */
+int ddsp_batch_input(ddsp_batch *batch, int beam, void **d_cm, int64_t *pitch,
+                     int64_t *nsamp_in);
+int ddsp_batch_series(ddsp_batch *batch, int beam, int32_t **d_series,
+                      int64_t *nsamp_out);
+
+/* One batch step on `stream` (asynchronous): persistent dedispersion and
+ * single-pulse search (threshold > 0) of every beam's ingested rows.  With
+ * use_graph != 0 the step is captured once into a CUDA graph (on an
+ * internal stream) and replayed on `stream` afterwards; the first call
+ * after creation or a tile change runs directly.  Synchronises only when it
+ * (re)captures. */
+int ddsp_batch_run(ddsp_batch *batch, float threshold, int use_graph,
+                   ddsp_stream_t stream);
+
+/* Synchronise `stream` and report a device-side timeout or range error of
+ * the last batch step (DDSP_E_TIMEOUT / DDSP_E_RANGE), then clear it. */
+int ddsp_batch_check(ddsp_batch *batch, ddsp_stream_t stream);
+
+/* The batch's warp-specialised tile (see ddsp_plan_set_tile) and the
+ * persistent grid size.  set_tile returns DDSP_E_INVALID_ARG if the shape
+ * does not fit every beam on chip.  Both synchronise. */
+int ddsp_batch_set_tile(ddsp_batch *batch, int dm_tile, int dm_per_thread,
+                        int chan_chunk, int stages);
+int ddsp_batch_get_tile(const ddsp_batch *batch, int *dm_tile,
+                        int *dm_per_thread, int *time_tile, int *chan_chunk,
+                        int *stages, int *grid);
+
+/* Autotuner: time the persistent dedispersion of the batch (best of `reps`
+ * runs after one warm-up, on the current input buffers) for each tile shape
+ * of the library's candidate list, keep the fastest.  ms_out[i] (up to cap
+ * entries, may be NULL) receives candidate i's time or -1 if it does not
+ * fit; *ntried the number of candidates, *best the chosen index. */
+int ddsp_batch_autotune(ddsp_batch *batch, int reps, ddsp_stream_t stream,
+                        float *ms_out, int cap, int *ntried, int *best);
+
 /* Name and text of the last CUDA error this library saw on the calling
  * host thread (empty if none); the storage is the library's. */
 const char *ddsp_last_error_detail(void);

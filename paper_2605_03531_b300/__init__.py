@@ -15,7 +15,7 @@ import numpy as np
 from . import _lib
 from ._lib import DdspError, DdspCand
 
-__all__ = ["Plan", "DdspError", "CAND_DTYPE", "delay_table"]
+__all__ = ["Plan", "Batch", "DdspError", "CAND_DTYPE", "delay_table"]
 
 CAND_DTYPE = np.dtype([("dm_idx", np.uint32), ("t", np.uint32),
                        ("w_idx", np.uint32), ("snr", np.float32)])
@@ -247,3 +247,87 @@ class Plan:
 
     def __exit__(self, *a):
         self.close()
+
+
+class Batch:
+    """Many plans (beams of uneven shape) searched together: one persistent
+    dedispersion launch plus one batched search launch per step, optionally
+    replayed from a captured CUDA graph (``ddsp_batch_*``)."""
+
+    def __init__(self, plans, nsamp_in, series=None):
+        import torch
+        self.plans = list(plans)
+        self.nbeams = len(self.plans)
+        self.nsamp_in = [int(n) for n in nsamp_in]
+        if series is None:
+            series = [torch.empty((p.ndm, p.nsamp_out(n)), dtype=torch.int32,
+                                  device="cuda")
+                      for p, n in zip(self.plans, self.nsamp_in)]
+        self.series = series
+        hs = (C.c_void_p * self.nbeams)(*[p._h.value for p in self.plans])
+        ns = (C.c_int64 * self.nbeams)(*self.nsamp_in)
+        outs = (C.c_void_p * self.nbeams)(
+            *[_dev_ptr(t, torch.int32, "series").value for t in series])
+        self._h = C.c_void_p()
+        _lib.check(_lib.lib().ddsp_batch_create(
+            C.byref(self._h), hs, self.nbeams, ns, outs), "ddsp_batch_create")
+
+    def ingest(self, beam, x, stream=None):
+        """Unpack beam `beam`'s time-major block (CUDA uint8 tensor)."""
+        import torch
+        _lib.check(_lib.lib().ddsp_batch_ingest(
+            self._h, int(beam), _dev_ptr(x, torch.uint8, "spectra"),
+            _stream_handle(stream)), "ddsp_batch_ingest")
+
+    def input_rows(self, beam):
+        """(device pointer, pitch, nsamp_in) of a beam's channel-major rows."""
+        ptr, pitch, nin = C.c_void_p(), C.c_int64(), C.c_int64()
+        _lib.check(_lib.lib().ddsp_batch_input(
+            self._h, int(beam), C.byref(ptr), C.byref(pitch), C.byref(nin)),
+            "ddsp_batch_input")
+        return ptr.value, pitch.value, nin.value
+
+    def run(self, threshold, use_graph=True, stream=None):
+        _lib.check(_lib.lib().ddsp_batch_run(self._h, float(threshold),
+                                             int(bool(use_graph)),
+                                             _stream_handle(stream)),
+                   "ddsp_batch_run")
+
+    def check(self, stream=None):
+        _lib.check(_lib.lib().ddsp_batch_check(self._h, _stream_handle(stream)),
+                   "ddsp_batch_check")
+
+    def set_tile(self, dm_tile, dm_per_thread, chan_chunk, stages):
+        _lib.check(_lib.lib().ddsp_batch_set_tile(
+            self._h, int(dm_tile), int(dm_per_thread), int(chan_chunk),
+            int(stages)), "ddsp_batch_set_tile")
+
+    def get_tile(self):
+        v = [C.c_int() for _ in range(6)]
+        _lib.check(_lib.lib().ddsp_batch_get_tile(self._h, *[C.byref(a) for a in v]),
+                   "ddsp_batch_get_tile")
+        keys = ("dm_tile", "dm_per_thread", "time_tile", "chan_chunk", "stages",
+                "grid")
+        return dict(zip(keys, (a.value for a in v)))
+
+    def autotune(self, reps=2, stream=None):
+        """Time every candidate tile, keep the fastest; returns
+        (list of ms per candidate (-1 = does not fit), chosen index)."""
+        cap = 64
+        ms = (C.c_float * cap)()
+        nt, best = C.c_int(), C.c_int()
+        _lib.check(_lib.lib().ddsp_batch_autotune(
+            self._h, int(reps), _stream_handle(stream), ms, cap, C.byref(nt),
+            C.byref(best)), "ddsp_batch_autotune")
+        return [ms[i] for i in range(nt.value)], best.value
+
+    def close(self):
+        if self._h:
+            _lib.lib().ddsp_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

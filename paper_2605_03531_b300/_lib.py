@@ -54,6 +54,17 @@ SIGNATURES = {
                                              C.c_size_t, C.POINTER(C.c_size_t),
                                              C.POINTER(C.c_size_t)]),
     "ddsp_plan_check": (I32, [P, P]),
+    "ddsp_batch_create": (I32, [C.POINTER(P), P, I32, P, P]),
+    "ddsp_batch_destroy": (None, [P]),
+    "ddsp_batch_input": (I32, [P, I32, C.POINTER(P), PI64, PI64]),
+    "ddsp_batch_ingest": (I32, [P, I32, P, P]),
+    "ddsp_batch_series": (I32, [P, I32, C.POINTER(P), PI64]),
+    "ddsp_batch_run": (I32, [P, C.c_float, I32, P]),
+    "ddsp_batch_check": (I32, [P, P]),
+    "ddsp_batch_set_tile": (I32, [P, I32, I32, I32, I32]),
+    "ddsp_batch_get_tile": (I32, [P] + [C.POINTER(C.c_int)] * 6),
+    "ddsp_batch_autotune": (I32, [P, I32, P, C.POINTER(C.c_float), I32,
+                                  C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "ddsp_plan_destroy": (None, [P]),
     "ddsp_error_string": (C.c_char_p, [I32]),
     "ddsp_last_error_detail": (C.c_char_p, []),

@@ -82,6 +82,28 @@ struct Plan {
   cudaStream_t last_stream = nullptr;
 };
 
+// ---- multi-beam descriptors (device arrays built by the batch) ---------
+struct UnpackBeam {          // one beam of the batched unpack
+  const uint8_t *in;         // time-major [nsamp_in][nchan]
+  uint8_t *out;              // channel-major [nchan][pitch]
+  int64_t nsamp_in, pitch, block0;
+  int nchan, pad;
+};
+
+struct SpsBeam {             // one beam of the batched search
+  const int32_t *series;     // [ndm][n]
+  const int32_t *widths;
+  int64_t *m2, *mad4;
+  ddsp_cand *cands;
+  uint32_t *count;
+  int32_t *err;
+  int64_t n, L, nwin, block0;
+  int ndm, nw;
+  uint32_t cap, pad;
+};
+
+struct WsBeam;  // ws_item.cuh
+
 // ---- launchers (each returns a cudaError_t from the launch) ------------
 cudaError_t launch_unpack(const void *d_in, int64_t nsamp_in, int nchan,
                           int nbits, void *d_out, int64_t pitch,
@@ -98,6 +120,8 @@ int dedisp_copy_bytes(const DedispTile &t, int span, int nbits);
 bool dedisp_tile_supported(const DedispTile &t, int nbits);
 
 size_t dedisp_smem_bytes(const DedispTile &t, int span_max, int nbits);
+void dedisp_buffer_sizes(const DedispTile &t, int span_max, int nbits,
+                         int *rawmax, int *elmax);
 size_t dedisp_ws_smem_bytes(int chan_chunk, int dm_tile, int rawmax,
                             int elmax, int nbuf);
 cudaError_t launch_dedisperse_ws(const Plan &p, const void *d_cm,
@@ -111,6 +135,23 @@ cudaError_t launch_sps(const Plan &p, const int32_t *d_series,
                        int32_t *d_best_sum, cudaStream_t s);
 
 int64_t sps_max_window_samples();
+
+int persistent_blocks_per_sm(const DedispTile &t, size_t smem);
+cudaError_t launch_batch_reset(int *d_queue, uint32_t *const *d_counts,
+                               int ncounts, cudaStream_t s);
+cudaError_t launch_dedisperse_persistent(const DedispTile &t,
+                                         const WsBeam *d_beams,
+                                         const int4 *d_items, int nitems,
+                                         int *d_queue, int rawmax, int elmax,
+                                         size_t smem, int32_t *d_err, int grid,
+                                         cudaStream_t s);
+int64_t unpack_batch_blocks(int64_t pitch, int nchan);
+cudaError_t launch_unpack_batch(const UnpackBeam *d_beams, int nbeams,
+                                int64_t total_blocks, cudaStream_t s);
+size_t sps_smem_bytes(int64_t maxlen, int wmax);
+cudaError_t launch_sps_batch(const SpsBeam *d_beams, int nbeams,
+                             int64_t total_blocks, float threshold,
+                             size_t smem, cudaStream_t s);
 
 }  // namespace ddsp
 

@@ -468,7 +468,14 @@ static int time_tile_of(const DedispTile &t, int nbits) {
   return (nbits == 8 ? 4 : 2) * 32 * kElemPerThread * t.wt;
 }
 
+void dedisp_buffer_sizes(const DedispTile &t, int span_max, int nbits,
+                         int *rawmax, int *elmax);
 static void buffer_sizes(const DedispTile &t, int span_max, int nbits,
+                         int *rawmax, int *elmax) {
+  dedisp_buffer_sizes(t, span_max, nbits, rawmax, elmax);
+}
+
+void dedisp_buffer_sizes(const DedispTile &t, int span_max, int nbits,
                          int *rawmax, int *elmax) {
   const int S = 32 * kElemPerThread * t.wt;
   const int TT = time_tile_of(t, nbits);

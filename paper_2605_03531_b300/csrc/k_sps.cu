@@ -185,22 +185,22 @@ __device__ void select2(KeyFn key, int n, int r1, int r2, uint32_t kmax,
   }
 }
 
+// The search of one (DM trial k, window j): the body of the per-plan kernel
+// and of the multi-beam kernel (k_batch.cu).
 template <bool DENSE>
-__global__ void __launch_bounds__(kSpsThreads)
-sps_kernel(const int32_t *__restrict__ series, int64_t n, int64_t L,
-           int64_t nwin, const int32_t *__restrict__ widths, int nw, float thr,
-           int64_t *__restrict__ m2_out, int64_t *__restrict__ mad4_out,
-           ddsp_cand *__restrict__ cands, uint32_t *__restrict__ count,
-           uint32_t cap, int32_t *__restrict__ best_w,
-           float *__restrict__ best_snr, int32_t *__restrict__ best_sum,
-           int32_t *__restrict__ err) {
+__device__ __forceinline__ void sps_window(
+    const int32_t *__restrict__ series, int64_t n, int64_t L, int64_t nwin,
+    const int32_t *__restrict__ widths, int nw, float thr,
+    int64_t *__restrict__ m2_out, int64_t *__restrict__ mad4_out,
+    ddsp_cand *__restrict__ cands, uint32_t *__restrict__ count, uint32_t cap,
+    int32_t *__restrict__ best_w, float *__restrict__ best_snr,
+    int32_t *__restrict__ best_sum, int32_t *__restrict__ err,
+    const int64_t j, const int k) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SpsShared &sh = *reinterpret_cast<SpsShared *>(smem_raw);
   int32_t *buf = reinterpret_cast<int32_t *>(smem_raw + sizeof(SpsShared));
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t j = blockIdx.x;
-  const int k = blockIdx.y;
   const int64_t lo = (L <= 0) ? 0 : j * L;
   const int64_t hi = (L <= 0 || j == nwin - 1) ? n : (j + 1) * L;
   const int wmax = widths[nw - 1];
@@ -357,9 +357,62 @@ sps_kernel(const int32_t *__restrict__ series, int64_t n, int64_t L,
   }
 }
 
+template <bool DENSE>
+__global__ void __launch_bounds__(kSpsThreads)
+sps_kernel(const int32_t *__restrict__ series, int64_t n, int64_t L,
+           int64_t nwin, const int32_t *__restrict__ widths, int nw, float thr,
+           int64_t *__restrict__ m2_out, int64_t *__restrict__ mad4_out,
+           ddsp_cand *__restrict__ cands, uint32_t *__restrict__ count,
+           uint32_t cap, int32_t *__restrict__ best_w,
+           float *__restrict__ best_snr, int32_t *__restrict__ best_sum,
+           int32_t *__restrict__ err) {
+  sps_window<DENSE>(series, n, L, nwin, widths, nw, thr, m2_out, mad4_out,
+                    cands, count, cap, best_w, best_snr, best_sum, err,
+                    blockIdx.x, blockIdx.y);
+}
+
+// Many beams in one launch: flattened block b -> the beam whose block0 is
+// the largest <= b, then (DM trial, window) inside it.
+__global__ void __launch_bounds__(kSpsThreads)
+sps_batch_kernel(const SpsBeam *__restrict__ beams, int nbeams, float thr) {
+  const int64_t bid = blockIdx.x;
+  int lo = 0, hi = nbeams - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (beams[mid].block0 <= bid) lo = mid; else hi = mid - 1;
+  }
+  const SpsBeam &b = beams[lo];
+  const int64_t local = bid - b.block0;
+  const int k = (int)(local / b.nwin);
+  const int64_t j = local - (int64_t)k * b.nwin;
+  sps_window<false>(b.series, b.n, b.L, b.nwin, b.widths, b.nw, thr, b.m2,
+                    b.mad4, b.cands, b.count, b.cap, nullptr, nullptr,
+                    nullptr, b.err, j, k);
+}
+
 }  // namespace
 
 int64_t sps_max_window_samples() { return kMaxWindowSamples; }
+
+size_t sps_smem_bytes(int64_t maxlen, int wmax) {
+  return sizeof(SpsShared) + 4 * (size_t)(maxlen + wmax + 4);
+}
+
+cudaError_t launch_sps_batch(const SpsBeam *d_beams, int nbeams,
+                             int64_t total_blocks, float threshold,
+                             size_t smem, cudaStream_t s) {
+  static size_t attr_bytes = 0;
+  if (smem > attr_bytes) {
+    cudaError_t e = cudaFuncSetAttribute(
+        sps_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        (int)smem);
+    if (e != cudaSuccess) return e;
+    attr_bytes = smem;
+  }
+  sps_batch_kernel<<<(unsigned)total_blocks, kSpsThreads, smem, s>>>(
+      d_beams, nbeams, threshold);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_sps(const Plan &p, const int32_t *d_series,
                        int64_t nsamp_out, float threshold, bool dense,

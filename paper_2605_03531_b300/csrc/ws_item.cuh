@@ -1,0 +1,364 @@
+// ws_item.cuh -- one work item of the warp-specialised dedispersion
+// (Sec.3.2): out[k][t] = sum_c x[c][t + d[k][c]] for one DM tile x one time
+// tile of one beam, exact in int32.  Used by the per-plan kernel
+// (k_dedisp_ws.cu, one item per block) and by the persistent multi-beam
+// kernel (k_batch.cu, items taken from a device work queue).
+//
+//   * producer warps (kWsProdWarps): one lane per channel issues 1-D TMA
+//     bulk copies of a chunk's raw windows into one of `nbuf` raw stages
+//     (transaction mbarrier), then the producers relayout the chunk into one
+//     of two element buffers -- element i = {x[i], x[i+S], x[i+2S], x[i+3S]}
+//     so a 32-bit shared load at any delay yields four output times -- and
+//     copy its delay offsets beside it;
+//   * consumer warps (WT x WD): SWAR accumulation of two channels per step
+//     (acc_even += (wa & M) + (wb & M), acc_odd += (wa >> 8) + (wb >> 8),
+//     exact for <= 256 channels), releasing each element buffer through its
+//     "empty" mbarrier; every <= 256 channels the byte lanes are unpacked and
+//     added into the output array (uint8) or into registers (uint16).
+// The mbarrier phases run on a chunk counter that continues across the
+// items a block processes (`jbase`).  Every wait is bounded; a role that
+// gives up records a timeout, drains its own copies in flight (bounded) and
+// returns false.
+#pragma once
+
+#include "dev_util.cuh"
+#include "internal.h"
+
+namespace ddsp {
+
+constexpr int kWsProdWarps = 2;
+
+// Shared-memory layout (bytes, 16-aligned offsets):
+//   [0, 64)                      mbarriers: raw_full[4], elem_full[2],
+//                                elem_empty[2]
+//   [64, 80)                     scratch words (work-item broadcast)
+//   raw_rel[nbuf][rel_stride]    delay offsets as copied with a raw stage
+//   raw[nbuf][cc][rawmax]        raw channel windows
+//   erel[2][rel_stride]          offsets beside each element buffer
+//   elem[2][cc][elmax]           interleaved elements (uint32)
+struct WsLayout {
+  int raw_rel_off, rel_stride, raw_off, erel_off, elem_off, elem_stride, total;
+  __host__ __device__ WsLayout(int cc, int dt, int rawmax, int elmax,
+                               int nbuf) {
+    raw_rel_off = 80;
+    rel_stride = ((cc * dt * 4 + 15) / 16) * 16;
+    raw_off = raw_rel_off + nbuf * rel_stride;
+    erel_off = raw_off + nbuf * cc * rawmax;
+    elem_off = erel_off + 2 * rel_stride;
+    elem_stride = cc * elmax * 4;
+    total = elem_off + 2 * elem_stride;
+  }
+};
+
+// One beam as the dedispersion sees it (device copy for the batch).
+struct WsBeam {
+  const void *cm;           // channel-major rows [nchan][pitch]
+  int64_t pitch;
+  int64_t nsamp_out;
+  const int2 *desc;         // [n_dm_tiles][nchan] {window start, bytes}
+  const int32_t *relb;      // [n_dm_tiles][nchan][DT] element-byte offsets
+  const int32_t *rowmap;    // [n_dm_tiles*DT] output row or -1
+  int32_t *out;             // [ndm][nsamp_out]
+  int nchan;
+  int n_dm_tiles;
+  int n_time_tiles;
+  int pad;
+};
+
+__device__ __forceinline__ void ws_init_barriers(unsigned char *smem,
+                                                 int nbuf, int nc, int np) {
+  uint64_t *raw_full = reinterpret_cast<uint64_t *>(smem);
+  uint64_t *elem_full = raw_full + 4;
+  uint64_t *elem_empty = raw_full + 6;
+  for (int b = 0; b < nbuf; ++b) mbar_init(&raw_full[b], 1);
+  for (int b = 0; b < 2; ++b) {
+    mbar_init(&elem_full[b], np);
+    mbar_init(&elem_empty[b], nc);
+  }
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// Process DM tile g x time tile starting at output sample T0 of beam `a`.
+// `jbase` is the number of chunks this block processed before (same value
+// in every thread).  Returns false if this thread's role gave up.
+template <int WT, int WD, int RD, typename T>
+__device__ __forceinline__ bool ws_item(const WsBeam &a, int g, int64_t T0,
+                                        int jbase, unsigned char *smem,
+                                        const WsLayout &L, int cc, int nbuf,
+                                        int rawmax, int elmax, int32_t *err,
+                                        long long timeout_cycles) {
+  constexpr int SPE = 4 / sizeof(T);   // samples per element
+  constexpr int E = kElemPerThread;
+  constexpr int S = 32 * E * WT;       // elements per segment
+  constexpr int DT = RD * WD;          // DM trials per tile
+  constexpr int NC = WT * WD;          // consumer warps
+  constexpr int NP = kWsProdWarps;
+  constexpr bool kRegTot = SPE != 4;   // uint16 totals stay in registers
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  uint64_t *raw_full = reinterpret_cast<uint64_t *>(smem);
+  uint64_t *elem_full = raw_full + 4;
+  uint64_t *elem_empty = raw_full + 6;
+  unsigned char *raw_rel = smem + L.raw_rel_off;
+  unsigned char *raw = smem + L.raw_off;
+  int32_t *erel = reinterpret_cast<int32_t *>(smem + L.erel_off);
+  unsigned char *elem = smem + L.elem_off;
+  const int rel_words = L.rel_stride / 4;
+
+  const T *cm = static_cast<const T *>(a.cm);
+  const int nchan = a.nchan;
+  const int64_t nsamp_out = a.nsamp_out;
+  const int nchunks = (nchan + cc - 1) / cc;
+  const int2 *desc_g = a.desc + (int64_t)g * nchan;
+  const int32_t *rel_g = a.relb + (int64_t)g * nchan * DT;
+
+  if (warp >= NC) {
+    // ============================ producers ============================
+    const int pw = warp - NC;
+    const bool issuer = pw == 0;
+    int2 nd = make_int2(0, 0);  // next copy descriptor of this lane's channel
+    auto load_desc = [&](int j) {
+      const int c = j * cc + lane;
+      if (lane < cc && j < nchunks && c < nchan) nd = __ldg(desc_g + c);
+    };
+    auto issue = [&](int j) {
+      const int c0 = j * cc;
+      const int ncur = min(cc, nchan - c0);
+      const bool v = lane < ncur;
+      const uint32_t nb = v ? (uint32_t)nd.y : 0u;
+      const uint32_t relbytes = (uint32_t)(ncur * DT * 4);
+      const uint32_t total = __reduce_add_sync(0xffffffffu, nb) + relbytes;
+      const int st = (jbase + j) % nbuf;
+      if (lane == 0) {
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_expect_tx(&raw_full[st], total);
+      }
+      __syncwarp();
+      if (v)
+        bulk_g2s(raw + (st * cc + lane) * rawmax,
+                 cm + (int64_t)(c0 + lane) * a.pitch + T0 + nd.x, nb,
+                 &raw_full[st]);
+      if (lane == 0)
+        bulk_g2s(raw_rel + st * L.rel_stride, rel_g + (int64_t)c0 * DT,
+                 relbytes, &raw_full[st]);
+    };
+    int last_issued = -1;
+    if (issuer) {
+      for (int j = 0; j < nbuf && j < nchunks; ++j) {
+        load_desc(j);
+        issue(j);
+        last_issued = j;
+      }
+      load_desc(nbuf);
+    }
+    int j = 0;
+    bool failed = false;
+    for (; j < nchunks; ++j) {
+      const int G = jbase + j;
+      const int st = G % nbuf, b = G & 1;
+      const int ncur = min(cc, nchan - j * cc);
+      bool ok = mbar_wait(&raw_full[st], (uint32_t)((G / nbuf) & 1),
+                          timeout_cycles);
+      ok = ok && mbar_wait(&elem_empty[b], (uint32_t)(((G >> 1) & 1) ^ 1),
+                           timeout_cycles);
+      if (ok) {
+        const int32_t *rs =
+            reinterpret_cast<const int32_t *>(raw_rel + st * L.rel_stride);
+        int32_t *er = erel + b * rel_words;
+        for (int i = pw * 32 + lane; i < ncur * DT; i += NP * 32) er[i] = rs[i];
+        const unsigned char *rb = raw + st * cc * rawmax;
+        uint32_t *eb = reinterpret_cast<uint32_t *>(elem + b * L.elem_stride);
+        for (int q = pw; q < ncur; q += NP) {
+          const unsigned char *rq = rb + q * rawmax;
+          uint32_t *eq = eb + q * elmax;
+          const int span = rs[q * DT + DT - 1] >> 2;
+          if constexpr (SPE == 4) {
+            const int nq = (S + span + 3) >> 2;
+            for (int i4 = lane; i4 < nq; i4 += 32) {
+              const unsigned char *p = rq + 4 * i4;
+              *reinterpret_cast<uint4 *>(eq + 4 * i4) = transpose4x4(
+                  *reinterpret_cast<const uint32_t *>(p),
+                  *reinterpret_cast<const uint32_t *>(p + S),
+                  *reinterpret_cast<const uint32_t *>(p + 2 * S),
+                  *reinterpret_cast<const uint32_t *>(p + 3 * S));
+            }
+          } else {
+            const int nq = (S + span + 1) >> 1;
+            for (int i2 = lane; i2 < nq; i2 += 32) {
+              const unsigned char *p = rq + 4 * i2;
+              const uint32_t w0 = *reinterpret_cast<const uint32_t *>(p);
+              const uint32_t w1 = *reinterpret_cast<const uint32_t *>(p + 2 * S);
+              uint2 o;
+              o.x = __byte_perm(w0, w1, 0x5410);
+              o.y = __byte_perm(w0, w1, 0x7632);
+              *reinterpret_cast<uint2 *>(eq + 2 * i2) = o;
+            }
+          }
+        }
+      }
+      __syncwarp();
+      // all producers are past raw stage st (it can be refilled) and agree
+      // on whether to give up
+      if (named_bar_or(1, NP * 32, !ok)) {
+        failed = true;
+        break;
+      }
+      if (lane == 0) mbar_arrive(&elem_full[b]);
+      if (issuer && j + nbuf < nchunks) {
+        issue(j + nbuf);
+        last_issued = j + nbuf;
+        load_desc(j + nbuf + 1);
+      }
+    }
+    if (failed && issuer && lane == 0) {
+      atomicExch(err, kErrTimeout);
+      for (int jj = j; jj <= last_issued; ++jj) {
+        const int G = jbase + jj;
+        mbar_wait(&raw_full[G % nbuf], (uint32_t)((G / nbuf) & 1),
+                  timeout_cycles);
+      }
+    }
+    return !failed;
+  }
+
+  // ============================= consumers =============================
+  const int wt = warp % WT, wd = warp / WT;
+  const int i0 = 32 * E * wt + lane;  // first element of this thread
+  uint32_t accE[RD][E], accO[RD][E];
+  int32_t tot[kRegTot ? RD : 1][E][SPE];
+#pragma unroll
+  for (int r = 0; r < RD; ++r)
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      accE[r][e] = 0;
+      accO[r][e] = 0;
+      if constexpr (kRegTot) {
+#pragma unroll
+        for (int m = 0; m < SPE; ++m) tot[r][e][m] = 0;
+      }
+    }
+  bool first_flush = true;
+  int since = 0;
+
+  for (int j = 0; j < nchunks; ++j) {
+    const int G = jbase + j;
+    const int b = G & 1;
+    const int ncur = min(cc, nchan - j * cc);
+    if (!mbar_wait(&elem_full[b], (uint32_t)((G >> 1) & 1), timeout_cycles)) {
+      if (lane == 0) atomicExch(err, kErrTimeout);
+      return false;
+    }
+    const int32_t *rel_s = erel + b * rel_words;
+    const unsigned char *ebase = elem + b * L.elem_stride + 4 * i0;
+    auto offsets = [&](int q, int(&rr)[RD]) {
+#pragma unroll
+      for (int h = 0; h < RD; h += 4) {
+        const int4 ro =
+            *reinterpret_cast<const int4 *>(rel_s + q * DT + RD * wd + h);
+        rr[h] = ro.x;
+        rr[h + 1] = ro.y;
+        rr[h + 2] = ro.z;
+        rr[h + 3] = ro.w;
+      }
+    };
+    // two channels per step: 3-input adds
+    int q = 0;
+    for (; q + 1 < ncur; q += 2) {
+      int ra[RD], rb[RD];
+      offsets(q, ra);
+      offsets(q + 1, rb);
+      const unsigned char *ea = ebase + q * elmax * 4;
+      const unsigned char *eb = ea + elmax * 4;
+#pragma unroll
+      for (int r = 0; r < RD; ++r) {
+        const unsigned char *pa = ea + ra[r];
+        const unsigned char *pb = eb + rb[r];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const uint32_t wa = *reinterpret_cast<const uint32_t *>(pa + 128 * e);
+          const uint32_t wb = *reinterpret_cast<const uint32_t *>(pb + 128 * e);
+          if constexpr (SPE == 4) {
+            accE[r][e] += (wa & 0x00FF00FFu) + (wb & 0x00FF00FFu);
+            accO[r][e] += (wa >> 8) + (wb >> 8);
+          } else {
+            tot[r][e][0] += (int32_t)((wa & 0xFFFFu) + (wb & 0xFFFFu));
+            tot[r][e][1] += (int32_t)((wa >> 16) + (wb >> 16));
+          }
+        }
+      }
+    }
+    if (q < ncur) {
+      int ra[RD];
+      offsets(q, ra);
+      const unsigned char *ea = ebase + q * elmax * 4;
+#pragma unroll
+      for (int r = 0; r < RD; ++r) {
+        const unsigned char *pa = ea + ra[r];
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const uint32_t wa = *reinterpret_cast<const uint32_t *>(pa + 128 * e);
+          if constexpr (SPE == 4) {
+            accE[r][e] += wa & 0x00FF00FFu;
+            accO[r][e] += wa >> 8;
+          } else {
+            tot[r][e][0] += (int32_t)(wa & 0xFFFFu);
+            tot[r][e][1] += (int32_t)(wa >> 16);
+          }
+        }
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&elem_empty[b]);
+
+    if constexpr (SPE == 4) {
+      since += ncur;
+      if (since + cc > 256 || j == nchunks - 1) {
+        // unpack the SWAR partials (<= 256 channels) into the output array
+#pragma unroll
+        for (int r = 0; r < RD; ++r) {
+          const int row = __ldg(a.rowmap + g * DT + RD * wd + r);
+          int32_t *o = a.out + (int64_t)(row < 0 ? 0 : row) * nsamp_out;
+#pragma unroll
+          for (int e = 0; e < E; ++e) {
+            const uint32_t Ev = accE[r][e], O = accO[r][e];
+            const uint32_t s2 = Ev >> 16;
+            const uint32_t rem = O - (s2 << 8);
+            const int32_t part[4] = {(int32_t)(Ev & 0xFFFFu),
+                                     (int32_t)(rem & 0xFFFFu), (int32_t)s2,
+                                     (int32_t)(rem >> 16)};
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+              const int64_t t = T0 + i0 + 32 * e + (int64_t)m * S;
+              if (row >= 0 && t < nsamp_out)
+                o[t] = first_flush ? part[m] : o[t] + part[m];
+            }
+            accE[r][e] = 0;
+            accO[r][e] = 0;
+          }
+        }
+        first_flush = false;
+        since = 0;
+      }
+    }
+  }
+
+  if constexpr (kRegTot) {
+#pragma unroll
+    for (int r = 0; r < RD; ++r) {
+      const int row = a.rowmap[g * DT + RD * wd + r];
+      if (row < 0) continue;
+      int32_t *o = a.out + (int64_t)row * nsamp_out;
+#pragma unroll
+      for (int e = 0; e < E; ++e)
+#pragma unroll
+        for (int m = 0; m < SPE; ++m) {
+          const int64_t t = T0 + i0 + 32 * e + (int64_t)m * S;
+          if (t < nsamp_out) o[t] = tot[r][e][m];
+        }
+    }
+  }
+  return true;
+}
+
+}  // namespace ddsp

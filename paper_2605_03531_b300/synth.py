@@ -324,3 +324,36 @@ def gaussian_series(ndm, n, seed, mean=524288.0, sd=1024.0, device="cpu",
         out[r0:r1] = x.view(r1 - r0, n).to(torch.int32)
         del x, ctr
     return out
+
+
+# --------------------------------------------------------- uneven beam mix
+def config3(nbeams=160, seed=3, nsamp_range=(65536, 262144),
+            nchan_choices=(1024, 1024, 2048, 4096), dm_hi_choices=(100.0, 250.0, 500.0),
+            ndm_choices=(256, 512, 1024, 2048)):
+    """Beams of uneven shape over 300-500 MHz at 81.92 us: channel counts in
+    a 2:1:1 mix of 1024/2048/4096, output blocks uniform in `nsamp_range`
+    (multiples of 4096), DM ranges 0-100/0-250/0-500 with 256..2048 trials,
+    0-5 dispersed pulses each (DM within the range, W ~ U{1..64}, S/N ~
+    U(8, 30)); widths 1..256, threshold 7, L 8192.  Returns a list of
+    FilterbankConfig, one per beam, each with its own noise seed."""
+    ctr = np.arange(8 * nbeams, dtype=np.uint64) + np.uint64(1 << 41)
+    u = uniform_np(ctr, seed).reshape(nbeams, 8)
+    lo, hi = nsamp_range[0] // 4096, nsamp_range[1] // 4096
+    beams = []
+    for b in range(nbeams):
+        nchan = nchan_choices[int(u[b, 0] * len(nchan_choices))]
+        nout = 4096 * (lo + int(u[b, 1] * (hi - lo + 1)))
+        dm_hi = dm_hi_choices[int(u[b, 2] * len(dm_hi_choices))]
+        ndm = ndm_choices[int(u[b, 3] * len(ndm_choices))]
+        npulse = int(u[b, 4] * 6)
+        cfg = FilterbankConfig(
+            name=f"c3-beam{b}", nchan=nchan, f_top=500.0, chan_bw=-200.0 / nchan,
+            tsamp=81.92e-6, nsamp_out=nout, dm_lo=0.0, dm_hi=dm_hi, ndm=ndm,
+            widths=[1 << i for i in range(9)], threshold=7.0,
+            seed=seed * 100000 + b)
+        spacing = max(4096, nout // max(npulse, 1) - 4096)
+        cfg.pulses = random_pulses(npulse, nchan, nout, seed=cfg.seed,
+                                   dm_range=(0.05 * dm_hi, 0.95 * dm_hi), wmax=64,
+                                   snr_range=(8.0, 30.0), spacing=spacing)
+        beams.append(cfg)
+    return beams
