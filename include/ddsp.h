@@ -288,21 +288,128 @@ int ddsp_batch_run(ddsp_batch *batch, float threshold, int use_graph,
 int ddsp_batch_check(ddsp_batch *batch, ddsp_stream_t stream);
 
 /* The batch's warp-specialised tile (see ddsp_plan_set_tile) and the
- * persistent grid size.  set_tile returns DDSP_E_INVALID_ARG if the shape
- * does not fit every beam on chip.  Both synchronise. */
+ * persistent grid size.  All beams share dm_tile, dm_per_thread and stages;
+ * chan_chunk (1..32) is an upper limit: each beam stages the largest chunk
+ * up to it whose buffers (which grow with the beam's delay span inside a
+ * DM tile) fit two blocks per SM, or one block per SM if some beam fits
+ * only that way.  set_tile returns DDSP_E_INVALID_ARG if the shape does not
+ * fit every beam on chip.  Both synchronise. */
 int ddsp_batch_set_tile(ddsp_batch *batch, int dm_tile, int dm_per_thread,
                         int chan_chunk, int stages);
 int ddsp_batch_get_tile(const ddsp_batch *batch, int *dm_tile,
                         int *dm_per_thread, int *time_tile, int *chan_chunk,
                         int *stages, int *grid);
 
-/* Autotuner: time the persistent dedispersion of the batch (best of `reps`
- * runs after one warm-up, on the current input buffers) for each tile shape
- * of the library's candidate list, keep the fastest.  ms_out[i] (up to cap
- * entries, may be NULL) receives candidate i's time or -1 if it does not
- * fit; *ntried the number of candidates, *best the chosen index. */
+/* The channel chunk beam `beam` stages under the current tile. */
+int ddsp_batch_get_beam_chunk(const ddsp_batch *batch, int beam,
+                              int *chan_chunk);
+
+/* Autotuner: for each tile shape of the library's candidate list, time the
+ * persistent dedispersion of every 16th work item of the cost-ordered work
+ * list (the same share of each beam's work; best of `reps` runs after one
+ * warm-up, on the current input buffers) and keep the fastest.  ms_out[i]
+ * (up to cap entries, may be NULL) receives candidate i's time scaled to
+ * the full work list, or -1 if the shape does not fit; *ntried the number
+ * of candidates, *best the chosen index.  The sampled runs overwrite parts
+ * of the output series. */
 int ddsp_batch_autotune(ddsp_batch *batch, int reps, ddsp_stream_t stream,
                         float *ms_out, int cap, int *ntried, int *best);
+
+/* ---- Streaming server (the real-time ring-buffer design of Sec.2.1 and
+ * Ch.3: every beam delivers blocks of B new spectra, each block is
+ * dedispersed and searched once the GPU is free, together with the blocks
+ * other beams have waiting).
+ *
+ * All beams have the shape of `plan` (channels, band, DM trials, widths,
+ * normalisation window, candidate capacity per block; uint8 samples,
+ * nchan a multiple of 16).  Per admitted beam the server owns a
+ * channel-major ring of ceil(D16/B) + 2 blocks (D16 = the largest delay
+ * rounded up to 16 samples) whose rows end in a copy of their first bytes,
+ * a series [ndm][C + B] (C = widest boxcar - 1 rounded up to 4, carried from
+ * the previous block), per-window statistics and two candidate buffers.
+ * Block j (0, 1, ...) is dedispersed for output samples s_j .. s_j + B - 1
+ * with s_j = j*B - D16 (input before the stream's first sample reads as 0),
+ * written to series columns C .. C + B - 1, and searched for start times
+ * 0 .. B - 1 of the series, normalised per window of the C + B columns as
+ * ddsp_single_pulse_search does: candidate t is global output sample
+ * s_j - C + t.  The results equal those of ddsp_dedisperse and
+ * ddsp_single_pulse_search on the same input window. */
+typedef struct ddsp_server ddsp_server;
+
+/* Create a server for up to max_beams beams of plan's shape receiving
+ * blocks of block_samples (a multiple of 16 and of the tile's time tile,
+ * >= C) spectra.  hbm_reserve_bytes: device memory admission leaves free.
+ * dm_tile = 0 lets the server choose the warp-specialised tile (see
+ * ddsp_plan_set_tile; chan_chunk is an upper limit), else the given shape.
+ * The plan must outlive the server; its own buffers are not used.
+ * DDSP_E_SHAPE if the block is too short for the tile or the search window
+ * (see ddsp_single_pulse_search), DDSP_E_INVALID_ARG for a shape the kernel
+ * does not implement. */
+int ddsp_server_create(ddsp_server **out, ddsp_plan *plan,
+                       int64_t block_samples, int max_beams,
+                       int64_t hbm_reserve_bytes, int dm_tile,
+                       int dm_per_thread, int chan_chunk, int stages);
+void ddsp_server_destroy(ddsp_server *server);
+
+/* Device bytes one admitted beam holds, ring length (samples), series
+ * columns (C + B), carry C and the output lag D16 (any pointer may be
+ * NULL). */
+int ddsp_server_info(const ddsp_server *server, int64_t *beam_bytes,
+                     int64_t *ring_samples, int64_t *series_cols,
+                     int64_t *carry, int64_t *first_delay);
+int ddsp_server_get_tile(const ddsp_server *server, int *dm_tile,
+                         int *dm_per_thread, int *time_tile, int *chan_chunk,
+                         int *stages, int *grid);
+
+/* Admission: allocate and zero a new beam's ring and buffers if the device's
+ * free memory, less the reserve, holds them; *beam = its index.
+ * DDSP_E_NOMEM if it does not fit, DDSP_E_RANGE if max_beams are admitted.
+ * Synchronises.  Evict frees a beam (synchronises the device first). */
+int ddsp_server_admit(ddsp_server *server, int *beam);
+int ddsp_server_evict(ddsp_server *server, int beam);
+
+/* Ingest the beam's next block: d_block is time-major uint8 [B][nchan] in
+ * device memory (16-byte aligned), read by kernels on `stream` (the caller
+ * keeps it unchanged until they ran).  The block's ring slot last served the
+ * step of block j - 2, which `stream` waits for.  DDSP_E_STATE if block j - 2
+ * has not been given to a step yet: run a step first (the caller holds the
+ * block meanwhile). */
+int ddsp_server_push(ddsp_server *server, int beam, const void *d_block,
+                     ddsp_stream_t stream);
+
+/* One step on `stream` (asynchronous): every admitted beam with a pushed,
+ * unsearched block contributes its oldest such block (max_beams_in_step > 0:
+ * only that many beams, those whose block was pushed first); the blocks are
+ * dedispersed by one persistent launch and searched by one batched launch.
+ * *nbeams = the number of beams in the step (0: nothing was launched),
+ * their indices in beams_out (up to cap entries, may be NULL), *step_id its
+ * number for ddsp_server_query.  Waits on the host for the step before the
+ * previous one, whose descriptor staging it reuses. */
+int ddsp_server_step(ddsp_server *server, float threshold,
+                     int max_beams_in_step, ddsp_stream_t stream,
+                     int64_t *step_id, int *beams_out, int cap, int *nbeams);
+
+/* 1 if step step_id has completed, 0 if it is still running; negative on
+ * error. */
+int ddsp_server_query(ddsp_server *server, int64_t step_id);
+
+/* Candidates of block `block` of a beam (one of its two most recently
+ * stepped blocks; DDSP_E_STATE otherwise), after waiting for its step:
+ * records sorted by (dm_idx, t), t relative to series column 0, *t_start =
+ * that column's global output sample (s_j - C).  As ddsp_candidates_fetch for cap,
+ * *n_found and DDSP_E_TRUNCATED. */
+int ddsp_server_fetch(ddsp_server *server, int beam, int64_t block,
+                      ddsp_cand *host_buf, size_t cap, size_t *n_found,
+                      int64_t *t_start);
+
+/* Device pointer of a beam's series [ndm][ncols] (the last stepped block's
+ * once its step completed). */
+int ddsp_server_series(ddsp_server *server, int beam, int32_t **d_series,
+                       int64_t *ncols);
+
+/* Synchronise `stream` and report a device-side timeout or range error of
+ * the server's steps, then clear it. */
+int ddsp_server_check(ddsp_server *server, ddsp_stream_t stream);
 
 /* Name and text of the last CUDA error this library saw on the calling
  * host thread (empty if none); the storage is the library's. */

@@ -15,7 +15,7 @@ import numpy as np
 from . import _lib
 from ._lib import DdspError, DdspCand
 
-__all__ = ["Plan", "Batch", "DdspError", "CAND_DTYPE", "delay_table"]
+__all__ = ["Plan", "Batch", "Server", "DdspError", "CAND_DTYPE", "delay_table"]
 
 CAND_DTYPE = np.dtype([("dm_idx", np.uint32), ("t", np.uint32),
                        ("w_idx", np.uint32), ("snr", np.float32)])
@@ -26,6 +26,22 @@ def _stream_handle(stream):
     if stream is None:
         stream = torch.cuda.current_stream()
     return C.c_void_p(stream.cuda_stream)
+
+
+class _DeviceArray:
+    """A library-owned device buffer exposed through the CUDA array
+    interface, so torch can view it without a copy."""
+
+    def __init__(self, ptr, shape, typestr):
+        self.__cuda_array_interface__ = {
+            "data": (int(ptr), False), "shape": tuple(int(d) for d in shape),
+            "typestr": typestr, "strides": None, "version": 3}
+
+
+def _tensor_view(ptr, shape, dtype):
+    import torch
+    typestr = {torch.int32: "<i4", torch.uint8: "|u1"}[dtype]
+    return torch.as_tensor(_DeviceArray(ptr, shape, typestr), device="cuda")
 
 
 def _dev_ptr(t, dtype=None, what="tensor"):
@@ -310,9 +326,19 @@ class Batch:
                 "grid")
         return dict(zip(keys, (a.value for a in v)))
 
+    def beam_chunk(self, beam):
+        """Channels per staging chunk beam `beam` uses under the current
+        tile (the tile's chan_chunk is the upper limit)."""
+        v = C.c_int()
+        _lib.check(_lib.lib().ddsp_batch_get_beam_chunk(self._h, int(beam),
+                                                         C.byref(v)),
+                   "ddsp_batch_get_beam_chunk")
+        return v.value
+
     def autotune(self, reps=2, stream=None):
-        """Time every candidate tile, keep the fastest; returns
-        (list of ms per candidate (-1 = does not fit), chosen index)."""
+        """Time every candidate tile on a 1/16 sample of the work items,
+        keep the fastest; returns (list of estimated full-launch ms per
+        candidate (-1 = does not fit), chosen index)."""
         cap = 64
         ms = (C.c_float * cap)()
         nt, best = C.c_int(), C.c_int()
@@ -324,6 +350,118 @@ class Batch:
     def close(self):
         if self._h:
             _lib.lib().ddsp_batch_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Streaming search of many beams of one plan's shape (``ddsp_server_*``):
+    per-beam rings in device memory, admission against free device memory,
+    and steps that dedisperse and search the waiting block of every ready
+    beam in one persistent launch plus one batched search launch."""
+
+    def __init__(self, plan, block_samples, max_beams, hbm_reserve_bytes=0,
+                 tile=None):
+        self.plan = plan
+        self.block = int(block_samples)
+        self.max_beams = int(max_beams)
+        dm_tile, dm_per_thread, chan_chunk, stages = tile or (0, 0, 0, 0)
+        self._h = C.c_void_p()
+        _lib.check(_lib.lib().ddsp_server_create(
+            C.byref(self._h), plan._h, self.block, self.max_beams,
+            int(hbm_reserve_bytes), int(dm_tile), int(dm_per_thread),
+            int(chan_chunk), int(stages)), "ddsp_server_create")
+        v = [C.c_int64() for _ in range(5)]
+        _lib.check(_lib.lib().ddsp_server_info(self._h, *[C.byref(a) for a in v]),
+                   "ddsp_server_info")
+        (self.beam_bytes, self.ring_samples, self.series_cols, self.carry,
+         self.first_delay) = (a.value for a in v)
+
+    def get_tile(self):
+        v = [C.c_int() for _ in range(6)]
+        _lib.check(_lib.lib().ddsp_server_get_tile(self._h, *[C.byref(a) for a in v]),
+                   "ddsp_server_get_tile")
+        keys = ("dm_tile", "dm_per_thread", "time_tile", "chan_chunk", "stages",
+                "grid")
+        return dict(zip(keys, (a.value for a in v)))
+
+    def admit(self):
+        """Index of a newly admitted beam; DdspError(DDSP_E_NOMEM) if its
+        buffers do not fit the free device memory less the reserve."""
+        b = C.c_int()
+        _lib.check(_lib.lib().ddsp_server_admit(self._h, C.byref(b)),
+                   "ddsp_server_admit")
+        return b.value
+
+    def evict(self, beam):
+        _lib.check(_lib.lib().ddsp_server_evict(self._h, int(beam)),
+                   "ddsp_server_evict")
+
+    def push(self, beam, x, stream=None):
+        """Ingest beam `beam`'s next block (CUDA uint8 [block][nchan]);
+        returns False (nothing done) if the beam already has two blocks
+        waiting for steps."""
+        import torch
+        rc = _lib.lib().ddsp_server_push(self._h, int(beam),
+                                         _dev_ptr(x, torch.uint8, "block"),
+                                         _stream_handle(stream))
+        if rc == _lib.DDSP_E_STATE:
+            return False
+        _lib.check(rc, "ddsp_server_push")
+        return True
+
+    def step(self, threshold, max_beams_in_step=0, stream=None):
+        """Launch one step; returns (step id, beams in it) or (-1, [])."""
+        sid, n = C.c_int64(), C.c_int()
+        beams = (C.c_int * self.max_beams)()
+        _lib.check(_lib.lib().ddsp_server_step(
+            self._h, float(threshold), int(max_beams_in_step),
+            _stream_handle(stream), C.byref(sid), beams, self.max_beams,
+            C.byref(n)), "ddsp_server_step")
+        return sid.value, list(beams[:n.value])
+
+    def done(self, step_id):
+        rc = _lib.lib().ddsp_server_query(self._h, int(step_id))
+        if rc < 0:
+            _lib.check(rc, "ddsp_server_query")
+        return rc == 1
+
+    def fetch(self, beam, block, cap=None):
+        """(candidates sorted by (dm_idx, t), true count, global output
+        sample of series column 0) of one of the beam's two most recently
+        stepped blocks."""
+        if cap is None:
+            cap = self.plan.cand_capacity
+        buf = np.zeros(cap, dtype=CAND_DTYPE)
+        n, t0 = C.c_size_t(), C.c_int64()
+        rc = _lib.lib().ddsp_server_fetch(
+            self._h, int(beam), int(block), buf.ctypes.data_as(C.c_void_p),
+            int(cap), C.byref(n), C.byref(t0))
+        _lib.check(rc, "ddsp_server_fetch")
+        return buf[:n.value].copy(), n.value, t0.value
+
+    def series(self, beam):
+        """The beam's series [ndm][carry + block] as a CUDA int32 tensor view
+        (the last stepped block's, once its step completed)."""
+        import torch
+        ptr, ncols = C.c_void_p(), C.c_int64()
+        _lib.check(_lib.lib().ddsp_server_series(self._h, int(beam), C.byref(ptr),
+                                                 C.byref(ncols)),
+                   "ddsp_server_series")
+        return _tensor_view(ptr.value, (self.plan.ndm, ncols.value), torch.int32)
+
+    def check(self, stream=None):
+        _lib.check(_lib.lib().ddsp_server_check(self._h, _stream_handle(stream)),
+                   "ddsp_server_check")
+
+    def close(self):
+        if self._h:
+            _lib.lib().ddsp_server_destroy(self._h)
             self._h = C.c_void_p()
 
     def __del__(self):

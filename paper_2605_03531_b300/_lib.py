@@ -63,8 +63,24 @@ SIGNATURES = {
     "ddsp_batch_check": (I32, [P, P]),
     "ddsp_batch_set_tile": (I32, [P, I32, I32, I32, I32]),
     "ddsp_batch_get_tile": (I32, [P] + [C.POINTER(C.c_int)] * 6),
+    "ddsp_batch_get_beam_chunk": (I32, [P, I32, C.POINTER(C.c_int)]),
     "ddsp_batch_autotune": (I32, [P, I32, P, C.POINTER(C.c_float), I32,
                                   C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "ddsp_server_create": (I32, [C.POINTER(P), P, I64, I32, I64, I32, I32,
+                                 I32, I32]),
+    "ddsp_server_destroy": (None, [P]),
+    "ddsp_server_info": (I32, [P] + [PI64] * 5),
+    "ddsp_server_get_tile": (I32, [P] + [C.POINTER(C.c_int)] * 6),
+    "ddsp_server_admit": (I32, [P, C.POINTER(C.c_int)]),
+    "ddsp_server_evict": (I32, [P, I32]),
+    "ddsp_server_push": (I32, [P, I32, P, P]),
+    "ddsp_server_step": (I32, [P, C.c_float, I32, P, PI64, C.POINTER(C.c_int),
+                               I32, C.POINTER(C.c_int)]),
+    "ddsp_server_query": (I32, [P, I64]),
+    "ddsp_server_fetch": (I32, [P, I32, I64, P, C.c_size_t,
+                                C.POINTER(C.c_size_t), PI64]),
+    "ddsp_server_series": (I32, [P, I32, C.POINTER(P), PI64]),
+    "ddsp_server_check": (I32, [P, P]),
     "ddsp_plan_destroy": (None, [P]),
     "ddsp_error_string": (C.c_char_p, [I32]),
     "ddsp_last_error_detail": (C.c_char_p, []),

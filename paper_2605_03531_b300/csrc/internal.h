@@ -98,6 +98,7 @@ struct SpsBeam {             // one beam of the batched search
   uint32_t *count;
   int32_t *err;
   int64_t n, L, nwin, block0;
+  int64_t nrep;              // candidates only for start times t < nrep
   int ndm, nw;
   uint32_t cap, pad;
 };
@@ -108,6 +109,11 @@ struct WsBeam;  // ws_item.cuh
 cudaError_t launch_unpack(const void *d_in, int64_t nsamp_in, int nchan,
                           int nbits, void *d_out, int64_t pitch,
                           cudaStream_t s);
+// Columns [0, ncols) of each row only (ncols <= pitch; a multiple of 4 for
+// the uint8 tile kernel).
+cudaError_t launch_unpack_cols(const void *d_in, int64_t nsamp_in, int nchan,
+                               int nbits, void *d_out, int64_t pitch,
+                               int64_t ncols, cudaStream_t s);
 
 cudaError_t launch_dedisperse(const Plan &p, const void *d_cm, int64_t pitch,
                               int64_t nsamp_out, int32_t *d_out,
@@ -139,11 +145,15 @@ int64_t sps_max_window_samples();
 int persistent_blocks_per_sm(const DedispTile &t, size_t smem);
 cudaError_t launch_batch_reset(int *d_queue, uint32_t *const *d_counts,
                                int ncounts, cudaStream_t s);
+cudaError_t launch_serve_prep(const SpsBeam *d_beams, int nbeams, int ndm,
+                              int64_t n, int carry, int *d_queue,
+                              cudaStream_t s);
 cudaError_t launch_dedisperse_persistent(const DedispTile &t,
                                          const WsBeam *d_beams,
                                          const int4 *d_items, int nitems,
-                                         int *d_queue, int rawmax, int elmax,
-                                         size_t smem, int32_t *d_err, int grid,
+                                         int ipb, int ntt, int *d_queue,
+                                         size_t smem,
+                                         int32_t *d_err, int grid,
                                          cudaStream_t s);
 int64_t unpack_batch_blocks(int64_t pitch, int nchan);
 cudaError_t launch_unpack_batch(const UnpackBeam *d_beams, int nbeams,

@@ -1,15 +1,21 @@
 // k_batch.cu -- many beams of uneven shape dedispersed in one persistent
-// launch (the batched form of Sec.3.2), plus the small reset kernel that
-// starts a batch step.
+// launch (the batched form of Sec.3.2), plus the small kernels that start a
+// batch step (queue and count reset) and a streaming step (the same, plus
+// the boxcar carry of every beam's series).
 //
 // A grid of (SMs x resident blocks) blocks loops: one thread takes the next
 // work item from a device queue (atomicAdd on a counter), the block runs it
 // with ws_item.cuh (producer warps stage and relayout, consumer warps
 // accumulate), and the mbarrier phases continue across items through a
 // running chunk counter.  Items are (beam, DM tile, time tile) triples,
-// ordered by the host so that the most expensive ones start first; all
-// beams share one tile shape and one shared-memory layout (the maxima over
-// the beams).
+// ordered by the host so that the most expensive ones start first.  All
+// beams share one tile shape (warps, DM trials per thread) and one stage
+// count; each beam has its own channel chunk and buffer extents, and the
+// dynamic shared memory is the largest layout over the beams.  When every
+// beam has the same shape the host passes no item list: item i is beam
+// i / ipb, DM tile (i % ipb) / ntt, time tile (i % ipb) % ntt.
+#include <algorithm>
+
 #include "ws_item.cuh"
 
 namespace ddsp {
@@ -19,12 +25,10 @@ template <int WT, int WD, int RD>
 __global__ void __launch_bounds__(32 * (WT * WD + kWsProdWarps), 2)
 dedisp_persistent_kernel(const WsBeam *__restrict__ beams,
                          const int4 *__restrict__ items, int nitems,
-                         int *queue, int cc, int nbuf, int rawmax, int elmax,
-                         int32_t *err, long long timeout_cycles) {
+                         int ipb, int ntt, int *queue, int nbuf, int32_t *err,
+                         long long timeout_cycles) {
   constexpr int TT = 4 * 32 * kElemPerThread * WT;
-  constexpr int DT = RD * WD;
   extern __shared__ __align__(16) unsigned char smem[];
-  const WsLayout L(cc, DT, rawmax, elmax, nbuf);
   int *s_item = reinterpret_cast<int *>(smem + 64);
   if (threadIdx.x == 0) ws_init_barriers(smem, nbuf, WT * WD, kWsProdWarps);
   int jbase = 0;
@@ -33,12 +37,17 @@ dedisp_persistent_kernel(const WsBeam *__restrict__ beams,
     __syncthreads();
     const int it = *s_item;
     if (it >= nitems) break;
-    const int4 w = items[it];           // {beam, DM tile, time tile, -}
+    int4 w;                             // {beam, DM tile, time tile, -}
+    if (items) {
+      w = items[it];
+    } else {
+      const int r = it % ipb;
+      w = make_int4(it / ipb, r / ntt, r % ntt, 0);
+    }
     const WsBeam a = beams[w.x];
     const bool ok = ws_item<WT, WD, RD, uint8_t>(
-        a, w.y, (int64_t)w.z * TT, jbase, smem, L, cc, nbuf, rawmax, elmax,
-        err, timeout_cycles);
-    jbase += (a.nchan + cc - 1) / cc;
+        a, w.y, (int64_t)w.z * TT, jbase, smem, nbuf, err, timeout_cycles);
+    jbase += (a.nchan + a.cc - 1) / a.cc;
     // every role is done with the item before the next one starts; a block
     // whose item failed stops taking work
     if (__syncthreads_or(!ok)) break;
@@ -52,11 +61,36 @@ __global__ void batch_reset_kernel(int *queue, uint32_t *const *counts,
   if (i < ncounts) *counts[i] = 0;
 }
 
+// Streaming step prologue: reset the queue and each beam's candidate count,
+// and move the last `carry` samples of every series row to its front (the
+// boxcars of the next block start there).  Rows are n samples, n and carry
+// multiples of 4, n >= 2 * carry; one int4 per thread.
+__global__ void serve_prep_kernel(const SpsBeam *__restrict__ beams,
+                                  int nbeams, int ndm, int64_t n, int carry,
+                                  int *queue) {
+  const int64_t q = carry / 4;
+  const int64_t total = (int64_t)nbeams * ndm * q;
+  const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i0 == 0) *queue = 0;
+  if (i0 < nbeams) *beams[i0].count = 0;
+  for (int64_t i = i0; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int b = (int)(i / ((int64_t)ndm * q));
+    const int64_t rem = i - (int64_t)b * ndm * q;
+    const int64_t row = rem / q, c4 = rem - row * q;
+    // the search only reads the series; this prologue is its one writer
+    // besides the dedispersion
+    int32_t *x = const_cast<int32_t *>(beams[b].series) + row * n;
+    reinterpret_cast<int4 *>(x)[c4] =
+        reinterpret_cast<const int4 *>(x + n - carry)[c4];
+  }
+}
+
 template <int WT, int WD, int RD>
 cudaError_t launch_persistent_t(const WsBeam *d_beams, const int4 *d_items,
-                                int nitems, int *d_queue, int cc, int nbuf,
-                                int rawmax, int elmax, size_t smem,
-                                int32_t *d_err, int grid, cudaStream_t s) {
+                                int nitems, int ipb, int ntt, int *d_queue,
+                                int nbuf,
+                                size_t smem, int32_t *d_err, int grid,
+                                cudaStream_t s) {
   auto kern = dedisp_persistent_kernel<WT, WD, RD>;
   static size_t attr_bytes = 0;
   if (smem > attr_bytes) {
@@ -67,8 +101,7 @@ cudaError_t launch_persistent_t(const WsBeam *d_beams, const int4 *d_items,
   }
   const long long timeout = 4000000000LL;  // ~2 s of SM clock
   kern<<<grid, 32 * (WT * WD + kWsProdWarps), smem, s>>>(
-      d_beams, d_items, nitems, d_queue, cc, nbuf, rawmax, elmax, d_err,
-      timeout);
+      d_beams, d_items, nitems, ipb, ntt, d_queue, nbuf, d_err, timeout);
   return cudaGetLastError();
 }
 
@@ -93,6 +126,17 @@ int persistent_blocks_per_sm(const DedispTile &t, size_t smem) {
   return e == cudaSuccess ? n : 0;
 }
 
+cudaError_t launch_serve_prep(const SpsBeam *d_beams, int nbeams, int ndm,
+                              int64_t n, int carry, int *d_queue,
+                              cudaStream_t s) {
+  const int64_t total = std::max<int64_t>((int64_t)nbeams * ndm * (carry / 4),
+                                          nbeams);
+  const int64_t blocks = std::min<int64_t>((total + 255) / 256, 148 * 16);
+  serve_prep_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, s>>>(
+      d_beams, nbeams, ndm, n, carry, d_queue);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_batch_reset(int *d_queue, uint32_t *const *d_counts,
                                int ncounts, cudaStream_t s) {
   const int n = ncounts > 1 ? ncounts : 1;
@@ -104,15 +148,15 @@ cudaError_t launch_batch_reset(int *d_queue, uint32_t *const *d_counts,
 cudaError_t launch_dedisperse_persistent(const DedispTile &t,
                                          const WsBeam *d_beams,
                                          const int4 *d_items, int nitems,
-                                         int *d_queue, int rawmax, int elmax,
-                                         size_t smem, int32_t *d_err, int grid,
+                                         int ipb, int ntt, int *d_queue,
+                                         size_t smem,
+                                         int32_t *d_err, int grid,
                                          cudaStream_t s) {
 #define DDSP_P(WT_, WD_, RD_)                                                 \
   if (t.wt == WT_ && t.wd == WD_ && t.rd == RD_)                              \
-    return launch_persistent_t<WT_, WD_, RD_>(d_beams, d_items, nitems,       \
-                                              d_queue, t.chan_chunk, t.nbuf,  \
-                                              rawmax, elmax, smem, d_err,     \
-                                              grid, s);
+    return launch_persistent_t<WT_, WD_, RD_>(d_beams, d_items, nitems, ipb,  \
+                                              ntt, d_queue, t.nbuf, smem,     \
+                                              d_err, grid, s);
   DDSP_P(4, 2, 4) DDSP_P(2, 4, 4) DDSP_P(8, 1, 4)
   DDSP_P(4, 2, 8) DDSP_P(2, 4, 8) DDSP_P(8, 1, 8)
 #undef DDSP_P

@@ -10,17 +10,14 @@ namespace {
 
 template <int WT, int WD, int RD, typename T>
 __global__ void __launch_bounds__(32 * (WT * WD + kWsProdWarps), 2)
-dedisp_ws_kernel(WsBeam a, int cc, int nbuf, int rawmax, int elmax,
-                 int32_t *err, long long timeout_cycles) {
+dedisp_ws_kernel(WsBeam a, int nbuf, int32_t *err, long long timeout_cycles) {
   constexpr int SPE = 4 / sizeof(T);
   constexpr int TT = SPE * 32 * kElemPerThread * WT;
-  constexpr int DT = RD * WD;
   extern __shared__ __align__(16) unsigned char smem[];
-  const WsLayout L(cc, DT, rawmax, elmax, nbuf);
   if (threadIdx.x == 0) ws_init_barriers(smem, nbuf, WT * WD, kWsProdWarps);
   __syncthreads();
-  ws_item<WT, WD, RD, T>(a, blockIdx.x, (int64_t)blockIdx.y * TT, 0, smem, L,
-                         cc, nbuf, rawmax, elmax, err, timeout_cycles);
+  ws_item<WT, WD, RD, T>(a, blockIdx.x, (int64_t)blockIdx.y * TT, 0, smem,
+                         nbuf, err, timeout_cycles);
 }
 
 template <int WT, int WD, int RD, typename T>
@@ -42,6 +39,9 @@ cudaError_t launch_ws_t(const Plan &p, const void *d_cm, int64_t pitch,
   a.cm = d_cm;
   a.pitch = pitch;
   a.nsamp_out = nsamp_out;
+  a.ring = 0;
+  a.t0 = 0;
+  a.out_pitch = nsamp_out;
   a.desc = reinterpret_cast<const int2 *>(p.tab.d_desc);
   a.relb = p.tab.d_relb;
   a.rowmap = p.tab.d_rowmap;
@@ -49,10 +49,13 @@ cudaError_t launch_ws_t(const Plan &p, const void *d_cm, int64_t pitch,
   a.nchan = p.nchan;
   a.n_dm_tiles = p.tab.n_dm_tiles;
   a.n_time_tiles = ntt;
+  a.cc = p.tile.chan_chunk;
+  a.rawmax = rawmax;
+  a.elmax = elmax;
   dim3 grid((unsigned)p.tab.n_dm_tiles, (unsigned)ntt);
   const long long timeout = 4000000000LL;  // ~2 s of SM clock
   kern<<<grid, 32 * (WT * WD + kWsProdWarps), smem, s>>>(
-      a, p.tile.chan_chunk, p.tile.nbuf, rawmax, elmax, p.d_err, timeout);
+      a, p.tile.nbuf, p.d_err, timeout);
   return cudaGetLastError();
 }
 

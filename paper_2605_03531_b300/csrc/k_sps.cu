@@ -195,7 +195,7 @@ __device__ __forceinline__ void sps_window(
     ddsp_cand *__restrict__ cands, uint32_t *__restrict__ count, uint32_t cap,
     int32_t *__restrict__ best_w, float *__restrict__ best_snr,
     int32_t *__restrict__ best_sum, int32_t *__restrict__ err,
-    const int64_t j, const int k) {
+    const int64_t j, const int k, const int64_t nrep) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SpsShared &sh = *reinterpret_cast<SpsShared *>(smem_raw);
   int32_t *buf = reinterpret_cast<int32_t *>(smem_raw + sizeof(SpsShared));
@@ -335,7 +335,7 @@ __device__ __forceinline__ void sps_window(
           best_sum[o] = bsum;
         }
       } else {
-        const bool cand = in && bw >= 0 && bs >= thr;
+        const bool cand = in && bw >= 0 && bs >= thr && lo + i < nrep;
         const uint32_t ball = __ballot_sync(__activemask(), cand);
         if (cand) {
           const int leader = __ffs(ball) - 1;
@@ -368,7 +368,7 @@ sps_kernel(const int32_t *__restrict__ series, int64_t n, int64_t L,
            int32_t *__restrict__ err) {
   sps_window<DENSE>(series, n, L, nwin, widths, nw, thr, m2_out, mad4_out,
                     cands, count, cap, best_w, best_snr, best_sum, err,
-                    blockIdx.x, blockIdx.y);
+                    blockIdx.x, blockIdx.y, n);
 }
 
 // Many beams in one launch: flattened block b -> the beam whose block0 is
@@ -387,7 +387,7 @@ sps_batch_kernel(const SpsBeam *__restrict__ beams, int nbeams, float thr) {
   const int64_t j = local - (int64_t)k * b.nwin;
   sps_window<false>(b.series, b.n, b.L, b.nwin, b.widths, b.nw, thr, b.m2,
                     b.mad4, b.cands, b.count, b.cap, nullptr, nullptr,
-                    nullptr, b.err, j, k);
+                    nullptr, b.err, j, k, b.nrep);
 }
 
 }  // namespace

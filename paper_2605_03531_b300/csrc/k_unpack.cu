@@ -2,6 +2,8 @@
 // one row of nchan samples per time sample, Sec.2.2) to channel-major rows
 // so the dedispersion kernel can stage a channel's time series with one
 // contiguous bulk copy.  HBM-bound: every byte is read once and written once.
+// Each row gets columns [0, ncols) (ncols <= pitch): input samples, then
+// zeros past nsamp_in; columns from ncols to the pitch are left untouched.
 #include "internal.h"
 
 namespace ddsp {
@@ -16,7 +18,8 @@ constexpr int kPitchW = kTC / 4 + 1; // smem row pitch in words (bank skew)
 
 __device__ __forceinline__ void unpack_u8_tile(
     const uint8_t *__restrict__ in, int64_t nsamp_in, int nchan,
-    uint8_t *__restrict__ out, int64_t pitch, int64_t tile_s, int tile_c) {
+    uint8_t *__restrict__ out, int64_t pitch, int64_t ncols, int64_t tile_s,
+    int tile_c) {
   __shared__ uint32_t tile[kTS * kPitchW];
   const int tid = threadIdx.x;
   const int64_t s0 = tile_s * kTS;
@@ -52,7 +55,7 @@ __device__ __forceinline__ void unpack_u8_tile(
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       int c = c0 + 4 * cq + j;
-      if (c < nchan && s < pitch)
+      if (c < nchan && s < ncols)
         *reinterpret_cast<uint32_t *>(out + (int64_t)c * pitch + s) = o[j];
     }
   }
@@ -60,8 +63,9 @@ __device__ __forceinline__ void unpack_u8_tile(
 
 __global__ void __launch_bounds__(256)
 unpack_u8_kernel(const uint8_t *__restrict__ in, int64_t nsamp_in, int nchan,
-                 uint8_t *__restrict__ out, int64_t pitch) {
-  unpack_u8_tile(in, nsamp_in, nchan, out, pitch, blockIdx.x, blockIdx.y);
+                 uint8_t *__restrict__ out, int64_t pitch, int64_t ncols) {
+  unpack_u8_tile(in, nsamp_in, nchan, out, pitch, ncols, blockIdx.x,
+                 blockIdx.y);
 }
 
 // Many beams in one launch: block b of the flattened grid belongs to the beam
@@ -77,8 +81,8 @@ unpack_u8_batch_kernel(const UnpackBeam *__restrict__ beams, int nbeams) {
   const UnpackBeam &b = beams[lo];
   const int64_t local = bid - b.block0;
   const int64_t tiles_s = b.pitch / kTS;
-  unpack_u8_tile(b.in, b.nsamp_in, b.nchan, b.out, b.pitch, local % tiles_s,
-                 (int)(local / tiles_s));
+  unpack_u8_tile(b.in, b.nsamp_in, b.nchan, b.out, b.pitch, b.pitch,
+                 local % tiles_s, (int)(local / tiles_s));
 }
 
 // Generic element-wise transpose (uint8 with nchan % 16 != 0, and uint16):
@@ -86,7 +90,7 @@ unpack_u8_batch_kernel(const UnpackBeam *__restrict__ beams, int nbeams) {
 template <typename T>
 __global__ void __launch_bounds__(256)
 unpack_generic_kernel(const T *__restrict__ in, int64_t nsamp_in, int nchan,
-                      T *__restrict__ out, int64_t pitch) {
+                      T *__restrict__ out, int64_t pitch, int64_t ncols) {
   __shared__ T tile[32][33];
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
   const int64_t s0 = (int64_t)blockIdx.x * 32;
@@ -104,7 +108,7 @@ unpack_generic_kernel(const T *__restrict__ in, int64_t nsamp_in, int nchan,
   for (int r = ty; r < 32; r += 8) {
     int c = c0 + r;
     int64_t s = s0 + tx;
-    if (c < nchan && s < pitch) out[(int64_t)c * pitch + s] = tile[tx][r];
+    if (c < nchan && s < ncols) out[(int64_t)c * pitch + s] = tile[tx][r];
   }
 }
 
@@ -121,26 +125,38 @@ cudaError_t launch_unpack_batch(const UnpackBeam *d_beams, int nbeams,
   return cudaGetLastError();
 }
 
+cudaError_t launch_unpack_cols(const void *d_in, int64_t nsamp_in, int nchan,
+                               int nbits, void *d_out, int64_t pitch,
+                               int64_t ncols, cudaStream_t s) {
+  if (ncols > pitch || ncols < 0) return cudaErrorInvalidValue;
+  if (ncols == 0) return cudaSuccess;
+  if (nbits == 8 && nchan % 16 == 0) {
+    if (ncols % 4) return cudaErrorInvalidValue;  // 4-sample word stores
+    dim3 grid((unsigned)((ncols + kTS - 1) / kTS),
+              (unsigned)((nchan + kTC - 1) / kTC));
+    unpack_u8_kernel<<<grid, 256, 0, s>>>(static_cast<const uint8_t *>(d_in),
+                                          nsamp_in, nchan,
+                                          static_cast<uint8_t *>(d_out), pitch,
+                                          ncols);
+  } else if (nbits == 8) {
+    dim3 grid((unsigned)((ncols + 31) / 32), (unsigned)((nchan + 31) / 32));
+    unpack_generic_kernel<uint8_t><<<grid, 256, 0, s>>>(
+        static_cast<const uint8_t *>(d_in), nsamp_in, nchan,
+        static_cast<uint8_t *>(d_out), pitch, ncols);
+  } else {
+    dim3 grid((unsigned)((ncols + 31) / 32), (unsigned)((nchan + 31) / 32));
+    unpack_generic_kernel<uint16_t><<<grid, 256, 0, s>>>(
+        static_cast<const uint16_t *>(d_in), nsamp_in, nchan,
+        static_cast<uint16_t *>(d_out), pitch, ncols);
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_unpack(const void *d_in, int64_t nsamp_in, int nchan,
                           int nbits, void *d_out, int64_t pitch,
                           cudaStream_t s) {
-  if (nbits == 8 && nchan % 16 == 0) {
-    dim3 grid((unsigned)(pitch / kTS), (unsigned)((nchan + kTC - 1) / kTC));
-    unpack_u8_kernel<<<grid, 256, 0, s>>>(static_cast<const uint8_t *>(d_in),
-                                          nsamp_in, nchan,
-                                          static_cast<uint8_t *>(d_out), pitch);
-  } else if (nbits == 8) {
-    dim3 grid((unsigned)((pitch + 31) / 32), (unsigned)((nchan + 31) / 32));
-    unpack_generic_kernel<uint8_t><<<grid, 256, 0, s>>>(
-        static_cast<const uint8_t *>(d_in), nsamp_in, nchan,
-        static_cast<uint8_t *>(d_out), pitch);
-  } else {
-    dim3 grid((unsigned)((pitch + 31) / 32), (unsigned)((nchan + 31) / 32));
-    unpack_generic_kernel<uint16_t><<<grid, 256, 0, s>>>(
-        static_cast<const uint16_t *>(d_in), nsamp_in, nchan,
-        static_cast<uint16_t *>(d_out), pitch);
-  }
-  return cudaGetLastError();
+  return launch_unpack_cols(d_in, nsamp_in, nchan, nbits, d_out, pitch, pitch,
+                            s);
 }
 
 }  // namespace ddsp

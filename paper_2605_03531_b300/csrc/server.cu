@@ -1,0 +1,550 @@
+// server.cu -- streaming search of many beams of one shape (the real-time
+// ring-buffer design of Sec.2.1 and Ch.3: each beam delivers a block of B new
+// spectra at a time and every block is dedispersed and searched as soon as
+// the GPU is free, alongside whatever other beams have a block waiting).
+//
+// Per beam the server holds
+//   * a channel-major ring of `slots` blocks (slots = ceil(D16 / B) + 2, D16 =
+//     the largest delay rounded up to 16 samples) whose rows carry past the
+//     ring a copy of their first M bytes, M >= the longest window one
+//     dedispersion work item stages, so a staged window never wraps;
+//   * a series [ndm][C + B]: C = the widest boxcar minus one, rounded up to 4,
+//     carried over from the previous block so every boxcar that starts in the
+//     new block is complete;
+//   * per-window statistics and two candidate buffers (by block parity), so a
+//     block's candidates can be read while the next block is processed.
+// Block j's input lands in slot j % slots.  Its step dedisperses output
+// samples [s_j, s_j + B) with s_j = j*B - D16 (input [s_j, s_j + B + D) is
+// then resident: blocks j-slots+2 .. j), writing series columns [C, C + B),
+// and searches start times [0, B) of the whole series (global time
+// s_j - C + t).  Samples before the stream's start read as zero.  Pushing
+// block j overwrites the slot of block j - slots, which the step of block
+// j - 2 is the last to read, so a push waits for that step.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "host.h"
+#include "ws_item.cuh"
+
+using namespace ddsp;
+
+namespace {
+
+constexpr int kStepEvents = 64;
+
+struct ServerBeam {
+  bool live = false;
+  uint8_t *ring = nullptr;      // [nchan][pitch]
+  int32_t *series = nullptr;    // [ndm][ncols]
+  int64_t *m2 = nullptr, *mad4 = nullptr;
+  ddsp_cand *cands = nullptr;   // [2][cap]
+  int64_t pushed = 0;           // blocks ingested
+  int64_t processed = 0;        // blocks taken by enqueued steps
+  int64_t step_of[4] = {-1, -1, -1, -1};  // step of block j, by j % 4
+  int64_t push_seq[2] = {0, 0};  // server-wide push order of block j, by j % 2
+  cudaEvent_t ev_push[2] = {nullptr, nullptr};  // by block parity
+};
+
+}  // namespace
+
+struct ddsp_server {
+  int device = 0;
+  ddsp_plan *plan = nullptr;
+  int64_t B = 0, C = 0, D16 = 0, R = 0, M = 0, pitch = 0, ncols = 0, nwin = 0;
+  int slots = 0;
+  DedispTile tile;
+  DedispTables tab;
+  int cc = 0, rawmax = 0, elmax = 0, grid = 0, ipb = 0, ntt = 0;
+  size_t smem = 0, sps_smem = 0;
+  int max_beams = 0;
+  int64_t reserve = 0;
+  uint32_t cap = 0;
+  std::vector<ServerBeam> beams;
+  uint32_t *d_counts = nullptr;  // [max_beams][2]
+  int32_t *d_err = nullptr;
+  int *d_queue = nullptr;
+  WsBeam *d_wsb[2] = {nullptr, nullptr};
+  SpsBeam *d_sb[2] = {nullptr, nullptr};
+  WsBeam *h_wsb[2] = {nullptr, nullptr};   // pinned staging of a step's
+  SpsBeam *h_sb[2] = {nullptr, nullptr};   // descriptors, by step parity
+  cudaEvent_t ev_step[kStepEvents] = {};
+  int64_t nsteps = 0;
+  int64_t npushes = 0;
+};
+
+namespace {
+
+int64_t floor_mod(int64_t a, int64_t m) {
+  const int64_t r = a % m;
+  return r < 0 ? r + m : r;
+}
+
+int64_t beam_bytes(const ddsp_server &S) {
+  const Plan &p = S.plan->p;
+  return (int64_t)p.nchan * S.pitch + (int64_t)p.ndm * S.ncols * 4 +
+         2 * (int64_t)p.ndm * S.nwin * 8 + 2 * (int64_t)S.cap * 16;
+}
+
+void free_beam(ServerBeam &b) {
+  cudaFree(b.ring);
+  cudaFree(b.series);
+  cudaFree(b.m2);
+  cudaFree(b.mad4);
+  cudaFree(b.cands);
+  for (auto &e : b.ev_push)
+    if (e) cudaEventDestroy(e);
+  b = ServerBeam{};
+}
+
+void server_release(ddsp_server &S) {
+  for (auto &b : S.beams)
+    if (b.live) free_beam(b);
+  free_tables(S.tab);
+  cudaFree(S.d_counts);
+  cudaFree(S.d_err);
+  cudaFree(S.d_queue);
+  for (int i = 0; i < 2; ++i) {
+    cudaFree(S.d_wsb[i]);
+    cudaFree(S.d_sb[i]);
+    cudaFreeHost(S.h_wsb[i]);
+    cudaFreeHost(S.h_sb[i]);
+  }
+  for (auto &e : S.ev_step)
+    if (e) cudaEventDestroy(e);
+}
+
+// Event of step `id` (a later step's record of the same event only makes a
+// wait on it longer, never wrong: steps complete in order).
+cudaEvent_t step_event(const ddsp_server &S, int64_t id) {
+  return S.ev_step[id % kStepEvents];
+}
+
+// Candidates tiles tried in order when the caller leaves the choice to the
+// server: the first whose windows fit two blocks per SM for this shape.
+const DedispTile kServerTiles[] = {
+    {4, 2, 8, 8, 2, kTileWarpSpecialized}, {8, 1, 8, 4, 3, kTileWarpSpecialized},
+    {4, 2, 8, 4, 3, kTileWarpSpecialized}, {8, 1, 4, 4, 3, kTileWarpSpecialized},
+    {4, 2, 4, 4, 2, kTileWarpSpecialized}, {8, 1, 4, 2, 2, kTileWarpSpecialized},
+    {8, 1, 4, 1, 2, kTileWarpSpecialized}};
+
+// Fit tile t to the server's shape: per-beam chunk (largest <= t.chan_chunk
+// within the two-block budget, else one block), buffers, grid.
+int server_apply_tile(ddsp_server &S, const DedispTile &t) {
+  const Plan &p = S.plan->p;
+  if (!dedisp_tile_supported(t, 8) || !(t.flags & kTileWarpSpecialized))
+    return DDSP_E_INVALID_ARG;
+  const int TT = dedisp_time_tile(t, 8);
+  if (S.B % TT) return DDSP_E_INVALID_ARG;
+  const int span = span_for(p, t.dm_tile());
+  int rawmax, elmax;
+  dedisp_buffer_sizes(t, span, 8, &rawmax, &elmax);
+  int cc = 0;
+  size_t smem = 0;
+  for (size_t budget : {kSmemBudgetTwoBlocks, kSmemBudgetOneBlock}) {
+    for (int c = t.chan_chunk; c >= 1 && !cc; --c) {
+      const size_t sm =
+          dedisp_ws_smem_bytes(c, t.dm_tile(), rawmax, elmax, t.nbuf);
+      if (sm <= budget) {
+        cc = c;
+        smem = sm;
+      }
+    }
+    if (cc) break;
+  }
+  if (!cc) return DDSP_E_INVALID_ARG;
+  int rc = build_tables_for(p, t, S.tab);
+  if (rc != DDSP_OK) return rc;
+  int per_sm = persistent_blocks_per_sm(t, smem);
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, S.device);
+  if (per_sm <= 0 || nsm <= 0) return DDSP_E_INVALID_ARG;
+  S.tile = t;
+  S.cc = cc;
+  S.rawmax = rawmax;
+  S.elmax = elmax;
+  S.smem = smem;
+  S.grid = per_sm * nsm;
+  S.ntt = (int)(S.B / TT);
+  S.ipb = S.tab.n_dm_tiles * S.ntt;
+  // the longest staged window, rounded up: the mirrored row tail
+  S.M = round_up(dedisp_copy_bytes(t, S.tab.span_max, 8) + 16, 128);
+  return DDSP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ddsp_server_create(ddsp_server **out, ddsp_plan *plan,
+                       int64_t block_samples, int max_beams,
+                       int64_t hbm_reserve_bytes, int dm_tile,
+                       int dm_per_thread, int chan_chunk, int stages) {
+  if (!out || !plan || max_beams <= 0 || hbm_reserve_bytes < 0)
+    return DDSP_E_INVALID_ARG;
+  *out = nullptr;
+  const Plan &p = plan->p;
+  if (p.nbits != 8 || p.nchan % 16 != 0) return DDSP_E_INVALID_ARG;
+  if (block_samples <= 0 || block_samples % 16) return DDSP_E_SHAPE;
+  ddsp_server *S = new (std::nothrow) ddsp_server;
+  if (!S) return DDSP_E_NOMEM;
+  S->device = p.device;
+  DeviceGuard g(S->device);
+  S->plan = plan;
+  S->B = block_samples;
+  S->C = round_up(p.widths.back() - 1, 4);
+  S->D16 = round_up(p.max_delay, 16);
+  S->slots = (int)((S->D16 + S->B - 1) / S->B) + 2;
+  S->R = S->slots * S->B;
+  S->ncols = S->C + S->B;
+  S->max_beams = max_beams;
+  S->reserve = hbm_reserve_bytes;
+  S->cap = (uint32_t)std::min<size_t>(p.cand_capacity, 0xffffffffu);
+  int rc = DDSP_OK;
+  if (S->B < S->C) rc = DDSP_E_SHAPE;
+  if (rc == DDSP_OK) rc = search_windows(p, S->ncols, &S->nwin);
+  if (rc == DDSP_OK) {
+    if (dm_tile > 0) {
+      DedispTile t;
+      if (dm_per_thread <= 0 || dm_tile % dm_per_thread) {
+        rc = DDSP_E_INVALID_ARG;
+      } else {
+        t.rd = dm_per_thread;
+        t.wd = dm_tile / dm_per_thread;
+        t.wt = t.wd > 0 ? (kThreads / 32) / t.wd : 0;
+        t.chan_chunk = chan_chunk;
+        t.nbuf = stages;
+        t.flags = kTileWarpSpecialized;
+        rc = server_apply_tile(*S, t);
+      }
+    } else {
+      rc = DDSP_E_INVALID_ARG;
+      for (const DedispTile &t : kServerTiles) {
+        rc = server_apply_tile(*S, t);
+        if (rc == DDSP_OK) break;
+      }
+    }
+  }
+  if (rc == DDSP_OK && S->M > S->B) rc = DDSP_E_SHAPE;  // mirror from one block
+  if (rc == DDSP_OK) {
+    S->pitch = round_up(S->R + S->M, 128);
+    const int64_t maxlen = (p.norm_window <= 0 || S->nwin == 1)
+                               ? S->ncols
+                               : std::max<int64_t>(p.norm_window,
+                                                   S->ncols - (S->nwin - 1) * p.norm_window);
+    S->sps_smem = sps_smem_bytes(maxlen, p.widths.back());
+    S->beams.resize(max_beams);
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+      if ((e = cudaMalloc(&S->d_wsb[i], max_beams * sizeof(WsBeam))) == cudaSuccess &&
+          (e = cudaMalloc(&S->d_sb[i], max_beams * sizeof(SpsBeam))) == cudaSuccess &&
+          (e = cudaMallocHost(&S->h_wsb[i], max_beams * sizeof(WsBeam))) == cudaSuccess)
+        e = cudaMallocHost(&S->h_sb[i], max_beams * sizeof(SpsBeam));
+    }
+    if (e == cudaSuccess &&
+        (e = cudaMalloc(&S->d_counts, 2 * max_beams * sizeof(uint32_t))) == cudaSuccess &&
+        (e = cudaMalloc(&S->d_err, sizeof(int32_t))) == cudaSuccess)
+      e = cudaMalloc(&S->d_queue, sizeof(int));
+    for (int i = 0; i < kStepEvents && e == cudaSuccess; ++i)
+      e = cudaEventCreateWithFlags(&S->ev_step[i], cudaEventDisableTiming);
+    if (e == cudaSuccess) {
+      cudaMemset(S->d_counts, 0, 2 * max_beams * sizeof(uint32_t));
+      e = cudaMemset(S->d_err, 0, sizeof(int32_t));
+    }
+    if (e != cudaSuccess) rc = cuda_rc(e);
+  }
+  if (rc != DDSP_OK) {
+    server_release(*S);
+    delete S;
+    return rc;
+  }
+  *out = S;
+  return DDSP_OK;
+}
+
+void ddsp_server_destroy(ddsp_server *S) {
+  if (!S) return;
+  DeviceGuard g(S->device);
+  cudaDeviceSynchronize();
+  server_release(*S);
+  delete S;
+}
+
+int ddsp_server_info(const ddsp_server *S, int64_t *beam_bytes_out,
+                     int64_t *ring_samples, int64_t *series_cols,
+                     int64_t *carry, int64_t *first_delay) {
+  if (!S) return DDSP_E_INVALID_ARG;
+  if (beam_bytes_out) *beam_bytes_out = beam_bytes(*S);
+  if (ring_samples) *ring_samples = S->R;
+  if (series_cols) *series_cols = S->ncols;
+  if (carry) *carry = S->C;
+  if (first_delay) *first_delay = S->D16;
+  return DDSP_OK;
+}
+
+int ddsp_server_get_tile(const ddsp_server *S, int *dm_tile, int *dm_per_thread,
+                         int *time_tile, int *chan_chunk, int *stages,
+                         int *grid) {
+  if (!S) return DDSP_E_INVALID_ARG;
+  if (dm_tile) *dm_tile = S->tile.dm_tile();
+  if (dm_per_thread) *dm_per_thread = S->tile.rd;
+  if (time_tile) *time_tile = dedisp_time_tile(S->tile, 8);
+  if (chan_chunk) *chan_chunk = S->cc;
+  if (stages) *stages = S->tile.nbuf;
+  if (grid) *grid = S->grid;
+  return DDSP_OK;
+}
+
+int ddsp_server_admit(ddsp_server *S, int *beam) {
+  if (!S || !beam) return DDSP_E_INVALID_ARG;
+  *beam = -1;
+  DeviceGuard g(S->device);
+  int slot = -1;
+  for (int i = 0; i < S->max_beams && slot < 0; ++i)
+    if (!S->beams[i].live) slot = i;
+  if (slot < 0) return DDSP_E_RANGE;
+  size_t free_b = 0, total_b = 0;
+  cudaError_t e = cudaMemGetInfo(&free_b, &total_b);
+  if (e != cudaSuccess) return cuda_rc(e);
+  if ((int64_t)free_b < beam_bytes(*S) + S->reserve) return DDSP_E_NOMEM;
+  const Plan &p = S->plan->p;
+  ServerBeam b;
+  if ((e = cudaMalloc(&b.ring, (size_t)p.nchan * S->pitch)) == cudaSuccess &&
+      (e = cudaMalloc(&b.series, (size_t)p.ndm * S->ncols * 4)) == cudaSuccess &&
+      (e = cudaMalloc(&b.m2, (size_t)p.ndm * S->nwin * 8)) == cudaSuccess &&
+      (e = cudaMalloc(&b.mad4, (size_t)p.ndm * S->nwin * 8)) == cudaSuccess &&
+      (e = cudaMalloc(&b.cands, 2 * (size_t)S->cap * sizeof(ddsp_cand))) == cudaSuccess &&
+      (e = cudaEventCreateWithFlags(&b.ev_push[0], cudaEventDisableTiming)) == cudaSuccess &&
+      (e = cudaEventCreateWithFlags(&b.ev_push[1], cudaEventDisableTiming)) == cudaSuccess &&
+      (e = cudaMemset(b.ring, 0, (size_t)p.nchan * S->pitch)) == cudaSuccess)
+    e = cudaMemset(b.series, 0, (size_t)p.ndm * S->ncols * 4);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) {
+    free_beam(b);
+    return cuda_rc(e);
+  }
+  b.live = true;
+  S->beams[slot] = b;
+  *beam = slot;
+  return DDSP_OK;
+}
+
+int ddsp_server_evict(ddsp_server *S, int beam) {
+  if (!S || beam < 0 || beam >= S->max_beams || !S->beams[beam].live)
+    return DDSP_E_INVALID_ARG;
+  DeviceGuard g(S->device);
+  cudaDeviceSynchronize();
+  free_beam(S->beams[beam]);
+  return DDSP_OK;
+}
+
+int ddsp_server_push(ddsp_server *S, int beam, const void *d_block,
+                     ddsp_stream_t stream) {
+  if (!S || beam < 0 || beam >= S->max_beams || !S->beams[beam].live ||
+      !d_block || ((uintptr_t)d_block & 15))
+    return DDSP_E_INVALID_ARG;
+  ServerBeam &b = S->beams[beam];
+  const int64_t j = b.pushed;
+  // the slot of block j - slots is read last by the step of block j - 2
+  if (j >= 2 && b.processed < j - 1) return DDSP_E_STATE;
+  DeviceGuard g(S->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  if (j >= 2) e = cudaStreamWaitEvent(s, step_event(*S, b.step_of[(j - 2) % 4]), 0);
+  const Plan &p = S->plan->p;
+  const int64_t slot = j % S->slots;
+  // only the slot's columns (and the mirror's) are written
+  if (e == cudaSuccess)
+    e = launch_unpack_cols(d_block, S->B, p.nchan, 8, b.ring + slot * S->B,
+                           S->pitch, S->B, s);
+  if (e == cudaSuccess && slot == 0)   // the mirrored row tail
+    e = launch_unpack_cols(d_block, S->M, p.nchan, 8, b.ring + S->R, S->pitch,
+                           S->M, s);
+  if (e == cudaSuccess) e = cudaEventRecord(b.ev_push[j & 1], s);
+  if (e != cudaSuccess) return cuda_rc(e);
+  b.push_seq[j & 1] = S->npushes++;
+  b.pushed = j + 1;
+  return DDSP_OK;
+}
+
+int ddsp_server_step(ddsp_server *S, float threshold, int max_beams_in_step,
+                     ddsp_stream_t stream, int64_t *step_id, int *beams_out,
+                     int cap, int *nbeams) {
+  if (!S || !nbeams || !(threshold > 0.0f) || !isfinite(threshold) ||
+      max_beams_in_step < 0)
+    return DDSP_E_INVALID_ARG;
+  *nbeams = 0;
+  if (step_id) *step_id = -1;
+  DeviceGuard g(S->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const Plan &p = S->plan->p;
+  const int64_t id = S->nsteps;
+  const int par = (int)(id & 1);
+  // the staging of step id - 2 must have been read before it is rewritten
+  cudaError_t e = cudaSuccess;
+  if (id >= 2) e = cudaEventSynchronize(step_event(*S, id - 2));
+  if (e != cudaSuccess) return cuda_rc(e);
+  // beams with a block waiting, oldest push first
+  std::vector<int> ready;
+  for (int i = 0; i < S->max_beams; ++i) {
+    const ServerBeam &b = S->beams[i];
+    if (b.live && b.processed < b.pushed) ready.push_back(i);
+  }
+  auto seq = [&](int i) {
+    const ServerBeam &b = S->beams[i];
+    return b.push_seq[b.processed & 1];
+  };
+  std::sort(ready.begin(), ready.end(),
+            [&](int a, int c) { return seq(a) < seq(c); });
+  if (max_beams_in_step > 0 && (int)ready.size() > max_beams_in_step)
+    ready.resize(max_beams_in_step);
+  int n = 0;
+  for (int i : ready) {
+    ServerBeam &b = S->beams[i];
+    const int64_t j = b.processed;
+    if ((e = cudaStreamWaitEvent(s, b.ev_push[j & 1], 0)) != cudaSuccess)
+      return cuda_rc(e);
+    WsBeam &w = S->h_wsb[par][n];
+    memset(&w, 0, sizeof(w));
+    w.cm = b.ring;
+    w.pitch = S->pitch;
+    w.nsamp_out = S->B;
+    w.ring = S->R;
+    w.t0 = floor_mod(j * S->B - S->D16, S->R);
+    w.out_pitch = S->ncols;
+    w.desc = reinterpret_cast<const int2 *>(S->tab.d_desc);
+    w.relb = S->tab.d_relb;
+    w.rowmap = S->tab.d_rowmap;
+    w.out = b.series + S->C;
+    w.nchan = p.nchan;
+    w.n_dm_tiles = S->tab.n_dm_tiles;
+    w.n_time_tiles = S->ntt;
+    w.cc = S->cc;
+    w.rawmax = S->rawmax;
+    w.elmax = S->elmax;
+    SpsBeam &q = S->h_sb[par][n];
+    memset(&q, 0, sizeof(q));
+    q.series = b.series;
+    q.widths = p.d_widths;
+    q.m2 = b.m2;
+    q.mad4 = b.mad4;
+    q.cands = b.cands + (size_t)(j & 1) * S->cap;
+    q.count = S->d_counts + 2 * i + (j & 1);
+    q.err = S->d_err;
+    q.n = S->ncols;
+    q.L = p.norm_window;
+    q.nwin = S->nwin;
+    q.block0 = (int64_t)n * p.ndm * S->nwin;
+    q.nrep = S->B;
+    q.ndm = p.ndm;
+    q.nw = p.nwidths;
+    q.cap = S->cap;
+    if (beams_out && n < cap) beams_out[n] = i;
+    ++n;
+  }
+  if (n == 0) return DDSP_OK;
+  // steps run in order even if the caller moves between streams
+  if (id >= 1) e = cudaStreamWaitEvent(s, step_event(*S, id - 1), 0);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(S->d_wsb[par], S->h_wsb[par], n * sizeof(WsBeam),
+                        cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(S->d_sb[par], S->h_sb[par], n * sizeof(SpsBeam),
+                        cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = launch_serve_prep(S->d_sb[par], n, p.ndm, S->ncols, (int)S->C,
+                          S->d_queue, s);
+  const int64_t nitems = (int64_t)n * S->ipb;
+  if (e == cudaSuccess && nitems > 0x7fffffff) e = cudaErrorInvalidValue;
+  if (e == cudaSuccess)
+    e = launch_dedisperse_persistent(
+        S->tile, S->d_wsb[par], nullptr, (int)nitems, S->ipb, S->ntt,
+        S->d_queue, S->smem, S->d_err, (int)std::min<int64_t>(S->grid, nitems), s);
+  if (e == cudaSuccess)
+    e = launch_sps_batch(S->d_sb[par], n, (int64_t)n * p.ndm * S->nwin,
+                         threshold, S->sps_smem, s);
+  if (e == cudaSuccess) e = cudaEventRecord(step_event(*S, id), s);
+  if (e != cudaSuccess) return cuda_rc(e);
+  for (int i : ready) {
+    ServerBeam &b = S->beams[i];
+    b.step_of[b.processed % 4] = id;
+    ++b.processed;
+  }
+  S->nsteps = id + 1;
+  if (step_id) *step_id = id;
+  *nbeams = n;
+  return DDSP_OK;
+}
+
+int ddsp_server_query(ddsp_server *S, int64_t step_id) {
+  if (!S || step_id < 0 || step_id >= S->nsteps) return DDSP_E_INVALID_ARG;
+  if (step_id < S->nsteps - kStepEvents) return 1;  // later steps were recorded
+  DeviceGuard g(S->device);
+  cudaError_t e = cudaEventQuery(step_event(*S, step_id));
+  if (e == cudaSuccess) return 1;
+  if (e == cudaErrorNotReady) return 0;
+  return cuda_rc(e);
+}
+
+int ddsp_server_fetch(ddsp_server *S, int beam, int64_t block,
+                      ddsp_cand *host_buf, size_t cap, size_t *n_found,
+                      int64_t *t_start) {
+  if (!S || beam < 0 || beam >= S->max_beams || !S->beams[beam].live ||
+      !n_found || (cap > 0 && !host_buf))
+    return DDSP_E_INVALID_ARG;
+  ServerBeam &b = S->beams[beam];
+  // the last two processed blocks keep their candidates
+  if (block < 0 || block >= b.processed || block < b.processed - 2)
+    return DDSP_E_STATE;
+  DeviceGuard g(S->device);
+  cudaError_t e = cudaEventSynchronize(step_event(*S, b.step_of[block % 4]));
+  uint32_t cnt = 0;
+  if (e == cudaSuccess)
+    e = cudaMemcpy(&cnt, S->d_counts + 2 * beam + (block & 1), 4,
+                   cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_rc(e);
+  const size_t stored = std::min<size_t>(cnt, S->cap);
+  const size_t ncopy = std::min(stored, cap);
+  if (ncopy > 0) {
+    e = cudaMemcpy(host_buf, b.cands + (size_t)(block & 1) * S->cap,
+                   ncopy * sizeof(ddsp_cand), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_rc(e);
+    std::sort(host_buf, host_buf + ncopy,
+              [](const ddsp_cand &a, const ddsp_cand &c) {
+                return a.dm_idx != c.dm_idx ? a.dm_idx < c.dm_idx : a.t < c.t;
+              });
+  }
+  *n_found = cnt;
+  if (t_start) *t_start = block * S->B - S->D16 - S->C;
+  return (cnt > ncopy) ? DDSP_E_TRUNCATED : DDSP_OK;
+}
+
+int ddsp_server_series(ddsp_server *S, int beam, int32_t **d_series,
+                       int64_t *ncols) {
+  if (!S || beam < 0 || beam >= S->max_beams || !S->beams[beam].live ||
+      !d_series)
+    return DDSP_E_INVALID_ARG;
+  *d_series = S->beams[beam].series;
+  if (ncols) *ncols = S->ncols;
+  return DDSP_OK;
+}
+
+int ddsp_server_check(ddsp_server *S, ddsp_stream_t stream) {
+  if (!S) return DDSP_E_INVALID_ARG;
+  DeviceGuard g(S->device);
+  cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_rc(e);
+  int32_t v = 0;
+  e = cudaMemcpy(&v, S->d_err, 4, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_rc(e);
+  if (v != kErrNone) {
+    cudaMemset(S->d_err, 0, 4);
+    return v == kErrRange ? DDSP_E_RANGE : DDSP_E_TIMEOUT;
+  }
+  return DDSP_OK;
+}
+
+}  // extern "C"

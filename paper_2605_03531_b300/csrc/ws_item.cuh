@@ -16,7 +16,11 @@
 //     "empty" mbarrier; every <= 256 channels the byte lanes are unpacked and
 //     added into the output array (uint8) or into registers (uint16).
 // The mbarrier phases run on a chunk counter that continues across the
-// items a block processes (`jbase`).  Every wait is bounded; a role that
+// items a block processes (`jbase`).  Each beam carries its own channel
+// chunk and buffer extents, so items of different beams lay out the same
+// shared memory differently; an item starts only after every role has
+// finished the previous one, so no copy of one layout is in flight when the
+// next begins.  Every wait is bounded; a role that
 // gives up records a timeout, drains its own copies in flight (bounded) and
 // returns false.
 #pragma once
@@ -50,19 +54,28 @@ struct WsLayout {
   }
 };
 
-// One beam as the dedispersion sees it (device copy for the batch).
+// One beam as the dedispersion sees it (device copy for the batch).  Input
+// sample t + d of channel c sits at row offset t + d (ring == 0), or at
+// (t0 + t + d) mod ring for a ring buffer whose rows carry, past `ring`, a
+// copy of their first bytes so no staged window wraps.
 struct WsBeam {
   const void *cm;           // channel-major rows [nchan][pitch]
   int64_t pitch;
   int64_t nsamp_out;
+  int64_t ring;             // ring length in samples, 0 = linear rows
+  int64_t t0;               // ring position of output sample 0's input
+  int64_t out_pitch;        // output row pitch (samples)
   const int2 *desc;         // [n_dm_tiles][nchan] {window start, bytes}
   const int32_t *relb;      // [n_dm_tiles][nchan][DT] element-byte offsets
   const int32_t *rowmap;    // [n_dm_tiles*DT] output row or -1
-  int32_t *out;             // [ndm][nsamp_out]
+  int32_t *out;             // [ndm][out_pitch]
   int nchan;
   int n_dm_tiles;
   int n_time_tiles;
-  int pad;
+  int cc;                   // channels per chunk (<= 32)
+  int rawmax;               // bytes of one raw channel window
+  int elmax;                // elements of one relayouted channel
+  int pad[2];
 };
 
 __device__ __forceinline__ void ws_init_barriers(unsigned char *smem,
@@ -85,8 +98,7 @@ __device__ __forceinline__ void ws_init_barriers(unsigned char *smem,
 template <int WT, int WD, int RD, typename T>
 __device__ __forceinline__ bool ws_item(const WsBeam &a, int g, int64_t T0,
                                         int jbase, unsigned char *smem,
-                                        const WsLayout &L, int cc, int nbuf,
-                                        int rawmax, int elmax, int32_t *err,
+                                        int nbuf, int32_t *err,
                                         long long timeout_cycles) {
   constexpr int SPE = 4 / sizeof(T);   // samples per element
   constexpr int E = kElemPerThread;
@@ -95,6 +107,8 @@ __device__ __forceinline__ bool ws_item(const WsBeam &a, int g, int64_t T0,
   constexpr int NC = WT * WD;          // consumer warps
   constexpr int NP = kWsProdWarps;
   constexpr bool kRegTot = SPE != 4;   // uint16 totals stay in registers
+  const int cc = a.cc, rawmax = a.rawmax, elmax = a.elmax;
+  const WsLayout L(cc, DT, rawmax, elmax, nbuf);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   uint64_t *raw_full = reinterpret_cast<uint64_t *>(smem);
@@ -135,10 +149,12 @@ __device__ __forceinline__ bool ws_item(const WsBeam &a, int g, int64_t T0,
         mbar_expect_tx(&raw_full[st], total);
       }
       __syncwarp();
-      if (v)
+      if (v) {
+        int64_t pos = T0 + nd.x;
+        if (a.ring > 0) pos = (a.t0 + pos) % a.ring;
         bulk_g2s(raw + (st * cc + lane) * rawmax,
-                 cm + (int64_t)(c0 + lane) * a.pitch + T0 + nd.x, nb,
-                 &raw_full[st]);
+                 cm + (int64_t)(c0 + lane) * a.pitch + pos, nb, &raw_full[st]);
+      }
       if (lane == 0)
         bulk_g2s(raw_rel + st * L.rel_stride, rel_g + (int64_t)c0 * DT,
                  relbytes, &raw_full[st]);
@@ -318,7 +334,7 @@ __device__ __forceinline__ bool ws_item(const WsBeam &a, int g, int64_t T0,
 #pragma unroll
         for (int r = 0; r < RD; ++r) {
           const int row = __ldg(a.rowmap + g * DT + RD * wd + r);
-          int32_t *o = a.out + (int64_t)(row < 0 ? 0 : row) * nsamp_out;
+          int32_t *o = a.out + (int64_t)(row < 0 ? 0 : row) * a.out_pitch;
 #pragma unroll
           for (int e = 0; e < E; ++e) {
             const uint32_t Ev = accE[r][e], O = accO[r][e];
@@ -348,7 +364,7 @@ __device__ __forceinline__ bool ws_item(const WsBeam &a, int g, int64_t T0,
     for (int r = 0; r < RD; ++r) {
       const int row = a.rowmap[g * DT + RD * wd + r];
       if (row < 0) continue;
-      int32_t *o = a.out + (int64_t)row * nsamp_out;
+      int32_t *o = a.out + (int64_t)row * a.out_pitch;
 #pragma unroll
       for (int e = 0; e < E; ++e)
 #pragma unroll

@@ -357,3 +357,42 @@ def config3(nbeams=160, seed=3, nsamp_range=(65536, 262144),
                                    snr_range=(8.0, 30.0), spacing=spacing)
         beams.append(cfg)
     return beams
+
+
+# ------------------------------------------------------ streaming arrivals (c5)
+BLOCK_PERIOD_S = 16384 * 81.92e-6   # one 16384-spectrum block at 81.92 us
+
+
+def arrival_times(nbeams, nblocks, period=BLOCK_PERIOD_S, seed=5,
+                  jitter_mean=0.05):
+    """Arrival time (s) of block k of beam b: k*period + phi_b + e_bk, with
+    a per-beam phase phi_b ~ U[0, period) and an exponential delay e_bk of
+    mean `jitter_mean` (inverse CDF of counter-based uniforms).  Returns
+    float64 [nbeams, nblocks], increasing along each beam."""
+    nb, nk = int(nbeams), int(nblocks)
+    ctr_phase = np.arange(nb, dtype=np.uint64) + np.uint64(1 << 44)
+    phi = uniform_np(ctr_phase, seed) * period
+    ctr = np.arange(nb * nk, dtype=np.uint64) + np.uint64(1 << 45)
+    u = uniform_np(ctr, seed).reshape(nb, nk)
+    e = -jitter_mean * np.log1p(-u)
+    t = np.arange(nk, dtype=np.float64)[None, :] * period + phi[:, None] + e
+    # a block cannot arrive before the one before it
+    return np.maximum.accumulate(t, axis=1)
+
+
+def config5(nbeams=64, seed=5):
+    """Streaming beams of the 4096-channel shape of config2 (300-500 MHz,
+    81.92 us, 1024 DMs over 0-250, widths 1..256, L 8192) delivering
+    16384-spectrum blocks; one FilterbankConfig per beam (nsamp_out = one
+    block) with its own seed."""
+    base = config2()
+    beams = []
+    for b in range(int(nbeams)):
+        cfg = FilterbankConfig(
+            name=f"c5-beam{b}", nchan=base.nchan, f_top=base.f_top,
+            chan_bw=base.chan_bw, tsamp=base.tsamp, nsamp_out=16384,
+            dm_lo=base.dm_lo, dm_hi=base.dm_hi, ndm=base.ndm,
+            widths=list(base.widths), threshold=base.threshold,
+            seed=seed * 100000 + b)
+        beams.append(cfg)
+    return beams

@@ -135,3 +135,35 @@ def test_batch_full_160_beams_sampled():
         for k, t in zip(rng.integers(0, c.ndm, 40), rng.integers(0, c.nsamp_out, 40)):
             assert int(s[k, t]) == oracle.dedisperse_at(xh, d, int(k), int(t))
         del x, s
+
+
+def test_batch_per_beam_chunks():
+    """Beams whose delay spans inside a DM tile differ by ~40x share one
+    launch: the coarse beam stages one channel per chunk, the fine ones up
+    to the tile's limit, and every beam stays exact for several limits."""
+    coarse = synth.config3(nbeams=1, seed=23, nsamp_range=(8192, 8192),
+                           nchan_choices=(256,), dm_hi_choices=(100.0,),
+                           ndm_choices=(64,))
+    fine = synth.config3(nbeams=2, seed=29, nsamp_range=(8192, 16384),
+                         nchan_choices=(1024,), dm_hi_choices=(10.0,),
+                         ndm_choices=(128,))
+    cfgs = coarse + fine
+    plans = [_plan(c) for c in cfgs]
+    blocks = [_block(c, p) for c, p in zip(cfgs, plans)]
+    ref = [p.dedisperse(x).clone() for p, x in zip(plans, blocks)]
+    batch = Batch(plans, [x.shape[0] for x in blocks])
+    for b, x in enumerate(blocks):
+        batch.ingest(b, x)
+    for cap in (8, 3, 1):
+        batch.set_tile(16, 8, cap, 3)
+        chunks = [batch.beam_chunk(b) for b in range(len(cfgs))]
+        # spans per 16-trial tile: ~8500 samples (coarse), ~440 (fine)
+        assert chunks[0] == 1 and all(1 <= c <= cap for c in chunks)
+        assert chunks[1] == chunks[2] >= min(cap, 3)
+        for s in batch.series:
+            s.fill_(-1)
+        batch.run(7.0, use_graph=True)
+        batch.run(7.0, use_graph=True)
+        batch.check()
+        for b in range(len(cfgs)):
+            assert torch.equal(batch.series[b], ref[b]), (cap, b)
