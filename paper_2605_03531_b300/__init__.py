@@ -431,10 +431,11 @@ class Server:
             _lib.check(rc, "ddsp_server_query")
         return rc == 1
 
-    def fetch(self, beam, block, cap=None):
+    def fetch(self, beam, block, cap=None, allow_truncated=False):
         """(candidates sorted by (dm_idx, t), true count, global output
         sample of series column 0) of one of the beam's two most recently
-        stepped blocks."""
+        stepped blocks.  With allow_truncated, a block that found more than
+        the capacity returns the stored records and the true count."""
         if cap is None:
             cap = self.plan.cand_capacity
         buf = np.zeros(cap, dtype=CAND_DTYPE)
@@ -442,6 +443,8 @@ class Server:
         rc = _lib.lib().ddsp_server_fetch(
             self._h, int(beam), int(block), buf.ctypes.data_as(C.c_void_p),
             int(cap), C.byref(n), C.byref(t0))
+        if rc == _lib.DDSP_E_TRUNCATED and allow_truncated:
+            return buf[:min(cap, self.plan.cand_capacity)].copy(), n.value, t0.value
         _lib.check(rc, "ddsp_server_fetch")
         return buf[:n.value].copy(), n.value, t0.value
 

@@ -76,17 +76,19 @@ class ServingLoop:
 
     server: push(beam, x, stream) -> bool, step(threshold, max_beams_in_step,
         stream) -> (step id, beams), done(step id) -> bool,
-        fetch(beam, block) -> (cands, count, t_start)
+        fetch(beam, block, allow_truncated) -> (cands, count, t_start)
     beams: the server's beam index for each schedule row
     source(i, k): host block k of schedule row i
     stager: stage(host) -> (device block, token), consumed(token); None
         passes the source's block through unchanged
+    first_block: the server's block number of schedule column 0 (blocks
+        the beams received before this run)
     """
 
     def __init__(self, server, beams, source, threshold, stager=None,
                  max_beams_in_step=0, max_inflight=1, compute_stream=None,
                  clock=time.monotonic, sleep=time.sleep, poll=2e-4,
-                 on_candidates=None):
+                 on_candidates=None, first_block=0):
         self.server = server
         self.beams = list(beams)
         self.source = source
@@ -99,6 +101,7 @@ class ServingLoop:
         self.sleep = sleep
         self.poll = float(poll)
         self.on_candidates = on_candidates
+        self.first_block = int(first_block)
 
     def run(self, arrivals, time_limit=None):
         """Serve the schedule (arrivals[i][k] = seconds after the start at
@@ -186,7 +189,10 @@ class ServingLoop:
                     res.step_sizes.append(len(sbeams))
                     busy = True
             for i, k in finished:
-                cands, n, t_start = self.server.fetch(self.beams[i], k)
+                # a block over the candidate capacity keeps its first records
+                # and reports the true count
+                cands, n, t_start = self.server.fetch(
+                    self.beams[i], self.first_block + k, allow_truncated=True)
                 ncand[i, k] = n
                 if self.on_candidates is not None:
                     self.on_candidates(i, k, cands, t_start)

@@ -71,7 +71,7 @@ class FakeServer:
     def done(self, sid):
         return self.clock() >= self.steps[sid][0]
 
-    def fetch(self, beam, block):
+    def fetch(self, beam, block, allow_truncated=False):
         assert self.processed[beam] - 2 <= block < self.processed[beam]
         assert self.done(self.step_of[(beam, block)])
         self.fetched.append((beam, block))
