@@ -32,6 +32,7 @@ def _sources():
 
 def _deps():
     return (_sources() + glob.glob(os.path.join(CSRC, "*.h"))
+            + glob.glob(os.path.join(CSRC, "*.cuh"))
             + [os.path.join(INCLUDE, "ddsp.h"), os.path.abspath(__file__)])
 
 

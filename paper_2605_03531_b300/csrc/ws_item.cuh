@@ -10,11 +10,15 @@
 //     of two element buffers -- element i = {x[i], x[i+S], x[i+2S], x[i+3S]}
 //     so a 32-bit shared load at any delay yields four output times -- and
 //     copy its delay offsets beside it;
-//   * consumer warps (WT x WD): SWAR accumulation of two channels per step
-//     (acc_even += (wa & M) + (wb & M), acc_odd += (wa >> 8) + (wb >> 8),
-//     exact for <= 256 channels), releasing each element buffer through its
-//     "empty" mbarrier; every <= 256 channels the byte lanes are unpacked and
-//     added into the output array (uint8) or into registers (uint16).
+//   * consumer warps (WT x WD): SWAR accumulation of two channels per step,
+//     A += wa + wb (whole words, mod 2^32) and B += p(wa) + p(wb) with p(w) =
+//     {b1, 0, b3, 0} (one byte permute against zero), releasing each element
+//     buffer through its "empty" mbarrier.  For <= 256 channels B's 16-bit
+//     halves are the exact sums of bytes 1 and 3, and A - (B << 8) holds
+//     those of bytes 0 and 2 (each < 2^16), so every <= 256 channels the
+//     four sums are recovered and added into the output array (uint8: the
+//     first time stored, then by reductions), or kept in registers
+//     (uint16).
 // The mbarrier phases run on a chunk counter that continues across the
 // items a block processes (`jbase`).  Each beam carries its own channel
 // chunk and buffer extents, so items of different beams lay out the same
@@ -241,14 +245,14 @@ __device__ __forceinline__ bool ws_item(const WsBeam &a, int g, int64_t T0,
   // ============================= consumers =============================
   const int wt = warp % WT, wd = warp / WT;
   const int i0 = 32 * E * wt + lane;  // first element of this thread
-  uint32_t accE[RD][E], accO[RD][E];
+  uint32_t accA[RD][E], accB[RD][E];
   int32_t tot[kRegTot ? RD : 1][E][SPE];
 #pragma unroll
   for (int r = 0; r < RD; ++r)
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-      accE[r][e] = 0;
-      accO[r][e] = 0;
+      accA[r][e] = 0;
+      accB[r][e] = 0;
       if constexpr (kRegTot) {
 #pragma unroll
         for (int m = 0; m < SPE; ++m) tot[r][e][m] = 0;
@@ -295,8 +299,8 @@ __device__ __forceinline__ bool ws_item(const WsBeam &a, int g, int64_t T0,
           const uint32_t wa = *reinterpret_cast<const uint32_t *>(pa + 128 * e);
           const uint32_t wb = *reinterpret_cast<const uint32_t *>(pb + 128 * e);
           if constexpr (SPE == 4) {
-            accE[r][e] += (wa & 0x00FF00FFu) + (wb & 0x00FF00FFu);
-            accO[r][e] += (wa >> 8) + (wb >> 8);
+            accA[r][e] += wa + wb;
+            accB[r][e] += __byte_perm(wa, 0u, 0x4341) + __byte_perm(wb, 0u, 0x4341);
           } else {
             tot[r][e][0] += (int32_t)((wa & 0xFFFFu) + (wb & 0xFFFFu));
             tot[r][e][1] += (int32_t)((wa >> 16) + (wb >> 16));
@@ -315,8 +319,8 @@ __device__ __forceinline__ bool ws_item(const WsBeam &a, int g, int64_t T0,
         for (int e = 0; e < E; ++e) {
           const uint32_t wa = *reinterpret_cast<const uint32_t *>(pa + 128 * e);
           if constexpr (SPE == 4) {
-            accE[r][e] += wa & 0x00FF00FFu;
-            accO[r][e] += wa >> 8;
+            accA[r][e] += wa;
+            accB[r][e] += __byte_perm(wa, 0u, 0x4341);
           } else {
             tot[r][e][0] += (int32_t)(wa & 0xFFFFu);
             tot[r][e][1] += (int32_t)(wa >> 16);
@@ -337,20 +341,24 @@ __device__ __forceinline__ bool ws_item(const WsBeam &a, int g, int64_t T0,
           int32_t *o = a.out + (int64_t)(row < 0 ? 0 : row) * a.out_pitch;
 #pragma unroll
           for (int e = 0; e < E; ++e) {
-            const uint32_t Ev = accE[r][e], O = accO[r][e];
-            const uint32_t s2 = Ev >> 16;
-            const uint32_t rem = O - (s2 << 8);
+            const uint32_t Bv = accB[r][e];
+            const uint32_t Ev = accA[r][e] - (Bv << 8);  // b0 + 2^16 b2 sums
             const int32_t part[4] = {(int32_t)(Ev & 0xFFFFu),
-                                     (int32_t)(rem & 0xFFFFu), (int32_t)s2,
-                                     (int32_t)(rem >> 16)};
+                                     (int32_t)(Bv & 0xFFFFu),
+                                     (int32_t)(Ev >> 16), (int32_t)(Bv >> 16)};
 #pragma unroll
             for (int m = 0; m < 4; ++m) {
               const int64_t t = T0 + i0 + 32 * e + (int64_t)m * S;
-              if (row >= 0 && t < nsamp_out)
-                o[t] = first_flush ? part[m] : o[t] + part[m];
+              // the first flush of the item stores; later ones are
+              // fire-and-forget reductions (no load for the warp to wait on;
+              // integer adds in any order give the same total)
+              if (row >= 0 && t < nsamp_out) {
+                if (first_flush) o[t] = part[m];
+                else atomicAdd(o + t, part[m]);
+              }
             }
-            accE[r][e] = 0;
-            accO[r][e] = 0;
+            accA[r][e] = 0;
+            accB[r][e] = 0;
           }
         }
         first_flush = false;

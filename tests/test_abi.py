@@ -132,3 +132,15 @@ def test_generator_numpy_torch_agree():
     b = synth.noise_u8_np(513, 48, 9)
     assert np.array_equal(a, b)
     assert abs(a.mean() - 128) < 0.5 and abs(a.std() - 16) < 0.5
+
+
+def test_every_source_file_is_a_build_dependency():
+    """A change to any file under csrc/ (kernels, headers, device headers)
+    must rebuild the library."""
+    import glob
+    import os
+    from paper_2605_03531_b300 import build as b
+    files = {os.path.abspath(f) for f in glob.glob(os.path.join(b.CSRC, "*"))
+             if os.path.isfile(f)}
+    deps = {os.path.abspath(d) for d in b._deps()}
+    assert files and files <= deps, sorted(files - deps)
