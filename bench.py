@@ -229,12 +229,14 @@ def traffic_record(kernel):
         rec = json.load(open(path))[kernel]
     except (OSError, KeyError, ValueError):
         return None
-    src = os.path.join(ROOT, "paper_2605_03531_b300", "csrc", rec["source"])
+    h = hashlib.sha256()
     try:
-        h = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    except OSError:
+        for name in rec["sources"]:
+            h.update(open(os.path.join(ROOT, "paper_2605_03531_b300", "csrc",
+                                       name), "rb").read())
+    except (OSError, KeyError):
         return None
-    if h != rec.get("source_sha256"):
+    if h.hexdigest() != rec.get("sources_sha256"):
         return None
     return rec.get("dram_bytes_per_launch")
 
@@ -603,8 +605,8 @@ def run_serve(args):
     reserve = 4 << 30
 
     # tile: the fastest full step of 32 beams among the server's shapes
-    tiles = [(16, 8, 8, 2), (8, 8, 4, 3), (16, 8, 4, 3), (8, 8, 6, 3),
-             (8, 4, 4, 3), (16, 4, 6, 3), (8, 4, 8, 2)]
+    tiles = [(16, 8, 8, 2), (8, 8, 4, 2), (16, 8, 4, 2), (8, 8, 6, 2),
+             (16, 8, 4, 4), (8, 4, 4, 2), (16, 4, 6, 2), (8, 4, 8, 2)]
     tune = {}
     for t in tiles:
         try:

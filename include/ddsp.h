@@ -428,7 +428,8 @@ const char *ddsp_last_error_detail(void);
  * registers and accept 0 or DDSP_TILE_SINGLE_ELEM_BUFFER), or
  * DDSP_TILE_WARP_SPECIALIZED alone (producer warps stage and relayout,
  * consumer warps accumulate, no block-wide barrier in the main loop;
- * dm_per_thread 4, or 8 for uint8).  Every variant computes the same exact
+ * dm_per_thread 4, or 8 for uint8; stages 2 or 4, since each of the two
+ * producer warps owns every other chunk and half the stages).  Every variant computes the same exact
  * sums.  dm_tile = 0 restores the library's choice, dm_tile = -1
  * selects the direct (unstaged) kernel.  DDSP_E_INVALID_ARG for a shape the
  * kernel does not implement or whose staging does not fit on chip.

@@ -208,11 +208,11 @@ int batch_apply_tile(ddsp_batch &B, const DedispTile &t) {
 // Candidate tiles; chan_chunk is the per-beam upper limit.
 const DedispTile kBatchTiles[] = {
     // {wt, wd, rd, chan_chunk, nbuf, flags}
-    {4, 2, 8, 8, 3, kTileWarpSpecialized}, {4, 2, 8, 6, 3, kTileWarpSpecialized},
-    {4, 2, 8, 4, 3, kTileWarpSpecialized}, {4, 2, 8, 8, 2, kTileWarpSpecialized},
-    {8, 1, 8, 6, 3, kTileWarpSpecialized}, {8, 1, 8, 4, 3, kTileWarpSpecialized},
-    {2, 4, 8, 8, 3, kTileWarpSpecialized}, {4, 2, 4, 8, 3, kTileWarpSpecialized},
-    {8, 1, 4, 6, 3, kTileWarpSpecialized}, {8, 1, 4, 4, 2, kTileWarpSpecialized}};
+    {4, 2, 8, 8, 2, kTileWarpSpecialized}, {4, 2, 8, 6, 2, kTileWarpSpecialized},
+    {4, 2, 8, 4, 2, kTileWarpSpecialized}, {4, 2, 8, 4, 4, kTileWarpSpecialized},
+    {8, 1, 8, 6, 2, kTileWarpSpecialized}, {8, 1, 8, 4, 2, kTileWarpSpecialized},
+    {2, 4, 8, 8, 2, kTileWarpSpecialized}, {4, 2, 4, 8, 2, kTileWarpSpecialized},
+    {8, 1, 4, 6, 2, kTileWarpSpecialized}, {8, 1, 4, 4, 4, kTileWarpSpecialized}};
 constexpr int kNumBatchTiles = sizeof(kBatchTiles) / sizeof(kBatchTiles[0]);
 constexpr size_t kAutotuneStride = 16;
 

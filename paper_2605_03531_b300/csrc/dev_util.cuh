@@ -58,21 +58,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity,
   }
 }
 
-// Barrier over the `nthreads` threads that use named barrier `id`, returning
-// the OR of `flag` over them (every participant sees the same result).
-__device__ __forceinline__ bool named_bar_or(int id, int nthreads, bool flag) {
-  uint32_t r;
-  asm volatile(
-      "{\n\t.reg .pred p, q;\n\t"
-      "setp.ne.u32 p, %1, 0;\n\t"
-      "bar.red.or.pred q, %2, %3, p;\n\t"
-      "selp.u32 %0, 1, 0, q;\n\t}"
-      : "=r"(r)
-      : "r"((uint32_t)flag), "r"(id), "r"(nthreads)
-      : "memory");
-  return r != 0;
-}
-
 // 4 raw words holding samples i..i+3 at stride S (rows m = 0..3) into the
 // 4 interleaved elements i..i+3, element i = {x[i], x[i+S], x[i+2S],
 // x[i+3S]} (byte m = row m): a 4x4 byte transpose.

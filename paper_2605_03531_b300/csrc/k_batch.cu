@@ -30,7 +30,7 @@ dedisp_persistent_kernel(const WsBeam *__restrict__ beams,
   constexpr int TT = 4 * 32 * kElemPerThread * WT;
   extern __shared__ __align__(16) unsigned char smem[];
   int *s_item = reinterpret_cast<int *>(smem + 64);
-  if (threadIdx.x == 0) ws_init_barriers(smem, nbuf, WT * WD, kWsProdWarps);
+  if (threadIdx.x == 0) ws_init_barriers(smem, nbuf, WT * WD);
   int jbase = 0;
   while (true) {
     if (threadIdx.x == 0) *s_item = atomicAdd(queue, 1);

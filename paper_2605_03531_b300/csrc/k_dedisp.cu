@@ -515,7 +515,8 @@ bool dedisp_tile_supported(const DedispTile &t, int nbits) {
     if (t.rd != 4 && !(t.rd == 8 && nbits == 8)) return false;
     if (t.wd != 1 && t.wd != 2 && t.wd != 4) return false;
     if (t.chan_chunk < 1 || t.chan_chunk > 32) return false;
-    return t.nbuf >= 2 && t.nbuf <= 4;
+    // each producer warp owns every other chunk and its own raw stages
+    return t.nbuf == 2 || t.nbuf == 4;
   }
   if (f & ~(kTileSingleElemBuffer | kTileRegisterTotals)) return false;
   if (nbits == 8 && (f & kTileRegisterTotals) && !(f & kTileSingleElemBuffer))

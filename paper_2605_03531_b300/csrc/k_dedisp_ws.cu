@@ -14,7 +14,7 @@ dedisp_ws_kernel(WsBeam a, int nbuf, int32_t *err, long long timeout_cycles) {
   constexpr int SPE = 4 / sizeof(T);
   constexpr int TT = SPE * 32 * kElemPerThread * WT;
   extern __shared__ __align__(16) unsigned char smem[];
-  if (threadIdx.x == 0) ws_init_barriers(smem, nbuf, WT * WD, kWsProdWarps);
+  if (threadIdx.x == 0) ws_init_barriers(smem, nbuf, WT * WD);
   __syncthreads();
   ws_item<WT, WD, RD, T>(a, blockIdx.x, (int64_t)blockIdx.y * TT, 0, smem,
                          nbuf, err, timeout_cycles);

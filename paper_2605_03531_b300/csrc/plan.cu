@@ -133,11 +133,12 @@ int build_tables(Plan &p) { return build_tables_for(p, p.tile, p.tab); }
 // the direct kernel.
 DedispTile choose_tile(const Plan &p) {
   // {wt, wd, rd, cc, flags}: the warp-specialised kernel first (fastest on
-  // the 4096-channel 1024-DM block), then the block-synchronous kernel with
-  // totals in registers, then smaller staging footprints
+  // the 4096-channel 1024-DM block; cc is an upper limit, the largest chunk
+  // that fits is taken), then the block-synchronous kernel with totals in
+  // registers, then smaller staging footprints
   struct Cand { int wt, wd, rd, cc, flags; };
   const Cand prefs[] = {
-      {4, 2, 8, 4, kTileWarpSpecialized}, {8, 1, 8, 4, kTileWarpSpecialized},
+      {4, 2, 8, 8, kTileWarpSpecialized}, {8, 1, 8, 8, kTileWarpSpecialized},
       {4, 2, 4, 8, kTileSingleElemBuffer | kTileRegisterTotals},
       {4, 2, 4, 6, kTileSingleElemBuffer}, {8, 1, 4, 4, kTileSingleElemBuffer},
       {8, 1, 4, 2, kTileSingleElemBuffer}, {8, 1, 2, 2, kTileSingleElemBuffer},
@@ -152,6 +153,14 @@ DedispTile choose_tile(const Plan &p) {
       t.flags = c.flags;
       if (!dedisp_tile_supported(t, p.nbits)) continue;
       const int span = span_for(p, t.dm_tile());
+      if (c.flags & kTileWarpSpecialized) {
+        t.nbuf = 2;
+        for (int cc = c.cc; cc >= 2; --cc) {
+          t.chan_chunk = cc;
+          if (dedisp_smem_bytes(t, span, p.nbits) <= budget) return t;
+        }
+        continue;
+      }
       for (int nbuf : {3, 2}) {
         t.nbuf = nbuf;
         if (dedisp_smem_bytes(t, span, p.nbits) <= budget) return t;

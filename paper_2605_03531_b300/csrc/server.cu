@@ -126,8 +126,8 @@ cudaEvent_t step_event(const ddsp_server &S, int64_t id) {
 // Candidates tiles tried in order when the caller leaves the choice to the
 // server: the first whose windows fit two blocks per SM for this shape.
 const DedispTile kServerTiles[] = {
-    {4, 2, 8, 8, 2, kTileWarpSpecialized}, {8, 1, 8, 4, 3, kTileWarpSpecialized},
-    {4, 2, 8, 4, 3, kTileWarpSpecialized}, {8, 1, 4, 4, 3, kTileWarpSpecialized},
+    {4, 2, 8, 8, 2, kTileWarpSpecialized}, {8, 1, 8, 4, 2, kTileWarpSpecialized},
+    {4, 2, 8, 4, 2, kTileWarpSpecialized}, {8, 1, 4, 4, 2, kTileWarpSpecialized},
     {4, 2, 4, 4, 2, kTileWarpSpecialized}, {8, 1, 4, 2, 2, kTileWarpSpecialized},
     {8, 1, 4, 1, 2, kTileWarpSpecialized}};
 

@@ -4,12 +4,14 @@
 // (k_dedisp_ws.cu, one item per block) and by the persistent multi-beam
 // kernel (k_batch.cu, items taken from a device work queue).
 //
-//   * producer warps (kWsProdWarps): one lane per channel issues 1-D TMA
-//     bulk copies of a chunk's raw windows into one of `nbuf` raw stages
-//     (transaction mbarrier), then the producers relayout the chunk into one
-//     of two element buffers -- element i = {x[i], x[i+S], x[i+2S], x[i+3S]}
-//     so a 32-bit shared load at any delay yields four output times -- and
-//     copy its delay offsets beside it;
+//   * producer warps (kWsProdWarps): warp w owns the chunks G with
+//     G % kWsProdWarps == w; one lane per channel issues 1-D TMA bulk copies
+//     of the chunk's raw windows into one of the warp's own raw stages
+//     (`nbuf`, a multiple of kWsProdWarps; transaction mbarrier), then the
+//     warp relayouts the chunk into element buffer G & 1 -- element i =
+//     {x[i], x[i+S], x[i+2S], x[i+3S]} so a 32-bit shared load at any delay
+//     yields four output times -- and copies its delay offsets beside it;
+//     the producer warps never wait for each other;
 //   * consumer warps (WT x WD): SWAR accumulation of two channels per step,
 //     A += wa + wb (whole words, mod 2^32) and B += p(wa) + p(wb) with p(w) =
 //     {b1, 0, b3, 0} (one byte permute against zero), releasing each element
@@ -83,13 +85,13 @@ struct WsBeam {
 };
 
 __device__ __forceinline__ void ws_init_barriers(unsigned char *smem,
-                                                 int nbuf, int nc, int np) {
+                                                 int nbuf, int nc) {
   uint64_t *raw_full = reinterpret_cast<uint64_t *>(smem);
   uint64_t *elem_full = raw_full + 4;
   uint64_t *elem_empty = raw_full + 6;
   for (int b = 0; b < nbuf; ++b) mbar_init(&raw_full[b], 1);
   for (int b = 0; b < 2; ++b) {
-    mbar_init(&elem_full[b], np);
+    mbar_init(&elem_full[b], 1);   // the one producer warp of the chunk
     mbar_init(&elem_empty[b], nc);
   }
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -133,8 +135,12 @@ __device__ __forceinline__ bool ws_item(const WsBeam &a, int g, int64_t T0,
 
   if (warp >= NC) {
     // ============================ producers ============================
+    // Producer warp pw owns the chunks G = jbase + j with G % NP == pw: it
+    // waits for their windows, relayouts all their channels into element
+    // buffer G & 1 and issues their refills, so the producer warps never
+    // wait for each other.  nbuf is a multiple of NP: a warp's raw stages
+    // are its own.
     const int pw = warp - NC;
-    const bool issuer = pw == 0;
     int2 nd = make_int2(0, 0);  // next copy descriptor of this lane's channel
     auto load_desc = [&](int j) {
       const int c = j * cc + lane;
@@ -163,18 +169,20 @@ __device__ __forceinline__ bool ws_item(const WsBeam &a, int g, int64_t T0,
         bulk_g2s(raw_rel + st * L.rel_stride, rel_g + (int64_t)c0 * DT,
                  relbytes, &raw_full[st]);
     };
+    const int j0 = ((pw - jbase) % NP + NP) % NP;   // first own chunk
     int last_issued = -1;
-    if (issuer) {
-      for (int j = 0; j < nbuf && j < nchunks; ++j) {
-        load_desc(j);
-        issue(j);
-        last_issued = j;
+    int jn = j0;
+    for (; jn < nbuf; jn += NP) {
+      if (jn < nchunks) {
+        load_desc(jn);
+        issue(jn);
+        last_issued = jn;
       }
-      load_desc(nbuf);
     }
-    int j = 0;
+    load_desc(jn);
+    int j = j0;
     bool failed = false;
-    for (; j < nchunks; ++j) {
+    for (; j < nchunks; j += NP) {
       const int G = jbase + j;
       const int st = G % nbuf, b = G & 1;
       const int ncur = min(cc, nchan - j * cc);
@@ -182,58 +190,54 @@ __device__ __forceinline__ bool ws_item(const WsBeam &a, int g, int64_t T0,
                           timeout_cycles);
       ok = ok && mbar_wait(&elem_empty[b], (uint32_t)(((G >> 1) & 1) ^ 1),
                            timeout_cycles);
-      if (ok) {
-        const int32_t *rs =
-            reinterpret_cast<const int32_t *>(raw_rel + st * L.rel_stride);
-        int32_t *er = erel + b * rel_words;
-        for (int i = pw * 32 + lane; i < ncur * DT; i += NP * 32) er[i] = rs[i];
-        const unsigned char *rb = raw + st * cc * rawmax;
-        uint32_t *eb = reinterpret_cast<uint32_t *>(elem + b * L.elem_stride);
-        for (int q = pw; q < ncur; q += NP) {
-          const unsigned char *rq = rb + q * rawmax;
-          uint32_t *eq = eb + q * elmax;
-          const int span = rs[q * DT + DT - 1] >> 2;
-          if constexpr (SPE == 4) {
-            const int nq = (S + span + 3) >> 2;
-            for (int i4 = lane; i4 < nq; i4 += 32) {
-              const unsigned char *p = rq + 4 * i4;
-              *reinterpret_cast<uint4 *>(eq + 4 * i4) = transpose4x4(
-                  *reinterpret_cast<const uint32_t *>(p),
-                  *reinterpret_cast<const uint32_t *>(p + S),
-                  *reinterpret_cast<const uint32_t *>(p + 2 * S),
-                  *reinterpret_cast<const uint32_t *>(p + 3 * S));
-            }
-          } else {
-            const int nq = (S + span + 1) >> 1;
-            for (int i2 = lane; i2 < nq; i2 += 32) {
-              const unsigned char *p = rq + 4 * i2;
-              const uint32_t w0 = *reinterpret_cast<const uint32_t *>(p);
-              const uint32_t w1 = *reinterpret_cast<const uint32_t *>(p + 2 * S);
-              uint2 o;
-              o.x = __byte_perm(w0, w1, 0x5410);
-              o.y = __byte_perm(w0, w1, 0x7632);
-              *reinterpret_cast<uint2 *>(eq + 2 * i2) = o;
-            }
+      if (!ok) {
+        failed = true;
+        break;
+      }
+      const int32_t *rs =
+          reinterpret_cast<const int32_t *>(raw_rel + st * L.rel_stride);
+      int32_t *er = erel + b * rel_words;
+      for (int i = lane; i < ncur * DT; i += 32) er[i] = rs[i];
+      const unsigned char *rb = raw + st * cc * rawmax;
+      uint32_t *eb = reinterpret_cast<uint32_t *>(elem + b * L.elem_stride);
+      for (int q = 0; q < ncur; ++q) {
+        const unsigned char *rq = rb + q * rawmax;
+        uint32_t *eq = eb + q * elmax;
+        const int span = rs[q * DT + DT - 1] >> 2;
+        if constexpr (SPE == 4) {
+          const int nq = (S + span + 3) >> 2;
+          for (int i4 = lane; i4 < nq; i4 += 32) {
+            const unsigned char *p = rq + 4 * i4;
+            *reinterpret_cast<uint4 *>(eq + 4 * i4) = transpose4x4(
+                *reinterpret_cast<const uint32_t *>(p),
+                *reinterpret_cast<const uint32_t *>(p + S),
+                *reinterpret_cast<const uint32_t *>(p + 2 * S),
+                *reinterpret_cast<const uint32_t *>(p + 3 * S));
+          }
+        } else {
+          const int nq = (S + span + 1) >> 1;
+          for (int i2 = lane; i2 < nq; i2 += 32) {
+            const unsigned char *p = rq + 4 * i2;
+            const uint32_t w0 = *reinterpret_cast<const uint32_t *>(p);
+            const uint32_t w1 = *reinterpret_cast<const uint32_t *>(p + 2 * S);
+            uint2 o;
+            o.x = __byte_perm(w0, w1, 0x5410);
+            o.y = __byte_perm(w0, w1, 0x7632);
+            *reinterpret_cast<uint2 *>(eq + 2 * i2) = o;
           }
         }
       }
       __syncwarp();
-      // all producers are past raw stage st (it can be refilled) and agree
-      // on whether to give up
-      if (named_bar_or(1, NP * 32, !ok)) {
-        failed = true;
-        break;
-      }
       if (lane == 0) mbar_arrive(&elem_full[b]);
-      if (issuer && j + nbuf < nchunks) {
+      if (j + nbuf < nchunks) {
         issue(j + nbuf);
         last_issued = j + nbuf;
-        load_desc(j + nbuf + 1);
+        load_desc(j + nbuf + NP);
       }
     }
-    if (failed && issuer && lane == 0) {
+    if (failed && lane == 0) {
       atomicExch(err, kErrTimeout);
-      for (int jj = j; jj <= last_issued; ++jj) {
+      for (int jj = j; jj <= last_issued; jj += NP) {
         const int G = jbase + jj;
         mbar_wait(&raw_full[G % nbuf], (uint32_t)((G / nbuf) & 1),
                   timeout_cycles);

@@ -155,7 +155,7 @@ def test_batch_per_beam_chunks():
     for b, x in enumerate(blocks):
         batch.ingest(b, x)
     for cap in (8, 3, 1):
-        batch.set_tile(16, 8, cap, 3)
+        batch.set_tile(16, 8, cap, 2)
         chunks = [batch.beam_chunk(b) for b in range(len(cfgs))]
         # spans per 16-trial tile: ~8500 samples (coarse), ~440 (fine)
         assert chunks[0] == 1 and all(1 <= c <= cap for c in chunks)

@@ -9,7 +9,8 @@ import pytest
 import torch
 
 import oracle
-from paper_2605_03531_b300 import Plan, build, synth
+from paper_2605_03531_b300 import DdspError, Plan, build, synth
+from paper_2605_03531_b300 import _lib as ddsp_lib
 
 pytestmark = pytest.mark.gpu
 
@@ -21,8 +22,8 @@ TILES = [(0, 4, 8, 2, 0), (4, 4, 1, 2, 0), (4, 4, 8, 3, 1), (8, 4, 8, 2, 0),
          (8, 4, 8, 3, 5), (16, 4, 5, 2, 5), (4, 2, 8, 2, 5), (8, 4, 7, 2, 0),
          (2, 2, 8, 2, 0), (4, 2, 5, 3, 0), (8, 2, 8, 2, 1), (8, 2, 3, 4, 1),
          # flags 8 = warp-specialised producer/consumer kernel
-         (8, 4, 6, 3, 8), (16, 8, 4, 2, 8), (8, 8, 5, 3, 8), (32, 8, 3, 4, 8),
-         (4, 4, 8, 2, 8), (16, 4, 7, 2, 8),
+         (8, 4, 6, 4, 8), (16, 8, 4, 2, 8), (8, 8, 5, 2, 8), (32, 8, 3, 4, 8),
+         (4, 4, 8, 2, 8), (16, 4, 7, 2, 8), (16, 8, 5, 2, 8),
          (-1, 4, 8, 2, 0)]
 
 
@@ -119,7 +120,7 @@ SHAPES = [
 @pytest.mark.parametrize("tile", [(0, 4, 8, 2, 0), (4, 4, 3, 2, 1),
                                   (8, 4, 8, 3, 0), (16, 4, 4, 2, 1),
                                   (8, 4, 7, 3, 5), (8, 2, 7, 3, 0),
-                                  (8, 2, 5, 2, 1), (8, 4, 5, 3, 8),
+                                  (8, 2, 5, 2, 1), (8, 4, 5, 4, 8),
                                   (16, 8, 3, 2, 8), (-1, 4, 8, 2, 0)])
 def test_ragged_shapes_bit_exact(shape, tile):
     nchan, nin, dms, nbits, f_top, bw, ts = SHAPES[shape]
@@ -211,3 +212,14 @@ def test_injected_pulse_found_on_gpu(c1):
     best = cands[np.argmax(cands["snr"])]
     assert best["dm_idx"] == 100 and cfg.widths[best["w_idx"]] == 4
     assert abs(int(best["t"]) - 8000) <= 1
+
+
+def test_warp_specialised_tile_needs_even_stages():
+    """Each of the two producer warps owns every other chunk and half the
+    raw stages, so an odd stage count is refused."""
+    p = _plan(256, 750.0, -200.0 / 256, 1.31072e-3, np.arange(64.0))
+    with pytest.raises(DdspError) as e:
+        p.set_tile(16, 8, 4, 3, 8)
+    assert e.value.code == ddsp_lib.DDSP_E_INVALID_ARG
+    p.set_tile(16, 8, 4, 2, 8)
+    assert p.get_tile()["stages"] == 2
