@@ -570,7 +570,7 @@ def run_serve(args):
     (67 MB, one per 1.342 s per beam) with seeded Poisson-jittered arrivals;
     the server ingests them into per-beam rings and searches every waiting
     block in continuous-batching steps.  Reported: the largest beam count
-    (multiple of 16 in 64..320) whose p99 block latency stays below the
+    (multiple of 16 in 64..448) whose p99 block latency stays below the
     1.342 s period, for batched steps and for one beam per step (the plain
     per-beam path), found by bisection on real-time runs of --steps blocks
     per beam.  Blocks come from a pool of pinned host blocks (noise plus
@@ -677,8 +677,8 @@ def run_serve(args):
     runs = {}
     clk = ClockSampler(local if world > 1 else 0)
     clk.start()
-    n_batched, _ = realtime_limit(lambda n: run_at(n, 0), 64, 320, 16, T)
-    n_plain, _ = realtime_limit(lambda n: run_at(n, 1), 64, 320, 16, T)
+    n_batched, _ = realtime_limit(lambda n: run_at(n, 0), 64, 448, 16, T)
+    n_plain, _ = realtime_limit(lambda n: run_at(n, 1), 64, 448, 16, T)
     clocks = clk.stop()
     if rank == 0:
         def table(per_step):
