@@ -39,6 +39,7 @@ struct SpsShared {
   int64_t bc[4];      // broadcast slots
   float inv[kMaxWidths];
   int32_t thr_by[kMaxWidths];
+  int32_t wid[kMaxWidths];
   uint32_t wsum[kWarps];
 };
 
@@ -269,6 +270,7 @@ __device__ __forceinline__ void sps_window(
     else if (tby <= -2.0e9f) tb = INT32_MIN;
     else tb = (int32_t)floorf(tby);
     sh.thr_by[tid] = tb;
+    sh.wid[tid] = widths[tid];
   }
 
   // ---- 3. y = x - floor(median); inclusive prefix sum Q[1..elen] in place
@@ -293,19 +295,35 @@ __device__ __forceinline__ void sps_window(
   const uint32_t *Q = reinterpret_cast<const uint32_t *>(buf);
 
   // ---- 4. boxcars, S/N, candidates
-  const int64_t nvalid_t = n - lo;  // t - lo + w <= n - lo
+  // The window's widths, integer thresholds and FP32 scales sit in
+  // registers; one unrolled pass loads every boxcar sum of a start time.
+  // Widths ascend, so those running past the series end (t - lo + w >
+  // n - lo) are a suffix of the list, as the reference loop's early exit.
+  int32_t wv[kMaxWidths], tbv[kMaxWidths];
+  float iv[kMaxWidths];
+#pragma unroll
+  for (int wi = 0; wi < kMaxWidths; ++wi) {
+    const bool use = wi < nw;
+    wv[wi] = use ? sh.wid[wi] : 0;
+    tbv[wi] = use ? sh.thr_by[wi] : INT32_MAX;
+    iv[wi] = use ? sh.inv[wi] : 0.0f;
+  }
+  // i + w <= n - lo also implies i + w <= elen, the last prefix index
+  const int nv = (int)min(n - lo, (int64_t)elen);
   for (int i0 = 0; i0 < len; i0 += kSpsThreads) {
     const int i = i0 + tid;
     const bool in = i < len;
+    int32_t by[kMaxWidths];
     bool pass = false;
-    if (in && !DENSE) {
+    if (in) {
       const uint32_t qi = Q[i];
-#pragma unroll 1
-      for (int wi = 0; wi < nw; ++wi) {
-        const int w = widths[wi];
-        if ((int64_t)i + w > nvalid_t) break;
-        int32_t by = (int32_t)(Q[i + w] - qi);
-        pass |= by >= sh.thr_by[wi];
+#pragma unroll
+      for (int wi = 0; wi < kMaxWidths; ++wi) {
+        by[wi] = 0;
+        if (wi < nw) {
+          by[wi] = (int32_t)(Q[min(i + wv[wi], nv)] - qi);
+          pass |= (i + wv[wi] <= nv) && by[wi] >= tbv[wi];
+        }
       }
     }
     if (DENSE || pass) {
@@ -313,17 +331,16 @@ __device__ __forceinline__ void sps_window(
       float bs = 0.0f;
       int32_t bsum = 0;
       if (in) {
-        const uint32_t qi = Q[i];
-        for (int wi = 0; wi < nw; ++wi) {
-          const int w = widths[wi];
-          if ((int64_t)i + w > nvalid_t) break;
-          int32_t by = (int32_t)(Q[i + w] - qi);
-          int64_t num = 2 * (int64_t)by - (int64_t)w * odd;
-          float s = (float)num * sh.inv[wi];
-          if (bw < 0 || s > bs) {
-            bw = wi;
-            bs = s;
-            bsum = by + w * mfloor;
+#pragma unroll
+        for (int wi = 0; wi < kMaxWidths; ++wi) {
+          if (wi < nw && i + wv[wi] <= nv) {
+            const int64_t num = 2 * (int64_t)by[wi] - (int64_t)wv[wi] * odd;
+            const float sn = (float)num * iv[wi];
+            if (bw < 0 || sn > bs) {
+              bw = wi;
+              bs = sn;
+              bsum = by[wi] + wv[wi] * mfloor;
+            }
           }
         }
       }
@@ -358,7 +375,7 @@ __device__ __forceinline__ void sps_window(
 }
 
 template <bool DENSE>
-__global__ void __launch_bounds__(kSpsThreads)
+__global__ void __launch_bounds__(kSpsThreads, 2)
 sps_kernel(const int32_t *__restrict__ series, int64_t n, int64_t L,
            int64_t nwin, const int32_t *__restrict__ widths, int nw, float thr,
            int64_t *__restrict__ m2_out, int64_t *__restrict__ mad4_out,
@@ -373,7 +390,7 @@ sps_kernel(const int32_t *__restrict__ series, int64_t n, int64_t L,
 
 // Many beams in one launch: flattened block b -> the beam whose block0 is
 // the largest <= b, then (DM trial, window) inside it.
-__global__ void __launch_bounds__(kSpsThreads)
+__global__ void __launch_bounds__(kSpsThreads, 2)
 sps_batch_kernel(const SpsBeam *__restrict__ beams, int nbeams, float thr) {
   const int64_t bid = blockIdx.x;
   int lo = 0, hi = nbeams - 1;
