@@ -115,33 +115,18 @@ class ClockSampler:
 
 # ---------------------------------------------------------- distributed
 def dist_setup(n_gpus):
-    import torch
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
-    elif torch.cuda.is_available():
-        torch.cuda.set_device(0)
-    return world, rank, local
+    from paper_2605_03531_b300 import shard
+    return shard.init()
 
 
 def barrier(world):
-    if world > 1:
-        import torch.distributed as dist
-        dist.barrier()
+    from paper_2605_03531_b300 import shard
+    shard.barrier(world)
 
 
 def max_over_ranks(v, world):
-    if world == 1:
-        return v
-    import torch
-    import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    return float(t.item())
+    from paper_2605_03531_b300 import shard
+    return shard.max_over_ranks(v, world)
 
 
 # ------------------------------------------------------------- oracle CPU
@@ -177,10 +162,10 @@ def cpu_cores():
 
 # ----------------------------------------------------------------- arms
 def run_reference(args):
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    if world > 1 and rank != 0:
-        return 0
+    from paper_2605_03531_b300 import shard
+    world, rank, _ = shard.world_from_env()
+    if not shard.runs_reference(world, rank):
+        return 0    # the CPU reference runs once, on rank 0
     cores = cpu_cores()
     os.environ["OMP_NUM_THREADS"] = str(cores)
     import oracle
@@ -243,13 +228,13 @@ def traffic_record(kernel):
 
 def run_ours(args):
     import torch
-    from paper_2605_03531_b300 import Plan, build, synth
+    from paper_2605_03531_b300 import Plan, build, shard, synth
     build.build()
     world, rank, local = dist_setup(args.gpus)
     dev = torch.device("cuda", local if world > 1 else 0)
     cfg = workload()
     if world > 1:
-        cfg.seed = cfg.seed + 1000 * rank   # each rank its own beam
+        cfg.seed = shard.rank_seed(cfg.seed, rank)   # each rank its own beam
     plan = Plan(cfg.nchan, cfg.f_top, cfg.chan_bw, cfg.tsamp, cfg.dm_list(),
                 cfg.widths, nbits=8, norm_window=cfg.norm_window,
                 cand_capacity=1 << 20)
@@ -441,14 +426,14 @@ def run_sps(args):
     the device.  HBM-bound: 4 bytes per series sample read once plus 16 bytes
     per candidate record written."""
     import torch
-    from paper_2605_03531_b300 import Plan, build, synth
+    from paper_2605_03531_b300 import Plan, build, shard, synth
     build.build()
     world, rank, local = dist_setup(args.gpus)
     dev = torch.device("cuda", local if world > 1 else 0)
     ndm, n = args.ndm or 2048, args.nsamp or (1 << 20)
     widths = [1 << i for i in range(11)]
     L, thr = 8192, 6.5
-    x = synth.gaussian_series(ndm, n, seed=4 + 1000 * rank, device=dev)
+    x = synth.gaussian_series(ndm, n, seed=shard.rank_seed(4, rank), device=dev)
     cap = min(1 << 30, ndm * n)
     plan = Plan(16, 500.0, -1.0, 1e-3, np.zeros(ndm), widths, nbits=8,
                 norm_window=L, cand_capacity=cap)
@@ -510,11 +495,11 @@ def run_batch(args):
     separate launches with the beam's own tile."""
     import ctypes as C
     import torch
-    from paper_2605_03531_b300 import Batch, Plan, _lib, build, synth
+    from paper_2605_03531_b300 import Batch, Plan, _lib, build, shard, synth
     build.build()
     world, rank, local = dist_setup(args.gpus)
     dev = torch.device("cuda", local if world > 1 else 0)
-    cfgs = synth.config3(nbeams=args.nbeams or 160, seed=3 + 1000 * rank)
+    cfgs = synth.config3(nbeams=args.nbeams or 160, seed=shard.rank_seed(3, rank))
     plans = [Plan(c.nchan, c.f_top, c.chan_bw, c.tsamp, c.dm_list(), c.widths,
                   nbits=8, norm_window=c.norm_window, cand_capacity=1 << 16)
              for c in cfgs]
