@@ -172,8 +172,10 @@ int batch_apply_tile(ddsp_batch &B, const DedispTile &t) {
     w.cc = lay[b].cc;
     w.rawmax = lay[b].rawmax;
     w.elmax = lay[b].elmax;
-    for (int g = 0; g < w.n_dm_tiles; ++g)
-      for (int tt = 0; tt < w.n_time_tiles; ++tt)
+    // DM tiles innermost: consecutive items stage overlapping windows of
+    // one time tile, which L2 then serves
+    for (int tt = 0; tt < w.n_time_tiles; ++tt)
+      for (int g = 0; g < w.n_dm_tiles; ++g)
         items.push_back(make_int4(b, g, tt, p.nchan));
   }
   // the costliest items (most channels) first, so the tail is short

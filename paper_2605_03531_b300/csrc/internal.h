@@ -151,7 +151,7 @@ cudaError_t launch_serve_prep(const SpsBeam *d_beams, int nbeams, int ndm,
 cudaError_t launch_dedisperse_persistent(const DedispTile &t,
                                          const WsBeam *d_beams,
                                          const int4 *d_items, int nitems,
-                                         int ipb, int ntt, int *d_queue,
+                                         int ipb, int ndt, int *d_queue,
                                          size_t smem,
                                          int32_t *d_err, int grid,
                                          cudaStream_t s);

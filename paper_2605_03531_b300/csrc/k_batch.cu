@@ -13,7 +13,9 @@
 // count; each beam has its own channel chunk and buffer extents, and the
 // dynamic shared memory is the largest layout over the beams.  When every
 // beam has the same shape the host passes no item list: item i is beam
-// i / ipb, DM tile (i % ipb) / ntt, time tile (i % ipb) % ntt.
+// i / ipb, DM tile (i % ipb) % ndt, time tile (i % ipb) / ndt (DM tiles
+// innermost: concurrent blocks stage overlapping windows of one time tile,
+// which L2 then serves).
 #include <algorithm>
 
 #include "ws_item.cuh"
@@ -25,7 +27,7 @@ template <int WT, int WD, int RD>
 __global__ void __launch_bounds__(32 * (WT * WD + kWsProdWarps), 2)
 dedisp_persistent_kernel(const WsBeam *__restrict__ beams,
                          const int4 *__restrict__ items, int nitems,
-                         int ipb, int ntt, int *queue, int nbuf, int32_t *err,
+                         int ipb, int ndt, int *queue, int nbuf, int32_t *err,
                          long long timeout_cycles) {
   constexpr int TT = 4 * 32 * kElemPerThread * WT;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -42,7 +44,7 @@ dedisp_persistent_kernel(const WsBeam *__restrict__ beams,
       w = items[it];
     } else {
       const int r = it % ipb;
-      w = make_int4(it / ipb, r / ntt, r % ntt, 0);
+      w = make_int4(it / ipb, r % ndt, r / ndt, 0);
     }
     const WsBeam a = beams[w.x];
     const bool ok = ws_item<WT, WD, RD, uint8_t>(
@@ -87,7 +89,7 @@ __global__ void serve_prep_kernel(const SpsBeam *__restrict__ beams,
 
 template <int WT, int WD, int RD>
 cudaError_t launch_persistent_t(const WsBeam *d_beams, const int4 *d_items,
-                                int nitems, int ipb, int ntt, int *d_queue,
+                                int nitems, int ipb, int ndt, int *d_queue,
                                 int nbuf,
                                 size_t smem, int32_t *d_err, int grid,
                                 cudaStream_t s) {
@@ -101,7 +103,7 @@ cudaError_t launch_persistent_t(const WsBeam *d_beams, const int4 *d_items,
   }
   const long long timeout = 4000000000LL;  // ~2 s of SM clock
   kern<<<grid, 32 * (WT * WD + kWsProdWarps), smem, s>>>(
-      d_beams, d_items, nitems, ipb, ntt, d_queue, nbuf, d_err, timeout);
+      d_beams, d_items, nitems, ipb, ndt, d_queue, nbuf, d_err, timeout);
   return cudaGetLastError();
 }
 
@@ -148,14 +150,14 @@ cudaError_t launch_batch_reset(int *d_queue, uint32_t *const *d_counts,
 cudaError_t launch_dedisperse_persistent(const DedispTile &t,
                                          const WsBeam *d_beams,
                                          const int4 *d_items, int nitems,
-                                         int ipb, int ntt, int *d_queue,
+                                         int ipb, int ndt, int *d_queue,
                                          size_t smem,
                                          int32_t *d_err, int grid,
                                          cudaStream_t s) {
 #define DDSP_P(WT_, WD_, RD_)                                                 \
   if (t.wt == WT_ && t.wd == WD_ && t.rd == RD_)                              \
     return launch_persistent_t<WT_, WD_, RD_>(d_beams, d_items, nitems, ipb,  \
-                                              ntt, d_queue, t.nbuf, smem,     \
+                                              ndt, d_queue, t.nbuf, smem,     \
                                               d_err, grid, s);
   DDSP_P(4, 2, 4) DDSP_P(2, 4, 4) DDSP_P(8, 1, 4)
   DDSP_P(4, 2, 8) DDSP_P(2, 4, 8) DDSP_P(8, 1, 8)

@@ -461,7 +461,7 @@ int ddsp_server_step(ddsp_server *S, float threshold, int max_beams_in_step,
   if (e == cudaSuccess && nitems > 0x7fffffff) e = cudaErrorInvalidValue;
   if (e == cudaSuccess)
     e = launch_dedisperse_persistent(
-        S->tile, S->d_wsb[par], nullptr, (int)nitems, S->ipb, S->ntt,
+        S->tile, S->d_wsb[par], nullptr, (int)nitems, S->ipb, S->tab.n_dm_tiles,
         S->d_queue, S->smem, S->d_err, (int)std::min<int64_t>(S->grid, nitems), s);
   if (e == cudaSuccess)
     e = launch_sps_batch(S->d_sb[par], n, (int64_t)n * p.ndm * S->nwin,
