@@ -83,13 +83,6 @@ struct Plan {
 };
 
 // ---- multi-beam descriptors (device arrays built by the batch) ---------
-struct UnpackBeam {          // one beam of the batched unpack
-  const uint8_t *in;         // time-major [nsamp_in][nchan]
-  uint8_t *out;              // channel-major [nchan][pitch]
-  int64_t nsamp_in, pitch, block0;
-  int nchan, pad;
-};
-
 struct SpsBeam {             // one beam of the batched search
   const int32_t *series;     // [ndm][n]
   const int32_t *widths;
@@ -155,9 +148,6 @@ cudaError_t launch_dedisperse_persistent(const DedispTile &t,
                                          size_t smem,
                                          int32_t *d_err, int grid,
                                          cudaStream_t s);
-int64_t unpack_batch_blocks(int64_t pitch, int nchan);
-cudaError_t launch_unpack_batch(const UnpackBeam *d_beams, int nbeams,
-                                int64_t total_blocks, cudaStream_t s);
 size_t sps_smem_bytes(int64_t maxlen, int wmax);
 cudaError_t launch_sps_batch(const SpsBeam *d_beams, int nbeams,
                              int64_t total_blocks, float threshold,

@@ -68,23 +68,6 @@ unpack_u8_kernel(const uint8_t *__restrict__ in, int64_t nsamp_in, int nchan,
                  blockIdx.y);
 }
 
-// Many beams in one launch: block b of the flattened grid belongs to the beam
-// whose first block is the largest beams[i].block0 <= b.
-__global__ void __launch_bounds__(256)
-unpack_u8_batch_kernel(const UnpackBeam *__restrict__ beams, int nbeams) {
-  const int64_t bid = blockIdx.x;
-  int lo = 0, hi = nbeams - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (beams[mid].block0 <= bid) lo = mid; else hi = mid - 1;
-  }
-  const UnpackBeam &b = beams[lo];
-  const int64_t local = bid - b.block0;
-  const int64_t tiles_s = b.pitch / kTS;
-  unpack_u8_tile(b.in, b.nsamp_in, b.nchan, b.out, b.pitch, b.pitch,
-                 local % tiles_s, (int)(local / tiles_s));
-}
-
 // Generic element-wise transpose (uint8 with nchan % 16 != 0, and uint16):
 // 32 x 32 elements per block through a skewed shared tile.
 template <typename T>
@@ -113,17 +96,6 @@ unpack_generic_kernel(const T *__restrict__ in, int64_t nsamp_in, int nchan,
 }
 
 }  // namespace
-
-int64_t unpack_batch_blocks(int64_t pitch, int nchan) {
-  return (pitch / kTS) * ((nchan + kTC - 1) / kTC);
-}
-
-cudaError_t launch_unpack_batch(const UnpackBeam *d_beams, int nbeams,
-                                int64_t total_blocks, cudaStream_t s) {
-  unpack_u8_batch_kernel<<<(unsigned)total_blocks, 256, 0, s>>>(d_beams,
-                                                                nbeams);
-  return cudaGetLastError();
-}
 
 cudaError_t launch_unpack_cols(const void *d_in, int64_t nsamp_in, int nchan,
                                int nbits, void *d_out, int64_t pitch,
