@@ -52,6 +52,20 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane) {
   return v;
 }
 
+// float(2*by - c), rounded to nearest, for any int32 by and 0 <= c < 2^16,
+// without a 64-bit integer conversion: 2*by - c = hi*2^17 + lo with
+// hi = by >> 16 and lo = 2*(by & 0xffff) - c; both parts (|.| < 2^22) are
+// converted exactly by the 1.5*2^23 magic-number trick and one fused
+// multiply-add rounds their exact sum once.
+__device__ __forceinline__ float twice_minus(int32_t by, int32_t c) {
+  const int32_t hi = by >> 16;
+  const int32_t lo = 2 * (by & 0xffff) - c;
+  const float magic = 12582912.0f;  // 1.5 * 2^23, bit pattern 0x4B400000
+  const float hf = __int_as_float(0x4B400000 + hi) - magic;
+  const float lf = __int_as_float(0x4B400000 + lo) - magic;
+  return __fmaf_rn(hf, 131072.0f, lf);
+}
+
 // Block-wide min & max of a per-thread pair (int64).
 __device__ void block_minmax(int64_t &mn, int64_t &mx, SpsShared &sh) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -334,8 +348,7 @@ __device__ __forceinline__ void sps_window(
 #pragma unroll
         for (int wi = 0; wi < kMaxWidths; ++wi) {
           if (wi < nw && i + wv[wi] <= nv) {
-            const int64_t num = 2 * (int64_t)by[wi] - (int64_t)wv[wi] * odd;
-            const float sn = (float)num * iv[wi];
+            const float sn = twice_minus(by[wi], wv[wi] * odd) * iv[wi];
             if (bw < 0 || sn > bs) {
               bw = wi;
               bs = sn;

@@ -218,3 +218,33 @@ def test_stress_config_full_size_sampled_rows():
         _compare_candidates(mine, n_mine, ref, n_ref, thr, xk[None, :],
                             widths, L)
     assert 0.1 * ndm * n < n_total < 0.6 * ndm * n
+
+
+def test_dense_snr_bits_with_large_sums():
+    """The S/N numerator 2*B_y - w*odd is rounded to FP32 exactly once: with
+    boxcar sums between 2^24 and 2^30 (where the rounding matters) the dense
+    S/N equals, bit for bit, the FP32 product rebuilt from the reported sum
+    and the window's exact statistics with the same IEEE operations."""
+    rng = np.random.default_rng(7)
+    ndm, n, L = 3, 16384, 4096
+    widths = [1, 4, 16, 64, 256]
+    x = rng.integers(-3_000_000, 3_000_000, size=(ndm, n)).astype(np.int32)
+    p = Plan(16, 500.0, -1.0, 1e-3, np.zeros(ndm), widths, nbits=8,
+             norm_window=L, cand_capacity=1024)
+    bw, bs, bsum = (t.cpu().numpy() for t in p.search_dense(torch.from_numpy(x).cuda()))
+    m2, mad4 = p.stats()
+    big = 0
+    for k in range(ndm):
+        for t in range(0, n - 256, 29):
+            j = min(t // L, m2.shape[1] - 1)
+            wi = int(bw[k, t])
+            w, M2, MAD4 = widths[wi], int(m2[k, j]), int(mad4[k, j])
+            odd, mfloor = M2 & 1, M2 >> 1
+            by = (int(bsum[k, t]) - w * mfloor + 2**31) % 2**32 - 2**31
+            big += abs(by) > 2**24
+            num = 2 * by - w * odd
+            two_sigma = np.float32(1.482602218505602) * np.float32(MAD4) * np.float32(0.5)
+            inv = np.float32(1.0) / (two_sigma * np.sqrt(np.float32(w)))
+            ref = np.float32(num) * inv
+            assert np.float32(bs[k, t]).view(np.uint32) == ref.view(np.uint32), (k, t)
+    assert big > 100
