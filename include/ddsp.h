@@ -287,7 +287,7 @@ int ddsp_batch_run(ddsp_batch *batch, float threshold, int use_graph,
  * the last batch step (DDSP_E_TIMEOUT / DDSP_E_RANGE), then clear it. */
 int ddsp_batch_check(ddsp_batch *batch, ddsp_stream_t stream);
 
-/* The batch's warp-specialised tile (see ddsp_plan_set_tile) and the
+/* The batch's main warp-specialised tile (see ddsp_plan_set_tile) and its
  * persistent grid size.  All beams share dm_tile, dm_per_thread and stages;
  * chan_chunk (1..32) is an upper limit: each beam stages the largest chunk
  * up to it whose buffers (which grow with the beam's delay span inside a
@@ -303,6 +303,15 @@ int ddsp_batch_get_tile(const ddsp_batch *batch, int *dm_tile,
 /* The channel chunk beam `beam` stages under the current tile. */
 int ddsp_batch_get_beam_chunk(const ddsp_batch *batch, int beam,
                               int *chan_chunk);
+
+/* The shape beam `beam` is dedispersed with: beams whose DM grid is coarse
+ * for the main shape (fewer than 2 channels per chunk, or a narrower-DM
+ * shape relayouts at least 30 % fewer bytes per add) go to a second
+ * persistent launch of the same step with that narrower shape; *group is 0
+ * (main) or 1 (that launch).  Any pointer may be NULL. */
+int ddsp_batch_get_beam_tile(const ddsp_batch *batch, int beam, int *dm_tile,
+                             int *dm_per_thread, int *time_tile,
+                             int *chan_chunk, int *group);
 
 /* Autotuner: for each tile shape of the library's candidate list, time the
  * persistent dedispersion of every 16th work item of the cost-ordered work

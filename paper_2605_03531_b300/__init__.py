@@ -335,6 +335,16 @@ class Batch:
                    "ddsp_batch_get_beam_chunk")
         return v.value
 
+    def beam_tile(self, beam):
+        """dict(dm_tile, dm_per_thread, time_tile, chan_chunk, group) of the
+        shape beam `beam` is dedispersed with (group 1: the second
+        persistent launch for coarse DM grids)."""
+        v = [C.c_int() for _ in range(5)]
+        _lib.check(_lib.lib().ddsp_batch_get_beam_tile(
+            self._h, int(beam), *[C.byref(a) for a in v]), "ddsp_batch_get_beam_tile")
+        keys = ("dm_tile", "dm_per_thread", "time_tile", "chan_chunk", "group")
+        return dict(zip(keys, (a.value for a in v)))
+
     def autotune(self, reps=2, stream=None):
         """Time every candidate tile on a 1/16 sample of the work items,
         keep the fastest; returns (list of estimated full-launch ms per

@@ -64,6 +64,7 @@ SIGNATURES = {
     "ddsp_batch_set_tile": (I32, [P, I32, I32, I32, I32]),
     "ddsp_batch_get_tile": (I32, [P] + [C.POINTER(C.c_int)] * 6),
     "ddsp_batch_get_beam_chunk": (I32, [P, I32, C.POINTER(C.c_int)]),
+    "ddsp_batch_get_beam_tile": (I32, [P, I32] + [C.POINTER(C.c_int)] * 5),
     "ddsp_batch_autotune": (I32, [P, I32, P, C.POINTER(C.c_float), I32,
                                   C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "ddsp_server_create": (I32, [C.POINTER(P), P, I64, I32, I64, I32, I32,

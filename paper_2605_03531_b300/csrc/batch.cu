@@ -1,6 +1,8 @@
-// batch.cu -- many beams (plans) of uneven shape dedispersed by one
-// persistent launch and searched by one batched launch, optionally replayed
-// from a captured CUDA graph; tile autotuner.
+// batch.cu -- many beams (plans) of uneven shape dedispersed by persistent
+// launches (one per tile group: the main shape, and a narrower-DM shape for
+// beams whose delay spans make the main one stage little and relayout a lot)
+// and searched by one batched launch, optionally replayed from a captured
+// CUDA graph; tile autotuner.
 #include <math.h>
 
 #include <algorithm>
@@ -12,27 +14,41 @@
 
 using namespace ddsp;
 
+namespace {
+constexpr int kMaxGroups = 2;
+
+// Beams that share one persistent launch (one tile shape).
+struct BatchGroup {
+  DedispTile tile;                 // chan_chunk = the per-beam upper limit
+  std::vector<int> beams;          // batch beam indices
+  WsBeam *d_wsb = nullptr;         // [beams.size()]
+  int4 *d_items = nullptr;         // {group-local beam, DM tile, time tile, cost}
+  std::vector<int4> items;         // host copy of the work list
+  int nitems = 0, grid = 0;
+  size_t smem = 0;
+};
+}  // namespace
+
 struct ddsp_batch {
   int device = 0;
   int nbeams = 0;
   std::vector<ddsp_plan *> plans;
   std::vector<int64_t> nin, nout, pitch;
-  std::vector<DedispTables> tabs;  // per beam, for the common tile
-  DedispTile tile;                 // chan_chunk = the per-beam upper limit
+  std::vector<DedispTables> tabs;  // per beam, for its group's tile
+  DedispTile tile;                 // the main group's tile
   std::vector<int> cc;             // per-beam channel chunk
-  int grid = 0;
-  size_t smem = 0;
+  std::vector<int> group_of;       // per-beam group
+  std::vector<BatchGroup> groups;
+  // largest delay spread inside a DM tile of 2^k trials, per beam (-1: not
+  // computed yet)
+  mutable std::vector<std::vector<int>> span_cache;
   // device buffers
   std::vector<int32_t *> d_out;     // per-beam series (caller's or own_out)
   std::vector<int32_t *> own_out;   // the ones the batch allocated
   uint8_t *d_cm = nullptr;
   size_t cm_bytes = 0;
   std::vector<size_t> cm_off;
-  WsBeam *d_wsb = nullptr;
-  int4 *d_items = nullptr;
-  int nitems = 0;
-  std::vector<int4> items;         // host copy of the work list
-  int *d_queue = nullptr;
+  int *d_queue = nullptr;          // [kMaxGroups] work-queue counters
   SpsBeam *d_sb = nullptr;
   int64_t sps_blocks = 0;
   size_t sps_smem = 0;
@@ -63,8 +79,10 @@ void batch_release(ddsp_batch &B) {
   for (auto &t : B.tabs) free_tables(t);
   for (auto p : B.own_out) cudaFree(p);
   cudaFree(B.d_cm);
-  cudaFree(B.d_wsb);
-  cudaFree(B.d_items);
+  for (auto &g : B.groups) {
+    cudaFree(g.d_wsb);
+    cudaFree(g.d_items);
+  }
   cudaFree(B.d_queue);
   cudaFree(B.d_sb);
   cudaFree(B.d_counts);
@@ -81,9 +99,21 @@ struct BeamLayout {
   size_t smem = 0;
 };
 
-BeamLayout beam_layout(const Plan &p, const DedispTile &t, size_t budget) {
+int beam_span(const ddsp_batch &B, int b, int dt) {
+  int k = 0;
+  while ((1 << k) < dt) ++k;
+  auto &c = B.span_cache;
+  if (c.size() != (size_t)B.nbeams) c.assign(B.nbeams, std::vector<int>(8, -1));
+  if ((1 << k) != dt || k >= 8) return span_for(B.plans[b]->p, dt);
+  if (c[b][k] < 0) c[b][k] = span_for(B.plans[b]->p, dt);
+  return c[b][k];
+}
+
+BeamLayout beam_layout(const ddsp_batch &B, int beam, const DedispTile &t,
+                       size_t budget) {
   BeamLayout b;
-  dedisp_buffer_sizes(t, span_for(p, t.dm_tile()), 8, &b.rawmax, &b.elmax);
+  dedisp_buffer_sizes(t, beam_span(B, beam, t.dm_tile()), 8, &b.rawmax,
+                      &b.elmax);
   for (int cc = t.chan_chunk; cc >= 1; --cc) {
     const size_t sm =
         dedisp_ws_smem_bytes(cc, t.dm_tile(), b.rawmax, b.elmax, t.nbuf);
@@ -96,45 +126,178 @@ BeamLayout beam_layout(const Plan &p, const DedispTile &t, size_t budget) {
   return b;
 }
 
-// Per-beam layouts of tile t: every beam within the two-blocks-per-SM
-// budget if they all fit it, else within the one-block budget.  The launch's
-// shared memory is the largest of them.
-bool batch_layout(const ddsp_batch &B, const DedispTile &t,
-                  std::vector<BeamLayout> *out, size_t *smem) {
+// Relayouted elements per consumed word of a beam under tile t:
+// (S + span) / (DT * S), S the element segment, span the largest delay
+// spread inside a DM tile.  Large values mean the producers' relayout, not
+// the accumulation, sets the pace.
+double relayout_ratio(const ddsp_batch &B, int beam, const DedispTile &t) {
+  const double S = 32.0 * kElemPerThread * t.wt;
+  return (S + beam_span(B, beam, t.dm_tile())) / (t.dm_tile() * S);
+}
+
+// Narrower-DM shapes for the second group.
+const DedispTile kFallbackTiles[] = {
+    {8, 1, 4, 8, 2, kTileWarpSpecialized}, {8, 1, 8, 8, 2, kTileWarpSpecialized},
+    {4, 2, 4, 8, 2, kTileWarpSpecialized}};
+
+// Per-beam layouts of the group's beams under tile t: all within the
+// two-blocks-per-SM budget if they fit it, else within the one-block budget.
+bool group_layout(const ddsp_batch &B, const DedispTile &t,
+                  const std::vector<int> &beams, std::vector<BeamLayout> *out,
+                  size_t *smem) {
   for (size_t budget : {kSmemBudgetTwoBlocks, kSmemBudgetOneBlock}) {
-    out->assign(B.nbeams, BeamLayout{});
+    out->assign(beams.size(), BeamLayout{});
     *smem = 0;
     bool all = true;
-    for (int b = 0; b < B.nbeams && all; ++b) {
-      (*out)[b] = beam_layout(B.plans[b]->p, t, budget);
-      all = (*out)[b].cc > 0;
-      *smem = std::max(*smem, (*out)[b].smem);
+    for (size_t i = 0; i < beams.size() && all; ++i) {
+      (*out)[i] = beam_layout(B, beams[i], t, budget);
+      all = (*out)[i].cc > 0;
+      *smem = std::max(*smem, (*out)[i].smem);
     }
     if (all) return true;
   }
   return false;
 }
 
-// Build per-beam tables, channel-major workspaces and the dedispersion work
-// list for tile t; the tile's time tile fixes every beam's pitch.
-int batch_apply_tile(ddsp_batch &B, const DedispTile &t) {
+// Split the beams between main tile t and (possibly) one fallback shape: a
+// beam moves to the fallback if the main shape cannot hold it, stages fewer
+// than 2 of its channels per chunk (when the chunk limit allows 2) or the
+// fallback relayouts 30 % less per consumed word;
+// the fallback shape is the one with the lowest adds-weighted relayout.
+void choose_groups(const ddsp_batch &B, const DedispTile &t,
+                   std::vector<int> *main_beams, std::vector<int> *fb_beams,
+                   DedispTile *fb_tile) {
+  std::vector<double> rmain(B.nbeams), adds(B.nbeams);
+  std::vector<int> ccmain(B.nbeams);
+  std::vector<char> nomain(B.nbeams);   // fits the main shape under no budget
+  bool main_ok = true;
+  for (int b = 0; b < B.nbeams; ++b) {
+    const Plan &p = B.plans[b]->p;
+    rmain[b] = relayout_ratio(B, b, t);
+    ccmain[b] = beam_layout(B, b, t, kSmemBudgetTwoBlocks).cc;
+    nomain[b] = ccmain[b] == 0 && beam_layout(B, b, t, kSmemBudgetOneBlock).cc == 0;
+    main_ok = main_ok && !nomain[b];
+    adds[b] = (double)p.nchan * p.ndm * B.nout[b];
+  }
+  double best = 0;
+  for (int b = 0; b < B.nbeams; ++b) best += adds[b] * rmain[b];
+  if (!main_ok) best = 1e300;
+  main_beams->clear();
+  for (int b = 0; b < B.nbeams; ++b) main_beams->push_back(b);
+  fb_beams->clear();
+  for (const DedispTile &f : kFallbackTiles) {
+    if (!dedisp_tile_supported(f, 8) || dedisp_time_tile(f, 8) > kBatchMaxTimeTile)
+      continue;
+    std::vector<int> mb, fbb;
+    double cost = 0;
+    bool feasible = true;
+    for (int b = 0; b < B.nbeams && feasible; ++b) {
+      const double rf = relayout_ratio(B, b, f);
+      const bool fits = beam_layout(B, b, f, kSmemBudgetTwoBlocks).cc > 0 ||
+                        beam_layout(B, b, f, kSmemBudgetOneBlock).cc > 0;
+      const bool move = fits && (nomain[b] || ccmain[b] < std::min(2, t.chan_chunk) ||
+                                 rf < 0.7 * rmain[b]);
+      feasible = move || !nomain[b];
+      (move ? fbb : mb).push_back(b);
+      cost += adds[b] * (move ? rf : rmain[b]);
+    }
+    if (feasible && !fbb.empty() && !mb.empty() && cost < 0.97 * best) {
+      best = cost;
+      *main_beams = mb;
+      *fb_beams = fbb;
+      *fb_tile = f;
+    }
+  }
+}
+
+// Build one group: per-beam tables for its tile, descriptors and the
+// cost-ordered work list (uploaded).
+int build_group(ddsp_batch &B, BatchGroup &G, const DedispTile &t,
+                const std::vector<int> &beams) {
   std::vector<BeamLayout> lay;
   size_t smem;
-  if (!dedisp_tile_supported(t, 8) || !(t.flags & kTileWarpSpecialized) ||
-      !batch_layout(B, t, &lay, &smem))
-    return DDSP_E_INVALID_ARG;
-  batch_free_graph(B);
-  cudaDeviceSynchronize();
+  if (!group_layout(B, t, beams, &lay, &smem)) return DDSP_E_INVALID_ARG;
   const int TT = dedisp_time_tile(t, 8);
-  if (TT > kBatchMaxTimeTile) return DDSP_E_INVALID_ARG;
-  B.tabs.resize(B.nbeams);
-  B.pitch.resize(B.nbeams);
-  B.cm_off.resize(B.nbeams);
-  size_t cm_bytes = 0;
-  for (int b = 0; b < B.nbeams; ++b) {
+  std::vector<WsBeam> wsb(beams.size());
+  std::vector<int4> items;
+  for (size_t i = 0; i < beams.size(); ++i) {
+    const int b = beams[i];
     const Plan &p = B.plans[b]->p;
     int rc = build_tables_for(p, t, B.tabs[b]);
     if (rc != DDSP_OK) return rc;
+    WsBeam &w = wsb[i];
+    w.cm = B.d_cm + B.cm_off[b];
+    w.pitch = B.pitch[b];
+    w.nsamp_out = B.nout[b];
+    w.ring = 0;
+    w.t0 = 0;
+    w.out_pitch = B.nout[b];
+    w.desc = reinterpret_cast<const int2 *>(B.tabs[b].d_desc);
+    w.relb = B.tabs[b].d_relb;
+    w.rowmap = B.tabs[b].d_rowmap;
+    w.out = B.d_out[b];
+    w.nchan = p.nchan;
+    w.n_dm_tiles = B.tabs[b].n_dm_tiles;
+    w.n_time_tiles = (int)((B.nout[b] + TT - 1) / TT);
+    w.cc = lay[i].cc;
+    w.rawmax = lay[i].rawmax;
+    w.elmax = lay[i].elmax;
+    B.cc[b] = lay[i].cc;
+    // DM tiles innermost: consecutive items stage overlapping windows of
+    // one time tile, which L2 then serves
+    for (int tt = 0; tt < w.n_time_tiles; ++tt)
+      for (int g = 0; g < w.n_dm_tiles; ++g)
+        items.push_back(make_int4((int)i, g, tt, p.nchan));
+  }
+  // the costliest items (most channels) first, so the tail is short
+  std::stable_sort(items.begin(), items.end(),
+                   [](const int4 &a, const int4 &b) { return a.w > b.w; });
+  cudaError_t e;
+  if ((e = cudaMalloc(&G.d_wsb, wsb.size() * sizeof(WsBeam))) != cudaSuccess ||
+      (e = cudaMalloc(&G.d_items, items.size() * sizeof(int4))) != cudaSuccess)
+    return cuda_rc(e);
+  cudaMemcpy(G.d_wsb, wsb.data(), wsb.size() * sizeof(WsBeam),
+             cudaMemcpyHostToDevice);
+  e = cudaMemcpy(G.d_items, items.data(), items.size() * sizeof(int4),
+                 cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_rc(e);
+  G.tile = t;
+  G.beams = beams;
+  G.nitems = (int)items.size();
+  G.items.swap(items);
+  G.smem = smem;
+  const int per_sm = persistent_blocks_per_sm(t, smem);
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, B.device);
+  if (per_sm <= 0 || nsm <= 0) return DDSP_E_INVALID_ARG;
+  G.grid = std::min(per_sm * nsm, std::max(1, G.nitems));
+  return DDSP_OK;
+}
+
+// Apply main tile t: split the beams into groups, size the channel-major
+// pool (pitches fit every time tile) and build each group.
+int batch_apply_tile(ddsp_batch &B, const DedispTile &t) {
+  if (!dedisp_tile_supported(t, 8) || !(t.flags & kTileWarpSpecialized) ||
+      dedisp_time_tile(t, 8) > kBatchMaxTimeTile)
+    return DDSP_E_INVALID_ARG;
+  std::vector<int> mb, fbb;
+  DedispTile ft;
+  choose_groups(B, t, &mb, &fbb, &ft);
+  {
+    std::vector<BeamLayout> lay;
+    size_t sm;
+    if (!group_layout(B, t, mb, &lay, &sm)) return DDSP_E_INVALID_ARG;
+  }
+  batch_free_graph(B);
+  cudaDeviceSynchronize();
+  B.tabs.resize(B.nbeams);
+  B.pitch.resize(B.nbeams);
+  B.cm_off.resize(B.nbeams);
+  B.cc.assign(B.nbeams, 0);
+  B.group_of.assign(B.nbeams, 0);
+  size_t cm_bytes = 0;
+  for (int b = 0; b < B.nbeams; ++b) {
+    const Plan &p = B.plans[b]->p;
     // pitch sized for the largest time tile of any shape, so the ingested
     // rows stay valid when the tile changes
     B.pitch[b] = round_up(round_up(B.nout[b], kBatchMaxTimeTile) +
@@ -150,60 +313,18 @@ int batch_apply_tile(ddsp_batch &B, const DedispTile &t) {
     B.d_cm = nw;
     B.cm_bytes = cm_bytes;
   }
-  // descriptors
-  std::vector<WsBeam> wsb(B.nbeams);
-  std::vector<int4> items;
-  for (int b = 0; b < B.nbeams; ++b) {
-    const Plan &p = B.plans[b]->p;
-    WsBeam &w = wsb[b];
-    w.cm = B.d_cm + B.cm_off[b];
-    w.pitch = B.pitch[b];
-    w.nsamp_out = B.nout[b];
-    w.ring = 0;
-    w.t0 = 0;
-    w.out_pitch = B.nout[b];
-    w.desc = reinterpret_cast<const int2 *>(B.tabs[b].d_desc);
-    w.relb = B.tabs[b].d_relb;
-    w.rowmap = B.tabs[b].d_rowmap;
-    w.out = B.d_out[b];
-    w.nchan = p.nchan;
-    w.n_dm_tiles = B.tabs[b].n_dm_tiles;
-    w.n_time_tiles = (int)((B.nout[b] + TT - 1) / TT);
-    w.cc = lay[b].cc;
-    w.rawmax = lay[b].rawmax;
-    w.elmax = lay[b].elmax;
-    // DM tiles innermost: consecutive items stage overlapping windows of
-    // one time tile, which L2 then serves
-    for (int tt = 0; tt < w.n_time_tiles; ++tt)
-      for (int g = 0; g < w.n_dm_tiles; ++g)
-        items.push_back(make_int4(b, g, tt, p.nchan));
+  for (auto &g : B.groups) {
+    cudaFree(g.d_wsb);
+    cudaFree(g.d_items);
   }
-  // the costliest items (most channels) first, so the tail is short
-  std::stable_sort(items.begin(), items.end(),
-                   [](const int4 &a, const int4 &b) { return a.w > b.w; });
-  cudaFree(B.d_wsb);
-  cudaFree(B.d_items);
-  B.d_wsb = nullptr;
-  B.d_items = nullptr;
-  if ((e = cudaMalloc(&B.d_wsb, wsb.size() * sizeof(WsBeam))) != cudaSuccess ||
-      (e = cudaMalloc(&B.d_items, items.size() * sizeof(int4))) != cudaSuccess)
-    return cuda_rc(e);
-  cudaMemcpy(B.d_wsb, wsb.data(), wsb.size() * sizeof(WsBeam),
-             cudaMemcpyHostToDevice);
-  e = cudaMemcpy(B.d_items, items.data(), items.size() * sizeof(int4),
-                 cudaMemcpyHostToDevice);
-  if (e != cudaSuccess) return cuda_rc(e);
-  B.nitems = (int)items.size();
-  B.items.swap(items);
+  B.groups.assign(fbb.empty() ? 1 : 2, BatchGroup{});
+  int rc = build_group(B, B.groups[0], t, mb);
+  if (rc == DDSP_OK && !fbb.empty()) {
+    rc = build_group(B, B.groups[1], ft, fbb);
+    for (int b : fbb) B.group_of[b] = 1;
+  }
+  if (rc != DDSP_OK) return rc;
   B.tile = t;
-  B.cc.resize(B.nbeams);
-  for (int b = 0; b < B.nbeams; ++b) B.cc[b] = lay[b].cc;
-  B.smem = smem;
-  int per_sm = persistent_blocks_per_sm(t, smem);
-  int nsm = 0;
-  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, B.device);
-  if (per_sm <= 0 || nsm <= 0) return DDSP_E_INVALID_ARG;
-  B.grid = std::min(per_sm * nsm, std::max(1, B.nitems));
   return DDSP_OK;
 }
 
@@ -219,10 +340,14 @@ constexpr int kNumBatchTiles = sizeof(kBatchTiles) / sizeof(kBatchTiles[0]);
 constexpr size_t kAutotuneStride = 16;
 
 int batch_enqueue(ddsp_batch &B, float thr, cudaStream_t s) {
-  cudaError_t e = launch_batch_reset(B.d_queue, B.d_counts, B.nbeams, s);
-  if (e == cudaSuccess)
-    e = launch_dedisperse_persistent(B.tile, B.d_wsb, B.d_items, B.nitems, 0,
-                                     0, B.d_queue, B.smem, B.d_err, B.grid, s);
+  cudaError_t e = launch_batch_reset(B.d_queue, kMaxGroups, B.d_counts,
+                                     B.nbeams, s);
+  for (size_t gi = 0; gi < B.groups.size() && e == cudaSuccess; ++gi) {
+    const BatchGroup &G = B.groups[gi];
+    e = launch_dedisperse_persistent(G.tile, G.d_wsb, G.d_items, G.nitems, 0,
+                                     0, B.d_queue + gi, G.smem, B.d_err,
+                                     G.grid, s);
+  }
   if (e == cudaSuccess)
     e = launch_sps_batch(B.d_sb, B.nbeams, B.sps_blocks, thr, B.sps_smem, s);
   return cuda_rc(e);
@@ -308,7 +433,7 @@ int ddsp_batch_create(ddsp_batch **out, ddsp_plan *const *plans, int nbeams,
     B->sps_smem = sps_smem_bytes(maxlen_all, wmax_all);
     if ((e = cudaMalloc(&B->d_sb, sb.size() * sizeof(SpsBeam))) != cudaSuccess ||
         (e = cudaMalloc(&B->d_counts, counts.size() * sizeof(uint32_t *))) != cudaSuccess ||
-        (e = cudaMalloc(&B->d_queue, sizeof(int))) != cudaSuccess ||
+        (e = cudaMalloc(&B->d_queue, kMaxGroups * sizeof(int))) != cudaSuccess ||
         (e = cudaMalloc(&B->d_err, sizeof(int32_t))) != cudaSuccess)
       rc = cuda_rc(e);
   }
@@ -400,7 +525,7 @@ int ddsp_batch_get_tile(const ddsp_batch *B, int *dm_tile, int *dm_per_thread,
   if (time_tile) *time_tile = dedisp_time_tile(B->tile, 8);
   if (chan_chunk) *chan_chunk = B->tile.chan_chunk;
   if (stages) *stages = B->tile.nbuf;
-  if (grid) *grid = B->grid;
+  if (grid) *grid = B->groups.empty() ? 0 : B->groups[0].grid;
   return DDSP_OK;
 }
 
@@ -479,11 +604,18 @@ int ddsp_batch_autotune(ddsp_batch *B, int reps, ddsp_stream_t stream,
   for (int i = 0; i < kNumBatchTiles; ++i) {
     float ms = -1.0f;
     if (batch_apply_tile(*B, kBatchTiles[i]) == DDSP_OK) {
-      // every kAutotuneStride-th item of the cost-ordered work list: the
-      // same share of every beam's work for each candidate
+      // every kAutotuneStride-th item of each group's cost-ordered work
+      // list: the same share of every beam's work for each candidate
       std::vector<int4> sample;
-      for (size_t k = 0; k < B->items.size(); k += kAutotuneStride)
-        sample.push_back(B->items[k]);
+      std::vector<size_t> off(B->groups.size() + 1, 0);
+      size_t all = 0;
+      for (size_t gi = 0; gi < B->groups.size(); ++gi) {
+        const auto &items = B->groups[gi].items;
+        for (size_t k = 0; k < items.size(); k += kAutotuneStride)
+          sample.push_back(items[k]);
+        off[gi + 1] = sample.size();
+        all += items.size();
+      }
       cudaError_t e = cudaSuccess;
       if (sample.size() > sample_cap) {
         cudaFree(d_sample);
@@ -495,22 +627,26 @@ int ddsp_batch_autotune(ddsp_batch *B, int reps, ddsp_stream_t stream,
       if (e == cudaSuccess)
         e = cudaMemcpy(d_sample, sample.data(), sample.size() * sizeof(int4),
                        cudaMemcpyHostToDevice);
-      const int grid = std::min(B->grid, (int)sample.size());
       float best_rep = 1e30f;
       for (int r = 0; r <= reps && e == cudaSuccess; ++r) {
-        launch_batch_reset(B->d_queue, B->d_counts, B->nbeams, s);
+        launch_batch_reset(B->d_queue, kMaxGroups, B->d_counts, B->nbeams, s);
         cudaEventRecord(e0, s);
-        e = launch_dedisperse_persistent(B->tile, B->d_wsb, d_sample,
-                                         (int)sample.size(), 0, 0, B->d_queue,
-                                         B->smem, B->d_err, grid, s);
+        for (size_t gi = 0; gi < B->groups.size() && e == cudaSuccess; ++gi) {
+          const BatchGroup &G = B->groups[gi];
+          const int n = (int)(off[gi + 1] - off[gi]);
+          if (n == 0) continue;
+          e = launch_dedisperse_persistent(G.tile, G.d_wsb, d_sample + off[gi],
+                                           n, 0, 0, B->d_queue + gi, G.smem,
+                                           B->d_err, std::min(G.grid, n), s);
+        }
         cudaEventRecord(e1, s);
         cudaEventSynchronize(e1);
         float t = 0;
         cudaEventElapsedTime(&t, e0, e1);
         if (r > 0) best_rep = std::min(best_rep, t);  // first run warms up
       }
-      if (e == cudaSuccess)
-        ms = best_rep * (float)B->items.size() / (float)sample.size();
+      if (e == cudaSuccess && !sample.empty())
+        ms = best_rep * (float)all / (float)sample.size();
       if (ms > 0 && ms < bestms) {
         bestms = ms;
         besti = i;
@@ -527,6 +663,21 @@ int ddsp_batch_autotune(ddsp_batch *B, int reps, ddsp_stream_t stream,
   if (besti < 0) return DDSP_E_INVALID_ARG;
   B->ran_direct = false;
   return batch_apply_tile(*B, kBatchTiles[besti]);
+}
+
+int ddsp_batch_get_beam_tile(const ddsp_batch *B, int beam, int *dm_tile,
+                             int *dm_per_thread, int *time_tile,
+                             int *chan_chunk, int *group) {
+  if (!B || beam < 0 || beam >= B->nbeams || B->groups.empty())
+    return DDSP_E_INVALID_ARG;
+  const int gi = B->group_of[beam];
+  const DedispTile &t = B->groups[gi].tile;
+  if (dm_tile) *dm_tile = t.dm_tile();
+  if (dm_per_thread) *dm_per_thread = t.rd;
+  if (time_tile) *time_tile = dedisp_time_tile(t, 8);
+  if (chan_chunk) *chan_chunk = B->cc[beam];
+  if (group) *group = gi;
+  return DDSP_OK;
 }
 
 }  // extern "C"

@@ -136,8 +136,9 @@ cudaError_t launch_sps(const Plan &p, const int32_t *d_series,
 int64_t sps_max_window_samples();
 
 int persistent_blocks_per_sm(const DedispTile &t, size_t smem);
-cudaError_t launch_batch_reset(int *d_queue, uint32_t *const *d_counts,
-                               int ncounts, cudaStream_t s);
+cudaError_t launch_batch_reset(int *d_queue, int nqueues,
+                               uint32_t *const *d_counts, int ncounts,
+                               cudaStream_t s);
 cudaError_t launch_serve_prep(const SpsBeam *d_beams, int nbeams, int ndm,
                               int64_t n, int carry, int *d_queue,
                               cudaStream_t s);

@@ -56,10 +56,10 @@ dedisp_persistent_kernel(const WsBeam *__restrict__ beams,
   }
 }
 
-__global__ void batch_reset_kernel(int *queue, uint32_t *const *counts,
-                                   int ncounts) {
+__global__ void batch_reset_kernel(int *queue, int nqueues,
+                                   uint32_t *const *counts, int ncounts) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i == 0) *queue = 0;
+  if (i < nqueues) queue[i] = 0;
   if (i < ncounts) *counts[i] = 0;
 }
 
@@ -139,11 +139,12 @@ cudaError_t launch_serve_prep(const SpsBeam *d_beams, int nbeams, int ndm,
   return cudaGetLastError();
 }
 
-cudaError_t launch_batch_reset(int *d_queue, uint32_t *const *d_counts,
-                               int ncounts, cudaStream_t s) {
-  const int n = ncounts > 1 ? ncounts : 1;
-  batch_reset_kernel<<<(n + 255) / 256, 256, 0, s>>>(d_queue, d_counts,
-                                                     ncounts);
+cudaError_t launch_batch_reset(int *d_queue, int nqueues,
+                               uint32_t *const *d_counts, int ncounts,
+                               cudaStream_t s) {
+  const int n = std::max(std::max(ncounts, nqueues), 1);
+  batch_reset_kernel<<<(n + 255) / 256, 256, 0, s>>>(d_queue, nqueues,
+                                                     d_counts, ncounts);
   return cudaGetLastError();
 }
 

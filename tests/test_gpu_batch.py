@@ -137,10 +137,11 @@ def test_batch_full_160_beams_sampled():
         del x, s
 
 
-def test_batch_per_beam_chunks():
+def test_batch_per_beam_chunks_and_groups():
     """Beams whose delay spans inside a DM tile differ by ~40x share one
-    launch: the coarse beam stages one channel per chunk, the fine ones up
-    to the tile's limit, and every beam stays exact for several limits."""
+    step: the fine beams stage up to the tile's chunk limit in the main
+    launch, the coarse one goes to the second launch with a narrower DM
+    tile, and every beam stays exact for several limits."""
     coarse = synth.config3(nbeams=1, seed=23, nsamp_range=(8192, 8192),
                            nchan_choices=(256,), dm_hi_choices=(100.0,),
                            ndm_choices=(64,))
@@ -151,19 +152,48 @@ def test_batch_per_beam_chunks():
     plans = [_plan(c) for c in cfgs]
     blocks = [_block(c, p) for c, p in zip(cfgs, plans)]
     ref = [p.dedisperse(x).clone() for p, x in zip(plans, blocks)]
+    refc = []
+    for c, p, r in zip(cfgs, plans, ref):
+        p.single_pulse_search(r, c.threshold)
+        refc.append(p.fetch()[0])
     batch = Batch(plans, [x.shape[0] for x in blocks])
     for b, x in enumerate(blocks):
         batch.ingest(b, x)
     for cap in (8, 3, 1):
         batch.set_tile(16, 8, cap, 2)
-        chunks = [batch.beam_chunk(b) for b in range(len(cfgs))]
+        t = [batch.beam_tile(b) for b in range(len(cfgs))]
         # spans per 16-trial tile: ~8500 samples (coarse), ~440 (fine)
-        assert chunks[0] == 1 and all(1 <= c <= cap for c in chunks)
-        assert chunks[1] == chunks[2] >= min(cap, 3)
-        for s in batch.series:
-            s.fill_(-1)
+        assert t[0]["group"] == 1 and t[0]["dm_tile"] < 16, (cap, t)
+        assert t[1]["group"] == t[2]["group"] == 0
+        assert t[1]["chan_chunk"] == t[2]["chan_chunk"] >= min(cap, 3)
+        assert all(x["chan_chunk"] >= 1 for x in t)
+        for s_ in batch.series:
+            s_.fill_(-1)
         batch.run(7.0, use_graph=True)
         batch.run(7.0, use_graph=True)
         batch.check()
         for b in range(len(cfgs)):
             assert torch.equal(batch.series[b], ref[b]), (cap, b)
+            _same_candidates(plans[b].fetch()[0], refc[b])
+
+
+def test_batch_autotune_with_two_groups_keeps_results():
+    cfgs = (synth.config3(nbeams=2, seed=41, nsamp_range=(8192, 8192),
+                          nchan_choices=(256,), dm_hi_choices=(100.0,),
+                          ndm_choices=(64,))
+            + small_mix(4, seed=43))
+    plans = [_plan(c) for c in cfgs]
+    blocks = [_block(c, p) for c, p in zip(cfgs, plans)]
+    ref = [p.dedisperse(x).clone() for p, x in zip(plans, blocks)]
+    batch = Batch(plans, [x.shape[0] for x in blocks])
+    for b, x in enumerate(blocks):
+        batch.ingest(b, x)
+    batch.set_tile(16, 8, 8, 2)
+    assert any(batch.beam_tile(b)["group"] == 1 for b in range(len(cfgs)))
+    ms, best = batch.autotune(reps=1)     # candidates with and without a split
+    assert best >= 0 and ms[best] > 0
+    batch.run(7.0, use_graph=True)
+    batch.run(7.0, use_graph=True)
+    batch.check()
+    for b in range(len(cfgs)):
+        assert torch.equal(batch.series[b], ref[b]), b
