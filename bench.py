@@ -149,6 +149,10 @@ def oracle_sample_rate(x_host, d, widths, L, target_s, min_t=8):
     el = run(cal_t)
     T = int(max(min_t, min(avail, cal_t * target_s / max(el, 1e-3))))
     el = run(T)
+    # a tiny calibration run is dominated by fixed costs: rescale once more
+    if el < 0.6 * target_s and T < avail:
+        T = int(max(min_t, min(avail, T * target_s / max(el, 1e-3))))
+        el = run(T)
     adds = d.shape[0] * d.shape[1] * T
     return adds / el, T, el
 
