@@ -645,7 +645,7 @@ def run_serve(args):
         torch.cuda.synchronize(dev)
     tile = min(tune, key=tune.get)
 
-    def run_at(n, per_step):
+    def run_at(n, per_step, inflight):
         try:
             srv = Server(plan, B, n, reserve, tile=tile)
         except Exception:
@@ -670,7 +670,8 @@ def run_serve(args):
         arr = synth.arrival_times(n, args.steps, seed=5)
         loop = ServingLoop(srv, beams, lambda i, k: pool[(3 * i + warm + k) % 8],
                            cfg.threshold, stager=stager, compute_stream=compute,
-                           max_beams_in_step=per_step, first_block=warm)
+                           max_beams_in_step=per_step, first_block=warm,
+                           max_inflight=inflight)
         res = loop.run(arr, time_limit=args.steps * T + 60.0)
         srv.check(compute)
         srv.close()
@@ -689,8 +690,12 @@ def run_serve(args):
     runs = {}
     clk = ClockSampler(local if world > 1 else 0)
     clk.start()
-    n_batched, _ = realtime_limit(lambda n: run_at(n, 0), 64, 448, 16, T)
-    n_plain, _ = realtime_limit(lambda n: run_at(n, 1), 64, 448, 16, T)
+    # each path at its own best queue depth: batched steps already keep the
+    # device busy, one-beam steps need a second step queued to hide the
+    # host's turnaround between launches
+    n_batched, _ = realtime_limit(lambda n: run_at(n, 0, args.inflight), 64, 448, 16, T)
+    n_plain, _ = realtime_limit(lambda n: run_at(n, 1, args.plain_inflight),
+                                64, 448, 16, T)
     clocks = clk.stop()
     if rank == 0:
         def table(per_step):
@@ -705,6 +710,8 @@ def run_serve(args):
                                    f"{T:.4f} s, 1024 DMs 0-250, widths 1-256, "
                                    "Poisson-jittered arrivals",
                        "deadline_s": T, "blocks_per_beam": args.steps,
+                       "steps_in_flight": {"batched": args.inflight,
+                                           "plain_per_beam": args.plain_inflight},
                        "adds_per_block": adds_block,
                        "tile": dict(zip(("dm_tile", "dm_per_thread", "chan_chunk",
                                          "stages"), tile)),
@@ -728,6 +735,10 @@ def main():
                          "160 uneven beams in one persistent launch; serve: "
                          "real-time streaming beams (--steps blocks per beam)")
     ap.add_argument("--nbeams", type=int, default=0, help="batch: beams (0 = 160)")
+    ap.add_argument("--inflight", type=int, default=1,
+                    help="serve: batched steps queued on the device at once")
+    ap.add_argument("--plain-inflight", type=int, default=2,
+                    help="serve: one-beam steps queued on the device at once")
     ap.add_argument("--nsamp-out", type=int, default=0,
                     help="beam: output samples per trial (0 = 262144)")
     ap.add_argument("--ndm", type=int, default=0, help="sps: DM trials (0 = 2048)")

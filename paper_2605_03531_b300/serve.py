@@ -173,7 +173,14 @@ class ServingLoop:
                 ndone += len(members)
                 res.wall = tdone
                 busy = True
-            # next step, before reading results, so the device stays busy
+            # with one step in flight, launch the next before reading the
+            # finished blocks' results so the device stays busy; with more,
+            # read first (a step launched now could reuse the candidate
+            # buffer of a block finished but not yet read), the queued step
+            # keeps the device busy meanwhile
+            if self.max_inflight > 1:
+                self._fetch(finished, res)
+                finished = []
             if len(inflight) < self.max_inflight and unstepped > 0:
                 sid, sbeams = self.server.step(self.threshold,
                                                self.max_beams_in_step,
@@ -188,20 +195,24 @@ class ServingLoop:
                     inflight.append((sid, members))
                     res.step_sizes.append(len(sbeams))
                     busy = True
-            for i, k in finished:
-                # a block over the candidate capacity keeps its first records
-                # and reports the true count
-                cands, n, t_start = self.server.fetch(
-                    self.beams[i], self.first_block + k, allow_truncated=True)
-                ncand[i, k] = n
-                if self.on_candidates is not None:
-                    self.on_candidates(i, k, cands, t_start)
+            self._fetch(finished, res)
             if not busy:
                 wait = self.poll
                 if nexta < total and np.isfinite(flat[order[nexta]]):
                     wait = min(wait, max(0.0, flat[order[nexta]] - now))
                 self.sleep(wait)
         return res
+
+
+    def _fetch(self, finished, res):
+        for i, k in finished:
+            # a block over the candidate capacity keeps its first records
+            # and reports the true count
+            cands, n, t_start = self.server.fetch(
+                self.beams[i], self.first_block + k, allow_truncated=True)
+            res.ncand[i, k] = n
+            if self.on_candidates is not None:
+                self.on_candidates(i, k, cands, t_start)
 
 
 def realtime_limit(run_at, lo, hi, step, deadline):

@@ -79,13 +79,13 @@ class FakeServer:
 
 
 def _run(nbeams, nblocks, per_beam, max_beams_in_step=0, arrivals=None,
-         time_limit=None, overhead=2e-3):
+         time_limit=None, overhead=2e-3, max_inflight=1):
     clock = SimClock()
     srv = FakeServer(clock, nbeams, overhead=overhead, per_beam=per_beam)
     arr = arrivals if arrivals is not None else synth.arrival_times(nbeams, nblocks, seed=5)
     loop = ServingLoop(srv, list(range(nbeams)), lambda i, k: (i, k), 7.0,
                        max_beams_in_step=max_beams_in_step, clock=clock,
-                       sleep=clock.sleep)
+                       sleep=clock.sleep, max_inflight=max_inflight)
     return loop.run(arr, time_limit=time_limit), srv
 
 
@@ -183,3 +183,13 @@ def test_realtime_limit_bisection():
     n, seen = realtime_limit(lambda n: 0.006 * n, 64, 320, 16, T)
     assert n == 208                      # 0.006*208 = 1.248 < 1.342 < 1.344
     assert realtime_limit(lambda n: 2.0, 64, 320, 16, T)[0] == 0
+
+
+def test_two_steps_in_flight_read_results_in_time():
+    """With a second step queued the loop reads each finished block while
+    the fake server still holds its results (it asserts the window), and
+    every block completes once."""
+    res, srv = _run(30, 8, per_beam=20e-3, overhead=0.05, max_inflight=2)
+    assert np.isfinite(res.latency).all()
+    assert sorted(srv.fetched) == sorted((b, j) for b in range(30) for j in range(8))
+    assert max(len(m) for _, m in srv.steps) > 1
