@@ -200,6 +200,108 @@ __device__ void select2(KeyFn key, int n, int r1, int r2, uint32_t kmax,
   }
 }
 
+// Step 4 of the search when the widths are 1, 2, 4, ..., 2^(NW-1): the
+// offsets of the boxcar ends are compile-time, and start times whose widest
+// boxcar ends inside the series (all but the last 2^(NW-1) of a series)
+// need no per-width check.  Outside the dense mode, the S/N is evaluated
+// only for the widths that passed the integer screen: any width whose FP32
+// S/N reaches the threshold passes it (the screen keeps a margin), so a
+// width that failed can never be the best one of an emitted candidate.
+template <int NW, bool DENSE>
+__device__ __forceinline__ void sweep_pow2(
+    const uint32_t *__restrict__ Q, const SpsShared &sh, int len, int nv,
+    const int32_t (&tbv)[kMaxWidths], int odd, int32_t mfloor, float thr,
+    int64_t lo, int64_t n, int64_t nrep, int k, ddsp_cand *__restrict__ cands,
+    uint32_t *__restrict__ count, uint32_t cap, int32_t *__restrict__ best_w,
+    float *__restrict__ best_snr, int32_t *__restrict__ best_sum) {
+  const int tid = threadIdx.x, lane = tid & 31;
+  constexpr int kWidest = 1 << (NW - 1);
+  for (int i0 = 0; i0 < len; i0 += kSpsThreads) {
+    const int i = i0 + tid;
+    const bool in = i < len;
+    uint32_t qi = 0;
+    int32_t by[NW];
+    unsigned pm = 0, vm = 0;   // widths passing the screen / ending inside
+    if (in) {
+      qi = Q[i];
+      if (i + kWidest <= nv) {
+        const uint32_t *qp = Q + i;
+#pragma unroll
+        for (int wi = 0; wi < NW; ++wi) {
+          by[wi] = (int32_t)(qp[1 << wi] - qi);
+          pm |= (unsigned)(by[wi] >= tbv[wi]) << wi;
+        }
+        vm = (1u << NW) - 1u;
+      } else {
+#pragma unroll
+        for (int wi = 0; wi < NW; ++wi) {
+          const bool v = i + (1 << wi) <= nv;
+          by[wi] = (int32_t)(Q[min(i + (1 << wi), nv)] - qi);
+          vm |= (unsigned)v << wi;
+          pm |= (unsigned)(v && by[wi] >= tbv[wi]) << wi;
+        }
+      }
+    }
+    if constexpr (DENSE) {
+      if (in) {
+        int bw = -1;
+        float bs = 0.0f;
+        int32_t bsum = 0;
+#pragma unroll
+        for (int wi = 0; wi < NW; ++wi) {
+          if ((vm >> wi) & 1u) {
+            const float sn = twice_minus(by[wi], (1 << wi) * odd) * sh.inv[wi];
+            if (bw < 0 || sn > bs) {
+              bw = wi;
+              bs = sn;
+              bsum = by[wi] + (1 << wi) * mfloor;
+            }
+          }
+        }
+        const int64_t o = (int64_t)k * n + lo + i;
+        best_w[o] = bw;
+        best_snr[o] = bs;
+        best_sum[o] = bsum;
+      }
+    } else {
+      const unsigned active = __ballot_sync(0xffffffffu, pm != 0u);
+      if (pm) {
+        int bw = -1;
+        float bs = 0.0f;
+        unsigned m = pm;
+        while (m) {
+          const int wi = __ffs(m) - 1;
+          m &= m - 1u;
+          const int w = 1 << wi;
+          const float sn =
+              twice_minus((int32_t)(Q[i + w] - qi), w * odd) * sh.inv[wi];
+          if (bw < 0 || sn > bs) {
+            bw = wi;
+            bs = sn;
+          }
+        }
+        const bool cand = bs >= thr && lo + i < nrep;
+        const uint32_t ball = __ballot_sync(active, cand);
+        if (cand) {
+          const int leader = __ffs(ball) - 1;
+          uint32_t base = 0;
+          if (lane == leader) base = atomicAdd(count, (uint32_t)__popc(ball));
+          base = __shfl_sync(ball, base, leader);
+          const uint32_t slot = base + __popc(ball & ((1u << lane) - 1u));
+          if (slot < cap) {
+            ddsp_cand c;
+            c.dm_idx = (uint32_t)k;
+            c.t = (uint32_t)(lo + i);
+            c.w_idx = (uint32_t)bw;
+            c.snr = bs;
+            cands[slot] = c;
+          }
+        }
+      }
+    }
+  }
+}
+
 // The search of one (DM trial k, window j): the body of the per-plan kernel
 // and of the multi-beam kernel (k_batch.cu).
 template <bool DENSE>
@@ -324,6 +426,24 @@ __device__ __forceinline__ void sps_window(
   }
   // i + w <= n - lo also implies i + w <= elen, the last prefix index
   const int nv = (int)min(n - lo, (int64_t)elen);
+  bool pow2 = true;
+  for (int wi = 0; wi < nw; ++wi) pow2 = pow2 && wv[wi] == (1 << wi);
+  if (pow2) {
+    switch (nw) {
+#define DDSP_SWEEP(N)                                                        \
+  case N:                                                                    \
+    sweep_pow2<N, DENSE>(Q, sh, len, nv, tbv, odd, mfloor, thr, lo, n, nrep, \
+                         k, cands, count, cap, best_w, best_snr, best_sum);  \
+    return;
+      DDSP_SWEEP(1) DDSP_SWEEP(2) DDSP_SWEEP(3) DDSP_SWEEP(4) DDSP_SWEEP(5)
+      DDSP_SWEEP(6) DDSP_SWEEP(7) DDSP_SWEEP(8) DDSP_SWEEP(9) DDSP_SWEEP(10)
+      DDSP_SWEEP(11)
+#undef DDSP_SWEEP
+      default:
+        break;
+    }
+  }
+  // any other ascending width list
   for (int i0 = 0; i0 < len; i0 += kSpsThreads) {
     const int i = i0 + tid;
     const bool in = i < len;
