@@ -43,6 +43,9 @@ struct SpsShared {
   uint32_t wsum[kWarps];
 };
 
+// The window buffer follows the struct, 16-byte aligned (vector accesses).
+constexpr size_t kBufOff = (sizeof(SpsShared) + 15) & ~(size_t)15;
+
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane) {
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -64,6 +67,15 @@ __device__ __forceinline__ float twice_minus(int32_t by, int32_t c) {
   const float hf = __int_as_float(0x4B400000 + hi) - magic;
   const float lf = __int_as_float(0x4B400000 + lo) - magic;
   return __fmaf_rn(hf, 131072.0f, lf);
+}
+
+// Sum of wsum[0 .. warp-1] (kWarps <= 32 per-warp totals), by one warp scan.
+__device__ __forceinline__ uint32_t warp_excl_offset(const uint32_t *wsum,
+                                                     int warp, int lane) {
+  const uint32_t v = lane < kWarps ? wsum[lane] : 0u;
+  const uint32_t inc = warp_incl_scan(v, lane);
+  const uint32_t below = __shfl_sync(0xffffffffu, inc, warp > 0 ? warp - 1 : 0);
+  return warp > 0 ? below : 0u;
 }
 
 // Block-wide min & max of a per-thread pair (int64).
@@ -110,10 +122,11 @@ __device__ void select2(KeyFn key, int n, int r1, int r2, uint32_t kmax,
     const int nb = (int)((span - 1) >> s) + 1;
     for (int b = tid; b < nb; b += kSpsThreads) sh.hist[b] = 0;
     __syncthreads();
+    const uint32_t smax = (uint32_t)(span - 1);   // span <= 2^32
     for (int i = tid; i < n; i += kSpsThreads) {
-      uint32_t k = key(i);
-      uint64_t d = (uint64_t)(k - lo);
-      if (k >= lo && d < span) atomicAdd(&sh.hist[d >> s], 1u);
+      const uint32_t k = key(i);
+      const uint32_t d = k - lo;
+      if (k >= lo && d <= smax) atomicAdd(&sh.hist[d >> s], 1u);
     }
     __syncthreads();
     // exclusive scan of the histogram: each thread owns 4 consecutive bins
@@ -127,8 +140,7 @@ __device__ void select2(KeyFn key, int n, int r1, int r2, uint32_t kmax,
     uint32_t incl = warp_incl_scan(tsum, lane);
     if (lane == 31) sh.wsum[warp] = incl;
     __syncthreads();
-    uint32_t wpre = 0;
-    for (int w = 0; w < warp; ++w) wpre += sh.wsum[w];
+    const uint32_t wpre = warp_excl_offset(sh.wsum, warp, lane);
     uint32_t run = wpre + incl - tsum;  // keys of this window below bin 4*tid
     const uint32_t q1 = (uint32_t)(r1 - below), q2 = (uint32_t)(r2 - below);
 #pragma unroll
@@ -164,10 +176,11 @@ __device__ void select2(KeyFn key, int n, int r1, int r2, uint32_t kmax,
     }
     // r2 = r1 + 1 sits in a later bin: k1 = max of bin b1, k2 = min of bin b2
     uint32_t mx = 0, mn = 0xffffffffu;
+    const uint32_t smax2 = (uint32_t)(span - 1);
     for (int i = tid; i < n; i += kSpsThreads) {
-      uint32_t k = key(i);
-      uint64_t d = (uint64_t)(k - lo);
-      if (k >= lo && d < span) {
+      const uint32_t k = key(i);
+      const uint32_t d = k - lo;
+      if (k >= lo && d <= smax2) {
         int b = (int)(d >> s);
         if (b == b1) mx = max(mx, k);
         if (b == b2) mn = min(mn, k);
@@ -315,7 +328,7 @@ __device__ __forceinline__ void sps_window(
     const int64_t j, const int k, const int64_t nrep) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SpsShared &sh = *reinterpret_cast<SpsShared *>(smem_raw);
-  int32_t *buf = reinterpret_cast<int32_t *>(smem_raw + sizeof(SpsShared));
+  int32_t *buf = reinterpret_cast<int32_t *>(smem_raw + kBufOff);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t lo = (L <= 0) ? 0 : j * L;
@@ -326,17 +339,18 @@ __device__ __forceinline__ void sps_window(
   const int32_t *x = series + (int64_t)k * n + lo;
 
   // ---- 1. load (buf[0] is the zero prefix slot)
-  int64_t mn = INT64_MAX, mx = INT64_MIN;
+  int32_t mn32 = INT32_MAX, mx32 = INT32_MIN;
   for (int i = tid; i < elen; i += kSpsThreads) {
     int32_t v = __ldg(x + i);
     buf[1 + i] = v;
     if (i < len) {
-      mn = min(mn, (int64_t)v);
-      mx = max(mx, (int64_t)v);
+      mn32 = min(mn32, v);
+      mx32 = max(mx32, v);
     }
   }
   if (tid == 0) buf[0] = 0;
   __syncthreads();
+  int64_t mn = mn32, mx = mx32;
   block_minmax(mn, mx, sh);
 
   // ---- 2. median and MAD
@@ -344,19 +358,21 @@ __device__ __forceinline__ void sps_window(
   const bool range_ok = (mx - mn) < (int64_t)1 << 31;
   if (range_ok) {
     const int r1 = (len - 1) / 2, r2 = len / 2;
-    const int32_t base = (int32_t)mn;
+    const uint32_t base = (uint32_t)(int32_t)mn;
     uint32_t k1, k2;
-    select2([&](int i) { return (uint32_t)(buf[1 + i] - base); }, len, r1,
-            r2, (uint32_t)(mx - mn), sh, k1, k2);
+    // keys x - min in [0, 2^31)
+    select2([&](int i) { return (uint32_t)buf[1 + i] - base; }, len, r1, r2,
+            (uint32_t)(mx - mn), sh, k1, k2);
     M2 = 2 * mn + (int64_t)k1 + (int64_t)k2;
-    // |2x - M2| <= 2*(max - min) < 2^32
+    // |2x - M2| = |2(x - min) - (M2 - 2 min)|, both terms in [0, 2^32)
     const int64_t m2c = M2;
+    const uint32_t m2r = (uint32_t)(m2c - 2 * mn);
     uint64_t umax = (uint64_t)max(2 * mx - m2c, m2c - 2 * mn);
     uint32_t u1, u2;
     select2(
         [&](int i) {
-          int64_t d = 2 * (int64_t)buf[1 + i] - m2c;
-          return (uint32_t)(d < 0 ? -d : d);
+          const uint32_t t2 = 2u * ((uint32_t)buf[1 + i] - base);
+          return t2 >= m2r ? t2 - m2r : m2r - t2;
         },
         len, r1, r2, (uint32_t)umax, sh, u1, u2);
     MAD4 = (int64_t)u1 + (int64_t)u2;
@@ -389,23 +405,53 @@ __device__ __forceinline__ void sps_window(
     sh.wid[tid] = widths[tid];
   }
 
-  // ---- 3. y = x - floor(median); inclusive prefix sum Q[1..elen] in place
+  // ---- 3. y = x - floor(median); inclusive prefix sum over buf[0..elen]
+  // in place (buf[0] = 0, so buf[i] = Q[i]).  Each warp walks its own run of
+  // 128-value groups; a lane takes 4 consecutive values with one 16-byte
+  // shared load, scans them, and one warp scan joins the lanes.
   {
-    const int chunk = ((elen + kWarps * 32 - 1) / (kWarps * 32)) * 32;
-    const int b0 = warp * chunk, b1 = min(elen, b0 + chunk);
+    const int ntot = elen + 1;
+    const int ngroups = (ntot + 127) / 128;
+    const int gpw = (ngroups + kWarps - 1) / kWarps;
+    const int g0 = warp * gpw, g1 = min(ngroups, g0 + gpw);
     uint32_t carry = 0;
-    for (int i = b0; i < b1; i += 32) {
-      int ii = i + lane;
-      uint32_t v = (ii < b1) ? (uint32_t)(buf[1 + ii] - mfloor) : 0u;
-      v = warp_incl_scan(v, lane) + carry;
-      if (ii < b1) buf[1 + ii] = (int32_t)v;
-      carry = __shfl_sync(0xffffffffu, v, 31);
+    for (int g = g0; g < g1; ++g) {
+      const int b4 = g * 128 + 4 * lane;
+      uint4 q = make_uint4(0, 0, 0, 0);
+      if (b4 < ntot) q = *reinterpret_cast<const uint4 *>(buf + b4);
+      // y for indices 1 .. elen, zero for index 0 and past the end
+      const uint32_t mf = (uint32_t)mfloor;
+      uint32_t a0 = (b4 >= 1 && b4 < ntot) ? q.x - mf : 0u;
+      uint32_t a1 = (b4 + 1 < ntot) ? q.y - mf : 0u;
+      uint32_t a2 = (b4 + 2 < ntot) ? q.z - mf : 0u;
+      uint32_t a3 = (b4 + 3 < ntot) ? q.w - mf : 0u;
+      a1 += a0;
+      a2 += a1;
+      a3 += a2;
+      const uint32_t inc = warp_incl_scan(a3, lane);
+      const uint32_t pre = carry + inc - a3;
+      if (b4 < ntot)
+        *reinterpret_cast<uint4 *>(buf + b4) =
+            make_uint4(pre + a0, pre + a1, pre + a2, pre + a3);
+      carry += __shfl_sync(0xffffffffu, inc, 31);
     }
     if (lane == 0) sh.wsum[warp] = carry;
     __syncthreads();
-    uint32_t off = 0;
-    for (int w = 0; w < warp; ++w) off += sh.wsum[w];
-    for (int i = b0 + lane; i < b1; i += 32) buf[1 + i] = (int32_t)((uint32_t)buf[1 + i] + off);
+    const uint32_t off = warp_excl_offset(sh.wsum, warp, lane);
+    if (off != 0u) {
+      for (int g = g0; g < g1; ++g) {
+        const int b4 = g * 128 + 4 * lane;
+        if (b4 < ntot) {
+          uint4 *p4 = reinterpret_cast<uint4 *>(buf + b4);
+          uint4 q = *p4;
+          q.x += off;
+          q.y += off;
+          q.z += off;
+          q.w += off;
+          *p4 = q;
+        }
+      }
+    }
     __syncthreads();
   }
   const uint32_t *Q = reinterpret_cast<const uint32_t *>(buf);
@@ -545,7 +591,7 @@ sps_batch_kernel(const SpsBeam *__restrict__ beams, int nbeams, float thr) {
 int64_t sps_max_window_samples() { return kMaxWindowSamples; }
 
 size_t sps_smem_bytes(int64_t maxlen, int wmax) {
-  return sizeof(SpsShared) + 4 * (size_t)(maxlen + wmax + 4);
+  return kBufOff + 4 * (size_t)(maxlen + wmax + 4);
 }
 
 cudaError_t launch_sps_batch(const SpsBeam *d_beams, int nbeams,
@@ -574,7 +620,7 @@ cudaError_t launch_sps(const Plan &p, const int32_t *d_series,
                                          : max(L, nsamp_out - (nwin - 1) * L);
   const int wmax = p.widths.back();
   const size_t smem =
-      sizeof(SpsShared) + 4 * (size_t)(maxlen + wmax + 4);
+      kBufOff + 4 * (size_t)(maxlen + wmax + 4);
   static size_t attr_bytes[2] = {0, 0};
   auto kern = dense ? sps_kernel<true> : sps_kernel<false>;
   if (smem > attr_bytes[dense]) {
@@ -670,7 +716,7 @@ extern "C" int ddsp_single_pulse_search_noalloc(
   int32_t *d_err = reinterpret_cast<int32_t *>(base + kNoAllocErrOff);
 
   cudaStream_t s = (cudaStream_t)stream;
-  const size_t smem = sizeof(SpsShared) + 4 * (size_t)(maxlen + wmax + 4);
+  const size_t smem = kBufOff + 4 * (size_t)(maxlen + wmax + 4);
   auto kern = sps_kernel<false>;
   if (smem > g_noalloc_attr[dev]) {
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
