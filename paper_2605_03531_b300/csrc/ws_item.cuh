@@ -26,9 +26,8 @@
 // chunk and buffer extents, so items of different beams lay out the same
 // shared memory differently; an item starts only after every role has
 // finished the previous one, so no copy of one layout is in flight when the
-// next begins.  Every wait is bounded; a role that
-// gives up records a timeout, drains its own copies in flight (bounded) and
-// returns false.
+// next begins.  Every wait is bounded; a role that gives up records a
+// timeout, drains its own copies in flight (bounded) and returns false.
 #pragma once
 
 #include "dev_util.cuh"
