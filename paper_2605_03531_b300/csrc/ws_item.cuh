@@ -204,14 +204,22 @@ __device__ __forceinline__ bool ws_item(const WsBeam &a, int g, int64_t T0,
         uint32_t *eq = eb + q * elmax;
         const int span = rs[q * DT + DT - 1] >> 2;
         if constexpr (SPE == 4) {
+          // two groups of 4 elements per lane and step: all 8 loads are
+          // issued before the stores, so their latencies overlap (the
+          // second group's index is clamped, its store skipped, past nq)
           const int nq = (S + span + 3) >> 2;
-          for (int i4 = lane; i4 < nq; i4 += 32) {
-            const unsigned char *p = rq + 4 * i4;
-            *reinterpret_cast<uint4 *>(eq + 4 * i4) = transpose4x4(
-                *reinterpret_cast<const uint32_t *>(p),
-                *reinterpret_cast<const uint32_t *>(p + S),
-                *reinterpret_cast<const uint32_t *>(p + 2 * S),
-                *reinterpret_cast<const uint32_t *>(p + 3 * S));
+          const uint32_t *rw = reinterpret_cast<const uint32_t *>(rq);
+          constexpr int SW = S / 4;   // words per segment
+          for (int i4 = lane; i4 < nq; i4 += 64) {
+            const int i4b = min(i4 + 32, nq - 1);
+            const uint32_t a0 = rw[i4], a1 = rw[i4 + SW], a2 = rw[i4 + 2 * SW],
+                           a3 = rw[i4 + 3 * SW];
+            const uint32_t b0 = rw[i4b], b1 = rw[i4b + SW],
+                           b2 = rw[i4b + 2 * SW], b3 = rw[i4b + 3 * SW];
+            *reinterpret_cast<uint4 *>(eq + 4 * i4) = transpose4x4(a0, a1, a2, a3);
+            if (i4 + 32 < nq)
+              *reinterpret_cast<uint4 *>(eq + 4 * (i4 + 32)) =
+                  transpose4x4(b0, b1, b2, b3);
           }
         } else {
           const int nq = (S + span + 1) >> 1;
