@@ -402,13 +402,22 @@ def run_ours(args):
         os.environ["OMP_NUM_THREADS"] = str(cores)
         d = plan.delays()
         xs = x[:min(nin, 65536 + D)].cpu().numpy()
+        import oracle
+        oracle.set_threads(cores)
         rate, T, el = oracle_sample_rate(xs, d, cfg.widths, cfg.norm_window,
                                          target_s=args.cpu_seconds)
+        oracle.set_threads(1)
+        rate1, T1, el1 = oracle_sample_rate(xs, d, cfg.widths, cfg.norm_window,
+                                            target_s=max(2.0, args.cpu_seconds / 3))
+        oracle.set_threads(cores)
         result["cpu_baseline"] = {
             "value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"all {cfg.ndm} DM trials x first {T} output samples x "
                       f"{cfg.nchan} channels (dedispersion + search), "
-                      f"{el:.1f} s"}
+                      f"{el:.1f} s",
+            "single_thread": {"value": rate1, "unit": UNIT, "cores": 1,
+                              "sample": f"all {cfg.ndm} DM trials x first {T1} "
+                                        f"output samples, {el1:.1f} s"}}
     if rank == 0:
         print(json.dumps(result), flush=True)
     if world > 1:

@@ -68,6 +68,8 @@ def lib():
         L.orc_sps.restype = C.c_int64
         L.orc_sps.argtypes = [P, C.c_int, C.c_int64, P, C.c_int, C.c_int64,
                               C.c_double, P, C.c_int64]
+        L.orc_set_threads.restype = None
+        L.orc_set_threads.argtypes = [C.c_int]
         _lib = L
     return _lib
 
@@ -77,8 +79,10 @@ def _ptr(a):
 
 
 def set_threads(n: int) -> None:
-    """Number of OpenMP threads the DM loop of ``dedisperse`` may use."""
+    """Number of OpenMP threads the DM loop of ``dedisperse`` uses from now
+    on (timing only; results do not depend on it)."""
     os.environ["OMP_NUM_THREADS"] = str(int(n))
+    lib().orc_set_threads(int(n))
 
 
 def delay_table(nchan, f_top, chan_bw, tsamp, dm_list):

@@ -28,6 +28,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_K_DISP 4148.808          /* s MHz^2 per (pc cm^-3), Ch.1 Eq.1 */
 #define ORC_MAD_TO_SIGMA 1.482602218505602
@@ -310,4 +313,14 @@ int64_t orc_sps(const int32_t *series, int ndm, int64_t n, const int *widths,
     int64_t nout = count < cap ? count : cap;
     qsort(out, (size_t)nout, sizeof(orc_cand), cmp_cand);
     return count;
+}
+
+/* Number of OpenMP threads the DM loop of orc_dedisperse uses from now on
+ * (timing only; results do not depend on it). */
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
 }
