@@ -213,6 +213,133 @@ __device__ void select2(KeyFn key, int n, int r1, int r2, uint32_t kmax,
   }
 }
 
+// Exact median and MAD in one histogram pass, for windows whose middle half
+// is narrow: keys k = x - min, ranks r1 <= r2 = r1 or r1 + 1.
+//  * estimate: 32 evenly spaced keys sorted in one warp give the median and
+//    the quartiles; wide windows (estimated IQR > 1400) go to select2;
+//  * one pass counts every key in single-value bins [A, A + 2048) around
+//    the estimate and the keys below A; their prefix sums P give the two
+//    middle order statistics k1, k2 directly;
+//  * with m = k1 + k2 (= M2 - 2*min), #{|2k - m| <= v} is the number of
+//    keys in [ceil((m - v)/2), floor((m + v)/2)], a difference of two prefix
+//    sums while that range lies inside the bins; the MAD order statistics
+//    are the smallest v reaching ranks r1 + 1 and r2 + 1.
+// Returns false (the caller then uses select2) when a rank falls outside
+// the bins.  The result, when true, equals select2's.
+template <typename KeyFn>
+__device__ bool median_mad_fast(KeyFn key, int n, int r1, int r2,
+                                SpsShared &sh, uint32_t &k1, uint32_t &k2,
+                                uint32_t &u1, uint32_t &u2) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // ---- estimate
+  if (warp == 0) {
+    uint32_t v = key((int)((int64_t)lane * n / 32));
+#pragma unroll
+    for (int kk = 2; kk <= 32; kk <<= 1) {
+#pragma unroll
+      for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+        const uint32_t o = __shfl_xor_sync(0xffffffffu, v, jj);
+        const bool up = (lane & kk) == 0, low = (lane & jj) == 0;
+        v = (low == up) ? min(v, o) : max(v, o);
+      }
+    }
+    const uint32_t med = __shfl_sync(0xffffffffu, v, 16);
+    const uint32_t q1 = __shfl_sync(0xffffffffu, v, 8);
+    const uint32_t q3 = __shfl_sync(0xffffffffu, v, 24);
+    if (lane == 0) {
+      sh.bc[0] = med;
+      sh.bc[1] = (int64_t)q3 - (int64_t)q1;
+      sh.bc[2] = -1;
+      sh.bc[3] = -1;
+    }
+  }
+  for (int b = tid; b < kBins; b += kSpsThreads) sh.hist[b] = 0;
+  __syncthreads();
+  const uint32_t est = (uint32_t)sh.bc[0];
+  if (sh.bc[1] > 1400) return false;  // block-uniform
+  const uint32_t A = est > kBins / 2 ? est - kBins / 2 : 0u;
+  // ---- one pass: single-value bins [A, A + kBins) and the count below A
+  uint32_t nb = 0;
+  for (int i = tid; i < n; i += kSpsThreads) {
+    const uint32_t k = key(i);
+    if (k < A) ++nb;
+    else if (k - A < (uint32_t)kBins) atomicAdd(&sh.hist[k - A], 1u);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) nb += __shfl_xor_sync(0xffffffffu, nb, o);
+  if (lane == 0) sh.wred[warp][0] = nb;
+  __syncthreads();
+  uint32_t below = 0;
+  for (int w = 0; w < kWarps; ++w) below += sh.wred[w][0];
+  // ---- inclusive prefix P[b] = below + #{keys in [A, A + b]}, in place
+  uint32_t c[4], tsum = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    c[q] = sh.hist[4 * tid + q];
+    tsum += c[q];
+  }
+  const uint32_t inc = warp_incl_scan(tsum, lane);
+  if (lane == 31) sh.wsum[warp] = inc;
+  __syncthreads();
+  uint32_t run = below + warp_excl_offset(sh.wsum, warp, lane) + inc - tsum;
+  const uint32_t prev0 = run;  // P[4*tid - 1] (or below)
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    run += c[q];
+    c[q] = run;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < 4; ++q) sh.hist[4 * tid + q] = c[q];
+  // ---- median: the smallest b with P[b] >= r + 1
+  {
+    uint32_t pv = prev0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const uint32_t cur = c[q];
+      if (pv < (uint32_t)r1 + 1u && (uint32_t)r1 + 1u <= cur) sh.bc[2] = 4 * tid + q;
+      if (pv < (uint32_t)r2 + 1u && (uint32_t)r2 + 1u <= cur) sh.bc[3] = 4 * tid + q;
+      pv = cur;
+    }
+  }
+  __syncthreads();
+  const int64_t b1 = sh.bc[2], b2 = sh.bc[3];
+  __syncthreads();
+  if (b1 < 0 || b2 < 0) return false;  // block-uniform
+  k1 = A + (uint32_t)b1;
+  k2 = A + (uint32_t)b2;
+  if (tid == 0) {
+    sh.bc[2] = -1;
+    sh.bc[3] = -1;
+  }
+  __syncthreads();
+  // ---- MAD: C(v) = #{|2k - m| <= v}, -1 when its key range leaves the bins
+  const int64_t m = (int64_t)k1 + (int64_t)k2;
+  const int64_t lo_ok = (int64_t)A, hi_ok = (int64_t)A + kBins - 1;
+  auto count_within = [&](int64_t v) -> int64_t {
+    const int64_t lo = (m - v + 1) >> 1, hi = (m + v) >> 1;
+    if (lo < lo_ok || hi > hi_ok) return -1;
+    const int64_t ph = sh.hist[hi - lo_ok];
+    const int64_t pl = lo == lo_ok ? (int64_t)below : (int64_t)sh.hist[lo - lo_ok - 1];
+    return ph - pl;
+  };
+  for (int q = 0; q < 2 * kBins / kSpsThreads; ++q) {
+    const int64_t v = tid + (int64_t)q * kSpsThreads;
+    const int64_t cv = count_within(v);
+    if (cv < 0) continue;
+    const int64_t cp = v == 0 ? 0 : count_within(v - 1);
+    if (cp < r1 + 1 && r1 + 1 <= cv) sh.bc[2] = v;
+    if (cp < r2 + 1 && r2 + 1 <= cv) sh.bc[3] = v;
+  }
+  __syncthreads();
+  const int64_t v1 = sh.bc[2], v2 = sh.bc[3];
+  __syncthreads();
+  if (v1 < 0 || v2 < 0) return false;  // block-uniform
+  u1 = (uint32_t)v1;
+  u2 = (uint32_t)v2;
+  return true;
+}
+
 // Step 4 of the search when the widths are 1, 2, 4, ..., 2^(NW-1): the
 // offsets of the boxcar ends are compile-time, and start times whose widest
 // boxcar ends inside the series (all but the last 2^(NW-1) of a series)
@@ -359,22 +486,24 @@ __device__ __forceinline__ void sps_window(
   if (range_ok) {
     const int r1 = (len - 1) / 2, r2 = len / 2;
     const uint32_t base = (uint32_t)(int32_t)mn;
-    uint32_t k1, k2;
+    uint32_t k1, k2, u1, u2;
     // keys x - min in [0, 2^31)
-    select2([&](int i) { return (uint32_t)buf[1 + i] - base; }, len, r1, r2,
-            (uint32_t)(mx - mn), sh, k1, k2);
+    auto kx = [&](int i) { return (uint32_t)buf[1 + i] - base; };
+    const bool fast = median_mad_fast(kx, len, r1, r2, sh, k1, k2, u1, u2);
+    if (!fast)
+      select2(kx, len, r1, r2, (uint32_t)(mx - mn), sh, k1, k2);
     M2 = 2 * mn + (int64_t)k1 + (int64_t)k2;
     // |2x - M2| = |2(x - min) - (M2 - 2 min)|, both terms in [0, 2^32)
     const int64_t m2c = M2;
     const uint32_t m2r = (uint32_t)(m2c - 2 * mn);
     uint64_t umax = (uint64_t)max(2 * mx - m2c, m2c - 2 * mn);
-    uint32_t u1, u2;
-    select2(
-        [&](int i) {
-          const uint32_t t2 = 2u * ((uint32_t)buf[1 + i] - base);
-          return t2 >= m2r ? t2 - m2r : m2r - t2;
-        },
-        len, r1, r2, (uint32_t)umax, sh, u1, u2);
+    if (!fast)
+      select2(
+          [&](int i) {
+            const uint32_t t2 = 2u * ((uint32_t)buf[1 + i] - base);
+            return t2 >= m2r ? t2 - m2r : m2r - t2;
+          },
+          len, r1, r2, (uint32_t)umax, sh, u1, u2);
     MAD4 = (int64_t)u1 + (int64_t)u2;
   } else if (tid == 0) {
     atomicExch(err, kErrRange);
