@@ -28,13 +28,15 @@ namespace {
 
 constexpr int kSpsThreads = 512;
 constexpr int kWarps = kSpsThreads / 32;
-constexpr int kBins = 2048;
+constexpr int kBins = 2048;      // bins per pass of the generic selection
+constexpr int kFastBins = 4096;  // single-value bins of the one-pass path
+constexpr int kFastPer = kFastBins / kSpsThreads;
 constexpr int kMaxWidths = 11;  // 1 .. 1024
 constexpr int64_t kMaxWindowSamples = 49152;
 constexpr float kMadToSigma = 1.482602218505602f;
 
 struct SpsShared {
-  uint32_t hist[kBins];
+  uint32_t hist[kFastBins];
   uint32_t wred[kWarps][2];
   int64_t bc[4];      // broadcast slots
   float inv[kMaxWidths];
@@ -216,8 +218,8 @@ __device__ void select2(KeyFn key, int n, int r1, int r2, uint32_t kmax,
 // Exact median and MAD in one histogram pass, for windows whose middle half
 // is narrow: keys k = x - min, ranks r1 <= r2 = r1 or r1 + 1.
 //  * estimate: 32 evenly spaced keys sorted in one warp give the median and
-//    the quartiles; wide windows (estimated IQR > 1400) go to select2;
-//  * one pass counts every key in single-value bins [A, A + 2048) around
+//    the quartiles; wide windows (estimated IQR > 2800) go to select2;
+//  * one pass counts every key in single-value bins [A, A + 4096) around
 //    the estimate and the keys below A; their prefix sums P give the two
 //    middle order statistics k1, k2 directly;
 //  * with m = k1 + k2 (= M2 - 2*min), #{|2k - m| <= v} is the number of
@@ -253,17 +255,17 @@ __device__ bool median_mad_fast(KeyFn key, int n, int r1, int r2,
       sh.bc[3] = -1;
     }
   }
-  for (int b = tid; b < kBins; b += kSpsThreads) sh.hist[b] = 0;
+  for (int b = tid; b < kFastBins; b += kSpsThreads) sh.hist[b] = 0;
   __syncthreads();
   const uint32_t est = (uint32_t)sh.bc[0];
-  if (sh.bc[1] > 1400) return false;  // block-uniform
-  const uint32_t A = est > kBins / 2 ? est - kBins / 2 : 0u;
-  // ---- one pass: single-value bins [A, A + kBins) and the count below A
+  if (sh.bc[1] > 2800) return false;  // block-uniform
+  const uint32_t A = est > kFastBins / 2 ? est - kFastBins / 2 : 0u;
+  // ---- one pass: single-value bins [A, A + kFastBins) and the count below A
   uint32_t nb = 0;
   for (int i = tid; i < n; i += kSpsThreads) {
     const uint32_t k = key(i);
     if (k < A) ++nb;
-    else if (k - A < (uint32_t)kBins) atomicAdd(&sh.hist[k - A], 1u);
+    else if (k - A < (uint32_t)kFastBins) atomicAdd(&sh.hist[k - A], 1u);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) nb += __shfl_xor_sync(0xffffffffu, nb, o);
@@ -272,33 +274,33 @@ __device__ bool median_mad_fast(KeyFn key, int n, int r1, int r2,
   uint32_t below = 0;
   for (int w = 0; w < kWarps; ++w) below += sh.wred[w][0];
   // ---- inclusive prefix P[b] = below + #{keys in [A, A + b]}, in place
-  uint32_t c[4], tsum = 0;
+  uint32_t c[kFastPer], tsum = 0;
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    c[q] = sh.hist[4 * tid + q];
+  for (int q = 0; q < kFastPer; ++q) {
+    c[q] = sh.hist[kFastPer * tid + q];
     tsum += c[q];
   }
   const uint32_t inc = warp_incl_scan(tsum, lane);
   if (lane == 31) sh.wsum[warp] = inc;
   __syncthreads();
   uint32_t run = below + warp_excl_offset(sh.wsum, warp, lane) + inc - tsum;
-  const uint32_t prev0 = run;  // P[4*tid - 1] (or below)
+  const uint32_t prev0 = run;  // P[kFastPer*tid - 1] (or below)
 #pragma unroll
-  for (int q = 0; q < 4; ++q) {
+  for (int q = 0; q < kFastPer; ++q) {
     run += c[q];
     c[q] = run;
   }
   __syncthreads();
 #pragma unroll
-  for (int q = 0; q < 4; ++q) sh.hist[4 * tid + q] = c[q];
+  for (int q = 0; q < kFastPer; ++q) sh.hist[kFastPer * tid + q] = c[q];
   // ---- median: the smallest b with P[b] >= r + 1
   {
     uint32_t pv = prev0;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < kFastPer; ++q) {
       const uint32_t cur = c[q];
-      if (pv < (uint32_t)r1 + 1u && (uint32_t)r1 + 1u <= cur) sh.bc[2] = 4 * tid + q;
-      if (pv < (uint32_t)r2 + 1u && (uint32_t)r2 + 1u <= cur) sh.bc[3] = 4 * tid + q;
+      if (pv < (uint32_t)r1 + 1u && (uint32_t)r1 + 1u <= cur) sh.bc[2] = kFastPer * tid + q;
+      if (pv < (uint32_t)r2 + 1u && (uint32_t)r2 + 1u <= cur) sh.bc[3] = kFastPer * tid + q;
       pv = cur;
     }
   }
@@ -315,7 +317,7 @@ __device__ bool median_mad_fast(KeyFn key, int n, int r1, int r2,
   __syncthreads();
   // ---- MAD: C(v) = #{|2k - m| <= v}, -1 when its key range leaves the bins
   const int64_t m = (int64_t)k1 + (int64_t)k2;
-  const int64_t lo_ok = (int64_t)A, hi_ok = (int64_t)A + kBins - 1;
+  const int64_t lo_ok = (int64_t)A, hi_ok = (int64_t)A + kFastBins - 1;
   auto count_within = [&](int64_t v) -> int64_t {
     const int64_t lo = (m - v + 1) >> 1, hi = (m + v) >> 1;
     if (lo < lo_ok || hi > hi_ok) return -1;
@@ -323,13 +325,30 @@ __device__ bool median_mad_fast(KeyFn key, int n, int r1, int r2,
     const int64_t pl = lo == lo_ok ? (int64_t)below : (int64_t)sh.hist[lo - lo_ok - 1];
     return ph - pl;
   };
-  for (int q = 0; q < 2 * kBins / kSpsThreads; ++q) {
-    const int64_t v = tid + (int64_t)q * kSpsThreads;
-    const int64_t cv = count_within(v);
-    if (cv < 0) continue;
-    const int64_t cp = v == 0 ? 0 : count_within(v - 1);
-    if (cp < r1 + 1 && r1 + 1 <= cv) sh.bc[2] = v;
-    if (cp < r2 + 1 && r2 + 1 <= cv) sh.bc[3] = v;
+  // C is non-decreasing in v and valid on a prefix of [0, 2 * kFastBins),
+  // so the smallest v with C(v) >= R is found by one warp in three 32-way
+  // steps of widths 256, 8 and 1, each lane testing the last v of its part.
+  static_assert(2 * kFastBins == 32 * 256, "MAD search covers [0, 8192)");
+  if (warp == 0) {
+#pragma unroll
+    for (int which = 0; which < 2; ++which) {
+      const int64_t R = (int64_t)(which ? r2 : r1) + 1;
+      int64_t base = 0;
+      bool found = true;
+#pragma unroll
+      for (int st = 0; st < 3; ++st) {
+        const int64_t w = st == 0 ? 256 : (st == 1 ? 8 : 1);
+        const int nl = st == 2 ? 8 : 32;
+        const int64_t cv = lane < nl ? count_within(base + lane * w + w - 1) : -1;
+        const unsigned hit = __ballot_sync(0xffffffffu, cv >= R);
+        if (hit == 0u) {   // warp-uniform: only possible in the first step
+          found = false;
+          break;
+        }
+        base += (int64_t)(__ffs(hit) - 1) * w;
+      }
+      if (lane == 0) sh.bc[2 + which] = found ? base : -1;
+    }
   }
   __syncthreads();
   const int64_t v1 = sh.bc[2], v2 = sh.bc[3];

@@ -204,23 +204,25 @@ __device__ __forceinline__ bool ws_item(const WsBeam &a, int g, int64_t T0,
         uint32_t *eq = eb + q * elmax;
         const int span = rs[q * DT + DT - 1] >> 2;
         if constexpr (SPE == 4) {
-          // two groups of 4 elements per lane and step: all 8 loads are
-          // issued before the stores, so their latencies overlap (the
-          // second group's index is clamped, its store skipped, past nq)
+          // groups of 4 elements: lane l takes groups l + 64m and
+          // l + 64m + 32 per step, all 8 loads issued before the stores so
+          // their latencies overlap; a lone last group is done after the
+          // loop.  Loads and stores use fixed offsets from two running
+          // pointers.
           const int nq = (S + span + 3) >> 2;
-          const uint32_t *rw = reinterpret_cast<const uint32_t *>(rq);
           constexpr int SW = S / 4;   // words per segment
-          for (int i4 = lane; i4 < nq; i4 += 64) {
-            const int i4b = min(i4 + 32, nq - 1);
-            const uint32_t a0 = rw[i4], a1 = rw[i4 + SW], a2 = rw[i4 + 2 * SW],
-                           a3 = rw[i4 + 3 * SW];
-            const uint32_t b0 = rw[i4b], b1 = rw[i4b + SW],
-                           b2 = rw[i4b + 2 * SW], b3 = rw[i4b + 3 * SW];
-            *reinterpret_cast<uint4 *>(eq + 4 * i4) = transpose4x4(a0, a1, a2, a3);
-            if (i4 + 32 < nq)
-              *reinterpret_cast<uint4 *>(eq + 4 * (i4 + 32)) =
-                  transpose4x4(b0, b1, b2, b3);
+          const uint32_t *rw = reinterpret_cast<const uint32_t *>(rq) + lane;
+          uint4 *ev = reinterpret_cast<uint4 *>(eq) + lane;
+          int i4 = lane;
+          for (; i4 + 32 < nq; i4 += 64, rw += 64, ev += 64) {
+            const uint32_t a0 = rw[0], a1 = rw[SW], a2 = rw[2 * SW],
+                           a3 = rw[3 * SW];
+            const uint32_t b0 = rw[32], b1 = rw[32 + SW], b2 = rw[32 + 2 * SW],
+                           b3 = rw[32 + 3 * SW];
+            ev[0] = transpose4x4(a0, a1, a2, a3);
+            ev[32] = transpose4x4(b0, b1, b2, b3);
           }
+          if (i4 < nq) ev[0] = transpose4x4(rw[0], rw[SW], rw[2 * SW], rw[3 * SW]);
         } else {
           const int nq = (S + span + 1) >> 1;
           for (int i2 = lane; i2 < nq; i2 += 32) {

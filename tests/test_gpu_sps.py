@@ -153,6 +153,59 @@ def test_candidates_c1_series():
                         cfg.widths, cfg.norm_window)
 
 
+def _stats_match(x, L):
+    p = _plan(x.shape[0], [1, 2, 4], L)
+    p.single_pulse_search(torch.from_numpy(x).cuda(), 1e6)
+    m2, mad4 = p.stats()
+    for k in range(x.shape[0]):
+        rm2, rmad4 = oracle.window_stats(x[k], L)
+        assert np.array_equal(m2[k], rm2), ("median", k)
+        assert np.array_equal(mad4[k], rmad4), ("mad", k)
+
+
+def test_window_stats_across_spreads():
+    """Gaussian windows whose middle half is far narrower, near, and far wider
+    than the single-value bins of the one-pass median, and windows whose
+    whole range sits near the series minimum: bit-exact against the oracle."""
+    L, n = 8192, 3 * 8192 + 1001
+    rows = [synth.gaussian_series(2, n, seed=60 + i, mean=m, sd=sd,
+                                  event_rate=0.0).numpy()
+            for i, (m, sd) in enumerate([(0.0, 3.0), (1000.0, 300.0),
+                                         (5e5, 1024.0), (5e5, 2000.0),
+                                         (5e5, 2100.0), (5e5, 2300.0),
+                                         (5e5, 5000.0), (-7e8, 4e7)])]
+    _stats_match(np.concatenate(rows), L)
+
+
+def test_window_stats_misleading_estimate():
+    """Rows built so that an estimate from 32 evenly spaced samples of each
+    window is wrong: (a) the sampled positions hold 0 and the rest of the
+    window lies 10^4 above, so the median leaves any bin range centred on
+    the estimate; (b) thirds at -6000, 0 and +6000 with the sampled positions
+    at 0, so the median is right but the MAD (6000) is far outside; (c) two
+    equal halves 2000 apart (median between them, every deviation 1000)."""
+    L, n = 8192, 3 * 8192 + 1000     # even-length windows
+    nwin = oracle.num_windows(n, L)
+    noise = synth.gaussian_series(3, n, seed=77, mean=0.0, sd=2.0,
+                                  event_rate=0.0).numpy()
+    x = np.zeros((3, n), np.int32)
+    t = np.arange(n)
+    x[0] = 10000 + noise[0]
+    x[1] = np.where(t % 3 == 0, -6000, np.where(t % 3 == 1, 0, 6000)) + noise[1]
+    x[2] = np.where(t % 2 == 0, 0, 2000)
+    for j in range(nwin):
+        lo, hi = oracle.window_bounds(n, L, j)
+        pos = lo + (np.arange(32, dtype=np.int64) * (hi - lo)) // 32
+        x[0, pos] = 0
+        x[1, pos] = noise[1, pos]
+    _stats_match(x, L)
+    # the planted structure really is what the docstring says
+    m2, mad4 = oracle.window_stats(x[1], L)
+    assert (np.abs(m2) <= 8).all() and (mad4 >= 4 * 5990).all()
+    m2, mad4 = oracle.window_stats(x[2], L)
+    assert (m2 == 2000).all() and (mad4 == 4000).all()
+
+
 def test_mad_zero_gives_no_candidates():
     x = np.full((3, 20000), 7, np.int32)
     x[1, 5000] = 10 ** 6
