@@ -4,12 +4,14 @@
 //
 //   1. load the window x[lo, hi) plus (w_max - 1) samples of look-ahead into
 //      shared memory (the series is read from HBM once);
-//   2. exact median and MAD of the window by histogram selection on integer
-//      keys: a 2048-bin shared histogram over the current key range narrows
-//      it by 2^11 per pass until the bin holding the wanted order statistic
-//      is one key wide (or the two middle order statistics fall in different
-//      bins: then max of the lower bin and min of the upper bin);
-//      m2 = 2*median, mad4 = 4*MAD are kept as exact integers;
+//   2. exact median and MAD of the window on integer keys: in one pass of
+//      4096 single-value bins around an estimate from 32 sorted samples
+//      when the window's middle half is narrow (median_mad_fast), else by
+//      histogram selection: a 2048-bin shared histogram over the current
+//      key range narrows it by 2^11 per pass until the bin holding the
+//      wanted order statistic is one key wide (or the two middle order
+//      statistics fall in different bins: then max of the lower bin and min
+//      of the upper bin); m2 = 2*median, mad4 = 4*MAD are exact integers;
 //   3. y = x - floor(median) and an inclusive prefix sum Q of y in uint32
 //      (modular, so every boxcar sum B_w(t) - w*floor(median) = Q[t+w]-Q[t]
 //      is exact), computed with warp-shuffle scans;
