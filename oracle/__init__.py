@@ -12,7 +12,10 @@ the passage of the paper its C function writes out:
 * ``delay_table``   -- dispersion delay law, Ch.1 Eq.1;
 * ``dedisperse``    -- brute-force shift-and-sum, Sec.3.2;
 * ``window_stats``  -- median / MAD noise estimate, Sec.3.3;
-* ``boxcar``, ``sps`` -- boxcar single-pulse search above a threshold, Sec.2.1.
+* ``boxcar``, ``sps`` -- boxcar single-pulse search above a threshold, Sec.2.1;
+* ``peaks``, ``dbscan``, ``cluster_reps``, ``peaks_cluster`` -- peaks
+  filtering with square DM-time stencils, DBSCAN clustering in the DM-time
+  plane and the strongest candidate of each cluster, Sec.2.1.
 """
 import ctypes as C
 import os
@@ -68,6 +71,12 @@ def lib():
         L.orc_sps.restype = C.c_int64
         L.orc_sps.argtypes = [P, C.c_int, C.c_int64, P, C.c_int, C.c_int64,
                               C.c_double, P, C.c_int64]
+        L.orc_peaks.restype = C.c_int
+        L.orc_peaks.argtypes = [P, P, P, P, C.c_int64, P, C.c_int, P, C.c_int64, P]
+        L.orc_dbscan.restype = C.c_int
+        L.orc_dbscan.argtypes = [P, P, C.c_int64, C.c_int64, C.c_int64, C.c_int64, P]
+        L.orc_cluster_reps.restype = None
+        L.orc_cluster_reps.argtypes = [P, P, C.c_int64, P]
         L.orc_set_threads.restype = None
         L.orc_set_threads.argtypes = [C.c_int]
         _lib = L
@@ -225,3 +234,76 @@ def sps(series, widths, L, thr, cap=None):
     cnt = lib().orc_sps(_ptr(series), ndm, n, _ptr(ws), ws.size, int(L),
                         float(thr), _ptr(out), int(cap))
     return out[:min(cnt, cap)].copy(), int(cnt)
+
+
+# ------------------------------------------------ peaks filtering, clustering
+# Candidate records as the search emits them: FP32 S/N, so both sides take
+# every comparison on the same values.
+CAND32_DTYPE = np.dtype([("dm_idx", np.uint32), ("t", np.uint32),
+                         ("w_idx", np.uint32), ("snr", np.float32)])
+
+
+def _cand_fields(c):
+    c = np.ascontiguousarray(c)
+    return (np.ascontiguousarray(c["dm_idx"], dtype=np.uint32),
+            np.ascontiguousarray(c["t"], dtype=np.uint32),
+            np.ascontiguousarray(c["w_idx"], dtype=np.uint32),
+            np.ascontiguousarray(c["snr"], dtype=np.float32))
+
+
+def peaks(cands, half, idx=None):
+    """Keep flags of the peaks filter (Sec.2.1, square stencils of half-size
+    half[w_idx]), for every candidate or for the indices ``idx``."""
+    k, t, w, s = _cand_fields(cands)
+    hf = np.ascontiguousarray(half, dtype=np.int32)
+    n = k.size
+    if idx is None:
+        m, ip = n, None
+    else:
+        idx = np.ascontiguousarray(idx, dtype=np.int64)
+        m, ip = idx.size, _ptr(idx)
+    keep = np.zeros(max(m, 1), dtype=np.uint8)
+    rc = lib().orc_peaks(_ptr(k), _ptr(t), _ptr(w), _ptr(s), n, _ptr(hf),
+                         hf.size, ip, m, _ptr(keep))
+    if rc != 0:
+        raise ValueError("width index or stencil size out of range")
+    return keep[:m].astype(bool)
+
+
+def dbscan(k, t, eps_dm, eps_t, min_pts):
+    """DBSCAN labels of points sorted by (k, t): the sorted index of the point
+    that started each cluster, -1 for noise."""
+    k = np.ascontiguousarray(k, dtype=np.uint32)
+    t = np.ascontiguousarray(t, dtype=np.uint32)
+    lab = np.empty(max(k.size, 1), dtype=np.int64)
+    rc = lib().orc_dbscan(_ptr(k), _ptr(t), k.size, int(eps_dm), int(eps_t),
+                          int(min_pts), _ptr(lab))
+    if rc != 0:
+        raise ValueError("points not sorted and distinct, or bad parameters")
+    return lab[:k.size]
+
+
+def cluster_reps(labels, snr):
+    """rep[c]: index of the strongest point with label c (ties to the smaller
+    index), -1 where c is not a label."""
+    labels = np.ascontiguousarray(labels, dtype=np.int64)
+    snr = np.ascontiguousarray(snr, dtype=np.float32)
+    rep = np.empty(max(labels.size, 1), dtype=np.int64)
+    lib().orc_cluster_reps(_ptr(labels), _ptr(snr), labels.size, _ptr(rep))
+    return rep[:labels.size]
+
+
+def peaks_cluster(cands, half, eps_dm, eps_t, min_pts):
+    """The whole step of Sec.2.1 after the search: peaks filtering, the kept
+    candidates sorted by (dm_idx, t), DBSCAN labels of those, and the index
+    (into the sorted peaks) of each cluster's strongest member, clusters in
+    increasing label order.  Returns (peaks, labels, reps)."""
+    cands = np.ascontiguousarray(cands)
+    keep = peaks(cands, half)
+    kept = cands[keep]
+    order = np.lexsort((kept["t"], kept["dm_idx"]))
+    pk = kept[order]
+    labels = dbscan(pk["dm_idx"], pk["t"], eps_dm, eps_t, min_pts)
+    rep = cluster_reps(labels, pk["snr"])
+    reps = rep[rep >= 0]
+    return pk, labels, reps

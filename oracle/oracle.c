@@ -16,7 +16,10 @@
  *   - window statistics: median and median absolute deviation, Sec.3.3
  *                        (median preferred for robustness to outliers);
  *   - boxcar S/N search: time-domain boxcar filtering above a user threshold,
- *                        Sec.2.1.
+ *                        Sec.2.1;
+ *   - peaks filtering and clustering of the candidates: square DM-time
+ *                        stencils, then DBSCAN in the DM-time plane keeping
+ *                        the strongest candidate of each cluster, Sec.2.1.
  * Readings where the paper is silent (channel frequencies, output length,
  * boxcar alignment, window layout, even-count median, MAD = 0) are listed at
  * each function.
@@ -313,6 +316,142 @@ int64_t orc_sps(const int32_t *series, int ndm, int64_t n, const int *widths,
     int64_t nout = count < cap ? count : cap;
     qsort(out, (size_t)nout, sizeof(orc_cand), cmp_cand);
     return count;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Peaks filtering (Sec.2.1): redundant candidates of one event are removed   */
+/* with square stencils of different sizes in the DM-time plane.              */
+/* Reading: the stencil of candidate i is the square |k - k_i| <= h,          */
+/* |t - t_i| <= h (trial index and sample units) whose half-size              */
+/* h = half[w_i] is set by the candidate's boxcar width; i is kept iff no     */
+/* other candidate j inside its square is stronger: s_j > s_i, or s_j == s_i  */
+/* and (k_j, t_j) precedes (k_i, t_i).  S/N values are compared exactly as    */
+/* given (FP32, the search's output).  The (k, t) pairs must be distinct.     */
+/* Direct loop over all other candidates for each decided one; idx lists the  */
+/* candidates to decide (NULL: all n, m = n) and keep[q] answers for idx[q].  */
+/* Returns -1 on a width index outside [0, nw) or a negative half-size.       */
+/* ------------------------------------------------------------------------ */
+static int orc_stronger(uint32_t kj, uint32_t tj, float sj, uint32_t ki,
+                        uint32_t ti, float si)
+{
+    if (sj != si) return sj > si;
+    return kj < ki || (kj == ki && tj < ti);
+}
+
+int orc_peaks(const uint32_t *k, const uint32_t *t, const uint32_t *w,
+              const float *s, int64_t n, const int32_t *half, int nw,
+              const int64_t *idx, int64_t m, uint8_t *keep)
+{
+    for (int64_t q = 0; q < m; ++q) {
+        int64_t i = idx ? idx[q] : q;
+        if (i < 0 || i >= n || w[i] >= (uint32_t)nw || half[w[i]] < 0) return -1;
+        int64_t h = half[w[i]];
+        int kept = 1;
+        for (int64_t j = 0; j < n && kept; ++j) {
+            if (j == i) continue;
+            int64_t dk = (int64_t)k[j] - (int64_t)k[i];
+            int64_t dt = (int64_t)t[j] - (int64_t)t[i];
+            if (dk < -h || dk > h || dt < -h || dt > h) continue;
+            if (orc_stronger(k[j], t[j], s[j], k[i], t[i], s[i])) kept = 0;
+        }
+        keep[q] = (uint8_t)kept;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* DBSCAN (density-based clustering, Ester et al. 1996) of the filtered       */
+/* candidates in the DM-time plane (the clustering step of Sec.2.1).          */
+/* Reading: the neighbourhood of point p is every point q with                */
+/* |k_q - k_p| <= eps_dm and |t_q - t_p| <= eps_t, p itself included; p is a  */
+/* core point if its neighbourhood holds >= min_pts points.  Points, sorted   */
+/* by (k, t), are visited in that order.  An unvisited core point starts a    */
+/* new cluster, expanded breadth-first: every point reached that is not yet   */
+/* in a cluster joins it, and the neighbourhoods of the core points reached   */
+/* are expanded in turn.  Border points therefore keep the first cluster that */
+/* reaches them; points no cluster reaches are noise (label -1).  A cluster's */
+/* label is the sorted index of the point that started it (its first core     */
+/* point).  Region queries are linear scans.                                  */
+/* Returns -1 if the points are not sorted by (k, t) and distinct, or if      */
+/* eps_dm, eps_t < 0 or min_pts < 1; 0 otherwise.                             */
+/* ------------------------------------------------------------------------ */
+static int orc_near(const uint32_t *k, const uint32_t *t, int64_t p, int64_t q,
+                    int64_t eps_dm, int64_t eps_t)
+{
+    int64_t dk = (int64_t)k[q] - (int64_t)k[p];
+    int64_t dt = (int64_t)t[q] - (int64_t)t[p];
+    return dk >= -eps_dm && dk <= eps_dm && dt >= -eps_t && dt <= eps_t;
+}
+
+static int64_t orc_region_count(const uint32_t *k, const uint32_t *t, int64_t n,
+                                int64_t p, int64_t eps_dm, int64_t eps_t)
+{
+    int64_t c = 0;
+    for (int64_t q = 0; q < n; ++q) c += orc_near(k, t, p, q, eps_dm, eps_t);
+    return c;
+}
+
+int orc_dbscan(const uint32_t *k, const uint32_t *t, int64_t n, int64_t eps_dm,
+               int64_t eps_t, int64_t min_pts, int64_t *label)
+{
+    const int64_t UNSET = -2, NOISE = -1;
+    if (eps_dm < 0 || eps_t < 0 || min_pts < 1 || n < 0) return -1;
+    for (int64_t i = 1; i < n; ++i)
+        if (k[i] < k[i - 1] || (k[i] == k[i - 1] && t[i] <= t[i - 1])) return -1;
+    uint8_t *visited = (uint8_t *)calloc((size_t)(n > 0 ? n : 1), 1);
+    int64_t *pushed = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+    int64_t *queue = (int64_t *)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+    for (int64_t i = 0; i < n; ++i) { label[i] = UNSET; pushed[i] = -1; }
+    for (int64_t p = 0; p < n; ++p) {
+        if (visited[p]) continue;
+        visited[p] = 1;
+        if (orc_region_count(k, t, n, p, eps_dm, eps_t) < min_pts) {
+            label[p] = NOISE;            /* may become a border point later */
+            continue;
+        }
+        const int64_t c = p;             /* a new cluster, labelled by p */
+        label[p] = c;
+        int64_t qh = 0, qt = 0;
+        pushed[p] = c;
+        for (int64_t q = 0; q < n; ++q)
+            if (pushed[q] != c && orc_near(k, t, p, q, eps_dm, eps_t)) {
+                pushed[q] = c;
+                queue[qt++] = q;
+            }
+        while (qh < qt) {
+            int64_t q = queue[qh++];
+            if (label[q] == UNSET || label[q] == NOISE) label[q] = c;
+            if (visited[q]) continue;
+            visited[q] = 1;
+            if (orc_region_count(k, t, n, q, eps_dm, eps_t) < min_pts) continue;
+            for (int64_t r = 0; r < n; ++r)
+                if (pushed[r] != c && orc_near(k, t, q, r, eps_dm, eps_t)) {
+                    pushed[r] = c;
+                    queue[qt++] = r;
+                }
+        }
+    }
+    for (int64_t i = 0; i < n; ++i)
+        if (label[i] == UNSET) label[i] = NOISE;
+    free(visited);
+    free(pushed);
+    free(queue);
+    return 0;
+}
+
+/* The strongest member of every cluster (Sec.2.1 keeps the highest-S/N       */
+/* candidate of each cluster): rep[c] = the point with label c and the        */
+/* largest S/N, ties to the smaller sorted index; rep[c] = -1 for every c     */
+/* in [0, n) that is not a label.                                             */
+void orc_cluster_reps(const int64_t *label, const float *s, int64_t n,
+                      int64_t *rep)
+{
+    for (int64_t c = 0; c < n; ++c) rep[c] = -1;
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t c = label[i];
+        if (c < 0) continue;
+        if (rep[c] < 0 || s[i] > s[rep[c]]) rep[c] = i;
+    }
 }
 
 /* Number of OpenMP threads the DM loop of orc_dedisperse uses from now on

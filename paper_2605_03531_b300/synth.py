@@ -396,3 +396,85 @@ def config5(nbeams=64, seed=5):
             seed=seed * 100000 + b)
         beams.append(cfg)
     return beams
+
+
+# ------------------------------------------------- single-pulse candidate lists
+CAND_DTYPE = np.dtype([("dm_idx", np.uint32), ("t", np.uint32),
+                       ("w_idx", np.uint32), ("snr", np.float32)])
+
+
+def candidate_list(ndm, nsamp, nwidths, n_events, seed, thr=6.5,
+                   snr_range=(8.0, 50.0), dm_half=(1, 40), t_half=(1, 256),
+                   noise=0, quantum=0.0):
+    """Seeded single-pulse candidate records in the DM-time plane, shaped
+    like a search's output for the peaks filter and the clustering stage.
+
+    Event e (stream ``seed``, counters e*8 ..): centre (k_e, t_e) uniform on
+    the plane, peak S/N S_e uniform in ``snr_range``, half extents a_e trials
+    and b_e samples log-uniform in ``dm_half`` / ``t_half``, width index w_e
+    uniform.  It yields a record at every (k, t) of its rectangle whose
+    S/N = S_e * (1 - |dk|/(a_e+1)) * (1 - |dt|/(b_e+1)) reaches ``thr``, with
+    width index w_e where |dt| <= b_e/2, else max(w_e - 1, 0).  ``quantum`` >
+    0 rounds every S/N to a multiple of it (exact ties between neighbours).
+    ``noise`` isolated records (stream seed+1) sit uniformly on the plane
+    with S/N thr + 0.5*Exp(1).  Where records meet at one (k, t) the one
+    with the largest S/N stays (then the first made).  The records come back
+    in a seeded random order (stream seed+2), as an unordered search
+    emits them."""
+    parts_k, parts_t, parts_w, parts_s = [], [], [], []
+    if n_events > 0:
+        u = uniform_np(np.arange(8 * n_events, dtype=np.uint64),
+                       seed).reshape(n_events, 8)
+        for e in range(n_events):
+            ke = int(u[e, 0] * ndm)
+            te = int(u[e, 1] * nsamp)
+            se = snr_range[0] + u[e, 2] * (snr_range[1] - snr_range[0])
+            a = int(round(math.exp(math.log(dm_half[0]) + u[e, 3] *
+                                   (math.log(dm_half[1]) - math.log(dm_half[0])))))
+            b = int(round(math.exp(math.log(t_half[0]) + u[e, 4] *
+                                   (math.log(t_half[1]) - math.log(t_half[0])))))
+            we = min(int(u[e, 5] * nwidths), nwidths - 1)
+            dk = np.arange(-a, a + 1)
+            dt = np.arange(-b, b + 1)
+            kk = ke + dk[:, None] + 0 * dt[None, :]
+            tt = te + dt[None, :] + 0 * dk[:, None]
+            sn = (se * (1.0 - np.abs(dk)[:, None] / (a + 1.0))
+                  * (1.0 - np.abs(dt)[None, :] / (b + 1.0)))
+            ww = np.where(np.abs(dt)[None, :] + 0 * dk[:, None] <= b // 2, we,
+                          max(we - 1, 0))
+            m = (kk >= 0) & (kk < ndm) & (tt >= 0) & (tt < nsamp) & (sn >= thr)
+            parts_k.append(kk[m])
+            parts_t.append(tt[m])
+            parts_w.append(ww[m])
+            parts_s.append(sn[m])
+    if noise > 0:
+        u = uniform_np(np.arange(4 * noise, dtype=np.uint64),
+                       seed + 1).reshape(noise, 4)
+        parts_k.append((u[:, 0] * ndm).astype(np.int64))
+        parts_t.append((u[:, 1] * nsamp).astype(np.int64))
+        parts_w.append(np.minimum((u[:, 2] * nwidths).astype(np.int64),
+                                  nwidths - 1))
+        parts_s.append(thr - 0.5 * np.log1p(-u[:, 3]))
+    if not parts_k:
+        return np.zeros(0, dtype=CAND_DTYPE)
+    k = np.concatenate(parts_k).astype(np.int64)
+    t = np.concatenate(parts_t).astype(np.int64)
+    w = np.concatenate(parts_w).astype(np.int64)
+    s = np.concatenate(parts_s)
+    if quantum > 0:
+        s = np.round(s / quantum) * quantum
+    s32 = s.astype(np.float32)
+    # one record per (k, t): the strongest, then the first made
+    key = k * nsamp + t
+    order = np.lexsort((np.arange(key.size), -s32.astype(np.float64), key))
+    first = np.ones(order.size, dtype=bool)
+    first[1:] = key[order][1:] != key[order][:-1]
+    sel = order[first]
+    out = np.empty(sel.size, dtype=CAND_DTYPE)
+    out["dm_idx"] = k[sel]
+    out["t"] = t[sel]
+    out["w_idx"] = w[sel]
+    out["snr"] = s32[sel]
+    perm = np.argsort(splitmix64_np(np.arange(sel.size, dtype=np.uint64),
+                                    seed + 2), kind="stable")
+    return out[perm]
