@@ -496,6 +496,146 @@ def run_sps(args):
     return 0
 
 
+# ------------------------------------------- peaks filter + DM-time clustering
+CLUSTER_METRIC = "single-pulse candidates filtered and clustered/s"
+CLUSTER_HALF = [1, 2, 4, 8, 16, 32, 64, 128, 256]   # stencil = boxcar width
+CLUSTER_EPS = (4, 32, 3)                            # eps_dm, eps_t, min_pts
+
+
+def cluster_candidates(seed):
+    """The beam's DM-time plane (1024 trials x 262144 samples, its 9 widths)
+    with 3000 events (half extents 1-30 trials x 1-120 samples, peak S/N
+    8-50, S/N on a 1/128 grid) and 200000 isolated noise candidates: about
+    110 times the list one search of the beam block emits."""
+    from paper_2605_03531_b300 import synth
+    return synth.candidate_list(1024, 262144, len(CLUSTER_HALF), 3000, seed,
+                                dm_half=(1, 30), t_half=(1, 120), noise=200000,
+                                quantum=1 / 128)
+
+
+def cluster_config(n):
+    return {"workload": "peaks filter (square stencils, half-size = boxcar "
+                        "width) + DBSCAN (4 trials x 32 samples, min_pts 3) of "
+                        f"{n} single-pulse candidates on the beam's 1024 x "
+                        "262144 DM-time plane (3000 events + 200000 noise)",
+            "candidates": int(n), "ndm": 1024, "nsamp": 262144,
+            "l2": "flushed between steps (256 MB write, outside the timed "
+                  "intervals)"}
+
+
+def cluster_oracle_rate(c, target_s):
+    """Oracle candidates/s on the candidates of the first R DM trials taken
+    as a list of their own, R sized to about target_s seconds (the filter
+    is quadratic in the list size)."""
+    import oracle
+    R, el, m = 4, 0.0, 0
+    for _ in range(3):
+        sub = c[c["dm_idx"] < R]
+        t0 = time.perf_counter()
+        oracle.peaks_cluster(sub, CLUSTER_HALF, *CLUSTER_EPS)
+        el, m = time.perf_counter() - t0, sub.size
+        if el > 0.5 * target_s or R >= 1024:
+            break
+        R = int(min(1024, max(R + 1, R * (target_s / max(el, 1e-3)) ** 0.5)))
+    return m / el, R, m, el
+
+
+def run_cluster(args):
+    import torch
+    from paper_2605_03531_b300 import Cluster, build, shard
+    build.build()
+    world, rank, local = dist_setup(args.gpus)
+    dev = torch.device("cuda", local if world > 1 else 0)
+    c = cluster_candidates(shard.rank_seed(6, rank))
+    n = c.size
+    d = Cluster.to_device(c, dev)
+    cl = Cluster(1024, 262144, n, device=dev.index or 0)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(64 << 20, dtype=torch.int32, device=dev)
+
+    def step():
+        cl.run(d, CLUSTER_HALF, *CLUSTER_EPS, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(dev.index or 0)
+    if not args.profile:
+        clocks.start()
+        time.sleep(0.3)
+    barrier(world)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    for e0, e1 in evs:
+        flush.fill_(1)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ck = clocks.stop()
+    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in evs) / args.steps, world)
+    peaks_n = cl.peaks()[0].size
+    reps, _ = cl.reps()
+    # end to end through the public calls: records from pinned host memory,
+    # the run, the representatives back on the host
+    ch = torch.from_numpy(np.ascontiguousarray(c).view(np.int32).reshape(-1, 4).copy())
+    ch = ch.pin_memory()
+
+    def e2e_step():
+        d.copy_(ch, non_blocking=True)
+        step()
+        return cl.reps()[0].size
+
+    e2e_step()
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        nr = e2e_step()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world) / args.steps
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm = peaks.get("hbm_gbs", 6400.0)
+    nbytes = 16.0 * n + 20.0 * peaks_n
+    achieved = nbytes / (ms * 1e-3) / 1e9
+    result = None
+    if rank == 0:
+        result = {
+            "metric": CLUSTER_METRIC, "value": world * n / (ms * 1e-3),
+            "unit": "candidates/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32+f32",
+            "data": "synthetic", "config": cluster_config(n),
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm,
+                         "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                         "kernel": "ddsp_peaks_cluster (all 24 launches of the "
+                                   "step, timed together)",
+                         "bytes_basis": "16 B per input record read once + 20 B "
+                                        "per peak (record + label) written"},
+            "peaks_per_step": int(peaks_n), "clusters_per_step": int(reps.size),
+            "e2e": {"value": world * n / e2e_s, "unit": "candidates/s",
+                    "h2d_bytes_per_step": int(16 * n),
+                    "d2h_bytes_per_step": int(16 * nr + 16),
+                    "ms_per_step": e2e_s * 1e3},
+            "gpu_launches": 24 * args.steps, "clocks": ck,
+            "profile": bool(args.profile)}
+        if not args.no_cpu_baseline and not args.profile:
+            cores = cpu_cores()
+            rate, R, m, el = cluster_oracle_rate(c, args.cpu_seconds)
+            result["cpu_baseline"] = {
+                "value": rate, "unit": "candidates/s", "cores": 1,
+                "kind": "oracle",
+                "sample": f"the {m} candidates of DM trials 0-{R - 1} as their "
+                          f"own list ({el:.1f} s; the oracle is single-threaded "
+                          f"and quadratic in the list size; {cores} cores seen)"}
+        print(json.dumps(result), flush=True)
+    cl.close()
+    return 0
+
+
 # ----------------------------------------------------- uneven multi-beam batch
 def run_batch(args):
     """160 beams of uneven shape (1024/2048/4096 channels in a 2:1:1 mix,
@@ -737,12 +877,14 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["beam", "sps", "batch", "serve"],
+    ap.add_argument("--workload", choices=["beam", "sps", "batch", "serve",
+                                           "cluster"],
                     default="beam",
                     help="beam: the full path on one 4096-channel beam block "
                          "(headline); sps: the search-only stress case; batch: "
                          "160 uneven beams in one persistent launch; serve: "
-                         "real-time streaming beams (--steps blocks per beam)")
+                         "real-time streaming beams (--steps blocks per beam); "
+                         "cluster: peaks filter + DBSCAN of a candidate list")
     ap.add_argument("--nbeams", type=int, default=0, help="batch: beams (0 = 160)")
     ap.add_argument("--inflight", type=int, default=1,
                     help="serve: batched steps queued on the device at once")
@@ -767,6 +909,8 @@ def main():
         return run_batch(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "cluster":
+        return run_cluster(args)
     return run_ours(args)
 
 

@@ -452,6 +452,75 @@ int ddsp_plan_get_tile(const ddsp_plan *plan, int *dm_tile,
                        int *dm_per_thread, int *time_tile, int *chan_chunk,
                        int *stages, int *flags);
 
+/* ------------------------------------------------------------------------
+ * Peaks filtering and DM-time clustering of candidates (Sec.2.1: the
+ * candidate list is thinned with square stencils of different sizes in the
+ * DM-time plane, the survivors are clustered with DBSCAN in that plane, and
+ * the highest-S/N candidate of each cluster is kept).
+ *
+ *   peaks:  candidate i stays unless a stronger candidate j -- snr_j >
+ *           snr_i, or equal S/N and (dm_idx_j, t_j) before (dm_idx_i, t_i)
+ *           -- lies in its square stencil |dm_idx_j - dm_idx_i| <= h,
+ *           |t_j - t_i| <= h, h = half[w_idx_i] (trials and samples);
+ *   DBSCAN: the peaks in (dm_idx, t) order; the neighbourhood of a peak is
+ *           every peak with |d dm_idx| <= eps_dm and |d t| <= eps_t, itself
+ *           included; core peaks have >= min_pts neighbours; a cluster (the
+ *           core peaks connected through neighbourhoods, plus the non-core
+ *           peaks next to them) is labelled by the index, in the sorted peak
+ *           list, of its first core peak; a non-core peak next to several
+ *           clusters takes the smallest label; the rest are noise (-1);
+ *   reps:   the strongest member of each cluster (ties to the earlier peak),
+ *           clusters in increasing label order.
+ * S/N values are compared exactly as given (FP32).
+ * --------------------------------------------------------------------- */
+typedef struct ddsp_cluster ddsp_cluster;
+
+/* Workspace on `device` for planes of ndm trials x nsamp samples and up to
+ * `capacity` candidates per call: two plane bitmaps with their prefix sums
+ * (about ndm*nsamp/4 bytes) plus 68 bytes per candidate, owned by the
+ * library.  DDSP_E_INVALID_ARG if a size is <= 0, capacity >= 2^31,
+ * nsamp >= 2^32 or the device does not exist; DDSP_E_NOMEM / DDSP_E_CUDA on
+ * allocation failure. */
+int ddsp_cluster_create(ddsp_cluster **out, int device, int ndm,
+                        int64_t nsamp, int64_t capacity);
+void ddsp_cluster_destroy(ddsp_cluster *cluster);
+
+/* Filter and cluster the records d_cands[0 .. m) (device, any order, each
+ * (dm_idx, t) at most once), m = n, or m = min(*d_count, n) when d_count (a
+ * device counter, such as the search's own: ddsp_plan_candidates_device) is
+ * given.  half: host array of nwidths (1..32) stencil half-sizes >= 0,
+ * indexed by w_idx; it is read before the call returns.  Stream-ordered
+ * and asynchronous.  DDSP_E_INVALID_ARG for n > capacity, a bad parameter,
+ * or a negative half-size.  Records outside the plane or with w_idx >=
+ * nwidths, and repeated (dm_idx, t), are found on the device and reported
+ * by the fetch calls as DDSP_E_INVALID_ARG. */
+int ddsp_peaks_cluster(ddsp_cluster *cluster, const ddsp_cand *d_cands,
+                       const uint32_t *d_count, int64_t n,
+                       const int32_t *half, int nwidths, int eps_dm,
+                       int eps_t, int min_pts, ddsp_stream_t stream);
+
+/* The peaks of the last call sorted by (dm_idx, t), and (host_labels may be
+ * NULL) their cluster labels.  Synchronises with that call's stream.
+ * *n_peaks is the true count; DDSP_E_TRUNCATED if it exceeds cap (cap
+ * records copied); DDSP_E_STATE before any call; DDSP_E_INVALID_ARG for a
+ * bad record (see ddsp_peaks_cluster); DDSP_E_TIMEOUT if a bounded device
+ * loop gave up. */
+int ddsp_cluster_fetch_peaks(ddsp_cluster *cluster, ddsp_cand *host_peaks,
+                             int32_t *host_labels, size_t cap,
+                             size_t *n_peaks);
+
+/* The strongest member of every cluster of the last call, in increasing
+ * label order, and (host_idx may be NULL) its index in the sorted peak
+ * list.  Same synchronisation and error codes as ddsp_cluster_fetch_peaks. */
+int ddsp_cluster_fetch_reps(ddsp_cluster *cluster, ddsp_cand *host_reps,
+                            uint32_t *host_idx, size_t cap, size_t *n_reps);
+
+/* The plan's device candidate buffer (records of the last search, in no
+ * particular order), its device counter (the true count, possibly above
+ * the capacity) and the capacity; valid until the plan is destroyed. */
+int ddsp_plan_candidates_device(ddsp_plan *plan, const ddsp_cand **d_cands,
+                                const uint32_t **d_count, size_t *capacity);
+
 #ifdef __cplusplus
 }
 #endif

@@ -15,7 +15,8 @@ import numpy as np
 from . import _lib
 from ._lib import DdspError, DdspCand
 
-__all__ = ["Plan", "Batch", "Server", "DdspError", "CAND_DTYPE", "delay_table"]
+__all__ = ["Plan", "Batch", "Server", "Cluster", "DdspError", "CAND_DTYPE",
+           "delay_table"]
 
 CAND_DTYPE = np.dtype([("dm_idx", np.uint32), ("t", np.uint32),
                        ("w_idx", np.uint32), ("snr", np.float32)])
@@ -263,6 +264,100 @@ class Plan:
 
     def __exit__(self, *a):
         self.close()
+
+
+class Cluster:
+    """Peaks filtering with square DM-time stencils, DBSCAN clustering of the
+    peaks in the DM-time plane and the strongest member of each cluster
+    (Sec.2.1), on a plane of ``ndm`` trials x ``nsamp`` samples; see
+    ddsp_peaks_cluster for the exact rules."""
+
+    def __init__(self, ndm, nsamp, capacity, device=None):
+        import torch
+        if device is None:
+            device = torch.cuda.current_device()
+        self.ndm, self.nsamp, self.capacity = int(ndm), int(nsamp), int(capacity)
+        self._h = C.c_void_p()
+        _lib.check(_lib.lib().ddsp_cluster_create(
+            C.byref(self._h), int(device), self.ndm, self.nsamp, self.capacity),
+            "ddsp_cluster_create")
+
+    @staticmethod
+    def to_device(cands, device="cuda"):
+        """Candidate records (CAND_DTYPE) as a contiguous int32 [n, 4] CUDA
+        tensor with the record layout of ddsp_cand."""
+        import torch
+        a = np.ascontiguousarray(cands, dtype=CAND_DTYPE)
+        return torch.from_numpy(a.view(np.int32).reshape(-1, 4).copy()).to(device)
+
+    def run(self, cands, half, eps_dm, eps_t, min_pts, n=None, count=None,
+            stream=None):
+        """cands: int32 [>= n, 4] CUDA tensor of records (``to_device``), or
+        a raw device pointer with ``n`` given; ``count``: optional device
+        counter pointer (the first min(*count, n) records are used)."""
+        import torch
+        if isinstance(cands, torch.Tensor):
+            if cands.dim() != 2 or cands.shape[1] != 4:
+                raise ValueError("cands must be [n, 4] int32 records")
+            ptr = _dev_ptr(cands, torch.int32, "cands")
+            if n is None:
+                n = cands.shape[0]
+        else:
+            ptr = C.c_void_p(int(cands))
+        hf = np.ascontiguousarray(half, dtype=np.int32)
+        _lib.check(_lib.lib().ddsp_peaks_cluster(
+            self._h, ptr, C.c_void_p(int(count)) if count else None, int(n),
+            hf.ctypes.data_as(C.c_void_p), int(hf.size), int(eps_dm),
+            int(eps_t), int(min_pts), _stream_handle(stream)),
+            "ddsp_peaks_cluster")
+
+    def run_plan(self, plan, half, eps_dm, eps_t, min_pts, stream=None):
+        """Cluster the candidates of ``plan``'s last search in place, with no
+        host round trip (its device buffer and counter)."""
+        d_c, d_n, cap = C.c_void_p(), C.c_void_p(), C.c_size_t()
+        _lib.check(_lib.lib().ddsp_plan_candidates_device(
+            plan._h, C.byref(d_c), C.byref(d_n), C.byref(cap)),
+            "ddsp_plan_candidates_device")
+        self.run(d_c.value, half, eps_dm, eps_t, min_pts,
+                 n=min(cap.value, self.capacity), count=d_n.value, stream=stream)
+
+    def peaks(self, cap=None):
+        """(peaks sorted by (dm_idx, t), their int32 cluster labels)."""
+        if cap is None:
+            cap = self.capacity
+        buf = np.zeros(max(cap, 1), dtype=CAND_DTYPE)
+        lab = np.zeros(max(cap, 1), dtype=np.int32)
+        n = C.c_size_t()
+        _lib.check(_lib.lib().ddsp_cluster_fetch_peaks(
+            self._h, buf.ctypes.data_as(C.c_void_p),
+            lab.ctypes.data_as(C.c_void_p), int(cap), C.byref(n)),
+            "ddsp_cluster_fetch_peaks")
+        return buf[:n.value].copy(), lab[:n.value].copy()
+
+    def reps(self, cap=None):
+        """(strongest member of each cluster in label order, its index in
+        the sorted peaks)."""
+        if cap is None:
+            cap = self.capacity
+        buf = np.zeros(max(cap, 1), dtype=CAND_DTYPE)
+        idx = np.zeros(max(cap, 1), dtype=np.uint32)
+        n = C.c_size_t()
+        _lib.check(_lib.lib().ddsp_cluster_fetch_reps(
+            self._h, buf.ctypes.data_as(C.c_void_p),
+            idx.ctypes.data_as(C.c_void_p), int(cap), C.byref(n)),
+            "ddsp_cluster_fetch_reps")
+        return buf[:n.value].copy(), idx[:n.value].copy()
+
+    def close(self):
+        if self._h:
+            _lib.lib().ddsp_cluster_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Batch:

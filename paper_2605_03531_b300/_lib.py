@@ -87,6 +87,15 @@ SIGNATURES = {
     "ddsp_last_error_detail": (C.c_char_p, []),
     "ddsp_plan_set_tile": (I32, [P, I32, I32, I32, I32, I32]),
     "ddsp_plan_get_tile": (I32, [P] + [C.POINTER(C.c_int)] * 6),
+    "ddsp_cluster_create": (I32, [C.POINTER(P), I32, I32, I64, I64]),
+    "ddsp_cluster_destroy": (None, [P]),
+    "ddsp_peaks_cluster": (I32, [P, P, P, I64, P, I32, I32, I32, I32, P]),
+    "ddsp_cluster_fetch_peaks": (I32, [P, P, P, C.c_size_t,
+                                       C.POINTER(C.c_size_t)]),
+    "ddsp_cluster_fetch_reps": (I32, [P, P, P, C.c_size_t,
+                                      C.POINTER(C.c_size_t)]),
+    "ddsp_plan_candidates_device": (I32, [P, C.POINTER(P), C.POINTER(P),
+                                          C.POINTER(C.c_size_t)]),
 }
 
 _lib = None
