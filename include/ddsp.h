@@ -477,8 +477,8 @@ typedef struct ddsp_cluster ddsp_cluster;
 
 /* Workspace on `device` for planes of ndm trials x nsamp samples and up to
  * `capacity` candidates per call: two plane bitmaps with their prefix sums
- * (about ndm*nsamp/4 bytes) plus 68 bytes per candidate, owned by the
- * library.  DDSP_E_INVALID_ARG if a size is <= 0, capacity >= 2^31,
+ * and the largest S/N of every 32 cells of a row (about 5/8 byte per plane
+ * cell) plus 72 bytes per candidate, owned by the library.  DDSP_E_INVALID_ARG if a size is <= 0, capacity >= 2^31,
  * nsamp >= 2^32 or the device does not exist; DDSP_E_NOMEM / DDSP_E_CUDA on
  * allocation failure. */
 int ddsp_cluster_create(ddsp_cluster **out, int device, int ndm,

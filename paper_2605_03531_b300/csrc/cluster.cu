@@ -16,7 +16,11 @@
 //   2. peaks: a candidate stays unless a stronger one (larger S/N, ties to
 //      the earlier (dm_idx, t)) lies in its square stencil of half-size
 //      half[w_idx]; rows are scanned nearest first and the scan stops at the
-//      first stronger record; survivors mark the peak bitmap;
+//      first stronger record: one thread per candidate takes the rows within
+//      distance 2 (most candidates end there), and the few still undecided
+//      are queued for one warp each, 32 rows at a time, so a wide stencil
+//      does not hold a block for hundreds of serial row lookups; survivors
+//      mark the peak bitmap;
 //   3. DBSCAN on the sorted peaks: neighbour counts from ranks (core if
 //      >= min_pts), a lock-free union-find over core-core neighbour pairs
 //      that always hooks the larger root under the smaller (so each
@@ -49,8 +53,14 @@ constexpr int kUnionLimit = 1 << 24;
 struct ClState {
   uint32_t n_in;      // records used this call
   uint32_t err;
-  uint32_t pad[2];
+  uint32_t n_queue;   // candidates left to the warp-wide stencil scan
+  uint32_t pad;
 };
+
+// rows of a stencil a thread checks on its own, nearest first (distance
+// <= kQuickRows); the candidates still undecided after them are queued for
+// a warp that scans 32 rows at a time
+constexpr int kQuickRows = 2;
 
 struct HalfTable {
   int32_t h[kMaxClusterWidths];
@@ -59,6 +69,7 @@ struct HalfTable {
 struct Plane {
   const uint32_t *bm;   // bitmap words (nwords + 1, last one zero)
   const uint32_t *pf;   // exclusive popcount prefix (nwords + 1)
+  const uint32_t *wmax; // largest ordered S/N key of each word's records
   int64_t wpr;          // words per row
   int ndm;
   int64_t nsamp;
@@ -77,9 +88,10 @@ __device__ __forceinline__ bool stronger(const ddsp_cand &o,
   return o.dm_idx < r.dm_idx || (o.dm_idx == r.dm_idx && o.t < r.t);
 }
 
-// uint32 whose unsigned order is the float order (finite values)
+// uint32 whose unsigned order is the float order (finite values; -0 and
+// +0 map to one key, as they compare equal)
 __device__ __forceinline__ uint32_t ordered_bits(float f) {
-  const uint32_t u = __float_as_uint(f);
+  const uint32_t u = __float_as_uint(f == 0.0f ? 0.0f : f);
   return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
 }
 
@@ -89,6 +101,7 @@ __global__ void cl_prep(const uint32_t *d_count, int64_t n, ClState *st) {
     if (d_count) c = min(*d_count, (uint32_t)n);
     st->n_in = c;
     st->err = 0;
+    st->n_queue = 0;
   }
 }
 
@@ -202,9 +215,11 @@ cudaError_t scan_words(const uint32_t *bm, int64_t nwords, uint32_t *pf,
   return cudaGetLastError();
 }
 
-// ---- sorted scatter: record i goes to the rank of its bit
+// ---- sorted scatter: record i goes to the rank of its bit; each bitmap
+// word also keeps the largest S/N key of its records
 __global__ void cl_scatter(const ddsp_cand *__restrict__ c, const ClState *st,
-                           Plane P, int nw, ddsp_cand *sorted) {
+                           Plane P, int nw, ddsp_cand *sorted,
+                           uint32_t *wmax) {
   const uint32_t n = st->n_in;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -213,12 +228,50 @@ __global__ void cl_scatter(const ddsp_cand *__restrict__ c, const ClState *st,
         r.w_idx >= (uint32_t)nw)
       continue;
     sorted[P.rank((int)r.dm_idx, r.t)] = r;
+    atomicMax(&wmax[(int64_t)r.dm_idx * P.wpr + (r.t >> 5)],
+              ordered_bits(r.snr));
   }
 }
 
 // ---- peaks filter over the sorted records
-__global__ void cl_peaks(const ddsp_cand *__restrict__ sorted, Plane P,
-                         HalfTable half, uint32_t *bm_peaks) {
+// Is any record of row kk inside [t0, t1] (other than record i) stronger
+// than r?  Words whose largest S/N is below r's hold none and are skipped;
+// the records of the others are checked one by one.
+__device__ __forceinline__ bool row_has_stronger(
+    const ddsp_cand *__restrict__ sorted, const Plane &P, int64_t kk,
+    int64_t t0, int64_t t1, int64_t i, const ddsp_cand &r) {
+  const uint32_t key = ordered_bits(r.snr);
+  const int64_t row = kk * P.wpr;
+  const int64_t w0 = row + (t0 >> 5), w1 = row + (t1 >> 5);
+  for (int64_t w = w0; w <= w1; ++w) {
+    if (P.wmax[w] < key) continue;
+    const uint32_t blo = w == w0 ? (uint32_t)(t0 & 31) : 0u;
+    const uint32_t bhi = w == w1 ? (uint32_t)(t1 & 31) : 31u;
+    const uint32_t word = P.bm[w];
+    uint32_t bits = word & ((2u << bhi) - 1u) & ~((1u << blo) - 1u);
+    while (bits) {
+      const uint32_t b = __ffs(bits) - 1;
+      bits &= bits - 1u;
+      const uint32_t j = P.pf[w] + __popc(word & ((1u << b) - 1u));
+      if (j != (uint32_t)i && stronger(sorted[j], r)) return true;
+    }
+  }
+  return false;
+}
+
+// Row of stencil order o (0: the candidate's own row; 2d - 1 and 2d: the
+// rows d below and d above), or -1 outside the plane.
+__device__ __forceinline__ int64_t stencil_row(int64_t k, int64_t o, int ndm) {
+  const int64_t d = (o + 1) >> 1;
+  const int64_t kk = (o & 1) ? k - d : k + d;
+  return (kk >= 0 && kk < ndm) ? kk : -1;
+}
+
+// One thread per candidate: the rows at distance <= kQuickRows.  Decided
+// candidates are done (survivors mark the peak bitmap); the rest queue.
+__global__ void cl_peaks_near(const ddsp_cand *__restrict__ sorted, Plane P,
+                              HalfTable half, uint32_t *bm_peaks,
+                              uint32_t *queue, ClState *st) {
   const uint32_t n = P.total();
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
        i += (int64_t)gridDim.x * blockDim.x) {
@@ -229,22 +282,55 @@ __global__ void cl_peaks(const ddsp_cand *__restrict__ sorted, Plane P,
     // rows nearest first, no further than the plane reaches
     const int64_t dmax = min(h, max((int64_t)r.dm_idx,
                                     (int64_t)P.ndm - 1 - (int64_t)r.dm_idx));
-    bool kept = true;
-    for (int64_t d = 0; d <= dmax && kept; ++d) {
-      for (int side = 0; side < (d > 0 ? 2 : 1) && kept; ++side) {
-        const int64_t kk = side ? (int64_t)r.dm_idx + d : (int64_t)r.dm_idx - d;
-        if (kk < 0 || kk >= P.ndm) continue;
-        const uint32_t lo = P.rank((int)kk, t0), hi = P.rank((int)kk, t1 + 1);
-        for (uint32_t j = lo; j < hi; ++j) {
-          if (j == (uint32_t)i) continue;
-          if (stronger(sorted[j], r)) {
-            kept = false;
-            break;
-          }
-        }
+    const int64_t onear = 2 * min(dmax, (int64_t)kQuickRows);
+    bool beaten = false;
+    for (int64_t o = 0; o <= onear && !beaten; ++o) {
+      const int64_t kk = stencil_row(r.dm_idx, o, P.ndm);
+      if (kk >= 0) beaten = row_has_stronger(sorted, P, kk, t0, t1, i, r);
+    }
+    if (beaten) continue;
+    if (dmax <= kQuickRows) {
+      atomicOr(&bm_peaks[(int64_t)r.dm_idx * P.wpr + (r.t >> 5)],
+               1u << (r.t & 31));
+    } else {
+      queue[atomicAdd(&st->n_queue, 1u)] = (uint32_t)i;
+    }
+  }
+}
+
+// One warp per queued candidate: the remaining rows of its stencil, 32 at a
+// time (one per lane), until a lane finds a stronger record.
+__global__ void cl_peaks_far(const ddsp_cand *__restrict__ sorted, Plane P,
+                             HalfTable half, uint32_t *bm_peaks,
+                             const uint32_t *__restrict__ queue,
+                             const ClState *st) {
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const uint32_t nq = st->n_queue;
+  for (int64_t q = warp; q < nq; q += nwarps) {
+    const int64_t i = queue[q];
+    const ddsp_cand r = sorted[i];
+    const int64_t h = half.h[r.w_idx];
+    const int64_t t0 = max((int64_t)0, (int64_t)r.t - h);
+    const int64_t t1 = min(P.nsamp - 1, (int64_t)r.t + h);
+    const int64_t dmax = min(h, max((int64_t)r.dm_idx,
+                                    (int64_t)P.ndm - 1 - (int64_t)r.dm_idx));
+    const int64_t oend = 2 * dmax;              // last stencil order
+    bool beaten = false;
+    for (int64_t o0 = 2 * kQuickRows + 1; o0 <= oend; o0 += 32) {
+      const int64_t o = o0 + lane;
+      bool mine = false;
+      if (o <= oend) {
+        const int64_t kk = stencil_row(r.dm_idx, o, P.ndm);
+        if (kk >= 0) mine = row_has_stronger(sorted, P, kk, t0, t1, i, r);
+      }
+      if (__any_sync(0xffffffffu, mine)) {
+        beaten = true;
+        break;
       }
     }
-    if (kept)
+    if (!beaten && lane == 0)
       atomicOr(&bm_peaks[(int64_t)r.dm_idx * P.wpr + (r.t >> 5)],
                1u << (r.t & 31));
   }
@@ -420,11 +506,12 @@ struct ddsp_cluster {
   int ndm = 0;
   int64_t nsamp = 0, wpr = 0, nwords = 0, cap = 0, rwords = 0;
   uint32_t *bm_c = nullptr, *pf_c = nullptr, *bm_p = nullptr, *pf_p = nullptr;
+  uint32_t *wmax = nullptr;
   uint32_t *bm_r = nullptr, *pf_r = nullptr, *bsum = nullptr;
   ddsp_cand *sorted = nullptr, *peaks = nullptr, *reps = nullptr;
   uint8_t *core = nullptr;
   int32_t *parent = nullptr, *label = nullptr;
-  uint32_t *rep_idx = nullptr;
+  uint32_t *rep_idx = nullptr, *queue = nullptr;
   unsigned long long *repkey = nullptr;
   ClState *st = nullptr;
   cudaStream_t last = nullptr;
@@ -432,9 +519,9 @@ struct ddsp_cluster {
 };
 
 static void cluster_free(ddsp_cluster *c) {
-  void *ptrs[] = {c->bm_c, c->pf_c, c->bm_p, c->pf_p, c->bm_r, c->pf_r,
+  void *ptrs[] = {c->bm_c, c->pf_c, c->bm_p, c->pf_p, c->wmax, c->bm_r, c->pf_r,
                   c->bsum, c->sorted, c->peaks, c->reps, c->core, c->parent,
-                  c->label, c->rep_idx, c->repkey, c->st};
+                  c->label, c->rep_idx, c->queue, c->repkey, c->st};
   for (void *p : ptrs) cudaFree(p);
 }
 
@@ -468,6 +555,7 @@ extern "C" int ddsp_cluster_create(ddsp_cluster **out, int device, int ndm,
   alloc((void **)&c->pf_c, pw);
   alloc((void **)&c->bm_p, pw);
   alloc((void **)&c->pf_p, pw);
+  alloc((void **)&c->wmax, pw);
   alloc((void **)&c->bm_r, (size_t)(c->rwords + 1) * 4);
   alloc((void **)&c->pf_r, (size_t)(c->rwords + 1) * 4);
   alloc((void **)&c->bsum, (size_t)nb * 4);
@@ -478,6 +566,7 @@ extern "C" int ddsp_cluster_create(ddsp_cluster **out, int device, int ndm,
   alloc((void **)&c->parent, (size_t)capacity * 4);
   alloc((void **)&c->label, (size_t)capacity * 4);
   alloc((void **)&c->rep_idx, (size_t)capacity * 4);
+  alloc((void **)&c->queue, (size_t)capacity * 4);
   alloc((void **)&c->repkey, (size_t)capacity * 8);
   alloc((void **)&c->st, sizeof(ClState));
   if (e != cudaSuccess) {
@@ -517,19 +606,23 @@ extern "C" int ddsp_peaks_cluster(ddsp_cluster *c, const ddsp_cand *d_cands,
   const unsigned gz = 148 * 8;
   const unsigned gc = (unsigned)std::max<int64_t>(
       1, std::min<int64_t>((n + 255) / 256, 148 * 16));
-  Plane P{c->bm_c, c->pf_c, c->wpr, c->ndm, c->nsamp};
-  Plane PK{c->bm_p, c->pf_p, c->wpr, c->ndm, c->nsamp};
+  Plane P{c->bm_c, c->pf_c, c->wmax, c->wpr, c->ndm, c->nsamp};
+  Plane PK{c->bm_p, c->pf_p, nullptr, c->wpr, c->ndm, c->nsamp};
   const Eps ep{eps_dm, eps_t, min_pts};
   cl_prep<<<1, 32, 0, s>>>(d_count, n, c->st);
   cl_zero<<<gz, 256, 0, s>>>(c->bm_c, nwp);
   cl_zero<<<gz, 256, 0, s>>>(c->bm_p, nwp);
+  cl_zero<<<gz, 256, 0, s>>>(c->wmax, nwp);
   cl_zero<<<gz, 256, 0, s>>>(c->bm_r, c->rwords + 1);
   cl_mark<<<gc, 256, 0, s>>>(d_cands, c->st, c->bm_c, c->ndm, c->nsamp, c->wpr,
                              nwidths);
   cudaError_t e = scan_words(c->bm_c, c->nwords, c->pf_c, c->bsum, s);
   if (e != cudaSuccess) return cuda_rc(e);
-  cl_scatter<<<gc, 256, 0, s>>>(d_cands, c->st, P, nwidths, c->sorted);
-  cl_peaks<<<gc, 256, 0, s>>>(c->sorted, P, ht, c->bm_p);
+  cl_scatter<<<gc, 256, 0, s>>>(d_cands, c->st, P, nwidths, c->sorted,
+                                c->wmax);
+  cl_peaks_near<<<gc, 256, 0, s>>>(c->sorted, P, ht, c->bm_p, c->queue, c->st);
+  cl_peaks_far<<<148 * 8, 256, 0, s>>>(c->sorted, P, ht, c->bm_p, c->queue,
+                                       c->st);
   e = scan_words(c->bm_p, c->nwords, c->pf_p, c->bsum, s);
   if (e != cudaSuccess) return cuda_rc(e);
   cl_gather_peaks<<<gc, 256, 0, s>>>(c->sorted, P, PK, c->peaks);
