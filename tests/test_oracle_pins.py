@@ -12,6 +12,7 @@
 * S/N: unit variance on pure noise, MAD = 0 gives no candidates.
 """
 import math
+import os
 from fractions import Fraction
 
 import numpy as np
@@ -55,16 +56,31 @@ def test_delay_table_equals_exact_rational():
             assert d[k, c] == exact_delay(nchan, f_top, bw, ts, dm, c), (k, c)
 
 
+def golden(name):
+    """key -> list of floats from a fixture under tests/golden/."""
+    out = {}
+    path = os.path.join(os.path.dirname(__file__), "golden", name)
+    for line in open(path):
+        line = line.split("#", 1)[0].split()
+        if line:
+            out[line[0]] = [float(v) for v in line[1:]]
+    return out
+
+
 def test_delay_paper_units():
-    """The paper writes the law as 4.14881 ms GHz^2 (Ch.1 Eq.1).  Evaluated in
-    those units (ms, GHz) the continuous delay matches the oracle's within
-    the 6-figure precision of that constant."""
+    """The paper writes the law with the constant 4.14881 ms GHz^2 (Ch.1
+    Eq.1; tests/golden/dispersion_law.txt).  Evaluated in those units (ms,
+    GHz), over the paper's trial-DM range (Sec.2.1), the continuous delay
+    matches the oracle's within the 6-figure precision of that constant."""
+    g = golden("dispersion_law.txt")
+    kc = g["constant_ms_ghz2"][0]
+    dm_lo, dm_hi = g["dm_range"]
     nchan, f_top, bw, ts = 128, 1460.0, -1.5625, 1.31072e-3
-    for dm in (10.0, 250.0, 1999.0):
+    for dm in (dm_lo + 10.0, 250.0, dm_hi - 1.0):
         f_ref_ghz = f_top / 1000.0
         for c in (1, 40, 127):
             f_ghz = (f_top + c * bw) / 1000.0
-            ms = 4.14881 * dm * (1 / f_ghz ** 2 - 1 / f_ref_ghz ** 2)
+            ms = kc * dm * (1 / f_ghz ** 2 - 1 / f_ref_ghz ** 2)
             samples = ms * 1e-3 / ts
             x = oracle.delay_exact(nchan, f_top, bw, ts, dm, c)
             assert abs(samples - x) <= 2e-6 * abs(x) + 1e-9
@@ -271,3 +287,15 @@ def test_sps_best_width_and_ties():
     assert best["t"] == 1000 and best["w_idx"] == 3
     wi, s = oracle.best_at(x, 0, [1, 2, 4, 8, 16], 1000)
     assert wi == 3 and abs(s - best["snr"]) < 1e-12
+
+
+# ----------------------------------------------------------------- unpack
+@pytest.mark.parametrize("dtype,shape", [(np.uint8, (37, 19)),
+                                         (np.uint16, (5, 64)),
+                                         (np.uint8, (1, 1))])
+def test_unpack_is_numpy_transpose(dtype, shape):
+    """Time-major spectra -> channel-major rows: numpy's transpose (a
+    library routine) of the same array."""
+    rng = np.random.default_rng(3)
+    x = rng.integers(0, np.iinfo(dtype).max + 1, size=shape).astype(dtype)
+    assert np.array_equal(oracle.unpack(x), np.ascontiguousarray(x.T))
