@@ -15,7 +15,9 @@ the passage of the paper its C function writes out:
 * ``boxcar``, ``sps`` -- boxcar single-pulse search above a threshold, Sec.2.1;
 * ``peaks``, ``dbscan``, ``cluster_reps``, ``peaks_cluster`` -- peaks
   filtering with square DM-time stencils, DBSCAN clustering in the DM-time
-  plane and the strongest candidate of each cluster, Sec.2.1.
+  plane and the strongest candidate of each cluster, Sec.2.1;
+* ``downsample``, ``running_median``, ``dered`` -- downsampling by a user
+  factor (Sec.3.2) and running-median de-reddening (Sec.3.3).
 """
 import ctypes as C
 import os
@@ -77,6 +79,12 @@ def lib():
         L.orc_dbscan.argtypes = [P, P, C.c_int64, C.c_int64, C.c_int64, C.c_int64, P]
         L.orc_cluster_reps.restype = None
         L.orc_cluster_reps.argtypes = [P, P, C.c_int64, P]
+        L.orc_downsample.restype = C.c_int
+        L.orc_downsample.argtypes = [P, C.c_int64, C.c_int64, P]
+        L.orc_running_median_at.restype = C.c_int64
+        L.orc_running_median_at.argtypes = [P, C.c_int64, C.c_int64, C.c_int64, P]
+        L.orc_running_median_subtract.restype = C.c_int
+        L.orc_running_median_subtract.argtypes = [P, C.c_int64, C.c_int64, P]
         L.orc_set_threads.restype = None
         L.orc_set_threads.argtypes = [C.c_int]
         _lib = L
@@ -307,3 +315,31 @@ def peaks_cluster(cands, half, eps_dm, eps_t, min_pts):
     rep = cluster_reps(labels, pk["snr"])
     reps = rep[rep >= 0]
     return pk, labels, reps
+
+
+# ------------------------------------------- downsampling and de-reddening
+def downsample(x, f):
+    """y[j] = sum of x[j*f .. j*f + f - 1] for j < len(x) // f (Sec.3.2)."""
+    x = np.ascontiguousarray(x, dtype=np.int32)
+    f = int(f)
+    y = np.empty(max(x.size // f, 1) if f >= 1 else 1, dtype=np.int32)
+    if lib().orc_downsample(_ptr(x), x.size, f, _ptr(y)) != 0:
+        raise OverflowError("factor < 1 or a sum leaves int32")
+    return y[:x.size // f]
+
+
+def running_median(x, h, t):
+    """Lower median of x over [t - h, t + h] clamped to the series."""
+    x = np.ascontiguousarray(x, dtype=np.int32)
+    work = np.empty(max(min(2 * int(h) + 1, x.size), 1), dtype=np.int32)
+    return int(lib().orc_running_median_at(_ptr(x), x.size, int(h), int(t),
+                                           _ptr(work)))
+
+
+def dered(x, h):
+    """z[t] = x[t] - running median over [t - h, t + h] (Sec.3.3)."""
+    x = np.ascontiguousarray(x, dtype=np.int32)
+    z = np.empty(max(x.size, 1), dtype=np.int32)
+    if lib().orc_running_median_subtract(_ptr(x), x.size, int(h), _ptr(z)) != 0:
+        raise OverflowError("h < 0 or a residual leaves int32")
+    return z[:x.size]

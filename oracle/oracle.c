@@ -19,7 +19,9 @@
  *                        Sec.2.1;
  *   - peaks filtering and clustering of the candidates: square DM-time
  *                        stencils, then DBSCAN in the DM-time plane keeping
- *                        the strongest candidate of each cluster, Sec.2.1.
+ *                        the strongest candidate of each cluster, Sec.2.1;
+ *   - downsampling of a dedispersed series by a user factor (Sec.3.2) and
+ *                        running-median de-reddening (Sec.3.3).
  * Readings where the paper is silent (channel frequencies, output length,
  * boxcar alignment, window layout, even-count median, MAD = 0) are listed at
  * each function.
@@ -452,6 +454,67 @@ void orc_cluster_reps(const int64_t *label, const float *s, int64_t n,
         if (c < 0) continue;
         if (rep[c] < 0 || s[i] > s[rep[c]]) rep[c] = i;
     }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Downsampling of a dedispersed series by a user factor (Sec.3.2 ends with   */
+/* it): y[j] = sum_{i<f} x[j*f + i] for j < floor(n / f); a trailing partial  */
+/* group is dropped (reading).  Sums in int64; returns -1 if f < 1 or a sum   */
+/* leaves int32, 0 otherwise.                                                 */
+/* ------------------------------------------------------------------------ */
+int orc_downsample(const int32_t *x, int64_t n, int64_t f, int32_t *y)
+{
+    if (f < 1 || n < 0) return -1;
+    for (int64_t j = 0; j < n / f; ++j) {
+        int64_t s = 0;
+        for (int64_t i = 0; i < f; ++i) s += x[j * f + i];
+        if (s < INT32_MIN || s > INT32_MAX) return -1;
+        y[j] = (int32_t)s;
+    }
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Running-median de-reddening (Sec.3.3): the slowly varying baseline of a    */
+/* series is removed by subtracting a running median, z[t] = x[t] - m[t].     */
+/* Reading: m[t] is the median of x over the window [t - h, t + h] clamped to */
+/* [0, n) (2h + 1 samples away from the ends); windows cut by an end may hold */
+/* an even count, and the median taken is then the lower middle order         */
+/* statistic, so m[t] is always a sample value and z stays an exact integer.  */
+/* Direct selection per output: copy the window, sort it, take element        */
+/* (count - 1) / 2.  Returns -1 if h < 0 or a residual leaves int32.          */
+/* ------------------------------------------------------------------------ */
+static int orc_cmp_i32(const void *a, const void *b)
+{
+    int32_t x = *(const int32_t *)a, y = *(const int32_t *)b;
+    return (x > y) - (x < y);
+}
+
+int64_t orc_running_median_at(const int32_t *x, int64_t n, int64_t h,
+                              int64_t t, int32_t *work)
+{
+    int64_t a = t - h < 0 ? 0 : t - h;
+    int64_t b = t + h > n - 1 ? n - 1 : t + h;
+    int64_t m = b - a + 1;
+    memcpy(work, x + a, (size_t)m * sizeof(int32_t));
+    qsort(work, (size_t)m, sizeof(int32_t), orc_cmp_i32);
+    return work[(m - 1) / 2];
+}
+
+int orc_running_median_subtract(const int32_t *x, int64_t n, int64_t h,
+                                int32_t *z)
+{
+    if (h < 0 || n < 0) return -1;
+    int64_t wmax = 2 * h + 1 < n ? 2 * h + 1 : n;
+    int32_t *work = (int32_t *)malloc((size_t)(wmax > 0 ? wmax : 1) * sizeof(int32_t));
+    int rc = 0;
+    for (int64_t t = 0; t < n; ++t) {
+        int64_t r = (int64_t)x[t] - orc_running_median_at(x, n, h, t, work);
+        if (r < INT32_MIN || r > INT32_MAX) { rc = -1; break; }
+        z[t] = (int32_t)r;
+    }
+    free(work);
+    return rc;
 }
 
 /* Number of OpenMP threads the DM loop of orc_dedisperse uses from now on
