@@ -521,6 +521,35 @@ int ddsp_cluster_fetch_reps(ddsp_cluster *cluster, ddsp_cand *host_reps,
 int ddsp_plan_candidates_device(ddsp_plan *plan, const ddsp_cand **d_cands,
                                 const uint32_t **d_count, size_t *capacity);
 
+/* ------------------------------------------------------------------------
+ * Downsampling and de-reddening of dedispersed series, between the
+ * dedispersion and the search.  Rows of int32 series in the caller's
+ * device buffers, row pitches in samples; overflow of int32 is reported
+ * through the plan's error word (ddsp_plan_check returns DDSP_E_RANGE).
+ * --------------------------------------------------------------------- */
+
+/* Downsampling by a user factor (Sec.3.2): out[r][j] = sum over
+ * i < factor of in[r][j*factor + i], j < nsamp / factor (a trailing partial
+ * group is dropped), r < nrows; nothing is written (and d_out may be NULL)
+ * when nsamp < factor.  Stream-ordered.  DDSP_E_INVALID_ARG for a NULL
+ * pointer, nrows or nsamp <= 0, factor < 1, in_pitch < nsamp or
+ * out_pitch < nsamp / factor. */
+int ddsp_downsample(ddsp_plan *plan, const int32_t *d_in, int64_t nrows,
+                    int64_t nsamp, int64_t in_pitch, int64_t factor,
+                    int32_t *d_out, int64_t out_pitch, ddsp_stream_t stream);
+
+/* Running-median de-reddening (Sec.3.3): out[r][t] = in[r][t] - m, with m
+ * the median of in[r] over [t - h, t + h] clamped to [0, nsamp); a window
+ * cut by an end may hold an even count, and m is then the lower of the two
+ * middle values, so m is always a sample and out is exact.  h =
+ * half_window, 0 .. 6700 (a chunk of outputs with its 2h-sample halo is
+ * processed on chip).  Stream-ordered.  DDSP_E_INVALID_ARG for a NULL
+ * pointer, d_in == d_out, nrows outside 1 .. 65535, nsamp <= 0 or >= 2^31,
+ * h out of range, or a pitch < nsamp. */
+int ddsp_dered(ddsp_plan *plan, const int32_t *d_in, int64_t nrows,
+               int64_t nsamp, int64_t in_pitch, int64_t half_window,
+               int32_t *d_out, int64_t out_pitch, ddsp_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -230,6 +230,35 @@ class Plan:
             int(cap), C.byref(nr), C.byref(nt)), "ddsp_candidates_fetch_dm_range")
         return buf[:nr.value].copy(), nr.value, nt.value
 
+    def downsample(self, series, factor, out=None, stream=None):
+        """int32 [rows][n] CUDA tensor -> [rows][n // factor], sums of
+        ``factor`` consecutive samples (Sec.3.2)."""
+        import torch
+        rows, n = series.shape
+        m = n // int(factor) if int(factor) >= 1 else 0
+        if out is None:
+            out = torch.empty((rows, m), dtype=torch.int32, device=series.device)
+        _lib.check(_lib.lib().ddsp_downsample(
+            self._h, _dev_ptr(series, torch.int32, "series"), int(rows), int(n),
+            int(series.stride(0)), int(factor),
+            _dev_ptr(out, torch.int32, "out") if m > 0 else None,
+            int(max(m, out.stride(0))), _stream_handle(stream)), "ddsp_downsample")
+        return out
+
+    def dered(self, series, half_window, out=None, stream=None):
+        """int32 [rows][n] CUDA tensor minus its running median over
+        [t - h, t + h] (Sec.3.3)."""
+        import torch
+        rows, n = series.shape
+        if out is None:
+            out = torch.empty_like(series)
+        _lib.check(_lib.lib().ddsp_dered(
+            self._h, _dev_ptr(series, torch.int32, "series"), int(rows), int(n),
+            int(series.stride(0)), int(half_window),
+            _dev_ptr(out, torch.int32, "out"), int(out.stride(0)),
+            _stream_handle(stream)), "ddsp_dered")
+        return out
+
     def stats(self):
         """Per-(DM, window) exact (2*median, 4*MAD) of the last search."""
         nwin = C.c_int64()

@@ -96,6 +96,8 @@ SIGNATURES = {
                                       C.POINTER(C.c_size_t)]),
     "ddsp_plan_candidates_device": (I32, [P, C.POINTER(P), C.POINTER(P),
                                           C.POINTER(C.c_size_t)]),
+    "ddsp_downsample": (I32, [P, P, I64, I64, I64, I64, P, I64, P]),
+    "ddsp_dered": (I32, [P, P, I64, I64, I64, I64, P, I64, P]),
 }
 
 _lib = None
