@@ -644,6 +644,132 @@ def run_cluster(args):
     return 0
 
 
+# ------------------------------------------------ downsampling + de-reddening
+DERED_METRIC = "series samples de-reddened/s"
+
+
+def dered_oracle_rate(x_row, h, target_s):
+    """Oracle samples/s of the running-median subtraction on the first S
+    samples of one row, S sized to about target_s seconds."""
+    import oracle
+    S, el = 2048, 0.0
+    for _ in range(3):
+        t0 = time.perf_counter()
+        oracle.dered(x_row[:S], h)
+        el = time.perf_counter() - t0
+        if el > 0.5 * target_s or S >= x_row.size:
+            break
+        S = int(min(x_row.size, max(S + 1, S * target_s / max(el, 1e-3))))
+    return S / el, S, el
+
+
+def run_dered(args):
+    """The beam's series shape, 1024 DM trials x 262144 int32 samples
+    (seeded Gaussian, sd 1024, with 0.1% boxcar events and a slow sinusoidal
+    baseline of amplitude 3000 and period 40000-200000 samples per row),
+    de-reddened by subtracting the running median over 2049 samples
+    (h = 1024: the window exceeds twice the widest boxcar, 256 samples, as
+    Sec.3.3 asks).  A step is one ddsp_dered call over all rows; beside it
+    the downsampling by 4 is timed on the same rows."""
+    import torch
+    from paper_2605_03531_b300 import Plan, build, shard, synth
+    build.build()
+    world, rank, local = dist_setup(args.gpus)
+    dev = torch.device("cuda", local if world > 1 else 0)
+    ndm, n, h, f = 1024, 262144, 1024, 4
+    x = synth.red_series(ndm, n, shard.rank_seed(15, rank), device=dev)
+    z = torch.empty_like(x)
+    y = torch.empty((ndm, n // f), dtype=torch.int32, device=dev)
+    plan = Plan(16, 500.0, -1.0, 1e-3, np.zeros(4), [1, 2], nbits=8,
+                norm_window=8192, cand_capacity=1024)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        plan.dered(x, h, out=z, stream=stream)
+        plan.downsample(x, f, out=y, stream=stream)
+    torch.cuda.synchronize(dev)
+    plan.check()
+    clocks = ClockSampler(dev.index or 0)
+    if not args.profile:
+        clocks.start()
+        time.sleep(0.3)
+    barrier(world)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev[0].record(stream)
+    for _ in range(args.steps):
+        plan.dered(x, h, out=z, stream=stream)
+    ev[1].record(stream)
+    for _ in range(args.steps):
+        plan.downsample(x, f, out=y, stream=stream)
+    ev[2].record(stream)
+    torch.cuda.synchronize(dev)
+    ck = clocks.stop()
+    plan.check()
+    ms = max_over_ranks(ev[0].elapsed_time(ev[1]) / args.steps, world)
+    ms_ds = ev[1].elapsed_time(ev[2]) / args.steps
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm = peaks.get("hbm_gbs", 6400.0)
+    nbytes = 8.0 * ndm * n
+    achieved = nbytes / (ms * 1e-3) / 1e9
+    ds_frac = (4.0 * ndm * n + 4.0 * ndm * (n // f)) / (ms_ds * 1e-3) / 1e9 / hbm
+    if args.profile:
+        if rank == 0:
+            print(json.dumps({"profile": True, "workload": "dered",
+                              "ms_per_step": ms, "downsample_ms": ms_ds}),
+                  flush=True)
+        return 0
+    # end to end: the rows from pinned host memory, the de-reddened rows back
+    xh = x.cpu().pin_memory()
+    zh = torch.empty_like(xh).pin_memory()
+
+    def e2e_step():
+        x.copy_(xh, non_blocking=True)
+        plan.dered(x, h, out=z, stream=stream)
+        zh.copy_(z, non_blocking=True)
+        torch.cuda.synchronize(dev)
+
+    e2e_step()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world) / args.steps
+    if rank == 0:
+        result = {
+            "metric": DERED_METRIC, "value": world * ndm * n / (ms * 1e-3),
+            "unit": "samples/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": f"running-median de-reddening of {ndm} x {n} "
+                                   f"int32 series (window {2 * h + 1} samples, "
+                                   "slow sinusoidal baselines)", "ndm": ndm,
+                       "nsamp": n, "half_window": h,
+                       "l2": "inputs larger than L2"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm,
+                         "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                         "kernel": "dered_kernel",
+                         "bytes_basis": "4 B read + 4 B written per sample"},
+            "kernels": {"downsample_ms": ms_ds, "downsample_factor": f,
+                        "downsample_hbm_frac": ds_frac},
+            "e2e": {"value": world * ndm * n / e2e_s, "unit": "samples/s",
+                    "h2d_bytes_per_step": int(4 * ndm * n),
+                    "d2h_bytes_per_step": int(4 * ndm * n),
+                    "ms_per_step": e2e_s * 1e3},
+            "gpu_launches": args.steps, "clocks": ck}
+        if not args.no_cpu_baseline:
+            rate, S, el = dered_oracle_rate(x[0].cpu().numpy(), h, args.cpu_seconds)
+            result["cpu_baseline"] = {
+                "value": rate, "unit": "samples/s", "cores": 1, "kind": "oracle",
+                "sample": f"the first {S} samples of one row ({el:.1f} s; the "
+                          "oracle sorts every window, single-threaded)"}
+        print(json.dumps(result), flush=True)
+    return 0
+
+
 # ----------------------------------------------------- uneven multi-beam batch
 def run_batch(args):
     """160 beams of uneven shape (1024/2048/4096 channels in a 2:1:1 mix,
@@ -886,13 +1012,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["beam", "sps", "batch", "serve",
-                                           "cluster"],
+                                           "cluster", "dered"],
                     default="beam",
                     help="beam: the full path on one 4096-channel beam block "
                          "(headline); sps: the search-only stress case; batch: "
                          "160 uneven beams in one persistent launch; serve: "
                          "real-time streaming beams (--steps blocks per beam); "
-                         "cluster: peaks filter + DBSCAN of a candidate list")
+                         "cluster: peaks filter + DBSCAN of a candidate list; "
+                         "dered: running-median de-reddening of the beam's "
+                         "series")
     ap.add_argument("--nbeams", type=int, default=0, help="batch: beams (0 = 160)")
     ap.add_argument("--inflight", type=int, default=1,
                     help="serve: batched steps queued on the device at once")
@@ -919,6 +1047,8 @@ def main():
         return run_serve(args)
     if args.workload == "cluster":
         return run_cluster(args)
+    if args.workload == "dered":
+        return run_dered(args)
     return run_ours(args)
 
 

@@ -478,3 +478,23 @@ def candidate_list(ndm, nsamp, nwidths, n_events, seed, thr=6.5,
     perm = np.argsort(splitmix64_np(np.arange(sel.size, dtype=np.uint64),
                                     seed + 2), kind="stable")
     return out[perm]
+
+
+def red_series(ndm, n, seed, amp=3000.0, period=(40000, 200000), device="cpu",
+               out=None):
+    """``gaussian_series`` (mean 524288, sd 1024, 0.1% boxcar events) plus a
+    slowly varying baseline per row, the "red noise" of Sec.3.3:
+    round(amp * sin(2 pi t / P_k + phi_k)), period P_k log-uniform in
+    ``period`` samples and phase phi_k uniform (stream seed+7)."""
+    x = gaussian_series(ndm, n, seed, device=device, out=out)
+    u = uniform_np(np.arange(2 * ndm, dtype=np.uint64), seed + 7).reshape(ndm, 2)
+    lp = np.log(period[0]) + u[:, 0] * (np.log(period[1]) - np.log(period[0]))
+    P = torch.from_numpy(np.exp(lp)).to(device)
+    phi = torch.from_numpy(2 * np.pi * u[:, 1]).to(device)
+    t = torch.arange(n, dtype=torch.float64, device=device)
+    for r0 in range(0, ndm, 64):
+        r1 = min(ndm, r0 + 64)
+        base = amp * torch.sin(2 * np.pi * t[None, :] / P[r0:r1, None]
+                               + phi[r0:r1, None])
+        x[r0:r1] += torch.round(base).to(torch.int32)
+    return x
