@@ -17,7 +17,9 @@ the passage of the paper its C function writes out:
   filtering with square DM-time stencils, DBSCAN clustering in the DM-time
   plane and the strongest candidate of each cluster, Sec.2.1;
 * ``downsample``, ``running_median``, ``dered`` -- downsampling by a user
-  factor (Sec.3.2) and running-median de-reddening (Sec.3.3).
+  factor (Sec.3.2) and running-median de-reddening (Sec.3.3);
+* ``ffa``, ``fold_snr`` -- the folding transform by the fast folding
+  algorithm and the boxcar search of a folded profile, Sec.3.5.
 """
 import ctypes as C
 import os
@@ -85,6 +87,12 @@ def lib():
         L.orc_running_median_at.argtypes = [P, C.c_int64, C.c_int64, C.c_int64, P]
         L.orc_running_median_subtract.restype = C.c_int
         L.orc_running_median_subtract.argtypes = [P, C.c_int64, C.c_int64, P]
+        L.orc_ffa.restype = C.c_int64
+        L.orc_ffa.argtypes = [P, C.c_int64, C.c_int64, P]
+        L.orc_fold_snr.restype = C.c_int
+        L.orc_fold_snr.argtypes = [P, C.c_int64, C.c_int64, P, C.c_int,
+                                   C.c_double, C.POINTER(C.c_double),
+                                   C.POINTER(C.c_int64)]
         L.orc_set_threads.restype = None
         L.orc_set_threads.argtypes = [C.c_int]
         _lib = L
@@ -343,3 +351,36 @@ def dered(x, h):
     if lib().orc_running_median_subtract(_ptr(x), x.size, int(h), _ptr(z)) != 0:
         raise OverflowError("h < 0 or a residual leaves int32")
     return z[:x.size]
+
+
+# ------------------------------------------------------- folding transform
+def ffa_rows(n, p):
+    """m: the largest power of two with m * p <= n (0 if p > n)."""
+    if p < 1 or n < p:
+        return 0
+    m = 1
+    while 2 * m * p <= n:
+        m *= 2
+    return m
+
+
+def ffa(x, p):
+    """Folding transform F[m][p] (int64) of series x at base period p."""
+    x = np.ascontiguousarray(x, dtype=np.int32)
+    m = ffa_rows(x.size, int(p))
+    if m == 0:
+        raise ValueError("p < 1 or the series is shorter than p")
+    out = np.empty((m, int(p)), dtype=np.int64)
+    lib().orc_ffa(_ptr(x), x.size, int(p), _ptr(out))
+    return out
+
+
+def fold_snr(P, m, widths, sigma):
+    """(best width index, best S/N, phase) of one folded profile."""
+    P = np.ascontiguousarray(P, dtype=np.int64)
+    ws = np.ascontiguousarray(widths, dtype=np.int32)
+    s = C.c_double()
+    ph = C.c_int64()
+    wi = lib().orc_fold_snr(_ptr(P), P.size, int(m), _ptr(ws), ws.size,
+                            float(sigma), C.byref(s), C.byref(ph))
+    return wi, s.value, ph.value

@@ -21,7 +21,9 @@
  *                        stencils, then DBSCAN in the DM-time plane keeping
  *                        the strongest candidate of each cluster, Sec.2.1;
  *   - downsampling of a dedispersed series by a user factor (Sec.3.2) and
- *                        running-median de-reddening (Sec.3.3).
+ *                        running-median de-reddening (Sec.3.3);
+ *   - the folding transform of a series by the fast folding algorithm and
+ *                        the boxcar search of its folded profiles, Sec.3.5.
  * Readings where the paper is silent (channel frequencies, output length,
  * boxcar alignment, window layout, even-count median, MAD = 0) are listed at
  * each function.
@@ -515,6 +517,85 @@ int orc_running_median_subtract(const int32_t *x, int64_t n, int64_t h,
     }
     free(work);
     return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Folding transform (Sec.3.5): a series cut into m rows of p samples,        */
+/* r_i[j] = x[i*p + j], is folded at the trial periods p + s/(m - 1),         */
+/* s = 0 .. m - 1 (the paper's p_s = p^2 / (p - s/(m - 1)) to first order),   */
+/* by the fast folding algorithm (Staelin 1969).  Reading: m is the largest   */
+/* power of two with m*p <= n (whole rows), and the transform of rows         */
+/* [i0, i0 + k) is, for k = 1, the row itself, else with A and B the          */
+/* transforms of the first and second halves,                                 */
+/*   F[s][j] = A[s/2][j] + B[s/2][(j + (s+1)/2) mod p]   (integer division),  */
+/* so profile s drifts by s samples over the m - 1 row steps.  Exact int64.   */
+/* out is [m][p]; returns m, or -1 if p < 1 or n < p.                         */
+/* ------------------------------------------------------------------------ */
+static void orc_ffa_rec(const int32_t *x, int64_t p, int64_t i0, int64_t k,
+                        int64_t *out, int64_t *tmp)
+{
+    if (k == 1) {
+        for (int64_t j = 0; j < p; ++j) out[j] = x[i0 * p + j];
+        return;
+    }
+    int64_t h = k / 2;
+    int64_t *A = tmp, *B = tmp + h * p;
+    int64_t *sub = (int64_t *)malloc((size_t)(k * p) * sizeof(int64_t));
+    orc_ffa_rec(x, p, i0, h, A, sub);
+    orc_ffa_rec(x, p, i0 + h, h, B, sub);
+    free(sub);
+    for (int64_t s = 0; s < k; ++s) {
+        const int64_t *a = A + (s / 2) * p, *b = B + (s / 2) * p;
+        int64_t sh = (s + 1) / 2;
+        for (int64_t j = 0; j < p; ++j) out[s * p + j] = a[j] + b[(j + sh) % p];
+    }
+}
+
+int64_t orc_ffa(const int32_t *x, int64_t n, int64_t p, int64_t *out)
+{
+    if (p < 1 || n < p) return -1;
+    int64_t m = 1;
+    while (2 * m * p <= n) m *= 2;
+    int64_t *tmp = (int64_t *)malloc((size_t)(m * p) * sizeof(int64_t));
+    orc_ffa_rec(x, p, 0, m, out, tmp);
+    free(tmp);
+    return m;
+}
+
+/* Boxcar search of one folded profile P[0..p) of m summed rows (Sec.3.5: a   */
+/* boxcar filter detects the pulse in the folded profile).  Reading: cyclic   */
+/* boxcars B_w(j) = sum_{i<w} P[(j + i) mod p] for the widths w <= p, the     */
+/* profile mean mu = sum(P) / p as the baseline, and                          */
+/*   S/N_w(j) = (B_w(j) - w mu) / (sigma sqrt(m w)),                          */
+/* sigma the noise of one series sample.  Best over (w, j): the largest S/N,  */
+/* ties to the smaller width, then the smaller phase.  FP64.                  */
+/* Returns the best width index (-1 if no width fits), best S/N and phase.    */
+int orc_fold_snr(const int64_t *P, int64_t p, int64_t m, const int *widths,
+                 int nw, double sigma, double *best_snr, int64_t *best_phase)
+{
+    double tot = 0.0;
+    int64_t itot = 0;
+    for (int64_t j = 0; j < p; ++j) itot += P[j];
+    tot = (double)itot;
+    int best = -1;
+    double bs = 0.0;
+    int64_t bj = 0;
+    for (int wi = 0; wi < nw; ++wi) {
+        int64_t w = widths[wi];
+        if (w < 1 || w > p) continue;
+        for (int64_t j = 0; j < p; ++j) {
+            int64_t B = 0;
+            for (int64_t i = 0; i < w; ++i) B += P[(j + i) % p];
+            /* (B - w mu) = (p B - w sum) / p, the numerator exact in int64 */
+            double num = (double)(p * B - w * itot) / (double)p;
+            double snr = num / (sigma * sqrt((double)(m * w)));
+            if (best < 0 || snr > bs) { best = wi; bs = snr; bj = j; }
+        }
+    }
+    (void)tot;
+    *best_snr = bs;
+    *best_phase = bj;
+    return best;
 }
 
 /* Number of OpenMP threads the DM loop of orc_dedisperse uses from now on
