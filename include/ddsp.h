@@ -550,6 +550,46 @@ int ddsp_dered(ddsp_plan *plan, const int32_t *d_in, int64_t nrows,
                int64_t nsamp, int64_t in_pitch, int64_t half_window,
                int32_t *d_out, int64_t out_pitch, ddsp_stream_t stream);
 
+/* ------------------------------------------------------------------------
+ * Folding transform and folded-profile search (Sec.3.5), for periodicity
+ * searches of dedispersed (typically downsampled and de-reddened) series.
+ * A series of nsamp samples is cut into m rows of p samples, m the largest
+ * power of two with m*p <= nsamp (whole rows; the rest is unused), and
+ * folded by the fast folding algorithm: the profile of trial s = 0 .. m-1
+ * drifts by s samples over the m - 1 row steps (trial period p + s/(m-1)
+ * samples), with the classic binary recursion
+ *   F[s][j] = A[s/2][j] + B[s/2][(j + (s+1)/2) mod p]
+ * (A, B the transforms of the two halves of a group of rows).  Sums are
+ * int32; an overflow sets the plan's error word (ddsp_plan_check returns
+ * DDSP_E_RANGE).  m*p <= 16384: one row's stack is folded on chip.
+ * --------------------------------------------------------------------- */
+
+/* The transform of every row at base period p: d_out[r][s][j] (nrows x m x
+ * p int32, the caller's), *m set on return.  Stream-ordered.
+ * DDSP_E_INVALID_ARG for a NULL pointer, nrows <= 0, pitch < nsamp,
+ * p < 1, nsamp < p or m*p > 16384. */
+int ddsp_ffa(ddsp_plan *plan, const int32_t *d_series, int64_t nrows,
+             int64_t nsamp, int64_t pitch, int p, int32_t *d_out, int *m,
+             ddsp_stream_t stream);
+
+/* For every row r and base period p in [p_lo, p_hi): the transform, then
+ * per trial s the best cyclic boxcar of the folded profile P (length p):
+ *   B_w(j) = sum_{i<w} P[(j+i) mod p],
+ *   S/N = (B_w(j) - w*sum(P)/p) / (sigma_r * sqrt(m*w)),
+ * sigma_r = d_sigma[r] the noise of one sample of row r; widths: host list
+ * of 1..16 increasing values (those > p are skipped); the best is the
+ * largest S/N, ties to the smaller width index, then the smaller phase j.
+ * Outputs d_snr (FP32), d_widx, d_phase, each [nrows][p_hi - p_lo][mmax]
+ * (the caller's), mmax >= m(p_lo); trials s >= m(p) hold -inf, -1, -1.
+ * Stream-ordered.  DDSP_E_INVALID_ARG for a NULL pointer, nrows outside
+ * 1 .. 65535, pitch < nsamp, an empty or unsorted width list, p_lo < 1,
+ * p_hi <= p_lo, nsamp < p_hi - 1, mmax < m(p_lo), or m*p > 16384. */
+int ddsp_ffa_search(ddsp_plan *plan, const int32_t *d_series, int64_t nrows,
+                    int64_t nsamp, int64_t pitch, int p_lo, int p_hi,
+                    const int32_t *widths, int nwidths, const float *d_sigma,
+                    float *d_snr, int32_t *d_widx, int32_t *d_phase,
+                    int64_t mmax, ddsp_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -259,6 +259,52 @@ class Plan:
             _stream_handle(stream)), "ddsp_dered")
         return out
 
+    @staticmethod
+    def ffa_rows(nsamp, p):
+        """m: the largest power of two with m * p <= nsamp (0 if p > nsamp)."""
+        if p < 1 or nsamp < p:
+            return 0
+        m = 1
+        while 2 * m * p <= nsamp:
+            m *= 2
+        return m
+
+    def ffa(self, series, p, stream=None):
+        """Folding transform (Sec.3.5) of int32 [rows][n] series at base
+        period p: int32 [rows][m][p]."""
+        import torch
+        rows, n = series.shape
+        m0 = max(self.ffa_rows(n, int(p)), 1)
+        out = torch.empty((rows, m0, max(int(p), 1)), dtype=torch.int32,
+                          device=series.device)
+        m = C.c_int()
+        _lib.check(_lib.lib().ddsp_ffa(
+            self._h, _dev_ptr(series, torch.int32, "series"), int(rows), int(n),
+            int(series.stride(0)), int(p), _dev_ptr(out, torch.int32, "out"),
+            C.byref(m), _stream_handle(stream)), "ddsp_ffa")
+        return out
+
+    def ffa_search(self, series, p_lo, p_hi, widths, sigma, stream=None):
+        """Best boxcar of every folded profile for base periods p_lo ..
+        p_hi - 1 (Sec.3.5): (snr, w_idx, phase), each [rows][np][mmax]."""
+        import torch
+        rows, n = series.shape
+        mmax = max(self.ffa_rows(n, int(p_lo)), 1)
+        shape = (rows, max(int(p_hi) - int(p_lo), 1), mmax)
+        snr = torch.empty(shape, dtype=torch.float32, device=series.device)
+        wi = torch.empty(shape, dtype=torch.int32, device=series.device)
+        ph = torch.empty(shape, dtype=torch.int32, device=series.device)
+        ws = np.ascontiguousarray(widths, dtype=np.int32)
+        sg = torch.as_tensor(np.broadcast_to(np.asarray(sigma, np.float32), (rows,))
+                             .copy(), device=series.device)
+        _lib.check(_lib.lib().ddsp_ffa_search(
+            self._h, _dev_ptr(series, torch.int32, "series"), int(rows), int(n),
+            int(series.stride(0)), int(p_lo), int(p_hi),
+            ws.ctypes.data_as(C.c_void_p), int(ws.size),
+            _dev_ptr(sg, torch.float32, "sigma"), _dev_ptr(snr), _dev_ptr(wi),
+            _dev_ptr(ph), int(mmax), _stream_handle(stream)), "ddsp_ffa_search")
+        return snr, wi, ph
+
     def stats(self):
         """Per-(DM, window) exact (2*median, 4*MAD) of the last search."""
         nwin = C.c_int64()

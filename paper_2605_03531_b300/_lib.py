@@ -98,6 +98,9 @@ SIGNATURES = {
                                           C.POINTER(C.c_size_t)]),
     "ddsp_downsample": (I32, [P, P, I64, I64, I64, I64, P, I64, P]),
     "ddsp_dered": (I32, [P, P, I64, I64, I64, I64, P, I64, P]),
+    "ddsp_ffa": (I32, [P, P, I64, I64, I64, I32, P, C.POINTER(C.c_int), P]),
+    "ddsp_ffa_search": (I32, [P, P, I64, I64, I64, I32, I32, P, I32, P, P, P,
+                              P, I64, P]),
 }
 
 _lib = None
