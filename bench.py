@@ -770,6 +770,136 @@ def run_dered(args):
     return 0
 
 
+# ------------------------------------------------ folding transform + search
+FFA_METRIC = "FFA trial periods folded and searched/s"
+
+
+def ffa_work(n, p_lo, p_hi, wmax):
+    """(trial periods, algorithmic adds) of one row: per base period m*p*
+    log2(m) transform adds and m*p*wmax running-window adds."""
+    trials = adds = 0
+    for p in range(p_lo, p_hi):
+        m = 1
+        while 2 * m * p <= n:
+            m *= 2
+        trials += m
+        adds += m * p * (m.bit_length() - 1) + m * p * wmax
+    return trials, adds
+
+
+def run_ffa(args):
+    """1024 DM-trial series of 16384 samples (a downsampled, de-reddened
+    stretch of the beam: seeded Gaussian, mean 0, sd 1024, 0.1% boxcar
+    events), folded at the base periods 128..255 (trial periods 128-256
+    samples, one octave) and searched with boxcars of 1-32 samples."""
+    import torch
+    from paper_2605_03531_b300 import Plan, build, shard, synth
+    build.build()
+    world, rank, local = dist_setup(args.gpus)
+    dev = torch.device("cuda", local if world > 1 else 0)
+    rows, n, p_lo, p_hi = 1024, 16384, 128, 256
+    widths = [1, 2, 4, 8, 16, 32]
+    x = synth.gaussian_series(rows, n, seed=shard.rank_seed(16, rank), mean=0.0,
+                              device=dev)
+    plan = Plan(16, 500.0, -1.0, 1e-3, np.zeros(4), [1, 2], nbits=8,
+                norm_window=8192, cand_capacity=1024)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        out = plan.ffa_search(x, p_lo, p_hi, widths, 1024.0, stream=stream)
+    torch.cuda.synchronize(dev)
+    plan.check()
+    clocks = ClockSampler(dev.index or 0)
+    if not args.profile:
+        clocks.start()
+        time.sleep(0.3)
+    barrier(world)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        out = plan.ffa_search(x, p_lo, p_hi, widths, 1024.0, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ck = clocks.stop()
+    plan.check()
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
+    trials, adds = ffa_work(n, p_lo, p_hi, widths[-1])
+    if args.profile:
+        if rank == 0:
+            print(json.dumps({"profile": True, "workload": "ffa", "ms_per_step": ms}),
+                  flush=True)
+        return 0
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    clk = (ck or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2032.0)
+    peak = SM_COUNT_B300 * ADDS_PER_SM_CLK * clk * 1e6 / 1e12
+    achieved = rows * adds / (ms * 1e-3) / 1e12
+    # end to end: the rows from pinned host memory, the S/N back
+    xh = x.cpu().pin_memory()
+
+    def e2e_step():
+        x.copy_(xh, non_blocking=True)
+        snr, wi, ph = plan.ffa_search(x, p_lo, p_hi, widths, 1024.0, stream=stream)
+        return snr.cpu()
+
+    e2e_step()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        res = e2e_step()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world) / args.steps
+    snr = out[0]
+    best = float(snr.max())
+    if rank == 0:
+        result = {
+            "metric": FFA_METRIC, "value": world * rows * trials / (ms * 1e-3),
+            "unit": "trials/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": {"workload": f"FFA search of {rows} x {n}-sample series, "
+                                   f"base periods {p_lo}-{p_hi - 1}, boxcars 1-32",
+                       "rows": rows, "nsamp": n, "p_lo": p_lo, "p_hi": p_hi,
+                       "l2": "each row's stack is folded on chip; the 64 MB "
+                             "input stays in L2 across periods"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
+                         "unit": "Tadd/s", "frac": achieved / peak, "traffic": None,
+                         "kernel": "ffa_search_kernel",
+                         "peak_basis": f"{SM_COUNT_B300} SMs x {ADDS_PER_SM_CLK} "
+                                       f"adds/clk x {clk:.0f} MHz",
+                         "adds_basis": "m p log2(m) transform adds + m p w_max "
+                                       "window adds per (row, base period)"},
+            "trials_per_step": rows * trials, "best_snr": best,
+            "e2e": {"value": world * rows * trials / e2e_s, "unit": "trials/s",
+                    "h2d_bytes_per_step": int(4 * rows * n),
+                    "d2h_bytes_per_step": int(res.numel() * 4),
+                    "ms_per_step": e2e_s * 1e3},
+            "gpu_launches": args.steps, "clocks": ck}
+        if not args.no_cpu_baseline:
+            import oracle
+            xr = x[0].cpu().numpy()
+            t0 = time.perf_counter()
+            done = 0
+            p = p_lo
+            while time.perf_counter() - t0 < args.cpu_seconds and p < p_hi:
+                F = oracle.ffa(xr, p)
+                for s_ in range(F.shape[0]):
+                    oracle.fold_snr(F[s_], F.shape[0], widths, 1024.0)
+                done += F.shape[0]
+                p += 1
+            el = time.perf_counter() - t0
+            result["cpu_baseline"] = {
+                "value": done / el, "unit": "trials/s", "cores": 1,
+                "kind": "oracle",
+                "sample": f"row 0, base periods {p_lo}-{p - 1} ({done} trials, "
+                          f"{el:.1f} s, one thread)"}
+        print(json.dumps(result), flush=True)
+    return 0
+
+
 # ----------------------------------------------------- uneven multi-beam batch
 def run_batch(args):
     """160 beams of uneven shape (1024/2048/4096 channels in a 2:1:1 mix,
@@ -1012,7 +1142,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["beam", "sps", "batch", "serve",
-                                           "cluster", "dered"],
+                                           "cluster", "dered", "ffa"],
                     default="beam",
                     help="beam: the full path on one 4096-channel beam block "
                          "(headline); sps: the search-only stress case; batch: "
@@ -1020,7 +1150,7 @@ def main():
                          "real-time streaming beams (--steps blocks per beam); "
                          "cluster: peaks filter + DBSCAN of a candidate list; "
                          "dered: running-median de-reddening of the beam's "
-                         "series")
+                         "series; ffa: folding transform + profile search")
     ap.add_argument("--nbeams", type=int, default=0, help="batch: beams (0 = 160)")
     ap.add_argument("--inflight", type=int, default=1,
                     help="serve: batched steps queued on the device at once")
@@ -1049,6 +1179,8 @@ def main():
         return run_cluster(args)
     if args.workload == "dered":
         return run_dered(args)
+    if args.workload == "ffa":
+        return run_ffa(args)
     return run_ours(args)
 
 

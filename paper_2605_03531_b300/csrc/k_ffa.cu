@@ -10,13 +10,15 @@
 // recursion: profile s drifts by s samples over the m - 1 row steps, i.e.
 // trial period p + s/(m - 1)).  Sums are int32, checked on every add.
 //
-// The search gives one warp to each profile: lanes take phases j and extend
-// a running window sum sample by sample, so every width of the (ascending)
-// list costs one add per sample of the widest window; the numerator
-// p*B - w*S of S/N = (B - w*S/p) / (sigma*sqrt(m*w)) is exact in int64 and
-// rounded to FP32 once (hi/lo split, magic-number conversion, one fma);
-// the warp keeps the largest S/N, ties to the smaller width, then the
-// smaller phase.
+// The search gives one warp to each profile: it writes the profile's
+// exclusive prefix sums (mod 2^32) into the spare transform buffer, and when
+// every boxcar sum of the profile fits int32 (w_max * max|P| < 2^31) a
+// cyclic boxcar is a difference of two of them; otherwise the lanes extend
+// running int64 window sums.  The numerator p*B - w*S of
+// S/N = (B - w*S/p) / (sigma*sqrt(m*w)) is exact in int64 and rounded to
+// FP32 once (hi/lo split, magic-number conversion, one fma), then scaled by
+// the width's 1/(p sigma sqrt(m w)); the largest S/N wins, ties to the
+// smaller width, then the smaller phase.
 #include <math.h>
 #include <stdint.h>
 
@@ -48,25 +50,33 @@ __device__ __forceinline__ float i64_to_float(long long v) {
 }
 
 // Transform the stack in buf0 (m rows of p); returns the buffer holding the
-// result.
+// result.  One warp per output row, lanes along the row: the row's sources
+// and shift are found once per row.
 __device__ int32_t *ffa_levels(int32_t *buf0, int32_t *buf1, int p, int m,
                                int32_t *err) {
   int32_t *src = buf0, *dst = buf1;
-  const int total = m * p;
-  for (int n = 2; n <= m; n *= 2) {
-    const int half = n / 2;
-    for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
-      const int row = idx / p, j = idx - row * p;
-      const int g = row / n, s = row - g * n;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nwarps = blockDim.x >> 5;
+  for (int lg = 1; (1 << lg) <= m; ++lg) {
+    const int n = 1 << lg, half = n >> 1;
+    bool bad = false;
+    for (int row = warp; row < m; row += nwarps) {
+      const int g = row >> lg, s = row & (n - 1);
       const int a = s >> 1;
-      int sh = ((s + 1) >> 1) % p;
-      int jj = j + sh;
-      if (jj >= p) jj -= p;
-      const long long v = (long long)src[(g * n + a) * p + j] +
-                          (long long)src[(g * n + half + a) * p + jj];
-      if (v < INT32_MIN || v > INT32_MAX) atomicExch(err, kErrRange);
-      dst[idx] = (int32_t)v;
+      const int sh = ((s + 1) >> 1) % p;
+      const int32_t *A = src + (g * n + a) * p;
+      const int32_t *B = src + (g * n + half + a) * p;
+      int32_t *D = dst + row * p;
+      for (int j = lane; j < p; j += 32) {
+        int jj = j + sh;
+        if (jj >= p) jj -= p;
+        const int32_t u = A[j], w = B[jj];
+        const int32_t v = (int32_t)((uint32_t)u + (uint32_t)w);
+        bad |= ((u ^ v) & (w ^ v)) < 0;      // signed overflow of u + w
+        D[j] = v;
+      }
     }
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicExch(err, kErrRange);
     __syncthreads();
     int32_t *t = src;
     src = dst;
@@ -112,6 +122,7 @@ ffa_search_kernel(const int32_t *__restrict__ in, int64_t nsamp, int64_t pitch,
   __syncthreads();
   const int32_t *F = ffa_levels(buf0, buf1, p, m, err);
 
+  int32_t *spare = F == buf0 ? buf1 : buf0;   // profiles' prefix sums
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int nwarps = blockDim.x >> 5;
   // widths that fit the profile, and their FP32 scales 1/(p sigma sqrt(m w))
@@ -119,6 +130,11 @@ ffa_search_kernel(const int32_t *__restrict__ in, int64_t nsamp, int64_t pitch,
   while (nw < W.n && W.w[nw] <= p) ++nw;
   const int wmax = nw > 0 ? W.w[nw - 1] : 0;
   const float sg = sigma[row];
+  __shared__ float inv[kFfaMaxWidths];
+  if (threadIdx.x < kFfaMaxWidths)
+    inv[threadIdx.x] = (int)threadIdx.x < nw
+        ? 1.0f / (p * sg * sqrtf((float)m * (float)W.w[threadIdx.x])) : 0.0f;
+  __syncthreads();
   const int64_t obase = (row * gridDim.x + blockIdx.x) * mmax;
   for (int s = warp; s < (int)mmax; s += nwarps) {
     if (s >= m || nw == 0) {
@@ -130,32 +146,76 @@ ffa_search_kernel(const int32_t *__restrict__ in, int64_t nsamp, int64_t pitch,
       continue;
     }
     const int32_t *P = F + s * p;
+    uint32_t *Q = reinterpret_cast<uint32_t *>(spare) + s * p;
+    // exclusive prefix sums (mod 2^32), the total and the largest |P|
     long long S = 0;
-    for (int j = lane; j < p; j += 32) S += P[j];
+    uint32_t run = 0, amax = 0;
+    for (int j0 = 0; j0 < p; j0 += 32) {
+      const int j = j0 + lane;
+      const int32_t v = j < p ? P[j] : 0;
+      amax = max(amax, v < 0 ? 0u - (uint32_t)v : (uint32_t)v);
+      S += v;
+      uint32_t inc = (uint32_t)v;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) S += __shfl_xor_sync(0xffffffffu, S, o);
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t u = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += u;
+      }
+      if (j < p) Q[j] = run + inc - (uint32_t)v;
+      run += __shfl_sync(0xffffffffu, inc, 31);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      S += __shfl_xor_sync(0xffffffffu, S, o);
+      amax = max(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+    }
+    __syncwarp();
+    // every boxcar sum fits int32, so prefix differences mod 2^32 are exact
+    const bool fast = (unsigned long long)amax * (unsigned long long)wmax <
+                      0x80000000ull;
+    const uint32_t Sq = (uint32_t)S;
     float best = -INFINITY;
     int bw = 0, bj = 0;
     for (int j = lane; j < p; j += 32) {
-      long long B = 0;
-      int wi = 0, jj = j;
-      for (int i = 0; i < wmax; ++i) {
-        B += P[jj];
-        if (++jj == p) jj = 0;
-        if (i + 1 == W.w[wi]) {
+      if (fast) {
+        const uint32_t q0 = Q[j];
+        for (int wi = 0; wi < nw; ++wi) {
+          const int e = j + W.w[wi];
+          const uint32_t q1 = e < p ? Q[e] : Sq + Q[e - p];
+          const int32_t B = (int32_t)(q1 - q0);
           const long long num = (long long)p * B - (long long)W.w[wi] * S;
           const float nf = (num < (1ll << 43) && num > -(1ll << 43))
                                ? i64_to_float(num) : __ll2float_rn(num);
-          const float sn = nf / (p * sg * sqrtf((float)m * (float)W.w[wi]));
+          const float sn = nf * inv[wi];
           if (sn > best || (sn == best && (wi < bw || (wi == bw && j < bj)))) {
             best = sn;
             bw = wi;
             bj = j;
           }
-          ++wi;
+        }
+      } else {
+        long long B = 0;
+        int wi = 0, jj = j;
+        for (int i = 0; i < wmax; ++i) {
+          B += P[jj];
+          if (++jj == p) jj = 0;
+          if (i + 1 == W.w[wi]) {
+            const long long num = (long long)p * B - (long long)W.w[wi] * S;
+            const float nf = (num < (1ll << 43) && num > -(1ll << 43))
+                                 ? i64_to_float(num) : __ll2float_rn(num);
+            const float sn = nf * inv[wi];
+            if (sn > best || (sn == best && (wi < bw || (wi == bw && j < bj)))) {
+              best = sn;
+              bw = wi;
+              bj = j;
+            }
+            ++wi;
+          }
         }
       }
     }
+    // ties go to the smaller width, then the smaller phase, within and
+    // across lanes
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       const float ob = __shfl_xor_sync(0xffffffffu, best, o);
