@@ -19,7 +19,8 @@ the passage of the paper its C function writes out:
 * ``downsample``, ``running_median``, ``dered`` -- downsampling by a user
   factor (Sec.3.2) and running-median de-reddening (Sec.3.3);
 * ``ffa``, ``fold_snr`` -- the folding transform by the fast folding
-  algorithm and the boxcar search of a folded profile, Sec.3.5.
+  algorithm and the boxcar search of a folded profile, Sec.3.5;
+* ``resample`` -- resampling for the frequency derivatives, Sec.3.4.
 """
 import ctypes as C
 import os
@@ -93,6 +94,9 @@ def lib():
         L.orc_fold_snr.argtypes = [P, C.c_int64, C.c_int64, P, C.c_int,
                                    C.c_double, C.POINTER(C.c_double),
                                    C.POINTER(C.c_int64)]
+        L.orc_resample.restype = C.c_int64
+        L.orc_resample.argtypes = [P, C.c_int64, C.c_double, C.c_double,
+                                   C.c_double, C.c_double, P, C.c_int64]
         L.orc_set_threads.restype = None
         L.orc_set_threads.argtypes = [C.c_int]
         _lib = L
@@ -384,3 +388,16 @@ def fold_snr(P, m, widths, sigma):
     wi = lib().orc_fold_snr(_ptr(P), P.size, int(m), _ptr(ws), ws.size,
                             float(sigma), C.byref(s), C.byref(ph))
     return wi, s.value, ph.value
+
+
+# ---------------------------------------------------------------- resampling
+def resample(x, f0, f1, f2, tsamp):
+    """Series resampled for f = f0 + f1 t + f2 t^2 / 2 (Sec.3.4), FP64."""
+    x = np.ascontiguousarray(x, dtype=np.int32)
+    cap = 2 * x.size + 16
+    out = np.empty(cap, dtype=np.float64)
+    k = lib().orc_resample(_ptr(x), x.size, float(f0), float(f1), float(f2),
+                           float(tsamp), _ptr(out), cap)
+    if k < 0:
+        raise ValueError("bad resampling arguments")
+    return out[:k]

@@ -23,7 +23,8 @@
  *   - downsampling of a dedispersed series by a user factor (Sec.3.2) and
  *                        running-median de-reddening (Sec.3.3);
  *   - the folding transform of a series by the fast folding algorithm and
- *                        the boxcar search of its folded profiles, Sec.3.5.
+ *                        the boxcar search of its folded profiles, Sec.3.5;
+ *   - resampling for the frequency derivatives f1, f2, Sec.3.4.
  * Readings where the paper is silent (channel frequencies, output length,
  * boxcar alignment, window layout, even-count median, MAD = 0) are listed at
  * each function.
@@ -596,6 +597,67 @@ int orc_fold_snr(const int64_t *P, int64_t p, int64_t m, const int *widths,
     *best_snr = bs;
     *best_phase = bj;
     return best;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Resampling for a frequency derivative (Sec.3.4).  A signal of frequency    */
+/* f = f0 + f1 t + f2 t^2/2 is brought to a constant frequency by resampling  */
+/* the series with the Doppler-transformed sampling interval                  */
+/*   tau = tau0 (1 + f' t / f0 + f'' t^2 / (2 f0)),                           */
+/* where f' = -f1, f'' = -f2 when f1 <= 0.  When f1 > 0 the series is        */
+/* reversed, transformed with f0~ = f0 + f1 T + f2 T^2/2, f' = f1 + f2 T and  */
+/* f'' = -f2 (T = n tau0 the duration), and reversed back.                    */
+/* Reading: output bin k starts at t_k and lasts tau evaluated at its         */
+/* nominal time t = k tau0; t_0 = 0 and t_{k+1} = t_k + tau_k, accumulated    */
+/* here bin by bin; the bins kept are those ending by T; out[k] sums the      */
+/* input bins [i tau0, (i+1) tau0) weighted by their overlap with             */
+/* [t_k, t_{k+1}) over tau0 (fractional powers).  FP64 throughout; times in   */
+/* units of tau0.  Returns the number of output bins (at most cap), -1 on a   */
+/* bad argument (f0 <= 0, n < 1, or an interval <= 0).                        */
+/* ------------------------------------------------------------------------ */
+int64_t orc_resample(const int32_t *x, int64_t n, double f0, double f1,
+                     double f2, double tau0, double *out, int64_t cap)
+{
+    if (n < 1 || !(f0 > 0.0) || !(tau0 > 0.0)) return -1;
+    const double T = (double)n * tau0;
+    const int rev = f1 > 0.0;
+    double F0 = f0, fp = -f1, fpp = -f2;
+    if (rev) {
+        F0 = f0 + f1 * T + f2 * T * T / 2.0;
+        fp = f1 + f2 * T;
+        fpp = -f2;
+        if (!(F0 > 0.0)) return -1;
+    }
+    int64_t k = 0;
+    double tk = 0.0;                    /* in units of tau0 */
+    while (k < cap) {
+        double t = (double)k * tau0;
+        double w = 1.0 + fp * t / F0 + fpp * t * t / (2.0 * F0);  /* tau/tau0 */
+        if (!(w > 0.0)) return -1;
+        double te = tk + w;
+        if (te > (double)n) break;
+        double acc = 0.0;
+        int64_t i0 = (int64_t)floor(tk), i1 = (int64_t)floor(te);
+        for (int64_t i = i0; i <= i1 && i < n; ++i) {
+            double lo = tk > (double)i ? tk : (double)i;
+            double hi = te < (double)(i + 1) ? te : (double)(i + 1);
+            if (hi > lo) {
+                double xi = rev ? (double)x[n - 1 - i] : (double)x[i];
+                acc += xi * (hi - lo);
+            }
+        }
+        out[k] = acc;
+        tk = te;
+        ++k;
+    }
+    if (rev) {
+        for (int64_t a = 0, b = k - 1; a < b; ++a, --b) {
+            double t = out[a];
+            out[a] = out[b];
+            out[b] = t;
+        }
+    }
+    return k;
 }
 
 /* Number of OpenMP threads the DM loop of orc_dedisperse uses from now on
