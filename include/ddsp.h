@@ -590,6 +590,35 @@ int ddsp_ffa_search(ddsp_plan *plan, const int32_t *d_series, int64_t nrows,
                     float *d_snr, int32_t *d_widx, int32_t *d_phase,
                     int64_t mmax, ddsp_stream_t stream);
 
+/* ------------------------------------------------------------------------
+ * Resampling for frequency derivatives (Sec.3.4): a periodic signal of
+ * frequency f0 + f1 t + f2 t^2/2 (t from the first sample, tsamp seconds per
+ * sample) is brought to a constant frequency.  Output bin k lasts
+ * tau_k = tsamp (1 + f' t/F + f'' t^2/(2F)) at t = k tsamp, with F = f0,
+ * f' = -f1, f'' = -f2 when f1 <= 0; when f1 > 0 the series is reversed,
+ * transformed with F = f0 + f1 T + f2 T^2/2, f' = f1 + f2 T, f'' = -f2
+ * (T = nsamp tsamp) and the result reversed, so the signal ends at
+ * frequency F.  out[k] sums the input samples the bin overlaps, each
+ * weighted by the overlap in samples (FP64 arithmetic, FP32 output); the
+ * bins kept are those ending within the series.
+ * --------------------------------------------------------------------- */
+
+/* The number of output bins for these parameters.  DDSP_E_INVALID_ARG for
+ * nsamp < 1, tsamp <= 0, f0 <= 0 (or F <= 0), non-finite derivatives, a
+ * bin width <= 0 before the end of the series, or widths averaging below
+ * about one half of a sample. */
+int ddsp_resample_length(int64_t nsamp, double tsamp, double f0, double f1,
+                         double f2, int64_t *nout);
+
+/* Resample every row: d_out[r][k], k < *nout (out_pitch >= *nout, the
+ * caller's FP32 buffer).  Stream-ordered.  Errors as ddsp_resample_length,
+ * plus DDSP_E_INVALID_ARG for a NULL pointer, nrows <= 0, in_pitch < nsamp
+ * or out_pitch < *nout. */
+int ddsp_resample(ddsp_plan *plan, const int32_t *d_in, int64_t nrows,
+                  int64_t nsamp, int64_t in_pitch, double tsamp, double f0,
+                  double f1, double f2, float *d_out, int64_t out_pitch,
+                  int64_t *nout, ddsp_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

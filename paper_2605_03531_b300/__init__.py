@@ -305,6 +305,31 @@ class Plan:
             _dev_ptr(ph), int(mmax), _stream_handle(stream)), "ddsp_ffa_search")
         return snr, wi, ph
 
+    @staticmethod
+    def resample_length(nsamp, tsamp, f0, f1, f2):
+        """Output bins of ``resample`` for these parameters."""
+        k = C.c_int64()
+        _lib.check(_lib.lib().ddsp_resample_length(
+            int(nsamp), float(tsamp), float(f0), float(f1), float(f2),
+            C.byref(k)), "ddsp_resample_length")
+        return k.value
+
+    def resample(self, series, tsamp, f0, f1, f2, stream=None):
+        """int32 [rows][n] CUDA tensor resampled for f = f0 + f1 t +
+        f2 t^2 / 2 (Sec.3.4): float32 [rows][nout]."""
+        import torch
+        rows, n = series.shape
+        nout = self.resample_length(n, tsamp, f0, f1, f2)
+        out = torch.empty((rows, max(nout, 1)), dtype=torch.float32,
+                          device=series.device)
+        k = C.c_int64()
+        _lib.check(_lib.lib().ddsp_resample(
+            self._h, _dev_ptr(series, torch.int32, "series"), int(rows), int(n),
+            int(series.stride(0)), float(tsamp), float(f0), float(f1), float(f2),
+            _dev_ptr(out, torch.float32, "out"), int(out.stride(0)), C.byref(k),
+            _stream_handle(stream)), "ddsp_resample")
+        return out[:, :k.value]
+
     def stats(self):
         """Per-(DM, window) exact (2*median, 4*MAD) of the last search."""
         nwin = C.c_int64()

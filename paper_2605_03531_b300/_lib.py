@@ -101,6 +101,10 @@ SIGNATURES = {
     "ddsp_ffa": (I32, [P, P, I64, I64, I64, I32, P, C.POINTER(C.c_int), P]),
     "ddsp_ffa_search": (I32, [P, P, I64, I64, I64, I32, I32, P, I32, P, P, P,
                               P, I64, P]),
+    "ddsp_resample_length": (I32, [I64, C.c_double, C.c_double, C.c_double,
+                                   C.c_double, PI64]),
+    "ddsp_resample": (I32, [P, P, I64, I64, I64, C.c_double, C.c_double,
+                            C.c_double, C.c_double, P, I64, PI64, P]),
 }
 
 _lib = None
