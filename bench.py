@@ -900,6 +900,108 @@ def run_ffa(args):
     return 0
 
 
+# ------------------------------------------------------------------ resample
+RESAMPLE_METRIC = "series samples resampled/s"
+
+
+def run_resample(args):
+    """1024 series of 262144 int32 samples (the beam's series shape, seeded
+    Gaussian with events) resampled for a signal of f0 = 3 Hz, f1 = -2e-4
+    Hz/s, f2 = -1e-8 Hz/s^2 at 81.92 us per sample (a drift of ~0.15 % over
+    the 21.5 s block).  One step: one ddsp_resample call over all rows."""
+    import torch
+    from paper_2605_03531_b300 import Plan, build, shard, synth
+    build.build()
+    world, rank, local = dist_setup(args.gpus)
+    dev = torch.device("cuda", local if world > 1 else 0)
+    rows, n, ts, f0, f1, f2 = 1024, 262144, 81.92e-6, 3.0, -2e-4, -1e-8
+    x = synth.gaussian_series(rows, n, seed=shard.rank_seed(17, rank), device=dev)
+    plan = Plan(16, 500.0, -1.0, 1e-3, np.zeros(4), [1, 2], nbits=8,
+                norm_window=8192, cand_capacity=1024)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(args.warmup):
+        y = plan.resample(x, ts, f0, f1, f2, stream=stream)
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(dev.index or 0)
+    if not args.profile:
+        clocks.start()
+        time.sleep(0.3)
+    barrier(world)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        y = plan.resample(x, ts, f0, f1, f2, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ck = clocks.stop()
+    ms = max_over_ranks(e0.elapsed_time(e1) / args.steps, world)
+    if args.profile:
+        if rank == 0:
+            print(json.dumps({"profile": True, "workload": "resample",
+                              "ms_per_step": ms}), flush=True)
+        return 0
+    K = y.shape[1]
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm = peaks.get("hbm_gbs", 6400.0)
+    nbytes = 4.0 * rows * n + 4.0 * rows * K
+    achieved = nbytes / (ms * 1e-3) / 1e9
+    xh = x.cpu().pin_memory()
+    yh = torch.empty((rows, K), dtype=torch.float32).pin_memory()
+
+    def e2e_step():
+        x.copy_(xh, non_blocking=True)
+        yy = plan.resample(x, ts, f0, f1, f2, stream=stream)
+        yh.copy_(yy, non_blocking=True)
+        torch.cuda.synchronize(dev)
+
+    e2e_step()
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        e2e_step()
+    e2e_s = max_over_ranks(time.perf_counter() - t0, world) / args.steps
+    if rank == 0:
+        result = {
+            "metric": RESAMPLE_METRIC, "value": world * rows * n / (ms * 1e-3),
+            "unit": "samples/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"resampling of {rows} x {n} int32 series for "
+                                   "f0 3 Hz, f1 -2e-4 Hz/s, f2 -1e-8 Hz/s^2",
+                       "rows": rows, "nsamp": n, "nout": K,
+                       "l2": "inputs larger than L2"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm,
+                         "unit": "GB/s", "frac": achieved / hbm, "traffic": None,
+                         "kernel": "resample_kernel",
+                         "bytes_basis": "4 B read per input + 4 B written per output"},
+            "e2e": {"value": world * rows * n / e2e_s, "unit": "samples/s",
+                    "h2d_bytes_per_step": int(4 * rows * n),
+                    "d2h_bytes_per_step": int(4 * rows * K),
+                    "ms_per_step": e2e_s * 1e3},
+            "gpu_launches": args.steps, "clocks": ck}
+        if not args.no_cpu_baseline:
+            import oracle
+            xr = x[0].cpu().numpy()
+            t0 = time.perf_counter()
+            reps = 0
+            while time.perf_counter() - t0 < args.cpu_seconds:
+                oracle.resample(xr, f0, f1, f2, ts)
+                reps += 1
+            el = time.perf_counter() - t0
+            result["cpu_baseline"] = {
+                "value": reps * n / el, "unit": "samples/s", "cores": 1,
+                "kind": "oracle",
+                "sample": f"row 0 resampled {reps} times ({el:.1f} s, one thread)"}
+        print(json.dumps(result), flush=True)
+    return 0
+
+
 # ----------------------------------------------------- uneven multi-beam batch
 def run_batch(args):
     """160 beams of uneven shape (1024/2048/4096 channels in a 2:1:1 mix,
@@ -1142,7 +1244,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["beam", "sps", "batch", "serve",
-                                           "cluster", "dered", "ffa"],
+                                           "cluster", "dered", "ffa",
+                                           "resample"],
                     default="beam",
                     help="beam: the full path on one 4096-channel beam block "
                          "(headline); sps: the search-only stress case; batch: "
@@ -1150,7 +1253,8 @@ def main():
                          "real-time streaming beams (--steps blocks per beam); "
                          "cluster: peaks filter + DBSCAN of a candidate list; "
                          "dered: running-median de-reddening of the beam's "
-                         "series; ffa: folding transform + profile search")
+                         "series; ffa: folding transform + profile search; "
+                         "resample: resampling for frequency derivatives")
     ap.add_argument("--nbeams", type=int, default=0, help="batch: beams (0 = 160)")
     ap.add_argument("--inflight", type=int, default=1,
                     help="serve: batched steps queued on the device at once")
@@ -1181,6 +1285,8 @@ def main():
         return run_dered(args)
     if args.workload == "ffa":
         return run_ffa(args)
+    if args.workload == "resample":
+        return run_resample(args)
     return run_ours(args)
 
 

@@ -7,9 +7,9 @@
 // at the bin's nominal time t = k tau0, alpha = f' tau0/f0,
 // beta = f'' tau0^2/(2 f0)), so its start is the closed form
 //   t_k = k + alpha k(k-1)/2 + beta (k-1)k(2k-1)/6
-// and every bin is computed on its own: out[k] sums the one to three input
-// samples it overlaps, each weighted by the overlap (FP64 arithmetic, FP32
-// result).  f1 > 0 reverses the series, uses f0~ = f0 + f1 T + f2 T^2/2,
+// and out[k] sums the one to three input samples the bin overlaps, each
+// weighted by the overlap (FP32, relative to an exact integer sample index
+// taken every 32 bins from the FP64 closed form).  f1 > 0 reverses the series, uses f0~ = f0 + f1 T + f2 T^2/2,
 // f' = f1 + f2 T, f'' = -f2, and reverses the result; f1 <= 0 uses f0,
 // f' = -f1, f'' = -f2.
 #include <math.h>
@@ -81,24 +81,68 @@ int64_t resample_count(int64_t n, const ResampleLaw &L) {
   return K;
 }
 
+constexpr int kRsGroups = 32;
+
+// A warp makes kRsGroups groups of 32 consecutive bins, one bin per lane:
+// lane l first takes group l's first edge from the closed form in FP64 (one
+// FP64 pass per 1024 bins: the FP64 pipe is narrow), split into an integer sample index ib and an FP32
+// fraction; per group a warp prefix sum of the bins' FP32 width
+// deviations from one sample places lane l's bin at ib + l + e, and the
+// overlaps are computed from the bin's own integer sample, so every FP32
+// value stays near 1 (edge error about 2^-22 samples) and the lanes read
+// and write consecutive samples.
 __global__ void resample_kernel(const int32_t *__restrict__ in, int64_t nrows,
                                 int64_t n, int64_t in_pitch, double a, double b,
                                 bool rev, int64_t K, float *__restrict__ out,
                                 int64_t out_pitch) {
-  const int64_t total = nrows * K;
-  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-       idx < total; idx += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = idx / K, k = idx - r * K;
-    const double t0 = bin_start((double)k, a, b);
-    const double t1 = bin_start((double)(k + 1), a, b);
-    const int32_t *x = in + r * in_pitch;
-    double acc = 0.0;
-    const int64_t i0 = (int64_t)floor(t0), i1 = (int64_t)floor(t1);
-    for (int64_t i = max(i0, (int64_t)0); i <= i1 && i < n; ++i) {
-      const double lo = fmax(t0, (double)i), hi = fmin(t1, (double)(i + 1));
-      if (hi > lo) acc += (double)x[rev ? n - 1 - i : i] * (hi - lo);
+  const int lane = threadIdx.x & 31;
+  const int64_t groups = (K + 31) / 32;            // 32 bins each
+  const int64_t supers = (groups + kRsGroups - 1) / kRsGroups;
+  const int64_t total = nrows * supers;
+  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const float af = (float)a, bf = (float)b;
+  for (int64_t sg = w0; sg < total; sg += nw) {
+    const int64_t r = sg / supers, g0 = (sg - r * supers) * kRsGroups;
+    // lane l: the FP64 first edge of group g0 + l (one FP64 pass per 32
+    // groups, the FP64 pipe being narrow)
+    long long ibl = 0;
+    float frl = 0.0f;
+    {
+      const double t0 = bin_start((double)((g0 + (lane % kRsGroups)) * 32), a, b);
+      ibl = (long long)floor(t0);
+      frl = (float)(t0 - (double)ibl);
     }
-    out[r * out_pitch + (rev ? K - 1 - k : k)] = (float)acc;
+    const int32_t *x = in + r * in_pitch;
+    const int gn = (int)min((int64_t)kRsGroups, groups - g0);
+    for (int q = 0; q < gn; ++q) {
+      const long long ib = __shfl_sync(0xffffffffu, ibl, q);
+      const float fr = __shfl_sync(0xffffffffu, frl, q);
+      const int64_t k = (g0 + q) * 32 + lane;
+      const float kf = (float)k;
+      // width deviation from one sample (small), and its exclusive prefix
+      const float dev = k < K ? af * kf + bf * kf * kf : 0.0f;
+      float incl = dev;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const float u = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += u;
+      }
+      if (k >= K) continue;
+      // the bin starts lane + e samples after ib; counted from its own
+      // integer sample it spans [f, f + 1 + dev): every value stays near 1
+      const float e = fr + (incl - dev);
+      const float fl = floorf(e);
+      const float f = e - fl, fe = f + 1.0f + dev;
+      const int64_t base = ib + lane + (int64_t)fl;
+      float acc = 0.0f;
+      for (int d = 0; (float)d < fe && base + d < n; ++d) {
+        const float lo = fmaxf(f, (float)d), hi = fminf(fe, (float)(d + 1));
+        const int64_t i = base + d;
+        if (hi > lo && i >= 0) acc += (float)x[rev ? n - 1 - i : i] * (hi - lo);
+      }
+      out[r * out_pitch + (rev ? K - 1 - k : k)] = acc;
+    }
   }
 }
 
@@ -132,8 +176,9 @@ extern "C" int ddsp_resample(ddsp_plan *h, const int32_t *d_in, int64_t nrows,
   *nout = K;
   if (K == 0) return DDSP_OK;
   DeviceGuard g(h->p.device);
-  const int64_t total = nrows * K;
-  const int64_t blocks = std::min<int64_t>((total + 255) / 256, 148 * 32);
+  const int64_t total =
+      nrows * (((K + 31) / 32 + kRsGroups - 1) / kRsGroups);      // warps
+  const int64_t blocks = std::min<int64_t>((total + 7) / 8, 148 * 32);
   resample_kernel<<<(unsigned)blocks, 256, 0,
                     reinterpret_cast<cudaStream_t>(stream)>>>(
       d_in, nrows, nsamp, in_pitch, L.alpha, L.beta, L.rev, K, d_out,
