@@ -20,7 +20,9 @@ the passage of the paper its C function writes out:
   factor (Sec.3.2) and running-median de-reddening (Sec.3.3);
 * ``ffa``, ``fold_snr`` -- the folding transform by the fast folding
   algorithm and the boxcar search of a folded profile, Sec.3.5;
-* ``resample`` -- resampling for the frequency derivatives, Sec.3.4.
+* ``resample`` -- resampling for the frequency derivatives, Sec.3.4;
+* ``rfi_clean`` -- gptool-style bandpass correction and channel / time
+  flagging of 8-bit spectra, Sec.2.1.
 """
 import ctypes as C
 import os
@@ -97,6 +99,9 @@ def lib():
         L.orc_resample.restype = C.c_int64
         L.orc_resample.argtypes = [P, C.c_int64, C.c_double, C.c_double,
                                    C.c_double, C.c_double, P, C.c_int64]
+        L.orc_rfi_clean.restype = C.c_int
+        L.orc_rfi_clean.argtypes = [P, C.c_int64, C.c_int64, C.c_int, C.c_int,
+                                    C.c_int, C.c_int, P, P, P]
         L.orc_set_threads.restype = None
         L.orc_set_threads.argtypes = [C.c_int]
         _lib = L
@@ -401,3 +406,18 @@ def resample(x, f0, f1, f2, tsamp):
     if k < 0:
         raise ValueError("bad resampling arguments")
     return out[:k]
+
+
+# ---------------------------------------------------------- RFI mitigation
+def rfi_clean(x, hw=10, kc=4, kt=3, rounds=2):
+    """(cleaned uint8 [nt][nc], channel flags, time flags) of a time-major
+    uint8 block (Sec.2.1, gptool style)."""
+    x = np.ascontiguousarray(x, dtype=np.uint8)
+    nt, nc = x.shape
+    out = np.empty_like(x)
+    fc = np.empty(nc, dtype=np.uint8)
+    ft = np.empty(nt, dtype=np.uint8)
+    if lib().orc_rfi_clean(_ptr(x), nt, nc, int(hw), int(kc), int(kt),
+                           int(rounds), _ptr(out), _ptr(fc), _ptr(ft)) != 0:
+        raise ValueError("bad RFI arguments")
+    return out, fc.astype(bool), ft.astype(bool)

@@ -24,7 +24,9 @@
  *                        running-median de-reddening (Sec.3.3);
  *   - the folding transform of a series by the fast folding algorithm and
  *                        the boxcar search of its folded profiles, Sec.3.5;
- *   - resampling for the frequency derivatives f1, f2, Sec.3.4.
+ *   - resampling for the frequency derivatives f1, f2, Sec.3.4;
+ *   - gptool-style RFI mitigation of 8-bit spectra (bandpass, channel and
+ *                        time flags), Sec.2.1.
  * Readings where the paper is silent (channel frequencies, output length,
  * boxcar alignment, window layout, even-count median, MAD = 0) are listed at
  * each function.
@@ -658,6 +660,145 @@ int64_t orc_resample(const int32_t *x, int64_t n, double f0, double f1,
         }
     }
     return k;
+}
+
+/* ------------------------------------------------------------------------ */
+/* RFI mitigation of a block of 8-bit spectra, gptool style (Sec.2.1 and the  */
+/* figure of its steps: bandpass from the mean spectrum median-filtered over  */
+/* 21 channels, channels beyond 4 sigma of the corrected mean spectrum and    */
+/* time samples beyond 3 sigma of the frequency-averaged series flagged,      */
+/* both done twice).  Readings, all in exact integer arithmetic:              */
+/*   round r: s[c] = sum of x[t][c] over unflagged t; b[c] = lower median of  */
+/*   s over channels [c - hw, c + hw] clamped (hw = 10: 21 channels); R =     */
+/*   lower median of b over all channels; e[c] = round(s[c] R / b[c]) (0 if  */
+/*   b[c] = 0); among unflagged channels, with (m2, mad4) = 2 median and 4    */
+/*   MAD of e (orc_median_mad), channel c is flagged when                     */
+/*   20000 |2 e[c] - m2| > kc 14826 mad4 (|e - median| > kc 1.4826 MAD) and   */
+/*   mad4 > 0; y[t][c] = min(255, round(x[t][c] R / b[c])); u[t] = sum of    */
+/*   y[t][c] over unflagged channels; among unflagged t, t is flagged when    */
+/*   20000 |2 u[t] - m2| > kt 14826 mad4 with (m2, mad4) of u.  Flags only    */
+/*   accumulate.  After the rounds, out = y of the last round, with every     */
+/*   flagged channel and time sample set to the fill level                    */
+/*   min(255, round(R / T')), T' the unflagged sample count of that round.    */
+/* round(a / b) = floor((2a + b) / (2b)) for a >= 0, b > 0.                   */
+/* x and out are time-major [nt][nc]; fc[nc], ft[nt] get the flags (0/1).     */
+/* Returns 0, or -1 on a bad argument.                                        */
+/* ------------------------------------------------------------------------ */
+static int orc_cmp_i64(const void *a, const void *b)
+{
+    int64_t x = *(const int64_t *)a, y = *(const int64_t *)b;
+    return (x > y) - (x < y);
+}
+
+static int64_t orc_round_div(int64_t a, int64_t b)
+{
+    return (2 * a + b) / (2 * b);
+}
+
+/* 2 * median and 4 * MAD of v[0..n) (n >= 1), like orc_median_mad. */
+static void orc_median_mad_i64(const int64_t *v, int64_t n, int64_t *m2,
+                               int64_t *mad4)
+{
+    int64_t *w = (int64_t *)malloc((size_t)n * sizeof(int64_t));
+    memcpy(w, v, (size_t)n * sizeof(int64_t));
+    qsort(w, (size_t)n, sizeof(int64_t), orc_cmp_i64);
+    int64_t med2 = w[(n - 1) / 2] + w[n / 2];
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t d = 2 * v[i] - med2;
+        w[i] = d < 0 ? -d : d;
+    }
+    qsort(w, (size_t)n, sizeof(int64_t), orc_cmp_i64);
+    *m2 = med2;
+    *mad4 = w[(n - 1) / 2] + w[n / 2];
+    free(w);
+}
+
+int orc_rfi_clean(const uint8_t *x, int64_t nt, int64_t nc, int hw, int kc,
+                  int kt, int rounds, uint8_t *out, uint8_t *fc, uint8_t *ft)
+{
+    if (nt < 1 || nc < 1 || hw < 0 || kc < 0 || kt < 0 || rounds < 1) return -1;
+    int64_t *s = (int64_t *)malloc((size_t)nc * sizeof(int64_t));
+    int64_t *b = (int64_t *)malloc((size_t)nc * sizeof(int64_t));
+    int64_t *e = (int64_t *)malloc((size_t)nc * sizeof(int64_t));
+    int64_t *u = (int64_t *)malloc((size_t)nt * sizeof(int64_t));
+    int64_t *tmp = (int64_t *)malloc((size_t)(nt > nc ? nt : nc) * sizeof(int64_t));
+    int64_t *win = (int64_t *)malloc((size_t)(2 * hw + 1) * sizeof(int64_t));
+    memset(fc, 0, (size_t)nc);
+    memset(ft, 0, (size_t)nt);
+    int64_t R = 0, tkeep = nt;
+    for (int r = 0; r < rounds; ++r) {
+        tkeep = 0;
+        for (int64_t t = 0; t < nt; ++t) tkeep += !ft[t];
+        for (int64_t c = 0; c < nc; ++c) {
+            int64_t acc = 0;
+            for (int64_t t = 0; t < nt; ++t)
+                if (!ft[t]) acc += x[t * nc + c];
+            s[c] = acc;
+        }
+        for (int64_t c = 0; c < nc; ++c) {
+            int64_t lo = c - hw < 0 ? 0 : c - hw;
+            int64_t hi = c + hw > nc - 1 ? nc - 1 : c + hw;
+            int64_t m = hi - lo + 1;
+            memcpy(win, s + lo, (size_t)m * sizeof(int64_t));
+            qsort(win, (size_t)m, sizeof(int64_t), orc_cmp_i64);
+            b[c] = win[(m - 1) / 2];
+        }
+        memcpy(tmp, b, (size_t)nc * sizeof(int64_t));
+        qsort(tmp, (size_t)nc, sizeof(int64_t), orc_cmp_i64);
+        R = tmp[(nc - 1) / 2];
+        for (int64_t c = 0; c < nc; ++c)
+            e[c] = b[c] > 0 ? orc_round_div(s[c] * R, b[c]) : 0;
+        int64_t k = 0;
+        for (int64_t c = 0; c < nc; ++c)
+            if (!fc[c]) tmp[k++] = e[c];
+        if (k > 0) {
+            int64_t m2, mad4;
+            orc_median_mad_i64(tmp, k, &m2, &mad4);
+            if (mad4 > 0)
+                for (int64_t c = 0; c < nc; ++c) {
+                    int64_t d = 2 * e[c] - m2;
+                    if (!fc[c] && 20000 * (d < 0 ? -d : d) > (int64_t)kc * 14826 * mad4)
+                        fc[c] = 1;
+                }
+        }
+        for (int64_t t = 0; t < nt; ++t) {
+            int64_t acc = 0;
+            for (int64_t c = 0; c < nc; ++c) {
+                int64_t y = b[c] > 0 ? orc_round_div((int64_t)x[t * nc + c] * R, b[c]) : 0;
+                if (y > 255) y = 255;
+                if (!fc[c]) acc += y;
+            }
+            u[t] = acc;
+        }
+        k = 0;
+        for (int64_t t = 0; t < nt; ++t)
+            if (!ft[t]) tmp[k++] = u[t];
+        if (k > 0) {
+            int64_t m2, mad4;
+            orc_median_mad_i64(tmp, k, &m2, &mad4);
+            if (mad4 > 0)
+                for (int64_t t = 0; t < nt; ++t) {
+                    int64_t d = 2 * u[t] - m2;
+                    if (!ft[t] && 20000 * (d < 0 ? -d : d) > (int64_t)kt * 14826 * mad4)
+                        ft[t] = 1;
+                }
+        }
+    }
+    int64_t fill = tkeep > 0 ? orc_round_div(R, tkeep) : 0;
+    if (fill > 255) fill = 255;
+    for (int64_t t = 0; t < nt; ++t)
+        for (int64_t c = 0; c < nc; ++c) {
+            int64_t y;
+            if (ft[t] || fc[c]) {
+                y = fill;
+            } else {
+                y = b[c] > 0 ? orc_round_div((int64_t)x[t * nc + c] * R, b[c]) : 0;
+                if (y > 255) y = 255;
+            }
+            out[t * nc + c] = (uint8_t)y;
+        }
+    free(s); free(b); free(e); free(u); free(tmp); free(win);
+    return 0;
 }
 
 /* Number of OpenMP threads the DM loop of orc_dedisperse uses from now on
