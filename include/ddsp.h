@@ -619,6 +619,47 @@ int ddsp_resample(ddsp_plan *plan, const int32_t *d_in, int64_t nrows,
                   double f1, double f2, float *d_out, int64_t out_pitch,
                   int64_t *nout, ddsp_stream_t stream);
 
+/* ------------------------------------------------------------------------
+ * RFI mitigation of a block of 8-bit spectra, gptool style (Sec.2.1: a
+ * bandpass from the mean spectrum median-filtered over 21 channels,
+ * channels beyond 4 sigma of the corrected mean spectrum and time samples
+ * beyond 3 sigma of the frequency-averaged series flagged, both twice).
+ * Exact integer arithmetic, per round: s[c] = sum of x[t][c] over unflagged
+ * samples; b[c] = lower median of s over [c - hw, c + hw] (clamped);
+ * R = lower median of b; e[c] = round(s[c] R / b[c]) (0 if b[c] = 0);
+ * among unflagged channels, c is flagged when |e - median| > kc 1.4826 MAD
+ * (evaluated as 20000 |2e - 2median| > kc 14826 (4 MAD)) and MAD > 0;
+ * y[t][c] = min(255, round(x[t][c] R / b[c])); u[t] = sum of y[t][c] over
+ * unflagged channels; among unflagged samples, t is flagged when
+ * |u - median| > kt 1.4826 MAD (same form).  Flags accumulate.  The output
+ * is y of the last round with flagged channels and samples set to the fill
+ * level min(255, round(R / T')), T' the unflagged samples of that round.
+ * round(a/b) = floor((2a + b) / (2b)).
+ * --------------------------------------------------------------------- */
+typedef struct ddsp_rfi ddsp_rfi;
+
+/* Workspace for blocks of up to max_nsamp (<= 2^22) spectra of up to
+ * max_nchan (<= 8192) channels: about 17 bytes per sample and 273 per
+ * channel.  DDSP_E_INVALID_ARG for sizes out of range or a missing device,
+ * DDSP_E_NOMEM / DDSP_E_CUDA on allocation failure. */
+int ddsp_rfi_create(ddsp_rfi **out, int device, int64_t max_nsamp,
+                    int max_nchan);
+void ddsp_rfi_destroy(ddsp_rfi *rfi);
+
+/* Clean the time-major block d_in[nsamp][nchan] into d_out (same layout;
+ * d_out may be d_in).  half_window 0..32 (10 for 21 channels), kc and kt
+ * 0..100 (4 and 3), rounds 1..16 (2).  Stream-ordered.
+ * DDSP_E_INVALID_ARG for a NULL pointer or an argument out of range. */
+int ddsp_rfi_clean(ddsp_rfi *rfi, const uint8_t *d_in, int64_t nsamp,
+                   int nchan, int half_window, int kc, int kt, int rounds,
+                   uint8_t *d_out, ddsp_stream_t stream);
+
+/* The flags of the last clean (host_chan_flags[nchan], host_time_flags
+ * [nsamp], either may be NULL; 1 = flagged) and the fill level.
+ * Synchronises.  DDSP_E_STATE before any clean. */
+int ddsp_rfi_flags(ddsp_rfi *rfi, uint8_t *host_chan_flags,
+                   uint8_t *host_time_flags, int64_t *fill);
+
 #ifdef __cplusplus
 }
 #endif

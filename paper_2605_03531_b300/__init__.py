@@ -15,8 +15,8 @@ import numpy as np
 from . import _lib
 from ._lib import DdspError, DdspCand
 
-__all__ = ["Plan", "Batch", "Server", "Cluster", "DdspError", "CAND_DTYPE",
-           "delay_table"]
+__all__ = ["Plan", "Batch", "Server", "Cluster", "Rfi", "DdspError",
+           "CAND_DTYPE", "delay_table"]
 
 CAND_DTYPE = np.dtype([("dm_idx", np.uint32), ("t", np.uint32),
                        ("w_idx", np.uint32), ("snr", np.float32)])
@@ -451,6 +451,58 @@ class Cluster:
     def close(self):
         if self._h:
             _lib.lib().ddsp_cluster_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Rfi:
+    """gptool-style RFI mitigation of blocks of 8-bit spectra (Sec.2.1);
+    see ddsp_rfi_clean for the exact rules."""
+
+    def __init__(self, max_nsamp, max_nchan, device=None):
+        import torch
+        if device is None:
+            device = torch.cuda.current_device()
+        self._h = C.c_void_p()
+        self._shape = (0, 0)
+        _lib.check(_lib.lib().ddsp_rfi_create(
+            C.byref(self._h), int(device), int(max_nsamp), int(max_nchan)),
+            "ddsp_rfi_create")
+
+    def clean(self, x, out=None, half_window=10, kc=4, kt=3, rounds=2,
+              stream=None):
+        """uint8 [nsamp][nchan] CUDA tensor -> cleaned uint8 tensor."""
+        import torch
+        nt, nc = x.shape
+        if out is None:
+            out = torch.empty_like(x)
+        _lib.check(_lib.lib().ddsp_rfi_clean(
+            self._h, _dev_ptr(x, torch.uint8, "spectra"), int(nt), int(nc),
+            int(half_window), int(kc), int(kt), int(rounds),
+            _dev_ptr(out, torch.uint8, "out"), _stream_handle(stream)),
+            "ddsp_rfi_clean")
+        self._shape = (nt, nc)
+        return out
+
+    def flags(self):
+        """(channel flags, time flags, fill level) of the last clean."""
+        nt, nc = self._shape
+        fc = np.zeros(nc, np.uint8)
+        ft = np.zeros(nt, np.uint8)
+        fill = C.c_int64()
+        _lib.check(_lib.lib().ddsp_rfi_flags(
+            self._h, fc.ctypes.data_as(C.c_void_p), ft.ctypes.data_as(C.c_void_p),
+            C.byref(fill)), "ddsp_rfi_flags")
+        return fc.astype(bool), ft.astype(bool), fill.value
+
+    def close(self):
+        if self._h:
+            _lib.lib().ddsp_rfi_destroy(self._h)
             self._h = C.c_void_p()
 
     def __del__(self):

@@ -105,6 +105,10 @@ SIGNATURES = {
                                    C.c_double, PI64]),
     "ddsp_resample": (I32, [P, P, I64, I64, I64, C.c_double, C.c_double,
                             C.c_double, C.c_double, P, I64, PI64, P]),
+    "ddsp_rfi_create": (I32, [C.POINTER(P), I32, I64, I32]),
+    "ddsp_rfi_destroy": (None, [P]),
+    "ddsp_rfi_clean": (I32, [P, P, I64, I32, I32, I32, I32, I32, P, P]),
+    "ddsp_rfi_flags": (I32, [P, P, P, PI64]),
 }
 
 _lib = None
