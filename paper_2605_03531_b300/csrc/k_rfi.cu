@@ -188,14 +188,33 @@ __device__ void block_median_mad(Key key, long long n, RfiShared &sh,
   mad4 = c + d;
 }
 
-// ---- per round: channel sums over unflagged samples
+// ---- per round: channel sums over unflagged samples (four channels per
+// thread with 32-bit loads when the row length allows it)
 __global__ void rfi_chan_sum(const uint8_t *__restrict__ x, long long nt, int nc,
                              const uint8_t *__restrict__ ft, int rows_per_block,
-                             unsigned long long *s) {
-  const int c = blockIdx.x * blockDim.x + threadIdx.x;
-  if (c >= nc) return;
+                             bool vec, unsigned long long *s) {
   const long long t0 = (long long)blockIdx.y * rows_per_block;
   const long long t1 = min(nt, t0 + rows_per_block);
+  if (vec) {                  // rows of a multiple of 4 bytes, 4-byte aligned
+    const int c4 = blockIdx.x * blockDim.x + threadIdx.x;
+    if (4 * c4 >= nc) return;
+    unsigned int a0 = 0, a1 = 0, a2 = 0, a3 = 0;   // <= 255 * rows_per_block
+    for (long long t = t0; t < t1; ++t) {
+      if (ft[t]) continue;
+      const uint32_t w = *reinterpret_cast<const uint32_t *>(x + t * nc + 4 * c4);
+      a0 += w & 0xFF;
+      a1 += (w >> 8) & 0xFF;
+      a2 += (w >> 16) & 0xFF;
+      a3 += w >> 24;
+    }
+    if (a0) atomicAdd(&s[4 * c4], (unsigned long long)a0);
+    if (a1) atomicAdd(&s[4 * c4 + 1], (unsigned long long)a1);
+    if (a2) atomicAdd(&s[4 * c4 + 2], (unsigned long long)a2);
+    if (a3) atomicAdd(&s[4 * c4 + 3], (unsigned long long)a3);
+    return;
+  }
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= nc) return;
   unsigned long long acc = 0;
   for (long long t = t0; t < t1; ++t)
     if (!ft[t]) acc += x[t * nc + c];
@@ -241,10 +260,13 @@ rfi_chan_stats(const unsigned long long *__restrict__ s_in, int nc, int hw,
   long long mn, mx, cnt;
   block_minmax(bkey, nc, sh, mn, mx, cnt);
   const long long R = block_select(bkey, nc, (nc - 1) / 2, mn, mx, sh);
-  // corrected channel sums and the channel flags
+  // corrected channel sums (in place of the sums) and the channel flags
+  for (int c = threadIdx.x; c < nc; c += blockDim.x)
+    sv[c] = bv[c] > 0 ? round_div(sv[c] * R, bv[c]) : 0;
+  __syncthreads();
   auto ekey = [&](long long i, long long &v) {
     if (fc[i]) return false;
-    v = bv[i] > 0 ? round_div(sv[i] * R, bv[i]) : 0;
+    v = sv[i];
     return true;
   };
   long long m2, mad4, ne;
@@ -253,16 +275,9 @@ rfi_chan_stats(const unsigned long long *__restrict__ s_in, int nc, int hw,
   if (ne > 0 && mad4 > 0) {
     for (int c = threadIdx.x; c < nc; c += blockDim.x) {
       if (fc[c]) continue;
-      const long long e = bv[c] > 0 ? round_div(sv[c] * R, bv[c]) : 0;
-      const long long d = 2 * e - m2;
+      const long long d = 2 * sv[c] - m2;
       if (20000 * (d < 0 ? -d : d) > (long long)kc * 14826 * mad4) fc[c] = 1;
     }
-  }
-  // tables y(x) = min(255, round(x R / b)) per channel
-  for (long long i = threadIdx.x; i < (long long)nc * 256; i += blockDim.x) {
-    const int c = (int)(i >> 8), xv = (int)(i & 255);
-    long long y = bv[c] > 0 ? round_div((long long)xv * R, bv[c]) : 0;
-    lut[i] = (uint8_t)min(y, 255ll);
   }
   // unflagged samples of this round and the fill level
   unsigned long long kept = 0;
@@ -283,7 +298,21 @@ rfi_chan_stats(const unsigned long long *__restrict__ s_in, int nc, int hw,
   }
 }
 
-// ---- per round: the frequency-averaged series through the tables
+// ---- per round: the tables y(x) = min(255, round(x R / b)) per channel
+__global__ void rfi_tables(const long long *__restrict__ b, int nc,
+                           const RfiState *st, uint8_t *lut) {
+  const long long R = st->R;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+       i < (long long)nc * 256; i += (long long)gridDim.x * blockDim.x) {
+    const int c = (int)(i >> 8), xv = (int)(i & 255);
+    const long long bc = b[c];
+    const long long y = bc > 0 ? round_div((long long)xv * R, bc) : 0;
+    lut[i] = (uint8_t)min(y, 255ll);
+  }
+}
+
+// ---- per round: the frequency-averaged series through the tables, one
+// block per row (grid-stride), threads along the row
 __global__ void rfi_time_sum(const uint8_t *__restrict__ x, long long nt, int nc,
                              const uint8_t *__restrict__ fc,
                              const uint8_t *__restrict__ lut, long long *u) {
@@ -327,19 +356,38 @@ rfi_time_stats(const long long *__restrict__ u, long long nt, int kt,
   }
 }
 
-// ---- the cleaned block
+// ---- the cleaned block, one block per row (grid-stride), 32-bit accesses
+// when the rows allow them
 __global__ void rfi_apply(const uint8_t *__restrict__ x, long long nt, int nc,
                           const uint8_t *__restrict__ fc,
                           const uint8_t *__restrict__ ft,
                           const uint8_t *__restrict__ lut, const RfiState *st,
-                          uint8_t *out) {
+                          bool vec, uint8_t *out) {
   const uint8_t fill = (uint8_t)st->fill;
-  const long long total = nt * nc;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-       i < total; i += (long long)gridDim.x * blockDim.x) {
-    const long long t = i / nc;
-    const int c = (int)(i - t * nc);
-    out[i] = (ft[t] || fc[c]) ? fill : lut[(long long)c * 256 + x[i]];
+  for (long long t = blockIdx.x; t < nt; t += gridDim.x) {
+    const uint8_t *xr = x + t * nc;
+    uint8_t *orow = out + t * nc;
+    if (ft[t]) {
+      for (int c = threadIdx.x; c < nc; c += blockDim.x) orow[c] = fill;
+      continue;
+    }
+    if (vec) {
+      for (int c4 = threadIdx.x; 4 * c4 < nc; c4 += blockDim.x) {
+        const uint32_t w = reinterpret_cast<const uint32_t *>(xr)[c4];
+        uint32_t o = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int c = 4 * c4 + q;
+          const uint32_t v = (w >> (8 * q)) & 0xFF;
+          const uint32_t y = fc[c] ? fill : lut[(long long)c * 256 + v];
+          o |= y << (8 * q);
+        }
+        reinterpret_cast<uint32_t *>(orow)[c4] = o;
+      }
+    } else {
+      for (int c = threadIdx.x; c < nc; c += blockDim.x)
+        orow[c] = fc[c] ? fill : lut[(long long)c * 256 + xr[c]];
+    }
   }
 }
 
@@ -429,22 +477,27 @@ extern "C" int ddsp_rfi_clean(ddsp_rfi *r, const uint8_t *d_in, int64_t nsamp,
   if (e == cudaSuccess) e = cudaMemsetAsync(r->ft, 0, (size_t)nsamp, s);
   if (e != cudaSuccess) return cuda_rc(e);
   const int rows = 256;
-  dim3 gsum((unsigned)((nchan + 255) / 256), (unsigned)((nsamp + rows - 1) / rows));
-  const unsigned gtime = (unsigned)std::min<int64_t>(nsamp, 148 * 8);
+  // 32-bit accesses only for rows of whole words at word-aligned addresses
+  const bool vec = (nchan & 3) == 0 &&
+                   (reinterpret_cast<uintptr_t>(d_in) & 3) == 0 &&
+                   (reinterpret_cast<uintptr_t>(d_out) & 3) == 0;
+  const int cols = vec ? nchan / 4 : nchan;
+  dim3 gsum((unsigned)((cols + 255) / 256), (unsigned)((nsamp + rows - 1) / rows));
+  const unsigned glut = (unsigned)std::min<long long>(((long long)nchan * 256 + 255) / 256, 148 * 8);
+  const unsigned grows = (unsigned)std::min<int64_t>(nsamp, 148 * 8);
   for (int rd = 0; rd < rounds; ++rd) {
     e = cudaMemsetAsync(r->s, 0, (size_t)nchan * 8, s);
     if (e != cudaSuccess) return cuda_rc(e);
-    rfi_chan_sum<<<gsum, 256, 0, s>>>(d_in, nsamp, nchan, r->ft, rows, r->s);
+    rfi_chan_sum<<<gsum, 256, 0, s>>>(d_in, nsamp, nchan, r->ft, rows, vec, r->s);
     rfi_chan_stats<<<1, kRfiThreads, csmem, s>>>(r->s, nchan, half_window, kc,
                                              r->ft, nsamp, r->b, r->fc, r->lut,
                                              r->st);
-    rfi_time_sum<<<gtime, 256, 0, s>>>(d_in, nsamp, nchan, r->fc, r->lut, r->u);
+    rfi_tables<<<glut, 256, 0, s>>>(r->b, nchan, r->st, r->lut);
+    rfi_time_sum<<<grows, 256, 0, s>>>(d_in, nsamp, nchan, r->fc, r->lut, r->u);
     rfi_time_stats<<<1, kRfiThreads, 0, s>>>(r->u, nsamp, kt, r->ft);
   }
-  const long long total = (long long)nsamp * nchan;
-  const unsigned gap = (unsigned)std::min<long long>((total + 255) / 256, 148 * 32);
-  rfi_apply<<<gap, 256, 0, s>>>(d_in, nsamp, nchan, r->fc, r->ft, r->lut,
-                                r->st, d_out);
+  rfi_apply<<<grows, 256, 0, s>>>(d_in, nsamp, nchan, r->fc, r->ft, r->lut,
+                                  r->st, vec, d_out);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_rc(e);
   r->nt = nsamp;

@@ -61,6 +61,20 @@ def test_parameters_match_oracle(kw):
     check(_block(2048, 300, 8, (10, 150), (5, 1500)), **kw)
 
 
+def test_unaligned_rows_match_oracle():
+    """A view starting one byte into its buffer (no 32-bit accesses)."""
+    x = _block(700, 128, 9, (3, 90), (11,))
+    buf = torch.zeros(x.size + 1, dtype=torch.uint8, device="cuda")
+    view = buf[1:].view(700, 128)
+    view.copy_(torch.from_numpy(x))
+    r = Rfi(700, 128)
+    out = r.clean(view).cpu().numpy()
+    fc, ft, fill = r.flags()
+    ref, rfc, rft = oracle.rfi_clean(x)
+    assert np.array_equal(out, ref) and np.array_equal(fc, rfc)
+    r.close()
+
+
 def test_in_place_and_constant_block():
     x = np.full((500, 64), 77, np.uint8)
     r = Rfi(500, 64)
