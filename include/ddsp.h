@@ -119,19 +119,40 @@ int ddsp_unpack(ddsp_plan *plan, const void *d_in, int64_t nsamp_in,
 /* Dedisperse (Sec.3.2): d_out[k][t] = sum_c in[t + d[k][c]][c] for every DM
  * trial k (plan order) and t in [0, N_out), N_out = nsamp_in - D, exact in
  * int32.  d_in: time-major spectra [nsamp_in][nchan] (uint8/uint16), 16-byte
- * aligned.  d_out: int32 [ndm][N_out], rows contiguous.  Runs the unpack
- * kernel into a plan-owned channel-major workspace (grown on demand with
- * cudaMalloc, so the first call for a new size synchronises) and then the
- * dedispersion kernel.  DDSP_E_SHAPE if N_out <= 0. */
+ * aligned.  d_out: int32 [ndm][N_out], rows contiguous.  Stages the block
+ * into plan-owned rows (ddsp_stage; the workspace grows on demand with
+ * cudaMalloc, so the first call for a new size synchronises) and then runs
+ * the dedispersion kernel (ddsp_dedisperse_staged).  DDSP_E_SHAPE if
+ * N_out <= 0. */
 int ddsp_dedisperse(ddsp_plan *plan, const void *d_in, int64_t nsamp_in,
                     int32_t *d_out, ddsp_stream_t stream);
+
+/* The two halves of ddsp_dedisperse, so that a block can be staged on one
+ * stream position and dedispersed on the next (and each timed alone).
+ * ddsp_stage: unpack the time-major block d_in[nsamp_in][nchan] (as in
+ * ddsp_dedisperse) into the plan-owned staging rows of the current tile
+ * shape: channel-major rows, or for DDSP_TILE_INTERLEAVED the interleaved
+ * rows that tile reads (4 bytes per uint8 sample, 2 per uint16 sample;
+ * uint8 plans with nchan % 16 == 0 write them in one pass straight from
+ * d_in).  DDSP_E_SHAPE if N_out <= 0.  ddsp_dedisperse_staged: dedisperse
+ * the staged block into d_out[ndm][nsamp_out]; nsamp_out must equal the
+ * staged block's N_out (DDSP_E_SHAPE otherwise); DDSP_E_STATE if nothing
+ * is staged (a tile change drops the staged block).  Both are stream-
+ * ordered: a stage must not be overwritten by the next ddsp_stage before
+ * the dedispersion that reads it has run (same stream, or an event). */
+int ddsp_stage(ddsp_plan *plan, const void *d_in, int64_t nsamp_in,
+               ddsp_stream_t stream);
+int ddsp_dedisperse_staged(ddsp_plan *plan, int64_t nsamp_out, int32_t *d_out,
+                           ddsp_stream_t stream);
 
 /* Dedisperse from channel-major rows already on the device (for example
  * the output of ddsp_unpack, or a per-beam ring kept in that layout):
  * d_cm[nchan][pitch] of the plan's sample type, 16-byte aligned; pitch a
  * multiple of 128 and at least ddsp_plan_cm_pitch(nsamp_out); samples
  * beyond nsamp_out + D of every row must be readable (they are read but do
- * not reach any stored output).  d_out as in ddsp_dedisperse. */
+ * not reach any stored output).  d_out as in ddsp_dedisperse.  With
+ * DDSP_TILE_INTERLEAVED the rows are first interleaved into the plan's
+ * staging rows (one extra streaming kernel). */
 int ddsp_dedisperse_cm(ddsp_plan *plan, const void *d_cm, int64_t pitch,
                        int64_t nsamp_out, int32_t *d_out, ddsp_stream_t stream);
 
@@ -438,14 +459,20 @@ const char *ddsp_last_error_detail(void);
  * DDSP_TILE_WARP_SPECIALIZED alone (producer warps stage and relayout,
  * consumer warps accumulate, no block-wide barrier in the main loop;
  * dm_per_thread 4, or 8 for uint8; stages 2 or 4, since each of the two
- * producer warps owns every other chunk and half the stages).  Every variant computes the same exact
- * sums.  dm_tile = 0 restores the library's choice, dm_tile = -1
+ * producer warps owns every other chunk and half the stages), or
+ * DDSP_TILE_INTERLEAVED alone (the default where it fits: rows interleaved
+ * once per block of data in HBM, element i = {x[i], x[i+S], x[i+2S],
+ * x[i+3S]} for the tile's segment S, are copied by TMA straight into a
+ * ring of `stages` (2..8) element stages of chan_chunk channels each; one
+ * producer warp, eight consumer warps; dm_per_thread 4, or 8 for uint8).
+ * Every variant computes the same exact sums.  dm_tile = 0 restores the library's choice, dm_tile = -1
  * selects the direct (unstaged) kernel.  DDSP_E_INVALID_ARG for a shape the
  * kernel does not implement or whose staging does not fit on chip.
  * Synchronises. */
 #define DDSP_TILE_SINGLE_ELEM_BUFFER 1
 #define DDSP_TILE_REGISTER_TOTALS 4
 #define DDSP_TILE_WARP_SPECIALIZED 8
+#define DDSP_TILE_INTERLEAVED 16
 int ddsp_plan_set_tile(ddsp_plan *plan, int dm_tile, int dm_per_thread,
                        int chan_chunk, int stages, int flags);
 int ddsp_plan_get_tile(const ddsp_plan *plan, int *dm_tile,

@@ -159,6 +159,32 @@ class Plan:
             "ddsp_dedisperse")
         return out
 
+    def stage(self, x, stream=None) -> int:
+        """Stage the time-major block x (CUDA [nsamp_in][nchan]) into the
+        plan's rows for the current tile; returns nsamp_out."""
+        if x.dim() != 2 or x.shape[1] != self.nchan:
+            raise ValueError("spectra must be [nsamp_in][nchan]")
+        nin = x.shape[0]
+        nout = self.nsamp_out(nin)
+        _lib.check(_lib.lib().ddsp_stage(
+            self._h, _dev_ptr(x, self._in_dtype(), "spectra"), int(nin),
+            _stream_handle(stream)), "ddsp_stage")
+        return nout
+
+    def dedisperse_staged(self, nsamp_out, out=None, device=None, stream=None):
+        """Dedisperse the block staged by stage() into int32
+        [ndm][nsamp_out]."""
+        import torch
+        if out is None:
+            out = torch.empty((self.ndm, int(nsamp_out)), dtype=torch.int32,
+                              device=device or "cuda")
+        elif tuple(out.shape) != (self.ndm, int(nsamp_out)):
+            raise ValueError("out must be [ndm][nsamp_out]")
+        _lib.check(_lib.lib().ddsp_dedisperse_staged(
+            self._h, int(nsamp_out), _dev_ptr(out, torch.int32, "out"),
+            _stream_handle(stream)), "ddsp_dedisperse_staged")
+        return out
+
     def cm_pitch(self, nsamp_out) -> int:
         v = C.c_int64()
         _lib.check(_lib.lib().ddsp_plan_cm_pitch(self._h, int(nsamp_out),

@@ -42,6 +42,8 @@ SIGNATURES = {
     "ddsp_unpack": (I32, [P, P, I64, P, I64, P]),
     "ddsp_dedisperse": (I32, [P, P, I64, P, P]),
     "ddsp_dedisperse_cm": (I32, [P, P, I64, I64, P, P]),
+    "ddsp_stage": (I32, [P, P, I64, P]),
+    "ddsp_dedisperse_staged": (I32, [P, I64, P, P]),
     "ddsp_plan_cm_pitch": (I32, [P, I64, PI64]),
     "ddsp_single_pulse_search": (I32, [P, P, I64, C.c_float, P]),
     "ddsp_single_pulse_search_dense": (I32, [P, P, I64, P, P, P, P]),

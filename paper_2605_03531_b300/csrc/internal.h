@@ -24,6 +24,7 @@ enum : int {
   kTileSingleElemBuffer = 1,  // one element buffer, two barriers per chunk
   kTileRegisterTotals = 4,    // int32 totals in registers, not in the output
   kTileWarpSpecialized = 8,   // producer / consumer warps (k_dedisp_ws.cu)
+  kTileInterleaved = 16,      // staged from pre-interleaved rows (k_dedisp_il.cu)
 };
 
 struct DedispTile {
@@ -32,7 +33,8 @@ struct DedispTile {
   int rd = 4;          // DM trials per thread (2 or 4; 4 or 8 when warp-
                        // specialised)
   int chan_chunk = 0;  // channels staged per pipeline step
-  int nbuf = 2;        // raw-window stages (bulk copies in flight + 1)
+  int nbuf = 2;        // raw-window stages (bulk copies in flight + 1);
+                       // element stages when interleaved
   int flags = 0;       // kTile* variant switches
   int dm_tile() const { return wd * rd; }
 };
@@ -66,9 +68,14 @@ struct Plan {
   DedispTables tab;
   int32_t *d_delays = nullptr;  // [ndm][nchan] device copy (direct kernel)
 
-  // channel-major workspace
+  // channel-major workspace, and the interleaved rows staged by the
+  // kTileInterleaved kernel ([nchan][cm pitch] uint32)
   void *d_cm = nullptr;
   size_t cm_bytes = 0;
+  void *d_il = nullptr;
+  size_t il_bytes = 0;
+  int64_t staged_nout = 0;    // block staged by ddsp_stage (0: none)
+  int64_t staged_pitch = 0;
 
   // search workspace
   int64_t *d_m2 = nullptr, *d_mad4 = nullptr;
@@ -108,9 +115,11 @@ cudaError_t launch_unpack_cols(const void *d_in, int64_t nsamp_in, int nchan,
                                int nbits, void *d_out, int64_t pitch,
                                int64_t ncols, cudaStream_t s);
 
+// ypitch: row pitch (elements) of the plan's interleaved rows p.d_il, used
+// by the kTileInterleaved tile only (which first rebuilds them from d_cm).
 cudaError_t launch_dedisperse(const Plan &p, const void *d_cm, int64_t pitch,
                               int64_t nsamp_out, int32_t *d_out,
-                              cudaStream_t s);
+                              cudaStream_t s, int64_t ypitch = 0);
 cudaError_t launch_dedisperse_direct(const Plan &p, const void *d_cm,
                                      int64_t pitch, int64_t nsamp_out,
                                      int32_t *d_out, cudaStream_t s);
@@ -127,6 +136,20 @@ cudaError_t launch_dedisperse_ws(const Plan &p, const void *d_cm,
                                  int64_t pitch, int64_t nsamp_out,
                                  int32_t *d_out, cudaStream_t s, int rawmax,
                                  int elmax, size_t smem);
+
+size_t dedisp_il_smem_bytes(int chan_chunk, int dm_tile, int elmax, int nst);
+int dedisp_il_max_stages();
+cudaError_t launch_interleave(const Plan &p, const void *d_cm, int64_t pitch,
+                              int64_t nvalid, int64_t ypitch, cudaStream_t s);
+// Time-major input straight to the plan's interleaved rows (uint8 with
+// nchan % 16 == 0 only: unpack_interleave_fused).
+bool unpack_interleave_fused(const Plan &p);
+cudaError_t launch_unpack_interleave(const Plan &p, const void *d_in,
+                                     int64_t nsamp_in, int64_t ypitch,
+                                     cudaStream_t s);
+cudaError_t launch_dedisperse_il(const Plan &p, int64_t ypitch,
+                                 int64_t nsamp_out, int32_t *d_out,
+                                 cudaStream_t s, int elmax, size_t smem);
 
 cudaError_t launch_sps(const Plan &p, const int32_t *d_series,
                        int64_t nsamp_out, float threshold, bool dense,

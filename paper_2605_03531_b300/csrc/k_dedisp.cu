@@ -29,6 +29,8 @@
 // only; nothing here is a dense contraction, so no tensor cores are used.
 #include <stdio.h>
 
+#include <algorithm>
+
 #include "internal.h"
 
 namespace ddsp {
@@ -491,6 +493,8 @@ void dedisp_buffer_sizes(const DedispTile &t, int span_max, int nbits,
 size_t dedisp_smem_bytes(const DedispTile &t, int span_max, int nbits) {
   int rawmax, elmax;
   buffer_sizes(t, span_max, nbits, &rawmax, &elmax);
+  if (t.flags & kTileInterleaved)
+    return dedisp_il_smem_bytes(t.chan_chunk, t.dm_tile(), elmax, t.nbuf);
   if (t.flags & kTileWarpSpecialized)
     return dedisp_ws_smem_bytes(t.chan_chunk, t.dm_tile(), rawmax, elmax,
                                 t.nbuf);
@@ -500,6 +504,11 @@ size_t dedisp_smem_bytes(const DedispTile &t, int span_max, int nbits) {
 }
 
 int dedisp_copy_bytes(const DedispTile &t, int span, int nbits) {
+  if (t.flags & kTileInterleaved) {
+    // elements 0 .. S + span - 1 of the window, whole 16-byte words
+    const int S = 32 * kElemPerThread * t.wt;
+    return ((S + span + 3) & ~3) * 4;
+  }
   const int TT = time_tile_of(t, nbits);
   return ((TT + span) * (nbits / 8) + 15) & ~15;
 }
@@ -510,6 +519,14 @@ bool dedisp_tile_supported(const DedispTile &t, int nbits) {
   // totals in registers only with one element buffer; uint16 totals are
   // always in registers (the flag is implied)
   const int f = t.flags;
+  if (f & kTileInterleaved) {
+    if (f != kTileInterleaved) return false;
+    if (t.rd != 4 && !(t.rd == 8 && nbits == 8)) return false;
+    if (t.wd != 1 && t.wd != 2 && t.wd != 4) return false;
+    if (nbits == 16 && t.rd == 8) return false;
+    if (t.chan_chunk < 1 || t.chan_chunk > 32) return false;
+    return t.nbuf >= 2 && t.nbuf <= dedisp_il_max_stages();
+  }
   if (f & kTileWarpSpecialized) {
     if (f != kTileWarpSpecialized) return false;
     if (t.rd != 4 && !(t.rd == 8 && nbits == 8)) return false;
@@ -534,10 +551,20 @@ int dedisp_time_tile(const DedispTile &t, int nbits) {
 
 cudaError_t launch_dedisperse(const Plan &p, const void *d_cm, int64_t pitch,
                               int64_t nsamp_out, int32_t *d_out,
-                              cudaStream_t s) {
+                              cudaStream_t s, int64_t ypitch) {
   int rawmax, elmax;
   buffer_sizes(p.tile, p.tab.span_max, p.nbits, &rawmax, &elmax);
   const size_t smem = dedisp_smem_bytes(p.tile, p.tab.span_max, p.nbits);
+  if (p.tile.flags & kTileInterleaved) {
+    // rebuild the interleaved rows from d_cm (null: p.d_il already holds
+    // them); samples past nsamp_out + max_delay only reach discarded outputs
+    if (d_cm) {
+      const int64_t nvalid = std::min<int64_t>(pitch, nsamp_out + p.max_delay);
+      cudaError_t e = launch_interleave(p, d_cm, pitch, nvalid, ypitch, s);
+      if (e != cudaSuccess) return e;
+    }
+    return launch_dedisperse_il(p, ypitch, nsamp_out, d_out, s, elmax, smem);
+  }
   if (p.tile.flags & kTileWarpSpecialized)
     return launch_dedisperse_ws(p, d_cm, pitch, nsamp_out, d_out, s, rawmax,
                                 elmax, smem);

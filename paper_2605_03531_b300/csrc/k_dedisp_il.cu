@@ -1,0 +1,406 @@
+// k_dedisp_il.cu -- brute-force dedispersion (Sec.3.2) from pre-interleaved
+// channel rows: out[k][t] = sum_c x[c][t + d[k][c]], exact in int32.
+//
+// The consumer arithmetic (ws_item.cuh) reads one 32-bit element per DM
+// trial that holds the samples of SPE output times S apart: element i of a
+// time tile = {x[i], x[i+S], x[i+2S], x[i+3S]} (uint8) or {x[i], x[i+S]}
+// (uint16).  That element does not depend on the tile: it is Y[i] of the
+// channel's interleaved row Y, which one streaming pass (interleave_kernel)
+// writes once per block of data.  The dedispersion kernel then stages its
+// windows of Y with 1-D TMA bulk copies straight into the element stages,
+// with no on-chip relayout: one producer warp only issues copies, and the
+// stages form an nst-deep ring (full / empty mbarriers) in front of the
+// consumer warps.  Y costs 4 bytes per sample in HBM (uint8; 2 for uint16)
+// and its windows are re-read from L2 across DM tiles, which is cheap next
+// to the shared-memory reads and writes the relayout took per element.
+//
+// Every wait is bounded; a role that gives up records a timeout, the
+// producer drains its copies in flight (bounded), and the block returns.
+#include "host.h"
+#include "ws_item.cuh"
+
+namespace ddsp {
+namespace {
+
+constexpr int kIlMaxStages = 8;
+constexpr int kIlBarBytes = 128;   // full[8], empty[8]
+
+// Shared memory: [0, 128) mbarriers, then nst stages of
+//   rel[cc][DT] int32 (element-byte offsets, 16-byte padded)
+//   elem[cc][elmax] uint32 (the channels' windows of Y)
+struct IlLayout {
+  int rel_stride, stage_stride, total;
+  __host__ __device__ IlLayout(int cc, int dt, int elmax, int nst) {
+    rel_stride = ((cc * dt * 4 + 15) / 16) * 16;
+    stage_stride = rel_stride + cc * elmax * 4;
+    total = kIlBarBytes + nst * stage_stride;
+  }
+};
+
+struct IlArgs {
+  const uint32_t *y;      // [nchan][ypitch] interleaved rows
+  int64_t ypitch;         // elements
+  int64_t nsamp_out;
+  int64_t out_pitch;
+  const int2 *desc;       // [n_dm_tiles][nchan] {window start, bytes}
+  const int32_t *relb;    // [n_dm_tiles][nchan][DT] element-byte offsets
+  const int32_t *rowmap;  // [n_dm_tiles*DT] output row or -1
+  int32_t *out;           // [ndm][out_pitch]
+  int nchan, cc, elmax, nst;
+};
+
+// Y[c][i] for i in [0, ypitch): byte (uint8) or half (uint16) m holds
+// x[c][i + m S] if that index is below nvalid, else 0.  One thread builds 4
+// consecutive elements from SPE aligned loads (a 4x4 byte transpose for
+// uint8) and stores them as one 16-byte word.
+template <typename T>
+__global__ void __launch_bounds__(256)
+interleave_kernel(const T *__restrict__ cm, int64_t pitch, int64_t nvalid,
+                  int S, uint32_t *__restrict__ y, int64_t ypitch) {
+  constexpr int SPE = 4 / sizeof(T);
+  const int c = blockIdx.y;
+  const int64_t i = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+  if (i >= ypitch) return;
+  const T *x = cm + (int64_t)c * pitch;
+  uint4 o;
+  if constexpr (SPE == 4) {
+    uint32_t w[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const int64_t b = i + (int64_t)m * S;
+      if (b + 4 <= nvalid) {
+        w[m] = __ldg(reinterpret_cast<const uint32_t *>(x + b));
+      } else {
+        uint32_t v = 0;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (b + k < nvalid) v |= (uint32_t)x[b + k] << (8 * k);
+        w[m] = v;
+      }
+    }
+    o = transpose4x4(w[0], w[1], w[2], w[3]);
+  } else {
+    uint32_t h[2][4];
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+      const int64_t b = i + (int64_t)m * S;
+      if (b + 4 <= nvalid) {
+        const uint2 v = __ldg(reinterpret_cast<const uint2 *>(x + b));
+        h[m][0] = v.x & 0xFFFFu;
+        h[m][1] = v.x >> 16;
+        h[m][2] = v.y & 0xFFFFu;
+        h[m][3] = v.y >> 16;
+      } else {
+#pragma unroll
+        for (int k = 0; k < 4; ++k) h[m][k] = b + k < nvalid ? x[b + k] : 0u;
+      }
+    }
+    o.x = h[0][0] | (h[1][0] << 16);
+    o.y = h[0][1] | (h[1][1] << 16);
+    o.z = h[0][2] | (h[1][2] << 16);
+    o.w = h[0][3] | (h[1][3] << 16);
+  }
+  *reinterpret_cast<uint4 *>(y + (int64_t)c * ypitch + i) = o;
+}
+
+// Time-major uint8 spectra (nchan % 16 == 0) straight to interleaved rows:
+// a block takes 64 elements x 128 channels, i.e. the four 64-sample x
+// 128-channel tiles of input rows i0 + m S (m < 4), loaded as 16-byte
+// vectors along channels.  A thread turns each 4x4 byte block (4 samples x
+// 4 channels) of every tile into 4 channel words with byte permutes, then
+// the 4 tiles' words of one channel into 4 elements (a second 4x4
+// transpose), stored as one 16-byte word along time.
+constexpr int kIlTS = 64;              // elements per block
+constexpr int kIlTC = 128;             // channels per block
+constexpr int kIlPW = kIlTC / 4 + 1;   // tile row pitch in words (skew)
+
+__global__ void __launch_bounds__(256)
+unpack_interleave_u8_kernel(const uint8_t *__restrict__ in, int64_t nsamp_in,
+                            int nchan, int S, uint32_t *__restrict__ y,
+                            int64_t ypitch) {
+  __shared__ uint32_t tile[4][kIlTS * kIlPW];
+  const int tid = threadIdx.x;
+  const int64_t i0 = (int64_t)blockIdx.x * kIlTS;
+  const int c0 = blockIdx.y * kIlTC;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      const int idx = tid + 256 * k;     // 64 rows x 8 vectors
+      const int row = idx >> 3, q = idx & 7;
+      const int64_t smp = i0 + row + (int64_t)m * S;
+      const int c = c0 + 16 * q;
+      uint4 v = make_uint4(0, 0, 0, 0);
+      if (smp < nsamp_in && c < nchan)
+        v = __ldg(reinterpret_cast<const uint4 *>(in + smp * nchan + c));
+      uint32_t *dst = tile[m] + row * kIlPW + 4 * q;
+      dst[0] = v.x;
+      dst[1] = v.y;
+      dst[2] = v.z;
+      dst[3] = v.w;
+    }
+  }
+  __syncthreads();
+  const int lane = tid & 31, w = tid >> 5;
+  const int sq = lane & 15;              // elements 4 sq .. 4 sq + 3
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const int cq = (lane >> 4) + 2 * w + 16 * it;   // channels 4 cq ..
+    uint32_t cw[4][4];                   // [m][channel j]: 4 samples
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const uint32_t *src = tile[m] + (4 * sq) * kIlPW + cq;
+      const uint4 o = transpose4x4(src[0], src[kIlPW], src[2 * kIlPW],
+                                   src[3 * kIlPW]);
+      cw[m][0] = o.x;
+      cw[m][1] = o.y;
+      cw[m][2] = o.z;
+      cw[m][3] = o.w;
+    }
+    const int64_t i = i0 + 4 * sq;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = c0 + 4 * cq + j;
+      if (c < nchan && i < ypitch)
+        *reinterpret_cast<uint4 *>(y + (int64_t)c * ypitch + i) =
+            transpose4x4(cw[0][j], cw[1][j], cw[2][j], cw[3][j]);
+    }
+  }
+}
+
+// One block per (DM tile, time tile): warp NC is the producer, warps
+// 0..NC-1 the consumers (WT along time x WD along DM).  Two blocks per SM:
+// 18 warps put 5 on some SM sub-partitions, whose 16K registers then allow
+// 96 a thread.
+template <int WT, int WD, int RD, typename T>
+__global__ void __launch_bounds__(32 * (WT * WD + 1), 2)
+dedisp_il_kernel(IlArgs a, int32_t *err, long long timeout_cycles) {
+  constexpr int SPE = 4 / sizeof(T);
+  constexpr int E = kElemPerThread;
+  constexpr int S = 32 * E * WT;     // elements per segment
+  constexpr int TT = SPE * S;        // output samples per tile
+  constexpr int DT = RD * WD;
+  constexpr int NC = WT * WD;
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint64_t *full = reinterpret_cast<uint64_t *>(smem);
+  uint64_t *empty = full + kIlMaxStages;
+  const int cc = a.cc, elmax = a.elmax, nst = a.nst, nchan = a.nchan;
+  const IlLayout L(cc, DT, elmax, nst);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int g = blockIdx.x;
+  const int64_t T0 = (int64_t)blockIdx.y * TT;
+  const int nchunks = (nchan + cc - 1) / cc;
+  unsigned char *stages = smem + kIlBarBytes;
+
+  if (tid == 0) {
+    for (int s = 0; s < nst; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], NC);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+
+  if (warp == NC) {
+    // ============================= producer =============================
+    const int2 *desc_g = a.desc + (int64_t)g * nchan;
+    const int32_t *rel_g = a.relb + (int64_t)g * nchan * DT;
+    // copy descriptors of channels [base, base + 32) and the 32 after them,
+    // lane l holding channel base + l: a chunk (cc <= 32) spans at most the
+    // two, and each batch is loaded one batch ahead of its use, so no chunk
+    // waits on a global load
+    auto ld_desc = [&](int c) {
+      return c < nchan ? __ldg(desc_g + c) : make_int2(0, 0);
+    };
+    int base = 0;
+    int2 dcur = ld_desc(lane), dnext = ld_desc(32 + lane);
+    int j = 0;
+    for (; j < nchunks; ++j) {
+      const int st = j % nst;
+      // the stage's previous chunk (j - nst) has been consumed (the warp
+      // gives up as a whole if any lane's wait ran out)
+      if (!__all_sync(0xffffffffu,
+                      mbar_wait(&empty[st], (uint32_t)(((j / nst) & 1) ^ 1),
+                                timeout_cycles)))
+        break;
+      const int c0 = j * cc;
+      const int ncur = min(cc, nchan - c0);
+      const bool v = lane < ncur;
+      const int off = c0 - base + lane;          // < 64
+      const int src = off & 31;
+      const int2 da = make_int2(__shfl_sync(0xffffffffu, dcur.x, src),
+                                __shfl_sync(0xffffffffu, dcur.y, src));
+      const int2 db = make_int2(__shfl_sync(0xffffffffu, dnext.x, src),
+                                __shfl_sync(0xffffffffu, dnext.y, src));
+      const int2 d = off < 32 ? da : db;
+      if (c0 + ncur >= base + 32) {    // the next chunk starts past dcur
+        base += 32;
+        dcur = dnext;
+        dnext = ld_desc(base + 32 + lane);
+      }
+      const uint32_t nb = v ? (uint32_t)d.y : 0u;
+      const uint32_t relbytes = (uint32_t)(ncur * DT * 4);
+      const uint32_t total = __reduce_add_sync(0xffffffffu, nb) + relbytes;
+      unsigned char *sb = stages + st * L.stage_stride;
+      if (lane == 0) mbar_expect_tx(&full[st], total);
+      __syncwarp();
+      if (v)
+        bulk_g2s(sb + L.rel_stride + lane * elmax * 4,
+                 a.y + (int64_t)(c0 + lane) * a.ypitch + T0 + d.x, nb,
+                 &full[st]);
+      if (lane == 0)
+        bulk_g2s(sb, rel_g + (int64_t)c0 * DT, relbytes, &full[st]);
+    }
+    if (j < nchunks) {
+      // gave up: record it and let the copies in flight (chunks j - nst ..
+      // j - 1) land before the block's shared memory goes away
+      if (lane == 0) {
+        atomicExch(err, kErrTimeout);
+        for (int jj = max(0, j - nst); jj < j; ++jj)
+          mbar_wait(&full[jj % nst], (uint32_t)((jj / nst) & 1),
+                    timeout_cycles);
+      }
+    }
+    return;
+  }
+
+  // ============================= consumers ==============================
+  const int wt = warp % WT, wd = warp / WT;
+  const int i0 = 32 * E * wt + lane;  // first element of this thread
+  WsAcc<RD, SPE> acc;
+  acc.zero();
+  bool first_flush = true;
+  int since = 0;
+  for (int j = 0; j < nchunks; ++j) {
+    const int st = j % nst;
+    const int ncur = min(cc, nchan - j * cc);
+    if (!__all_sync(0xffffffffu, mbar_wait(&full[st], (uint32_t)((j / nst) & 1),
+                                           timeout_cycles))) {
+      if (lane == 0) atomicExch(err, kErrTimeout);
+      return;
+    }
+    const unsigned char *sb = stages + st * L.stage_stride;
+    ws_accumulate<RD, SPE>(acc,
+                           reinterpret_cast<const int32_t *>(sb) + RD * wd, DT,
+                           sb + L.rel_stride + 4 * i0, elmax, ncur);
+    __syncwarp();
+    if (lane == 0) mbar_arrive(&empty[st]);
+    if constexpr (SPE == 4) {
+      since += ncur;
+      if (since + cc > 256 || j == nchunks - 1) {
+        ws_flush<RD>(acc, a.rowmap + g * DT + RD * wd, a.out, a.out_pitch,
+                     T0 + i0, S, a.nsamp_out, first_flush);
+        first_flush = false;
+        since = 0;
+      }
+    }
+  }
+  if constexpr (SPE != 4)
+    ws_store_totals<RD, SPE>(acc, a.rowmap + g * DT + RD * wd, a.out,
+                             a.out_pitch, T0 + i0, S, a.nsamp_out);
+}
+
+template <int WT, int WD, int RD, typename T>
+cudaError_t launch_il_t(const Plan &p, int64_t ypitch, int64_t nsamp_out,
+                        int32_t *d_out, cudaStream_t s, int elmax,
+                        size_t smem) {
+  auto kern = dedisp_il_kernel<WT, WD, RD, T>;
+  static size_t attr_bytes = 0;
+  if (smem > attr_bytes) {
+    cudaError_t e = cudaFuncSetAttribute(
+        kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // the largest shared-memory carveout, so two blocks fit beside each other
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(kern,
+                               cudaFuncAttributePreferredSharedMemoryCarveout,
+                               (int)cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    attr_bytes = smem;
+  }
+  constexpr int SPE = 4 / sizeof(T);
+  constexpr int TT = SPE * 32 * kElemPerThread * WT;
+  const int ntt = (int)((nsamp_out + TT - 1) / TT);
+  IlArgs a{};
+  a.y = static_cast<const uint32_t *>(p.d_il);
+  a.ypitch = ypitch;
+  a.nsamp_out = nsamp_out;
+  a.out_pitch = nsamp_out;
+  a.desc = reinterpret_cast<const int2 *>(p.tab.d_desc);
+  a.relb = p.tab.d_relb;
+  a.rowmap = p.tab.d_rowmap;
+  a.out = d_out;
+  a.nchan = p.nchan;
+  a.cc = p.tile.chan_chunk;
+  a.elmax = elmax;
+  a.nst = p.tile.nbuf;
+  dim3 grid((unsigned)p.tab.n_dm_tiles, (unsigned)ntt);
+  const long long timeout = 4000000000LL;  // ~2 s of SM clock
+  kern<<<grid, 32 * (WT * WD + 1), smem, s>>>(a, p.d_err, timeout);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t dedisp_il_smem_bytes(int chan_chunk, int dm_tile, int elmax,
+                            int nst) {
+  return (size_t)IlLayout(chan_chunk, dm_tile, elmax, nst).total;
+}
+
+int dedisp_il_max_stages() { return kIlMaxStages; }
+
+cudaError_t launch_interleave(const Plan &p, const void *d_cm, int64_t pitch,
+                              int64_t nvalid, int64_t ypitch, cudaStream_t s) {
+  const int S = 32 * kElemPerThread * p.tile.wt;
+  const dim3 grid((unsigned)((ypitch / 4 + 255) / 256), (unsigned)p.nchan);
+  uint32_t *y = static_cast<uint32_t *>(p.d_il);
+  if (p.nbits == 8)
+    interleave_kernel<uint8_t><<<grid, 256, 0, s>>>(
+        static_cast<const uint8_t *>(d_cm), pitch, nvalid, S, y, ypitch);
+  else
+    interleave_kernel<uint16_t><<<grid, 256, 0, s>>>(
+        static_cast<const uint16_t *>(d_cm), pitch, nvalid, S, y, ypitch);
+  return cudaGetLastError();
+}
+
+bool unpack_interleave_fused(const Plan &p) {
+  return p.nbits == 8 && p.nchan % 16 == 0;
+}
+
+cudaError_t launch_unpack_interleave(const Plan &p, const void *d_in,
+                                     int64_t nsamp_in, int64_t ypitch,
+                                     cudaStream_t s) {
+  const int S = 32 * kElemPerThread * p.tile.wt;
+  const dim3 grid((unsigned)((ypitch + kIlTS - 1) / kIlTS),
+                  (unsigned)((p.nchan + kIlTC - 1) / kIlTC));
+  unpack_interleave_u8_kernel<<<grid, 256, 0, s>>>(
+      static_cast<const uint8_t *>(d_in), nsamp_in, p.nchan, S,
+      static_cast<uint32_t *>(p.d_il), ypitch);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dedisperse_il(const Plan &p, int64_t ypitch,
+                                 int64_t nsamp_out, int32_t *d_out,
+                                 cudaStream_t s, int elmax, size_t smem) {
+  const int wt = p.tile.wt, wd = p.tile.wd, rd = p.tile.rd;
+#define DDSP_IL(WT_, WD_, RD_, T_)                                          \
+  if (wt == WT_ && wd == WD_ && rd == RD_)                                  \
+    return launch_il_t<WT_, WD_, RD_, T_>(p, ypitch, nsamp_out, d_out, s,   \
+                                          elmax, smem);
+  if (p.nbits == 8) {
+    DDSP_IL(4, 2, 8, uint8_t)
+    DDSP_IL(8, 1, 8, uint8_t)
+    DDSP_IL(2, 4, 8, uint8_t)
+    DDSP_IL(4, 2, 4, uint8_t)
+    DDSP_IL(8, 1, 4, uint8_t)
+    DDSP_IL(2, 4, 4, uint8_t)
+  } else {
+    DDSP_IL(4, 2, 4, uint16_t)
+    DDSP_IL(8, 1, 4, uint16_t)
+    DDSP_IL(2, 4, 4, uint16_t)
+  }
+#undef DDSP_IL
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace ddsp

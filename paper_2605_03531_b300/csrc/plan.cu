@@ -138,6 +138,8 @@ DedispTile choose_tile(const Plan &p) {
   // registers, then smaller staging footprints
   struct Cand { int wt, wd, rd, cc, flags; };
   const Cand prefs[] = {
+      {4, 2, 8, 8, kTileInterleaved}, {8, 1, 8, 8, kTileInterleaved},
+      {4, 2, 4, 8, kTileInterleaved},
       {4, 2, 8, 8, kTileWarpSpecialized}, {8, 1, 8, 8, kTileWarpSpecialized},
       {4, 2, 4, 8, kTileSingleElemBuffer | kTileRegisterTotals},
       {4, 2, 4, 6, kTileSingleElemBuffer}, {8, 1, 4, 4, kTileSingleElemBuffer},
@@ -153,6 +155,19 @@ DedispTile choose_tile(const Plan &p) {
       t.flags = c.flags;
       if (!dedisp_tile_supported(t, p.nbits)) continue;
       const int span = span_for(p, t.dm_tile());
+      if (c.flags & kTileInterleaved) {
+        // two element stages of the largest chunk that fits: each chunk
+        // costs the consumers a fixed synchronisation latency, which larger
+        // chunks amortise better than a deeper ring hides it (4096-channel
+        // 1024-DM block: 7 channels x 2 stages 49 ms, 4 x 3 54 ms, 2 x 6
+        // 64 ms)
+        t.nbuf = 2;
+        for (int cc = c.cc; cc >= 2; --cc) {
+          t.chan_chunk = cc;
+          if (dedisp_smem_bytes(t, span, p.nbits) <= budget) return t;
+        }
+        continue;
+      }
       if (c.flags & kTileWarpSpecialized) {
         t.nbuf = 2;
         for (int cc = c.cc; cc >= 2; --cc) {
@@ -195,6 +210,21 @@ int ensure_cm(Plan &p, size_t bytes) {
   return DDSP_OK;
 }
 
+// Interleaved rows for the kTileInterleaved tile: [nchan][pitch] uint32.
+int ensure_il(Plan &p, int64_t pitch) {
+  if (!(p.tile.flags & kTileInterleaved)) return DDSP_OK;
+  const size_t bytes = (size_t)p.nchan * pitch * 4;
+  if (bytes <= p.il_bytes) return DDSP_OK;
+  cudaDeviceSynchronize();
+  cudaFree(p.d_il);
+  p.d_il = nullptr;
+  p.il_bytes = 0;
+  cudaError_t e = cudaMalloc(&p.d_il, bytes);
+  if (e != cudaSuccess) return cuda_rc(e);
+  p.il_bytes = bytes;
+  return DDSP_OK;
+}
+
 int ensure_stats(Plan &p, size_t n) {
   if (n <= p.stats_cap) return DDSP_OK;
   cudaDeviceSynchronize();
@@ -217,6 +247,7 @@ void release(Plan &p) {
   free_tables(p.tab);
   cudaFree(p.d_delays);
   cudaFree(p.d_cm);
+  cudaFree(p.d_il);
   cudaFree(p.d_m2);
   cudaFree(p.d_mad4);
   cudaFree(p.d_cands);
@@ -417,7 +448,7 @@ int ddsp_plan_set_tile(ddsp_plan *h, int dm_tile, int dm_per_thread,
     t.chan_chunk = chan_chunk;
     t.nbuf = stages;
     if (flags & ~(kTileSingleElemBuffer | kTileRegisterTotals |
-                  kTileWarpSpecialized))
+                  kTileWarpSpecialized | kTileInterleaved))
       return DDSP_E_INVALID_ARG;
     t.flags = flags;
     if (!dedisp_tile_supported(t, p.nbits)) return DDSP_E_INVALID_ARG;
@@ -427,6 +458,12 @@ int ddsp_plan_set_tile(ddsp_plan *h, int dm_tile, int dm_per_thread,
   }
   cudaDeviceSynchronize();
   p.tile = t;
+  p.staged_nout = 0;   // a staged block belongs to the tile that staged it
+  if (!(t.flags & kTileInterleaved)) {
+    cudaFree(p.d_il);
+    p.d_il = nullptr;
+    p.il_bytes = 0;
+  }
   return build_tables(p);
 }
 
@@ -456,26 +493,75 @@ int ddsp_unpack(ddsp_plan *h, const void *d_in, int64_t nsamp_in, void *d_out,
                                (cudaStream_t)stream));
 }
 
+// Stage a time-major block into the plan's workspace for the current tile:
+// channel-major rows (unpack), plus or instead of them (uint8, nchan % 16
+// == 0) the interleaved rows of the kTileInterleaved tile.
+static int stage_block(Plan &p, const void *d_in, int64_t nsamp_in,
+                       cudaStream_t s) {
+  p.staged_nout = 0;
+  const int64_t nout = nsamp_in - p.max_delay;
+  if (nout <= 0) return DDSP_E_SHAPE;
+  const int64_t pitch = cm_pitch(p, nout);
+  const bool il = p.tile.wt > 0 && (p.tile.flags & kTileInterleaved);
+  const bool fused = il && unpack_interleave_fused(p);
+  int rc = il ? ensure_il(p, pitch) : DDSP_OK;
+  if (rc == DDSP_OK && !fused)
+    rc = ensure_cm(p, (size_t)p.nchan * pitch * (p.nbits / 8));
+  if (rc != DDSP_OK) return rc;
+  cudaError_t e;
+  if (fused) {
+    e = launch_unpack_interleave(p, d_in, nsamp_in, pitch, s);
+  } else {
+    e = launch_unpack(d_in, nsamp_in, p.nchan, p.nbits, p.d_cm, pitch, s);
+    if (e == cudaSuccess && il)
+      e = launch_interleave(p, p.d_cm, pitch, nsamp_in, pitch, s);
+  }
+  if (e != cudaSuccess) return cuda_rc(e);
+  p.staged_nout = nout;
+  p.staged_pitch = pitch;
+  return DDSP_OK;
+}
+
+static int dedisperse_staged(Plan &p, int32_t *d_out, cudaStream_t s) {
+  const int64_t nout = p.staged_nout, pitch = p.staged_pitch;
+  cudaError_t e;
+  if (p.tile.wt == 0)
+    e = launch_dedisperse_direct(p, p.d_cm, pitch, nout, d_out, s);
+  else if (p.tile.flags & kTileInterleaved)
+    e = launch_dedisperse(p, nullptr, pitch, nout, d_out, s, pitch);
+  else
+    e = launch_dedisperse(p, p.d_cm, pitch, nout, d_out, s, pitch);
+  return cuda_rc(e);
+}
+
+int ddsp_stage(ddsp_plan *h, const void *d_in, int64_t nsamp_in,
+               ddsp_stream_t stream) {
+  if (!h || !d_in || ((uintptr_t)d_in & 15)) return DDSP_E_INVALID_ARG;
+  Plan &p = h->p;
+  DeviceGuard g(p.device);
+  return stage_block(p, d_in, nsamp_in, (cudaStream_t)stream);
+}
+
+int ddsp_dedisperse_staged(ddsp_plan *h, int64_t nsamp_out, int32_t *d_out,
+                           ddsp_stream_t stream) {
+  if (!h || !d_out) return DDSP_E_INVALID_ARG;
+  Plan &p = h->p;
+  if (p.staged_nout <= 0) return DDSP_E_STATE;
+  if (nsamp_out != p.staged_nout) return DDSP_E_SHAPE;
+  DeviceGuard g(p.device);
+  return dedisperse_staged(p, d_out, (cudaStream_t)stream);
+}
+
 int ddsp_dedisperse(ddsp_plan *h, const void *d_in, int64_t nsamp_in,
                     int32_t *d_out, ddsp_stream_t stream) {
   if (!h || !d_in || !d_out || ((uintptr_t)d_in & 15))
     return DDSP_E_INVALID_ARG;
   Plan &p = h->p;
   DeviceGuard g(p.device);
-  const int64_t nout = nsamp_in - p.max_delay;
-  if (nout <= 0) return DDSP_E_SHAPE;
-  const int64_t pitch = cm_pitch(p, nout);
-  const size_t bytes = (size_t)p.nchan * pitch * (p.nbits / 8);
-  int rc = ensure_cm(p, bytes);
-  if (rc != DDSP_OK) return rc;
   cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e = launch_unpack(d_in, nsamp_in, p.nchan, p.nbits, p.d_cm,
-                                pitch, s);
-  if (e != cudaSuccess) return cuda_rc(e);
-  e = p.tile.wt > 0
-          ? launch_dedisperse(p, p.d_cm, pitch, nout, d_out, s)
-          : launch_dedisperse_direct(p, p.d_cm, pitch, nout, d_out, s);
-  return cuda_rc(e);
+  int rc = stage_block(p, d_in, nsamp_in, s);
+  if (rc != DDSP_OK) return rc;
+  return dedisperse_staged(p, d_out, s);
 }
 
 int ddsp_plan_cm_pitch(const ddsp_plan *h, int64_t nsamp_out, int64_t *pitch) {
@@ -490,12 +576,15 @@ int ddsp_dedisperse_cm(ddsp_plan *h, const void *d_cm, int64_t pitch,
       (pitch % 128) != 0)
     return DDSP_E_INVALID_ARG;
   Plan &p = h->p;
-  if (pitch < cm_pitch(p, nsamp_out)) return DDSP_E_SHAPE;
+  const int64_t ypitch = cm_pitch(p, nsamp_out);
+  if (pitch < ypitch) return DDSP_E_SHAPE;
   DeviceGuard g(p.device);
+  int rc = ensure_il(p, ypitch);
+  if (rc != DDSP_OK) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e =
       p.tile.wt > 0
-          ? launch_dedisperse(p, d_cm, pitch, nsamp_out, d_out, s)
+          ? launch_dedisperse(p, d_cm, pitch, nsamp_out, d_out, s, ypitch)
           : launch_dedisperse_direct(p, d_cm, pitch, nsamp_out, d_out, s);
   return cuda_rc(e);
 }

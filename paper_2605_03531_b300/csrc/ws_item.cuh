@@ -59,6 +59,159 @@ struct WsLayout {
   }
 };
 
+// ---------------------------------------------------------------------------
+// Consumer arithmetic shared by the warp-specialised kernels.  A consumer
+// thread owns RD DM trials x E interleaved elements (i0 + 32 e, e < E) of
+// one time tile; element i holds SPE samples, i + m S for m < SPE.
+
+// SWAR partials (uint8: A, B, flushed every <= 256 channels) or int32
+// totals (uint16: two 16-bit samples per element, exact in int32).
+template <int RD, int SPE>
+struct WsAcc {
+  static constexpr int E = kElemPerThread;
+  uint32_t A[RD][E], B[RD][E];
+  int32_t tot[SPE != 4 ? RD : 1][E][SPE];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int r = 0; r < RD; ++r)
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        A[r][e] = 0;
+        B[r][e] = 0;
+        if constexpr (SPE != 4) {
+#pragma unroll
+          for (int m = 0; m < SPE; ++m) tot[r][e][m] = 0;
+        }
+      }
+  }
+};
+
+// Accumulate `ncur` staged channels: channel q's elements start at
+// ebase + q * elmax * 4 (ebase already points at this thread's element
+// i0), its DM trial r's byte offset is rel[q * dt + r] (rel already points
+// at this warp's first trial; 16-byte aligned).  Two channels per step
+// (3-input adds), then a lone last channel.
+template <int RD, int SPE>
+__device__ __forceinline__ void ws_accumulate(WsAcc<RD, SPE> &acc,
+                                              const int32_t *rel, int dt,
+                                              const unsigned char *ebase,
+                                              int elmax, int ncur) {
+  constexpr int E = kElemPerThread;
+  auto offsets = [&](int q, int(&rr)[RD]) {
+#pragma unroll
+    for (int h = 0; h < RD; h += 4) {
+      const int4 ro = *reinterpret_cast<const int4 *>(rel + q * dt + h);
+      rr[h] = ro.x;
+      rr[h + 1] = ro.y;
+      rr[h + 2] = ro.z;
+      rr[h + 3] = ro.w;
+    }
+  };
+  int q = 0;
+  for (; q + 1 < ncur; q += 2) {
+    int ra[RD], rb[RD];
+    offsets(q, ra);
+    offsets(q + 1, rb);
+    const unsigned char *ea = ebase + q * elmax * 4;
+    const unsigned char *eb = ea + elmax * 4;
+#pragma unroll
+    for (int r = 0; r < RD; ++r) {
+      const unsigned char *pa = ea + ra[r];
+      const unsigned char *pb = eb + rb[r];
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const uint32_t wa = *reinterpret_cast<const uint32_t *>(pa + 128 * e);
+        const uint32_t wb = *reinterpret_cast<const uint32_t *>(pb + 128 * e);
+        if constexpr (SPE == 4) {
+          acc.A[r][e] += wa + wb;
+          acc.B[r][e] +=
+              __byte_perm(wa, 0u, 0x4341) + __byte_perm(wb, 0u, 0x4341);
+        } else {
+          acc.tot[r][e][0] += (int32_t)((wa & 0xFFFFu) + (wb & 0xFFFFu));
+          acc.tot[r][e][1] += (int32_t)((wa >> 16) + (wb >> 16));
+        }
+      }
+    }
+  }
+  if (q < ncur) {
+    int ra[RD];
+    offsets(q, ra);
+    const unsigned char *ea = ebase + q * elmax * 4;
+#pragma unroll
+    for (int r = 0; r < RD; ++r) {
+      const unsigned char *pa = ea + ra[r];
+#pragma unroll
+      for (int e = 0; e < E; ++e) {
+        const uint32_t wa = *reinterpret_cast<const uint32_t *>(pa + 128 * e);
+        if constexpr (SPE == 4) {
+          acc.A[r][e] += wa;
+          acc.B[r][e] += __byte_perm(wa, 0u, 0x4341);
+        } else {
+          acc.tot[r][e][0] += (int32_t)(wa & 0xFFFFu);
+          acc.tot[r][e][1] += (int32_t)(wa >> 16);
+        }
+      }
+    }
+  }
+}
+
+// uint8: unpack the SWAR partials (<= 256 channels since the last flush)
+// into the output rows rowmap[r] (-1: padding trial) at times t0 + 32 e +
+// m S; the item's first flush stores, later ones are fire-and-forget
+// reductions (integer adds in any order give the same total).
+template <int RD>
+__device__ __forceinline__ void ws_flush(WsAcc<RD, 4> &acc,
+                                         const int32_t *rowmap, int32_t *out,
+                                         int64_t out_pitch, int64_t t0, int S,
+                                         int64_t nsamp_out, bool first) {
+  constexpr int E = kElemPerThread;
+#pragma unroll
+  for (int r = 0; r < RD; ++r) {
+    const int row = __ldg(rowmap + r);
+    int32_t *o = out + (int64_t)(row < 0 ? 0 : row) * out_pitch;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+      const uint32_t Bv = acc.B[r][e];
+      const uint32_t Ev = acc.A[r][e] - (Bv << 8);  // b0 + 2^16 b2 sums
+      const int32_t part[4] = {(int32_t)(Ev & 0xFFFFu), (int32_t)(Bv & 0xFFFFu),
+                               (int32_t)(Ev >> 16), (int32_t)(Bv >> 16)};
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const int64_t t = t0 + 32 * e + (int64_t)m * S;
+        if (row >= 0 && t < nsamp_out) {
+          if (first) o[t] = part[m];
+          else atomicAdd(o + t, part[m]);
+        }
+      }
+      acc.A[r][e] = 0;
+      acc.B[r][e] = 0;
+    }
+  }
+}
+
+// uint16: store the register totals once, after the last channel.
+template <int RD, int SPE>
+__device__ __forceinline__ void ws_store_totals(const WsAcc<RD, SPE> &acc,
+                                                const int32_t *rowmap,
+                                                int32_t *out, int64_t out_pitch,
+                                                int64_t t0, int S,
+                                                int64_t nsamp_out) {
+  constexpr int E = kElemPerThread;
+#pragma unroll
+  for (int r = 0; r < RD; ++r) {
+    const int row = rowmap[r];
+    if (row < 0) continue;
+    int32_t *o = out + (int64_t)row * out_pitch;
+#pragma unroll
+    for (int e = 0; e < E; ++e)
+#pragma unroll
+      for (int m = 0; m < SPE; ++m) {
+        const int64_t t = t0 + 32 * e + (int64_t)m * S;
+        if (t < nsamp_out) o[t] = acc.tot[r][e][m];
+      }
+  }
+}
+
 // One beam as the dedispersion sees it (device copy for the batch).  Input
 // sample t + d of channel c sits at row offset t + d (ring == 0), or at
 // (t0 + t + d) mod ring for a ring buffer whose rows carry, past `ring`, a
@@ -111,7 +264,6 @@ __device__ __forceinline__ bool ws_item(const WsBeam &a, int g, int64_t T0,
   constexpr int DT = RD * WD;          // DM trials per tile
   constexpr int NC = WT * WD;          // consumer warps
   constexpr int NP = kWsProdWarps;
-  constexpr bool kRegTot = SPE != 4;   // uint16 totals stay in registers
   const int cc = a.cc, rawmax = a.rawmax, elmax = a.elmax;
   const WsLayout L(cc, DT, rawmax, elmax, nbuf);
 
@@ -258,19 +410,8 @@ __device__ __forceinline__ bool ws_item(const WsBeam &a, int g, int64_t T0,
   // ============================= consumers =============================
   const int wt = warp % WT, wd = warp / WT;
   const int i0 = 32 * E * wt + lane;  // first element of this thread
-  uint32_t accA[RD][E], accB[RD][E];
-  int32_t tot[kRegTot ? RD : 1][E][SPE];
-#pragma unroll
-  for (int r = 0; r < RD; ++r)
-#pragma unroll
-    for (int e = 0; e < E; ++e) {
-      accA[r][e] = 0;
-      accB[r][e] = 0;
-      if constexpr (kRegTot) {
-#pragma unroll
-        for (int m = 0; m < SPE; ++m) tot[r][e][m] = 0;
-      }
-    }
+  WsAcc<RD, SPE> acc;
+  acc.zero();
   bool first_flush = true;
   int since = 0;
 
@@ -282,119 +423,23 @@ __device__ __forceinline__ bool ws_item(const WsBeam &a, int g, int64_t T0,
       if (lane == 0) atomicExch(err, kErrTimeout);
       return false;
     }
-    const int32_t *rel_s = erel + b * rel_words;
-    const unsigned char *ebase = elem + b * L.elem_stride + 4 * i0;
-    auto offsets = [&](int q, int(&rr)[RD]) {
-#pragma unroll
-      for (int h = 0; h < RD; h += 4) {
-        const int4 ro =
-            *reinterpret_cast<const int4 *>(rel_s + q * DT + RD * wd + h);
-        rr[h] = ro.x;
-        rr[h + 1] = ro.y;
-        rr[h + 2] = ro.z;
-        rr[h + 3] = ro.w;
-      }
-    };
-    // two channels per step: 3-input adds
-    int q = 0;
-    for (; q + 1 < ncur; q += 2) {
-      int ra[RD], rb[RD];
-      offsets(q, ra);
-      offsets(q + 1, rb);
-      const unsigned char *ea = ebase + q * elmax * 4;
-      const unsigned char *eb = ea + elmax * 4;
-#pragma unroll
-      for (int r = 0; r < RD; ++r) {
-        const unsigned char *pa = ea + ra[r];
-        const unsigned char *pb = eb + rb[r];
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const uint32_t wa = *reinterpret_cast<const uint32_t *>(pa + 128 * e);
-          const uint32_t wb = *reinterpret_cast<const uint32_t *>(pb + 128 * e);
-          if constexpr (SPE == 4) {
-            accA[r][e] += wa + wb;
-            accB[r][e] += __byte_perm(wa, 0u, 0x4341) + __byte_perm(wb, 0u, 0x4341);
-          } else {
-            tot[r][e][0] += (int32_t)((wa & 0xFFFFu) + (wb & 0xFFFFu));
-            tot[r][e][1] += (int32_t)((wa >> 16) + (wb >> 16));
-          }
-        }
-      }
-    }
-    if (q < ncur) {
-      int ra[RD];
-      offsets(q, ra);
-      const unsigned char *ea = ebase + q * elmax * 4;
-#pragma unroll
-      for (int r = 0; r < RD; ++r) {
-        const unsigned char *pa = ea + ra[r];
-#pragma unroll
-        for (int e = 0; e < E; ++e) {
-          const uint32_t wa = *reinterpret_cast<const uint32_t *>(pa + 128 * e);
-          if constexpr (SPE == 4) {
-            accA[r][e] += wa;
-            accB[r][e] += __byte_perm(wa, 0u, 0x4341);
-          } else {
-            tot[r][e][0] += (int32_t)(wa & 0xFFFFu);
-            tot[r][e][1] += (int32_t)(wa >> 16);
-          }
-        }
-      }
-    }
+    ws_accumulate<RD, SPE>(acc, erel + b * rel_words + RD * wd, DT,
+                           elem + b * L.elem_stride + 4 * i0, elmax, ncur);
     __syncwarp();
     if (lane == 0) mbar_arrive(&elem_empty[b]);
-
     if constexpr (SPE == 4) {
       since += ncur;
       if (since + cc > 256 || j == nchunks - 1) {
-        // unpack the SWAR partials (<= 256 channels) into the output array
-#pragma unroll
-        for (int r = 0; r < RD; ++r) {
-          const int row = __ldg(a.rowmap + g * DT + RD * wd + r);
-          int32_t *o = a.out + (int64_t)(row < 0 ? 0 : row) * a.out_pitch;
-#pragma unroll
-          for (int e = 0; e < E; ++e) {
-            const uint32_t Bv = accB[r][e];
-            const uint32_t Ev = accA[r][e] - (Bv << 8);  // b0 + 2^16 b2 sums
-            const int32_t part[4] = {(int32_t)(Ev & 0xFFFFu),
-                                     (int32_t)(Bv & 0xFFFFu),
-                                     (int32_t)(Ev >> 16), (int32_t)(Bv >> 16)};
-#pragma unroll
-            for (int m = 0; m < 4; ++m) {
-              const int64_t t = T0 + i0 + 32 * e + (int64_t)m * S;
-              // the first flush of the item stores; later ones are
-              // fire-and-forget reductions (no load for the warp to wait on;
-              // integer adds in any order give the same total)
-              if (row >= 0 && t < nsamp_out) {
-                if (first_flush) o[t] = part[m];
-                else atomicAdd(o + t, part[m]);
-              }
-            }
-            accA[r][e] = 0;
-            accB[r][e] = 0;
-          }
-        }
+        ws_flush<RD>(acc, a.rowmap + g * DT + RD * wd, a.out, a.out_pitch,
+                     T0 + i0, S, nsamp_out, first_flush);
         first_flush = false;
         since = 0;
       }
     }
   }
-
-  if constexpr (kRegTot) {
-#pragma unroll
-    for (int r = 0; r < RD; ++r) {
-      const int row = a.rowmap[g * DT + RD * wd + r];
-      if (row < 0) continue;
-      int32_t *o = a.out + (int64_t)row * a.out_pitch;
-#pragma unroll
-      for (int e = 0; e < E; ++e)
-#pragma unroll
-        for (int m = 0; m < SPE; ++m) {
-          const int64_t t = T0 + i0 + 32 * e + (int64_t)m * S;
-          if (t < nsamp_out) o[t] = tot[r][e][m];
-        }
-    }
-  }
+  if constexpr (SPE != 4)
+    ws_store_totals<RD, SPE>(acc, a.rowmap + g * DT + RD * wd, a.out,
+                             a.out_pitch, T0 + i0, S, nsamp_out);
   return true;
 }
 

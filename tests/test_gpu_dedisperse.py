@@ -16,7 +16,8 @@ pytestmark = pytest.mark.gpu
 
 # (dm_tile, dm_per_thread, chan_chunk, stages, flags); dm_tile 0 = library's
 # choice, -1 = direct kernel; flags 1 = single element buffer, 4 = int32
-# totals in registers (only with 1), 8 = warp-specialised kernel
+# totals in registers (only with 1), 8 = warp-specialised kernel, 16 =
+# interleaved rows staged by TMA
 TILES = [(0, 4, 8, 2, 0), (4, 4, 1, 2, 0), (4, 4, 8, 3, 1), (8, 4, 8, 2, 0),
          (8, 4, 6, 3, 1), (8, 4, 32, 4, 1), (16, 4, 8, 2, 0), (16, 4, 16, 3, 1),
          (8, 4, 8, 3, 5), (16, 4, 5, 2, 5), (4, 2, 8, 2, 5), (8, 4, 7, 2, 0),
@@ -24,6 +25,10 @@ TILES = [(0, 4, 8, 2, 0), (4, 4, 1, 2, 0), (4, 4, 8, 3, 1), (8, 4, 8, 2, 0),
          # flags 8 = warp-specialised producer/consumer kernel
          (8, 4, 6, 4, 8), (16, 8, 4, 2, 8), (8, 8, 5, 2, 8), (32, 8, 3, 4, 8),
          (4, 4, 8, 2, 8), (16, 4, 7, 2, 8), (16, 8, 5, 2, 8),
+         # flags 16 = TMA-staged pre-interleaved rows, a ring of 2..8 stages
+         (16, 8, 7, 2, 16), (16, 8, 4, 3, 16), (16, 8, 2, 8, 16),
+         (8, 8, 5, 2, 16), (32, 8, 3, 4, 16), (8, 4, 4, 4, 16),
+         (4, 4, 7, 2, 16), (16, 4, 1, 8, 16), (16, 4, 6, 2, 16),
          (-1, 4, 8, 2, 0)]
 
 
@@ -121,7 +126,9 @@ SHAPES = [
                                   (8, 4, 8, 3, 0), (16, 4, 4, 2, 1),
                                   (8, 4, 7, 3, 5), (8, 2, 7, 3, 0),
                                   (8, 2, 5, 2, 1), (8, 4, 5, 4, 8),
-                                  (16, 8, 3, 2, 8), (-1, 4, 8, 2, 0)])
+                                  (16, 8, 3, 2, 8), (16, 8, 7, 2, 16),
+                                  (8, 4, 3, 5, 16), (4, 4, 1, 2, 16),
+                                  (-1, 4, 8, 2, 0)])
 def test_ragged_shapes_bit_exact(shape, tile):
     nchan, nin, dms, nbits, f_top, bw, ts = SHAPES[shape]
     rng = np.random.default_rng(shape)
@@ -129,7 +136,7 @@ def test_ragged_shapes_bit_exact(shape, tile):
     hi = 256 if nbits == 8 else 65536
     x = rng.integers(0, hi, size=(nin, nchan)).astype(dt)
     p = _plan(nchan, f_top, bw, ts, dms, nbits=nbits)
-    if nbits == 16:
+    if nbits == 16 and tile[4] != 16:
         tile = tile[:4] + (tile[4] & 1,)   # uint16 totals are always in registers
     if not _set_tile(p, tile):
         pytest.skip("tile does not fit")
@@ -223,3 +230,49 @@ def test_warp_specialised_tile_needs_even_stages():
     assert e.value.code == ddsp_lib.DDSP_E_INVALID_ARG
     p.set_tile(16, 8, 4, 2, 8)
     assert p.get_tile()["stages"] == 2
+
+
+@pytest.mark.parametrize("nchan,nbits", [(256, 8), (100, 8), (48, 16)])
+def test_stage_then_dedisperse_staged(nchan, nbits):
+    """ddsp_stage + ddsp_dedisperse_staged give ddsp_dedisperse's output for
+    the interleaved tile (fused single-pass staging for uint8 with nchan % 16
+    == 0, unpack + interleave otherwise) and for the relayout tile; a tile
+    change drops the staged block and a wrong nsamp_out is refused."""
+    rng = np.random.default_rng(nchan)
+    dt = np.uint8 if nbits == 8 else np.uint16
+    hi = 256 if nbits == 8 else 65536
+    dms = np.linspace(0, 30, 24)
+    p = _plan(nchan, 500.0, -1.0, 1e-3, dms, nbits=nbits)
+    x = rng.integers(0, hi, size=(4000, nchan)).astype(dt)
+    ref = oracle.dedisperse(x, p.delays())
+    xd = to_dev(x)
+    for tile in [(16, 4, 6, 2, 16), (8, 4, 5, 4, 8 if nbits == 8 else 0)]:
+        p.set_tile(*tile)
+        with pytest.raises(DdspError) as e:
+            p.dedisperse_staged(ref.shape[1])
+        assert e.value.code == ddsp_lib.DDSP_E_STATE
+        nout = p.stage(xd)
+        assert nout == ref.shape[1]
+        with pytest.raises(DdspError) as e:
+            p.dedisperse_staged(nout - 1)
+        assert e.value.code == ddsp_lib.DDSP_E_SHAPE
+        out = p.dedisperse_staged(nout)
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy(), ref), tile
+
+
+def test_interleaved_cm_path_matches_oracle():
+    """dedisperse_cm with the interleaved tile rebuilds the interleaved rows
+    from caller-owned channel-major rows (zeros past the valid samples)."""
+    cfg_nchan, nin = 128, 6000
+    dms = np.linspace(0, 50, 40)
+    p = _plan(cfg_nchan, 600.0, -1.5, 1e-3, dms)
+    p.set_tile(16, 8, 7, 2, 16)
+    x = np.random.default_rng(9).integers(0, 256, size=(nin, cfg_nchan)).astype(np.uint8)
+    ref = oracle.dedisperse(x, p.delays())
+    nout = ref.shape[1]
+    pitch = p.cm_pitch(nout)
+    cm = p.unpack(to_dev(x), pitch)
+    out = p.dedisperse_cm(cm, pitch, nout)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy(), ref)
