@@ -445,8 +445,8 @@ int ddsp_server_check(ddsp_server *server, ddsp_stream_t stream);
  * host thread (empty if none); the storage is the library's. */
 const char *ddsp_last_error_detail(void);
 
-/* Tile shape of the dedispersion kernel.  A block of 8 warps computes
- * dm_tile DM trials x time_tile output samples; each thread owns
+/* Tile shape of the dedispersion kernel.  A block of 8 (consumer) warps
+ * computes dm_tile DM trials x time_tile output samples; each thread owns
  * dm_per_thread (2, 4 or 8) trials x 16 samples; chan_chunk channels (1..32)
  * are staged per pipeline step with `stages` (2..4) raw-window buffers.
  * dm_tile must be dm_per_thread x {1, 2, 4}; time_tile follows from it.
@@ -464,8 +464,10 @@ const char *ddsp_last_error_detail(void);
  * once per block of data in HBM, element i = {x[i], x[i+S], x[i+2S],
  * x[i+3S]} for the tile's segment S, are copied by TMA straight into a
  * ring of `stages` (2..8) element stages of chan_chunk channels each; one
- * producer warp, eight consumer warps; dm_per_thread 4, or 8 for uint8).
- * Every variant computes the same exact sums.  dm_tile = 0 restores the library's choice, dm_tile = -1
+ * producer warp, eight consumer warps; dm_per_thread 4, or 8 for uint8),
+ * optionally with DDSP_TILE_WIDE (sixteen consumer warps and one block per
+ * SM: time_tile doubles for the same dm_tile).  Every variant computes the
+ * same exact sums.  dm_tile = 0 restores the library's choice, dm_tile = -1
  * selects the direct (unstaged) kernel.  DDSP_E_INVALID_ARG for a shape the
  * kernel does not implement or whose staging does not fit on chip.
  * Synchronises. */
@@ -473,6 +475,7 @@ const char *ddsp_last_error_detail(void);
 #define DDSP_TILE_REGISTER_TOTALS 4
 #define DDSP_TILE_WARP_SPECIALIZED 8
 #define DDSP_TILE_INTERLEAVED 16
+#define DDSP_TILE_WIDE 32
 int ddsp_plan_set_tile(ddsp_plan *plan, int dm_tile, int dm_per_thread,
                        int chan_chunk, int stages, int flags);
 int ddsp_plan_get_tile(const ddsp_plan *plan, int *dm_tile,

@@ -25,10 +25,12 @@ enum : int {
   kTileRegisterTotals = 4,    // int32 totals in registers, not in the output
   kTileWarpSpecialized = 8,   // producer / consumer warps (k_dedisp_ws.cu)
   kTileInterleaved = 16,      // staged from pre-interleaved rows (k_dedisp_il.cu)
+  kTileWide = 32,             // with kTileInterleaved: 16 consumer warps
 };
 
 struct DedispTile {
-  int wt = 0;          // warps along time (0: use the direct kernel)
+  int wt = 0;          // warps along time (0: use the direct kernel);
+                       // wt * wd = 8 consumer warps, 16 for kTileWide
   int wd = 0;          // warps along DM
   int rd = 4;          // DM trials per thread (2 or 4; 4 or 8 when warp-
                        // specialised)

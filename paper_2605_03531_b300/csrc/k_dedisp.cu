@@ -514,13 +514,14 @@ int dedisp_copy_bytes(const DedispTile &t, int span, int nbits) {
 }
 
 bool dedisp_tile_supported(const DedispTile &t, int nbits) {
-  if (t.wt * t.wd != kThreads / 32) return false;
+  const bool wide = (t.flags & kTileWide) != 0;
+  if (t.wt * t.wd != (wide ? 2 : 1) * (kThreads / 32)) return false;
   // instantiated variants (the dispatch list in launch_dedisperse): int32
   // totals in registers only with one element buffer; uint16 totals are
   // always in registers (the flag is implied)
   const int f = t.flags;
   if (f & kTileInterleaved) {
-    if (f != kTileInterleaved) return false;
+    if ((f & ~kTileWide) != kTileInterleaved) return false;
     if (t.rd != 4 && !(t.rd == 8 && nbits == 8)) return false;
     if (t.wd != 1 && t.wd != 2 && t.wd != 4) return false;
     if (nbits == 16 && t.rd == 8) return false;

@@ -169,11 +169,14 @@ unpack_interleave_u8_kernel(const uint8_t *__restrict__ in, int64_t nsamp_in,
 }
 
 // One block per (DM tile, time tile): warp NC is the producer, warps
-// 0..NC-1 the consumers (WT along time x WD along DM).  Two blocks per SM:
-// 18 warps put 5 on some SM sub-partitions, whose 16K registers then allow
-// 96 a thread.
+// 0..NC-1 the consumers (WT along time x WD along DM).  NC = 8: two blocks
+// per SM; NC = 16 (wide tile): one block per SM, twice the time tile and
+// the chunk, so each chunk's synchronisation and each window's delay span
+// are spread over twice the adds.  Either way an SM sub-partition holds 5
+// warps, whose 16K registers allow 96 a thread (the bound below).
 template <int WT, int WD, int RD, typename T>
-__global__ void __launch_bounds__(32 * (WT * WD + 1), 2)
+__global__ void __launch_bounds__(WT * WD == 16 ? 640 : 32 * (WT * WD + 1),
+                                  WT * WD == 16 ? 1 : 2)
 dedisp_il_kernel(IlArgs a, int32_t *err, long long timeout_cycles) {
   constexpr int SPE = 4 / sizeof(T);
   constexpr int E = kElemPerThread;
@@ -216,13 +219,14 @@ dedisp_il_kernel(IlArgs a, int32_t *err, long long timeout_cycles) {
     int base = 0;
     int2 dcur = ld_desc(lane), dnext = ld_desc(32 + lane);
     int j = 0;
+    // ring position of chunk j: stage st, pass (j / nst) parity ph
+    int st = 0;
+    uint32_t ph = 0;
     for (; j < nchunks; ++j) {
-      const int st = j % nst;
       // the stage's previous chunk (j - nst) has been consumed (the warp
       // gives up as a whole if any lane's wait ran out)
       if (!__all_sync(0xffffffffu,
-                      mbar_wait(&empty[st], (uint32_t)(((j / nst) & 1) ^ 1),
-                                timeout_cycles)))
+                      mbar_wait(&empty[st], ph ^ 1u, timeout_cycles)))
         break;
       const int c0 = j * cc;
       const int ncur = min(cc, nchan - c0);
@@ -251,6 +255,10 @@ dedisp_il_kernel(IlArgs a, int32_t *err, long long timeout_cycles) {
                  &full[st]);
       if (lane == 0)
         bulk_g2s(sb, rel_g + (int64_t)c0 * DT, relbytes, &full[st]);
+      if (++st == nst) {
+        st = 0;
+        ph ^= 1u;
+      }
     }
     if (j < nchunks) {
       // gave up: record it and let the copies in flight (chunks j - nst ..
@@ -272,11 +280,11 @@ dedisp_il_kernel(IlArgs a, int32_t *err, long long timeout_cycles) {
   acc.zero();
   bool first_flush = true;
   int since = 0;
+  int st = 0;
+  uint32_t ph = 0;
   for (int j = 0; j < nchunks; ++j) {
-    const int st = j % nst;
     const int ncur = min(cc, nchan - j * cc);
-    if (!__all_sync(0xffffffffu, mbar_wait(&full[st], (uint32_t)((j / nst) & 1),
-                                           timeout_cycles))) {
+    if (!__all_sync(0xffffffffu, mbar_wait(&full[st], ph, timeout_cycles))) {
       if (lane == 0) atomicExch(err, kErrTimeout);
       return;
     }
@@ -286,6 +294,10 @@ dedisp_il_kernel(IlArgs a, int32_t *err, long long timeout_cycles) {
                            sb + L.rel_stride + 4 * i0, elmax, ncur);
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[st]);
+    if (++st == nst) {
+      st = 0;
+      ph ^= 1u;
+    }
     if constexpr (SPE == 4) {
       since += ncur;
       if (since + cc > 256 || j == nchunks - 1) {
@@ -388,13 +400,22 @@ cudaError_t launch_dedisperse_il(const Plan &p, int64_t ypitch,
     return launch_il_t<WT_, WD_, RD_, T_>(p, ypitch, nsamp_out, d_out, s,   \
                                           elmax, smem);
   if (p.nbits == 8) {
-    DDSP_IL(4, 2, 8, uint8_t)
+    DDSP_IL(8, 2, 8, uint8_t)     // wide: 16 consumer warps
+    DDSP_IL(16, 1, 8, uint8_t)
+    DDSP_IL(4, 4, 8, uint8_t)
+    DDSP_IL(8, 2, 4, uint8_t)
+    DDSP_IL(16, 1, 4, uint8_t)
+    DDSP_IL(4, 4, 4, uint8_t)
+    DDSP_IL(4, 2, 8, uint8_t)     // 8 consumer warps
     DDSP_IL(8, 1, 8, uint8_t)
     DDSP_IL(2, 4, 8, uint8_t)
     DDSP_IL(4, 2, 4, uint8_t)
     DDSP_IL(8, 1, 4, uint8_t)
     DDSP_IL(2, 4, 4, uint8_t)
   } else {
+    DDSP_IL(8, 2, 4, uint16_t)
+    DDSP_IL(16, 1, 4, uint16_t)
+    DDSP_IL(4, 4, 4, uint16_t)
     DDSP_IL(4, 2, 4, uint16_t)
     DDSP_IL(8, 1, 4, uint16_t)
     DDSP_IL(2, 4, 4, uint16_t)

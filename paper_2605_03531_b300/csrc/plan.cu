@@ -129,15 +129,19 @@ int build_tables_for(const Plan &p, const DedispTile &tile, DedispTables &tab) {
 int build_tables(Plan &p) { return build_tables_for(p, p.tile, p.tab); }
 
 // Default tile: the first shape (in order of preference) whose staged
-// windows fit with two resident blocks per SM, else one block per SM, else
-// the direct kernel.
+// windows fit: the wide interleaved tile (one block per SM), then the
+// others with two resident blocks per SM, else one block per SM, else the
+// direct kernel.
 DedispTile choose_tile(const Plan &p) {
-  // {wt, wd, rd, cc, flags}: the warp-specialised kernel first (fastest on
-  // the 4096-channel 1024-DM block; cc is an upper limit, the largest chunk
-  // that fits is taken), then the block-synchronous kernel with totals in
-  // registers, then smaller staging footprints
+  // {wt, wd, rd, cc, flags}: the interleaved kernel first (fastest on the
+  // 4096-channel 1024-DM block: wide 41 ms, 8 consumer warps 48 ms, the
+  // warp-specialised relayout kernel 54 ms; cc is an upper limit, the
+  // largest chunk that fits is taken), then the relayout kernels, then the
+  // block-synchronous kernel, then smaller staging footprints
   struct Cand { int wt, wd, rd, cc, flags; };
+  constexpr int kIlWide = kTileInterleaved | kTileWide;
   const Cand prefs[] = {
+      {8, 2, 8, 16, kIlWide}, {16, 1, 8, 16, kIlWide}, {8, 2, 4, 16, kIlWide},
       {4, 2, 8, 8, kTileInterleaved}, {8, 1, 8, 8, kTileInterleaved},
       {4, 2, 4, 8, kTileInterleaved},
       {4, 2, 8, 8, kTileWarpSpecialized}, {8, 1, 8, 8, kTileWarpSpecialized},
@@ -145,8 +149,12 @@ DedispTile choose_tile(const Plan &p) {
       {4, 2, 4, 6, kTileSingleElemBuffer}, {8, 1, 4, 4, kTileSingleElemBuffer},
       {8, 1, 4, 2, kTileSingleElemBuffer}, {8, 1, 2, 2, kTileSingleElemBuffer},
       {8, 1, 2, 1, kTileSingleElemBuffer}};
-  for (size_t budget : {kSmemBudgetTwoBlocks, kSmemBudgetOneBlock}) {
+  // the wide tiles (one block per SM) against the one-block budget first,
+  // then the rest with two blocks per SM, then with one
+  for (int pass = 0; pass < 3; ++pass) {
+    const size_t budget = pass == 1 ? kSmemBudgetTwoBlocks : kSmemBudgetOneBlock;
     for (const Cand &c : prefs) {
+      if (((c.flags & kTileWide) != 0) != (pass == 0)) continue;
       DedispTile t;
       t.wt = c.wt;
       t.wd = c.wd;
@@ -159,8 +167,8 @@ DedispTile choose_tile(const Plan &p) {
         // two element stages of the largest chunk that fits: each chunk
         // costs the consumers a fixed synchronisation latency, which larger
         // chunks amortise better than a deeper ring hides it (4096-channel
-        // 1024-DM block: 7 channels x 2 stages 49 ms, 4 x 3 54 ms, 2 x 6
-        // 64 ms)
+        // 1024-DM block, 8 consumer warps: 7 channels x 2 stages 49 ms, 4 x
+        // 3 54 ms, 2 x 6 64 ms; wide: 11 x 2 42 ms, 7 x 3 43 ms)
         t.nbuf = 2;
         for (int cc = c.cc; cc >= 2; --cc) {
           t.chan_chunk = cc;
@@ -444,11 +452,11 @@ int ddsp_plan_set_tile(ddsp_plan *h, int dm_tile, int dm_per_thread,
     if (dm_tile % t.rd) return DDSP_E_INVALID_ARG;
     t.wd = dm_tile / t.rd;
     if (t.wd <= 0 || (kThreads / 32) % t.wd) return DDSP_E_INVALID_ARG;
-    t.wt = (kThreads / 32) / t.wd;
+    t.wt = (kThreads / 32) / t.wd * ((flags & kTileWide) ? 2 : 1);
     t.chan_chunk = chan_chunk;
     t.nbuf = stages;
     if (flags & ~(kTileSingleElemBuffer | kTileRegisterTotals |
-                  kTileWarpSpecialized | kTileInterleaved))
+                  kTileWarpSpecialized | kTileInterleaved | kTileWide))
       return DDSP_E_INVALID_ARG;
     t.flags = flags;
     if (!dedisp_tile_supported(t, p.nbits)) return DDSP_E_INVALID_ARG;

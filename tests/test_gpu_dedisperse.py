@@ -17,7 +17,7 @@ pytestmark = pytest.mark.gpu
 # (dm_tile, dm_per_thread, chan_chunk, stages, flags); dm_tile 0 = library's
 # choice, -1 = direct kernel; flags 1 = single element buffer, 4 = int32
 # totals in registers (only with 1), 8 = warp-specialised kernel, 16 =
-# interleaved rows staged by TMA
+# interleaved rows staged by TMA, 48 = that with 16 consumer warps
 TILES = [(0, 4, 8, 2, 0), (4, 4, 1, 2, 0), (4, 4, 8, 3, 1), (8, 4, 8, 2, 0),
          (8, 4, 6, 3, 1), (8, 4, 32, 4, 1), (16, 4, 8, 2, 0), (16, 4, 16, 3, 1),
          (8, 4, 8, 3, 5), (16, 4, 5, 2, 5), (4, 2, 8, 2, 5), (8, 4, 7, 2, 0),
@@ -29,6 +29,10 @@ TILES = [(0, 4, 8, 2, 0), (4, 4, 1, 2, 0), (4, 4, 8, 3, 1), (8, 4, 8, 2, 0),
          (16, 8, 7, 2, 16), (16, 8, 4, 3, 16), (16, 8, 2, 8, 16),
          (8, 8, 5, 2, 16), (32, 8, 3, 4, 16), (8, 4, 4, 4, 16),
          (4, 4, 7, 2, 16), (16, 4, 1, 8, 16), (16, 4, 6, 2, 16),
+         # flags 48 = the same with 16 consumer warps (one block per SM)
+         (16, 8, 11, 2, 48), (8, 8, 5, 2, 48), (32, 8, 3, 5, 48),
+         (16, 8, 1, 8, 48), (16, 4, 9, 2, 48), (8, 4, 6, 3, 48),
+         (4, 4, 16, 2, 48),
          (-1, 4, 8, 2, 0)]
 
 
@@ -128,6 +132,7 @@ SHAPES = [
                                   (8, 2, 5, 2, 1), (8, 4, 5, 4, 8),
                                   (16, 8, 3, 2, 8), (16, 8, 7, 2, 16),
                                   (8, 4, 3, 5, 16), (4, 4, 1, 2, 16),
+                                  (16, 8, 11, 2, 48), (8, 4, 5, 3, 48),
                                   (-1, 4, 8, 2, 0)])
 def test_ragged_shapes_bit_exact(shape, tile):
     nchan, nin, dms, nbits, f_top, bw, ts = SHAPES[shape]
@@ -136,7 +141,7 @@ def test_ragged_shapes_bit_exact(shape, tile):
     hi = 256 if nbits == 8 else 65536
     x = rng.integers(0, hi, size=(nin, nchan)).astype(dt)
     p = _plan(nchan, f_top, bw, ts, dms, nbits=nbits)
-    if nbits == 16 and tile[4] != 16:
+    if nbits == 16 and not tile[4] & 16:
         tile = tile[:4] + (tile[4] & 1,)   # uint16 totals are always in registers
     if not _set_tile(p, tile):
         pytest.skip("tile does not fit")
@@ -246,7 +251,8 @@ def test_stage_then_dedisperse_staged(nchan, nbits):
     x = rng.integers(0, hi, size=(4000, nchan)).astype(dt)
     ref = oracle.dedisperse(x, p.delays())
     xd = to_dev(x)
-    for tile in [(16, 4, 6, 2, 16), (8, 4, 5, 4, 8 if nbits == 8 else 0)]:
+    for tile in [(16, 4, 6, 2, 16), (16, 4, 9, 2, 48),
+                 (8, 4, 5, 4, 8 if nbits == 8 else 0)]:
         p.set_tile(*tile)
         with pytest.raises(DdspError) as e:
             p.dedisperse_staged(ref.shape[1])
