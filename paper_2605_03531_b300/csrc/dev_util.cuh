@@ -53,15 +53,32 @@ __device__ __forceinline__ bool mbar_try(uint32_t a, uint32_t parity) {
   return done != 0;
 }
 
+// One test that lets the hardware suspend the thread until the phase
+// completes or about `hint_ns` pass, so a long wait costs a few polls of
+// shared memory instead of one every few cycles.
+__device__ __forceinline__ bool mbar_try_sleep(uint32_t a, uint32_t parity,
+                                               uint32_t hint_ns) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(a), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return done != 0;
+}
+
 // Bounded wait on an mbarrier phase: false if `limit` cycles pass first.
-// A phase that is already complete costs one test and no clock read.
+// A phase that is already complete costs one test and no clock read; later
+// tests suspend the thread (up to 20 us each) until the phase completes.
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity,
                                           long long limit) {
   const uint32_t a = smem_u32(bar);
   if (mbar_try(a, parity)) return true;
   const long long t0 = clock64();
   while (true) {
-    if (mbar_try(a, parity)) return true;
+    if (mbar_try_sleep(a, parity, 20000u)) return true;
     if (clock64() - t0 > limit) return false;
   }
 }
