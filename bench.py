@@ -242,6 +242,8 @@ def run_ours(args):
     plan = Plan(cfg.nchan, cfg.f_top, cfg.chan_bw, cfg.tsamp, cfg.dm_list(),
                 cfg.widths, nbits=8, norm_window=cfg.norm_window,
                 cand_capacity=1 << 20)
+    if args.tile:
+        plan.set_tile(*(int(v) for v in args.tile.split(",")))
     D = plan.max_delay
     nout = args.nsamp_out or cfg.nsamp_out
     nin = nout + D
@@ -1387,6 +1389,10 @@ def main():
     ap.add_argument("--ndm", type=int, default=0, help="sps: DM trials (0 = 2048)")
     ap.add_argument("--nsamp", type=int, default=0,
                     help="sps: samples per trial (0 = 1048576)")
+    ap.add_argument("--tile", default="",
+                    help="beam: dedispersion tile 'dm_tile,dm_per_thread,"
+                         "chan_chunk,stages,flags' (ddsp_plan_set_tile; "
+                         "default: the library's choice)")
     ap.add_argument("--profile", action="store_true",
                     help="kernels only: no clocks, end-to-end or CPU baseline "
                          "(for profiler captures)")
