@@ -126,6 +126,8 @@ cudaError_t launch_dedisperse_direct(const Plan &p, const void *d_cm,
                                      int64_t pitch, int64_t nsamp_out,
                                      int32_t *d_out, cudaStream_t s);
 int dedisp_time_tile(const DedispTile &t, int nbits);
+int dedisp_elems_per_thread(const DedispTile &t);
+int dedisp_segment(const DedispTile &t);   // elements per segment S
 int dedisp_copy_bytes(const DedispTile &t, int span, int nbits);
 bool dedisp_tile_supported(const DedispTile &t, int nbits);
 

@@ -465,9 +465,21 @@ cudaError_t launch_t(const Plan &p, const void *d_cm, int64_t pitch,
 
 }  // namespace
 
+// Interleaved elements per consumer thread: 4, except for the wide
+// interleaved tile, where every thread holds 32 (DM trial, element) pairs.
+int dedisp_elems_per_thread(const DedispTile &t) {
+  const int wide = kTileInterleaved | kTileWide;
+  return (t.flags & wide) == wide && t.rd > 0 ? 32 / t.rd : kElemPerThread;
+}
+
+// Elements per segment S (a time tile holds SPE segments).
+int dedisp_segment(const DedispTile &t) {
+  return 32 * dedisp_elems_per_thread(t) * t.wt;
+}
+
 // Time tile of a tile shape (samples per block).
 static int time_tile_of(const DedispTile &t, int nbits) {
-  return (nbits == 8 ? 4 : 2) * 32 * kElemPerThread * t.wt;
+  return (nbits == 8 ? 4 : 2) * dedisp_segment(t);
 }
 
 void dedisp_buffer_sizes(const DedispTile &t, int span_max, int nbits,
@@ -479,7 +491,7 @@ static void buffer_sizes(const DedispTile &t, int span_max, int nbits,
 
 void dedisp_buffer_sizes(const DedispTile &t, int span_max, int nbits,
                          int *rawmax, int *elmax) {
-  const int S = 32 * kElemPerThread * t.wt;
+  const int S = dedisp_segment(t);
   const int TT = time_tile_of(t, nbits);
   const int bps = nbits / 8;
   *elmax = ((S + span_max + 4) + 3) & ~3;
@@ -506,7 +518,7 @@ size_t dedisp_smem_bytes(const DedispTile &t, int span_max, int nbits) {
 int dedisp_copy_bytes(const DedispTile &t, int span, int nbits) {
   if (t.flags & kTileInterleaved) {
     // elements 0 .. S + span - 1 of the window, whole 16-byte words
-    const int S = 32 * kElemPerThread * t.wt;
+    const int S = dedisp_segment(t);
     return ((S + span + 3) & ~3) * 4;
   }
   const int TT = time_tile_of(t, nbits);

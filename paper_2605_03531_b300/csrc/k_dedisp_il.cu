@@ -174,12 +174,11 @@ unpack_interleave_u8_kernel(const uint8_t *__restrict__ in, int64_t nsamp_in,
 // the chunk, so each chunk's synchronisation and each window's delay span
 // are spread over twice the adds.  Either way an SM sub-partition holds 5
 // warps, whose 16K registers allow 96 a thread (the bound below).
-template <int WT, int WD, int RD, typename T>
+template <int WT, int WD, int RD, int E, typename T>
 __global__ void __launch_bounds__(WT * WD == 16 ? 640 : 32 * (WT * WD + 1),
                                   WT * WD == 16 ? 1 : 2)
 dedisp_il_kernel(IlArgs a, int32_t *err, long long timeout_cycles) {
   constexpr int SPE = 4 / sizeof(T);
-  constexpr int E = kElemPerThread;
   constexpr int S = 32 * E * WT;     // elements per segment
   constexpr int TT = SPE * S;        // output samples per tile
   constexpr int DT = RD * WD;
@@ -276,7 +275,7 @@ dedisp_il_kernel(IlArgs a, int32_t *err, long long timeout_cycles) {
   // ============================= consumers ==============================
   const int wt = warp % WT, wd = warp / WT;
   const int i0 = 32 * E * wt + lane;  // first element of this thread
-  WsAcc<RD, SPE> acc;
+  WsAcc<RD, SPE, E> acc;
   acc.zero();
   bool first_flush = true;
   int since = 0;
@@ -289,9 +288,8 @@ dedisp_il_kernel(IlArgs a, int32_t *err, long long timeout_cycles) {
       return;
     }
     const unsigned char *sb = stages + st * L.stage_stride;
-    ws_accumulate<RD, SPE>(acc,
-                           reinterpret_cast<const int32_t *>(sb) + RD * wd, DT,
-                           sb + L.rel_stride + 4 * i0, elmax, ncur);
+    ws_accumulate(acc, reinterpret_cast<const int32_t *>(sb) + RD * wd, DT,
+                  sb + L.rel_stride + 4 * i0, elmax, ncur);
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[st]);
     if (++st == nst) {
@@ -301,23 +299,23 @@ dedisp_il_kernel(IlArgs a, int32_t *err, long long timeout_cycles) {
     if constexpr (SPE == 4) {
       since += ncur;
       if (since + cc > 256 || j == nchunks - 1) {
-        ws_flush<RD>(acc, a.rowmap + g * DT + RD * wd, a.out, a.out_pitch,
-                     T0 + i0, S, a.nsamp_out, first_flush);
+        ws_flush(acc, a.rowmap + g * DT + RD * wd, a.out, a.out_pitch,
+                 T0 + i0, S, a.nsamp_out, first_flush);
         first_flush = false;
         since = 0;
       }
     }
   }
   if constexpr (SPE != 4)
-    ws_store_totals<RD, SPE>(acc, a.rowmap + g * DT + RD * wd, a.out,
-                             a.out_pitch, T0 + i0, S, a.nsamp_out);
+    ws_store_totals(acc, a.rowmap + g * DT + RD * wd, a.out, a.out_pitch,
+                    T0 + i0, S, a.nsamp_out);
 }
 
-template <int WT, int WD, int RD, typename T>
+template <int WT, int WD, int RD, int E, typename T>
 cudaError_t launch_il_t(const Plan &p, int64_t ypitch, int64_t nsamp_out,
                         int32_t *d_out, cudaStream_t s, int elmax,
                         size_t smem) {
-  auto kern = dedisp_il_kernel<WT, WD, RD, T>;
+  auto kern = dedisp_il_kernel<WT, WD, RD, E, T>;
   static size_t attr_bytes = 0;
   if (smem > attr_bytes) {
     cudaError_t e = cudaFuncSetAttribute(
@@ -331,7 +329,7 @@ cudaError_t launch_il_t(const Plan &p, int64_t ypitch, int64_t nsamp_out,
     attr_bytes = smem;
   }
   constexpr int SPE = 4 / sizeof(T);
-  constexpr int TT = SPE * 32 * kElemPerThread * WT;
+  constexpr int TT = SPE * 32 * E * WT;
   const int ntt = (int)((nsamp_out + TT - 1) / TT);
   IlArgs a{};
   a.y = static_cast<const uint32_t *>(p.d_il);
@@ -363,7 +361,7 @@ int dedisp_il_max_stages() { return kIlMaxStages; }
 
 cudaError_t launch_interleave(const Plan &p, const void *d_cm, int64_t pitch,
                               int64_t nvalid, int64_t ypitch, cudaStream_t s) {
-  const int S = 32 * kElemPerThread * p.tile.wt;
+  const int S = dedisp_segment(p.tile);
   const dim3 grid((unsigned)((ypitch / 4 + 255) / 256), (unsigned)p.nchan);
   uint32_t *y = static_cast<uint32_t *>(p.d_il);
   if (p.nbits == 8)
@@ -382,7 +380,7 @@ bool unpack_interleave_fused(const Plan &p) {
 cudaError_t launch_unpack_interleave(const Plan &p, const void *d_in,
                                      int64_t nsamp_in, int64_t ypitch,
                                      cudaStream_t s) {
-  const int S = 32 * kElemPerThread * p.tile.wt;
+  const int S = dedisp_segment(p.tile);
   const dim3 grid((unsigned)((ypitch + kIlTS - 1) / kIlTS),
                   (unsigned)((p.nchan + kIlTC - 1) / kIlTC));
   unpack_interleave_u8_kernel<<<grid, 256, 0, s>>>(
@@ -395,30 +393,31 @@ cudaError_t launch_dedisperse_il(const Plan &p, int64_t ypitch,
                                  int64_t nsamp_out, int32_t *d_out,
                                  cudaStream_t s, int elmax, size_t smem) {
   const int wt = p.tile.wt, wd = p.tile.wd, rd = p.tile.rd;
-#define DDSP_IL(WT_, WD_, RD_, T_)                                          \
-  if (wt == WT_ && wd == WD_ && rd == RD_)                                  \
-    return launch_il_t<WT_, WD_, RD_, T_>(p, ypitch, nsamp_out, d_out, s,   \
-                                          elmax, smem);
+  const int ept = dedisp_elems_per_thread(p.tile);
+#define DDSP_IL(WT_, WD_, RD_, E_, T_)                                      \
+  if (wt == WT_ && wd == WD_ && rd == RD_ && ept == E_)                     \
+    return launch_il_t<WT_, WD_, RD_, E_, T_>(p, ypitch, nsamp_out, d_out,  \
+                                              s, elmax, smem);
   if (p.nbits == 8) {
-    DDSP_IL(8, 2, 8, uint8_t)     // wide: 16 consumer warps
-    DDSP_IL(16, 1, 8, uint8_t)
-    DDSP_IL(4, 4, 8, uint8_t)
-    DDSP_IL(8, 2, 4, uint8_t)
-    DDSP_IL(16, 1, 4, uint8_t)
-    DDSP_IL(4, 4, 4, uint8_t)
-    DDSP_IL(4, 2, 8, uint8_t)     // 8 consumer warps
-    DDSP_IL(8, 1, 8, uint8_t)
-    DDSP_IL(2, 4, 8, uint8_t)
-    DDSP_IL(4, 2, 4, uint8_t)
-    DDSP_IL(8, 1, 4, uint8_t)
-    DDSP_IL(2, 4, 4, uint8_t)
+    DDSP_IL(8, 2, 8, 4, uint8_t)     // wide: 16 consumer warps, E = 32 / RD
+    DDSP_IL(16, 1, 8, 4, uint8_t)
+    DDSP_IL(4, 4, 8, 4, uint8_t)
+    DDSP_IL(4, 4, 4, 8, uint8_t)
+    DDSP_IL(8, 2, 4, 8, uint8_t)
+    DDSP_IL(16, 1, 4, 8, uint8_t)
+    DDSP_IL(4, 2, 8, 4, uint8_t)     // 8 consumer warps, E = 4
+    DDSP_IL(8, 1, 8, 4, uint8_t)
+    DDSP_IL(2, 4, 8, 4, uint8_t)
+    DDSP_IL(4, 2, 4, 4, uint8_t)
+    DDSP_IL(8, 1, 4, 4, uint8_t)
+    DDSP_IL(2, 4, 4, 4, uint8_t)
   } else {
-    DDSP_IL(8, 2, 4, uint16_t)
-    DDSP_IL(16, 1, 4, uint16_t)
-    DDSP_IL(4, 4, 4, uint16_t)
-    DDSP_IL(4, 2, 4, uint16_t)
-    DDSP_IL(8, 1, 4, uint16_t)
-    DDSP_IL(2, 4, 4, uint16_t)
+    DDSP_IL(4, 4, 4, 8, uint16_t)
+    DDSP_IL(8, 2, 4, 8, uint16_t)
+    DDSP_IL(16, 1, 4, 8, uint16_t)
+    DDSP_IL(4, 2, 4, 4, uint16_t)
+    DDSP_IL(8, 1, 4, 4, uint16_t)
+    DDSP_IL(2, 4, 4, 4, uint16_t)
   }
 #undef DDSP_IL
   return cudaErrorInvalidValue;

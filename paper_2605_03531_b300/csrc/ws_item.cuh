@@ -62,13 +62,15 @@ struct WsLayout {
 // ---------------------------------------------------------------------------
 // Consumer arithmetic shared by the warp-specialised kernels.  A consumer
 // thread owns RD DM trials x E interleaved elements (i0 + 32 e, e < E) of
-// one time tile; element i holds SPE samples, i + m S for m < SPE.
+// one time tile; element i holds SPE samples, i + m S for m < SPE.  Each DM
+// offset serves E loads, so a larger E spends fewer offset loads and
+// address adds per operand.
 
 // SWAR partials (uint8: A, B, flushed every <= 256 channels) or int32
-// totals (uint16: two 16-bit samples per element, exact in int32).
-template <int RD, int SPE>
+// totals (uint16: two 16-bit samples per element, exact in int32); E
+// elements per thread.
+template <int RD, int SPE, int E = kElemPerThread>
 struct WsAcc {
-  static constexpr int E = kElemPerThread;
   uint32_t A[RD][E], B[RD][E];
   int32_t tot[SPE != 4 ? RD : 1][E][SPE];
   __device__ __forceinline__ void zero() {
@@ -91,12 +93,11 @@ struct WsAcc {
 // i0), its DM trial r's byte offset is rel[q * dt + r] (rel already points
 // at this warp's first trial; 16-byte aligned).  Two channels per step
 // (3-input adds), then a lone last channel.
-template <int RD, int SPE>
-__device__ __forceinline__ void ws_accumulate(WsAcc<RD, SPE> &acc,
+template <int RD, int SPE, int E>
+__device__ __forceinline__ void ws_accumulate(WsAcc<RD, SPE, E> &acc,
                                               const int32_t *rel, int dt,
                                               const unsigned char *ebase,
                                               int elmax, int ncur) {
-  constexpr int E = kElemPerThread;
   auto offsets = [&](int q, int(&rr)[RD]) {
 #pragma unroll
     for (int h = 0; h < RD; h += 4) {
@@ -159,12 +160,11 @@ __device__ __forceinline__ void ws_accumulate(WsAcc<RD, SPE> &acc,
 // into the output rows rowmap[r] (-1: padding trial) at times t0 + 32 e +
 // m S; the item's first flush stores, later ones are fire-and-forget
 // reductions (integer adds in any order give the same total).
-template <int RD>
-__device__ __forceinline__ void ws_flush(WsAcc<RD, 4> &acc,
+template <int RD, int E>
+__device__ __forceinline__ void ws_flush(WsAcc<RD, 4, E> &acc,
                                          const int32_t *rowmap, int32_t *out,
                                          int64_t out_pitch, int64_t t0, int S,
                                          int64_t nsamp_out, bool first) {
-  constexpr int E = kElemPerThread;
 #pragma unroll
   for (int r = 0; r < RD; ++r) {
     const int row = __ldg(rowmap + r);
@@ -190,13 +190,12 @@ __device__ __forceinline__ void ws_flush(WsAcc<RD, 4> &acc,
 }
 
 // uint16: store the register totals once, after the last channel.
-template <int RD, int SPE>
-__device__ __forceinline__ void ws_store_totals(const WsAcc<RD, SPE> &acc,
+template <int RD, int SPE, int E>
+__device__ __forceinline__ void ws_store_totals(const WsAcc<RD, SPE, E> &acc,
                                                 const int32_t *rowmap,
                                                 int32_t *out, int64_t out_pitch,
                                                 int64_t t0, int S,
                                                 int64_t nsamp_out) {
-  constexpr int E = kElemPerThread;
 #pragma unroll
   for (int r = 0; r < RD; ++r) {
     const int row = rowmap[r];
@@ -423,23 +422,23 @@ __device__ __forceinline__ bool ws_item(const WsBeam &a, int g, int64_t T0,
       if (lane == 0) atomicExch(err, kErrTimeout);
       return false;
     }
-    ws_accumulate<RD, SPE>(acc, erel + b * rel_words + RD * wd, DT,
+    ws_accumulate(acc, erel + b * rel_words + RD * wd, DT,
                            elem + b * L.elem_stride + 4 * i0, elmax, ncur);
     __syncwarp();
     if (lane == 0) mbar_arrive(&elem_empty[b]);
     if constexpr (SPE == 4) {
       since += ncur;
       if (since + cc > 256 || j == nchunks - 1) {
-        ws_flush<RD>(acc, a.rowmap + g * DT + RD * wd, a.out, a.out_pitch,
-                     T0 + i0, S, nsamp_out, first_flush);
+        ws_flush(acc, a.rowmap + g * DT + RD * wd, a.out, a.out_pitch,
+                 T0 + i0, S, nsamp_out, first_flush);
         first_flush = false;
         since = 0;
       }
     }
   }
   if constexpr (SPE != 4)
-    ws_store_totals<RD, SPE>(acc, a.rowmap + g * DT + RD * wd, a.out,
-                             a.out_pitch, T0 + i0, S, nsamp_out);
+    ws_store_totals(acc, a.rowmap + g * DT + RD * wd, a.out, a.out_pitch,
+                    T0 + i0, S, nsamp_out);
   return true;
 }
 
