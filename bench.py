@@ -432,6 +432,28 @@ def run_ours(args):
     return 0
 
 
+# ------------------------------------------------ unit peaks (measurement)
+def run_peaks(args):
+    """Microbenchmarks of the on-chip units the dedispersion is bound by
+    (ddsp_probe_unit_peaks): shared-memory load bytes, 3-input adds and byte
+    permutes per SM clock, and the dedispersion inner loop on resident
+    data, with the add rates each implies (1 shared byte per add; 4 ALU
+    operations per pair of 4-sample words)."""
+    from paper_2605_03531_b300 import build, probe_unit_peaks
+    build.build()
+    r = probe_unit_peaks(0)
+    alu = min(r["iadd3_per_clk"], r["prmt_per_clk"])
+    out = {"metric": "unit peaks per SM clock", "workload": "peaks",
+           "impl": "ours", **r,
+           "adds_per_clk_bounds": {
+               "shared_memory": r["smem_bytes_per_clk"],
+               "alu": 2.0 * alu,
+               "inner_loop_resident": r["swar_adds_per_clk"],
+               "nominal_used_for_roofline": ADDS_PER_SM_CLK}}
+    print(json.dumps(out), flush=True)
+    return 0
+
+
 # ------------------------------------------------ search-only stress workload
 SPS_METRIC = "single-pulse search series samples/s"
 
@@ -1375,7 +1397,7 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["beam", "sps", "batch", "serve",
+    ap.add_argument("--workload", choices=["beam", "sps", "batch", "serve", "peaks",
                                            "cluster", "dered", "ffa",
                                            "resample", "rfi"],
                     default="beam",
@@ -1387,7 +1409,9 @@ def main():
                          "dered: running-median de-reddening of the beam's "
                          "series; ffa: folding transform + profile search; "
                          "resample: resampling for frequency derivatives; "
-                         "rfi: gptool-style RFI cleaning of a block")
+                         "rfi: gptool-style RFI cleaning of a block; peaks: "
+                         "microbenchmarks of the shared-memory and integer "
+                         "ALU rates per SM clock")
     ap.add_argument("--nbeams", type=int, default=0, help="batch: beams (0 = 160)")
     ap.add_argument("--inflight", type=int, default=1,
                     help="serve: batched steps queued on the device at once")
@@ -1426,6 +1450,8 @@ def main():
         return run_resample(args)
     if args.workload == "rfi":
         return run_rfi(args)
+    if args.workload == "peaks":
+        return run_peaks(args)
     return run_ours(args)
 
 

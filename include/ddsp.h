@@ -483,6 +483,31 @@ int ddsp_plan_get_tile(const ddsp_plan *plan, int *dm_tile,
                        int *stages, int *flags);
 
 /* ------------------------------------------------------------------------
+ * Unit peaks (measurement): microbenchmarks of the on-chip units the
+ * dedispersion is bound by, per SM and SM clock, each over one full wave of
+ * identical blocks timed by clock64 (rate = resident blocks x work per
+ * block / the median block's cycles):
+ *   smem_bytes_per_clk  conflict-free 32-bit shared-memory loads;
+ *   iadd3_per_clk       3-input integer adds (lane operations);
+ *   prmt_per_clk        byte permutes (lane operations);
+ *   swar_adds_per_clk   the dedispersion inner loop (8 DM trials x 16
+ *                       samples per thread, two channels per step) on
+ *                       channels resident in shared memory: sample adds.
+ * blocks_per_sm: the resident blocks of each probe, in that order.
+ * Allocates and frees a few MB on `device`; synchronises.  Returns
+ * DDSP_E_INVALID_ARG for a bad device or out == NULL.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+    int sms;
+    int blocks_per_sm[4];
+    double smem_bytes_per_clk;
+    double iadd3_per_clk;
+    double prmt_per_clk;
+    double swar_adds_per_clk;
+} ddsp_unit_peaks;
+int ddsp_probe_unit_peaks(int device, ddsp_unit_peaks *out);
+
+/* ------------------------------------------------------------------------
  * Peaks filtering and DM-time clustering of candidates (Sec.2.1: the
  * candidate list is thinned with square stencils of different sizes in the
  * DM-time plane, the survivors are clustered with DBSCAN in that plane, and

@@ -15,8 +15,9 @@ import numpy as np
 from . import _lib
 from ._lib import DdspError, DdspCand
 
+
 __all__ = ["Plan", "Batch", "Server", "Cluster", "Rfi", "DdspError",
-           "CAND_DTYPE", "delay_table"]
+           "CAND_DTYPE", "delay_table", "probe_unit_peaks"]
 
 CAND_DTYPE = np.dtype([("dm_idx", np.uint32), ("t", np.uint32),
                        ("w_idx", np.uint32), ("snr", np.float32)])
@@ -755,3 +756,16 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def probe_unit_peaks(device=0) -> dict:
+    """Measured per-SM rates of the units the dedispersion is bound by
+    (ddsp_probe_unit_peaks): shared-memory bytes, 3-input adds, byte
+    permutes and dedispersion-loop sample adds per SM clock."""
+    v = _lib.DdspUnitPeaks()
+    _lib.check(_lib.lib().ddsp_probe_unit_peaks(int(device), C.byref(v)),
+               "ddsp_probe_unit_peaks")
+    return {"sms": v.sms, "blocks_per_sm": list(v.blocks_per_sm),
+            "smem_bytes_per_clk": v.smem_bytes_per_clk,
+            "iadd3_per_clk": v.iadd3_per_clk, "prmt_per_clk": v.prmt_per_clk,
+            "swar_adds_per_clk": v.swar_adds_per_clk}

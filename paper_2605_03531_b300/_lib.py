@@ -25,6 +25,13 @@ class DdspCand(C.Structure):
                 ("w_idx", C.c_uint32), ("snr", C.c_float)]
 
 
+class DdspUnitPeaks(C.Structure):
+    _fields_ = [("sms", C.c_int), ("blocks_per_sm", C.c_int * 4),
+                ("smem_bytes_per_clk", C.c_double),
+                ("iadd3_per_clk", C.c_double), ("prmt_per_clk", C.c_double),
+                ("swar_adds_per_clk", C.c_double)]
+
+
 P = C.c_void_p
 I64 = C.c_int64
 I32 = C.c_int
@@ -111,6 +118,7 @@ SIGNATURES = {
     "ddsp_rfi_destroy": (None, [P]),
     "ddsp_rfi_clean": (I32, [P, P, I64, I32, I32, I32, I32, I32, P, P]),
     "ddsp_rfi_flags": (I32, [P, P, P, PI64]),
+    "ddsp_probe_unit_peaks": (I32, [I32, C.POINTER(DdspUnitPeaks)]),
 }
 
 _lib = None

@@ -1,0 +1,239 @@
+// k_probe.cu -- microbenchmarks of the two on-chip units the dedispersion
+// kernels are bound by (Sec.3.2 is integer adds of bytes read from shared
+// memory): 32-bit shared-memory load bandwidth, the integer ALU rate of the
+// two instructions the SWAR accumulation uses (3-input add, byte permute),
+// and the dedispersion inner loop itself on data resident in shared memory
+// (no staging, no synchronisation).  Each kernel runs one full wave (SMs x
+// resident blocks) of identical blocks; every block times its own loop with
+// clock64, so a rate per SM clock is occupancy x work per block / cycles.
+#include <stdint.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "host.h"
+
+namespace ddsp {
+namespace {
+
+constexpr int kProbeThreads = 512;
+constexpr int kProbeWords = 8192;   // 32 KB of shared memory
+
+// 16 conflict-free 32-bit loads per thread and iteration (consecutive lanes,
+// consecutive words), folded into 2 accumulators by 3-input XORs.
+__global__ void __launch_bounds__(kProbeThreads)
+probe_smem_kernel(int iters, uint32_t *sink, long long *cycles) {
+  __shared__ uint32_t buf[kProbeWords];
+  for (int i = threadIdx.x; i < kProbeWords; i += blockDim.x)
+    buf[i] = (uint32_t)i * 2654435761u;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t a0 = 0, a1 = 0;
+  const long long t0 = clock64();
+  for (int it = 0; it < iters; ++it) {
+    asm volatile("" ::: "memory");
+    // 16 rows of 512 words; the base (< 512 words) rotates per warp and
+    // iteration; the largest index is 511 + 512 * 12 + 1536 = 8191
+    const uint32_t *q = buf + lane + ((warp + it) & 15) * 32;
+#pragma unroll
+    for (int k = 0; k < 16; k += 4) {
+      a0 ^= q[512 * k] ^ q[512 * k + 512];
+      a1 ^= q[512 * k + 1024] ^ q[512 * k + 1536];
+    }
+  }
+  __syncthreads();
+  const long long t1 = clock64();
+  if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
+  sink[blockIdx.x * blockDim.x + threadIdx.x] = a0 ^ a1;
+}
+
+// 8 chains per thread of the instruction under test; each step also reads
+// the next chain's value, so the compiler cannot fold repeated steps.
+template <int OP>   // 0: 3-input add, 1: byte permute
+__global__ void __launch_bounds__(kProbeThreads)
+probe_alu_kernel(int iters, uint32_t seed, uint32_t *sink, long long *cycles) {
+  uint32_t a[8], b[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    a[k] = seed * (threadIdx.x + 1) + k;
+    b[k] = seed ^ (k * 0x9E3779B9u);
+  }
+  __syncthreads();
+  const long long t0 = clock64();
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        if (OP == 0) a[k] = a[k] + a[(k + 1) & 7] + b[k];
+        else a[k] = __byte_perm(a[k], a[(k + 1) & 7], 0x6351 + r);
+      }
+  }
+  __syncthreads();
+  const long long t1 = clock64();
+  if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
+  uint32_t x = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) x ^= a[k];
+  sink[blockIdx.x * blockDim.x + threadIdx.x] = x;
+}
+
+// The dedispersion consumer loop (8 DM trials x 4 elements per thread, two
+// channels per step: two 32-bit loads, two 3-input adds, two byte permutes
+// per word pair) over 8 resident channels of 1024 elements with fixed delay
+// offsets: the ceiling of the inner loop with no staging and no handoff.
+__global__ void __launch_bounds__(kProbeThreads)
+probe_swar_kernel(int iters, uint32_t *sink, long long *cycles) {
+  constexpr int RD = 8, E = 4, NQ = 8, EL = 1024;
+  __shared__ uint32_t elem[NQ * EL];   // 32 KB
+  __shared__ int rel[NQ * 16];
+  for (int i = threadIdx.x; i < NQ * EL; i += blockDim.x)
+    elem[i] = (uint32_t)i * 2654435761u;
+  for (int i = threadIdx.x; i < NQ * 16; i += blockDim.x)
+    rel[i] = 4 * ((i % 16) * 37 % 480);   // offsets below 480 elements
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int wt = warp & 3, wd = (warp >> 2) & 1;   // 4 x 2 per 8 warps
+  const unsigned char *eb =
+      reinterpret_cast<const unsigned char *>(elem) + 4 * (128 * wt + lane);
+  uint32_t A[RD][E], B[RD][E];
+#pragma unroll
+  for (int r = 0; r < RD; ++r)
+#pragma unroll
+    for (int e = 0; e < E; ++e) A[r][e] = B[r][e] = 0;
+  const long long t0 = clock64();
+  for (int it = 0; it < iters; ++it) {
+    // reload every iteration, a few bytes further along: the largest byte
+    // address in a channel is 4*479 + 4*(384+31) + 384 + 28 = 3988 < 4*EL
+    asm volatile("" ::: "memory");
+    const unsigned char *ei = eb + 4 * (it & 7);
+    for (int q = 0; q < NQ; q += 2) {
+      int ra[RD], rb[RD];
+#pragma unroll
+      for (int h = 0; h < RD; h += 4) {
+        const int4 x = *reinterpret_cast<const int4 *>(rel + q * 16 + RD * wd + h);
+        const int4 y =
+            *reinterpret_cast<const int4 *>(rel + (q + 1) * 16 + RD * wd + h);
+        ra[h] = x.x; ra[h + 1] = x.y; ra[h + 2] = x.z; ra[h + 3] = x.w;
+        rb[h] = y.x; rb[h + 1] = y.y; rb[h + 2] = y.z; rb[h + 3] = y.w;
+      }
+      const unsigned char *ea = ei + q * EL * 4, *eb2 = ea + EL * 4;
+#pragma unroll
+      for (int r = 0; r < RD; ++r)
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+          const uint32_t wa = *reinterpret_cast<const uint32_t *>(ea + ra[r] + 128 * e);
+          const uint32_t wb = *reinterpret_cast<const uint32_t *>(eb2 + rb[r] + 128 * e);
+          A[r][e] += wa + wb;
+          B[r][e] += __byte_perm(wa, 0u, 0x4341) + __byte_perm(wb, 0u, 0x4341);
+        }
+    }
+  }
+  __syncthreads();
+  const long long t1 = clock64();
+  if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
+  uint32_t x = 0;
+#pragma unroll
+  for (int r = 0; r < RD; ++r)
+#pragma unroll
+    for (int e = 0; e < E; ++e) x ^= A[r][e] ^ B[r][e];
+  sink[blockIdx.x * blockDim.x + threadIdx.x] = x;
+}
+
+// Median over the blocks of a wave: cycles of one block's loop.
+double median_cycles(const long long *d_cycles, int n) {
+  std::vector<long long> h(n);
+  cudaMemcpy(h.data(), d_cycles, n * sizeof(long long), cudaMemcpyDeviceToHost);
+  std::sort(h.begin(), h.end());
+  return (double)h[n / 2];
+}
+
+template <typename Kern, typename Launch>
+int run_probe(Kern kern, Launch launch, int sms, int *blocks_per_sm,
+              double work_per_block, uint32_t *d_sink, long long *d_cycles,
+              double *rate) {
+  int occ = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+      &occ, kern, kProbeThreads, 0);
+  if (e != cudaSuccess) return cuda_rc(e);
+  if (occ < 1) return DDSP_E_CUDA;
+  occ = std::min(occ, 8);      // the sink and cycle arrays hold 8 per SM
+  const int grid = sms * occ;
+  launch(grid, 1);            // warm-up
+  launch(grid, 0);
+  e = cudaDeviceSynchronize();
+  if (e != cudaSuccess) return cuda_rc(e);
+  *blocks_per_sm = occ;
+  *rate = occ * work_per_block / median_cycles(d_cycles, grid);
+  return DDSP_OK;
+}
+
+}  // namespace
+}  // namespace ddsp
+
+using namespace ddsp;
+
+extern "C" int ddsp_probe_unit_peaks(int device, ddsp_unit_peaks *out) {
+  if (!out) return DDSP_E_INVALID_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev)
+    return DDSP_E_INVALID_ARG;
+  DeviceGuard g(device);
+  int sms = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount,
+                                         device);
+  if (e != cudaSuccess) return cuda_rc(e);
+  *out = ddsp_unit_peaks{};
+  out->sms = sms;
+  const int maxgrid = sms * 8;
+  uint32_t *d_sink = nullptr;
+  long long *d_cycles = nullptr;
+  if ((e = cudaMalloc(&d_sink, (size_t)maxgrid * kProbeThreads * 4)) !=
+          cudaSuccess ||
+      (e = cudaMalloc(&d_cycles, (size_t)maxgrid * sizeof(long long))) !=
+          cudaSuccess) {
+    cudaFree(d_sink);
+    return cuda_rc(e);
+  }
+  const int it_smem = 4096, it_alu = 4096, it_swar = 512;
+  int rc = run_probe(
+      probe_smem_kernel,
+      [&](int grid, int warm) {
+        probe_smem_kernel<<<grid, kProbeThreads>>>(warm ? 16 : it_smem, d_sink,
+                                                   d_cycles);
+      },
+      sms, &out->blocks_per_sm[0], (double)kProbeThreads * it_smem * 16 * 4,
+      d_sink, d_cycles, &out->smem_bytes_per_clk);
+  if (rc == DDSP_OK)
+    rc = run_probe(
+        probe_alu_kernel<0>,
+        [&](int grid, int warm) {
+          probe_alu_kernel<0><<<grid, kProbeThreads>>>(warm ? 16 : it_alu, 12345u,
+                                                      d_sink, d_cycles);
+        },
+        sms, &out->blocks_per_sm[1], (double)kProbeThreads * it_alu * 32,
+        d_sink, d_cycles, &out->iadd3_per_clk);
+  if (rc == DDSP_OK)
+    rc = run_probe(
+        probe_alu_kernel<1>,
+        [&](int grid, int warm) {
+          probe_alu_kernel<1><<<grid, kProbeThreads>>>(warm ? 16 : it_alu, 12345u,
+                                                      d_sink, d_cycles);
+        },
+        sms, &out->blocks_per_sm[2], (double)kProbeThreads * it_alu * 32,
+        d_sink, d_cycles, &out->prmt_per_clk);
+  if (rc == DDSP_OK)
+    // per thread and iteration: 8 channels x 8 trials x 4 elements x 4 adds
+    rc = run_probe(
+        probe_swar_kernel,
+        [&](int grid, int warm) {
+          probe_swar_kernel<<<grid, kProbeThreads>>>(warm ? 4 : it_swar, d_sink,
+                                                     d_cycles);
+        },
+        sms, &out->blocks_per_sm[3],
+        (double)kProbeThreads * it_swar * 8 * 8 * 4 * 4, d_sink, d_cycles,
+        &out->swar_adds_per_clk);
+  cudaFree(d_sink);
+  cudaFree(d_cycles);
+  return rc;
+}
