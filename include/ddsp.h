@@ -485,8 +485,8 @@ int ddsp_plan_get_tile(const ddsp_plan *plan, int *dm_tile,
 /* ------------------------------------------------------------------------
  * Unit peaks (measurement): microbenchmarks of the on-chip units the
  * dedispersion is bound by, per SM and SM clock, each over one full wave of
- * identical blocks timed by clock64 (rate = resident blocks x work per
- * block / the median block's cycles):
+ * identical blocks timed by clock64 (an SM's rate = the work of its blocks
+ * over the span from their first start to their last end; the median SM):
  *   smem_bytes_per_clk  conflict-free 32-bit shared-memory loads;
  *   iadd3_per_clk       3-input integer adds (lane operations);
  *   prmt_per_clk        byte permutes (lane operations);

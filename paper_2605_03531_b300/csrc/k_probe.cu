@@ -3,9 +3,11 @@
 // memory): 32-bit shared-memory load bandwidth, the integer ALU rate of the
 // two instructions the SWAR accumulation uses (3-input add, byte permute),
 // and the dedispersion inner loop itself on data resident in shared memory
-// (no staging, no synchronisation).  Each kernel runs one full wave (SMs x
-// resident blocks) of identical blocks; every block times its own loop with
-// clock64, so a rate per SM clock is occupancy x work per block / cycles.
+// (no staging, no synchronisation).  Each kernel runs a wave of identical
+// blocks (SMs x resident blocks); every block records its SM and the clock64
+// values around its loop, and an SM's rate is the work of its blocks over
+// the span from their first start to their last end (clock64 is per SM),
+// whatever number of blocks actually shared the SM.
 #include <stdint.h>
 
 #include <algorithm>
@@ -18,6 +20,16 @@ namespace {
 
 constexpr int kProbeThreads = 512;
 constexpr int kProbeWords = 8192;   // 32 KB of shared memory
+
+// Block b's {SM id, loop start, loop end} (clock64 of that SM).
+__device__ __forceinline__ void record(long long *rec, long long t0,
+                                       long long t1) {
+  uint32_t smid;
+  asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+  rec[3 * blockIdx.x] = smid;
+  rec[3 * blockIdx.x + 1] = t0;
+  rec[3 * blockIdx.x + 2] = t1;
+}
 
 // 16 conflict-free 32-bit loads per thread and iteration (consecutive lanes,
 // consecutive words), folded into 2 accumulators by 3-input XORs.
@@ -43,7 +55,7 @@ probe_smem_kernel(int iters, uint32_t *sink, long long *cycles) {
   }
   __syncthreads();
   const long long t1 = clock64();
-  if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
+  if (threadIdx.x == 0) record(cycles, t0, t1);
   sink[blockIdx.x * blockDim.x + threadIdx.x] = a0 ^ a1;
 }
 
@@ -71,7 +83,7 @@ probe_alu_kernel(int iters, uint32_t seed, uint32_t *sink, long long *cycles) {
   }
   __syncthreads();
   const long long t1 = clock64();
-  if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
+  if (threadIdx.x == 0) record(cycles, t0, t1);
   uint32_t x = 0;
 #pragma unroll
   for (int k = 0; k < 8; ++k) x ^= a[k];
@@ -131,7 +143,7 @@ probe_swar_kernel(int iters, uint32_t *sink, long long *cycles) {
   }
   __syncthreads();
   const long long t1 = clock64();
-  if (threadIdx.x == 0) cycles[blockIdx.x] = t1 - t0;
+  if (threadIdx.x == 0) record(cycles, t0, t1);
   uint32_t x = 0;
 #pragma unroll
   for (int r = 0; r < RD; ++r)
@@ -140,12 +152,31 @@ probe_swar_kernel(int iters, uint32_t *sink, long long *cycles) {
   sink[blockIdx.x * blockDim.x + threadIdx.x] = x;
 }
 
-// Median over the blocks of a wave: cycles of one block's loop.
-double median_cycles(const long long *d_cycles, int n) {
-  std::vector<long long> h(n);
-  cudaMemcpy(h.data(), d_cycles, n * sizeof(long long), cudaMemcpyDeviceToHost);
-  std::sort(h.begin(), h.end());
-  return (double)h[n / 2];
+// Median over SMs of (work of the SM's blocks) / (cycles from the first
+// start to the last end among them).
+double median_sm_rate(const long long *d_rec, int n, double work_per_block) {
+  std::vector<long long> h(3 * (size_t)n);
+  cudaMemcpy(h.data(), d_rec, h.size() * sizeof(long long),
+             cudaMemcpyDeviceToHost);
+  struct Span { long long lo, hi; int blocks; };
+  std::vector<Span> sm;
+  for (int b = 0; b < n; ++b) {
+    const long long id = h[3 * b], t0 = h[3 * b + 1], t1 = h[3 * b + 2];
+    if (id < 0 || id > 4096) continue;
+    if ((size_t)id >= sm.size()) sm.resize(id + 1, Span{0, 0, 0});
+    Span &x = sm[id];
+    if (x.blocks == 0) x = Span{t0, t1, 0};
+    x.lo = std::min(x.lo, t0);
+    x.hi = std::max(x.hi, t1);
+    ++x.blocks;
+  }
+  std::vector<double> rate;
+  for (const Span &x : sm)
+    if (x.blocks > 0 && x.hi > x.lo)
+      rate.push_back(x.blocks * work_per_block / (double)(x.hi - x.lo));
+  if (rate.empty()) return 0.0;
+  std::sort(rate.begin(), rate.end());
+  return rate[rate.size() / 2];
 }
 
 template <typename Kern, typename Launch>
@@ -164,8 +195,8 @@ int run_probe(Kern kern, Launch launch, int sms, int *blocks_per_sm,
   e = cudaDeviceSynchronize();
   if (e != cudaSuccess) return cuda_rc(e);
   *blocks_per_sm = occ;
-  *rate = occ * work_per_block / median_cycles(d_cycles, grid);
-  return DDSP_OK;
+  *rate = median_sm_rate(d_cycles, grid, work_per_block);
+  return *rate > 0.0 ? DDSP_OK : DDSP_E_CUDA;
 }
 
 }  // namespace
@@ -190,7 +221,7 @@ extern "C" int ddsp_probe_unit_peaks(int device, ddsp_unit_peaks *out) {
   long long *d_cycles = nullptr;
   if ((e = cudaMalloc(&d_sink, (size_t)maxgrid * kProbeThreads * 4)) !=
           cudaSuccess ||
-      (e = cudaMalloc(&d_cycles, (size_t)maxgrid * sizeof(long long))) !=
+      (e = cudaMalloc(&d_cycles, (size_t)maxgrid * 3 * sizeof(long long))) !=
           cudaSuccess) {
     cudaFree(d_sink);
     return cuda_rc(e);
