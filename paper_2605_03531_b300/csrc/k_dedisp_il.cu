@@ -47,6 +47,8 @@ struct IlArgs {
   const int32_t *rowmap;  // [n_dm_tiles*DT] output row or -1
   int32_t *out;           // [ndm][out_pitch]
   int nchan, cc, elmax, nst;
+  uint32_t one;           // 1: the multiplier of the FMA-pipe adds (a
+                          // kernel argument, so the compiler cannot fold it)
 };
 
 // Y[c][i] for i in [0, ypitch): byte (uint8) or half (uint16) m holds
@@ -275,6 +277,7 @@ dedisp_il_kernel(IlArgs a, int32_t *err, long long timeout_cycles) {
   // ============================= consumers ==============================
   const int wt = warp % WT, wd = warp / WT;
   const int i0 = 32 * E * wt + lane;  // first element of this thread
+  const uint32_t one = a.one;
   WsAcc<RD, SPE, E> acc;
   acc.zero();
   bool first_flush = true;
@@ -289,7 +292,7 @@ dedisp_il_kernel(IlArgs a, int32_t *err, long long timeout_cycles) {
     }
     const unsigned char *sb = stages + st * L.stage_stride;
     ws_accumulate(acc, reinterpret_cast<const int32_t *>(sb) + RD * wd, DT,
-                  sb + L.rel_stride + 4 * i0, elmax, ncur);
+                  sb + L.rel_stride + 4 * i0, elmax, ncur, one);
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[st]);
     if (++st == nst) {
@@ -344,6 +347,7 @@ cudaError_t launch_il_t(const Plan &p, int64_t ypitch, int64_t nsamp_out,
   a.cc = p.tile.chan_chunk;
   a.elmax = elmax;
   a.nst = p.tile.nbuf;
+  a.one = 1u;
   dim3 grid((unsigned)p.tab.n_dm_tiles, (unsigned)ntt);
   const long long timeout = 4000000000LL;  // ~2 s of SM clock
   kern<<<grid, 32 * (WT * WD + 1), smem, s>>>(a, p.d_err, timeout);

@@ -141,7 +141,8 @@ DedispTile choose_tile(const Plan &p) {
   struct Cand { int wt, wd, rd, cc, flags; };
   constexpr int kIlWide = kTileInterleaved | kTileWide;
   const Cand prefs[] = {
-      {8, 2, 8, 16, kIlWide}, {16, 1, 8, 16, kIlWide}, {8, 2, 4, 16, kIlWide},
+      {4, 4, 4, 16, kIlWide}, {8, 2, 8, 16, kIlWide}, {16, 1, 8, 16, kIlWide},
+      {8, 2, 4, 16, kIlWide},
       {4, 2, 8, 8, kTileInterleaved}, {8, 1, 8, 8, kTileInterleaved},
       {4, 2, 4, 8, kTileInterleaved},
       {4, 2, 8, 8, kTileWarpSpecialized}, {8, 1, 8, 8, kTileWarpSpecialized},

@@ -66,6 +66,12 @@ struct WsLayout {
 // offset serves E loads, so a larger E spends fewer offset loads and
 // address adds per operand.
 
+// A 1 the compiler cannot see (a device variable the host could change):
+// x * ws_one() + y is an integer multiply-add, which runs on the FMA pipe,
+// while x + y would take the integer ALU pipe the byte permutes also use.
+static __device__ uint32_t g_ws_one = 1u;
+__device__ __forceinline__ uint32_t ws_one() { return g_ws_one; }
+
 // SWAR partials (uint8: A, B, flushed every <= 256 channels) or int32
 // totals (uint16: two 16-bit samples per element, exact in int32); E
 // elements per thread.
@@ -93,11 +99,18 @@ struct WsAcc {
 // i0), its DM trial r's byte offset is rel[q * dt + r] (rel already points
 // at this warp's first trial; 16-byte aligned).  Two channels per step
 // (3-input adds), then a lone last channel.
+//
+// uint8 per pair of words: A += wa + wb (one 3-input add on the ALU pipe),
+// B += p(wa) + p(wb) as two multiply-adds by `one` (== 1, from ws_one())
+// on the FMA pipe, and the two byte permutes on the ALU pipe: 3 ALU and 2
+// FMA operations per 8 sample adds, where all-ALU would be 4 against the
+// half-rate ALU pipe's 64 operations per SM clock.
 template <int RD, int SPE, int E>
 __device__ __forceinline__ void ws_accumulate(WsAcc<RD, SPE, E> &acc,
                                               const int32_t *rel, int dt,
                                               const unsigned char *ebase,
-                                              int elmax, int ncur) {
+                                              int elmax, int ncur,
+                                              uint32_t one) {
   auto offsets = [&](int q, int(&rr)[RD]) {
 #pragma unroll
     for (int h = 0; h < RD; h += 4) {
@@ -125,8 +138,8 @@ __device__ __forceinline__ void ws_accumulate(WsAcc<RD, SPE, E> &acc,
         const uint32_t wb = *reinterpret_cast<const uint32_t *>(pb + 128 * e);
         if constexpr (SPE == 4) {
           acc.A[r][e] += wa + wb;
-          acc.B[r][e] +=
-              __byte_perm(wa, 0u, 0x4341) + __byte_perm(wb, 0u, 0x4341);
+          acc.B[r][e] = __byte_perm(wa, 0u, 0x4341) * one + acc.B[r][e];
+          acc.B[r][e] = __byte_perm(wb, 0u, 0x4341) * one + acc.B[r][e];
         } else {
           acc.tot[r][e][0] += (int32_t)((wa & 0xFFFFu) + (wb & 0xFFFFu));
           acc.tot[r][e][1] += (int32_t)((wa >> 16) + (wb >> 16));
@@ -409,6 +422,7 @@ __device__ __forceinline__ bool ws_item(const WsBeam &a, int g, int64_t T0,
   // ============================= consumers =============================
   const int wt = warp % WT, wd = warp / WT;
   const int i0 = 32 * E * wt + lane;  // first element of this thread
+  const uint32_t one = ws_one();
   WsAcc<RD, SPE> acc;
   acc.zero();
   bool first_flush = true;
@@ -423,7 +437,7 @@ __device__ __forceinline__ bool ws_item(const WsBeam &a, int g, int64_t T0,
       return false;
     }
     ws_accumulate(acc, erel + b * rel_words + RD * wd, DT,
-                           elem + b * L.elem_stride + 4 * i0, elmax, ncur);
+                  elem + b * L.elem_stride + 4 * i0, elmax, ncur, one);
     __syncwarp();
     if (lane == 0) mbar_arrive(&elem_empty[b]);
     if constexpr (SPE == 4) {
