@@ -490,8 +490,9 @@ int ddsp_plan_get_tile(const ddsp_plan *plan, int *dm_tile,
  *   smem_bytes_per_clk  conflict-free 32-bit shared-memory loads;
  *   iadd3_per_clk       3-input integer adds (lane operations);
  *   prmt_per_clk        byte permutes (lane operations);
- *   swar_adds_per_clk   the dedispersion inner loop (8 DM trials x 16
- *                       samples per thread, two channels per step) on
+ *   swar_adds_per_clk   the dedispersion inner loop as the default tile
+ *                       runs it (4 DM trials x 32 samples per thread, two
+ *                       channels per step, B's adds on the FMA pipe) on
  *                       channels resident in shared memory: sample adds.
  * blocks_per_sm: the resident blocks of each probe, in that order.
  * Allocates and frees a few MB on `device`; synchronises.  Returns

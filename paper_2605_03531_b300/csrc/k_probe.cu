@@ -90,13 +90,15 @@ probe_alu_kernel(int iters, uint32_t seed, uint32_t *sink, long long *cycles) {
   sink[blockIdx.x * blockDim.x + threadIdx.x] = x;
 }
 
-// The dedispersion consumer loop (8 DM trials x 4 elements per thread, two
-// channels per step: two 32-bit loads, two 3-input adds, two byte permutes
-// per word pair) over 8 resident channels of 1024 elements with fixed delay
-// offsets: the ceiling of the inner loop with no staging and no handoff.
+// The dedispersion consumer loop as the default tile runs it (4 DM trials x
+// 8 elements per thread, 16 warps as 4 along time x 4 along DM, two
+// channels per step: per pair of words two 32-bit loads, one 3-input add,
+// two byte permutes and two multiply-adds by `one` on the FMA pipe) over 4
+// resident channels of 2048 elements with fixed delay offsets: the ceiling
+// of the inner loop with no staging and no handoff.
 __global__ void __launch_bounds__(kProbeThreads)
-probe_swar_kernel(int iters, uint32_t *sink, long long *cycles) {
-  constexpr int RD = 8, E = 4, NQ = 8, EL = 1024;
+probe_swar_kernel(int iters, uint32_t one, uint32_t *sink, long long *cycles) {
+  constexpr int RD = 4, E = 8, NQ = 4, EL = 2048;
   __shared__ uint32_t elem[NQ * EL];   // 32 KB
   __shared__ int rel[NQ * 16];
   for (int i = threadIdx.x; i < NQ * EL; i += blockDim.x)
@@ -105,9 +107,9 @@ probe_swar_kernel(int iters, uint32_t *sink, long long *cycles) {
     rel[i] = 4 * ((i % 16) * 37 % 480);   // offsets below 480 elements
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int wt = warp & 3, wd = (warp >> 2) & 1;   // 4 x 2 per 8 warps
+  const int wt = warp & 3, wd = warp >> 2;   // 4 x 4 warps
   const unsigned char *eb =
-      reinterpret_cast<const unsigned char *>(elem) + 4 * (128 * wt + lane);
+      reinterpret_cast<const unsigned char *>(elem) + 4 * (256 * wt + lane);
   uint32_t A[RD][E], B[RD][E];
 #pragma unroll
   for (int r = 0; r < RD; ++r)
@@ -116,19 +118,15 @@ probe_swar_kernel(int iters, uint32_t *sink, long long *cycles) {
   const long long t0 = clock64();
   for (int it = 0; it < iters; ++it) {
     // reload every iteration, a few bytes further along: the largest byte
-    // address in a channel is 4*479 + 4*(384+31) + 384 + 28 = 3988 < 4*EL
+    // address in a channel is 4*479 + 4*(768+31) + 128*7 + 28 = 6036 < 4*EL
     asm volatile("" ::: "memory");
     const unsigned char *ei = eb + 4 * (it & 7);
     for (int q = 0; q < NQ; q += 2) {
       int ra[RD], rb[RD];
-#pragma unroll
-      for (int h = 0; h < RD; h += 4) {
-        const int4 x = *reinterpret_cast<const int4 *>(rel + q * 16 + RD * wd + h);
-        const int4 y =
-            *reinterpret_cast<const int4 *>(rel + (q + 1) * 16 + RD * wd + h);
-        ra[h] = x.x; ra[h + 1] = x.y; ra[h + 2] = x.z; ra[h + 3] = x.w;
-        rb[h] = y.x; rb[h + 1] = y.y; rb[h + 2] = y.z; rb[h + 3] = y.w;
-      }
+      const int4 x = *reinterpret_cast<const int4 *>(rel + q * 16 + RD * wd);
+      const int4 y = *reinterpret_cast<const int4 *>(rel + (q + 1) * 16 + RD * wd);
+      ra[0] = x.x; ra[1] = x.y; ra[2] = x.z; ra[3] = x.w;
+      rb[0] = y.x; rb[1] = y.y; rb[2] = y.z; rb[3] = y.w;
       const unsigned char *ea = ei + q * EL * 4, *eb2 = ea + EL * 4;
 #pragma unroll
       for (int r = 0; r < RD; ++r)
@@ -137,7 +135,8 @@ probe_swar_kernel(int iters, uint32_t *sink, long long *cycles) {
           const uint32_t wa = *reinterpret_cast<const uint32_t *>(ea + ra[r] + 128 * e);
           const uint32_t wb = *reinterpret_cast<const uint32_t *>(eb2 + rb[r] + 128 * e);
           A[r][e] += wa + wb;
-          B[r][e] += __byte_perm(wa, 0u, 0x4341) + __byte_perm(wb, 0u, 0x4341);
+          B[r][e] = __byte_perm(wa, 0u, 0x4341) * one + B[r][e];
+          B[r][e] = __byte_perm(wb, 0u, 0x4341) * one + B[r][e];
         }
     }
   }
@@ -254,15 +253,15 @@ extern "C" int ddsp_probe_unit_peaks(int device, ddsp_unit_peaks *out) {
         sms, &out->blocks_per_sm[2], (double)kProbeThreads * it_alu * 32,
         d_sink, d_cycles, &out->prmt_per_clk);
   if (rc == DDSP_OK)
-    // per thread and iteration: 8 channels x 8 trials x 4 elements x 4 adds
+    // per thread and iteration: 4 channels x 4 trials x 8 elements x 4 adds
     rc = run_probe(
         probe_swar_kernel,
         [&](int grid, int warm) {
-          probe_swar_kernel<<<grid, kProbeThreads>>>(warm ? 4 : it_swar, d_sink,
-                                                     d_cycles);
+          probe_swar_kernel<<<grid, kProbeThreads>>>(warm ? 4 : it_swar, 1u,
+                                                     d_sink, d_cycles);
         },
         sms, &out->blocks_per_sm[3],
-        (double)kProbeThreads * it_swar * 8 * 8 * 4 * 4, d_sink, d_cycles,
+        (double)kProbeThreads * it_swar * 4 * 4 * 8 * 4, d_sink, d_cycles,
         &out->swar_adds_per_clk);
   cudaFree(d_sink);
   cudaFree(d_cycles);
