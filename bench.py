@@ -1151,12 +1151,13 @@ def run_rfi(args):
 def run_batch(args):
     """160 beams of uneven shape (1024/2048/4096 channels in a 2:1:1 mix,
     65536-262144-sample blocks, DM ranges 0-100/0-250/0-500 with 256-2048
-    trials, 0-5 injected pulses each).  One step = one persistent
-    dedispersion launch over all beams + one batched search launch,
-    replayed from a CUDA graph, with the tile chosen by the autotuner; the
+    trials, 0-5 injected pulses each).  One step = the dedispersion of all
+    beams (persistent relayout launches over a work queue, or beam after
+    beam through the interleaved kernel: the autotuner picks the mode and
+    the tile) + one batched search launch, replayed from a CUDA graph; the
     rows are ingested (unpacked) once beforehand, as a ring buffer holds
     them.  Beside it: the plain path, each beam's dedispersion and search as
-    separate launches with the same kernel shape as the batch."""
+    separate launches with the persistent mode's relayout tile."""
     import ctypes as C
     import torch
     from paper_2605_03531_b300 import Batch, Plan, _lib, build, shard, synth
@@ -1229,15 +1230,19 @@ def run_batch(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_batch,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "int32", "data": "synthetic",
-            "config": {"workload": f"{len(cfgs)} uneven beams in one persistent "
-                                   "launch (CUDA graph, autotuned tile): 1024/2048/"
+            "config": {"workload": f"{len(cfgs)} uneven beams in one batched step "
+                                   "(CUDA graph, autotuned mode and tile): 1024/2048/"
                                    "4096 ch, 65536-262144 samples, DM 0-100/250/500 "
                                    "x 256-2048 trials", "beams": len(cfgs),
                        "adds_per_step": adds,
                        "l2": "inputs larger than L2"},
+            "mode": "per_beam" if batch.get_mode() == Batch.PER_BEAM
+                    else "persistent",
             "plain_per_beam": {"value": world * adds / (ms_plain * 1e-3),
                                "ms_per_step": ms_plain,
-                               "launches_per_step": 2 * len(cfgs)},
+                               "launches_per_step": 2 * len(cfgs),
+                               "kernel": "relayout tile of the persistent "
+                                         "mode, per beam"},
             "batched_over_plain": ms_plain / ms_batch,
             "tile": tile, "autotune_ms": tune_ms, "autotune_best": best,
             "candidates_per_step": int(ncand), "gpu_launches": 3 * args.steps}),

@@ -337,13 +337,35 @@ int ddsp_batch_get_beam_tile(const ddsp_batch *batch, int beam, int *dm_tile,
 /* Autotuner: for each tile shape of the library's candidate list, time the
  * persistent dedispersion of every 16th work item of the cost-ordered work
  * list (the same share of each beam's work; best of `reps` runs after one
- * warm-up, on the current input buffers) and keep the fastest.  ms_out[i]
- * (up to cap entries, may be NULL) receives candidate i's time scaled to
- * the full work list, or -1 if the shape does not fit; *ntried the number
- * of candidates, *best the chosen index.  The sampled runs overwrite parts
- * of the output series. */
+ * warm-up, on the current input buffers) and keep the fastest; then time
+ * one whole pass of the per-beam interleaved mode (DDSP_BATCH_PER_BEAM,
+ * when every beam fits an interleaved shape) and take it if it is
+ * faster.  ms_out[i] (up to cap entries, may be NULL) receives candidate
+ * i's time scaled to the full work list, or -1 if the shape does not fit;
+ * the last candidate is the per-beam mode; *ntried the number of
+ * candidates, *best the chosen index.  The runs overwrite the output
+ * series. */
 int ddsp_batch_autotune(ddsp_batch *batch, int reps, ddsp_stream_t stream,
                         float *ms_out, int cap, int *ntried, int *best);
+
+/* Execution mode of ddsp_batch_run.  DDSP_BATCH_PERSISTENT: persistent
+ * launches of the warp-specialised relayout kernel over a device work
+ * queue of every beam's (DM tile, time tile) items (the tile from
+ * ddsp_batch_set_tile or the autotuner).  DDSP_BATCH_PER_BEAM: beam after
+ * beam, its channel-major rows interleaved into one staging area the
+ * batch owns (4 bytes per sample of the largest beam; allocated on the
+ * first switch) and dedispersed by the interleaved kernel (per beam the
+ * first of the 16-trial wide, 16-trial, 8-trial and 4-trial interleaved
+ * shapes whose staging fits: coarse DM grids take the narrower ones), then
+ * the same batched search.  set_mode returns DDSP_E_INVALID_ARG for an
+ * unknown mode or if some beam fits none of those shapes, DDSP_E_NOMEM if
+ * the staging area cannot be allocated;
+ * ddsp_batch_set_tile switches back to DDSP_BATCH_PERSISTENT.  Both modes
+ * compute the same exact sums. */
+#define DDSP_BATCH_PERSISTENT 0
+#define DDSP_BATCH_PER_BEAM 1
+int ddsp_batch_set_mode(ddsp_batch *batch, int mode);
+int ddsp_batch_get_mode(const ddsp_batch *batch, int *mode);
 
 /* ---- Streaming server (the real-time ring-buffer design of Sec.2.1 and
  * Ch.3: every beam delivers blocks of B new spectra, each block is

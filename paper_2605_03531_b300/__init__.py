@@ -609,6 +609,22 @@ class Batch:
                    "ddsp_batch_get_beam_chunk")
         return v.value
 
+    PERSISTENT = 0
+    PER_BEAM = 1
+
+    def set_mode(self, mode):
+        """Batch.PERSISTENT (persistent relayout kernel over a work queue)
+        or Batch.PER_BEAM (beam after beam through the interleaved kernel,
+        one shared staging area); see ddsp_batch_set_mode."""
+        _lib.check(_lib.lib().ddsp_batch_set_mode(self._h, int(mode)),
+                   "ddsp_batch_set_mode")
+
+    def get_mode(self) -> int:
+        v = C.c_int()
+        _lib.check(_lib.lib().ddsp_batch_get_mode(self._h, C.byref(v)),
+                   "ddsp_batch_get_mode")
+        return v.value
+
     def beam_tile(self, beam):
         """dict(dm_tile, dm_per_thread, time_tile, chan_chunk, group) of the
         shape beam `beam` is dedispersed with (group 1: the second
@@ -621,8 +637,10 @@ class Batch:
 
     def autotune(self, reps=2, stream=None):
         """Time every candidate tile on a 1/16 sample of the work items,
-        keep the fastest; returns (list of estimated full-launch ms per
-        candidate (-1 = does not fit), chosen index)."""
+        keep the fastest, then one whole pass of the per-beam interleaved
+        mode (the last candidate), taken if faster; returns (list of
+        estimated full-launch ms per candidate (-1 = does not fit or not
+        available), chosen index)."""
         cap = 64
         ms = (C.c_float * cap)()
         nt, best = C.c_int(), C.c_int()

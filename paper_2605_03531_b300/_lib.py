@@ -119,6 +119,8 @@ SIGNATURES = {
     "ddsp_rfi_clean": (I32, [P, P, I64, I32, I32, I32, I32, I32, P, P]),
     "ddsp_rfi_flags": (I32, [P, P, P, PI64]),
     "ddsp_probe_unit_peaks": (I32, [I32, C.POINTER(DdspUnitPeaks)]),
+    "ddsp_batch_set_mode": (I32, [P, I32]),
+    "ddsp_batch_get_mode": (I32, [P, C.POINTER(C.c_int)]),
 }
 
 _lib = None

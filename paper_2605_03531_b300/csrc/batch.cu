@@ -1,8 +1,11 @@
 // batch.cu -- many beams (plans) of uneven shape dedispersed by persistent
 // launches (one per tile group: the main shape, and a narrower-DM shape for
 // beams whose delay spans make the main one stage little and relayout a lot)
-// and searched by one batched launch, optionally replayed from a captured
-// CUDA graph; tile autotuner.
+// or, in the per-beam mode, beam after beam by the interleaved kernel
+// (each beam's rows interleaved into one shared staging area first: the
+// interleaved rows of all beams at once would not fit in HBM), and
+// searched by one batched launch, optionally replayed from a captured CUDA
+// graph; tile and mode autotuner.
 #include <math.h>
 
 #include <algorithm>
@@ -61,6 +64,12 @@ struct ddsp_batch {
   bool graph_ok = false;
   float graph_thr = 0.0f;
   bool ran_direct = false;
+  // per-beam interleaved mode (DDSP_BATCH_PER_BEAM)
+  int mode = DDSP_BATCH_PERSISTENT;
+  std::vector<DedispTile> il_tile;   // per beam: its plan's default tile
+  std::vector<DedispTables> il_tabs; // per beam, for il_tile
+  void *d_il = nullptr;              // shared staging rows (largest beam)
+  size_t il_bytes = 0;
 };
 
 namespace {
@@ -77,6 +86,8 @@ void batch_release(ddsp_batch &B) {
   batch_free_graph(B);
   if (B.cap_stream) cudaStreamDestroy(B.cap_stream);
   for (auto &t : B.tabs) free_tables(t);
+  for (auto &t : B.il_tabs) free_tables(t);
+  cudaFree(B.d_il);
   for (auto p : B.own_out) cudaFree(p);
   cudaFree(B.d_cm);
   for (auto &g : B.groups) {
@@ -339,9 +350,95 @@ const DedispTile kBatchTiles[] = {
 constexpr int kNumBatchTiles = sizeof(kBatchTiles) / sizeof(kBatchTiles[0]);
 constexpr size_t kAutotuneStride = 16;
 
+// The interleaved tile a beam runs with in the per-beam mode: the first of
+// these shapes (16-trial wide, 16-trial, 8-trial, 4-trial: narrower DM
+// tiles for coarse DM grids, whose delay spans inside a tile are long)
+// whose time tile the pool's pitch allows and whose two element stages
+// fit with the largest chunk (<= 16 channels); wt == 0 if none fits.
+DedispTile il_tile_for(const ddsp_batch &B, int b) {
+  const int wide = kTileInterleaved | kTileWide;
+  const DedispTile cands[] = {{4, 4, 4, 16, 2, wide}, {8, 2, 8, 16, 2, wide},
+                              {4, 2, 8, 8, 2, kTileInterleaved},
+                              {8, 1, 8, 8, 2, kTileInterleaved},
+                              {8, 1, 4, 8, 2, kTileInterleaved}};
+  for (DedispTile t : cands) {
+    if (!dedisp_tile_supported(t, 8) ||
+        dedisp_time_tile(t, 8) > kBatchMaxTimeTile)
+      continue;
+    const int span = beam_span(B, b, t.dm_tile());
+    for (int cc = t.chan_chunk; cc >= 1; --cc) {
+      t.chan_chunk = cc;
+      if (dedisp_smem_bytes(t, span, 8) <= kSmemBudgetOneBlock) return t;
+    }
+  }
+  return DedispTile{};
+}
+
+// Per-beam interleaved mode: every beam needs an interleaved tile
+// (il_tile_for); one staging area, sized for the largest beam, serves the
+// beams in turn (stream order).  Builds the tables once.
+int batch_setup_il(ddsp_batch &B) {
+  if (!B.il_tabs.empty()) return DDSP_OK;
+  std::vector<DedispTile> tiles(B.nbeams);
+  size_t bytes = 0;
+  for (int b = 0; b < B.nbeams; ++b) {
+    const Plan &p = B.plans[b]->p;
+    const DedispTile t = il_tile_for(B, b);
+    if (t.wt == 0) return DDSP_E_INVALID_ARG;
+    tiles[b] = t;
+    bytes = std::max(bytes, (size_t)p.nchan * B.pitch[b] * 4);
+  }
+  std::vector<DedispTables> tabs(B.nbeams);
+  int rc = DDSP_OK;
+  for (int b = 0; b < B.nbeams && rc == DDSP_OK; ++b)
+    rc = build_tables_for(B.plans[b]->p, tiles[b], tabs[b]);
+  void *d_il = nullptr;
+  if (rc == DDSP_OK) {
+    cudaError_t e = cudaMalloc(&d_il, bytes);
+    if (e != cudaSuccess) rc = cuda_rc(e);
+  }
+  if (rc != DDSP_OK) {
+    for (auto &t : tabs) free_tables(t);
+    return rc;
+  }
+  B.il_tile.swap(tiles);
+  B.il_tabs.swap(tabs);
+  B.d_il = d_il;
+  B.il_bytes = bytes;
+  return DDSP_OK;
+}
+
+// Every beam's interleave + dedispersion, in turn, into its series.
+cudaError_t batch_dedisperse_per_beam(ddsp_batch &B, cudaStream_t s) {
+  cudaError_t e = cudaSuccess;
+  for (int b = 0; b < B.nbeams && e == cudaSuccess; ++b) {
+    const Plan &p = B.plans[b]->p;
+    IlLaunch v;
+    v.tile = B.il_tile[b];
+    v.tab = &B.il_tabs[b];
+    v.nchan = p.nchan;
+    v.nbits = 8;
+    v.d_err = B.d_err;
+    v.d_il = B.d_il;
+    // the pool's rows hold the block, zeros past it (ingest) or whatever
+    // the caller wrote; samples past N_in reach no stored output
+    e = launch_interleave(v, B.d_cm + B.cm_off[b], B.pitch[b], B.nin[b],
+                          B.pitch[b], s);
+    if (e == cudaSuccess)
+      e = launch_dedisperse_il(v, B.pitch[b], B.nout[b], B.d_out[b], s);
+  }
+  return e;
+}
+
 int batch_enqueue(ddsp_batch &B, float thr, cudaStream_t s) {
   cudaError_t e = launch_batch_reset(B.d_queue, kMaxGroups, B.d_counts,
                                      B.nbeams, s);
+  if (B.mode == DDSP_BATCH_PER_BEAM) {
+    if (e == cudaSuccess) e = batch_dedisperse_per_beam(B, s);
+    if (e == cudaSuccess)
+      e = launch_sps_batch(B.d_sb, B.nbeams, B.sps_blocks, thr, B.sps_smem, s);
+    return cuda_rc(e);
+  }
   for (size_t gi = 0; gi < B.groups.size() && e == cudaSuccess; ++gi) {
     const BatchGroup &G = B.groups[gi];
     e = launch_dedisperse_persistent(G.tile, G.d_wsb, G.d_items, G.nitems, 0,
@@ -506,7 +603,12 @@ int ddsp_batch_set_tile(ddsp_batch *B, int dm_tile, int dm_per_thread,
   t.chan_chunk = chan_chunk;
   t.nbuf = stages;
   t.flags = kTileWarpSpecialized;
-  return batch_apply_tile(*B, t);
+  const int rc = batch_apply_tile(*B, t);
+  if (rc == DDSP_OK && B->mode != DDSP_BATCH_PERSISTENT) {
+    B->mode = DDSP_BATCH_PERSISTENT;   // a tile is a persistent-mode choice
+    B->ran_direct = false;
+  }
+  return rc;
 }
 
 int ddsp_batch_get_beam_chunk(const ddsp_batch *B, int beam, int *chan_chunk) {
@@ -656,13 +758,61 @@ int ddsp_batch_autotune(ddsp_batch *B, int reps, ddsp_stream_t stream,
     ++tried;
   }
   cudaFree(d_sample);
+  int rc = besti < 0 ? DDSP_E_INVALID_ARG
+                     : batch_apply_tile(*B, kBatchTiles[besti]);
+  B->mode = DDSP_BATCH_PERSISTENT;
+  // the per-beam interleaved mode: one whole dedispersion pass per rep
+  float ms_il = -1.0f;
+  if (rc == DDSP_OK && batch_setup_il(*B) == DDSP_OK) {
+    float best_rep = 1e30f;
+    cudaError_t e = cudaSuccess;
+    for (int r = 0; r <= reps && e == cudaSuccess; ++r) {
+      cudaEventRecord(e0, s);
+      e = batch_dedisperse_per_beam(*B, s);
+      cudaEventRecord(e1, s);
+      cudaEventSynchronize(e1);
+      float t = 0;
+      cudaEventElapsedTime(&t, e0, e1);
+      if (r > 0) best_rep = std::min(best_rep, t);  // first run warms up
+    }
+    if (e == cudaSuccess) ms_il = best_rep;
+    if (ms_il > 0 && ms_il < bestms) {
+      B->mode = DDSP_BATCH_PER_BEAM;
+      besti = kNumBatchTiles;
+    }
+  }
+  if (ms_out && kNumBatchTiles < cap) ms_out[kNumBatchTiles] = ms_il;
+  ++tried;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (ntried) *ntried = tried;
   if (best) *best = besti;
-  if (besti < 0) return DDSP_E_INVALID_ARG;
   B->ran_direct = false;
-  return batch_apply_tile(*B, kBatchTiles[besti]);
+  batch_free_graph(*B);
+  return rc;
+}
+
+int ddsp_batch_set_mode(ddsp_batch *B, int mode) {
+  if (!B || (mode != DDSP_BATCH_PERSISTENT && mode != DDSP_BATCH_PER_BEAM))
+    return DDSP_E_INVALID_ARG;
+  DeviceGuard g(B->device);
+  if (mode == DDSP_BATCH_PER_BEAM) {
+    cudaDeviceSynchronize();
+    const int rc = batch_setup_il(*B);
+    if (rc != DDSP_OK) return rc;
+  }
+  if (mode != B->mode) {
+    batch_free_graph(*B);
+    B->ran_direct = false;
+    B->mode = mode;
+  }
+  return DDSP_OK;
+}
+
+int ddsp_batch_get_mode(const ddsp_batch *B, int *mode) {
+  if (!B || !mode) return DDSP_E_INVALID_ARG;
+  *mode = B->mode;
+  return DDSP_OK;
 }
 
 int ddsp_batch_get_beam_tile(const ddsp_batch *B, int beam, int *dm_tile,

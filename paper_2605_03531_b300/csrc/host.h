@@ -33,6 +33,8 @@ int64_t round_up(int64_t v, int64_t m);
 // 16-sample-aligned window start.
 int span_for(const Plan &p, int dt);
 int build_tables_for(const Plan &p, const DedispTile &tile, DedispTables &tab);
+// The library's default tile for plan p (the plan's own choice).
+DedispTile choose_tile(const Plan &p);
 void free_tables(DedispTables &t);
 int ensure_stats(Plan &p, size_t n);
 // Normalisation windows of an n-sample series; DDSP_E_SHAPE if one window

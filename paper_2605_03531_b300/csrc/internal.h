@@ -141,6 +141,25 @@ cudaError_t launch_dedisperse_ws(const Plan &p, const void *d_cm,
                                  int32_t *d_out, cudaStream_t s, int rawmax,
                                  int elmax, size_t smem);
 
+// What the interleaved kernels need of a plan, so that a batch can run
+// them on its own tables and staging rows.
+struct IlLaunch {
+  DedispTile tile;
+  const DedispTables *tab = nullptr;
+  int nchan = 0, nbits = 8;
+  int32_t *d_err = nullptr;
+  void *d_il = nullptr;         // interleaved rows [nchan][ypitch] uint32
+};
+IlLaunch il_launch_of(const Plan &p);
+cudaError_t launch_interleave(const IlLaunch &v, const void *d_cm,
+                              int64_t pitch, int64_t nvalid, int64_t ypitch,
+                              cudaStream_t s);
+cudaError_t launch_dedisperse_il(const IlLaunch &v, int64_t ypitch,
+                                 int64_t nsamp_out, int32_t *d_out,
+                                 cudaStream_t s);
+cudaError_t launch_dedisperse_il(const IlLaunch &v, int64_t ypitch,
+                                 int64_t nsamp_out, int32_t *d_out,
+                                 cudaStream_t s, int elmax, size_t smem);
 size_t dedisp_il_smem_bytes(int chan_chunk, int dm_tile, int elmax, int nst);
 int dedisp_il_max_stages();
 cudaError_t launch_interleave(const Plan &p, const void *d_cm, int64_t pitch,

@@ -315,7 +315,7 @@ dedisp_il_kernel(IlArgs a, int32_t *err, long long timeout_cycles) {
 }
 
 template <int WT, int WD, int RD, int E, typename T>
-cudaError_t launch_il_t(const Plan &p, int64_t ypitch, int64_t nsamp_out,
+cudaError_t launch_il_t(const IlLaunch &p, int64_t ypitch, int64_t nsamp_out,
                         int32_t *d_out, cudaStream_t s, int elmax,
                         size_t smem) {
   auto kern = dedisp_il_kernel<WT, WD, RD, E, T>;
@@ -339,16 +339,16 @@ cudaError_t launch_il_t(const Plan &p, int64_t ypitch, int64_t nsamp_out,
   a.ypitch = ypitch;
   a.nsamp_out = nsamp_out;
   a.out_pitch = nsamp_out;
-  a.desc = reinterpret_cast<const int2 *>(p.tab.d_desc);
-  a.relb = p.tab.d_relb;
-  a.rowmap = p.tab.d_rowmap;
+  a.desc = reinterpret_cast<const int2 *>(p.tab->d_desc);
+  a.relb = p.tab->d_relb;
+  a.rowmap = p.tab->d_rowmap;
   a.out = d_out;
   a.nchan = p.nchan;
   a.cc = p.tile.chan_chunk;
   a.elmax = elmax;
   a.nst = p.tile.nbuf;
   a.one = 1u;
-  dim3 grid((unsigned)p.tab.n_dm_tiles, (unsigned)ntt);
+  dim3 grid((unsigned)p.tab->n_dm_tiles, (unsigned)ntt);
   const long long timeout = 4000000000LL;  // ~2 s of SM clock
   kern<<<grid, 32 * (WT * WD + 1), smem, s>>>(a, p.d_err, timeout);
   return cudaGetLastError();
@@ -363,8 +363,25 @@ size_t dedisp_il_smem_bytes(int chan_chunk, int dm_tile, int elmax,
 
 int dedisp_il_max_stages() { return kIlMaxStages; }
 
+IlLaunch il_launch_of(const Plan &p) {
+  IlLaunch v;
+  v.tile = p.tile;
+  v.tab = &p.tab;
+  v.nchan = p.nchan;
+  v.nbits = p.nbits;
+  v.d_err = p.d_err;
+  v.d_il = p.d_il;
+  return v;
+}
+
 cudaError_t launch_interleave(const Plan &p, const void *d_cm, int64_t pitch,
                               int64_t nvalid, int64_t ypitch, cudaStream_t s) {
+  return launch_interleave(il_launch_of(p), d_cm, pitch, nvalid, ypitch, s);
+}
+
+cudaError_t launch_interleave(const IlLaunch &p, const void *d_cm,
+                              int64_t pitch, int64_t nvalid, int64_t ypitch,
+                              cudaStream_t s) {
   const int S = dedisp_segment(p.tile);
   const dim3 grid((unsigned)((ypitch / 4 + 255) / 256), (unsigned)p.nchan);
   uint32_t *y = static_cast<uint32_t *>(p.d_il);
@@ -394,6 +411,23 @@ cudaError_t launch_unpack_interleave(const Plan &p, const void *d_in,
 }
 
 cudaError_t launch_dedisperse_il(const Plan &p, int64_t ypitch,
+                                 int64_t nsamp_out, int32_t *d_out,
+                                 cudaStream_t s, int elmax, size_t smem) {
+  return launch_dedisperse_il(il_launch_of(p), ypitch, nsamp_out, d_out, s,
+                              elmax, smem);
+}
+
+cudaError_t launch_dedisperse_il(const IlLaunch &p, int64_t ypitch,
+                                 int64_t nsamp_out, int32_t *d_out,
+                                 cudaStream_t s) {
+  int rawmax, elmax;
+  dedisp_buffer_sizes(p.tile, p.tab->span_max, p.nbits, &rawmax, &elmax);
+  return launch_dedisperse_il(p, ypitch, nsamp_out, d_out, s, elmax,
+                              dedisp_smem_bytes(p.tile, p.tab->span_max,
+                                                p.nbits));
+}
+
+cudaError_t launch_dedisperse_il(const IlLaunch &p, int64_t ypitch,
                                  int64_t nsamp_out, int32_t *d_out,
                                  cudaStream_t s, int elmax, size_t smem) {
   const int wt = p.tile.wt, wd = p.tile.wd, rd = p.tile.rd;

@@ -1,6 +1,7 @@
 """Batched multi-beam search: one persistent dedispersion launch over uneven
-beams (replayed from a CUDA graph, with an autotuned tile) gives every beam
-exactly what its plan gives alone, and matches the oracle."""
+beams (replayed from a CUDA graph, with an autotuned tile), or the per-beam
+interleaved mode, gives every beam exactly what its plan gives alone, and
+matches the oracle."""
 import numpy as np
 import pytest
 import torch
@@ -197,3 +198,52 @@ def test_batch_autotune_with_two_groups_keeps_results():
     batch.check()
     for b in range(len(cfgs)):
         assert torch.equal(batch.series[b], ref[b]), b
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_batch_per_beam_mode_equals_plain(use_graph):
+    """The per-beam interleaved mode (each beam's rows interleaved into the
+    batch's one staging area, then its plan's default tile) reproduces every
+    beam's series and candidates; set_tile returns to the persistent mode,
+    which still agrees."""
+    cfgs = small_mix(8, seed=17)
+    plans = [_plan(c) for c in cfgs]
+    blocks = [_block(c, p) for c, p in zip(cfgs, plans)]
+    ref_series, ref_cands = [], []
+    for c, p, x in zip(cfgs, plans, blocks):
+        s = p.dedisperse(x)
+        p.single_pulse_search(s, c.threshold)
+        ref_series.append(s.clone())
+        ref_cands.append(p.fetch()[0])
+    batch = Batch(plans, [x.shape[0] for x in blocks])
+    for b, x in enumerate(blocks):
+        batch.ingest(b, x)
+    assert batch.get_mode() == Batch.PERSISTENT
+    batch.set_mode(Batch.PER_BEAM)
+    assert batch.get_mode() == Batch.PER_BEAM
+    for rep in range(3):
+        for s_ in batch.series:
+            s_.fill_(-1)
+        batch.run(7.0, use_graph=use_graph)
+        batch.check()
+        for b in range(len(cfgs)):
+            assert torch.equal(batch.series[b], ref_series[b]), (rep, b)
+            _same_candidates(plans[b].fetch()[0], ref_cands[b])
+    batch.set_tile(16, 8, 8, 2)
+    assert batch.get_mode() == Batch.PERSISTENT
+    for s_ in batch.series:
+        s_.fill_(-1)
+    batch.run(7.0, use_graph=use_graph)
+    batch.check()
+    for b in range(len(cfgs)):
+        assert torch.equal(batch.series[b], ref_series[b]), b
+
+
+def test_batch_mode_refused_for_unknown_value():
+    cfgs = small_mix(2, seed=19)
+    plans = [_plan(c) for c in cfgs]
+    batch = Batch(plans, [c.nsamp_out + p.max_delay for c, p in zip(cfgs, plans)])
+    from paper_2605_03531_b300 import DdspError
+    with pytest.raises(DdspError):
+        batch.set_mode(7)
+    assert batch.get_mode() == Batch.PERSISTENT
