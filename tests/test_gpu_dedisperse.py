@@ -282,3 +282,21 @@ def test_interleaved_cm_path_matches_oracle():
     out = p.dedisperse_cm(cm, pitch, nout)
     torch.cuda.synchronize()
     assert np.array_equal(out.cpu().numpy(), ref)
+
+
+def test_wide_flag_needs_the_interleaved_tile():
+    """DDSP_TILE_WIDE (16 consumer warps) exists only for the interleaved
+    kernel: alone or with the relayout kernel it is refused; with it the
+    time tile doubles for the same DM tile."""
+    p = _plan(256, 750.0, -200.0 / 256, 1.31072e-3, np.arange(64.0))
+    for flags in (32, 32 | 8, 32 | 1):
+        with pytest.raises(DdspError) as e:
+            p.set_tile(16, 8, 4, 2, flags)
+        assert e.value.code == ddsp_lib.DDSP_E_INVALID_ARG
+    p.set_tile(16, 8, 4, 2, 16)
+    narrow = p.get_tile()["time_tile"]
+    p.set_tile(16, 8, 4, 2, 48)
+    t = p.get_tile()
+    assert t["flags"] == 48 and t["time_tile"] == 2 * narrow
+    p.set_tile(16, 4, 4, 2, 48)           # 4 trials x 8 elements per thread
+    assert p.get_tile()["time_tile"] == 2 * narrow
