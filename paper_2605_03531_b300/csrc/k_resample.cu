@@ -136,7 +136,16 @@ __global__ void resample_kernel(const int32_t *__restrict__ in, int64_t nrows,
       const float f = e - fl, fe = f + 1.0f + dev;
       const int64_t base = ib + lane + (int64_t)fl;
       float acc = 0.0f;
-      for (int d = 0; (float)d < fe && base + d < n; ++d) {
+      // the first two overlap terms unrolled (their loads issue together),
+      // then bins wider than two samples; same order of terms as a loop
+#pragma unroll
+      for (int d = 0; d < 2; ++d) {
+        const float lo = fmaxf(f, (float)d), hi = fminf(fe, (float)(d + 1));
+        const int64_t i = base + d;
+        if (hi > lo && i >= 0 && i < n)
+          acc += (float)x[rev ? n - 1 - i : i] * (hi - lo);
+      }
+      for (int d = 2; (float)d < fe && base + d < n; ++d) {
         const float lo = fmaxf(f, (float)d), hi = fminf(fe, (float)(d + 1));
         const int64_t i = base + d;
         if (hi > lo && i >= 0) acc += (float)x[rev ? n - 1 - i : i] * (hi - lo);
