@@ -1290,13 +1290,23 @@ def run_serve(args):
     stager = DeviceStager(16, (B, cfg.nchan), compute)
     reserve = 4 << 30
 
-    # tile: the fastest full step of 32 beams among the server's shapes
+    # dedispersion: the fastest full step of 32 beams among the server's
+    # relayout shapes and its interleaved mode (8 staging slots)
     tiles = [(16, 8, 8, 2), (8, 8, 4, 2), (16, 8, 4, 2), (8, 8, 6, 2),
-             (16, 8, 4, 4), (8, 4, 4, 2), (16, 4, 6, 2), (8, 4, 8, 2)]
+             (16, 8, 4, 4), (8, 4, 4, 2), (16, 4, 6, 2), (8, 4, 8, 2),
+             ("interleaved", 8)]
+
+    def make_server(t, n):
+        if t[0] == "interleaved":
+            srv = Server(plan, B, n, reserve)
+            srv.set_mode(Server.INTERLEAVED, t[1])
+            return srv
+        return Server(plan, B, n, reserve, tile=t)
+
     tune = {}
     for t in tiles:
         try:
-            srv = Server(plan, B, 32, reserve, tile=t)
+            srv = make_server(t, 32)
         except Exception:
             continue
         bs = [srv.admit() for _ in range(32)]
@@ -1321,7 +1331,7 @@ def run_serve(args):
 
     def run_at(n, per_step, inflight):
         try:
-            srv = Server(plan, B, n, reserve, tile=tile)
+            srv = make_server(tile, n)
         except Exception:
             return float("inf")
         beams = []
@@ -1387,9 +1397,14 @@ def run_serve(args):
                        "steps_in_flight": {"batched": args.inflight,
                                            "plain_per_beam": args.plain_inflight},
                        "adds_per_block": adds_block,
-                       "tile": dict(zip(("dm_tile", "dm_per_thread", "chan_chunk",
-                                         "stages"), tile)),
-                       "tile_step_ms_32_beams": {str(k): v for k, v in tune.items()}},
+                       "dedispersion": ({"mode": "interleaved",
+                                         "staging_slots": tile[1]}
+                                        if tile[0] == "interleaved" else
+                                        {"mode": "relayout",
+                                         **dict(zip(("dm_tile", "dm_per_thread",
+                                                     "chan_chunk", "stages"),
+                                                    tile))}),
+                       "step_ms_32_beams": {str(k): v for k, v in tune.items()}},
             "batched": table(0),
             "plain_per_beam": {"value": n_plain * world, "runs": table(1)},
             "clocks": clocks}), flush=True)

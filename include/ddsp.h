@@ -463,6 +463,25 @@ int ddsp_server_series(ddsp_server *server, int beam, int32_t **d_series,
  * the server's steps, then clear it. */
 int ddsp_server_check(ddsp_server *server, ddsp_stream_t stream);
 
+/* Dedispersion mode of the server's steps.  DDSP_SERVER_RELAYOUT (the
+ * default): one persistent launch of the warp-specialised relayout kernel
+ * over every waiting beam-block's work items, staging straight from the
+ * rings.  DDSP_SERVER_INTERLEAVED: each waiting beam-block's window of its
+ * ring is interleaved into one of `staging_slots` (1..16) staging slots
+ * the server allocates (4 * nchan * (B + D16 + 64, rounded up to 128)
+ * bytes each; set the mode before admitting beams, so admission sees the
+ * memory), and each group of slots is dedispersed by one launch of the
+ * interleaved kernel; the search is the same.  Synchronises the device.
+ * DDSP_E_INVALID_ARG for an unknown mode, a slot count outside 1..16 or a
+ * shape no interleaved tile fits (the time tile must divide the block);
+ * DDSP_E_NOMEM if the slots cannot be allocated.  Both modes compute the
+ * same exact sums. */
+#define DDSP_SERVER_RELAYOUT 0
+#define DDSP_SERVER_INTERLEAVED 1
+int ddsp_server_set_mode(ddsp_server *server, int mode, int staging_slots);
+int ddsp_server_get_mode(const ddsp_server *server, int *mode,
+                         int *staging_slots);
+
 /* Name and text of the last CUDA error this library saw on the calling
  * host thread (empty if none); the storage is the library's. */
 const char *ddsp_last_error_detail(void);

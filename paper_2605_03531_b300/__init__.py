@@ -684,6 +684,26 @@ class Server:
         (self.beam_bytes, self.ring_samples, self.series_cols, self.carry,
          self.first_delay) = (a.value for a in v)
 
+    RELAYOUT = 0
+    INTERLEAVED = 1
+
+    def set_mode(self, mode, staging_slots=8):
+        """Server.RELAYOUT (persistent relayout kernel on the rings) or
+        Server.INTERLEAVED (beam-blocks interleaved into staging_slots
+        slots, one interleaved launch per group); see ddsp_server_set_mode.
+        Set it before admitting beams."""
+        _lib.check(_lib.lib().ddsp_server_set_mode(self._h, int(mode),
+                                                   int(staging_slots)),
+                   "ddsp_server_set_mode")
+
+    def get_mode(self):
+        """(mode, staging slots)."""
+        m, k = C.c_int(), C.c_int()
+        _lib.check(_lib.lib().ddsp_server_get_mode(self._h, C.byref(m),
+                                                   C.byref(k)),
+                   "ddsp_server_get_mode")
+        return m.value, k.value
+
     def get_tile(self):
         v = [C.c_int() for _ in range(6)]
         _lib.check(_lib.lib().ddsp_server_get_tile(self._h, *[C.byref(a) for a in v]),

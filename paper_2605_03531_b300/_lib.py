@@ -121,6 +121,8 @@ SIGNATURES = {
     "ddsp_probe_unit_peaks": (I32, [I32, C.POINTER(DdspUnitPeaks)]),
     "ddsp_batch_set_mode": (I32, [P, I32]),
     "ddsp_batch_get_mode": (I32, [P, C.POINTER(C.c_int)]),
+    "ddsp_server_set_mode": (I32, [P, I32, I32]),
+    "ddsp_server_get_mode": (I32, [P, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
 }
 
 _lib = None

@@ -141,6 +141,14 @@ cudaError_t launch_dedisperse_ws(const Plan &p, const void *d_cm,
                                  int32_t *d_out, cudaStream_t s, int rawmax,
                                  int elmax, size_t smem);
 
+// One of several same-shape row sets an interleaved launch can take
+// (blockIdx.z): its interleaved rows and its output.
+struct IlRows {
+  const uint32_t *y;
+  int32_t *out;
+};
+constexpr int kIlMaxRows = 16;
+
 // What the interleaved kernels need of a plan, so that a batch can run
 // them on its own tables and staging rows.
 struct IlLaunch {
@@ -151,9 +159,19 @@ struct IlLaunch {
   void *d_il = nullptr;         // interleaved rows [nchan][ypitch] uint32
 };
 IlLaunch il_launch_of(const Plan &p);
+// Rows of d_cm to interleaved rows y (v.d_il if null).  ring > 0: the rows
+// are rings of `ring` samples and logical sample b sits at (t0 + b) % ring
+// (t0 and ring multiples of 4).
 cudaError_t launch_interleave(const IlLaunch &v, const void *d_cm,
                               int64_t pitch, int64_t nvalid, int64_t ypitch,
-                              cudaStream_t s);
+                              cudaStream_t s, int64_t ring = 0, int64_t t0 = 0,
+                              void *y = nullptr);
+// nrows (<= kIlMaxRows) same-shape row sets in one launch (blockIdx.z),
+// outputs with row pitch out_pitch.
+cudaError_t launch_dedisperse_il_rows(const IlLaunch &v, int64_t ypitch,
+                                      int64_t nsamp_out, int64_t out_pitch,
+                                      const IlRows *rows, int nrows,
+                                      cudaStream_t s);
 cudaError_t launch_dedisperse_il(const IlLaunch &v, int64_t ypitch,
                                  int64_t nsamp_out, int32_t *d_out,
                                  cudaStream_t s);

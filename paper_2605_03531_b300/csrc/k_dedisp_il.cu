@@ -49,21 +49,28 @@ struct IlArgs {
   int nchan, cc, elmax, nst;
   uint32_t one;           // 1: the multiplier of the FMA-pipe adds (a
                           // kernel argument, so the compiler cannot fold it)
+  int nz;                 // > 0: blockIdx.z picks rows and output from z[]
+  IlRows z[kIlMaxRows];   // (same tables, same shape: e.g. beam-blocks)
 };
 
 // Y[c][i] for i in [0, ypitch): byte (uint8) or half (uint16) m holds
 // x[c][i + m S] if that index is below nvalid, else 0.  One thread builds 4
 // consecutive elements from SPE aligned loads (a 4x4 byte transpose for
 // uint8) and stores them as one 16-byte word.
+// With ring > 0 the rows are rings: logical sample b sits at (t0 + b) %
+// ring; t0, ring, S and i are multiples of 4, so a 4-sample group never
+// straddles the wrap.
 template <typename T>
 __global__ void __launch_bounds__(256)
 interleave_kernel(const T *__restrict__ cm, int64_t pitch, int64_t nvalid,
-                  int S, uint32_t *__restrict__ y, int64_t ypitch) {
+                  int S, uint32_t *__restrict__ y, int64_t ypitch,
+                  int64_t ring, int64_t t0) {
   constexpr int SPE = 4 / sizeof(T);
   const int c = blockIdx.y;
   const int64_t i = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
   if (i >= ypitch) return;
   const T *x = cm + (int64_t)c * pitch;
+  auto at = [&](int64_t b) { return ring > 0 ? (t0 + b) % ring : b; };
   uint4 o;
   if constexpr (SPE == 4) {
     uint32_t w[4];
@@ -71,12 +78,12 @@ interleave_kernel(const T *__restrict__ cm, int64_t pitch, int64_t nvalid,
     for (int m = 0; m < 4; ++m) {
       const int64_t b = i + (int64_t)m * S;
       if (b + 4 <= nvalid) {
-        w[m] = __ldg(reinterpret_cast<const uint32_t *>(x + b));
+        w[m] = __ldg(reinterpret_cast<const uint32_t *>(x + at(b)));
       } else {
         uint32_t v = 0;
 #pragma unroll
         for (int k = 0; k < 4; ++k)
-          if (b + k < nvalid) v |= (uint32_t)x[b + k] << (8 * k);
+          if (b + k < nvalid) v |= (uint32_t)x[at(b + k)] << (8 * k);
         w[m] = v;
       }
     }
@@ -87,14 +94,14 @@ interleave_kernel(const T *__restrict__ cm, int64_t pitch, int64_t nvalid,
     for (int m = 0; m < 2; ++m) {
       const int64_t b = i + (int64_t)m * S;
       if (b + 4 <= nvalid) {
-        const uint2 v = __ldg(reinterpret_cast<const uint2 *>(x + b));
+        const uint2 v = __ldg(reinterpret_cast<const uint2 *>(x + at(b)));
         h[m][0] = v.x & 0xFFFFu;
         h[m][1] = v.x >> 16;
         h[m][2] = v.y & 0xFFFFu;
         h[m][3] = v.y >> 16;
       } else {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) h[m][k] = b + k < nvalid ? x[b + k] : 0u;
+        for (int k = 0; k < 4; ++k) h[m][k] = b + k < nvalid ? x[at(b + k)] : 0u;
       }
     }
     o.x = h[0][0] | (h[1][0] << 16);
@@ -195,6 +202,8 @@ dedisp_il_kernel(IlArgs a, int32_t *err, long long timeout_cycles) {
   const int64_t T0 = (int64_t)blockIdx.y * TT;
   const int nchunks = (nchan + cc - 1) / cc;
   unsigned char *stages = smem + kIlBarBytes;
+  const uint32_t *yrows = a.nz > 0 ? a.z[blockIdx.z].y : a.y;
+  int32_t *out = a.nz > 0 ? a.z[blockIdx.z].out : a.out;
 
   if (tid == 0) {
     for (int s = 0; s < nst; ++s) {
@@ -252,7 +261,7 @@ dedisp_il_kernel(IlArgs a, int32_t *err, long long timeout_cycles) {
       __syncwarp();
       if (v)
         bulk_g2s(sb + L.rel_stride + lane * elmax * 4,
-                 a.y + (int64_t)(c0 + lane) * a.ypitch + T0 + d.x, nb,
+                 yrows + (int64_t)(c0 + lane) * a.ypitch + T0 + d.x, nb,
                  &full[st]);
       if (lane == 0)
         bulk_g2s(sb, rel_g + (int64_t)c0 * DT, relbytes, &full[st]);
@@ -302,7 +311,7 @@ dedisp_il_kernel(IlArgs a, int32_t *err, long long timeout_cycles) {
     if constexpr (SPE == 4) {
       since += ncur;
       if (since + cc > 256 || j == nchunks - 1) {
-        ws_flush(acc, a.rowmap + g * DT + RD * wd, a.out, a.out_pitch,
+        ws_flush(acc, a.rowmap + g * DT + RD * wd, out, a.out_pitch,
                  T0 + i0, S, a.nsamp_out, first_flush);
         first_flush = false;
         since = 0;
@@ -310,14 +319,15 @@ dedisp_il_kernel(IlArgs a, int32_t *err, long long timeout_cycles) {
     }
   }
   if constexpr (SPE != 4)
-    ws_store_totals(acc, a.rowmap + g * DT + RD * wd, a.out, a.out_pitch,
+    ws_store_totals(acc, a.rowmap + g * DT + RD * wd, out, a.out_pitch,
                     T0 + i0, S, a.nsamp_out);
 }
 
 template <int WT, int WD, int RD, int E, typename T>
 cudaError_t launch_il_t(const IlLaunch &p, int64_t ypitch, int64_t nsamp_out,
                         int32_t *d_out, cudaStream_t s, int elmax,
-                        size_t smem) {
+                        size_t smem, int64_t out_pitch, const IlRows *rows,
+                        int nrows) {
   auto kern = dedisp_il_kernel<WT, WD, RD, E, T>;
   static size_t attr_bytes = 0;
   if (smem > attr_bytes) {
@@ -338,7 +348,7 @@ cudaError_t launch_il_t(const IlLaunch &p, int64_t ypitch, int64_t nsamp_out,
   a.y = static_cast<const uint32_t *>(p.d_il);
   a.ypitch = ypitch;
   a.nsamp_out = nsamp_out;
-  a.out_pitch = nsamp_out;
+  a.out_pitch = out_pitch > 0 ? out_pitch : nsamp_out;
   a.desc = reinterpret_cast<const int2 *>(p.tab->d_desc);
   a.relb = p.tab->d_relb;
   a.rowmap = p.tab->d_rowmap;
@@ -348,7 +358,10 @@ cudaError_t launch_il_t(const IlLaunch &p, int64_t ypitch, int64_t nsamp_out,
   a.elmax = elmax;
   a.nst = p.tile.nbuf;
   a.one = 1u;
-  dim3 grid((unsigned)p.tab->n_dm_tiles, (unsigned)ntt);
+  a.nz = rows ? nrows : 0;
+  for (int i = 0; i < a.nz; ++i) a.z[i] = rows[i];
+  dim3 grid((unsigned)p.tab->n_dm_tiles, (unsigned)ntt,
+            (unsigned)(a.nz > 0 ? a.nz : 1));
   const long long timeout = 4000000000LL;  // ~2 s of SM clock
   kern<<<grid, 32 * (WT * WD + 1), smem, s>>>(a, p.d_err, timeout);
   return cudaGetLastError();
@@ -381,16 +394,19 @@ cudaError_t launch_interleave(const Plan &p, const void *d_cm, int64_t pitch,
 
 cudaError_t launch_interleave(const IlLaunch &p, const void *d_cm,
                               int64_t pitch, int64_t nvalid, int64_t ypitch,
-                              cudaStream_t s) {
+                              cudaStream_t s, int64_t ring, int64_t t0,
+                              void *ydst) {
   const int S = dedisp_segment(p.tile);
   const dim3 grid((unsigned)((ypitch / 4 + 255) / 256), (unsigned)p.nchan);
-  uint32_t *y = static_cast<uint32_t *>(p.d_il);
+  uint32_t *y = static_cast<uint32_t *>(ydst ? ydst : p.d_il);
   if (p.nbits == 8)
     interleave_kernel<uint8_t><<<grid, 256, 0, s>>>(
-        static_cast<const uint8_t *>(d_cm), pitch, nvalid, S, y, ypitch);
+        static_cast<const uint8_t *>(d_cm), pitch, nvalid, S, y, ypitch, ring,
+        t0);
   else
     interleave_kernel<uint16_t><<<grid, 256, 0, s>>>(
-        static_cast<const uint16_t *>(d_cm), pitch, nvalid, S, y, ypitch);
+        static_cast<const uint16_t *>(d_cm), pitch, nvalid, S, y, ypitch, ring,
+        t0);
   return cudaGetLastError();
 }
 
@@ -427,15 +443,47 @@ cudaError_t launch_dedisperse_il(const IlLaunch &p, int64_t ypitch,
                                                 p.nbits));
 }
 
+namespace {
+cudaError_t launch_il_dispatch(const IlLaunch &p, int64_t ypitch,
+                               int64_t nsamp_out, int32_t *d_out,
+                               cudaStream_t s, int elmax, size_t smem,
+                               int64_t out_pitch, const IlRows *rows,
+                               int nrows);
+}  // namespace
+
+cudaError_t launch_dedisperse_il_rows(const IlLaunch &p, int64_t ypitch,
+                                      int64_t nsamp_out, int64_t out_pitch,
+                                      const IlRows *rows, int nrows,
+                                      cudaStream_t s) {
+  if (!rows || nrows < 1 || nrows > kIlMaxRows) return cudaErrorInvalidValue;
+  int rawmax, elmax;
+  dedisp_buffer_sizes(p.tile, p.tab->span_max, p.nbits, &rawmax, &elmax);
+  return launch_il_dispatch(
+      p, ypitch, nsamp_out, nullptr, s, elmax,
+      dedisp_smem_bytes(p.tile, p.tab->span_max, p.nbits), out_pitch, rows,
+      nrows);
+}
+
 cudaError_t launch_dedisperse_il(const IlLaunch &p, int64_t ypitch,
                                  int64_t nsamp_out, int32_t *d_out,
                                  cudaStream_t s, int elmax, size_t smem) {
+  return launch_il_dispatch(p, ypitch, nsamp_out, d_out, s, elmax, smem, 0,
+                            nullptr, 0);
+}
+
+namespace {
+cudaError_t launch_il_dispatch(const IlLaunch &p, int64_t ypitch,
+                               int64_t nsamp_out, int32_t *d_out,
+                               cudaStream_t s, int elmax, size_t smem,
+                               int64_t out_pitch, const IlRows *rows,
+                               int nrows) {
   const int wt = p.tile.wt, wd = p.tile.wd, rd = p.tile.rd;
   const int ept = dedisp_elems_per_thread(p.tile);
 #define DDSP_IL(WT_, WD_, RD_, E_, T_)                                      \
   if (wt == WT_ && wd == WD_ && rd == RD_ && ept == E_)                     \
     return launch_il_t<WT_, WD_, RD_, E_, T_>(p, ypitch, nsamp_out, d_out,  \
-                                              s, elmax, smem);
+                                              s, elmax, smem, out_pitch,    \
+                                              rows, nrows);
   if (p.nbits == 8) {
     DDSP_IL(8, 2, 8, 4, uint8_t)     // wide: 16 consumer warps, E = 32 / RD
     DDSP_IL(16, 1, 8, 4, uint8_t)
@@ -460,5 +508,6 @@ cudaError_t launch_dedisperse_il(const IlLaunch &p, int64_t ypitch,
 #undef DDSP_IL
   return cudaErrorInvalidValue;
 }
+}  // namespace
 
 }  // namespace ddsp

@@ -74,6 +74,16 @@ struct ddsp_server {
   cudaEvent_t ev_step[kStepEvents] = {};
   int64_t nsteps = 0;
   int64_t npushes = 0;
+  // interleaved mode: waiting beam-blocks are interleaved from their rings
+  // into `il_slots` staging slots and dedispersed by one interleaved launch
+  // per group of slots
+  int mode = DDSP_SERVER_RELAYOUT;
+  DedispTile il_tile;
+  DedispTables il_tab;
+  int il_slots = 0;
+  int64_t ypitch = 0;
+  size_t slot_bytes = 0;
+  uint8_t *d_il = nullptr;
 };
 
 namespace {
@@ -104,6 +114,8 @@ void server_release(ddsp_server &S) {
   for (auto &b : S.beams)
     if (b.live) free_beam(b);
   free_tables(S.tab);
+  free_tables(S.il_tab);
+  cudaFree(S.d_il);
   cudaFree(S.d_counts);
   cudaFree(S.d_err);
   cudaFree(S.d_queue);
@@ -175,9 +187,112 @@ int server_apply_tile(ddsp_server &S, const DedispTile &t) {
   return DDSP_OK;
 }
 
+// The interleaved tile of the interleaved mode: the first of these shapes
+// whose time tile divides the block and whose two element stages fit.
+DedispTile server_il_tile(const ddsp_server &S) {
+  const Plan &p = S.plan->p;
+  const int wide = kTileInterleaved | kTileWide;
+  const DedispTile cands[] = {{4, 4, 4, 16, 2, wide}, {8, 2, 8, 16, 2, wide},
+                              {4, 2, 8, 8, 2, kTileInterleaved},
+                              {8, 1, 8, 8, 2, kTileInterleaved},
+                              {8, 1, 4, 8, 2, kTileInterleaved}};
+  for (DedispTile t : cands) {
+    if (!dedisp_tile_supported(t, 8) || S.B % dedisp_time_tile(t, 8)) continue;
+    const int span = span_for(p, t.dm_tile());
+    for (int cc = t.chan_chunk; cc >= 1; --cc) {
+      t.chan_chunk = cc;
+      if (dedisp_smem_bytes(t, span, 8) <= kSmemBudgetOneBlock) return t;
+    }
+  }
+  return DedispTile{};
+}
+
+// The interleaved mode's dedispersion of n waiting beam-blocks, groups of
+// il_slots at a time: each block's window of its ring (logical samples
+// [0, B + D16) from ring position t0) is interleaved into a slot, then one
+// launch covers the group (blockIdx.z = slot).  Stream order keeps a slot's
+// next interleave behind the launch that read it.
+cudaError_t server_dedisperse_il(ddsp_server &S, const std::vector<int> &beams,
+                                 const std::vector<int64_t> &t0,
+                                 cudaStream_t s) {
+  const Plan &p = S.plan->p;
+  IlLaunch v;
+  v.tile = S.il_tile;
+  v.tab = &S.il_tab;
+  v.nchan = p.nchan;
+  v.nbits = 8;
+  v.d_err = S.d_err;
+  cudaError_t e = cudaSuccess;
+  const int n = (int)beams.size();
+  for (int g0 = 0; g0 < n && e == cudaSuccess; g0 += S.il_slots) {
+    const int gn = std::min(S.il_slots, n - g0);
+    IlRows rows[kIlMaxRows];
+    for (int q = 0; q < gn && e == cudaSuccess; ++q) {
+      const ServerBeam &b = S.beams[beams[g0 + q]];
+      uint8_t *slot = S.d_il + (size_t)q * S.slot_bytes;
+      e = launch_interleave(v, b.ring, S.pitch, S.B + S.D16, S.ypitch, s, S.R,
+                            t0[g0 + q], slot);
+      rows[q].y = reinterpret_cast<const uint32_t *>(slot);
+      rows[q].out = b.series + S.C;
+    }
+    if (e == cudaSuccess)
+      e = launch_dedisperse_il_rows(v, S.ypitch, S.B, S.ncols, rows, gn, s);
+  }
+  return e;
+}
+
 }  // namespace
 
 extern "C" {
+
+int ddsp_server_set_mode(ddsp_server *S, int mode, int staging_slots) {
+  if (!S || (mode != DDSP_SERVER_RELAYOUT && mode != DDSP_SERVER_INTERLEAVED))
+    return DDSP_E_INVALID_ARG;
+  if (mode == DDSP_SERVER_INTERLEAVED &&
+      (staging_slots < 1 || staging_slots > kIlMaxRows))
+    return DDSP_E_INVALID_ARG;
+  DeviceGuard g(S->device);
+  cudaDeviceSynchronize();   // no step may still read the staging slots
+  if (mode == DDSP_SERVER_RELAYOUT) {
+    free_tables(S->il_tab);
+    cudaFree(S->d_il);
+    S->d_il = nullptr;
+    S->il_slots = 0;
+    S->mode = mode;
+    return DDSP_OK;
+  }
+  const DedispTile t = server_il_tile(*S);
+  if (t.wt == 0) return DDSP_E_INVALID_ARG;
+  const Plan &p = S->plan->p;
+  const int64_t ypitch = round_up(S->B + S->D16 + 64, 128);
+  const size_t slot_bytes = (size_t)p.nchan * ypitch * 4;
+  DedispTables tab;
+  int rc = build_tables_for(p, t, tab);
+  if (rc != DDSP_OK) return rc;
+  uint8_t *d_il = nullptr;
+  cudaError_t e = cudaMalloc(&d_il, slot_bytes * staging_slots);
+  if (e != cudaSuccess) {
+    free_tables(tab);
+    return cuda_rc(e);
+  }
+  free_tables(S->il_tab);
+  cudaFree(S->d_il);
+  S->il_tab = tab;
+  S->il_tile = t;
+  S->d_il = d_il;
+  S->ypitch = ypitch;
+  S->slot_bytes = slot_bytes;
+  S->il_slots = staging_slots;
+  S->mode = mode;
+  return DDSP_OK;
+}
+
+int ddsp_server_get_mode(const ddsp_server *S, int *mode, int *staging_slots) {
+  if (!S) return DDSP_E_INVALID_ARG;
+  if (mode) *mode = S->mode;
+  if (staging_slots) *staging_slots = S->il_slots;
+  return DDSP_OK;
+}
 
 int ddsp_server_create(ddsp_server **out, ddsp_plan *plan,
                        int64_t block_samples, int max_beams,
@@ -402,6 +517,7 @@ int ddsp_server_step(ddsp_server *S, float threshold, int max_beams_in_step,
   if (max_beams_in_step > 0 && (int)ready.size() > max_beams_in_step)
     ready.resize(max_beams_in_step);
   int n = 0;
+  std::vector<int64_t> t0s;
   for (int i : ready) {
     ServerBeam &b = S->beams[i];
     const int64_t j = b.processed;
@@ -414,6 +530,7 @@ int ddsp_server_step(ddsp_server *S, float threshold, int max_beams_in_step,
     w.nsamp_out = S->B;
     w.ring = S->R;
     w.t0 = floor_mod(j * S->B - S->D16, S->R);
+    t0s.push_back(w.t0);
     w.out_pitch = S->ncols;
     w.desc = reinterpret_cast<const int2 *>(S->tab.d_desc);
     w.relb = S->tab.d_relb;
@@ -459,10 +576,14 @@ int ddsp_server_step(ddsp_server *S, float threshold, int max_beams_in_step,
                           S->d_queue, s);
   const int64_t nitems = (int64_t)n * S->ipb;
   if (e == cudaSuccess && nitems > 0x7fffffff) e = cudaErrorInvalidValue;
-  if (e == cudaSuccess)
+  if (e == cudaSuccess && S->mode == DDSP_SERVER_INTERLEAVED) {
+    std::vector<int> bl(ready.begin(), ready.begin() + n);
+    e = server_dedisperse_il(*S, bl, t0s, s);
+  } else if (e == cudaSuccess) {
     e = launch_dedisperse_persistent(
         S->tile, S->d_wsb[par], nullptr, (int)nitems, S->ipb, S->tab.n_dm_tiles,
         S->d_queue, S->smem, S->d_err, (int)std::min<int64_t>(S->grid, nitems), s);
+  }
   if (e == cudaSuccess)
     e = launch_sps_batch(S->d_sb[par], n, (int64_t)n * p.ndm * S->nwin,
                          threshold, S->sps_smem, s);

@@ -73,9 +73,15 @@ def test_server_shape():
     srv.close()
 
 
-def test_server_blocks_equal_plain_path_in_any_mix():
+@pytest.mark.parametrize("mode", ["relayout", "interleaved"])
+def test_server_blocks_equal_plain_path_in_any_mix(mode):
+    """Both dedispersion modes; the interleaved one with 2 staging slots,
+    so a step of three beam-blocks takes two groups."""
     plan, ref_plan = _plan(), _plan()
     srv = Server(plan, B, 4)
+    if mode == "interleaved":
+        srv.set_mode(Server.INTERLEAVED, 2)
+        assert srv.get_mode() == (Server.INTERLEAVED, 2)
     beams = [srv.admit() for _ in range(3)]
     xs = [_stream(100 + i) for i in range(3)]
     refs = [[_reference(ref_plan, srv, xs[i], j) for j in range(NBLK)]
@@ -243,4 +249,16 @@ def test_serving_loop_on_the_server():
             _, c_ref = _reference(ref_plan, srv, xs[i], k)
             _same(got[(i, k)][0], c_ref)
     srv.check(compute)
+    srv.close()
+
+
+def test_server_mode_arguments():
+    srv = Server(_plan(), B, 2)
+    for mode, slots in ((2, 4), (1, 0), (1, 17)):
+        with pytest.raises(DdspError):
+            srv.set_mode(mode, slots)
+    assert srv.get_mode() == (Server.RELAYOUT, 0)
+    srv.set_mode(Server.INTERLEAVED, 3)
+    srv.set_mode(Server.RELAYOUT)
+    assert srv.get_mode()[0] == Server.RELAYOUT
     srv.close()
