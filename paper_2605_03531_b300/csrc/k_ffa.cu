@@ -29,7 +29,7 @@
 namespace ddsp {
 namespace {
 
-constexpr int kFfaThreads = 512;
+constexpr int kFfaThreads = 1024;
 constexpr int kFfaMaxStack = 16384;        // m * p per block (shared memory)
 constexpr int kFfaMaxWidths = 16;
 
