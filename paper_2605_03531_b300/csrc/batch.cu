@@ -350,28 +350,12 @@ const DedispTile kBatchTiles[] = {
 constexpr int kNumBatchTiles = sizeof(kBatchTiles) / sizeof(kBatchTiles[0]);
 constexpr size_t kAutotuneStride = 16;
 
-// The interleaved tile a beam runs with in the per-beam mode: the first of
-// these shapes (16-trial wide, 16-trial, 8-trial, 4-trial: narrower DM
-// tiles for coarse DM grids, whose delay spans inside a tile are long)
-// whose time tile the pool's pitch allows and whose two element stages
-// fit with the largest chunk (<= 16 channels); wt == 0 if none fits.
+// The interleaved tile a beam runs with in the per-beam mode, within the
+// time tiles the pool's pitch allows.
 DedispTile il_tile_for(const ddsp_batch &B, int b) {
-  const int wide = kTileInterleaved | kTileWide;
-  const DedispTile cands[] = {{4, 4, 4, 16, 2, wide}, {8, 2, 8, 16, 2, wide},
-                              {4, 2, 8, 8, 2, kTileInterleaved},
-                              {8, 1, 8, 8, 2, kTileInterleaved},
-                              {8, 1, 4, 8, 2, kTileInterleaved}};
-  for (DedispTile t : cands) {
-    if (!dedisp_tile_supported(t, 8) ||
-        dedisp_time_tile(t, 8) > kBatchMaxTimeTile)
-      continue;
-    const int span = beam_span(B, b, t.dm_tile());
-    for (int cc = t.chan_chunk; cc >= 1; --cc) {
-      t.chan_chunk = cc;
-      if (dedisp_smem_bytes(t, span, 8) <= kSmemBudgetOneBlock) return t;
-    }
-  }
-  return DedispTile{};
+  return fit_interleaved_tile(
+      [](int tt) { return tt <= kBatchMaxTimeTile; },
+      [&](int dt) { return beam_span(B, b, dt); });
 }
 
 // Per-beam interleaved mode: every beam needs an interleaved tile

@@ -35,6 +35,32 @@ int span_for(const Plan &p, int dt);
 int build_tables_for(const Plan &p, const DedispTile &tile, DedispTables &tab);
 // The library's default tile for plan p (the plan's own choice).
 DedispTile choose_tile(const Plan &p);
+
+// The interleaved shape a multi-beam mode (batch per beam, server) runs a
+// beam with: the first of the 16-trial wide tiles, then the 16-, 8- and
+// 4-trial tiles of 8 consumer warps (narrower DM tiles for coarse DM
+// grids, whose delay spans inside a tile are long) whose time tile passes
+// time_ok and whose two element stages fit one block per SM with the
+// largest chunk (<= 16 or 8 channels); span(dt) is the beam's delay span
+// inside a DM tile of dt trials.  wt == 0 if none fits.
+template <typename TimeOk, typename Span>
+DedispTile fit_interleaved_tile(TimeOk time_ok, Span span) {
+  const int wide = kTileInterleaved | kTileWide;
+  const DedispTile cands[] = {{4, 4, 4, 16, 2, wide}, {8, 2, 8, 16, 2, wide},
+                              {4, 2, 8, 8, 2, kTileInterleaved},
+                              {8, 1, 8, 8, 2, kTileInterleaved},
+                              {8, 1, 4, 8, 2, kTileInterleaved}};
+  for (DedispTile t : cands) {
+    if (!dedisp_tile_supported(t, 8) || !time_ok(dedisp_time_tile(t, 8)))
+      continue;
+    const int sp = span(t.dm_tile());
+    for (int cc = t.chan_chunk; cc >= 1; --cc) {
+      t.chan_chunk = cc;
+      if (dedisp_smem_bytes(t, sp, 8) <= kSmemBudgetOneBlock) return t;
+    }
+  }
+  return DedispTile{};
+}
 void free_tables(DedispTables &t);
 int ensure_stats(Plan &p, size_t n);
 // Normalisation windows of an n-sample series; DDSP_E_SHAPE if one window

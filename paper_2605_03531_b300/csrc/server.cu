@@ -187,24 +187,12 @@ int server_apply_tile(ddsp_server &S, const DedispTile &t) {
   return DDSP_OK;
 }
 
-// The interleaved tile of the interleaved mode: the first of these shapes
-// whose time tile divides the block and whose two element stages fit.
+// The interleaved tile of the interleaved mode: its time tile divides the
+// block.
 DedispTile server_il_tile(const ddsp_server &S) {
   const Plan &p = S.plan->p;
-  const int wide = kTileInterleaved | kTileWide;
-  const DedispTile cands[] = {{4, 4, 4, 16, 2, wide}, {8, 2, 8, 16, 2, wide},
-                              {4, 2, 8, 8, 2, kTileInterleaved},
-                              {8, 1, 8, 8, 2, kTileInterleaved},
-                              {8, 1, 4, 8, 2, kTileInterleaved}};
-  for (DedispTile t : cands) {
-    if (!dedisp_tile_supported(t, 8) || S.B % dedisp_time_tile(t, 8)) continue;
-    const int span = span_for(p, t.dm_tile());
-    for (int cc = t.chan_chunk; cc >= 1; --cc) {
-      t.chan_chunk = cc;
-      if (dedisp_smem_bytes(t, span, 8) <= kSmemBudgetOneBlock) return t;
-    }
-  }
-  return DedispTile{};
+  return fit_interleaved_tile([&](int tt) { return S.B % tt == 0; },
+                              [&](int dt) { return span_for(p, dt); });
 }
 
 // The interleaved mode's dedispersion of n waiting beam-blocks, groups of
