@@ -277,11 +277,13 @@ def test_interleaved_cm_path_matches_oracle():
     x = np.random.default_rng(9).integers(0, 256, size=(nin, cfg_nchan)).astype(np.uint8)
     ref = oracle.dedisperse(x, p.delays())
     nout = ref.shape[1]
-    pitch = p.cm_pitch(nout)
-    cm = p.unpack(to_dev(x), pitch)
-    out = p.dedisperse_cm(cm, pitch, nout)
-    torch.cuda.synchronize()
-    assert np.array_equal(out.cpu().numpy(), ref)
+    # the plan's smallest pitch, and a wider caller pitch (the interleave
+    # reads with the caller's pitch and writes the plan's rows)
+    for pitch in (p.cm_pitch(nout), p.cm_pitch(nout) + 384):
+        cm = p.unpack(to_dev(x), pitch)
+        out = p.dedisperse_cm(cm, pitch, nout)
+        torch.cuda.synchronize()
+        assert np.array_equal(out.cpu().numpy(), ref), pitch
 
 
 def test_wide_flag_needs_the_interleaved_tile():
