@@ -166,11 +166,10 @@ class Plan:
         if x.dim() != 2 or x.shape[1] != self.nchan:
             raise ValueError("spectra must be [nsamp_in][nchan]")
         nin = x.shape[0]
-        nout = self.nsamp_out(nin)
         _lib.check(_lib.lib().ddsp_stage(
             self._h, _dev_ptr(x, self._in_dtype(), "spectra"), int(nin),
             _stream_handle(stream)), "ddsp_stage")
-        return nout
+        return self.nsamp_out(nin)
 
     def dedisperse_staged(self, nsamp_out, out=None, device=None, stream=None):
         """Dedisperse the block staged by stage() into int32

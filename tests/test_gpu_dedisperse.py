@@ -302,3 +302,19 @@ def test_wide_flag_needs_the_interleaved_tile():
     assert t["flags"] == 48 and t["time_tile"] == 2 * narrow
     p.set_tile(16, 4, 4, 2, 48)           # 4 trials x 8 elements per thread
     assert p.get_tile()["time_tile"] == 2 * narrow
+
+
+def test_stage_refuses_a_block_shorter_than_the_delays():
+    """N_out = N_in - D must be positive: ddsp_stage refuses the block with
+    DDSP_E_SHAPE and leaves nothing staged."""
+    dms = np.linspace(0, 30, 8)
+    p = _plan(64, 500.0, -1.0, 1e-3, dms)
+    x = np.zeros((p.max_delay + 100, 64), np.uint8)
+    assert p.stage(to_dev(x)) == 100
+    short = to_dev(np.zeros((p.max_delay, 64), np.uint8))
+    with pytest.raises(DdspError) as e:
+        p.stage(short)
+    assert e.value.code == ddsp_lib.DDSP_E_SHAPE
+    with pytest.raises(DdspError) as e:
+        p.dedisperse_staged(100)
+    assert e.value.code == ddsp_lib.DDSP_E_STATE
