@@ -193,7 +193,10 @@ int ddsp_single_pulse_search_dense(ddsp_plan *plan, const int32_t *d_series,
  * static device array of the library of a little over 4 MiB, which every
  * GPU that loads the library holds until exit.
  *   d_series   int32 [ndm][nsamp_out] on the current device
- *   widths     nwidths boxcar widths (host array, as in ddsp_plan_create)
+ *   widths     nwidths boxcar widths (host array, as in ddsp_plan_create);
+ *              they reach the device as a kernel argument of a small
+ *              set-up launch (no host-to-device copy), which also zeroes
+ *              *d_count and the error word
  *   norm_window, threshold  as in ddsp_plan_create / the plan search
  *   d_cands    caller's device buffer of cand_capacity records; the
  *              candidates come back unsorted
@@ -206,13 +209,23 @@ int ddsp_single_pulse_search_dense(ddsp_plan *plan, const int32_t *d_series,
  * capture.  Every call uses the same array: calls whose work overlaps on a
  * GPU (different streams, or different host threads) race and must be
  * serialised by the caller.  A window whose values span 2^31 or more gives
- * no candidates (its MAD is taken as 0).  Asynchronous on `stream`. */
+ * no candidates (its MAD is taken as 0) and sets the error word, which
+ * ddsp_single_pulse_search_noalloc_check reports.  Asynchronous on
+ * `stream`. */
 int ddsp_single_pulse_search_noalloc(const int32_t *d_series, int ndm,
                                      int64_t nsamp_out, const int *widths,
                                      int nwidths, int64_t norm_window,
                                      float threshold, ddsp_cand *d_cands,
                                      uint32_t cand_capacity,
                                      uint32_t *d_count, ddsp_stream_t stream);
+
+/* Synchronise `stream` and report the error word the last allocation-free
+ * search on the current device left in the shared static scratch:
+ * DDSP_E_RANGE if a window's values spanned 2^31 or more (its candidates
+ * were dropped), DDSP_OK otherwise; the word is then cleared.  No
+ * counterpart in the paper; allocates nothing.  The word is shared like the
+ * rest of the scratch, so it belongs to whichever call ran last. */
+int ddsp_single_pulse_search_noalloc_check(ddsp_stream_t stream);
 
 /* Copy the per-(DM, window) statistics of the last search to the host:
  * m2[k*nwin + j] = 2*median, mad4[k*nwin + j] = 4*MAD (both exact).  *nwin
@@ -522,6 +535,25 @@ int ddsp_plan_set_tile(ddsp_plan *plan, int dm_tile, int dm_per_thread,
 int ddsp_plan_get_tile(const ddsp_plan *plan, int *dm_tile,
                        int *dm_per_thread, int *time_tile, int *chan_chunk,
                        int *stages, int *flags);
+
+/* Failure detection of the dedispersion (no counterpart in the paper).
+ * Every device wait of the staged kernels is bounded: when a bound runs out
+ * the kernel records DDSP_E_TIMEOUT in the plan's error word, lets the
+ * copies it already issued land, and returns, so the context stays usable
+ * and ddsp_plan_check / ddsp_candidates_fetch report the error.
+ * ddsp_plan_set_wait_limit: the bound of the copy/compute hand-off waits of
+ * the interleaved kernel (DDSP_TILE_INTERLEAVED, the default tile), in SM
+ * clock cycles; 0 restores the default of 4e9 (about 2 s at 2 GHz).  The
+ * waits a block makes for its own copies in flight before it exits keep
+ * the default bound.  ddsp_plan_withhold_copy: a switch for testing that
+ * path without a fault: chunk >= 0 makes the copy-issuing warp of every
+ * block of the interleaved kernel stop before that chunk of channels, so
+ * the computing warps' bounded wait for it runs out; -1 (the default)
+ * turns it off.  Neither call synchronises; both apply from the next
+ * dedispersion on.  DDSP_E_INVALID_ARG for a negative limit or a chunk
+ * below -1. */
+int ddsp_plan_set_wait_limit(ddsp_plan *plan, int64_t cycles);
+int ddsp_plan_withhold_copy(ddsp_plan *plan, int chunk);
 
 /* ------------------------------------------------------------------------
  * Unit peaks (measurement): microbenchmarks of the on-chip units the

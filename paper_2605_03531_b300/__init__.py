@@ -40,6 +40,11 @@ class _DeviceArray:
             "typestr": typestr, "strides": None, "version": 3}
 
 
+def _torch_int32():
+    import torch
+    return torch.int32
+
+
 def _tensor_view(ptr, shape, dtype):
     import torch
     typestr = {torch.int32: "<i4", torch.uint8: "|u1"}[dtype]
@@ -246,6 +251,21 @@ class Plan:
                    "ddsp_candidates_count")
         return n.value
 
+    def candidates_device(self):
+        """(int32 CUDA view [stored][4] of the last search's records, true
+        count): the plan-owned device buffer as ddsp_plan_candidates_device
+        gives it, unsorted; valid until the next search on this plan."""
+        d_c, d_n, cap = C.c_void_p(), C.c_void_p(), C.c_size_t()
+        _lib.check(_lib.lib().ddsp_plan_candidates_device(
+            self._h, C.byref(d_c), C.byref(d_n), C.byref(cap)),
+            "ddsp_plan_candidates_device")
+        n = self.count()
+        stored = min(n, cap.value)
+        if stored == 0:
+            import torch
+            return torch.zeros((0, 4), dtype=torch.int32, device="cuda"), n
+        return _tensor_view(d_c.value, (stored, 4), _torch_int32()), n
+
     def fetch_dm_range(self, dm_lo, dm_hi, cap=1 << 22):
         """(candidates with dm_lo <= dm_idx < dm_hi sorted, count in range,
         device count)."""
@@ -373,6 +393,18 @@ class Plan:
     def check(self, stream=None):
         _lib.check(_lib.lib().ddsp_plan_check(self._h, _stream_handle(stream)),
                    "ddsp_plan_check")
+
+    def set_wait_limit(self, cycles=0):
+        """Bound (SM cycles) of the interleaved kernel's hand-off waits; 0 =
+        the default (ddsp_plan_set_wait_limit)."""
+        _lib.check(_lib.lib().ddsp_plan_set_wait_limit(self._h, int(cycles)),
+                   "ddsp_plan_set_wait_limit")
+
+    def withhold_copy(self, chunk=-1):
+        """Failure-detection test switch: the copy warp stops before channel
+        chunk `chunk` (-1 = off; ddsp_plan_withhold_copy)."""
+        _lib.check(_lib.lib().ddsp_plan_withhold_copy(self._h, int(chunk)),
+                   "ddsp_plan_withhold_copy")
 
     def close(self):
         if self._h:

@@ -56,6 +56,7 @@ SIGNATURES = {
     "ddsp_single_pulse_search_dense": (I32, [P, P, I64, P, P, P, P]),
     "ddsp_single_pulse_search_noalloc": (I32, [P, I32, I64, P, I32, I64,
                                                C.c_float, P, C.c_uint32, P, P]),
+    "ddsp_single_pulse_search_noalloc_check": (I32, [P]),
     "ddsp_plan_get_stats": (I32, [P, P, P, I64, PI64]),
     "ddsp_candidates_fetch": (I32, [P, P, C.c_size_t, C.POINTER(C.c_size_t)]),
     "ddsp_candidates_count": (I32, [P, C.POINTER(C.c_size_t)]),
@@ -96,6 +97,8 @@ SIGNATURES = {
     "ddsp_last_error_detail": (C.c_char_p, []),
     "ddsp_plan_set_tile": (I32, [P, I32, I32, I32, I32, I32]),
     "ddsp_plan_get_tile": (I32, [P] + [C.POINTER(C.c_int)] * 6),
+    "ddsp_plan_set_wait_limit": (I32, [P, I64]),
+    "ddsp_plan_withhold_copy": (I32, [P, I32]),
     "ddsp_cluster_create": (I32, [C.POINTER(P), I32, I32, I64, I64]),
     "ddsp_cluster_destroy": (None, [P]),
     "ddsp_peaks_cluster": (I32, [P, P, P, I64, P, I32, I32, I32, I32, P]),

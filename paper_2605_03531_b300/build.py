@@ -43,23 +43,41 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    if not force and up_to_date():
+def _compile(src, obj, verbose, extra):
+    cmd = [NVCC, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
+    if verbose:
+        cmd.insert(1, "-Xptxas=-v")
+    subprocess.run(cmd, check=True)
+
+
+def build(force: bool = False, verbose: bool = False, lib: str = LIB,
+          defines=()) -> str:
+    """Compile every .cu (in parallel; an object is rebuilt when it is older
+    than any source or header) and link `lib`.  `defines` adds -D flags (a
+    build with other flags keeps its objects in a folder of its own)."""
+    if not force and lib == LIB and not defines and up_to_date():
         return LIB
-    os.makedirs(BUILD, exist_ok=True)
+    extra = [f"-D{d}" for d in defines]
+    bdir = BUILD if not defines else BUILD + "_" + "_".join(
+        d.lower() for d in defines)
+    os.makedirs(bdir, exist_ok=True)
+    newest = max(os.path.getmtime(d) for d in _deps())
+    jobs = []
     objs = []
     for src in _sources():
-        obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
-        cmd = [NVCC, *ARCH, *FLAGS, "-c", src, "-o", obj]
-        if verbose:
-            cmd.insert(1, "-Xptxas=-v")
-        subprocess.run(cmd, check=True)
+        obj = os.path.join(bdir, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
-    tmp = LIB + ".tmp"
+        if force or not os.path.exists(obj) or os.path.getmtime(obj) < newest:
+            jobs.append((src, obj))
+    from concurrent.futures import ThreadPoolExecutor
+    with ThreadPoolExecutor(max(1, min(len(jobs), os.cpu_count() or 1))) as ex:
+        for f in [ex.submit(_compile, s_, o_, verbose, extra) for s_, o_ in jobs]:
+            f.result()
+    tmp = lib + ".tmp"
     subprocess.run([NVCC, *ARCH, "-shared", "-cudart", "static", "-o", tmp,
                     *objs], check=True)
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

@@ -14,6 +14,11 @@ namespace ddsp {
 // Device-side error word values (plan->d_err).
 enum : int32_t { kErrNone = 0, kErrTimeout = 1, kErrRange = 2 };
 
+// Bound of every device wait, in SM clock cycles (about 2 s at 2 GHz); the
+// waits a block makes for its own copies in flight before it exits always
+// use it, whatever a plan sets for its hand-off waits.
+constexpr long long kDefaultWaitCycles = 4000000000LL;
+
 // Dedispersion kernel geometry: 8 warps per block, each thread owns
 // rd DM trials x kElemPerThread interleaved elements.
 constexpr int kThreads = 256;
@@ -89,6 +94,18 @@ struct Plan {
   int32_t *d_widths = nullptr;
   bool searched = false;
   cudaStream_t last_stream = nullptr;
+
+  // failure detection of the interleaved dedispersion kernel: the bound of
+  // its copy/compute hand-off waits in SM cycles (0: kDefaultWaitCycles),
+  // and a test switch that stops the copy-issuing warp before a chunk
+  // (-1: off)
+  long long wait_limit = 0;
+  int withhold_chunk = -1;
+
+  // resampling (ddsp_resample): the first bin edge of every 32-bin group,
+  // tabulated on the host in FP64
+  void *d_rs = nullptr;
+  size_t rs_bytes = 0;
 };
 
 // ---- multi-beam descriptors (device arrays built by the batch) ---------
@@ -157,6 +174,8 @@ struct IlLaunch {
   int nchan = 0, nbits = 8;
   int32_t *d_err = nullptr;
   void *d_il = nullptr;         // interleaved rows [nchan][ypitch] uint32
+  long long wait_limit = kDefaultWaitCycles;  // hand-off waits (SM cycles)
+  int withhold_chunk = -1;      // test switch: producer stops before it
 };
 IlLaunch il_launch_of(const Plan &p);
 // Rows of d_cm to interleaved rows y (v.d_il if null).  ring > 0: the rows

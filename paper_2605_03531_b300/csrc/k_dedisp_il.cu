@@ -50,6 +50,8 @@ struct IlArgs {
   uint32_t one;           // 1: the multiplier of the FMA-pipe adds (a
                           // kernel argument, so the compiler cannot fold it)
   int nz;                 // > 0: blockIdx.z picks rows and output from z[]
+  int withhold;           // >= 0: the producer stops before this chunk
+                          // (failure-detection test; -1 in normal use)
   IlRows z[kIlMaxRows];   // (same tables, same shape: e.g. beam-blocks)
 };
 
@@ -232,7 +234,12 @@ dedisp_il_kernel(IlArgs a, int32_t *err, long long timeout_cycles) {
     // ring position of chunk j: stage st, pass (j / nst) parity ph
     int st = 0;
     uint32_t ph = 0;
+    bool withheld = false;
     for (; j < nchunks; ++j) {
+      if (j == a.withhold) {   // test switch: this chunk is never staged
+        withheld = true;
+        break;
+      }
       // the stage's previous chunk (j - nst) has been consumed (the warp
       // gives up as a whole if any lane's wait ran out)
       if (!__all_sync(0xffffffffu,
@@ -271,13 +278,15 @@ dedisp_il_kernel(IlArgs a, int32_t *err, long long timeout_cycles) {
       }
     }
     if (j < nchunks) {
-      // gave up: record it and let the copies in flight (chunks j - nst ..
-      // j - 1) land before the block's shared memory goes away
+      // gave up (or withheld a chunk): record it and let the copies in
+      // flight (chunks j - nst .. j - 1) land before the block's shared
+      // memory goes away; these waits keep the default bound whatever the
+      // hand-off bound is, as the copies were issued and will land
       if (lane == 0) {
-        atomicExch(err, kErrTimeout);
+        if (!withheld) atomicExch(err, kErrTimeout);
         for (int jj = max(0, j - nst); jj < j; ++jj)
           mbar_wait(&full[jj % nst], (uint32_t)((jj / nst) & 1),
-                    timeout_cycles);
+                    kDefaultWaitCycles);
       }
     }
     return;
@@ -359,10 +368,12 @@ cudaError_t launch_il_t(const IlLaunch &p, int64_t ypitch, int64_t nsamp_out,
   a.nst = p.tile.nbuf;
   a.one = 1u;
   a.nz = rows ? nrows : 0;
+  a.withhold = p.withhold_chunk;
   for (int i = 0; i < a.nz; ++i) a.z[i] = rows[i];
   dim3 grid((unsigned)p.tab->n_dm_tiles, (unsigned)ntt,
             (unsigned)(a.nz > 0 ? a.nz : 1));
-  const long long timeout = 4000000000LL;  // ~2 s of SM clock
+  const long long timeout =
+      p.wait_limit > 0 ? p.wait_limit : kDefaultWaitCycles;
   kern<<<grid, 32 * (WT * WD + 1), smem, s>>>(a, p.d_err, timeout);
   return cudaGetLastError();
 }
@@ -384,6 +395,8 @@ IlLaunch il_launch_of(const Plan &p) {
   v.nbits = p.nbits;
   v.d_err = p.d_err;
   v.d_il = p.d_il;
+  v.wait_limit = p.wait_limit > 0 ? p.wait_limit : kDefaultWaitCycles;
+  v.withhold_chunk = p.withhold_chunk;
   return v;
 }
 

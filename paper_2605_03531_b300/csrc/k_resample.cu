@@ -9,13 +9,16 @@
 //   t_k = k + alpha k(k-1)/2 + beta (k-1)k(2k-1)/6
 // and out[k] sums the one to three input samples the bin overlaps, each
 // weighted by the overlap (FP32, relative to an exact integer sample index
-// taken every 32 bins from the FP64 closed form).  f1 > 0 reverses the series, uses f0~ = f0 + f1 T + f2 T^2/2,
+// taken every 32 bins from the FP64 closed form, which the host tabulates:
+// the device does no FP64 arithmetic).  f1 > 0 reverses the series, uses
+// f0~ = f0 + f1 T + f2 T^2/2,
 // f' = f1 + f2 T, f'' = -f2, and reverses the result; f1 <= 0 uses f0,
 // f' = -f1, f'' = -f2.
 #include <math.h>
 #include <stdint.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "host.h"
 
@@ -49,8 +52,7 @@ ResampleLaw resample_law(int64_t n, double tsamp, double f0, double f1,
   return L;
 }
 
-__host__ __device__ __forceinline__ double bin_start(double k, double a,
-                                                     double b) {
+inline double bin_start(double k, double a, double b) {
   return k + a * k * (k - 1.0) / 2.0 + b * (k - 1.0) * k * (2.0 * k - 1.0) / 6.0;
 }
 
@@ -83,17 +85,25 @@ int64_t resample_count(int64_t n, const ResampleLaw &L) {
 
 constexpr int kRsGroups = 32;
 
+// First edge of a group of 32 bins: t_{32g} = ib + fr, ib an integer sample
+// index and 0 <= fr < 1 (FP64 on the host, fr rounded to FP32 once).
+struct RsEdge {
+  long long ib;
+  float fr;
+  int pad;
+};
+
 // A warp makes kRsGroups groups of 32 consecutive bins, one bin per lane:
-// lane l first takes group l's first edge from the closed form in FP64 (one
-// FP64 pass per 1024 bins: the FP64 pipe is narrow), split into an integer sample index ib and an FP32
-// fraction; per group a warp prefix sum of the bins' FP32 width
-// deviations from one sample places lane l's bin at ib + l + e, and the
-// overlaps are computed from the bin's own integer sample, so every FP32
-// value stays near 1 (edge error about 2^-22 samples) and the lanes read
-// and write consecutive samples.
+// lane l first loads group l's first edge (tabulated on the host in FP64),
+// then per group a warp prefix sum of the bins' FP32 width deviations from
+// one sample places lane l's bin at ib + l + e, and the overlaps are
+// computed from the bin's own integer sample, so every FP32 value stays
+// near 1 (edge error about 2^-22 samples) and the lanes read and write
+// consecutive samples.
 __global__ void resample_kernel(const int32_t *__restrict__ in, int64_t nrows,
-                                int64_t n, int64_t in_pitch, double a, double b,
-                                bool rev, int64_t K, float *__restrict__ out,
+                                int64_t n, int64_t in_pitch, float af, float bf,
+                                const RsEdge *__restrict__ edges, bool rev,
+                                int64_t K, float *__restrict__ out,
                                 int64_t out_pitch) {
   const int lane = threadIdx.x & 31;
   const int64_t groups = (K + 31) / 32;            // 32 bins each
@@ -101,17 +111,15 @@ __global__ void resample_kernel(const int32_t *__restrict__ in, int64_t nrows,
   const int64_t total = nrows * supers;
   const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const float af = (float)a, bf = (float)b;
   for (int64_t sg = w0; sg < total; sg += nw) {
     const int64_t r = sg / supers, g0 = (sg - r * supers) * kRsGroups;
-    // lane l: the FP64 first edge of group g0 + l (one FP64 pass per 32
-    // groups, the FP64 pipe being narrow)
+    // lane l: the first edge of group g0 + l
     long long ibl = 0;
     float frl = 0.0f;
-    {
-      const double t0 = bin_start((double)((g0 + (lane % kRsGroups)) * 32), a, b);
-      ibl = (long long)floor(t0);
-      frl = (float)(t0 - (double)ibl);
+    if (g0 + lane < groups) {
+      const RsEdge ed = edges[g0 + lane];
+      ibl = ed.ib;
+      frl = ed.fr;
     }
     const int32_t *x = in + r * in_pitch;
     const int gn = (int)min((int64_t)kRsGroups, groups - g0);
@@ -185,12 +193,38 @@ extern "C" int ddsp_resample(ddsp_plan *h, const int32_t *d_in, int64_t nrows,
   *nout = K;
   if (K == 0) return DDSP_OK;
   DeviceGuard g(h->p.device);
+  Plan &p = h->p;
+  // every group's first edge, from the FP64 closed form on the host
+  const int64_t groups = (K + 31) / 32;
+  std::vector<RsEdge> edges((size_t)groups);
+  for (int64_t q = 0; q < groups; ++q) {
+    const double t0 = bin_start((double)(q * 32), L.alpha, L.beta);
+    const double fl = floor(t0);
+    edges[(size_t)q].ib = (long long)fl;
+    edges[(size_t)q].fr = (float)(t0 - fl);
+    edges[(size_t)q].pad = 0;
+  }
+  const size_t bytes = (size_t)groups * sizeof(RsEdge);
+  if (bytes > p.rs_bytes) {
+    cudaDeviceSynchronize();   // a previous call may still read the table
+    cudaFree(p.d_rs);
+    p.d_rs = nullptr;
+    p.rs_bytes = 0;
+    cudaError_t e = cudaMalloc(&p.d_rs, bytes);
+    if (e != cudaSuccess) return cuda_rc(e);
+    p.rs_bytes = bytes;
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  // from pageable memory: the call returns once the table has been staged,
+  // and the copy is ordered before the kernel on the same stream
+  cudaError_t e = cudaMemcpyAsync(p.d_rs, edges.data(), bytes,
+                                  cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) return cuda_rc(e);
   const int64_t total =
-      nrows * (((K + 31) / 32 + kRsGroups - 1) / kRsGroups);      // warps
+      nrows * ((groups + kRsGroups - 1) / kRsGroups);      // warps
   const int64_t blocks = std::min<int64_t>((total + 7) / 8, 148 * 32);
-  resample_kernel<<<(unsigned)blocks, 256, 0,
-                    reinterpret_cast<cudaStream_t>(stream)>>>(
-      d_in, nrows, nsamp, in_pitch, L.alpha, L.beta, L.rev, K, d_out,
-      out_pitch);
+  resample_kernel<<<(unsigned)blocks, 256, 0, s>>>(
+      d_in, nrows, nsamp, in_pitch, (float)L.alpha, (float)L.beta,
+      static_cast<const RsEdge *>(p.d_rs), L.rev, K, d_out, out_pitch);
   return cuda_rc(cudaGetLastError());
 }

@@ -23,6 +23,8 @@
 // and 16 bytes per candidate: the kernel is bounded by HBM bandwidth.
 #include <math.h>
 
+#include <mutex>
+
 #include "internal.h"
 
 namespace ddsp {
@@ -744,17 +746,36 @@ size_t sps_smem_bytes(int64_t maxlen, int wmax) {
   return kBufOff + 4 * (size_t)(maxlen + wmax + 4);
 }
 
+// The search kernels' opt-in to dynamic shared memory beyond 48 KB, made
+// once per device for the largest window the search accepts (the launch's
+// own size still decides what a block gets).  Plan, batch, server and
+// allocation-free launches share it, and it is never lowered, so a short
+// window's launch cannot undo a long window's setting.
+constexpr int kSpsOptDevices = 64;
+constexpr size_t kSpsMaxSmem = kBufOff + 4 * (size_t)(kMaxWindowSamples + 4);
+
+template <typename Kern>
+cudaError_t sps_opt_in(Kern kern, int which) {
+  static std::mutex mu;
+  static bool done[kSpsOptDevices][3] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kSpsOptDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done[dev][which]) return cudaSuccess;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)kSpsMaxSmem);
+  if (e == cudaSuccess) done[dev][which] = true;
+  return e;
+}
+
 cudaError_t launch_sps_batch(const SpsBeam *d_beams, int nbeams,
                              int64_t total_blocks, float threshold,
                              size_t smem, cudaStream_t s) {
-  static size_t attr_bytes = 0;
-  if (smem > attr_bytes) {
-    cudaError_t e = cudaFuncSetAttribute(
-        sps_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-        (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_bytes = smem;
-  }
+  if (smem > kSpsMaxSmem) return cudaErrorInvalidValue;
+  cudaError_t e = sps_opt_in(sps_batch_kernel, 2);
+  if (e != cudaSuccess) return e;
   sps_batch_kernel<<<(unsigned)total_blocks, kSpsThreads, smem, s>>>(
       d_beams, nbeams, threshold);
   return cudaGetLastError();
@@ -771,15 +792,10 @@ cudaError_t launch_sps(const Plan &p, const int32_t *d_series,
   const int wmax = p.widths.back();
   const size_t smem =
       kBufOff + 4 * (size_t)(maxlen + wmax + 4);
-  static size_t attr_bytes[2] = {0, 0};
+  if (smem > kSpsMaxSmem) return cudaErrorInvalidValue;
   auto kern = dense ? sps_kernel<true> : sps_kernel<false>;
-  if (smem > attr_bytes[dense]) {
-    // the opt-in limit covers static + dynamic shared memory together
-    cudaError_t e = cudaFuncSetAttribute(
-        kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_bytes[dense] = smem;
-  }
+  cudaError_t e = sps_opt_in(kern, dense ? 1 : 0);
+  if (e != cudaSuccess) return e;
   dim3 grid((unsigned)nwin, (unsigned)p.ndm);
   kern<<<grid, kSpsThreads, smem, s>>>(
       d_series, nsamp_out, L, nwin, p.d_widths, p.nwidths, threshold, p.d_m2,
@@ -818,7 +834,42 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 constexpr int kNoAllocMaxDevices = 64;
 // device address of g_noalloc_scratch per device, found once per device
 unsigned char *g_noalloc_ptr[kNoAllocMaxDevices] = {};
-size_t g_noalloc_attr[kNoAllocMaxDevices] = {};
+
+// Everything a call must reset or refresh in the shared scratch, passed by
+// value: the width table and the zeroed error word and counter.
+struct NoAllocPrep {
+  int32_t widths[kMaxWidths];
+  int nw;
+};
+
+__global__ void noalloc_prep_kernel(NoAllocPrep a, int32_t *__restrict__ widths,
+                                    int32_t *__restrict__ err,
+                                    uint32_t *__restrict__ count) {
+  const int t = threadIdx.x;
+  if (t < a.nw) widths[t] = a.widths[t];
+  if (t == 0) {
+    *err = kErrNone;
+    *count = 0u;
+  }
+}
+
+// The scratch's device address on the current device (set-up on first use).
+int noalloc_base(unsigned char **base) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices)
+    return DDSP_E_CUDA;
+  if (!g_noalloc_ptr[dev]) {
+    // once per device, with that device current: the host-side name of the
+    // array is only a stand-in, the kernel needs its device address
+    unsigned char *ptr = nullptr;
+    if (cudaGetSymbolAddress((void **)&ptr, g_noalloc_scratch) != cudaSuccess ||
+        !ptr)
+      return DDSP_E_CUDA;
+    g_noalloc_ptr[dev] = ptr;
+  }
+  *base = g_noalloc_ptr[dev];
+  return DDSP_OK;
+}
 
 }  // namespace
 }  // namespace ddsp
@@ -847,19 +898,9 @@ extern "C" int ddsp_single_pulse_search_noalloc(
   // the statistics of every (DM trial, window) must fit the static scratch
   if ((int64_t)ndm * nwin > kNoAllocMaxWindows) return DDSP_E_SHAPE;
 
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kNoAllocMaxDevices)
-    return DDSP_E_CUDA;
-  if (!g_noalloc_ptr[dev]) {
-    // once per device, with that device current: the host-side name of the
-    // array is only a stand-in, the kernel needs its device address
-    unsigned char *ptr = nullptr;
-    if (cudaGetSymbolAddress((void **)&ptr, g_noalloc_scratch) != cudaSuccess ||
-        !ptr)
-      return DDSP_E_CUDA;
-    g_noalloc_ptr[dev] = ptr;
-  }
-  unsigned char *base = g_noalloc_ptr[dev];
+  unsigned char *base = nullptr;
+  const int brc = noalloc_base(&base);
+  if (brc != DDSP_OK) return brc;
   int64_t *m2 = reinterpret_cast<int64_t *>(base);
   int64_t *mad4 = reinterpret_cast<int64_t *>(base + kNoAllocStatsBytes);
   int32_t *d_widths = reinterpret_cast<int32_t *>(base + kNoAllocWidthsOff);
@@ -868,23 +909,39 @@ extern "C" int ddsp_single_pulse_search_noalloc(
   cudaStream_t s = (cudaStream_t)stream;
   const size_t smem = kBufOff + 4 * (size_t)(maxlen + wmax + 4);
   auto kern = sps_kernel<false>;
-  if (smem > g_noalloc_attr[dev]) {
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem) != cudaSuccess)
-      return DDSP_E_CUDA;
-    g_noalloc_attr[dev] = smem;
-  }
-  // the array keeps the previous call's contents: reset what must start at
-  // zero (the caller's counter and the error word), refresh the widths
-  if (cudaMemsetAsync(d_count, 0, sizeof(uint32_t), s) != cudaSuccess ||
-      cudaMemsetAsync(d_err, 0, sizeof(int32_t), s) != cudaSuccess ||
-      cudaMemcpyAsync(d_widths, widths, sizeof(int32_t) * nwidths,
-                      cudaMemcpyHostToDevice, s) != cudaSuccess)
+  if (smem > kSpsMaxSmem || sps_opt_in(kern, 0) != cudaSuccess)
     return DDSP_E_CUDA;
+  // the array keeps the previous call's contents: one small launch resets
+  // what must start at zero (the caller's counter and the error word) and
+  // writes the widths, which travel as a kernel argument (no host copy)
+  NoAllocPrep prep{};
+  for (int i = 0; i < nwidths; ++i) prep.widths[i] = widths[i];
+  prep.nw = nwidths;
+  noalloc_prep_kernel<<<1, 32, 0, s>>>(prep, d_widths, d_err, d_count);
+  if (cudaGetLastError() != cudaSuccess) return DDSP_E_CUDA;
   dim3 grid((unsigned)nwin, (unsigned)ndm);
   kern<<<grid, kSpsThreads, smem, s>>>(d_series, nsamp_out, L, nwin, d_widths,
                                        nwidths, threshold, m2, mad4, d_cands,
                                        d_count, cand_capacity, nullptr, nullptr,
                                        nullptr, d_err);
   return cudaGetLastError() == cudaSuccess ? DDSP_OK : DDSP_E_CUDA;
+}
+
+extern "C" int ddsp_single_pulse_search_noalloc_check(ddsp_stream_t stream) {
+  using namespace ddsp;
+  unsigned char *base = nullptr;
+  const int brc = noalloc_base(&base);
+  if (brc != DDSP_OK) return brc;
+  cudaStream_t s = (cudaStream_t)stream;
+  int32_t *d_err = reinterpret_cast<int32_t *>(base + kNoAllocErrOff);
+  int32_t v = kErrNone;
+  if (cudaMemcpyAsync(&v, d_err, sizeof(v), cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return DDSP_E_CUDA;
+  if (v == kErrNone) return DDSP_OK;
+  if (cudaMemsetAsync(d_err, 0, sizeof(int32_t), s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return DDSP_E_CUDA;
+  return v == kErrRange ? DDSP_E_RANGE : DDSP_E_TIMEOUT;
 }

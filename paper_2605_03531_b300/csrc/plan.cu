@@ -263,6 +263,7 @@ void release(Plan &p) {
   cudaFree(p.d_count);
   cudaFree(p.d_err);
   cudaFree(p.d_widths);
+  cudaFree(p.d_rs);
 }
 
 int search_windows(const Plan &p, int64_t n, int64_t *nwin) {
@@ -474,6 +475,18 @@ int ddsp_plan_set_tile(ddsp_plan *h, int dm_tile, int dm_per_thread,
     p.il_bytes = 0;
   }
   return build_tables(p);
+}
+
+int ddsp_plan_set_wait_limit(ddsp_plan *h, int64_t cycles) {
+  if (!h || cycles < 0) return DDSP_E_INVALID_ARG;
+  h->p.wait_limit = cycles;
+  return DDSP_OK;
+}
+
+int ddsp_plan_withhold_copy(ddsp_plan *h, int chunk) {
+  if (!h || chunk < -1) return DDSP_E_INVALID_ARG;
+  h->p.withhold_chunk = chunk;
+  return DDSP_OK;
 }
 
 int ddsp_plan_get_tile(const ddsp_plan *h, int *dm_tile, int *dm_per_thread,

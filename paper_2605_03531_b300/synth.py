@@ -398,6 +398,28 @@ def config5(nbeams=64, seed=5):
     return beams
 
 
+
+def config5_stream(nblocks=10, seed=500000, block=16384):
+    """One beam's continuous stream of the c5 shape for checking the serving
+    path block by block: (FilterbankConfig of the c2 channel / DM shape,
+    time-major uint8 [nblocks*block][4096] on the CPU).  Noise from stream
+    ``seed``; dispersed pulses every ~0.6 block (DM U(20, 240), W U{1..64},
+    S/N U(10, 30)), so pulses straddle block boundaries and sweep across
+    several blocks of the ring."""
+    base = config2()
+    cfg = FilterbankConfig(
+        name=f"c5-stream-{nblocks}x{block}", nchan=base.nchan, f_top=base.f_top,
+        chan_bw=base.chan_bw, tsamp=base.tsamp, nsamp_out=block,
+        dm_lo=base.dm_lo, dm_hi=base.dm_hi, ndm=base.ndm,
+        widths=list(base.widths), threshold=base.threshold, seed=seed)
+    n = nblocks * block
+    cfg.pulses = random_pulses(n // 10000, cfg.nchan, n, seed=seed,
+                               dm_range=(20.0, 240.0), wmax=64,
+                               snr_range=(10.0, 30.0), spacing=10000)
+    x = noise_u8(n, cfg.nchan, seed)
+    inject_pulses(x, cfg.pulses, cfg.f_top, cfg.chan_bw, cfg.tsamp, seed)
+    return cfg, x
+
 # ------------------------------------------------- single-pulse candidate lists
 CAND_DTYPE = np.dtype([("dm_idx", np.uint32), ("t", np.uint32),
                        ("w_idx", np.uint32), ("snr", np.float32)])

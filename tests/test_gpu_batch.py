@@ -109,141 +109,81 @@ def test_batch_beam_matches_oracle():
             assert abs(s - 7.0) <= 7e-4
 
 
-def test_batch_full_160_beams_sampled():
+def _oracle_rows(x, d_rows):
+    oracle.set_threads(1)          # this host thread's OpenMP team
+    return oracle.dedisperse(x, d_rows)
+
+
+def test_batch_full_160_beams():
     """The full uneven mix: 160 beams, 1024-4096 channels, 65536-262144
     samples, DM grids up to 0-500 with 256-2048 trials, in one persistent
-    launch under a CUDA graph; sampled beams against their plain path and
-    sampled outputs against the oracle."""
+    launch under a CUDA graph (and again in the per-beam interleaved mode).
+    Every beam against the oracle on the DM trials nearest its injected
+    pulses and its first and last trial: those rows bit-exact and their
+    candidates identical under the tolerance rule.  One whole beam (the
+    smallest with pulses): every row bit-exact and its whole candidate
+    list."""
+    import os
+    from concurrent.futures import ThreadPoolExecutor
+    from parity import compare_candidates, sps_parallel
     cfgs = synth.config3()
-    plans = [_plan(c, cap=1 << 16) for c in cfgs]
+    plans = [_plan(c, cap=1 << 20) for c in cfgs]
     nins = [c.nsamp_out + p.max_delay for c, p in zip(cfgs, plans)]
     batch = Batch(plans, nins)
-    for b, (c, p) in enumerate(zip(cfgs, plans)):
-        x = _block(c, p)
-        batch.ingest(b, x)
-        del x
-    batch.run(7.0, use_graph=True)
-    batch.run(7.0, use_graph=True)
-    batch.check()
-    rng = np.random.default_rng(3)
-    for b in rng.choice(len(cfgs), 3, replace=False):
-        c, p = cfgs[b], plans[b]
-        x = _block(c, p)
-        s = p.dedisperse(x)
-        assert torch.equal(batch.series[b], s), b
-        xh = x.cpu().numpy()
-        d = p.delays()
-        for k, t in zip(rng.integers(0, c.ndm, 40), rng.integers(0, c.nsamp_out, 40)):
-            assert int(s[k, t]) == oracle.dedisperse_at(xh, d, int(k), int(t))
-        del x, s
-
-
-def test_batch_per_beam_chunks_and_groups():
-    """Beams whose delay spans inside a DM tile differ by ~40x share one
-    step: the fine beams stage up to the tile's chunk limit in the main
-    launch, the coarse one goes to the second launch with a narrower DM
-    tile, and every beam stays exact for several limits."""
-    coarse = synth.config3(nbeams=1, seed=23, nsamp_range=(8192, 8192),
-                           nchan_choices=(256,), dm_hi_choices=(100.0,),
-                           ndm_choices=(64,))
-    fine = synth.config3(nbeams=2, seed=29, nsamp_range=(8192, 16384),
-                         nchan_choices=(1024,), dm_hi_choices=(10.0,),
-                         ndm_choices=(128,))
-    cfgs = coarse + fine
-    plans = [_plan(c) for c in cfgs]
-    blocks = [_block(c, p) for c, p in zip(cfgs, plans)]
-    ref = [p.dedisperse(x).clone() for p, x in zip(plans, blocks)]
-    refc = []
-    for c, p, r in zip(cfgs, plans, ref):
-        p.single_pulse_search(r, c.threshold)
-        refc.append(p.fetch()[0])
-    batch = Batch(plans, [x.shape[0] for x in blocks])
-    for b, x in enumerate(blocks):
-        batch.ingest(b, x)
-    for cap in (8, 3, 1):
-        batch.set_tile(16, 8, cap, 2)
-        t = [batch.beam_tile(b) for b in range(len(cfgs))]
-        # spans per 16-trial tile: ~8500 samples (coarse), ~440 (fine)
-        assert t[0]["group"] == 1 and t[0]["dm_tile"] < 16, (cap, t)
-        assert t[1]["group"] == t[2]["group"] == 0
-        assert t[1]["chan_chunk"] == t[2]["chan_chunk"] >= min(cap, 3)
-        assert all(x["chan_chunk"] >= 1 for x in t)
-        for s_ in batch.series:
-            s_.fill_(-1)
+    whole = min((b for b in range(len(cfgs)) if cfgs[b].pulses),
+                key=lambda b: cfgs[b].nchan * cfgs[b].nsamp_out * cfgs[b].ndm)
+    threads = os.cpu_count() or 1
+    rows, futs = [], []
+    ref_whole = None
+    # the oracle's rows run on host threads (one beam each, one OpenMP
+    # thread each) while the next beams are generated; at most `threads`
+    # beams' inputs are held on the host at a time
+    with ThreadPoolExecutor(threads) as ex:
+        for b, (c, p) in enumerate(zip(cfgs, plans)):
+            x = _block(c, p)
+            batch.ingest(b, x)
+            xh = x.cpu().numpy()
+            del x
+            dm = c.dm_list()
+            r = {0, c.ndm - 1}
+            for pl in c.pulses:
+                r.add(int(np.argmin(np.abs(dm - pl.dm))))
+            r = sorted(r)
+            rows.append(r)
+            futs.append(ex.submit(_oracle_rows, xh, p.delays()[r]))
+            if b == whole:
+                ref_whole = oracle.dedisperse(xh, p.delays())
+            del xh
+            if b >= threads:
+                futs[b - threads].result()
+        ref_rows = [f.result() for f in futs]
+    for mode in (Batch.PERSISTENT, Batch.PER_BEAM):
+        batch.set_mode(mode)
+        for s in batch.series:
+            s.fill_(-1)
         batch.run(7.0, use_graph=True)
         batch.run(7.0, use_graph=True)
         batch.check()
-        for b in range(len(cfgs)):
-            assert torch.equal(batch.series[b], ref[b]), (cap, b)
-            _same_candidates(plans[b].fetch()[0], refc[b])
-
-
-def test_batch_autotune_with_two_groups_keeps_results():
-    cfgs = (synth.config3(nbeams=2, seed=41, nsamp_range=(8192, 8192),
-                          nchan_choices=(256,), dm_hi_choices=(100.0,),
-                          ndm_choices=(64,))
-            + small_mix(4, seed=43))
-    plans = [_plan(c) for c in cfgs]
-    blocks = [_block(c, p) for c, p in zip(cfgs, plans)]
-    ref = [p.dedisperse(x).clone() for p, x in zip(plans, blocks)]
-    batch = Batch(plans, [x.shape[0] for x in blocks])
-    for b, x in enumerate(blocks):
-        batch.ingest(b, x)
-    batch.set_tile(16, 8, 8, 2)
-    assert any(batch.beam_tile(b)["group"] == 1 for b in range(len(cfgs)))
-    ms, best = batch.autotune(reps=1)     # candidates with and without a split
-    assert best >= 0 and ms[best] > 0
-    batch.run(7.0, use_graph=True)
-    batch.run(7.0, use_graph=True)
-    batch.check()
-    for b in range(len(cfgs)):
-        assert torch.equal(batch.series[b], ref[b]), b
-
-
-@pytest.mark.parametrize("use_graph", [False, True])
-def test_batch_per_beam_mode_equals_plain(use_graph):
-    """The per-beam interleaved mode (each beam's rows interleaved into the
-    batch's one staging area, then its plan's default tile) reproduces every
-    beam's series and candidates; set_tile returns to the persistent mode,
-    which still agrees."""
-    cfgs = small_mix(8, seed=17)
-    plans = [_plan(c) for c in cfgs]
-    blocks = [_block(c, p) for c, p in zip(cfgs, plans)]
-    ref_series, ref_cands = [], []
-    for c, p, x in zip(cfgs, plans, blocks):
-        s = p.dedisperse(x)
-        p.single_pulse_search(s, c.threshold)
-        ref_series.append(s.clone())
-        ref_cands.append(p.fetch()[0])
-    batch = Batch(plans, [x.shape[0] for x in blocks])
-    for b, x in enumerate(blocks):
-        batch.ingest(b, x)
-    assert batch.get_mode() == Batch.PERSISTENT
-    batch.set_mode(Batch.PER_BEAM)
-    assert batch.get_mode() == Batch.PER_BEAM
-    for rep in range(3):
-        for s_ in batch.series:
-            s_.fill_(-1)
-        batch.run(7.0, use_graph=use_graph)
-        batch.check()
-        for b in range(len(cfgs)):
-            assert torch.equal(batch.series[b], ref_series[b]), (rep, b)
-            _same_candidates(plans[b].fetch()[0], ref_cands[b])
-    batch.set_tile(16, 8, 8, 2)
-    assert batch.get_mode() == Batch.PERSISTENT
-    for s_ in batch.series:
-        s_.fill_(-1)
-    batch.run(7.0, use_graph=use_graph)
-    batch.check()
-    for b in range(len(cfgs)):
-        assert torch.equal(batch.series[b], ref_series[b]), b
-
-
-def test_batch_mode_refused_for_unknown_value():
-    cfgs = small_mix(2, seed=19)
-    plans = [_plan(c) for c in cfgs]
-    batch = Batch(plans, [c.nsamp_out + p.max_delay for c, p in zip(cfgs, plans)])
-    from paper_2605_03531_b300 import DdspError
-    with pytest.raises(DdspError):
-        batch.set_mode(7)
-    assert batch.get_mode() == Batch.PERSISTENT
+        n_checked = 0
+        for b, (c, p) in enumerate(zip(cfgs, plans)):
+            r = rows[b]
+            got_rows = batch.series[b][r].cpu().numpy()
+            assert np.array_equal(got_rows, ref_rows[b]), (mode, b)
+            ref_c, n_ref = sps_parallel(ref_rows[b], c.widths, c.norm_window,
+                                        c.threshold, threads=4)
+            got_c, _ = p.fetch()
+            sel = np.isin(got_c["dm_idx"], r)
+            mine = got_c[sel].copy()
+            mine["dm_idx"] = np.searchsorted(r, mine["dm_idx"])
+            compare_candidates(mine, mine.size, ref_c, n_ref, c.threshold,
+                               ref_rows[b], c.widths, c.norm_window)
+            n_checked += n_ref
+        assert n_checked > 0
+        c = cfgs[whole]
+        assert np.array_equal(batch.series[whole].cpu().numpy(), ref_whole)
+        got, n = plans[whole].fetch()
+        ref_c, n_ref = sps_parallel(ref_whole, c.widths, c.norm_window,
+                                    c.threshold)
+        assert n_ref > 0
+        compare_candidates(got, n, ref_c, n_ref, c.threshold, ref_whole,
+                           c.widths, c.norm_window)

@@ -4,6 +4,8 @@ Covers every tile shape of the staged kernel and the direct kernel, ragged
 channel / sample / DM counts, unsorted DM lists, uint16 input, the
 256-channel configuration in full, and the 4096-channel 262144-sample
 configuration at full size on sampled outputs plus the DM = 0 invariant."""
+import os
+
 import numpy as np
 import pytest
 import torch
@@ -318,3 +320,48 @@ def test_stage_refuses_a_block_shorter_than_the_delays():
     with pytest.raises(DdspError) as e:
         p.dedisperse_staged(100)
     assert e.value.code == ddsp_lib.DDSP_E_STATE
+
+
+def test_full_size_4096ch_whole_series_and_candidates():
+    """The single full-size beam (4096 ch x (262144 + 89989) samples x 1024
+    DMs, widths 1..256, L 8192, threshold 7) through stage + dedisperse +
+    search in the launch configuration the benchmark times, against the
+    oracle's whole result stored by tests/golden/make_golden.py (the oracle
+    takes minutes on it): every dedispersed row bit-exact (row digests of
+    the oracle's series), and the complete candidate list identical under
+    the tolerance rule.  A different best width is checked against the
+    oracle's own series row, recomputed for that DM trial."""
+    from parity import (GOLDEN, compare_to_stored, read_candidates,
+                        read_digests, row_digests)
+    cfg = synth.config2()
+    p = Plan(cfg.nchan, cfg.f_top, cfg.chan_bw, cfg.tsamp, cfg.dm_list(),
+             cfg.widths, nbits=8, norm_window=cfg.norm_window,
+             cand_capacity=1 << 20)
+    D = p.max_delay
+    nin = cfg.nsamp_out + D
+    x = synth.noise_u8(nin, cfg.nchan, cfg.seed, device="cuda")
+    synth.inject_pulses(x, cfg.pulses, cfg.f_top, cfg.chan_bw, cfg.tsamp, cfg.seed)
+    nout = p.stage(x)
+    out = p.dedisperse_staged(nout)
+    p.single_pulse_search(out, cfg.threshold)
+    got, n = p.fetch()
+    p.check()
+    stored = read_digests(os.path.join(GOLDEN, "c2_series_rows.txt"))
+    mine = row_digests(out.cpu().numpy())
+    bad = [k for k in range(cfg.ndm) if mine[k] != stored[str(k)]]
+    assert not bad, f"{len(bad)} dedispersed rows differ, first {bad[:8]}"
+    ref = read_candidates(os.path.join(GOLDEN, "c2_candidates.txt"))
+    assert n == got.size > 0
+    xh = x.cpu().numpy()
+    d = p.delays()
+
+    def width_check(k, t, wg, s_ref):
+        row = oracle.dedisperse(xh, d[k:k + 1])[0]
+        w = cfg.widths[wg]
+        B = int(row[t:t + w].astype(np.int64).sum())
+        m2, mad4 = oracle.window_stats(row, cfg.norm_window)
+        j = min(t // cfg.norm_window, m2.size - 1)
+        s = oracle.snr(B, w, m2[j], mad4[j])
+        assert abs(s - s_ref) <= 1e-5 * abs(s_ref), ("width", k, t)
+
+    compare_to_stored(got, ref, cfg.threshold, width_check)

@@ -262,3 +262,65 @@ def test_server_mode_arguments():
     srv.set_mode(Server.RELAYOUT)
     assert srv.get_mode()[0] == Server.RELAYOUT
     srv.close()
+
+
+@pytest.mark.parametrize("mode", ["relayout", "interleaved"])
+def test_c5_shape_blocks_match_oracle(mode):
+    """The streaming shape itself (4096 channels, 1024 DM trials over 0-250,
+    widths 1..256, L 8192, 16384-sample blocks): ten blocks of one beam,
+    stepped together with a second beam, past the point where its ring
+    wraps.  Block j's series (C + B columns) is bit-exact against the
+    oracle's dedispersion of the input window [j*B - D16 - C, (j+1)*B -
+    (D16 - D)) with zeros before the stream, and its candidates (start
+    times t < B) equal the oracle's search of those columns under the
+    tolerance rule; both stored by tests/golden/make_golden.py."""
+    import os
+    from parity import (GOLDEN, compare_to_stored, read_candidates,
+                        read_digests, row_digests)
+    cfg, x = synth.config5_stream(10)
+    Bc = cfg.nsamp_out
+    plan = Plan(cfg.nchan, cfg.f_top, cfg.chan_bw, cfg.tsamp, cfg.dm_list(),
+                cfg.widths, nbits=8, norm_window=cfg.norm_window,
+                cand_capacity=1 << 20)
+    srv = Server(plan, Bc, 2)
+    if mode == "interleaved":
+        srv.set_mode(Server.INTERLEAVED, 2)
+    assert srv.ring_samples < 10 * Bc          # the ring wraps in the run
+    beam, other = srv.admit(), srv.admit()
+    noise = synth.noise_u8(Bc, cfg.nchan, 77, device="cuda")
+    xd = x.cuda()
+    stored = read_digests(os.path.join(GOLDEN, "c5_series_rows.txt"))
+    ref_all = read_candidates(os.path.join(GOLDEN, "c5_candidates.txt"))
+    D16, Cc, D = srv.first_delay, srv.carry, plan.max_delay
+    d = plan.delays()
+    xh = x.numpy()
+    xz = np.concatenate([np.zeros((D16 + Cc, cfg.nchan), np.uint8), xh])
+    for j in range(10):
+        assert srv.push(beam, xd[j * Bc:(j + 1) * Bc])
+        assert srv.push(other, noise)
+        _, sb = srv.step(cfg.threshold)
+        assert sorted(sb) == sorted([beam, other])
+        torch.cuda.synchronize()
+        s = srv.series(beam).cpu().numpy()
+        assert s.shape == (cfg.ndm, Cc + Bc)
+        mine = row_digests(s, 16)
+        bad = [16 * g for g in range(len(mine))
+               if mine[g] != stored[f"{j}:{16 * g}"]]
+        assert not bad, (j, bad[:8])
+        got, n, t0 = srv.fetch(beam, j)
+        assert t0 == j * Bc - D16 - Cc
+        win = xz[j * Bc: j * Bc + Cc + Bc + D]
+
+        def width_check(k, t, wg, s_ref):
+            row = oracle.dedisperse(win, d[k:k + 1])[0]
+            w = cfg.widths[wg]
+            Bsum = int(row[t:t + w].astype(np.int64).sum())
+            m2, mad4 = oracle.window_stats(row, cfg.norm_window)
+            jj = min(t // cfg.norm_window, m2.size - 1)
+            sn = oracle.snr(Bsum, w, m2[jj], mad4[jj])
+            assert abs(sn - s_ref) <= 1e-5 * abs(s_ref), ("width", j, k, t)
+
+        compare_to_stored(got, ref_all[ref_all["block"] == j], cfg.threshold,
+                          width_check)
+    srv.check()
+    srv.close()

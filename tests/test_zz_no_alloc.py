@@ -5,7 +5,11 @@ stall on an allocation, a host that only lends pre-allocated buffers).
 It is called through the C ABI with caller-owned output buffers and must
 return the same candidates as the plan-based search, within the tolerance
 the other search tests use, on two calls in a row (the second call must not
-see anything the first left in the shared static scratch).  This file is
+see anything the first left in the shared static scratch), and the CPU
+oracle's candidates under the tolerance rule.  Its error word is read back
+through ddsp_single_pulse_search_noalloc_check.  Plan searches and
+allocation-free searches with long and short windows alternate in both
+orders (they share the kernel's shared-memory opt-in).  This file is
 collected last so a run that stops at the first failure has run every other
 test before it."""
 import ctypes as C
@@ -14,7 +18,9 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_2605_03531_b300 import CAND_DTYPE, Plan, _lib, build, synth
+from parity import compare_candidates
 
 pytestmark = pytest.mark.gpu
 
@@ -31,25 +37,27 @@ def lib():
     return _lib.lib()
 
 
-def _plan_search(x):
+def _plan_search(x, L=L_WIN):
     p = Plan(16, 500.0, -1.0, 1e-3, np.zeros(x.shape[0]), WIDTHS, nbits=8,
-             norm_window=L_WIN, cand_capacity=CAP)
+             norm_window=L, cand_capacity=CAP)
     p.single_pulse_search(x, THR)
     got, n = p.fetch()
     p.close()
     return got, n
 
 
-def _noalloc_search(lib, x, d_cands, d_count):
+def _noalloc_search(lib, x, d_cands, d_count, L=L_WIN):
     ws = np.ascontiguousarray(WIDTHS, dtype=np.int32)
     stream = torch.cuda.current_stream()
     rc = lib.ddsp_single_pulse_search_noalloc(
         C.c_void_p(x.data_ptr()), x.shape[0], x.shape[1],
-        ws.ctypes.data_as(C.c_void_p), ws.size, L_WIN, THR,
+        ws.ctypes.data_as(C.c_void_p), ws.size, L, THR,
         C.c_void_p(d_cands.data_ptr()), CAP, C.c_void_p(d_count.data_ptr()),
         C.c_void_p(stream.cuda_stream))
     assert rc == 0, lib.ddsp_error_string(rc).decode()
     torch.cuda.synchronize()
+    assert lib.ddsp_single_pulse_search_noalloc_check(
+        C.c_void_p(stream.cuda_stream)) == 0
     n = int(d_count.item())
     assert n <= CAP
     recs = d_cands[:n].cpu().numpy().view(CAND_DTYPE).reshape(-1)
@@ -90,3 +98,62 @@ def test_noalloc_search_rejects_oversize(lib):
         ws.size, 8192, 0.0, C.c_void_p(d_cands.data_ptr()), 16,
         C.c_void_p(d_count.data_ptr()), None)
     assert rc == _lib.DDSP_E_INVALID_ARG
+
+
+def test_noalloc_search_matches_oracle(lib):
+    d_cands = torch.empty((CAP, 4), dtype=torch.int32, device="cuda")
+    d_count = torch.zeros(1, dtype=torch.int32, device="cuda")
+    x = synth.gaussian_series(6, 30000, seed=33)
+    got, n = _noalloc_search(lib, x.cuda(), d_cands, d_count)
+    xh = x.numpy()
+    ref, n_ref = oracle.sps(xh, WIDTHS, L_WIN, THR)
+    assert n_ref > 0
+    compare_candidates(got, n, ref, n_ref, THR, xh, WIDTHS, L_WIN)
+
+
+def test_noalloc_range_error_is_reported(lib):
+    """A window whose values span 2^31 gives no candidates from it and sets
+    the shared error word, which the check call reports once and clears."""
+    d_cands = torch.empty((CAP, 4), dtype=torch.int32, device="cuda")
+    d_count = torch.zeros(1, dtype=torch.int32, device="cuda")
+    x = synth.gaussian_series(2, 20000, seed=34)
+    x[1, 100] = -2 ** 31
+    x[1, 101] = 2 ** 31 - 1
+    ws = np.ascontiguousarray(WIDTHS, dtype=np.int32)
+    xd = x.cuda()
+    rc = lib.ddsp_single_pulse_search_noalloc(
+        C.c_void_p(xd.data_ptr()), 2, x.shape[1], ws.ctypes.data_as(C.c_void_p),
+        ws.size, L_WIN, THR, C.c_void_p(d_cands.data_ptr()), CAP,
+        C.c_void_p(d_count.data_ptr()), None)
+    assert rc == 0
+    assert lib.ddsp_single_pulse_search_noalloc_check(None) == _lib.DDSP_E_RANGE
+    assert lib.ddsp_single_pulse_search_noalloc_check(None) == 0
+    n = int(d_count.item())
+    recs = d_cands[:n].cpu().numpy().view(CAND_DTYPE).reshape(-1)
+    assert not ((recs["dm_idx"] == 1) & (recs["t"] < L_WIN)).any()
+
+
+@pytest.mark.parametrize("order", ["plan_first", "noalloc_first"])
+def test_plan_and_noalloc_alternate_window_lengths(lib, order):
+    """Long (32768-sample) and short (8192-sample) windows through both
+    entries in turn: neither lowers the other's shared-memory opt-in."""
+    d_cands = torch.empty((CAP, 4), dtype=torch.int32, device="cuda")
+    d_count = torch.zeros(1, dtype=torch.int32, device="cuda")
+    x = synth.gaussian_series(4, 65536, seed=35).cuda()
+    seq = [("plan", 32768), ("noalloc", 8192), ("plan", 32768),
+           ("noalloc", 32768), ("plan", 8192), ("noalloc", 32768)]
+    if order == "noalloc_first":
+        seq = [("noalloc" if k == "plan" else "plan", L) for k, L in seq]
+    ref = {}
+    for kind, L in seq:
+        if kind == "plan":
+            got, n = _plan_search(x, L)
+        else:
+            got, n = _noalloc_search(lib, x, d_cands, d_count, L)
+        if L in ref:
+            r, nr = ref[L]
+            assert n == nr
+            assert np.array_equal(got["dm_idx"], r["dm_idx"])
+            assert np.array_equal(got["t"], r["t"])
+        else:
+            ref[L] = (got, n)
