@@ -424,12 +424,154 @@ def run_ours(args):
             "single_thread": {"value": rate1, "unit": UNIT, "cores": 1,
                               "sample": f"all {cfg.ndm} DM trials x first {T1} "
                                         f"output samples, {el1:.1f} s"}}
+    if rank == 0 and world == 1 and not args.no_serving:
+        del x, series, xd2, series2, xh
+        plan.close()
+        torch.cuda.empty_cache()
+        try:
+            result["serving"] = serving_check(
+                dev, log=lambda m: print(m, file=sys.stderr, flush=True))
+        except Exception as e:            # reported, never fatal to the line
+            result["serving"] = {"error": f"{type(e).__name__}: {e}"}
     if rank == 0:
         print(json.dumps(result), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
     return 0
+
+
+# ------------------------------------------------ serving check (default run)
+def serving_check(dev, blocks_per_beam=5, log=None):
+    """The streaming target in bounded time: beams of the 4096-channel shape
+    (16384-spectrum blocks every 1.342 s, Poisson-jittered arrivals) served
+    by batched steps (every waiting beam-block, interleaved mode, 8 staging
+    slots) and by the plain per-beam path (one beam per step, a second step
+    queued), each at the same two beam counts: the plain path's estimated
+    real-time limit and the batched one's, from an untimed calibration of
+    the step time per beam-block.  Rings are filled first (untimed), then
+    `blocks_per_beam` blocks per beam arrive in real time; p50/p99 latency
+    from arrival to the host seeing the block's step complete.  The full
+    bisection is `--workload serve`."""
+    import torch
+    from paper_2605_03531_b300 import Plan, Server, synth
+    from paper_2605_03531_b300.serve import DeviceStager, ServingLoop
+    cfg = synth.config5(1)[0]
+    B, T = cfg.nsamp_out, synth.BLOCK_PERIOD_S
+    plan = Plan(cfg.nchan, cfg.f_top, cfg.chan_bw, cfg.tsamp, cfg.dm_list(),
+                cfg.widths, nbits=8, norm_window=cfg.norm_window,
+                cand_capacity=1 << 18)
+    pool = []
+    for i in range(8):
+        x = synth.noise_u8(B, cfg.nchan, cfg.seed + 17 * i, device=dev)
+        synth.inject_pulses(x, synth.random_pulses(2, cfg.nchan, B - 4096, seed=i,
+                                                   dm_range=(10.0, 240.0), wmax=64,
+                                                   snr_range=(10.0, 30.0),
+                                                   spacing=4096),
+                            cfg.f_top, cfg.chan_bw, cfg.tsamp, cfg.seed + i)
+        pool.append(x.cpu().pin_memory())
+        del x
+    compute = torch.cuda.Stream(dev)
+    stager = DeviceStager(16, (B, cfg.nchan), compute)
+    reserve, slots = 4 << 30, 8
+
+    def make(n):
+        srv = Server(plan, B, n, reserve)
+        srv.set_mode(Server.INTERLEAVED, slots)
+        return srv
+
+    # calibration (untimed): device time per beam-block of a 32-beam step
+    # and of a one-beam step
+    def step_ms(nb):
+        srv = make(nb)
+        bs = [srv.admit() for _ in range(nb)]
+        ms = []
+        for rep in range(4):
+            for i, b in enumerate(bs):
+                xb, tok = stager.stage(pool[(i + rep) % 8])
+                srv.push(b, xb, stream=compute)
+                stager.consumed(tok)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(compute)
+            srv.step(cfg.threshold, stream=compute)
+            e1.record(compute)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        srv.close()
+        torch.cuda.synchronize(dev)
+        return min(ms[1:]) / nb
+    ms_b, ms_p = step_ms(32), step_ms(1)
+    per_beam_bytes = make(1).beam_bytes
+    free, _ = torch.cuda.mem_get_info(dev)
+    n_mem = int((free - reserve - slots * 4 * cfg.nchan * (B + 90112)) //
+                per_beam_bytes) // 16 * 16
+    est_b = int(0.95 * T * 1e3 / ms_b) // 16 * 16
+    est_p = int(0.95 * T * 1e3 / ms_p) // 16 * 16
+    lo = min(est_p, n_mem)
+    hi = min(max(est_b, lo + 16), n_mem)
+    counts = sorted(set([lo, hi]))
+    runs = {"batched": {}, "plain_per_beam": {}}
+
+    def run_at(n, per_step, inflight):
+        srv = make(n)
+        beams = []
+        try:
+            for _ in range(n):
+                beams.append(srv.admit())
+        except Exception as e:           # not admitted: memory
+            srv.close()
+            return {"admitted": len(beams), "error": str(e)}
+        warm = -(-(srv.first_delay + srv.carry) // B)
+        for k in range(warm):            # fill every ring (untimed)
+            for i, b in enumerate(beams):
+                xb, tok = stager.stage(pool[(3 * i + k) % 8])
+                srv.push(b, xb, stream=compute)
+                stager.consumed(tok)
+            srv.step(cfg.threshold, stream=compute)
+        srv.check(compute)
+        arr = synth.arrival_times(n, blocks_per_beam, seed=5)
+        loop = ServingLoop(srv, beams,
+                           lambda i, k: pool[(3 * i + warm + k) % 8],
+                           cfg.threshold, stager=stager, compute_stream=compute,
+                           max_beams_in_step=per_step, first_block=warm,
+                           max_inflight=inflight)
+        res = loop.run(arr, time_limit=blocks_per_beam * T + 30.0)
+        srv.check(compute)
+        srv.close()
+        torch.cuda.synchronize(dev)
+        lat = res.latency
+        p99 = float("inf") if not np.isfinite(lat).all() else res.percentile(99)
+        return {"p50_s": res.percentile(50), "p99_s": p99,
+                "max_s": float(np.nanmax(lat)) if np.isfinite(lat).any() else None,
+                "blocks": int(np.isfinite(lat).sum()),
+                "mean_beams_per_step": float(np.mean(res.step_sizes)),
+                "real_time": bool(p99 < T)}
+
+    for n in counts:
+        runs["batched"][str(n)] = run_at(n, 0, 1)
+        runs["plain_per_beam"][str(n)] = run_at(n, 1, 2)
+        if log:
+            log(f"serving {n}: {runs['batched'][str(n)]} | "
+                f"{runs['plain_per_beam'][str(n)]}")
+
+    def best(path):
+        ok = [int(n) for n, r in runs[path].items() if r.get("real_time")]
+        return max(ok) if ok else 0
+    return {
+        "metric": "real-time beams per B300 at p99 (of the beam counts run)",
+        "unit": "beams", "deadline_s": T, "blocks_per_beam": blocks_per_beam,
+        "beams_tested": counts,
+        "real_time_beams": {"batched": best("batched"),
+                            "plain_per_beam": best("plain_per_beam")},
+        "step_ms_per_beam_block": {"batched_32": ms_b, "plain_1": ms_p},
+        "beam_bytes": per_beam_bytes, "beams_fit_in_memory": n_mem,
+        "workload": "streaming 4096-ch beams (300-500 MHz, 81.92 us), "
+                    "16384-spectrum blocks, 1024 DMs 0-250, widths 1-256; "
+                    "batched = interleaved mode with 8 staging slots, every "
+                    "waiting beam-block per step; plain = one beam per step, "
+                    "two steps in flight",
+        "runs": runs}
 
 
 # ------------------------------------------------ unit peaks (measurement)
@@ -1417,6 +1559,8 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="beam workload: skip the bounded serving check")
     ap.add_argument("--workload", choices=["beam", "sps", "batch", "serve", "peaks",
                                            "cluster", "dered", "ffa",
                                            "resample", "rfi"],

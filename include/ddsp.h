@@ -388,17 +388,21 @@ int ddsp_batch_get_mode(const ddsp_batch *batch, int *mode);
  * All beams have the shape of `plan` (channels, band, DM trials, widths,
  * normalisation window, candidate capacity per block; uint8 samples,
  * nchan a multiple of 16).  Per admitted beam the server owns a
- * channel-major ring of ceil(D16/B) + 2 blocks (D16 = the largest delay
+ * channel-major ring of ceil(D16/B) + 1 blocks (D16 = the largest delay
  * rounded up to 16 samples) whose rows end in a copy of their first bytes,
- * a series [ndm][C + B] (C = widest boxcar - 1 rounded up to 4, carried from
- * the previous block), per-window statistics and two candidate buffers.
- * Block j (0, 1, ...) is dedispersed for output samples s_j .. s_j + B - 1
- * with s_j = j*B - D16 (input before the stream's first sample reads as 0),
- * written to series columns C .. C + B - 1, and searched for start times
- * 0 .. B - 1 of the series, normalised per window of the C + B columns as
- * ddsp_single_pulse_search does: candidate t is global output sample
- * s_j - C + t.  The results equal those of ddsp_dedisperse and
- * ddsp_single_pulse_search on the same input window. */
+ * the carry [ndm][C] (C = widest boxcar - 1 rounded up to 4: the last C
+ * outputs of the previous block), per-window statistics and two candidate
+ * buffers.  Block j (0, 1, ...) is dedispersed for output samples s_j ..
+ * s_j + B - 1 with s_j = j*B - D16 (input before the stream's first sample
+ * reads as 0) into a series [ndm][C + B] whose first C columns are the
+ * carry, and searched for start times 0 .. B - 1 of the series, normalised
+ * per window of the C + B columns as ddsp_single_pulse_search does:
+ * candidate t is global output sample s_j - C + t.  The results equal those
+ * of ddsp_dedisperse and ddsp_single_pulse_search on the same input
+ * window.  The series live in G series slots the server shares among the
+ * beams: a step runs its beam-blocks in groups of G (16 in the relayout
+ * mode, the staging slot count in the interleaved mode), each group's
+ * dedispersion, search and carry in turn. */
 typedef struct ddsp_server ddsp_server;
 
 /* Create a server for up to max_beams beams of plan's shape receiving
@@ -436,16 +440,18 @@ int ddsp_server_evict(ddsp_server *server, int beam);
 /* Ingest the beam's next block: d_block is time-major uint8 [B][nchan] in
  * device memory (16-byte aligned), read by kernels on `stream` (the caller
  * keeps it unchanged until they ran).  The block's ring slot last served the
- * step of block j - 2, which `stream` waits for.  DDSP_E_STATE if block j - 2
- * has not been given to a step yet: run a step first (the caller holds the
- * block meanwhile). */
+ * step of block j - 1, which `stream` waits for.  DDSP_E_STATE if block j - 1
+ * has not been given to a step yet (one block per beam waits for a step):
+ * run a step first (the caller holds the block meanwhile). */
 int ddsp_server_push(ddsp_server *server, int beam, const void *d_block,
                      ddsp_stream_t stream);
 
 /* One step on `stream` (asynchronous): every admitted beam with a pushed,
  * unsearched block contributes its oldest such block (max_beams_in_step > 0:
- * only that many beams, those whose block was pushed first); the blocks are
- * dedispersed by one persistent launch and searched by one batched launch.
+ * only that many beams, those whose block was pushed first); each group of
+ * G of them is carried in, dedispersed (one persistent launch, or the
+ * interleaves and one interleaved launch), searched (one batched launch)
+ * and carried out.
  * *nbeams = the number of beams in the step (0: nothing was launched),
  * their indices in beams_out (up to cap entries, may be NULL), *step_id its
  * number for ddsp_server_query.  Waits on the host for the step before the
@@ -467,8 +473,10 @@ int ddsp_server_fetch(ddsp_server *server, int beam, int64_t block,
                       ddsp_cand *host_buf, size_t cap, size_t *n_found,
                       int64_t *t_start);
 
-/* Device pointer of a beam's series [ndm][ncols] (the last stepped block's
- * once its step completed). */
+/* Device pointer of the series [ndm][ncols] of a beam's last stepped block
+ * (valid once its step completed, until the next step): its series slot,
+ * which holds it only if the block was in the last group of the latest
+ * step; DDSP_E_STATE otherwise. */
 int ddsp_server_series(ddsp_server *server, int beam, int32_t **d_series,
                        int64_t *ncols);
 
@@ -484,7 +492,9 @@ int ddsp_server_check(ddsp_server *server, ddsp_stream_t stream);
  * the server allocates (4 * nchan * (B + D16 + 64, rounded up to 128)
  * bytes each; set the mode before admitting beams, so admission sees the
  * memory), and each group of slots is dedispersed by one launch of the
- * interleaved kernel; the search is the same.  Synchronises the device.
+ * interleaved kernel; the search is the same.  The mode also sets the
+ * series slots (16 for the relayout mode, staging_slots for the
+ * interleaved one; 4 * ndm * (C + B) bytes each).  Synchronises the device.
  * DDSP_E_INVALID_ARG for an unknown mode, a slot count outside 1..16 or a
  * shape no interleaved tile fits (the time tile must divide the block);
  * DDSP_E_NOMEM if the slots cannot be allocated.  Both modes compute the

@@ -714,6 +714,9 @@ class Server:
                    "ddsp_server_info")
         (self.beam_bytes, self.ring_samples, self.series_cols, self.carry,
          self.first_delay) = (a.value for a in v)
+        # a beam's ring holds the B + D16 samples a step reads plus one
+        # block: one block per beam may wait for a step
+        self.max_waiting = 1
 
     RELAYOUT = 0
     INTERLEAVED = 1
@@ -757,8 +760,8 @@ class Server:
 
     def push(self, beam, x, stream=None):
         """Ingest beam `beam`'s next block (CUDA uint8 [block][nchan]);
-        returns False (nothing done) if the beam already has two blocks
-        waiting for steps."""
+        returns False (nothing done) if the beam's previous block has not
+        been taken by a step yet."""
         import torch
         rc = _lib.lib().ddsp_server_push(self._h, int(beam),
                                          _dev_ptr(x, torch.uint8, "block"),
@@ -802,8 +805,10 @@ class Server:
         return buf[:n.value].copy(), n.value, t0.value
 
     def series(self, beam):
-        """The beam's series [ndm][carry + block] as a CUDA int32 tensor view
-        (the last stepped block's, once its step completed)."""
+        """The series [ndm][carry + block] of the beam's last stepped block as
+        a CUDA int32 view of its series slot (once its step completed), while
+        it is still there: only blocks of the last group of the latest step
+        (DdspError DDSP_E_STATE otherwise); the next step reuses the slot."""
         import torch
         ptr, ncols = C.c_void_p(), C.c_int64()
         _lib.check(_lib.lib().ddsp_server_series(self._h, int(beam), C.byref(ptr),

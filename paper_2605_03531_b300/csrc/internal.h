@@ -218,13 +218,27 @@ cudaError_t launch_sps(const Plan &p, const int32_t *d_series,
 
 int64_t sps_max_window_samples();
 
+// Opt kernel `func` in to the largest dynamic shared memory the device
+// allows (its static shared memory deducted), once per (device, kernel).
+// Every launcher of a kernel shares the setting and nothing lowers it; a
+// launch still gets only the dynamic size it asks for.
+cudaError_t smem_opt_in(const void *func);
+template <typename F>
+cudaError_t smem_opt_in(F *func) {
+  return smem_opt_in(reinterpret_cast<const void *>(func));
+}
+
 int persistent_blocks_per_sm(const DedispTile &t, size_t smem);
 cudaError_t launch_batch_reset(int *d_queue, int nqueues,
                                uint32_t *const *d_counts, int ncounts,
                                cudaStream_t s);
-cudaError_t launch_serve_prep(const SpsBeam *d_beams, int nbeams, int ndm,
-                              int64_t n, int carry, int *d_queue,
-                              cudaStream_t s);
+// A streaming group's carry: in (d_queue reset, each beam's candidate count
+// reset, carry[b][k][0, C) -> series[b][k][0, C)) before its dedispersion,
+// or out (series[b][k][n - C, n) -> carry[b][k]) after it.
+cudaError_t launch_serve_carry(const SpsBeam *d_beams,
+                               int32_t *const *d_carry, int nbeams, int ndm,
+                               int64_t n, int carry, bool in, int *d_queue,
+                               cudaStream_t s);
 cudaError_t launch_dedisperse_persistent(const DedispTile &t,
                                          const WsBeam *d_beams,
                                          const int4 *d_items, int nitems,

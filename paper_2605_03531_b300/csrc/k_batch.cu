@@ -1,7 +1,7 @@
 // k_batch.cu -- many beams of uneven shape dedispersed in one persistent
 // launch (the batched form of Sec.3.2), plus the small kernels that start a
-// batch step (queue and count reset) and a streaming step (the same, plus
-// the boxcar carry of every beam's series).
+// batch step (queue and count reset) and a streaming group (the same, plus
+// the boxcar carry of every beam in and out of its series slot).
 //
 // A grid of (SMs x resident blocks) blocks loops: one thread takes the next
 // work item from a device queue (atomicAdd on a counter), the block runs it
@@ -63,27 +63,34 @@ __global__ void batch_reset_kernel(int *queue, int nqueues,
   if (i < ncounts) *counts[i] = 0;
 }
 
-// Streaming step prologue: reset the queue and each beam's candidate count,
-// and move the last `carry` samples of every series row to its front (the
-// boxcars of the next block start there).  Rows are n samples, n and carry
-// multiples of 4, n >= 2 * carry; one int4 per thread.
-__global__ void serve_prep_kernel(const SpsBeam *__restrict__ beams,
-                                  int nbeams, int ndm, int64_t n, int carry,
-                                  int *queue) {
+// Streaming group carry.  in: reset the queue and each beam's candidate
+// count and copy the beam's carry (the last `carry` outputs of its previous
+// block) to the front of its series slot; out: copy the series' last
+// `carry` samples back to the beam's carry for its next block.  Rows are n
+// samples, n and carry multiples of 4, n >= 2 * carry; one int4 per thread.
+__global__ void serve_carry_kernel(const SpsBeam *__restrict__ beams,
+                                   int32_t *const *__restrict__ carries,
+                                   int nbeams, int ndm, int64_t n, int carry,
+                                   bool in, int *queue) {
   const int64_t q = carry / 4;
   const int64_t total = (int64_t)nbeams * ndm * q;
   const int64_t i0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i0 == 0) *queue = 0;
-  if (i0 < nbeams) *beams[i0].count = 0;
+  if (in) {
+    if (i0 == 0) *queue = 0;
+    if (i0 < nbeams) *beams[i0].count = 0;
+  }
   for (int64_t i = i0; i < total; i += (int64_t)gridDim.x * blockDim.x) {
     const int b = (int)(i / ((int64_t)ndm * q));
     const int64_t rem = i - (int64_t)b * ndm * q;
     const int64_t row = rem / q, c4 = rem - row * q;
-    // the search only reads the series; this prologue is its one writer
+    // the search only reads the series; this kernel is its one writer
     // besides the dedispersion
     int32_t *x = const_cast<int32_t *>(beams[b].series) + row * n;
-    reinterpret_cast<int4 *>(x)[c4] =
-        reinterpret_cast<const int4 *>(x + n - carry)[c4];
+    int4 *cy = reinterpret_cast<int4 *>(carries[b] + row * carry);
+    if (in)
+      reinterpret_cast<int4 *>(x)[c4] = cy[c4];
+    else
+      cy[c4] = reinterpret_cast<const int4 *>(x + n - carry)[c4];
   }
 }
 
@@ -94,13 +101,8 @@ cudaError_t launch_persistent_t(const WsBeam *d_beams, const int4 *d_items,
                                 size_t smem, int32_t *d_err, int grid,
                                 cudaStream_t s) {
   auto kern = dedisp_persistent_kernel<WT, WD, RD>;
-  static size_t attr_bytes = 0;
-  if (smem > attr_bytes) {
-    cudaError_t e = cudaFuncSetAttribute(
-        kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_bytes = smem;
-  }
+  cudaError_t e = smem_opt_in(kern);
+  if (e != cudaSuccess) return e;
   const long long timeout = 4000000000LL;  // ~2 s of SM clock
   kern<<<grid, 32 * (WT * WD + kWsProdWarps), smem, s>>>(
       d_beams, d_items, nitems, ipb, ndt, d_queue, nbuf, d_err, timeout);
@@ -116,8 +118,7 @@ int persistent_blocks_per_sm(const DedispTile &t, size_t smem) {
 #define DDSP_OCC(WT_, WD_, RD_)                                                \
   if (t.wt == WT_ && t.wd == WD_ && t.rd == RD_) {                             \
     auto k = dedisp_persistent_kernel<WT_, WD_, RD_>;                          \
-    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
-                             (int)smem);                                       \
+    e = smem_opt_in(k);                                                        \
     if (e == cudaSuccess)                                                      \
       e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(                       \
           &n, k, 32 * (WT_ * WD_ + kWsProdWarps), smem);                       \
@@ -128,14 +129,15 @@ int persistent_blocks_per_sm(const DedispTile &t, size_t smem) {
   return e == cudaSuccess ? n : 0;
 }
 
-cudaError_t launch_serve_prep(const SpsBeam *d_beams, int nbeams, int ndm,
-                              int64_t n, int carry, int *d_queue,
-                              cudaStream_t s) {
+cudaError_t launch_serve_carry(const SpsBeam *d_beams,
+                               int32_t *const *d_carry, int nbeams, int ndm,
+                               int64_t n, int carry, bool in, int *d_queue,
+                               cudaStream_t s) {
   const int64_t total = std::max<int64_t>((int64_t)nbeams * ndm * (carry / 4),
                                           nbeams);
   const int64_t blocks = std::min<int64_t>((total + 255) / 256, 148 * 16);
-  serve_prep_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, s>>>(
-      d_beams, nbeams, ndm, n, carry, d_queue);
+  serve_carry_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, s>>>(
+      d_beams, d_carry, nbeams, ndm, n, carry, in, d_queue);
   return cudaGetLastError();
 }
 

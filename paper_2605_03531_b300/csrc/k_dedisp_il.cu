@@ -338,17 +338,14 @@ cudaError_t launch_il_t(const IlLaunch &p, int64_t ypitch, int64_t nsamp_out,
                         size_t smem, int64_t out_pitch, const IlRows *rows,
                         int nrows) {
   auto kern = dedisp_il_kernel<WT, WD, RD, E, T>;
-  static size_t attr_bytes = 0;
-  if (smem > attr_bytes) {
-    cudaError_t e = cudaFuncSetAttribute(
-        kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  {
+    cudaError_t e = smem_opt_in(kern);
     // the largest shared-memory carveout, so two blocks fit beside each other
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(kern,
                                cudaFuncAttributePreferredSharedMemoryCarveout,
                                (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
-    attr_bytes = smem;
   }
   constexpr int SPE = 4 / sizeof(T);
   constexpr int TT = SPE * 32 * E * WT;

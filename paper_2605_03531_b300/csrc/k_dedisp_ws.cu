@@ -25,12 +25,9 @@ cudaError_t launch_ws_t(const Plan &p, const void *d_cm, int64_t pitch,
                         int64_t nsamp_out, int32_t *d_out, cudaStream_t s,
                         int rawmax, int elmax, size_t smem) {
   auto kern = dedisp_ws_kernel<WT, WD, RD, T>;
-  static size_t attr_bytes = 0;
-  if (smem > attr_bytes) {
-    cudaError_t e = cudaFuncSetAttribute(
-        kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  {
+    cudaError_t e = smem_opt_in(kern);
     if (e != cudaSuccess) return e;
-    attr_bytes = smem;
   }
   constexpr int SPE = 4 / sizeof(T);
   constexpr int TT = SPE * 32 * kElemPerThread * WT;

@@ -269,12 +269,9 @@ cudaError_t launch_dered(const int32_t *d_in, int64_t nrows, int64_t n,
   size_t smem = 0;
   const int T = dered_chunk(h, &smem);
   if (T == 0) return cudaErrorInvalidValue;
-  static size_t attr = 0;
-  if (smem > attr) {
-    cudaError_t e = cudaFuncSetAttribute(
-        dered_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  {
+    cudaError_t e = smem_opt_in(dered_kernel);
     if (e != cudaSuccess) return e;
-    attr = smem;
   }
   const int ns_max = (int)std::min<int64_t>(n, T + 2 * h);
   dim3 grid((unsigned)((n + T - 1) / T), (unsigned)nrows);

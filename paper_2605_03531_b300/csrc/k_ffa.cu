@@ -258,8 +258,7 @@ extern "C" int ddsp_ffa(ddsp_plan *h, const int32_t *d_series, int64_t nrows,
   *m_out = m;
   DeviceGuard g(h->p.device);
   const size_t smem = (size_t)2 * m * p * 4;
-  cudaError_t e = cudaFuncSetAttribute(
-      ffa_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = smem_opt_in(ffa_kernel);
   if (e != cudaSuccess) return cuda_rc(e);
   ffa_kernel<<<(unsigned)nrows, kFfaThreads, smem,
                reinterpret_cast<cudaStream_t>(stream)>>>(d_series, nsamp, pitch,
@@ -294,9 +293,7 @@ extern "C" int ddsp_ffa_search(ddsp_plan *h, const int32_t *d_series,
     smem = std::max(smem, (size_t)(2 * st * 4));
   }
   DeviceGuard g(h->p.device);
-  cudaError_t e = cudaFuncSetAttribute(
-      ffa_search_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-      (int)smem);
+  cudaError_t e = smem_opt_in(ffa_search_kernel);
   if (e != cudaSuccess) return cuda_rc(e);
   dim3 grid((unsigned)(p_hi - p_lo), (unsigned)nrows);
   ffa_search_kernel<<<grid, kFfaThreads, smem,

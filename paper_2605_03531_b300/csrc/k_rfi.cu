@@ -470,8 +470,7 @@ extern "C" int ddsp_rfi_clean(ddsp_rfi *r, const uint8_t *d_in, int64_t nsamp,
   DeviceGuard g(r->device);
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const size_t csmem = (size_t)2 * nchan * 8;
-  cudaError_t ea = cudaFuncSetAttribute(
-      rfi_chan_stats, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)csmem);
+  cudaError_t ea = smem_opt_in(rfi_chan_stats);
   if (ea != cudaSuccess) return cuda_rc(ea);
   cudaError_t e = cudaMemsetAsync(r->fc, 0, (size_t)nchan, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(r->ft, 0, (size_t)nsamp, s);

@@ -23,8 +23,6 @@
 // and 16 bytes per candidate: the kernel is bounded by HBM bandwidth.
 #include <math.h>
 
-#include <mutex>
-
 #include "internal.h"
 
 namespace ddsp {
@@ -746,35 +744,17 @@ size_t sps_smem_bytes(int64_t maxlen, int wmax) {
   return kBufOff + 4 * (size_t)(maxlen + wmax + 4);
 }
 
-// The search kernels' opt-in to dynamic shared memory beyond 48 KB, made
-// once per device for the largest window the search accepts (the launch's
-// own size still decides what a block gets).  Plan, batch, server and
-// allocation-free launches share it, and it is never lowered, so a short
-// window's launch cannot undo a long window's setting.
-constexpr int kSpsOptDevices = 64;
+// Largest dynamic shared memory a search launch asks for (the largest
+// window the search accepts); the kernels are opted in to the device's
+// limit once (smem_opt_in), shared by plan, batch, server and
+// allocation-free launches and never lowered.
 constexpr size_t kSpsMaxSmem = kBufOff + 4 * (size_t)(kMaxWindowSamples + 4);
-
-template <typename Kern>
-cudaError_t sps_opt_in(Kern kern, int which) {
-  static std::mutex mu;
-  static bool done[kSpsOptDevices][3] = {};
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kSpsOptDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(mu);
-  if (done[dev][which]) return cudaSuccess;
-  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)kSpsMaxSmem);
-  if (e == cudaSuccess) done[dev][which] = true;
-  return e;
-}
 
 cudaError_t launch_sps_batch(const SpsBeam *d_beams, int nbeams,
                              int64_t total_blocks, float threshold,
                              size_t smem, cudaStream_t s) {
   if (smem > kSpsMaxSmem) return cudaErrorInvalidValue;
-  cudaError_t e = sps_opt_in(sps_batch_kernel, 2);
+  cudaError_t e = smem_opt_in(sps_batch_kernel);
   if (e != cudaSuccess) return e;
   sps_batch_kernel<<<(unsigned)total_blocks, kSpsThreads, smem, s>>>(
       d_beams, nbeams, threshold);
@@ -794,7 +774,7 @@ cudaError_t launch_sps(const Plan &p, const int32_t *d_series,
       kBufOff + 4 * (size_t)(maxlen + wmax + 4);
   if (smem > kSpsMaxSmem) return cudaErrorInvalidValue;
   auto kern = dense ? sps_kernel<true> : sps_kernel<false>;
-  cudaError_t e = sps_opt_in(kern, dense ? 1 : 0);
+  cudaError_t e = smem_opt_in(kern);
   if (e != cudaSuccess) return e;
   dim3 grid((unsigned)nwin, (unsigned)p.ndm);
   kern<<<grid, kSpsThreads, smem, s>>>(
@@ -909,7 +889,7 @@ extern "C" int ddsp_single_pulse_search_noalloc(
   cudaStream_t s = (cudaStream_t)stream;
   const size_t smem = kBufOff + 4 * (size_t)(maxlen + wmax + 4);
   auto kern = sps_kernel<false>;
-  if (smem > kSpsMaxSmem || sps_opt_in(kern, 0) != cudaSuccess)
+  if (smem > kSpsMaxSmem || smem_opt_in(kern) != cudaSuccess)
     return DDSP_E_CUDA;
   // the array keeps the previous call's contents: one small launch resets
   // what must start at zero (the caller's counter and the error word) and

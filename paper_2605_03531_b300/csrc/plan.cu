@@ -8,6 +8,9 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
+#include <set>
+#include <utility>
 #include <new>
 #include <numeric>
 #include <vector>
@@ -21,6 +24,26 @@ namespace ddsp {
 constexpr double kDispersionConst = 4148.808;  // s MHz^2 per (pc cm^-3)
 
 thread_local char g_detail[256] = "";
+
+cudaError_t smem_opt_in(const void *func) {
+  static std::mutex mu;
+  static std::set<std::pair<int, const void *>> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  if (done.count({dev, func})) return cudaSuccess;
+  int optin = 0;
+  cudaFuncAttributes fa;
+  if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin,
+                                  dev)) != cudaSuccess ||
+      (e = cudaFuncGetAttributes(&fa, func)) != cudaSuccess)
+    return e;
+  e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           optin - (int)fa.sharedSizeBytes);
+  if (e == cudaSuccess) done.insert({dev, func});
+  return e;
+}
 
 int cuda_rc(cudaError_t e) {
   if (e == cudaSuccess) return DDSP_OK;

@@ -4,22 +4,28 @@
 // the GPU is free, alongside whatever other beams have a block waiting).
 //
 // Per beam the server holds
-//   * a channel-major ring of `slots` blocks (slots = ceil(D16 / B) + 2, D16 =
-//     the largest delay rounded up to 16 samples) whose rows carry past the
+//   * a channel-major ring of `slots` blocks (slots = ceil(D16 / B) + 1, D16 =
+//     the largest delay rounded up to 16 samples: the B + D16 input samples a
+//     block's step reads plus the rest of one block) whose rows carry past the
 //     ring a copy of their first M bytes, M >= the longest window one
 //     dedispersion work item stages, so a staged window never wraps;
-//   * a series [ndm][C + B]: C = the widest boxcar minus one, rounded up to 4,
-//     carried over from the previous block so every boxcar that starts in the
-//     new block is complete;
+//   * the carry [ndm][C]: the last C output samples of the previous block
+//     (C = the widest boxcar minus one, rounded up to 4), so every boxcar that
+//     starts in the new block is complete;
 //   * per-window statistics and two candidate buffers (by block parity), so a
 //     block's candidates can be read while the next block is processed.
+// The series [ndm][C + B] a block is searched on lives only during its step,
+// in one of G series slots the server shares among the beams (G = the
+// group size: a step runs its beam-blocks in groups of G, each group's
+// carry in, dedispersion, search and carry out one after the other), so a
+// beam costs its ring and a few MB, not a series of its own.
 // Block j's input lands in slot j % slots.  Its step dedisperses output
 // samples [s_j, s_j + B) with s_j = j*B - D16 (input [s_j, s_j + B + D) is
-// then resident: blocks j-slots+2 .. j), writing series columns [C, C + B),
+// then resident: blocks j-slots+1 .. j), writing series columns [C, C + B),
 // and searches start times [0, B) of the whole series (global time
 // s_j - C + t).  Samples before the stream's start read as zero.  Pushing
 // block j overwrites the slot of block j - slots, which the step of block
-// j - 2 is the last to read, so a push waits for that step.
+// j - 1 is the last to read, so a push waits for that step.
 #include <math.h>
 #include <string.h>
 
@@ -36,10 +42,14 @@ namespace {
 
 constexpr int kStepEvents = 64;
 
+// Series slots of the relayout mode's groups (one persistent launch each).
+constexpr int kRelayoutGroup = 16;
+
 struct ServerBeam {
   bool live = false;
   uint8_t *ring = nullptr;      // [nchan][pitch]
-  int32_t *series = nullptr;    // [ndm][ncols]
+  int32_t *carry = nullptr;     // [ndm][C]
+  int series_slot = -1;         // series slot of the last step (G slots)
   int64_t *m2 = nullptr, *mad4 = nullptr;
   ddsp_cand *cands = nullptr;   // [2][cap]
   int64_t pushed = 0;           // blocks ingested
@@ -69,8 +79,13 @@ struct ddsp_server {
   int *d_queue = nullptr;
   WsBeam *d_wsb[2] = {nullptr, nullptr};
   SpsBeam *d_sb[2] = {nullptr, nullptr};
+  int32_t **d_carry[2] = {nullptr, nullptr};
   WsBeam *h_wsb[2] = {nullptr, nullptr};   // pinned staging of a step's
   SpsBeam *h_sb[2] = {nullptr, nullptr};   // descriptors, by step parity
+  int32_t **h_carry[2] = {nullptr, nullptr};
+  // series slots [G][ndm][ncols] shared by the beam-blocks of a group
+  int G = 0;
+  int32_t *d_pool = nullptr;
   cudaEvent_t ev_step[kStepEvents] = {};
   int64_t nsteps = 0;
   int64_t npushes = 0;
@@ -95,13 +110,13 @@ int64_t floor_mod(int64_t a, int64_t m) {
 
 int64_t beam_bytes(const ddsp_server &S) {
   const Plan &p = S.plan->p;
-  return (int64_t)p.nchan * S.pitch + (int64_t)p.ndm * S.ncols * 4 +
+  return (int64_t)p.nchan * S.pitch + (int64_t)p.ndm * S.C * 4 +
          2 * (int64_t)p.ndm * S.nwin * 8 + 2 * (int64_t)S.cap * 16;
 }
 
 void free_beam(ServerBeam &b) {
   cudaFree(b.ring);
-  cudaFree(b.series);
+  cudaFree(b.carry);
   cudaFree(b.m2);
   cudaFree(b.mad4);
   cudaFree(b.cands);
@@ -116,14 +131,17 @@ void server_release(ddsp_server &S) {
   free_tables(S.tab);
   free_tables(S.il_tab);
   cudaFree(S.d_il);
+  cudaFree(S.d_pool);
   cudaFree(S.d_counts);
   cudaFree(S.d_err);
   cudaFree(S.d_queue);
   for (int i = 0; i < 2; ++i) {
     cudaFree(S.d_wsb[i]);
     cudaFree(S.d_sb[i]);
+    cudaFree(S.d_carry[i]);
     cudaFreeHost(S.h_wsb[i]);
     cudaFreeHost(S.h_sb[i]);
+    cudaFreeHost(S.h_carry[i]);
   }
   for (auto &e : S.ev_step)
     if (e) cudaEventDestroy(e);
@@ -133,6 +151,25 @@ void server_release(ddsp_server &S) {
 // wait on it longer, never wrong: steps complete in order).
 cudaEvent_t step_event(const ddsp_server &S, int64_t id) {
   return S.ev_step[id % kStepEvents];
+}
+
+// (Re)allocate the G series slots; nothing may be running on them.
+int set_pool(ddsp_server &S, int G) {
+  const Plan &p = S.plan->p;
+  cudaDeviceSynchronize();
+  cudaFree(S.d_pool);
+  S.d_pool = nullptr;
+  S.G = 0;
+  cudaError_t e = cudaMalloc(&S.d_pool, (size_t)G * p.ndm * S.ncols * 4);
+  if (e != cudaSuccess) return cuda_rc(e);
+  S.G = G;
+  for (auto &b : S.beams) b.series_slot = -1;
+  return DDSP_OK;
+}
+
+int32_t *pool_slot(const ddsp_server &S, int q) {
+  const Plan &p = S.plan->p;
+  return S.d_pool + (size_t)q * p.ndm * S.ncols;
 }
 
 // Candidates tiles tried in order when the caller leaves the choice to the
@@ -195,14 +232,14 @@ DedispTile server_il_tile(const ddsp_server &S) {
                               [&](int dt) { return span_for(p, dt); });
 }
 
-// The interleaved mode's dedispersion of n waiting beam-blocks, groups of
-// il_slots at a time: each block's window of its ring (logical samples
-// [0, B + D16) from ring position t0) is interleaved into a slot, then one
-// launch covers the group (blockIdx.z = slot).  Stream order keeps a slot's
-// next interleave behind the launch that read it.
-cudaError_t server_dedisperse_il(ddsp_server &S, const std::vector<int> &beams,
-                                 const std::vector<int64_t> &t0,
-                                 cudaStream_t s) {
+// The interleaved mode's dedispersion of one group of n <= il_slots waiting
+// beam-blocks: each block's window of its ring (logical samples [0, B + D16)
+// from ring position t0) is interleaved into a staging slot, then one launch
+// covers the group (blockIdx.z = slot) and writes series slot q's columns
+// [C, C + B).  Stream order keeps a slot's next interleave behind the launch
+// that read it.
+cudaError_t server_dedisperse_il(ddsp_server &S, const int *beams,
+                                 const int64_t *t0, int n, cudaStream_t s) {
   const Plan &p = S.plan->p;
   IlLaunch v;
   v.tile = S.il_tile;
@@ -211,21 +248,17 @@ cudaError_t server_dedisperse_il(ddsp_server &S, const std::vector<int> &beams,
   v.nbits = 8;
   v.d_err = S.d_err;
   cudaError_t e = cudaSuccess;
-  const int n = (int)beams.size();
-  for (int g0 = 0; g0 < n && e == cudaSuccess; g0 += S.il_slots) {
-    const int gn = std::min(S.il_slots, n - g0);
-    IlRows rows[kIlMaxRows];
-    for (int q = 0; q < gn && e == cudaSuccess; ++q) {
-      const ServerBeam &b = S.beams[beams[g0 + q]];
-      uint8_t *slot = S.d_il + (size_t)q * S.slot_bytes;
-      e = launch_interleave(v, b.ring, S.pitch, S.B + S.D16, S.ypitch, s, S.R,
-                            t0[g0 + q], slot);
-      rows[q].y = reinterpret_cast<const uint32_t *>(slot);
-      rows[q].out = b.series + S.C;
-    }
-    if (e == cudaSuccess)
-      e = launch_dedisperse_il_rows(v, S.ypitch, S.B, S.ncols, rows, gn, s);
+  IlRows rows[kIlMaxRows];
+  for (int q = 0; q < n && e == cudaSuccess; ++q) {
+    const ServerBeam &b = S.beams[beams[q]];
+    uint8_t *slot = S.d_il + (size_t)q * S.slot_bytes;
+    e = launch_interleave(v, b.ring, S.pitch, S.B + S.D16, S.ypitch, s, S.R,
+                          t0[q], slot);
+    rows[q].y = reinterpret_cast<const uint32_t *>(slot);
+    rows[q].out = pool_slot(S, q) + S.C;
   }
+  if (e == cudaSuccess)
+    e = launch_dedisperse_il_rows(v, S.ypitch, S.B, S.ncols, rows, n, s);
   return e;
 }
 
@@ -242,6 +275,8 @@ int ddsp_server_set_mode(ddsp_server *S, int mode, int staging_slots) {
   DeviceGuard g(S->device);
   cudaDeviceSynchronize();   // no step may still read the staging slots
   if (mode == DDSP_SERVER_RELAYOUT) {
+    const int rc = set_pool(*S, kRelayoutGroup);
+    if (rc != DDSP_OK) return rc;
     free_tables(S->il_tab);
     cudaFree(S->d_il);
     S->d_il = nullptr;
@@ -262,6 +297,12 @@ int ddsp_server_set_mode(ddsp_server *S, int mode, int staging_slots) {
   if (e != cudaSuccess) {
     free_tables(tab);
     return cuda_rc(e);
+  }
+  rc = set_pool(*S, staging_slots);
+  if (rc != DDSP_OK) {
+    free_tables(tab);
+    cudaFree(d_il);
+    return rc;
   }
   free_tables(S->il_tab);
   cudaFree(S->d_il);
@@ -300,7 +341,7 @@ int ddsp_server_create(ddsp_server **out, ddsp_plan *plan,
   S->B = block_samples;
   S->C = round_up(p.widths.back() - 1, 4);
   S->D16 = round_up(p.max_delay, 16);
-  S->slots = (int)((S->D16 + S->B - 1) / S->B) + 2;
+  S->slots = (int)((S->D16 + S->B - 1) / S->B) + 1;
   S->R = S->slots * S->B;
   S->ncols = S->C + S->B;
   S->max_beams = max_beams;
@@ -344,7 +385,9 @@ int ddsp_server_create(ddsp_server **out, ddsp_plan *plan,
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
       if ((e = cudaMalloc(&S->d_wsb[i], max_beams * sizeof(WsBeam))) == cudaSuccess &&
           (e = cudaMalloc(&S->d_sb[i], max_beams * sizeof(SpsBeam))) == cudaSuccess &&
-          (e = cudaMallocHost(&S->h_wsb[i], max_beams * sizeof(WsBeam))) == cudaSuccess)
+          (e = cudaMalloc(&S->d_carry[i], max_beams * sizeof(int32_t *))) == cudaSuccess &&
+          (e = cudaMallocHost(&S->h_wsb[i], max_beams * sizeof(WsBeam))) == cudaSuccess &&
+          (e = cudaMallocHost(&S->h_carry[i], max_beams * sizeof(int32_t *))) == cudaSuccess)
         e = cudaMallocHost(&S->h_sb[i], max_beams * sizeof(SpsBeam));
     }
     if (e == cudaSuccess &&
@@ -358,6 +401,7 @@ int ddsp_server_create(ddsp_server **out, ddsp_plan *plan,
       e = cudaMemset(S->d_err, 0, sizeof(int32_t));
     }
     if (e != cudaSuccess) rc = cuda_rc(e);
+    if (rc == DDSP_OK) rc = set_pool(*S, kRelayoutGroup);
   }
   if (rc != DDSP_OK) {
     server_release(*S);
@@ -416,14 +460,14 @@ int ddsp_server_admit(ddsp_server *S, int *beam) {
   const Plan &p = S->plan->p;
   ServerBeam b;
   if ((e = cudaMalloc(&b.ring, (size_t)p.nchan * S->pitch)) == cudaSuccess &&
-      (e = cudaMalloc(&b.series, (size_t)p.ndm * S->ncols * 4)) == cudaSuccess &&
+      (e = cudaMalloc(&b.carry, (size_t)p.ndm * S->C * 4)) == cudaSuccess &&
       (e = cudaMalloc(&b.m2, (size_t)p.ndm * S->nwin * 8)) == cudaSuccess &&
       (e = cudaMalloc(&b.mad4, (size_t)p.ndm * S->nwin * 8)) == cudaSuccess &&
       (e = cudaMalloc(&b.cands, 2 * (size_t)S->cap * sizeof(ddsp_cand))) == cudaSuccess &&
       (e = cudaEventCreateWithFlags(&b.ev_push[0], cudaEventDisableTiming)) == cudaSuccess &&
       (e = cudaEventCreateWithFlags(&b.ev_push[1], cudaEventDisableTiming)) == cudaSuccess &&
       (e = cudaMemset(b.ring, 0, (size_t)p.nchan * S->pitch)) == cudaSuccess)
-    e = cudaMemset(b.series, 0, (size_t)p.ndm * S->ncols * 4);
+    e = cudaMemset(b.carry, 0, (size_t)p.ndm * S->C * 4);
   if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (e != cudaSuccess) {
     free_beam(b);
@@ -451,12 +495,12 @@ int ddsp_server_push(ddsp_server *S, int beam, const void *d_block,
     return DDSP_E_INVALID_ARG;
   ServerBeam &b = S->beams[beam];
   const int64_t j = b.pushed;
-  // the slot of block j - slots is read last by the step of block j - 2
-  if (j >= 2 && b.processed < j - 1) return DDSP_E_STATE;
+  // the slot of block j - slots is read last by the step of block j - 1
+  if (j >= 1 && b.processed < j) return DDSP_E_STATE;
   DeviceGuard g(S->device);
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e = cudaSuccess;
-  if (j >= 2) e = cudaStreamWaitEvent(s, step_event(*S, b.step_of[(j - 2) % 4]), 0);
+  if (j >= 1) e = cudaStreamWaitEvent(s, step_event(*S, b.step_of[(j - 1) % 4]), 0);
   const Plan &p = S->plan->p;
   const int64_t slot = j % S->slots;
   // only the slot's columns (and the mirror's) are written
@@ -506,11 +550,15 @@ int ddsp_server_step(ddsp_server *S, float threshold, int max_beams_in_step,
     ready.resize(max_beams_in_step);
   int n = 0;
   std::vector<int64_t> t0s;
+  std::vector<int> members;
   for (int i : ready) {
     ServerBeam &b = S->beams[i];
     const int64_t j = b.processed;
     if ((e = cudaStreamWaitEvent(s, b.ev_push[j & 1], 0)) != cudaSuccess)
       return cuda_rc(e);
+    // series slot q of its group (groups of G beam-blocks in step order)
+    const int q = n % S->G;
+    int32_t *series = pool_slot(*S, q);
     WsBeam &w = S->h_wsb[par][n];
     memset(&w, 0, sizeof(w));
     w.cm = b.ring;
@@ -519,34 +567,36 @@ int ddsp_server_step(ddsp_server *S, float threshold, int max_beams_in_step,
     w.ring = S->R;
     w.t0 = floor_mod(j * S->B - S->D16, S->R);
     t0s.push_back(w.t0);
+    members.push_back(i);
     w.out_pitch = S->ncols;
     w.desc = reinterpret_cast<const int2 *>(S->tab.d_desc);
     w.relb = S->tab.d_relb;
     w.rowmap = S->tab.d_rowmap;
-    w.out = b.series + S->C;
+    w.out = series + S->C;
     w.nchan = p.nchan;
     w.n_dm_tiles = S->tab.n_dm_tiles;
     w.n_time_tiles = S->ntt;
     w.cc = S->cc;
     w.rawmax = S->rawmax;
     w.elmax = S->elmax;
-    SpsBeam &q = S->h_sb[par][n];
-    memset(&q, 0, sizeof(q));
-    q.series = b.series;
-    q.widths = p.d_widths;
-    q.m2 = b.m2;
-    q.mad4 = b.mad4;
-    q.cands = b.cands + (size_t)(j & 1) * S->cap;
-    q.count = S->d_counts + 2 * i + (j & 1);
-    q.err = S->d_err;
-    q.n = S->ncols;
-    q.L = p.norm_window;
-    q.nwin = S->nwin;
-    q.block0 = (int64_t)n * p.ndm * S->nwin;
-    q.nrep = S->B;
-    q.ndm = p.ndm;
-    q.nw = p.nwidths;
-    q.cap = S->cap;
+    SpsBeam &q_ = S->h_sb[par][n];
+    memset(&q_, 0, sizeof(q_));
+    q_.series = series;
+    q_.widths = p.d_widths;
+    q_.m2 = b.m2;
+    q_.mad4 = b.mad4;
+    q_.cands = b.cands + (size_t)(j & 1) * S->cap;
+    q_.count = S->d_counts + 2 * i + (j & 1);
+    q_.err = S->d_err;
+    q_.n = S->ncols;
+    q_.L = p.norm_window;
+    q_.nwin = S->nwin;
+    q_.block0 = (int64_t)q * p.ndm * S->nwin;   // within its group's launch
+    q_.nrep = S->B;
+    q_.ndm = p.ndm;
+    q_.nw = p.nwidths;
+    q_.cap = S->cap;
+    S->h_carry[par][n] = b.carry;
     if (beams_out && n < cap) beams_out[n] = i;
     ++n;
   }
@@ -560,27 +610,44 @@ int ddsp_server_step(ddsp_server *S, float threshold, int max_beams_in_step,
     e = cudaMemcpyAsync(S->d_sb[par], S->h_sb[par], n * sizeof(SpsBeam),
                         cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
-    e = launch_serve_prep(S->d_sb[par], n, p.ndm, S->ncols, (int)S->C,
-                          S->d_queue, s);
-  const int64_t nitems = (int64_t)n * S->ipb;
-  if (e == cudaSuccess && nitems > 0x7fffffff) e = cudaErrorInvalidValue;
-  if (e == cudaSuccess && S->mode == DDSP_SERVER_INTERLEAVED) {
-    std::vector<int> bl(ready.begin(), ready.begin() + n);
-    e = server_dedisperse_il(*S, bl, t0s, s);
-  } else if (e == cudaSuccess) {
-    e = launch_dedisperse_persistent(
-        S->tile, S->d_wsb[par], nullptr, (int)nitems, S->ipb, S->tab.n_dm_tiles,
-        S->d_queue, S->smem, S->d_err, (int)std::min<int64_t>(S->grid, nitems), s);
+    e = cudaMemcpyAsync(S->d_carry[par], S->h_carry[par],
+                        n * sizeof(int32_t *), cudaMemcpyHostToDevice, s);
+  // groups of G beam-blocks, each through carry in, dedispersion, search and
+  // carry out on the G series slots
+  for (int g0 = 0; g0 < n && e == cudaSuccess; g0 += S->G) {
+    const int gn = std::min(S->G, n - g0);
+    const int64_t nitems = (int64_t)gn * S->ipb;
+    if (nitems > 0x7fffffff) e = cudaErrorInvalidValue;
+    if (e == cudaSuccess)
+      e = launch_serve_carry(S->d_sb[par] + g0, S->d_carry[par] + g0, gn,
+                             p.ndm, S->ncols, (int)S->C, true, S->d_queue, s);
+    if (e == cudaSuccess && S->mode == DDSP_SERVER_INTERLEAVED) {
+      e = server_dedisperse_il(*S, members.data() + g0, t0s.data() + g0, gn,
+                               s);
+    } else if (e == cudaSuccess) {
+      e = launch_dedisperse_persistent(
+          S->tile, S->d_wsb[par] + g0, nullptr, (int)nitems, S->ipb,
+          S->tab.n_dm_tiles, S->d_queue, S->smem, S->d_err,
+          (int)std::min<int64_t>(S->grid, nitems), s);
+    }
+    if (e == cudaSuccess)
+      e = launch_sps_batch(S->d_sb[par] + g0, gn,
+                           (int64_t)gn * p.ndm * S->nwin, threshold,
+                           S->sps_smem, s);
+    if (e == cudaSuccess)
+      e = launch_serve_carry(S->d_sb[par] + g0, S->d_carry[par] + g0, gn,
+                             p.ndm, S->ncols, (int)S->C, false, nullptr, s);
   }
-  if (e == cudaSuccess)
-    e = launch_sps_batch(S->d_sb[par], n, (int64_t)n * p.ndm * S->nwin,
-                         threshold, S->sps_smem, s);
   if (e == cudaSuccess) e = cudaEventRecord(step_event(*S, id), s);
   if (e != cudaSuccess) return cuda_rc(e);
-  for (int i : ready) {
-    ServerBeam &b = S->beams[i];
+  // only the last group's series are still in their slots after the step
+  for (auto &b : S->beams) b.series_slot = -1;
+  const int last0 = ((n - 1) / S->G) * S->G;
+  for (int k = 0; k < n; ++k) {
+    ServerBeam &b = S->beams[members[k]];
     b.step_of[b.processed % 4] = id;
     ++b.processed;
+    if (k >= last0) b.series_slot = k % S->G;
   }
   S->nsteps = id + 1;
   if (step_id) *step_id = id;
@@ -636,7 +703,9 @@ int ddsp_server_series(ddsp_server *S, int beam, int32_t **d_series,
   if (!S || beam < 0 || beam >= S->max_beams || !S->beams[beam].live ||
       !d_series)
     return DDSP_E_INVALID_ARG;
-  *d_series = S->beams[beam].series;
+  const int q = S->beams[beam].series_slot;
+  if (q < 0) return DDSP_E_STATE;
+  *d_series = pool_slot(*S, q);
   if (ncols) *ncols = S->ncols;
   return DDSP_OK;
 }

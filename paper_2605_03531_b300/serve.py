@@ -76,7 +76,8 @@ class ServingLoop:
 
     server: push(beam, x, stream) -> bool, step(threshold, max_beams_in_step,
         stream) -> (step id, beams), done(step id) -> bool,
-        fetch(beam, block, allow_truncated) -> (cands, count, t_start)
+        fetch(beam, block, allow_truncated) -> (cands, count, t_start),
+        max_waiting: blocks a beam may have pushed but not yet stepped
     beams: the server's beam index for each schedule row
     source(i, k): host block k of schedule row i
     stager: stage(host) -> (device block, token), consumed(token); None
@@ -102,6 +103,7 @@ class ServingLoop:
         self.poll = float(poll)
         self.on_candidates = on_candidates
         self.first_block = int(first_block)
+        self.max_waiting = int(getattr(server, "max_waiting", 1))
 
     def run(self, arrivals, time_limit=None):
         """Serve the schedule (arrivals[i][k] = seconds after the start at
@@ -140,10 +142,11 @@ class ServingLoop:
                 nexta += 1
                 busy = True
             # ingest in block order (a later block waits in host memory for
-            # a missing one); at most two blocks per beam wait for steps
+            # a missing one, or for a step to take the beam's block before
+            # it: the server holds max_waiting blocks per beam)
             for i in sorted(has_waiting):
                 while (waiting[i] and waiting[i][0] == pushed[i]
-                       and pushed[i] - stepped[i] < 2):
+                       and pushed[i] - stepped[i] < self.max_waiting):
                     k = waiting[i][0]
                     host = self.source(i, k)
                     if self.stager is not None:

@@ -67,7 +67,8 @@ def test_server_shape():
     srv = Server(p, B, 4)
     assert srv.carry == 64 and srv.series_cols == B + 64
     assert srv.first_delay == (p.max_delay + 15) // 16 * 16
-    assert srv.ring_samples == (-(-srv.first_delay // B) + 2) * B
+    assert srv.ring_samples == (-(-srv.first_delay // B) + 1) * B
+    assert srv.max_waiting == 1
     t = srv.get_tile()
     assert B % t["time_tile"] == 0 and t["chan_chunk"] >= 1
     srv.close()
@@ -89,13 +90,14 @@ def test_server_blocks_equal_plain_path_in_any_mix(mode):
     pushed = [0, 0, 0]
     stepped = [0, 0, 0]
     got_any = 0
+    series_checked = 0
 
     def push(i):
         assert srv.push(beams[i], xs[i][pushed[i] * B:(pushed[i] + 1) * B])
         pushed[i] += 1
 
     def step_and_check(expect):
-        nonlocal got_any
+        nonlocal got_any, series_checked
         sid, sb = srv.step(THR)
         assert sorted(sb) == sorted(beams[i] for i in expect)
         torch.cuda.synchronize()
@@ -103,7 +105,14 @@ def test_server_blocks_equal_plain_path_in_any_mix(mode):
         for i in expect:
             j = stepped[i]
             s_ref, c_ref = refs[i][j]
-            assert torch.equal(srv.series(beams[i]), s_ref), (i, j)
+            try:      # the series of the step's last group stay in their slots
+                s_got = srv.series(beams[i])
+            except DdspError as e:
+                assert e.code == _lib.DDSP_E_STATE
+                s_got = None
+            if s_got is not None:
+                assert torch.equal(s_got, s_ref), (i, j)
+                series_checked += 1
             c, n, t0 = srv.fetch(beams[i], j)
             assert t0 == j * B - srv.first_delay - srv.carry
             _same(c, c_ref)
@@ -112,19 +121,20 @@ def test_server_blocks_equal_plain_path_in_any_mix(mode):
 
     push(0); step_and_check([0])                      # alone
     push(1); push(2); step_and_check([1, 2])           # two together
-    push(0); push(0); push(1)                          # beam 0 two ahead
-    assert not srv.push(beams[0], xs[0][3 * B:4 * B])  # third waits
+    push(0); push(1)
+    # beam 0's next block waits until a step took the one before it
+    assert not srv.push(beams[0], xs[0][2 * B:3 * B])
     step_and_check([0, 1])
-    step_and_check([0])
+    push(0); step_and_check([0])
     push(2); push(1); push(0); step_and_check([0, 1, 2])
     while min(pushed) < NBLK:
         for i in range(3):
-            if pushed[i] < NBLK and pushed[i] - stepped[i] < 2:
+            if pushed[i] < NBLK and pushed[i] - stepped[i] < 1:
                 push(i)
         step_and_check([i for i in range(3) if pushed[i] > stepped[i]])
     while max(p - s for p, s in zip(pushed, stepped)) > 0:
         step_and_check([i for i in range(3) if pushed[i] > stepped[i]])
-    assert got_any > 0
+    assert got_any > 0 and series_checked >= NBLK
     srv.check()
     srv.close()
 

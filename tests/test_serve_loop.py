@@ -1,9 +1,9 @@
 """Host side of the streaming search: the seeded arrival schedule, the
 continuous-batching loop and the real-time limit search, run against a fake
 server on a simulated clock (no GPU).  The fake enforces the same rules as
-the library's server: at most two blocks per beam waiting for steps, a step
-takes the waiting block of the beams pushed first, a block's results can be
-read only while it is one of the beam's two latest stepped blocks."""
+the library's server: at most one block per beam waiting for a step, a step takes the
+waiting block of the beams pushed first, a block's results can be read only
+while it is one of the beam's two latest stepped blocks."""
 import math
 
 import numpy as np
@@ -40,11 +40,12 @@ class FakeServer:
         self.busy_until = 0.0
         self.step_of = {}
         self.fetched = []
+        self.max_waiting = 1
 
     def push(self, beam, x, stream=None):
         j = self.pushed[beam]
         assert x == (beam, j)
-        if j >= 2 and self.processed[beam] < j - 1:
+        if j >= 1 and self.processed[beam] < j:
             return False
         self.push_seq[(beam, j)] = self.nseq
         self.nseq += 1
