@@ -169,9 +169,11 @@ int ddsp_plan_cm_pitch(const ddsp_plan *plan, int64_t nsamp_out, int64_t *pitch)
  *     in FP32 (0 when MAD = 0), best = first width reaching the maximum;
  *   a candidate is every (k, t) whose best S/N >= threshold (> 0).
  * Candidates go to a plan-owned device buffer (capacity from plan creation);
- * read them with ddsp_candidates_fetch.  Windows are processed on chip, so
- * every window plus (max width - 1) samples must fit in 49152 samples;
- * DDSP_E_SHAPE otherwise.  Boxcar sums must fit in int32. */
+ * read them with ddsp_candidates_fetch.  A window of up to 49152 samples
+ * (with the max width - 1 samples after it) is searched on chip in one
+ * pass; longer windows (norm_window = 0 over a long series, or a long L)
+ * take two: an exact median / MAD pass over global memory, then the search
+ * in segments of 8192 start times.  Boxcar sums must fit in int32. */
 int ddsp_single_pulse_search(ddsp_plan *plan, const int32_t *d_series,
                              int64_t nsamp_out, float threshold,
                              ddsp_stream_t stream);
@@ -546,6 +548,40 @@ int ddsp_plan_get_tile(const ddsp_plan *plan, int *dm_tile,
                        int *dm_per_thread, int *time_tile, int *chan_chunk,
                        int *stages, int *flags);
 
+/* Tile autotuning of a single-beam plan, with a cache (no counterpart in
+ * the paper: which dedispersion tile shape runs fastest depends on the
+ * channel count, the DM grid's delay spans and the GPU).
+ * ddsp_plan_autotune: time the candidate tiles the plan's shape fits (the
+ * interleaved kernel with 16 or 8 consumer warps and 4..32 DM trials per
+ * tile, the relayout kernel), each the best of `reps` passes of
+ * ddsp_stage + ddsp_dedisperse_staged over the caller's block d_in (as in
+ * ddsp_dedisperse), keep the fastest on the plan, and, if cache_path is
+ * not NULL, record it in that JSON file under the plan's key, replacing an
+ * older entry of the key.  ms (cap entries, may be NULL) receives each
+ * candidate's best time in ms (-1: does not fit), *best (may be NULL) the
+ * winner's index.  Allocates a scratch output of ndm * N_out int32 for the
+ * time of the call; synchronises.  DDSP_E_SHAPE if N_out <= 0.
+ * ddsp_plan_tile_key: the key ("<GPU name>/nchan=.../nbits=.../ndm=.../
+ * D=.../span16=...", the largest delay span inside a 16-trial DM tile) into
+ * buf (cap bytes with the terminating 0; DDSP_E_INVALID_ARG if too short).
+ * ddsp_plan_create uses the tile cached under the new plan's key in the
+ * file named by the environment variable DDSP_TILE_CACHE, if there is one
+ * that fits, instead of its built-in choice.
+ * ddsp_tile_cache_get / _put: read or write one entry of a cache file on
+ * the host (tile = dm_tile, dm_per_thread, chan_chunk, stages, flags as
+ * ddsp_plan_set_tile takes them; keys without '"', '\\' or control
+ * characters); get returns DDSP_E_STATE when the key is absent and
+ * DDSP_E_INVALID_ARG for a file that does not parse; a missing file is an
+ * empty cache. */
+int ddsp_plan_autotune(ddsp_plan *plan, const void *d_in, int64_t nsamp_in,
+                       const char *cache_path, int reps,
+                       ddsp_stream_t stream, float *ms, int cap, int *best);
+int ddsp_plan_tile_key(const ddsp_plan *plan, char *buf, size_t cap);
+int ddsp_tile_cache_get(const char *path, const char *key, int *tile,
+                        float *ms);
+int ddsp_tile_cache_put(const char *path, const char *key, const int *tile,
+                        float ms);
+
 /* Failure detection of the dedispersion (no counterpart in the paper).
  * Every device wait of the staged kernels is bounded: when a bound runs out
  * the kernel records DDSP_E_TIMEOUT in the plan's error word, lets the
@@ -564,6 +600,16 @@ int ddsp_plan_get_tile(const ddsp_plan *plan, int *dm_tile,
  * below -1. */
 int ddsp_plan_set_wait_limit(ddsp_plan *plan, int64_t cycles);
 int ddsp_plan_withhold_copy(ddsp_plan *plan, int chunk);
+
+/* Bounds-checked build (no counterpart in the paper): the library compiled
+ * with -DDDSP_BOUNDS_CHECK (libddsp_bounds.so, for tests) checks the index
+ * of every shared- and global-memory access of the staging, interleave,
+ * dedispersion and search kernels against its buffer before making it; a
+ * failing check skips the access and records the first violation as
+ * (site << 32 | low 32 bits of the index) in one device word.  Synchronises
+ * the device, sets *enabled (1 in the checked build, 0 otherwise) and
+ * *violation (0: none), then clears the word. */
+int ddsp_bounds_check_status(int *enabled, uint64_t *violation);
 
 /* ------------------------------------------------------------------------
  * Unit peaks (measurement): microbenchmarks of the on-chip units the

@@ -17,7 +17,8 @@ from ._lib import DdspError, DdspCand
 
 
 __all__ = ["Plan", "Batch", "Server", "Cluster", "Rfi", "DdspError",
-           "CAND_DTYPE", "delay_table", "probe_unit_peaks"]
+           "CAND_DTYPE", "delay_table", "probe_unit_peaks", "tile_cache_get",
+           "tile_cache_put"]
 
 CAND_DTYPE = np.dtype([("dm_idx", np.uint32), ("t", np.uint32),
                        ("w_idx", np.uint32), ("snr", np.float32)])
@@ -60,6 +61,28 @@ def _dev_ptr(t, dtype=None, what="tensor"):
     if dtype is not None and t.dtype != dtype:
         raise TypeError(f"{what} must be {dtype}, got {t.dtype}")
     return C.c_void_p(t.data_ptr())
+
+
+def tile_cache_get(path, key):
+    """(tile tuple, ms) cached under `key` in the JSON file `path`, or None
+    (ddsp_tile_cache_get; host only)."""
+    t = (C.c_int * 5)()
+    ms = C.c_float()
+    rc = _lib.lib().ddsp_tile_cache_get(str(path).encode(), key.encode(), t,
+                                        C.byref(ms))
+    if rc == _lib.DDSP_E_STATE:
+        return None
+    _lib.check(rc, "ddsp_tile_cache_get")
+    return tuple(t), ms.value
+
+
+def tile_cache_put(path, key, tile, ms):
+    """Record `tile` (dm_tile, dm_per_thread, chan_chunk, stages, flags)
+    under `key` in the JSON file `path` (ddsp_tile_cache_put; host only)."""
+    t = (C.c_int * 5)(*[int(v) for v in tile])
+    _lib.check(_lib.lib().ddsp_tile_cache_put(str(path).encode(), key.encode(),
+                                              t, float(ms)),
+               "ddsp_tile_cache_put")
 
 
 def delay_table(nchan, f_top, chan_bw, tsamp, dm_list):
@@ -393,6 +416,28 @@ class Plan:
     def check(self, stream=None):
         _lib.check(_lib.lib().ddsp_plan_check(self._h, _stream_handle(stream)),
                    "ddsp_plan_check")
+
+    TUNE_CANDIDATES = 10   # tiles ddsp_plan_autotune tries
+
+    def autotune(self, x, cache=None, reps=2, stream=None):
+        """Time the candidate dedispersion tiles on block x (time-major CUDA
+        tensor), keep the fastest, record it in the JSON cache file `cache`
+        (if given); returns (ms per candidate, -1 where it does not fit;
+        index of the winner).  See ddsp_plan_autotune."""
+        ms = (C.c_float * self.TUNE_CANDIDATES)()
+        best = C.c_int()
+        _lib.check(_lib.lib().ddsp_plan_autotune(
+            self._h, _dev_ptr(x, self._in_dtype(), "block"), int(x.shape[0]),
+            cache.encode() if cache else None, int(reps), _stream_handle(stream),
+            ms, self.TUNE_CANDIDATES, C.byref(best)), "ddsp_plan_autotune")
+        return list(ms), best.value
+
+    def tile_key(self):
+        """The key this plan's tile is cached under (ddsp_plan_tile_key)."""
+        buf = C.create_string_buffer(512)
+        _lib.check(_lib.lib().ddsp_plan_tile_key(self._h, buf, 512),
+                   "ddsp_plan_tile_key")
+        return buf.value.decode()
 
     def set_wait_limit(self, cycles=0):
         """Bound (SM cycles) of the interleaved kernel's hand-off waits; 0 =

@@ -7,7 +7,9 @@ import ctypes as C
 import os
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libddsp.so")
+# DDSP_LIB selects another build of the same ABI (the tests' bounds-checked
+# libddsp_bounds.so); the default is the in-tree libddsp.so
+LIB_PATH = os.environ.get("DDSP_LIB") or os.path.join(_HERE, "libddsp.so")
 
 DDSP_OK = 0
 DDSP_E_INVALID_ARG = -1
@@ -98,6 +100,15 @@ SIGNATURES = {
     "ddsp_plan_set_tile": (I32, [P, I32, I32, I32, I32, I32]),
     "ddsp_plan_get_tile": (I32, [P] + [C.POINTER(C.c_int)] * 6),
     "ddsp_plan_set_wait_limit": (I32, [P, I64]),
+    "ddsp_plan_autotune": (I32, [P, P, I64, C.c_char_p, I32, P,
+                                 C.POINTER(C.c_float), I32, C.POINTER(C.c_int)]),
+    "ddsp_plan_tile_key": (I32, [P, C.c_char_p, C.c_size_t]),
+    "ddsp_tile_cache_get": (I32, [C.c_char_p, C.c_char_p, C.POINTER(C.c_int),
+                                  C.POINTER(C.c_float)]),
+    "ddsp_tile_cache_put": (I32, [C.c_char_p, C.c_char_p, C.POINTER(C.c_int),
+                                  C.c_float]),
+    "ddsp_bounds_check_status": (I32, [C.POINTER(C.c_int),
+                                       C.POINTER(C.c_uint64)]),
     "ddsp_plan_withhold_copy": (I32, [P, I32]),
     "ddsp_cluster_create": (I32, [C.POINTER(P), I32, I32, I64, I64]),
     "ddsp_cluster_destroy": (None, [P]),

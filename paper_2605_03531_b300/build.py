@@ -43,6 +43,13 @@ def up_to_date() -> bool:
     return all(os.path.getmtime(d) <= t for d in _deps())
 
 
+# The bounds-checked build (tests only): every checked access records the
+# first violation in one device variable the translation units share, which
+# takes relocatable device code.
+BOUNDS_LIB = os.path.join(PKG, "libddsp_bounds.so")
+BOUNDS_DEFINES = ("DDSP_BOUNDS_CHECK",)
+
+
 def _compile(src, obj, verbose, extra):
     cmd = [NVCC, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
     if verbose:
@@ -58,6 +65,8 @@ def build(force: bool = False, verbose: bool = False, lib: str = LIB,
     if not force and lib == LIB and not defines and up_to_date():
         return LIB
     extra = [f"-D{d}" for d in defines]
+    if "DDSP_BOUNDS_CHECK" in defines:
+        extra.append("-rdc=true")
     bdir = BUILD if not defines else BUILD + "_" + "_".join(
         d.lower() for d in defines)
     os.makedirs(bdir, exist_ok=True)
@@ -74,11 +83,20 @@ def build(force: bool = False, verbose: bool = False, lib: str = LIB,
         for f in [ex.submit(_compile, s_, o_, verbose, extra) for s_, o_ in jobs]:
             f.result()
     tmp = lib + ".tmp"
-    subprocess.run([NVCC, *ARCH, "-shared", "-cudart", "static", "-o", tmp,
-                    *objs], check=True)
+    rdc = ["-rdc=true"] if "DDSP_BOUNDS_CHECK" in defines else []
+    subprocess.run([NVCC, *ARCH, *rdc, "-shared", "-cudart", "static", "-o",
+                    tmp, *objs], check=True)
     os.replace(tmp, lib)
     return lib
 
 
+def build_bounds(force: bool = False) -> str:
+    """The bounds-checked library (tests only), beside the normal one."""
+    return build(force=force, lib=BOUNDS_LIB, defines=BOUNDS_DEFINES)
+
+
 if __name__ == "__main__":
-    print(build(force="--force" in sys.argv, verbose="--verbose" in sys.argv))
+    if "--bounds" in sys.argv:
+        print(build_bounds(force="--force" in sys.argv))
+    else:
+        print(build(force="--force" in sys.argv, verbose="--verbose" in sys.argv))

@@ -55,6 +55,7 @@ struct ddsp_batch {
   SpsBeam *d_sb = nullptr;
   int64_t sps_blocks = 0;
   size_t sps_smem = 0;
+  int64_t sps_cap = 0;
   uint32_t **d_counts = nullptr;
   int32_t *d_err = nullptr;
   // graph
@@ -420,7 +421,8 @@ int batch_enqueue(ddsp_batch &B, float thr, cudaStream_t s) {
   if (B.mode == DDSP_BATCH_PER_BEAM) {
     if (e == cudaSuccess) e = batch_dedisperse_per_beam(B, s);
     if (e == cudaSuccess)
-      e = launch_sps_batch(B.d_sb, B.nbeams, B.sps_blocks, thr, B.sps_smem, s);
+      e = launch_sps_batch(B.d_sb, B.nbeams, B.sps_blocks, thr, B.sps_smem,
+                           B.sps_cap, s);
     return cuda_rc(e);
   }
   for (size_t gi = 0; gi < B.groups.size() && e == cudaSuccess; ++gi) {
@@ -430,7 +432,8 @@ int batch_enqueue(ddsp_batch &B, float thr, cudaStream_t s) {
                                      G.grid, s);
   }
   if (e == cudaSuccess)
-    e = launch_sps_batch(B.d_sb, B.nbeams, B.sps_blocks, thr, B.sps_smem, s);
+    e = launch_sps_batch(B.d_sb, B.nbeams, B.sps_blocks, thr, B.sps_smem,
+                           B.sps_cap, s);
   return cuda_rc(e);
 }
 
@@ -512,6 +515,7 @@ int ddsp_batch_create(ddsp_batch **out, ddsp_plan *const *plans, int nbeams,
   if (rc == DDSP_OK) {
     B->sps_blocks = sblocks;
     B->sps_smem = sps_smem_bytes(maxlen_all, wmax_all);
+    B->sps_cap = sps_bufcap(maxlen_all, wmax_all);
     if ((e = cudaMalloc(&B->d_sb, sb.size() * sizeof(SpsBeam))) != cudaSuccess ||
         (e = cudaMalloc(&B->d_counts, counts.size() * sizeof(uint32_t *))) != cudaSuccess ||
         (e = cudaMalloc(&B->d_queue, kMaxGroups * sizeof(int))) != cudaSuccess ||

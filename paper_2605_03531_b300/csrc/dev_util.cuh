@@ -7,6 +7,50 @@
 
 namespace ddsp {
 
+// Bounds-checked build (compiled with -DDDSP_BOUNDS_CHECK and relocatable
+// device code): a checked access first tests its index against the extent
+// of its buffer; a failing test records (site << 32 | the index's low 32
+// bits) as the library's first violation, if none is recorded yet
+// (ddsp_bounds_check_status reads it), and the access is skipped.  In the
+// normal build a check is the constant true and its expression is not
+// evaluated.
+#ifdef DDSP_BOUNDS_CHECK
+extern __device__ unsigned long long g_bounds_first;
+__device__ __forceinline__ bool bounds_ok(bool ok, uint32_t site,
+                                          int64_t index) {
+  if (!ok)
+    atomicCAS(&g_bounds_first, 0ull,
+              ((unsigned long long)site << 32) | (uint32_t)index);
+  return ok;
+}
+#define DDSP_BC(cond, site, index) \
+  (::ddsp::bounds_ok((cond), (site), (int64_t)(index)))
+#else
+#define DDSP_BC(cond, site, index) true
+#endif
+
+// Sites of the checks (the high word of a recorded violation).
+enum : uint32_t {
+  kBcSpsLoad = 101,     // series sample inside its row
+  kBcSpsBuf = 102,      // window buffer (shared)
+  kBcSpsScan = 103,     // scan group inside the buffer
+  kBcSpsStats = 104,    // chunk statistics (shared)
+  kBcSpsBound = 105,    // chunk read by the screen's bound
+  kBcSpsQ = 106,        // prefix value read by the exact screen
+  kBcSpsDense = 107,    // dense output inside its row
+  kBcIlSrc = 201,       // interleaved row window of a bulk copy
+  kBcIlDst = 202,       // bulk copy inside its channel's element stage
+  kBcIlRel = 203,       // offsets copy inside its stage slot
+  kBcIlElem = 204,      // consumer element reads inside the channel's stage
+  kBcIlOut = 205,       // output sample inside the output row
+  kBcStageIn = 301,     // spectra vector load inside the row
+  kBcStageOut = 302,    // interleaved row store inside the row
+  kBcIntlvIn = 303,     // channel-major (ring) read inside the row
+  kBcIntlvOut = 304,    // interleaved store inside the row
+  kBcUnpackIn = 305,    // spectra load inside the block
+  kBcUnpackOut = 306,   // channel-major store inside the row
+};
+
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }

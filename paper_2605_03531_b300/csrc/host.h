@@ -61,11 +61,23 @@ DedispTile fit_interleaved_tile(TimeOk time_ok, Span span) {
   }
   return DedispTile{};
 }
+// The tile of ddsp_plan_set_tile's arguments (nonzero dm_tile), checked
+// against the plan's shape; and the switch of a plan to a tile (drops a
+// staged block, rebuilds the tables).
+int tile_from_args(const Plan &p, int dm_tile, int dm_per_thread,
+                   int chan_chunk, int stages, int flags, DedispTile *out);
+int apply_tile(Plan &p, const DedispTile &t);
+// At plan creation: the tile autotuned for this plan's shape on this GPU,
+// if the cache file named by DDSP_TILE_CACHE holds one that still fits
+// (tune.cu); p.tile is left as it is otherwise.
+void apply_cached_tile(Plan &p);
 void free_tables(DedispTables &t);
 int ensure_stats(Plan &p, size_t n);
 // Normalisation windows of an n-sample series; DDSP_E_SHAPE if one window
-// (plus the widest boxcar) exceeds the search kernel's shared memory.
-int search_windows(const Plan &p, int64_t n, int64_t *nwin);
+// (plus the widest boxcar) exceeds the search kernel's shared memory, unless
+// allow_long (the plan search, which then takes its long mode).
+int search_windows(const Plan &p, int64_t n, int64_t *nwin,
+                   bool allow_long = false);
 // Reads and clears the plan's device error word.
 int read_err(Plan &p);
 

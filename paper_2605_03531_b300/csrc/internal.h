@@ -246,10 +246,14 @@ cudaError_t launch_dedisperse_persistent(const DedispTile &t,
                                          size_t smem,
                                          int32_t *d_err, int grid,
                                          cudaStream_t s);
+// Search launch layout for windows of up to maxlen samples and the widest
+// boxcar wmax: the buffer capacity (samples) every block lays out its shared
+// memory with, and the dynamic shared memory that takes.
+int64_t sps_bufcap(int64_t maxlen, int wmax);
 size_t sps_smem_bytes(int64_t maxlen, int wmax);
 cudaError_t launch_sps_batch(const SpsBeam *d_beams, int nbeams,
                              int64_t total_blocks, float threshold,
-                             size_t smem, cudaStream_t s);
+                             size_t smem, int64_t bufcap, cudaStream_t s);
 
 }  // namespace ddsp
 

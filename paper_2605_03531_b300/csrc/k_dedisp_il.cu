@@ -70,7 +70,7 @@ interleave_kernel(const T *__restrict__ cm, int64_t pitch, int64_t nvalid,
   constexpr int SPE = 4 / sizeof(T);
   const int c = blockIdx.y;
   const int64_t i = 4 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
-  if (i >= ypitch) return;
+  if (i >= ypitch || !DDSP_BC(i + 4 <= ypitch, kBcIntlvOut, i)) return;
   const T *x = cm + (int64_t)c * pitch;
   auto at = [&](int64_t b) { return ring > 0 ? (t0 + b) % ring : b; };
   uint4 o;
@@ -80,7 +80,9 @@ interleave_kernel(const T *__restrict__ cm, int64_t pitch, int64_t nvalid,
     for (int m = 0; m < 4; ++m) {
       const int64_t b = i + (int64_t)m * S;
       if (b + 4 <= nvalid) {
-        w[m] = __ldg(reinterpret_cast<const uint32_t *>(x + at(b)));
+        w[m] = DDSP_BC(at(b) >= 0 && at(b) + 4 <= pitch, kBcIntlvIn, at(b))
+                   ? __ldg(reinterpret_cast<const uint32_t *>(x + at(b)))
+                   : 0u;
       } else {
         uint32_t v = 0;
 #pragma unroll
@@ -142,7 +144,8 @@ unpack_interleave_u8_kernel(const uint8_t *__restrict__ in, int64_t nsamp_in,
       const int64_t smp = i0 + row + (int64_t)m * S;
       const int c = c0 + 16 * q;
       uint4 v = make_uint4(0, 0, 0, 0);
-      if (smp < nsamp_in && c < nchan)
+      if (smp < nsamp_in && c < nchan &&
+          DDSP_BC(c + 16 <= nchan, kBcStageIn, c))
         v = __ldg(reinterpret_cast<const uint4 *>(in + smp * nchan + c));
       uint32_t *dst = tile[m] + row * kIlPW + 4 * q;
       dst[0] = v.x;
@@ -172,7 +175,8 @@ unpack_interleave_u8_kernel(const uint8_t *__restrict__ in, int64_t nsamp_in,
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int c = c0 + 4 * cq + j;
-      if (c < nchan && i < ypitch)
+      if (c < nchan && i < ypitch &&
+          DDSP_BC(i + 4 <= ypitch, kBcStageOut, i))
         *reinterpret_cast<uint4 *>(y + (int64_t)c * ypitch + i) =
             transpose4x4(cw[0][j], cw[1][j], cw[2][j], cw[3][j]);
     }
@@ -260,13 +264,24 @@ dedisp_il_kernel(IlArgs a, int32_t *err, long long timeout_cycles) {
         dcur = dnext;
         dnext = ld_desc(base + 32 + lane);
       }
-      const uint32_t nb = v ? (uint32_t)d.y : 0u;
+      uint32_t nb = v ? (uint32_t)d.y : 0u;
       const uint32_t relbytes = (uint32_t)(ncur * DT * 4);
+#ifdef DDSP_BOUNDS_CHECK
+      // the window [T0 + start, + nb/4) inside the row, the copy inside the
+      // channel's slot of the stage; a failing copy is left out (its bytes
+      // too, so the stage still completes)
+      if (v && !(DDSP_BC(T0 + d.x >= 0 && T0 + d.x + nb / 4 <= a.ypitch,
+                         kBcIlSrc, T0 + d.x) &&
+                 DDSP_BC(nb <= (uint32_t)elmax * 4u && (nb & 15u) == 0,
+                         kBcIlDst, nb)))
+        nb = 0u;
+      DDSP_BC(relbytes <= (uint32_t)L.rel_stride, kBcIlRel, relbytes);
+#endif
       const uint32_t total = __reduce_add_sync(0xffffffffu, nb) + relbytes;
       unsigned char *sb = stages + st * L.stage_stride;
       if (lane == 0) mbar_expect_tx(&full[st], total);
       __syncwarp();
-      if (v)
+      if (v && nb > 0u)
         bulk_g2s(sb + L.rel_stride + lane * elmax * 4,
                  yrows + (int64_t)(c0 + lane) * a.ypitch + T0 + d.x, nb,
                  &full[st]);
@@ -310,7 +325,7 @@ dedisp_il_kernel(IlArgs a, int32_t *err, long long timeout_cycles) {
     }
     const unsigned char *sb = stages + st * L.stage_stride;
     ws_accumulate(acc, reinterpret_cast<const int32_t *>(sb) + RD * wd, DT,
-                  sb + L.rel_stride + 4 * i0, elmax, ncur, one);
+                  sb + L.rel_stride + 4 * i0, elmax, ncur, one, i0);
     __syncwarp();
     if (lane == 0) mbar_arrive(&empty[st]);
     if (++st == nst) {

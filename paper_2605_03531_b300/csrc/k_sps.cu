@@ -12,25 +12,31 @@
 //      wanted order statistic is one key wide (or the two middle order
 //      statistics fall in different bins: then max of the lower bin and min
 //      of the upper bin); m2 = 2*median, mad4 = 4*MAD are exact integers;
-//   3. y = x - floor(median) and an inclusive prefix sum Q of y in uint32
+//   3. y = x - floor(median) and an exclusive prefix sum Q of y in uint32
 //      (modular, so every boxcar sum B_w(t) - w*floor(median) = Q[t+w]-Q[t]
-//      is exact), computed with warp-shuffle scans;
-//   4. per sample an integer screen against per-width thresholds derived
-//      from the S/N threshold with a small safety margin, then for the
-//      survivors the FP32 S/N of every width, the best one (first maximum),
-//      and candidate emission with one atomicAdd per warp (ballot + popc).
+//      is exact), computed with warp-shuffle scans, recording per chunk of
+//      8 start times the extremes of Q and the largest y;
+//   4. per chunk a bound of every width's boxcar sums from those extremes
+//      against the integer screen thresholds (derived from the S/N
+//      threshold with a small safety margin); only chunks that could pass
+//      go start by start through the exact integer screen, then for the
+//      survivors the FP32 S/N of the widths that passed, the best one
+//      (first maximum), and candidate emission with one atomicAdd per warp
+//      (ballot + popc).
 // Memory traffic is 4 bytes per series sample read once (plus the look-ahead)
 // and 16 bytes per candidate: the kernel is bounded by HBM bandwidth.
 #include <math.h>
 
+#include "dev_util.cuh"
 #include "internal.h"
 
 namespace ddsp {
 namespace {
 
-constexpr int kSpsThreads = 512;
+constexpr int kSpsThreads = 256;  // four blocks per SM
 constexpr int kWarps = kSpsThreads / 32;
 constexpr int kBins = 2048;      // bins per pass of the generic selection
+constexpr int kSelPer = kBins / kSpsThreads;
 constexpr int kFastBins = 4096;  // single-value bins of the one-pass path
 constexpr int kFastPer = kFastBins / kSpsThreads;
 constexpr int kMaxWidths = 11;  // 1 .. 1024
@@ -40,6 +46,7 @@ constexpr float kMadToSigma = 1.482602218505602f;
 struct SpsShared {
   uint32_t hist[kFastBins];
   uint32_t wred[kWarps][2];
+  uint32_t hred[kWarps][2];
   int64_t bc[4];      // broadcast slots
   float inv[kMaxWidths];
   int32_t thr_by[kMaxWidths];
@@ -82,35 +89,6 @@ __device__ __forceinline__ uint32_t warp_excl_offset(const uint32_t *wsum,
   return warp > 0 ? below : 0u;
 }
 
-// Block-wide min & max of a per-thread pair (int64).
-__device__ void block_minmax(int64_t &mn, int64_t &mx, SpsShared &sh) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    mn = min(mn, (int64_t)__shfl_xor_sync(0xffffffffu, (long long)mn, o));
-    mx = max(mx, (int64_t)__shfl_xor_sync(0xffffffffu, (long long)mx, o));
-  }
-  __shared__ int64_t red[kWarps][2];
-  if (lane == 0) {
-    red[warp][0] = mn;
-    red[warp][1] = mx;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int64_t a = red[0][0], b = red[0][1];
-    for (int w = 1; w < kWarps; ++w) {
-      a = min(a, red[w][0]);
-      b = max(b, red[w][1]);
-    }
-    sh.bc[0] = a;
-    sh.bc[1] = b;
-  }
-  __syncthreads();
-  mn = sh.bc[0];
-  mx = sh.bc[1];
-  __syncthreads();
-}
-
 // Exact order statistics of rank r1 and r2 = r1 or r1 + 1 (0-based) of n
 // uint32 keys produced by key(i), all <= kmax.  Returns them in k1, k2.
 template <typename KeyFn>
@@ -133,11 +111,12 @@ __device__ void select2(KeyFn key, int n, int r1, int r2, uint32_t kmax,
       if (k >= lo && d <= smax) atomicAdd(&sh.hist[d >> s], 1u);
     }
     __syncthreads();
-    // exclusive scan of the histogram: each thread owns 4 consecutive bins
-    uint32_t c[4], tsum = 0;
+    // exclusive scan of the histogram: each thread owns kSelPer
+    // consecutive bins
+    uint32_t c[kSelPer], tsum = 0;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      int b = 4 * tid + q;
+    for (int q = 0; q < kSelPer; ++q) {
+      int b = kSelPer * tid + q;
       c[q] = (b < nb) ? sh.hist[b] : 0;
       tsum += c[q];
     }
@@ -145,11 +124,12 @@ __device__ void select2(KeyFn key, int n, int r1, int r2, uint32_t kmax,
     if (lane == 31) sh.wsum[warp] = incl;
     __syncthreads();
     const uint32_t wpre = warp_excl_offset(sh.wsum, warp, lane);
-    uint32_t run = wpre + incl - tsum;  // keys of this window below bin 4*tid
+    // keys of this window below bin kSelPer * tid
+    uint32_t run = wpre + incl - tsum;
     const uint32_t q1 = (uint32_t)(r1 - below), q2 = (uint32_t)(r2 - below);
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      int b = 4 * tid + q;
+    for (int q = 0; q < kSelPer; ++q) {
+      int b = kSelPer * tid + q;
       if (b < nb && c[q] > 0) {
         if (q1 >= run && q1 < run + c[q]) {
           sh.bc[0] = b;
@@ -230,11 +210,12 @@ __device__ void select2(KeyFn key, int n, int r1, int r2, uint32_t kmax,
 //    are the smallest v reaching ranks r1 + 1 and r2 + 1.
 // Returns false (the caller then uses select2) when a rank falls outside
 // the bins.  The result, when true, equals select2's.
-template <typename KeyFn>
-__device__ bool median_mad_fast(KeyFn key, int n, int r1, int r2,
-                                SpsShared &sh, uint32_t &k1, uint32_t &k2,
-                                uint32_t &u1, uint32_t &u2) {
+__device__ bool median_mad_fast(const int32_t *__restrict__ buf, uint32_t base,
+                                int n, int r1, int r2, SpsShared &sh,
+                                uint32_t &k1, uint32_t &k2, uint32_t &u1,
+                                uint32_t &u2) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  auto key = [&](int i) { return (uint32_t)buf[i] - base; };
   // ---- estimate
   if (warp == 0) {
     uint32_t v = key((int)((int64_t)lane * n / 32));
@@ -264,10 +245,23 @@ __device__ bool median_mad_fast(KeyFn key, int n, int r1, int r2,
   const uint32_t A = est > kFastBins / 2 ? est - kFastBins / 2 : 0u;
   // ---- one pass: single-value bins [A, A + kFastBins) and the count below A
   uint32_t nb = 0;
-  for (int i = tid; i < n; i += kSpsThreads) {
-    const uint32_t k = key(i);
+  auto bin = [&](int32_t v) {
+    const uint32_t k = (uint32_t)v - base;
     if (k < A) ++nb;
     else if (k - A < (uint32_t)kFastBins) atomicAdd(&sh.hist[k - A], 1u);
+  };
+  {
+    // 16-byte shared loads (buf is 16-byte aligned), then the ragged tail
+    const int n4 = n >> 2;
+    const int4 *b4 = reinterpret_cast<const int4 *>(buf);
+    for (int q = tid; q < n4; q += kSpsThreads) {
+      const int4 v = b4[q];
+      bin(v.x);
+      bin(v.y);
+      bin(v.z);
+      bin(v.w);
+    }
+    for (int i = 4 * n4 + tid; i < n; i += kSpsThreads) bin(buf[i]);
   }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) nb += __shfl_xor_sync(0xffffffffu, nb, o);
@@ -361,110 +355,231 @@ __device__ bool median_mad_fast(KeyFn key, int n, int r1, int r2,
   return true;
 }
 
-// Step 4 of the search when the widths are 1, 2, 4, ..., 2^(NW-1): the
-// offsets of the boxcar ends are compile-time, and start times whose widest
-// boxcar ends inside the series (all but the last 2^(NW-1) of a series)
-// need no per-width check.  Outside the dense mode, the S/N is evaluated
-// only for the widths that passed the integer screen: any width whose FP32
-// S/N reaches the threshold passes it (the screen keeps a margin), so a
-// width that failed can never be the best one of an emitted candidate.
-template <int NW, bool DENSE>
-__device__ __forceinline__ void sweep_pow2(
-    const uint32_t *__restrict__ Q, const SpsShared &sh, int len, int nv,
-    const int32_t (&tbv)[kMaxWidths], int odd, int32_t mfloor, float thr,
-    int64_t lo, int64_t n, int64_t nrep, int k, ddsp_cand *__restrict__ cands,
-    uint32_t *__restrict__ count, uint32_t cap, int32_t *__restrict__ best_w,
-    float *__restrict__ best_snr, int32_t *__restrict__ best_sum) {
-  const int tid = threadIdx.x, lane = tid & 31;
-  constexpr int kWidest = 1 << (NW - 1);
-  for (int i0 = 0; i0 < len; i0 += kSpsThreads) {
-    const int i = i0 + tid;
-    const bool in = i < len;
-    uint32_t qi = 0;
+// Chunk bounds of the screen.  Start times are taken in chunks of kChunk;
+// per chunk c the scan records the smallest and largest prefix value
+// Q[8c .. 8c+7] and the largest y[8c .. 8c+7].  For every start i of chunk
+// c and width w, B_w(i) = Q[i + w] - Q[i] is at most the largest Q over the
+// chunks holding [8c + w, 8c + w + 8) minus the smallest Q of chunk c, and
+// also at most w times the largest y over [8c, 8c + 7 + w); a chunk none of
+// whose widths can reach its integer threshold is skipped without looking
+// at its starts.  On noise that rejects all but a few chunks in a thousand,
+// so the screen costs a few operations per sample instead of one load, add
+// and compare per sample and width.
+constexpr int kChunk = 8;
+// windows up to this many buffered samples keep the chunk statistics in
+// shared memory (longer ones take every start through the exact screen)
+constexpr int64_t kStatsMaxCap = 32768;
+// Windows longer than the on-chip limit (long mode): exact statistics by a
+// separate pass over global memory, then the search in segments of kSeg
+// start times (each with its look-ahead), all of a window sharing them.
+constexpr int64_t kSeg = 8192;
+
+__host__ __device__ __forceinline__ int64_t sps_buf_cap(int64_t maxlen,
+                                                        int wmax) {
+  // x[0 .. elen) then, in place, Q[0 .. elen]; rounded to whole 128-value
+  // scan groups
+  return ((maxlen + wmax + 1 + 127) / 128) * 128;
+}
+__host__ __device__ __forceinline__ int64_t sps_chunk_cap(int64_t cap) {
+  return cap / kChunk + 2;
+}
+
+// One start time through the exact screen: the boxcar sums of every width
+// from the prefix sums, the integer screen, and (for widths that pass, or
+// every width in the dense mode) the FP32 S/N; best = first maximum.
+// Returns the best width index (-1: none) with its S/N and boxcar sum.
+// NW > 0: the widths are 1, 2, 4, ..., 2^(NW-1), so the boxcar ends are
+// compile-time offsets and a start whose widest boxcar ends inside the
+// series needs no per-width check; NW = 0: any ascending width list.
+template <bool DENSE, int NW>
+__device__ __forceinline__ int exact_start(
+    const uint32_t *__restrict__ Q, int qcap, int i, int nv, int nw,
+    const int32_t (&wv)[kMaxWidths], const int32_t (&tbv)[kMaxWidths],
+    const float (&iv)[kMaxWidths], int odd, int32_t mfloor, float &bs,
+    int32_t &bsum) {
+  const uint32_t qi = Q[i];
+  int bw = -1;
+  bs = 0.0f;
+  bsum = 0;
+  if constexpr (NW > 0) {
+    constexpr int kWidest = 1 << (NW - 1);
     int32_t by[NW];
-    unsigned pm = 0, vm = 0;   // widths passing the screen / ending inside
-    if (in) {
-      qi = Q[i];
-      if (i + kWidest <= nv) {
-        const uint32_t *qp = Q + i;
+    unsigned pm = 0u;   // widths that end inside the series and pass
+    const bool inner = i + kWidest <= nv &&
+                       DDSP_BC(i + kWidest < qcap, kBcSpsQ, i + kWidest);
 #pragma unroll
-        for (int wi = 0; wi < NW; ++wi) {
-          by[wi] = (int32_t)(qp[1 << wi] - qi);
-          pm |= (unsigned)(by[wi] >= tbv[wi]) << wi;
-        }
-        vm = (1u << NW) - 1u;
-      } else {
+    for (int wi = 0; wi < NW; ++wi) {
+      const bool v = inner || (i + (1 << wi) <= nv &&
+                               DDSP_BC(i + (1 << wi) < qcap, kBcSpsQ, i));
+      by[wi] = v ? (int32_t)(Q[i + (1 << wi)] - qi) : 0;
+      pm |= (unsigned)(v && (DENSE || by[wi] >= tbv[wi])) << wi;
+    }
+    // a width whose FP32 S/N reaches the threshold always passes the integer
+    // screen (it keeps a margin), so a width that failed can never be the
+    // best one of an emitted candidate
+    if (pm == 0u) return -1;
 #pragma unroll
-        for (int wi = 0; wi < NW; ++wi) {
-          const bool v = i + (1 << wi) <= nv;
-          by[wi] = (int32_t)(Q[min(i + (1 << wi), nv)] - qi);
-          vm |= (unsigned)v << wi;
-          pm |= (unsigned)(v && by[wi] >= tbv[wi]) << wi;
+    for (int wi = 0; wi < NW; ++wi) {
+      if ((pm >> wi) & 1u) {
+        const float sn = twice_minus(by[wi], (1 << wi) * odd) * iv[wi];
+        if (bw < 0 || sn > bs) {
+          bw = wi;
+          bs = sn;
+          bsum = by[wi] + (1 << wi) * mfloor;
         }
       }
     }
-    if constexpr (DENSE) {
-      if (in) {
-        int bw = -1;
-        float bs = 0.0f;
-        int32_t bsum = 0;
+  } else {
 #pragma unroll
-        for (int wi = 0; wi < NW; ++wi) {
-          if ((vm >> wi) & 1u) {
-            const float sn = twice_minus(by[wi], (1 << wi) * odd) * sh.inv[wi];
-            if (bw < 0 || sn > bs) {
-              bw = wi;
-              bs = sn;
-              bsum = by[wi] + (1 << wi) * mfloor;
-            }
-          }
-        }
-        const int64_t o = (int64_t)k * n + lo + i;
-        best_w[o] = bw;
-        best_snr[o] = bs;
-        best_sum[o] = bsum;
-      }
-    } else {
-      const unsigned active = __ballot_sync(0xffffffffu, pm != 0u);
-      if (pm) {
-        int bw = -1;
-        float bs = 0.0f;
-        unsigned m = pm;
-        while (m) {
-          const int wi = __ffs(m) - 1;
-          m &= m - 1u;
-          const int w = 1 << wi;
-          const float sn =
-              twice_minus((int32_t)(Q[i + w] - qi), w * odd) * sh.inv[wi];
+    for (int wi = 0; wi < kMaxWidths; ++wi) {
+      if (wi < nw && i + wv[wi] <= nv &&
+          DDSP_BC(i + wv[wi] < qcap, kBcSpsQ, i + wv[wi])) {
+        const int32_t by = (int32_t)(Q[i + wv[wi]] - qi);
+        if (DENSE || by >= tbv[wi]) {
+          const float sn = twice_minus(by, wv[wi] * odd) * iv[wi];
           if (bw < 0 || sn > bs) {
             bw = wi;
             bs = sn;
-          }
-        }
-        const bool cand = bs >= thr && lo + i < nrep;
-        const uint32_t ball = __ballot_sync(active, cand);
-        if (cand) {
-          const int leader = __ffs(ball) - 1;
-          uint32_t base = 0;
-          if (lane == leader) base = atomicAdd(count, (uint32_t)__popc(ball));
-          base = __shfl_sync(ball, base, leader);
-          const uint32_t slot = base + __popc(ball & ((1u << lane) - 1u));
-          if (slot < cap) {
-            ddsp_cand c;
-            c.dm_idx = (uint32_t)k;
-            c.t = (uint32_t)(lo + i);
-            c.w_idx = (uint32_t)bw;
-            c.snr = bs;
-            cands[slot] = c;
+            bsum = by + wv[wi] * mfloor;
           }
         }
       }
     }
   }
+  return bw;
+}
+
+// Candidate emission of the lanes in `mask` that execute it together: one
+// atomicAdd per warp (ballot + popc), records beyond the capacity dropped
+// (the count stays exact).
+__device__ __forceinline__ void emit(unsigned mask, bool cand, int k, int64_t t,
+                                     int bw, float bs,
+                                     ddsp_cand *__restrict__ cands,
+                                     uint32_t *__restrict__ count,
+                                     uint32_t cap) {
+  const int lane = threadIdx.x & 31;
+  const unsigned ball = __ballot_sync(mask, cand);
+  if (!cand) return;
+  const int leader = __ffs(ball) - 1;
+  uint32_t base = 0;
+  if (lane == leader) base = atomicAdd(count, (uint32_t)__popc(ball));
+  base = __shfl_sync(ball, base, leader);
+  const uint32_t slot = base + __popc(ball & ((1u << lane) - 1u));
+  if (slot < cap) {
+    ddsp_cand c;
+    c.dm_idx = (uint32_t)k;
+    c.t = (uint32_t)t;
+    c.w_idx = (uint32_t)bw;
+    c.snr = bs;
+    cands[slot] = c;
+  }
+}
+
+// What the sweep of one window needs (step 4).
+struct SweepArgs {
+  const uint32_t *Q;
+  int qcap, len, nv, nw, odd;
+  int32_t mfloor;
+  float thr;
+  int64_t lo, n, nrep;
+  int k, wmax;
+  bool bounds;
+  const int32_t *cmin, *cmax, *ymax;
+  ddsp_cand *cands;
+  uint32_t *count;
+  uint32_t cap;
+  int32_t *best_w;
+  float *best_snr;
+  int32_t *best_sum;
+};
+
+// Step 4: boxcars, S/N, candidates of one window (NW as in exact_start).
+template <bool DENSE, int NW>
+__device__ __forceinline__ void sweep(const SweepArgs &g,
+                                      const int32_t (&wv)[kMaxWidths],
+                                      const int32_t (&tbv)[kMaxWidths],
+                                      const float (&iv)[kMaxWidths],
+                                      int64_t bufcap) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  if (DENSE) {
+    for (int i = tid; i < g.len; i += kSpsThreads) {
+      float bs;
+      int32_t bsum;
+      const int bw = exact_start<true, NW>(g.Q, g.qcap, i, g.nv, g.nw, wv, tbv,
+                                           iv, g.odd, g.mfloor, bs, bsum);
+      const int64_t o = (int64_t)g.k * g.n + g.lo + i;
+      if (DDSP_BC(g.lo + i < g.n, kBcSpsDense, g.lo + i)) {
+        g.best_w[o] = bw;
+        g.best_snr[o] = bs;
+        g.best_sum[o] = bsum;
+      }
+    }
+    return;
+  }
+  // A warp takes 32 consecutive chunks (256 start times) at a time: lane l
+  // bounds chunk l; the chunks that could pass then go through the exact
+  // screen 32 consecutive starts at a time, one per lane (consecutive
+  // shared-memory words: no bank conflicts), skipping the 32-start runs
+  // whose four chunks all failed their bounds.
+  const int nch = (g.len + kChunk - 1) / kChunk;
+  for (int cb = warp * 32; cb < nch; cb += kSpsThreads) {
+    const int c = cb + lane;
+    bool need = false;
+    if (c < nch) {
+      const int i0 = c * kChunk;
+      need = true;
+      if (g.bounds && i0 + kChunk + g.wmax <= g.nv &&
+          DDSP_BC((c + g.wmax / kChunk + 1) < sps_chunk_cap(bufcap),
+                  kBcSpsBound, c)) {
+        const int32_t lmin = g.cmin[c];
+        const int32_t ym1 = g.ymax[c];
+        const int32_t ym2 = max(ym1, g.ymax[c + 1]);
+        bool pass = false;
+#pragma unroll
+        for (int wi = 0; wi < kMaxWidths; ++wi) {
+          if (NW > 0 ? wi < NW : wi < g.nw) {
+            const int w = NW > 0 ? (1 << wi) : wv[wi];
+            const int c2 = c + w / kChunk;
+            int32_t top = g.cmax[c2];
+            if (w % kChunk) top = max(top, g.cmax[c2 + 1]);
+            // |Q| < 2^30 here, so the difference is exact in int32
+            int32_t ub = top - lmin;
+            if (w < kChunk) {
+              // w * max y fits: |y| (elen + 1) < 2^30 and w < 8 <= elen
+              const int32_t yb = w * (w == 1 ? ym1 : ym2);
+              ub = min(ub, yb);
+            }
+            pass |= ub >= tbv[wi];
+          }
+        }
+        need = pass;
+      }
+    }
+    const unsigned pm = __ballot_sync(0xffffffffu, need);
+    if (pm == 0u) continue;                      // warp-uniform
+#pragma unroll 1
+    for (int sb = 0; sb < kChunk; ++sb) {        // 8 runs of 32 starts
+      // starts [8 cb + 32 sb, + 32): chunks cb + 4 sb .. cb + 4 sb + 3
+      const unsigned sub = (pm >> (4 * sb)) & 0xFu;
+      if (sub == 0u) continue;                   // warp-uniform
+      const int i = kChunk * cb + 32 * sb + lane;
+      const bool mine = ((sub >> (lane >> 3)) & 1u) && i < g.len;
+      float bs = 0.0f;
+      int32_t bsum;
+      int bw = -1;
+      if (mine)
+        bw = exact_start<false, NW>(g.Q, g.qcap, i, g.nv, g.nw, wv, tbv, iv,
+                                    g.odd, g.mfloor, bs, bsum);
+      const bool cand = bw >= 0 && bs >= g.thr && g.lo + i < g.nrep;
+      emit(0xffffffffu, cand, g.k, g.lo + i, bw, bs, g.cands, g.count, g.cap);
+    }
+  }
 }
 
 // The search of one (DM trial k, window j): the body of the per-plan kernel
-// and of the multi-beam kernel (k_batch.cu).
+// and of the multi-beam kernel (k_batch.cu).  Shared memory: SpsShared, then
+// buf[bufcap] (x, then Q in place), then, for bufcap <= kStatsMaxCap, the
+// chunk statistics cmin / cmax / ymax [sps_chunk_cap(bufcap)] each.
 template <bool DENSE>
 __device__ __forceinline__ void sps_window(
     const int32_t *__restrict__ series, int64_t n, int64_t L, int64_t nwin,
@@ -473,44 +588,126 @@ __device__ __forceinline__ void sps_window(
     ddsp_cand *__restrict__ cands, uint32_t *__restrict__ count, uint32_t cap,
     int32_t *__restrict__ best_w, float *__restrict__ best_snr,
     int32_t *__restrict__ best_sum, int32_t *__restrict__ err,
-    const int64_t j, const int k, const int64_t nrep) {
+    const int64_t j, const int k, const int64_t nrep, const int64_t bufcap,
+    const int64_t seg = -1) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   SpsShared &sh = *reinterpret_cast<SpsShared *>(smem_raw);
   int32_t *buf = reinterpret_cast<int32_t *>(smem_raw + kBufOff);
+  // chunk statistics: in the histogram's space when they fit (the
+  // histogram is done before the scan writes them), else after the buffer
+  const int64_t ccap = sps_chunk_cap(bufcap);
+  const bool stats_in_hist = 3 * ccap <= kFastBins;
+  const bool have_stats = stats_in_hist || bufcap <= kStatsMaxCap;
+  int32_t *cmin = stats_in_hist ? reinterpret_cast<int32_t *>(sh.hist)
+                                : buf + bufcap;
+  int32_t *cmax = cmin + ccap;
+  int32_t *ymax = cmax + ccap;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int64_t lo = (L <= 0) ? 0 : j * L;
-  const int64_t hi = (L <= 0 || j == nwin - 1) ? n : (j + 1) * L;
+  // seg < 0: the whole window j, its statistics computed here; seg >= 0
+  // (long windows): start times [lo, hi) = segment seg of kSeg samples of
+  // window j, whose statistics sps_long_stats_kernel already wrote
+  const bool given = seg >= 0;
+  const int64_t wlo = (L <= 0) ? 0 : j * L;
+  const int64_t whi = (L <= 0 || j == nwin - 1) ? n : (j + 1) * L;
+  const int64_t lo = given ? wlo + seg * kSeg : wlo;
+  const int64_t hi = given ? min(lo + kSeg, whi) : whi;
   const int wmax = widths[nw - 1];
   const int64_t ext = min(hi + wmax - 1, n);
   const int len = (int)(hi - lo), elen = (int)(ext - lo);
   const int32_t *x = series + (int64_t)k * n + lo;
 
-  // ---- 1. load (buf[0] is the zero prefix slot)
-  int32_t mn32 = INT32_MAX, mx32 = INT32_MIN;
-  for (int i = tid; i < elen; i += kSpsThreads) {
-    int32_t v = __ldg(x + i);
-    buf[1 + i] = v;
+  // ---- 1. load x[0 .. elen) to buf (16-byte loads when the window starts
+  // on a 16-byte boundary, as it does when n and L are multiples of 4),
+  // min and max over the window [0, len)
+  int32_t mn32 = INT32_MAX, mx32 = INT32_MIN;   // the window [0, len)
+  int32_t hmn = INT32_MAX, hmx = INT32_MIN;     // look-ahead [len, elen)
+  auto take = [&](int i, int32_t v) {
     if (i < len) {
       mn32 = min(mn32, v);
       mx32 = max(mx32, v);
+    } else {
+      hmn = min(hmn, v);
+      hmx = max(hmx, v);
+    }
+  };
+  if ((reinterpret_cast<uintptr_t>(x) & 15) == 0) {
+    const int n4 = elen >> 2;
+    const int4 *x4 = reinterpret_cast<const int4 *>(x);
+    int4 *b4 = reinterpret_cast<int4 *>(buf);
+#pragma unroll 2
+    for (int q = tid; q < n4; q += kSpsThreads) {
+      if (!DDSP_BC(lo + 4 * q + 4 <= n, kBcSpsLoad, lo + 4 * q) ||
+          !DDSP_BC(4 * q + 4 <= bufcap, kBcSpsBuf, 4 * q))
+        continue;
+      const int4 v = __ldg(x4 + q);
+      b4[q] = v;
+      const int i = 4 * q;
+      if (i + 4 <= len) {
+        mn32 = min(mn32, min(min(v.x, v.y), min(v.z, v.w)));
+        mx32 = max(mx32, max(max(v.x, v.y), max(v.z, v.w)));
+      } else {
+        take(i, v.x);
+        take(i + 1, v.y);
+        take(i + 2, v.z);
+        take(i + 3, v.w);
+      }
+    }
+    for (int i = 4 * n4 + tid; i < elen; i += kSpsThreads) {
+      if (!DDSP_BC(lo + i < n, kBcSpsLoad, lo + i) ||
+          !DDSP_BC(i < bufcap, kBcSpsBuf, i))
+        continue;
+      const int32_t v = __ldg(x + i);
+      buf[i] = v;
+      take(i, v);
+    }
+  } else {
+    for (int i = tid; i < elen; i += kSpsThreads) {
+      if (!DDSP_BC(lo + i < n, kBcSpsLoad, lo + i) ||
+          !DDSP_BC(i < bufcap, kBcSpsBuf, i))
+        continue;
+      const int32_t v = __ldg(x + i);
+      buf[i] = v;
+      take(i, v);
     }
   }
-  if (tid == 0) buf[0] = 0;
+  mn32 = __reduce_min_sync(0xffffffffu, mn32);
+  mx32 = __reduce_max_sync(0xffffffffu, mx32);
+  hmn = __reduce_min_sync(0xffffffffu, hmn);
+  hmx = __reduce_max_sync(0xffffffffu, hmx);
+  if (lane == 0) {
+    sh.wred[warp][0] = (uint32_t)mn32;
+    sh.wred[warp][1] = (uint32_t)mx32;
+    sh.hred[warp][0] = (uint32_t)hmn;
+    sh.hred[warp][1] = (uint32_t)hmx;
+  }
   __syncthreads();
-  int64_t mn = mn32, mx = mx32;
-  block_minmax(mn, mx, sh);
+  int64_t mn = INT32_MAX, mx = INT32_MIN, fmn, fmx;
+  int64_t hn = INT32_MAX, hx = INT32_MIN;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) {
+    mn = min(mn, (int64_t)(int32_t)sh.wred[w][0]);
+    mx = max(mx, (int64_t)(int32_t)sh.wred[w][1]);
+    hn = min(hn, (int64_t)(int32_t)sh.hred[w][0]);
+    hx = max(hx, (int64_t)(int32_t)sh.hred[w][1]);
+  }
+  fmn = min(mn, hn);    // everything loaded: window and look-ahead
+  fmx = max(mx, hx);
+  __syncthreads();
 
   // ---- 2. median and MAD
   int64_t M2 = 0, MAD4 = 0;
-  const bool range_ok = (mx - mn) < (int64_t)1 << 31;
-  if (range_ok) {
+  const bool range_ok = given || (mx - mn) < (int64_t)1 << 31;
+  if (given) {
+    M2 = m2_out[(int64_t)k * nwin + j];
+    MAD4 = mad4_out[(int64_t)k * nwin + j];
+  } else if (range_ok) {
     const int r1 = (len - 1) / 2, r2 = len / 2;
     const uint32_t base = (uint32_t)(int32_t)mn;
     uint32_t k1, k2, u1, u2;
     // keys x - min in [0, 2^31)
-    auto kx = [&](int i) { return (uint32_t)buf[1 + i] - base; };
-    const bool fast = median_mad_fast(kx, len, r1, r2, sh, k1, k2, u1, u2);
+    auto kx = [&](int i) { return (uint32_t)buf[i] - base; };
+    const bool fast = median_mad_fast(buf, base, len, r1, r2, sh, k1, k2, u1, u2);
     if (!fast)
       select2(kx, len, r1, r2, (uint32_t)(mx - mn), sh, k1, k2);
     M2 = 2 * mn + (int64_t)k1 + (int64_t)k2;
@@ -521,7 +718,7 @@ __device__ __forceinline__ void sps_window(
     if (!fast)
       select2(
           [&](int i) {
-            const uint32_t t2 = 2u * ((uint32_t)buf[1 + i] - base);
+            const uint32_t t2 = 2u * ((uint32_t)buf[i] - base);
             return t2 >= m2r ? t2 - m2r : m2r - t2;
           },
           len, r1, r2, (uint32_t)umax, sh, u1, u2);
@@ -529,7 +726,7 @@ __device__ __forceinline__ void sps_window(
   } else if (tid == 0) {
     atomicExch(err, kErrRange);
   }
-  if (tid == 0) {
+  if (tid == 0 && !given) {
     m2_out[(int64_t)k * nwin + j] = M2;
     mad4_out[(int64_t)k * nwin + j] = MAD4;
   }
@@ -555,50 +752,76 @@ __device__ __forceinline__ void sps_window(
     sh.wid[tid] = widths[tid];
   }
 
-  // ---- 3. y = x - floor(median); inclusive prefix sum over buf[0..elen]
-  // in place (buf[0] = 0, so buf[i] = Q[i]).  Each warp walks its own run of
-  // 128-value groups; a lane takes 4 consecutive values with one 16-byte
-  // shared load, scans them, and one warp scan joins the lanes.
+  // ---- 3. y = x - floor(median) and the exclusive prefix sum Q, in place:
+  // buf[p] = Q[p] = sum_{t < p} y[t] for p = 0 .. elen (uint32, modular, so
+  // every boxcar sum Q[t + w] - Q[t] is exact).  Groups of 128 positions, a
+  // lane taking 4 consecutive ones with a 16-byte shared load, each warp a
+  // contiguous run of groups: first the runs' totals, then the scan with
+  // every warp's offset known, recording the chunk statistics on the way.
+  // Statistics are kept only when every prefix value fits in 30 bits in
+  // magnitude (|y| <= the larger distance of floor(median) to the extremes
+  // of everything loaded, so that times (elen + 1) below 2^30), where
+  // minima, maxima and their differences are exact.
+  const int64_t ybound = max(fmx - (int64_t)mfloor, (int64_t)mfloor - fmn);
+  const bool bounds =
+      !DENSE && have_stats && range_ok && MAD4 > 0 && elen > 0 &&
+      ybound * (int64_t)(elen + 1) < ((int64_t)1 << 30);
   {
     const int ntot = elen + 1;
     const int ngroups = (ntot + 127) / 128;
     const int gpw = (ngroups + kWarps - 1) / kWarps;
     const int g0 = warp * gpw, g1 = min(ngroups, g0 + gpw);
-    uint32_t carry = 0;
+    const uint32_t mf = (uint32_t)mfloor;
+    auto yv = [&](int p, int32_t v) {
+      return p < elen ? (uint32_t)v - mf : 0u;
+    };
+    // totals of every warp's run
+    uint32_t tsum = 0;
     for (int g = g0; g < g1; ++g) {
       const int b4 = g * 128 + 4 * lane;
-      uint4 q = make_uint4(0, 0, 0, 0);
-      if (b4 < ntot) q = *reinterpret_cast<const uint4 *>(buf + b4);
-      // y for indices 1 .. elen, zero for index 0 and past the end
-      const uint32_t mf = (uint32_t)mfloor;
-      uint32_t a0 = (b4 >= 1 && b4 < ntot) ? q.x - mf : 0u;
-      uint32_t a1 = (b4 + 1 < ntot) ? q.y - mf : 0u;
-      uint32_t a2 = (b4 + 2 < ntot) ? q.z - mf : 0u;
-      uint32_t a3 = (b4 + 3 < ntot) ? q.w - mf : 0u;
-      a1 += a0;
-      a2 += a1;
-      a3 += a2;
-      const uint32_t inc = warp_incl_scan(a3, lane);
-      const uint32_t pre = carry + inc - a3;
-      if (b4 < ntot)
-        *reinterpret_cast<uint4 *>(buf + b4) =
-            make_uint4(pre + a0, pre + a1, pre + a2, pre + a3);
-      carry += __shfl_sync(0xffffffffu, inc, 31);
+      if (!DDSP_BC(b4 + 4 <= bufcap, kBcSpsScan, b4)) continue;
+      const int4 v = *reinterpret_cast<const int4 *>(buf + b4);
+      if (b4 + 4 <= elen)
+        tsum += (uint32_t)v.x + (uint32_t)v.y + (uint32_t)v.z + (uint32_t)v.w -
+                4u * mf;
+      else
+        tsum += yv(b4, v.x) + yv(b4 + 1, v.y) + yv(b4 + 2, v.z) +
+                yv(b4 + 3, v.w);
     }
-    if (lane == 0) sh.wsum[warp] = carry;
+    tsum = __reduce_add_sync(0xffffffffu, tsum);
+    if (lane == 0) sh.wsum[warp] = tsum;
     __syncthreads();
-    const uint32_t off = warp_excl_offset(sh.wsum, warp, lane);
-    if (off != 0u) {
-      for (int g = g0; g < g1; ++g) {
-        const int b4 = g * 128 + 4 * lane;
-        if (b4 < ntot) {
-          uint4 *p4 = reinterpret_cast<uint4 *>(buf + b4);
-          uint4 q = *p4;
-          q.x += off;
-          q.y += off;
-          q.z += off;
-          q.w += off;
-          *p4 = q;
+    uint32_t carry = warp_excl_offset(sh.wsum, warp, lane);
+    for (int g = g0; g < g1; ++g) {
+      const int b4 = g * 128 + 4 * lane;
+      // (a failed check leaves this lane's values out; the warp's scan and
+      // shuffles below still run with all lanes)
+      const bool in_buf = DDSP_BC(b4 + 4 <= bufcap, kBcSpsScan, b4);
+      int4 v = make_int4(0, 0, 0, 0);
+      if (in_buf) v = *reinterpret_cast<const int4 *>(buf + b4);
+      const uint32_t y0 = yv(b4, v.x), y1 = yv(b4 + 1, v.y);
+      const uint32_t y2 = yv(b4 + 2, v.z), y3 = yv(b4 + 3, v.w);
+      const uint32_t e1 = y0, e2 = y0 + y1, e3 = e2 + y2, tot = e3 + y3;
+      const uint32_t inc = warp_incl_scan(tot, lane);
+      const uint32_t pre = carry + inc - tot;
+      const uint32_t q0 = pre, q1 = pre + e1, q2 = pre + e2, q3 = pre + e3;
+      if (in_buf)
+        *reinterpret_cast<uint4 *>(buf + b4) = make_uint4(q0, q1, q2, q3);
+      carry += __shfl_sync(0xffffffffu, inc, 31);
+      if (bounds) {
+        // chunk of 8 = this lane's 4 positions and its partner's
+        int32_t cn = min(min((int32_t)q0, (int32_t)q1), min((int32_t)q2, (int32_t)q3));
+        int32_t cx = max(max((int32_t)q0, (int32_t)q1), max((int32_t)q2, (int32_t)q3));
+        int32_t ym = max(max((int32_t)y0, (int32_t)y1), max((int32_t)y2, (int32_t)y3));
+        cn = min(cn, __shfl_xor_sync(0xffffffffu, cn, 1));
+        cx = max(cx, __shfl_xor_sync(0xffffffffu, cx, 1));
+        ym = max(ym, __shfl_xor_sync(0xffffffffu, ym, 1));
+        const int c = b4 / kChunk;
+        if ((lane & 1) == 0 &&
+            DDSP_BC(c < sps_chunk_cap(bufcap), kBcSpsStats, c)) {
+          cmin[c] = cn;
+          cmax[c] = cx;
+          ymax[c] = ym;
         }
       }
     }
@@ -607,10 +830,6 @@ __device__ __forceinline__ void sps_window(
   const uint32_t *Q = reinterpret_cast<const uint32_t *>(buf);
 
   // ---- 4. boxcars, S/N, candidates
-  // The window's widths, integer thresholds and FP32 scales sit in
-  // registers; one unrolled pass loads every boxcar sum of a start time.
-  // Widths ascend, so those running past the series end (t - lo + w >
-  // n - lo) are a suffix of the list, as the reference loop's early exit.
   int32_t wv[kMaxWidths], tbv[kMaxWidths];
   float iv[kMaxWidths];
 #pragma unroll
@@ -622,105 +841,144 @@ __device__ __forceinline__ void sps_window(
   }
   // i + w <= n - lo also implies i + w <= elen, the last prefix index
   const int nv = (int)min(n - lo, (int64_t)elen);
+  if (!DENSE && MAD4 <= 0)
+    return;   // S/N 0 everywhere: no candidates (threshold > 0)
   bool pow2 = true;
-  for (int wi = 0; wi < nw; ++wi) pow2 = pow2 && wv[wi] == (1 << wi);
-  if (pow2) {
-    switch (nw) {
-#define DDSP_SWEEP(N)                                                        \
-  case N:                                                                    \
-    sweep_pow2<N, DENSE>(Q, sh, len, nv, tbv, odd, mfloor, thr, lo, n, nrep, \
-                         k, cands, count, cap, best_w, best_snr, best_sum);  \
+#pragma unroll
+  for (int wi = 0; wi < kMaxWidths; ++wi)
+    pow2 = pow2 && (wi >= nw || wv[wi] == (1 << wi));
+  const SweepArgs g{Q,    (int)bufcap, len,   nv,    nw,     odd,  mfloor,
+                    thr,  lo,          n,     nrep,  k,      wmax, bounds,
+                    cmin, cmax,        ymax,  cands, count,  cap,  best_w,
+                    best_snr, best_sum};
+  switch (pow2 ? nw : 0) {
+#define DDSP_SWEEP(N)                        \
+  case N:                                    \
+    sweep<DENSE, N>(g, wv, tbv, iv, bufcap); \
     return;
-      DDSP_SWEEP(1) DDSP_SWEEP(2) DDSP_SWEEP(3) DDSP_SWEEP(4) DDSP_SWEEP(5)
-      DDSP_SWEEP(6) DDSP_SWEEP(7) DDSP_SWEEP(8) DDSP_SWEEP(9) DDSP_SWEEP(10)
-      DDSP_SWEEP(11)
+    DDSP_SWEEP(1) DDSP_SWEEP(2) DDSP_SWEEP(3) DDSP_SWEEP(4) DDSP_SWEEP(5)
+    DDSP_SWEEP(6) DDSP_SWEEP(7) DDSP_SWEEP(8) DDSP_SWEEP(9) DDSP_SWEEP(10)
+    DDSP_SWEEP(11)
 #undef DDSP_SWEEP
-      default:
-        break;
-    }
-  }
-  // any other ascending width list
-  for (int i0 = 0; i0 < len; i0 += kSpsThreads) {
-    const int i = i0 + tid;
-    const bool in = i < len;
-    int32_t by[kMaxWidths];
-    bool pass = false;
-    if (in) {
-      const uint32_t qi = Q[i];
-#pragma unroll
-      for (int wi = 0; wi < kMaxWidths; ++wi) {
-        by[wi] = 0;
-        if (wi < nw) {
-          by[wi] = (int32_t)(Q[min(i + wv[wi], nv)] - qi);
-          pass |= (i + wv[wi] <= nv) && by[wi] >= tbv[wi];
-        }
-      }
-    }
-    if (DENSE || pass) {
-      int bw = -1;
-      float bs = 0.0f;
-      int32_t bsum = 0;
-      if (in) {
-#pragma unroll
-        for (int wi = 0; wi < kMaxWidths; ++wi) {
-          if (wi < nw && i + wv[wi] <= nv) {
-            const float sn = twice_minus(by[wi], wv[wi] * odd) * iv[wi];
-            if (bw < 0 || sn > bs) {
-              bw = wi;
-              bs = sn;
-              bsum = by[wi] + wv[wi] * mfloor;
-            }
-          }
-        }
-      }
-      if (DENSE) {
-        if (in) {
-          const int64_t o = (int64_t)k * n + lo + i;
-          best_w[o] = bw;
-          best_snr[o] = bs;
-          best_sum[o] = bsum;
-        }
-      } else {
-        const bool cand = in && bw >= 0 && bs >= thr && lo + i < nrep;
-        const uint32_t ball = __ballot_sync(__activemask(), cand);
-        if (cand) {
-          const int leader = __ffs(ball) - 1;
-          uint32_t base = 0;
-          if (lane == leader) base = atomicAdd(count, (uint32_t)__popc(ball));
-          base = __shfl_sync(ball, base, leader);
-          const uint32_t slot = base + __popc(ball & ((1u << lane) - 1u));
-          if (slot < cap) {
-            ddsp_cand c;
-            c.dm_idx = (uint32_t)k;
-            c.t = (uint32_t)(lo + i);
-            c.w_idx = (uint32_t)bw;
-            c.snr = bs;
-            cands[slot] = c;
-          }
-        }
-      }
-    }
+    default:
+      sweep<DENSE, 0>(g, wv, tbv, iv, bufcap);
   }
 }
 
 template <bool DENSE>
-__global__ void __launch_bounds__(kSpsThreads, 2)
+__global__ void __launch_bounds__(kSpsThreads, 4)
 sps_kernel(const int32_t *__restrict__ series, int64_t n, int64_t L,
            int64_t nwin, const int32_t *__restrict__ widths, int nw, float thr,
            int64_t *__restrict__ m2_out, int64_t *__restrict__ mad4_out,
            ddsp_cand *__restrict__ cands, uint32_t *__restrict__ count,
            uint32_t cap, int32_t *__restrict__ best_w,
            float *__restrict__ best_snr, int32_t *__restrict__ best_sum,
-           int32_t *__restrict__ err) {
+           int32_t *__restrict__ err, int64_t bufcap) {
   sps_window<DENSE>(series, n, L, nwin, widths, nw, thr, m2_out, mad4_out,
                     cands, count, cap, best_w, best_snr, best_sum, err,
-                    blockIdx.x, blockIdx.y, n);
+                    blockIdx.x, blockIdx.y, n, bufcap);
+}
+
+// Long mode, first pass: the exact median and MAD of each window straight
+// from global memory (windows too long for shared memory): the window's
+// minimum and maximum, then the histogram narrowing of select2 (2048 bins
+// per pass over the window) for the two middle order statistics of
+// x - min and of |2(x - min) - (m2 - 2 min)|; grid (window, DM trial).
+__global__ void __launch_bounds__(kSpsThreads)
+sps_long_stats_kernel(const int32_t *__restrict__ series, int64_t n, int64_t L,
+                      int64_t nwin, int64_t *__restrict__ m2_out,
+                      int64_t *__restrict__ mad4_out, int32_t *__restrict__ err) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SpsShared &sh = *reinterpret_cast<SpsShared *>(smem_raw);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t j = blockIdx.x;
+  const int k = blockIdx.y;
+  const int64_t lo = (L <= 0) ? 0 : j * L;
+  const int64_t hi = (L <= 0 || j == nwin - 1) ? n : (j + 1) * L;
+  const int len = (int)(hi - lo);
+  const int32_t *x = series + (int64_t)k * n + lo;
+  int32_t mn32 = INT32_MAX, mx32 = INT32_MIN;
+  for (int i = tid; i < len; i += kSpsThreads) {
+    if (!DDSP_BC(lo + i < n, kBcSpsLoad, lo + i)) continue;
+    const int32_t v = __ldg(x + i);
+    mn32 = min(mn32, v);
+    mx32 = max(mx32, v);
+  }
+  mn32 = __reduce_min_sync(0xffffffffu, mn32);
+  mx32 = __reduce_max_sync(0xffffffffu, mx32);
+  if (lane == 0) {
+    sh.wred[warp][0] = (uint32_t)mn32;
+    sh.wred[warp][1] = (uint32_t)mx32;
+  }
+  __syncthreads();
+  int64_t mn = INT32_MAX, mx = INT32_MIN;
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) {
+    mn = min(mn, (int64_t)(int32_t)sh.wred[w][0]);
+    mx = max(mx, (int64_t)(int32_t)sh.wred[w][1]);
+  }
+  __syncthreads();
+  int64_t M2 = 0, MAD4 = 0;
+  if ((mx - mn) < (int64_t)1 << 31) {
+    const int r1 = (len - 1) / 2, r2 = len / 2;
+    const uint32_t base = (uint32_t)(int32_t)mn;
+    uint32_t k1, k2, u1, u2;
+    select2([&](int i) { return (uint32_t)__ldg(x + i) - base; }, len, r1, r2,
+            (uint32_t)(mx - mn), sh, k1, k2);
+    M2 = 2 * mn + (int64_t)k1 + (int64_t)k2;
+    const uint32_t m2r = (uint32_t)(M2 - 2 * mn);
+    const uint64_t umax = (uint64_t)max(2 * mx - M2, M2 - 2 * mn);
+    select2(
+        [&](int i) {
+          const uint32_t t2 = 2u * ((uint32_t)__ldg(x + i) - base);
+          return t2 >= m2r ? t2 - m2r : m2r - t2;
+        },
+        len, r1, r2, (uint32_t)umax, sh, u1, u2);
+    MAD4 = (int64_t)u1 + (int64_t)u2;
+  } else if (tid == 0) {
+    atomicExch(err, kErrRange);
+  }
+  if (tid == 0) {
+    m2_out[(int64_t)k * nwin + j] = M2;
+    mad4_out[(int64_t)k * nwin + j] = MAD4;
+  }
+}
+
+// Long mode, second pass: block (b, k) searches segment s of window j of DM
+// trial k with that window's statistics; windows 0 .. nwin-2 (L samples)
+// have segs_full segments each, the last window the rest.
+template <bool DENSE>
+__global__ void __launch_bounds__(kSpsThreads, 4)
+sps_seg_kernel(const int32_t *__restrict__ series, int64_t n, int64_t L,
+               int64_t nwin, const int32_t *__restrict__ widths, int nw,
+               float thr, int64_t *__restrict__ m2_out,
+               int64_t *__restrict__ mad4_out, ddsp_cand *__restrict__ cands,
+               uint32_t *__restrict__ count, uint32_t cap,
+               int32_t *__restrict__ best_w, float *__restrict__ best_snr,
+               int32_t *__restrict__ best_sum, int32_t *__restrict__ err,
+               int64_t bufcap, int64_t segs_full) {
+  const int64_t bx = blockIdx.x;
+  int64_t j, sg;
+  if (nwin == 1) {
+    j = 0;
+    sg = bx;
+  } else if (bx < (nwin - 1) * segs_full) {
+    j = bx / segs_full;
+    sg = bx - j * segs_full;
+  } else {
+    j = nwin - 1;
+    sg = bx - (nwin - 1) * segs_full;
+  }
+  sps_window<DENSE>(series, n, L, nwin, widths, nw, thr, m2_out, mad4_out,
+                    cands, count, cap, best_w, best_snr, best_sum, err, j,
+                    blockIdx.y, n, bufcap, sg);
 }
 
 // Many beams in one launch: flattened block b -> the beam whose block0 is
 // the largest <= b, then (DM trial, window) inside it.
-__global__ void __launch_bounds__(kSpsThreads, 2)
-sps_batch_kernel(const SpsBeam *__restrict__ beams, int nbeams, float thr) {
+__global__ void __launch_bounds__(kSpsThreads, 4)
+sps_batch_kernel(const SpsBeam *__restrict__ beams, int nbeams, float thr,
+                 int64_t bufcap) {
   const int64_t bid = blockIdx.x;
   int lo = 0, hi = nbeams - 1;
   while (lo < hi) {
@@ -733,31 +991,37 @@ sps_batch_kernel(const SpsBeam *__restrict__ beams, int nbeams, float thr) {
   const int64_t j = local - (int64_t)k * b.nwin;
   sps_window<false>(b.series, b.n, b.L, b.nwin, b.widths, b.nw, thr, b.m2,
                     b.mad4, b.cands, b.count, b.cap, nullptr, nullptr,
-                    nullptr, b.err, j, k, b.nrep);
+                    nullptr, b.err, j, k, b.nrep, bufcap);
 }
 
 }  // namespace
 
 int64_t sps_max_window_samples() { return kMaxWindowSamples; }
 
+int64_t sps_bufcap(int64_t maxlen, int wmax) { return sps_buf_cap(maxlen, wmax); }
+
 size_t sps_smem_bytes(int64_t maxlen, int wmax) {
-  return kBufOff + 4 * (size_t)(maxlen + wmax + 4);
+  const int64_t cap = sps_buf_cap(maxlen, wmax);
+  const int64_t ccap = sps_chunk_cap(cap);
+  const bool separate = 3 * ccap > kFastBins && cap <= kStatsMaxCap;
+  return kBufOff + 4 * (size_t)cap + (separate ? 12 * (size_t)ccap : 0);
 }
 
 // Largest dynamic shared memory a search launch asks for (the largest
 // window the search accepts); the kernels are opted in to the device's
 // limit once (smem_opt_in), shared by plan, batch, server and
 // allocation-free launches and never lowered.
-constexpr size_t kSpsMaxSmem = kBufOff + 4 * (size_t)(kMaxWindowSamples + 4);
+constexpr size_t kSpsMaxSmem =
+    kBufOff + 4 * (size_t)(((kMaxWindowSamples + 1 + 127) / 128) * 128);
 
 cudaError_t launch_sps_batch(const SpsBeam *d_beams, int nbeams,
                              int64_t total_blocks, float threshold,
-                             size_t smem, cudaStream_t s) {
+                             size_t smem, int64_t bufcap, cudaStream_t s) {
   if (smem > kSpsMaxSmem) return cudaErrorInvalidValue;
   cudaError_t e = smem_opt_in(sps_batch_kernel);
   if (e != cudaSuccess) return e;
   sps_batch_kernel<<<(unsigned)total_blocks, kSpsThreads, smem, s>>>(
-      d_beams, nbeams, threshold);
+      d_beams, nbeams, threshold, bufcap);
   return cudaGetLastError();
 }
 
@@ -770,8 +1034,27 @@ cudaError_t launch_sps(const Plan &p, const int32_t *d_series,
   int64_t maxlen = (L <= 0 || nwin == 1) ? nsamp_out
                                          : max(L, nsamp_out - (nwin - 1) * L);
   const int wmax = p.widths.back();
-  const size_t smem =
-      kBufOff + 4 * (size_t)(maxlen + wmax + 4);
+  if (maxlen + wmax > kMaxWindowSamples) {
+    // long mode: statistics pass, then segments of kSeg start times
+    cudaError_t e = cudaSuccess;
+    sps_long_stats_kernel<<<dim3((unsigned)nwin, (unsigned)p.ndm), kSpsThreads,
+                            kBufOff, s>>>(d_series, nsamp_out, L, nwin, p.d_m2,
+                                          p.d_mad4, p.d_err);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const int64_t segs_full = L > 0 ? (L + kSeg - 1) / kSeg : 0;
+    const int64_t last = nwin == 1 ? nsamp_out : nsamp_out - (nwin - 1) * L;
+    const int64_t nblocks = (nwin - 1) * segs_full + (last + kSeg - 1) / kSeg;
+    if (nblocks > 0x7fffffff) return cudaErrorInvalidValue;
+    const size_t smem = sps_smem_bytes(kSeg, wmax);
+    auto seg = dense ? sps_seg_kernel<true> : sps_seg_kernel<false>;
+    if ((e = smem_opt_in(seg)) != cudaSuccess) return e;
+    seg<<<dim3((unsigned)nblocks, (unsigned)p.ndm), kSpsThreads, smem, s>>>(
+        d_series, nsamp_out, L, nwin, p.d_widths, p.nwidths, threshold, p.d_m2,
+        p.d_mad4, p.d_cands, p.d_count, (uint32_t)p.cand_capacity, d_best_w,
+        d_best_snr, d_best_sum, p.d_err, sps_buf_cap(kSeg, wmax), segs_full);
+    return cudaGetLastError();
+  }
+  const size_t smem = sps_smem_bytes(maxlen, wmax);
   if (smem > kSpsMaxSmem) return cudaErrorInvalidValue;
   auto kern = dense ? sps_kernel<true> : sps_kernel<false>;
   cudaError_t e = smem_opt_in(kern);
@@ -780,7 +1063,7 @@ cudaError_t launch_sps(const Plan &p, const int32_t *d_series,
   kern<<<grid, kSpsThreads, smem, s>>>(
       d_series, nsamp_out, L, nwin, p.d_widths, p.nwidths, threshold, p.d_m2,
       p.d_mad4, p.d_cands, p.d_count, (uint32_t)p.cand_capacity, d_best_w,
-      d_best_snr, d_best_sum, p.d_err);
+      d_best_snr, d_best_sum, p.d_err, sps_buf_cap(maxlen, wmax));
   return cudaGetLastError();
 }
 
@@ -887,7 +1170,7 @@ extern "C" int ddsp_single_pulse_search_noalloc(
   int32_t *d_err = reinterpret_cast<int32_t *>(base + kNoAllocErrOff);
 
   cudaStream_t s = (cudaStream_t)stream;
-  const size_t smem = kBufOff + 4 * (size_t)(maxlen + wmax + 4);
+  const size_t smem = sps_smem_bytes(maxlen, wmax);
   auto kern = sps_kernel<false>;
   if (smem > kSpsMaxSmem || smem_opt_in(kern) != cudaSuccess)
     return DDSP_E_CUDA;
@@ -903,7 +1186,7 @@ extern "C" int ddsp_single_pulse_search_noalloc(
   kern<<<grid, kSpsThreads, smem, s>>>(d_series, nsamp_out, L, nwin, d_widths,
                                        nwidths, threshold, m2, mad4, d_cands,
                                        d_count, cand_capacity, nullptr, nullptr,
-                                       nullptr, d_err);
+                                       nullptr, d_err, sps_bufcap(maxlen, wmax));
   return cudaGetLastError() == cudaSuccess ? DDSP_OK : DDSP_E_CUDA;
 }
 

@@ -4,6 +4,7 @@
 // contiguous bulk copy.  HBM-bound: every byte is read once and written once.
 // Each row gets columns [0, ncols) (ncols <= pitch): input samples, then
 // zeros past nsamp_in; columns from ncols to the pitch are left untouched.
+#include "dev_util.cuh"
 #include "internal.h"
 
 namespace ddsp {
@@ -32,7 +33,7 @@ __device__ __forceinline__ void unpack_u8_tile(
     int64_t s = s0 + row;
     int c = c0 + 16 * q;
     uint4 v = make_uint4(0, 0, 0, 0);
-    if (s < nsamp_in && c < nchan)
+    if (s < nsamp_in && c < nchan && DDSP_BC(c + 16 <= nchan, kBcUnpackIn, c))
       v = __ldg(reinterpret_cast<const uint4 *>(in + s * nchan + c));
     uint32_t *dst = tile + row * kPitchW + 4 * q;
     dst[0] = v.x; dst[1] = v.y; dst[2] = v.z; dst[3] = v.w;
@@ -55,7 +56,7 @@ __device__ __forceinline__ void unpack_u8_tile(
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       int c = c0 + 4 * cq + j;
-      if (c < nchan && s < ncols)
+      if (c < nchan && s < ncols && DDSP_BC(s + 4 <= pitch, kBcUnpackOut, s))
         *reinterpret_cast<uint32_t *>(out + (int64_t)c * pitch + s) = o[j];
     }
   }
@@ -91,7 +92,8 @@ unpack_generic_kernel(const T *__restrict__ in, int64_t nsamp_in, int nchan,
   for (int r = ty; r < 32; r += 8) {
     int c = c0 + r;
     int64_t s = s0 + tx;
-    if (c < nchan && s < ncols) out[(int64_t)c * pitch + s] = tile[tx][r];
+    if (c < nchan && s < ncols && DDSP_BC(s < pitch, kBcUnpackOut, s))
+      out[(int64_t)c * pitch + s] = tile[tx][r];
   }
 }
 

@@ -21,6 +21,11 @@ using namespace ddsp;
 
 namespace ddsp {
 
+#ifdef DDSP_BOUNDS_CHECK
+// First bounds violation of any kernel of the checked build (0: none).
+__device__ unsigned long long g_bounds_first = 0ull;
+#endif
+
 constexpr double kDispersionConst = 4148.808;  // s MHz^2 per (pc cm^-3)
 
 thread_local char g_detail[256] = "";
@@ -289,12 +294,13 @@ void release(Plan &p) {
   cudaFree(p.d_rs);
 }
 
-int search_windows(const Plan &p, int64_t n, int64_t *nwin) {
+int search_windows(const Plan &p, int64_t n, int64_t *nwin, bool allow_long) {
   const int64_t L = p.norm_window;
   *nwin = (L <= 0) ? 1 : std::max<int64_t>(1, n / L);
   const int64_t maxlen =
       (L <= 0 || *nwin == 1) ? n : std::max(L, n - (*nwin - 1) * L);
-  if (maxlen + p.widths.back() > sps_max_window_samples()) return DDSP_E_SHAPE;
+  if (!allow_long && maxlen + p.widths.back() > sps_max_window_samples())
+    return DDSP_E_SHAPE;
   if (*nwin > 0x7fffffff) return DDSP_E_SHAPE;
   return DDSP_OK;
 }
@@ -404,6 +410,7 @@ int ddsp_plan_create(ddsp_plan **out, int nchan, double f_top_mhz,
   std::stable_sort(p.order.begin(), p.order.end(),
                    [&](int a, int b) { return p.dms[a] < p.dms[b]; });
   p.tile = choose_tile(p);
+  apply_cached_tile(p);   // a tile autotuned for this shape, if cached
 
   int rc = build_tables(p);
   cudaError_t e = cudaSuccess;
@@ -472,23 +479,41 @@ int ddsp_plan_set_tile(ddsp_plan *h, int dm_tile, int dm_per_thread,
   } else if (dm_tile == -1) {
     t = DedispTile{};  // direct kernel
   } else {
-    t.rd = dm_per_thread;
-    if (t.rd != 2 && t.rd != 4 && t.rd != 8) return DDSP_E_INVALID_ARG;
-    if (dm_tile % t.rd) return DDSP_E_INVALID_ARG;
-    t.wd = dm_tile / t.rd;
-    if (t.wd <= 0 || (kThreads / 32) % t.wd) return DDSP_E_INVALID_ARG;
-    t.wt = (kThreads / 32) / t.wd * ((flags & kTileWide) ? 2 : 1);
-    t.chan_chunk = chan_chunk;
-    t.nbuf = stages;
-    if (flags & ~(kTileSingleElemBuffer | kTileRegisterTotals |
-                  kTileWarpSpecialized | kTileInterleaved | kTileWide))
-      return DDSP_E_INVALID_ARG;
-    t.flags = flags;
-    if (!dedisp_tile_supported(t, p.nbits)) return DDSP_E_INVALID_ARG;
-    const int span = span_for(p, t.dm_tile());
-    if (dedisp_smem_bytes(t, span, p.nbits) > kSmemBudgetOneBlock)
-      return DDSP_E_INVALID_ARG;
+    const int rc = tile_from_args(p, dm_tile, dm_per_thread, chan_chunk,
+                                  stages, flags, &t);
+    if (rc != DDSP_OK) return rc;
   }
+  return apply_tile(p, t);
+}
+
+}  // extern "C"
+
+namespace ddsp {
+
+int tile_from_args(const Plan &p, int dm_tile, int dm_per_thread,
+                   int chan_chunk, int stages, int flags, DedispTile *out) {
+  DedispTile t;
+  t.rd = dm_per_thread;
+  if (t.rd != 2 && t.rd != 4 && t.rd != 8) return DDSP_E_INVALID_ARG;
+  if (dm_tile <= 0 || dm_tile % t.rd) return DDSP_E_INVALID_ARG;
+  t.wd = dm_tile / t.rd;
+  if (t.wd <= 0 || (kThreads / 32) % t.wd) return DDSP_E_INVALID_ARG;
+  t.wt = (kThreads / 32) / t.wd * ((flags & kTileWide) ? 2 : 1);
+  t.chan_chunk = chan_chunk;
+  t.nbuf = stages;
+  if (flags & ~(kTileSingleElemBuffer | kTileRegisterTotals |
+                kTileWarpSpecialized | kTileInterleaved | kTileWide))
+    return DDSP_E_INVALID_ARG;
+  t.flags = flags;
+  if (!dedisp_tile_supported(t, p.nbits)) return DDSP_E_INVALID_ARG;
+  const int span = span_for(p, t.dm_tile());
+  if (dedisp_smem_bytes(t, span, p.nbits) > kSmemBudgetOneBlock)
+    return DDSP_E_INVALID_ARG;
+  *out = t;
+  return DDSP_OK;
+}
+
+int apply_tile(Plan &p, const DedispTile &t) {
   cudaDeviceSynchronize();
   p.tile = t;
   p.staged_nout = 0;   // a staged block belongs to the tile that staged it
@@ -498,6 +523,29 @@ int ddsp_plan_set_tile(ddsp_plan *h, int dm_tile, int dm_per_thread,
     p.il_bytes = 0;
   }
   return build_tables(p);
+}
+
+}  // namespace ddsp
+
+extern "C" {
+
+int ddsp_bounds_check_status(int *enabled, uint64_t *first) {
+  if (!enabled || !first) return DDSP_E_INVALID_ARG;
+#ifdef DDSP_BOUNDS_CHECK
+  *enabled = 1;
+  unsigned long long v = 0, zero = 0;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess)
+    e = cudaMemcpyFromSymbol(&v, g_bounds_first, sizeof(v));
+  if (e == cudaSuccess && v)
+    e = cudaMemcpyToSymbol(g_bounds_first, &zero, sizeof(zero));
+  if (e != cudaSuccess) return cuda_rc(e);
+  *first = v;
+#else
+  *enabled = 0;
+  *first = 0;
+#endif
+  return DDSP_OK;
 }
 
 int ddsp_plan_set_wait_limit(ddsp_plan *h, int64_t cycles) {
@@ -643,7 +691,8 @@ static int run_search(ddsp_plan *h, const int32_t *d_series, int64_t n,
   Plan &p = h->p;
   DeviceGuard g(p.device);
   int64_t nwin;
-  int rc = search_windows(p, n, &nwin);
+  // windows longer than the on-chip limit take the two-pass long mode
+  int rc = search_windows(p, n, &nwin, true);
   if (rc != DDSP_OK) return rc;
   if (nwin > 0x7fffffff) return DDSP_E_SHAPE;
   rc = ensure_stats(p, (size_t)nwin * p.ndm);

@@ -70,6 +70,7 @@ struct ddsp_server {
   DedispTables tab;
   int cc = 0, rawmax = 0, elmax = 0, grid = 0, ipb = 0, ntt = 0;
   size_t smem = 0, sps_smem = 0;
+  int64_t sps_cap = 0;
   int max_beams = 0;
   int64_t reserve = 0;
   uint32_t cap = 0;
@@ -380,6 +381,7 @@ int ddsp_server_create(ddsp_server **out, ddsp_plan *plan,
                                : std::max<int64_t>(p.norm_window,
                                                    S->ncols - (S->nwin - 1) * p.norm_window);
     S->sps_smem = sps_smem_bytes(maxlen, p.widths.back());
+    S->sps_cap = sps_bufcap(maxlen, p.widths.back());
     S->beams.resize(max_beams);
     cudaError_t e = cudaSuccess;
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
@@ -633,7 +635,7 @@ int ddsp_server_step(ddsp_server *S, float threshold, int max_beams_in_step,
     if (e == cudaSuccess)
       e = launch_sps_batch(S->d_sb[par] + g0, gn,
                            (int64_t)gn * p.ndm * S->nwin, threshold,
-                           S->sps_smem, s);
+                           S->sps_smem, S->sps_cap, s);
     if (e == cudaSuccess)
       e = launch_serve_carry(S->d_sb[par] + g0, S->d_carry[par] + g0, gn,
                              p.ndm, S->ncols, (int)S->C, false, nullptr, s);

@@ -105,12 +105,16 @@ struct WsAcc {
 // on the FMA pipe, and the two byte permutes on the ALU pipe: 3 ALU and 2
 // FMA operations per 8 sample adds, where all-ALU would be 4 against the
 // half-rate ALU pipe's 64 operations per SM clock.
+// (i0: this thread's first element, for the bounds-checked build: every
+// element it reads of a channel, i0 + rel/4 + 32 e for e < E, must lie in
+// the channel's elmax elements; an offset that does not is replaced by one
+// that reads element i0 and the violation is recorded.)
 template <int RD, int SPE, int E>
 __device__ __forceinline__ void ws_accumulate(WsAcc<RD, SPE, E> &acc,
                                               const int32_t *rel, int dt,
                                               const unsigned char *ebase,
                                               int elmax, int ncur,
-                                              uint32_t one) {
+                                              uint32_t one, int i0 = 0) {
   auto offsets = [&](int q, int(&rr)[RD]) {
 #pragma unroll
     for (int h = 0; h < RD; h += 4) {
@@ -120,6 +124,15 @@ __device__ __forceinline__ void ws_accumulate(WsAcc<RD, SPE, E> &acc,
       rr[h + 2] = ro.z;
       rr[h + 3] = ro.w;
     }
+#ifdef DDSP_BOUNDS_CHECK
+#pragma unroll
+    for (int h = 0; h < RD; ++h) {
+      const int64_t last = (int64_t)i0 + rr[h] / 4 + 32 * (E - 1);
+      if (!DDSP_BC(rr[h] >= 0 && (rr[h] & 3) == 0 && last < elmax, kBcIlElem,
+                   last))
+        rr[h] = 0;
+    }
+#endif
   };
   int q = 0;
   for (; q + 1 < ncur; q += 2) {
@@ -191,7 +204,7 @@ __device__ __forceinline__ void ws_flush(WsAcc<RD, 4, E> &acc,
 #pragma unroll
       for (int m = 0; m < 4; ++m) {
         const int64_t t = t0 + 32 * e + (int64_t)m * S;
-        if (row >= 0 && t < nsamp_out) {
+        if (row >= 0 && t < nsamp_out && DDSP_BC(t >= 0, kBcIlOut, t)) {
           if (first) o[t] = part[m];
           else atomicAdd(o + t, part[m]);
         }
@@ -437,7 +450,7 @@ __device__ __forceinline__ bool ws_item(const WsBeam &a, int g, int64_t T0,
       return false;
     }
     ws_accumulate(acc, erel + b * rel_words + RD * wd, DT,
-                  elem + b * L.elem_stride + 4 * i0, elmax, ncur, one);
+                  elem + b * L.elem_stride + 4 * i0, elmax, ncur, one, i0);
     __syncwarp();
     if (lane == 0) mbar_arrive(&elem_empty[b]);
     if constexpr (SPE == 4) {

@@ -29,6 +29,8 @@ class ServeResult:
     ncand: np.ndarray              # [beams, blocks] candidates found
     step_sizes: list = field(default_factory=list)  # beams per step
     wall: float = 0.0              # seconds from start to the last completion
+    busy: float = float("nan")     # device seconds of the pushes and steps
+                                   # (with device timing), nan otherwise
 
     def percentile(self, q):
         v = self.latency[np.isfinite(self.latency)]
@@ -89,7 +91,7 @@ class ServingLoop:
     def __init__(self, server, beams, source, threshold, stager=None,
                  max_beams_in_step=0, max_inflight=1, compute_stream=None,
                  clock=time.monotonic, sleep=time.sleep, poll=2e-4,
-                 on_candidates=None, first_block=0):
+                 on_candidates=None, first_block=0, device_timing=False):
         self.server = server
         self.beams = list(beams)
         self.source = source
@@ -104,6 +106,24 @@ class ServingLoop:
         self.on_candidates = on_candidates
         self.first_block = int(first_block)
         self.max_waiting = int(getattr(server, "max_waiting", 1))
+        # device_timing: CUDA events around every push and step on the
+        # compute stream, summed into ServeResult.busy (the device time the
+        # schedule needed: above the schedule's span the load is not
+        # sustainable however short the run)
+        self.device_timing = bool(device_timing)
+        self._spans = []
+
+    def _timed(self, fn):
+        if not self.device_timing:
+            return fn()
+        import torch
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(self.stream)
+        out = fn()
+        e1.record(self.stream)
+        self._spans.append((e0, e1))
+        return out
 
     def run(self, arrivals, time_limit=None):
         """Serve the schedule (arrivals[i][k] = seconds after the start at
@@ -153,7 +173,8 @@ class ServingLoop:
                         x, token = self.stager.stage(host)
                     else:
                         x, token = host, None
-                    ok = self.server.push(self.beams[i], x, stream=self.stream)
+                    ok = self._timed(lambda: self.server.push(
+                        self.beams[i], x, stream=self.stream))
                     if self.stager is not None:
                         self.stager.consumed(token)
                     if not ok:
@@ -185,9 +206,8 @@ class ServingLoop:
                 self._fetch(finished, res)
                 finished = []
             if len(inflight) < self.max_inflight and unstepped > 0:
-                sid, sbeams = self.server.step(self.threshold,
-                                               self.max_beams_in_step,
-                                               stream=self.stream)
+                sid, sbeams = self._timed(lambda: self.server.step(
+                    self.threshold, self.max_beams_in_step, stream=self.stream))
                 if sbeams:
                     members = []
                     for b in sbeams:
@@ -204,6 +224,13 @@ class ServingLoop:
                 if nexta < total and np.isfinite(flat[order[nexta]]):
                     wait = min(wait, max(0.0, flat[order[nexta]] - now))
                 self.sleep(wait)
+        if self.device_timing:
+            import torch
+            torch.cuda.current_stream().synchronize()
+            if self.stream is not None:
+                self.stream.synchronize()
+            res.busy = sum(a.elapsed_time(b) for a, b in self._spans) * 1e-3
+            self._spans = []
         return res
 
 

@@ -30,3 +30,20 @@ def pytest_collection_modifyitems(config, items):
     for it in items:
         if "gpu" in it.keywords:
             it.add_marker(skip)
+
+
+def pytest_sessionfinish(session, exitstatus):
+    """With DDSP_BOUNDS_REPORT set (a run against the bounds-checked build,
+    see test_gpu_bounds.py): write '<enabled> <first violation>' there and
+    fail the session if a check failed."""
+    path = os.environ.get("DDSP_BOUNDS_REPORT")
+    if not path:
+        return
+    import ctypes as C
+    from paper_2605_03531_b300 import _lib
+    en, v = C.c_int(), C.c_uint64()
+    rc = _lib.lib().ddsp_bounds_check_status(C.byref(en), C.byref(v))
+    with open(path, "w") as f:
+        f.write(f"{en.value} {v.value}\n")
+    if rc != 0 or v.value:
+        session.exitstatus = 1

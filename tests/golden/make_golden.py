@@ -13,7 +13,9 @@ c5: ten 16384-sample blocks of one streaming beam of that shape
     window [j*B - D16 - C, (j+1)*B - (D16 - D)) with zeros before the stream
     (D16 = D rounded up to 16, C = the widest boxcar minus one rounded up to
     4), i.e. C + B output columns whose candidates are reported for start
-    times t < B; a digest of every 16 dedispersed rows and the candidates.
+    times t < B; a digest of every 16 dedispersed rows and the candidates
+    (for the first blocks, whose windows reach before the stream, those of
+    a few DM rows).
 """
 import os
 import sys
@@ -28,8 +30,9 @@ sys.path.insert(0, os.path.dirname(HERE))
 
 import oracle                                     # noqa: E402
 from paper_2605_03531_b300 import synth           # noqa: E402
-from parity import (THR_EXEMPT, row_digests, sps_parallel,  # noqa: E402
-                    write_candidates, write_digests, STORED_DTYPE)
+from parity import (THR_EXEMPT, C5_EARLY_ROWS, row_digests,  # noqa: E402
+                    sps_parallel, write_candidates, write_digests,
+                    STORED_DTYPE)
 
 
 def _stored(c, block=0, keep=None):
@@ -79,6 +82,7 @@ def make_c5(nblocks=10):
     D16 = -(-D // 16) * 16
     C = -(-(max(cfg.widths) - 1) // 4) * 4
     pre = D16 + C
+    warm = -(-pre // B)     # blocks whose window reaches before the stream
     xz = np.concatenate([np.zeros((pre, cfg.nchan), np.uint8), x])
     thr_lo = cfg.threshold * (1.0 - THR_EXEMPT)
     digests, cands = [], []
@@ -89,9 +93,12 @@ def make_c5(nblocks=10):
         for g, dg in enumerate(row_digests(s, 16)):
             digests.append((f"{j}:{16 * g}", dg))
         c, _ = sps_parallel(s, cfg.widths, cfg.norm_window, thr_lo)
-        cands.append(_stored(c, j, c["t"] < B))
+        keep = c["t"] < B
+        if j < warm:
+            keep &= np.isin(c["dm_idx"], C5_EARLY_ROWS)
+        cands.append(_stored(c, j, keep))
         print(f"c5 block {j}: {int((c['t'] < B).sum())} candidates, "
-              f"{time.time() - t0:.0f} s", flush=True)
+              f"{int(keep.sum())} kept, {time.time() - t0:.0f} s", flush=True)
     head = [f"c5: {cfg.name}, B {B}, D {D}, D16 {D16}, C {C}, seed {cfg.seed}, "
             f"{len(cfg.pulses)} pulses",
             "block j = oracle.dedisperse of the input window "
@@ -104,6 +111,8 @@ def make_c5(nblocks=10):
         os.path.join(HERE, "c5_candidates.txt"),
         [f"c5: oracle.sps per block (C + B columns, L {cfg.norm_window}, "
          f"thr 7*(1-1e-4)), start times t < B kept -> {allc.size} records",
+         f"blocks 0..{warm - 1} (windows reaching before the stream): DM rows "
+         f"{list(C5_EARLY_ROWS)} only",
          "columns: block dm_idx t(column of the block's series) w_idx snr",
          "written by tests/golden/make_golden.py c5"], allc)
 

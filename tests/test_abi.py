@@ -43,6 +43,19 @@ def test_exports_every_declared_symbol(L):
     assert sorted(_lib.SIGNATURES) == names
 
 
+def test_bounds_build_exports_the_same_symbols(L):
+    """The bounds-checked build (tests only) has the same ABI; only it
+    reports itself as checked."""
+    lib = build.build_bounds()
+    out = subprocess.run(["nm", "-D", "--defined-only", lib],
+                         capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\sT\s+(\S+)", out))
+    assert not [n for n in declared_functions() if n not in exported]
+    en, v = C.c_int(), C.c_uint64()
+    assert L.ddsp_bounds_check_status(C.byref(en), C.byref(v)) == 0
+    assert en.value == 0 and v.value == 0
+
+
 def test_error_strings(L):
     for code in range(0, -9, -1):
         s = L.ddsp_error_string(code).decode()

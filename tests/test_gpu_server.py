@@ -209,11 +209,13 @@ def test_server_fetch_window_and_errors():
 
 def test_server_admission_by_free_memory():
     plan = _plan()
-    probe = Server(plan, B, 1)
+    probe = Server(plan, B, 8)
     need = probe.beam_bytes
+    torch.cuda.synchronize()
+    # free memory with a server's own buffers (series slots) in place
+    free, _ = torch.cuda.mem_get_info()
     probe.close()
     torch.cuda.synchronize()
-    free, _ = torch.cuda.mem_get_info()
     # leave room for exactly one more beam (plus slack for allocator rounding)
     srv = Server(plan, B, 8, hbm_reserve_bytes=free - need - need // 2)
     srv.admit()
@@ -283,15 +285,17 @@ def test_c5_shape_blocks_match_oracle(mode):
     oracle's dedispersion of the input window [j*B - D16 - C, (j+1)*B -
     (D16 - D)) with zeros before the stream, and its candidates (start
     times t < B) equal the oracle's search of those columns under the
-    tolerance rule; both stored by tests/golden/make_golden.py."""
+    tolerance rule (for the first blocks, whose windows reach before the
+    stream and light up ~5e5 candidates, on a few DM rows); both stored by
+    tests/golden/make_golden.py."""
     import os
-    from parity import (GOLDEN, compare_to_stored, read_candidates,
-                        read_digests, row_digests)
+    from parity import (C5_EARLY_ROWS, GOLDEN, compare_to_stored,
+                        read_candidates, read_digests, row_digests)
     cfg, x = synth.config5_stream(10)
     Bc = cfg.nsamp_out
     plan = Plan(cfg.nchan, cfg.f_top, cfg.chan_bw, cfg.tsamp, cfg.dm_list(),
                 cfg.widths, nbits=8, norm_window=cfg.norm_window,
-                cand_capacity=1 << 20)
+                cand_capacity=1 << 23)
     srv = Server(plan, Bc, 2)
     if mode == "interleaved":
         srv.set_mode(Server.INTERLEAVED, 2)
@@ -319,6 +323,10 @@ def test_c5_shape_blocks_match_oracle(mode):
         assert not bad, (j, bad[:8])
         got, n, t0 = srv.fetch(beam, j)
         assert t0 == j * Bc - D16 - Cc
+        if j * Bc < D16 + Cc:
+            # the window reaches before the stream: the stored candidates
+            # are those of a few DM rows
+            got = got[np.isin(got["dm_idx"], C5_EARLY_ROWS)]
         win = xz[j * Bc: j * Bc + Cc + Bc + D]
 
         def width_check(k, t, wg, s_ref):

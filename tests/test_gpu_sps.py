@@ -221,11 +221,11 @@ def test_argument_errors():
         p.single_pulse_search(x, 0.0)
     with pytest.raises(DdspError):
         p.single_pulse_search(x, float("nan"))
+    # a window longer than the on-chip limit takes the long mode (no error)
     big = _plan(1, [1, 1024], 0)
-    with pytest.raises(DdspError) as e:
-        big.single_pulse_search(torch.zeros((1, 60000), dtype=torch.int32,
-                                            device="cuda"), 5.0)
-    assert e.value.code == -2
+    big.single_pulse_search(torch.zeros((1, 60000), dtype=torch.int32,
+                                        device="cuda"), 5.0)
+    assert big.fetch()[1] == 0          # MAD 0: no candidates
 
 
 def test_stress_config_full_size_64_rows():
@@ -304,3 +304,32 @@ def test_dense_snr_bits_with_large_sums():
             ref = np.float32(num) * inv
             assert np.float32(bs[k, t]).view(np.uint32) == ref.view(np.uint32), (k, t)
     assert big > 100
+
+
+@pytest.mark.parametrize("n,L,widths", [
+    (300000, 0, [1, 2, 4, 8, 16, 32, 64, 128, 256]),  # one window, whole series
+    (200001, 60000, [1, 4, 16, 64, 1024]),            # long windows, ragged last
+    (49152, 0, [1, 2, 4]),                             # just past the limit
+])
+def test_long_windows_dense_match_oracle(n, L, widths):
+    """Windows longer than the on-chip limit: exact statistics by a pass over
+    global memory, then the search in 8192-sample segments; statistics,
+    best widths, S/N and boxcar sums as the oracle's."""
+    x = synth.gaussian_series(3, n, seed=n % 1000 + 7).numpy()
+    check_dense(x, widths, L)
+
+
+def test_long_window_candidates_match_oracle():
+    """Normalisation over the whole series (L = 0) of 16 beam-length rows."""
+    widths = [1 << i for i in range(9)]
+    x = synth.gaussian_series(16, 262144, seed=41).numpy()
+    p = _plan(16, widths, 0)
+    p.single_pulse_search(torch.from_numpy(x).cuda(), 6.0)
+    got, n_got = p.fetch()
+    ref, n_ref = sps_parallel(x, widths, 0, 6.0)
+    assert n_ref > 0
+    compare_candidates(got, n_got, ref, n_ref, 6.0, x, widths, 0)
+    m2, mad4 = p.stats()
+    for k in (0, 15):
+        rm2, rmad4 = oracle.window_stats(x[k], 0)
+        assert np.array_equal(m2[k], rm2) and np.array_equal(mad4[k], rmad4)
