@@ -209,9 +209,10 @@ def run_reference(args):
     return 0
 
 
-def traffic_record(kernel):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source (else None)."""
+def traffic_record(kernel, field="dram_bytes_per_launch"):
+    """A per-launch figure (DRAM bytes, warp instructions) of the full-size
+    launch from the committed ncu summary, if it was taken on the current
+    kernel source (else None)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
@@ -227,7 +228,7 @@ def traffic_record(kernel):
         return None
     if h.hexdigest() != rec.get("sources_sha256"):
         return None
-    return rec.get("dram_bytes_per_launch")
+    return rec.get(field)
 
 
 def run_ours(args):
@@ -373,6 +374,12 @@ def run_ours(args):
     peak = SM_COUNT_B300 * ADDS_PER_SM_CLK * clk * 1e6 / 1e12
     achieved = adds / (k_dedisp * 1e-3) / 1e12
     traffic = traffic_record(kname) if nout == cfg.nsamp_out else None
+    # issue slots: warp instructions of the launch (ncu record) over the
+    # 4 schedulers x 148 SMs x the sampled clock x the measured duration
+    winst = (traffic_record(kname, "warp_inst_per_launch")
+             if nout == cfg.nsamp_out else None)
+    issue_frac = (winst / (k_dedisp * 1e-3 * SM_COUNT_B300 * 4 * clk * 1e6)
+                  if winst else None)
     hbm_peak = peaks.get("hbm_gbs", 6400.0)
     sps_bytes = 4.0 * cfg.ndm * nout + 16 * ncand
     # staging reads the block once and writes 4 bytes per sample (the
@@ -388,6 +395,7 @@ def run_ours(args):
             "config": workload_config(cfg, nout),
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak,
                          "unit": "Tadd/s", "frac": achieved / peak,
+                         "issue_frac": issue_frac,
                          "traffic": traffic,
                          "kernel": kname, "tile": tile,
                          "peak_basis": f"{SM_COUNT_B300} SMs x {ADDS_PER_SM_CLK} "
@@ -504,20 +512,20 @@ def serving_check(dev, blocks_per_beam=5, log=None):
         srv.close()
         torch.cuda.synchronize(dev)
         return min(ms[1:]) / nb
-    ms_b, ms_p = step_ms(32), step_ms(1)
+    ms_b, ms_p = step_ms(8), step_ms(1)
     per_beam_bytes = make(1).beam_bytes
     free, _ = torch.cuda.mem_get_info(dev)
     n_mem = int((free - reserve - slots * 4 * cfg.nchan * (B + 90112)) //
                 per_beam_bytes) // 16 * 16
-    # the counts each path's step time allows (the runs decide)
+    # the counts each path's step time allows (the runs decide): the plain
+    # path's, the next multiple of 16, and the batched path's
     est_b = int(T * 1e3 / ms_b) // 16 * 16
     est_p = int(T * 1e3 / ms_p) // 16 * 16
-    lo = min(est_p, n_mem)
-    hi = min(max(est_b, lo + 16), n_mem)
-    counts = sorted(set([lo, hi]))
+    counts = sorted(set(min(c, n_mem) for c in (est_p, est_p + 16,
+                                                max(est_b, est_p + 16))))
     runs = {"batched": {}, "plain_per_beam": {}}
 
-    def run_at(n, per_step, inflight):
+    def run_at(n, per_step, inflight, min_batch=1):
         srv = make(n)
         beams = []
         try:
@@ -539,7 +547,8 @@ def serving_check(dev, blocks_per_beam=5, log=None):
                            lambda i, k: pool[(3 * i + warm + k) % 8],
                            cfg.threshold, stager=stager, compute_stream=compute,
                            max_beams_in_step=per_step, first_block=warm,
-                           max_inflight=inflight, device_timing=True)
+                           max_inflight=inflight, device_timing=True,
+                           min_batch=min_batch, max_wait=0.05)
         res = loop.run(arr, time_limit=blocks_per_beam * T + 30.0)
         srv.check(compute)
         srv.close()
@@ -557,7 +566,9 @@ def serving_check(dev, blocks_per_beam=5, log=None):
                 "real_time": bool(p99 < T and duty < 1.0)}
 
     for n in counts:
-        runs["batched"][str(n)] = run_at(n, 0, 1)
+        # batched: a step waits for 4 beam-blocks (a launch of fewer leaves
+        # its last wave of work items mostly empty) or 50 ms
+        runs["batched"][str(n)] = run_at(n, 0, 1, min_batch=4)
         runs["plain_per_beam"][str(n)] = run_at(n, 1, 2)
         if log:
             log(f"serving {n}: {runs['batched'][str(n)]} | "
@@ -572,13 +583,14 @@ def serving_check(dev, blocks_per_beam=5, log=None):
         "beams_tested": counts,
         "real_time_beams": {"batched": best("batched"),
                             "plain_per_beam": best("plain_per_beam")},
-        "step_ms_per_beam_block": {"batched_32": ms_b, "plain_1": ms_p},
+        "step_ms_per_beam_block": {"batched_8": ms_b, "plain_1": ms_p},
         "beam_bytes": per_beam_bytes, "beams_fit_in_memory": n_mem,
         "workload": "streaming 4096-ch beams (300-500 MHz, 81.92 us), "
                     "16384-spectrum blocks, 1024 DMs 0-250, widths 1-256; "
                     "batched = interleaved mode with 8 staging slots, every "
-                    "waiting beam-block per step; plain = one beam per step, "
-                    "two steps in flight",
+                    "waiting beam-block per step once 4 wait or the oldest "
+                    "waited 50 ms; plain = one beam per step, two steps in "
+                    "flight",
         "runs": runs}
 
 
@@ -1479,7 +1491,7 @@ def run_serve(args):
         torch.cuda.synchronize(dev)
     tile = min(tune, key=tune.get)
 
-    def run_at(n, per_step, inflight):
+    def run_at(n, per_step, inflight, min_batch=1):
         try:
             srv = make_server(tile, n)
         except Exception:
@@ -1505,7 +1517,8 @@ def run_serve(args):
         loop = ServingLoop(srv, beams, lambda i, k: pool[(3 * i + warm + k) % 8],
                            cfg.threshold, stager=stager, compute_stream=compute,
                            max_beams_in_step=per_step, first_block=warm,
-                           max_inflight=inflight, device_timing=True)
+                           max_inflight=inflight, device_timing=True,
+                           min_batch=min_batch, max_wait=0.05)
         res = loop.run(arr, time_limit=args.steps * T + 60.0)
         srv.check(compute)
         srv.close()
@@ -1530,7 +1543,8 @@ def run_serve(args):
     # each path at its own best queue depth: batched steps already keep the
     # device busy, one-beam steps need a second step queued to hide the
     # host's turnaround between launches
-    n_batched, _ = realtime_limit(lambda n: run_at(n, 0, args.inflight), 64, 448, 16, T)
+    n_batched, _ = realtime_limit(lambda n: run_at(n, 0, args.inflight, 4),
+                                  64, 448, 16, T)
     n_plain, _ = realtime_limit(lambda n: run_at(n, 1, args.plain_inflight),
                                 64, 448, 16, T)
     clocks = clk.stop()

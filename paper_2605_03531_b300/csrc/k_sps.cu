@@ -38,7 +38,6 @@ constexpr int kWarps = kSpsThreads / 32;
 constexpr int kBins = 2048;      // bins per pass of the generic selection
 constexpr int kSelPer = kBins / kSpsThreads;
 constexpr int kFastBins = 4096;  // single-value bins of the one-pass path
-constexpr int kFastPer = kFastBins / kSpsThreads;
 constexpr int kMaxWidths = 11;  // 1 .. 1024
 constexpr int64_t kMaxWindowSamples = 49152;
 constexpr float kMadToSigma = 1.482602218505602f;
@@ -244,11 +243,15 @@ __device__ bool median_mad_fast(const int32_t *__restrict__ buf, uint32_t base,
   if (sh.bc[1] > 2800) return false;  // block-uniform
   const uint32_t A = est > kFastBins / 2 ? est - kFastBins / 2 : 0u;
   // ---- one pass: single-value bins [A, A + kFastBins) and the count below A
+  // d = (x - min) - A mod 2^32: below the bins (x - min < A <= 2^31) d has
+  // its top bit set, above them (x - min < 2^31) it does not, so one
+  // subtraction both bins a key and counts the keys below A
   uint32_t nb = 0;
+  const uint32_t AB = base + A;
   auto bin = [&](int32_t v) {
-    const uint32_t k = (uint32_t)v - base;
-    if (k < A) ++nb;
-    else if (k - A < (uint32_t)kFastBins) atomicAdd(&sh.hist[k - A], 1u);
+    const uint32_t d = (uint32_t)v - AB;
+    if (d < (uint32_t)kFastBins) atomicAdd(&sh.hist[d], 1u);
+    nb += d >> 31;
   };
   {
     // 16-byte shared loads (buf is 16-byte aligned), then the ragged tail
@@ -269,36 +272,46 @@ __device__ bool median_mad_fast(const int32_t *__restrict__ buf, uint32_t base,
   __syncthreads();
   uint32_t below = 0;
   for (int w = 0; w < kWarps; ++w) below += sh.wred[w][0];
-  // ---- inclusive prefix P[b] = below + #{keys in [A, A + b]}, in place
-  uint32_t c[kFastPer], tsum = 0;
+  // ---- inclusive prefix P[b] = below + #{keys in [A, A + b]}, in place.
+  // Warp w owns bins [kWarpBins w, kWarpBins (w + 1)) and lane l the four
+  // bins 4l .. 4l + 3 of each 128-bin segment of them, so every 16-byte
+  // shared access of a warp touches 512 consecutive bytes (no bank
+  // conflicts): the warps' totals first, then the prefix with every warp's
+  // offset known, and the median ranks found on the way.
+  constexpr int kWarpBins = kFastBins / kWarps;
+  constexpr int kSegs = kWarpBins / 128;
+  uint32_t *wbins = sh.hist + kWarpBins * warp + 4 * lane;
+  uint4 cnt[kSegs];
+  uint32_t wtot = 0;
 #pragma unroll
-  for (int q = 0; q < kFastPer; ++q) {
-    c[q] = sh.hist[kFastPer * tid + q];
-    tsum += c[q];
+  for (int sg = 0; sg < kSegs; ++sg) {
+    cnt[sg] = *reinterpret_cast<const uint4 *>(wbins + 128 * sg);
+    wtot += cnt[sg].x + cnt[sg].y + cnt[sg].z + cnt[sg].w;
   }
-  const uint32_t inc = warp_incl_scan(tsum, lane);
-  if (lane == 31) sh.wsum[warp] = inc;
+  wtot = __reduce_add_sync(0xffffffffu, wtot);
+  if (lane == 0) sh.wsum[warp] = wtot;
   __syncthreads();
-  uint32_t run = below + warp_excl_offset(sh.wsum, warp, lane) + inc - tsum;
-  const uint32_t prev0 = run;  // P[kFastPer*tid - 1] (or below)
-#pragma unroll
-  for (int q = 0; q < kFastPer; ++q) {
-    run += c[q];
-    c[q] = run;
-  }
-  __syncthreads();
-#pragma unroll
-  for (int q = 0; q < kFastPer; ++q) sh.hist[kFastPer * tid + q] = c[q];
+  uint32_t run = below + warp_excl_offset(sh.wsum, warp, lane);
+  const uint32_t R1 = (uint32_t)r1 + 1u, R2 = (uint32_t)r2 + 1u;
   // ---- median: the smallest b with P[b] >= r + 1
-  {
-    uint32_t pv = prev0;
+  auto hit = [&](uint32_t prev, uint32_t cur, int b) {
+    if (prev < R1 && R1 <= cur) sh.bc[2] = b;
+    if (prev < R2 && R2 <= cur) sh.bc[3] = b;
+  };
 #pragma unroll
-    for (int q = 0; q < kFastPer; ++q) {
-      const uint32_t cur = c[q];
-      if (pv < (uint32_t)r1 + 1u && (uint32_t)r1 + 1u <= cur) sh.bc[2] = kFastPer * tid + q;
-      if (pv < (uint32_t)r2 + 1u && (uint32_t)r2 + 1u <= cur) sh.bc[3] = kFastPer * tid + q;
-      pv = cur;
-    }
+  for (int sg = 0; sg < kSegs; ++sg) {
+    const uint4 c = cnt[sg];
+    const uint32_t t = c.x + c.y + c.z + c.w;
+    const uint32_t inc = warp_incl_scan(t, lane);
+    const uint32_t pre = run + inc - t;
+    const uint32_t p0 = pre + c.x, p1 = p0 + c.y, p2 = p1 + c.z, p3 = p2 + c.w;
+    const int b0 = kWarpBins * warp + 128 * sg + 4 * lane;
+    hit(pre, p0, b0);
+    hit(p0, p1, b0 + 1);
+    hit(p1, p2, b0 + 2);
+    hit(p2, p3, b0 + 3);
+    *reinterpret_cast<uint4 *>(wbins + 128 * sg) = make_uint4(p0, p1, p2, p3);
+    run += __shfl_sync(0xffffffffu, inc, 31);
   }
   __syncthreads();
   const int64_t b1 = sh.bc[2], b2 = sh.bc[3];
@@ -799,8 +812,18 @@ __device__ __forceinline__ void sps_window(
       const bool in_buf = DDSP_BC(b4 + 4 <= bufcap, kBcSpsScan, b4);
       int4 v = make_int4(0, 0, 0, 0);
       if (in_buf) v = *reinterpret_cast<const int4 *>(buf + b4);
-      const uint32_t y0 = yv(b4, v.x), y1 = yv(b4 + 1, v.y);
-      const uint32_t y2 = yv(b4 + 2, v.z), y3 = yv(b4 + 3, v.w);
+      uint32_t y0, y1, y2, y3;
+      if (b4 + 4 <= elen) {
+        y0 = (uint32_t)v.x - mf;
+        y1 = (uint32_t)v.y - mf;
+        y2 = (uint32_t)v.z - mf;
+        y3 = (uint32_t)v.w - mf;
+      } else {
+        y0 = yv(b4, v.x);
+        y1 = yv(b4 + 1, v.y);
+        y2 = yv(b4 + 2, v.z);
+        y3 = yv(b4 + 3, v.w);
+      }
       const uint32_t e1 = y0, e2 = y0 + y1, e3 = e2 + y2, tot = e3 + y3;
       const uint32_t inc = warp_incl_scan(tot, lane);
       const uint32_t pre = carry + inc - tot;

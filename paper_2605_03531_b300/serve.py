@@ -4,8 +4,9 @@ block must be searched before the next one is due).
 
 Continuous batching: blocks are ingested as they arrive (host -> device copy
 on a copy stream, then the server's push on the compute stream); whenever no
-step is running, one step takes the waiting block of every ready beam (or
-only the longest-waiting beam, for the per-beam sequential comparison).  The
+step is running (and, optionally, once a few blocks wait or the oldest has
+waited long enough), one step takes the waiting block of every ready beam
+(or only the longest-waiting beam, for the per-beam sequential comparison).  The
 latency of a block is the time from its arrival to the moment the host sees
 its step complete.
 
@@ -91,7 +92,8 @@ class ServingLoop:
     def __init__(self, server, beams, source, threshold, stager=None,
                  max_beams_in_step=0, max_inflight=1, compute_stream=None,
                  clock=time.monotonic, sleep=time.sleep, poll=2e-4,
-                 on_candidates=None, first_block=0, device_timing=False):
+                 on_candidates=None, first_block=0, device_timing=False,
+                 min_batch=1, max_wait=0.0):
         self.server = server
         self.beams = list(beams)
         self.source = source
@@ -112,6 +114,12 @@ class ServingLoop:
         # sustainable however short the run)
         self.device_timing = bool(device_timing)
         self._spans = []
+        # a step waits for min_batch pushed blocks (a device launch of a few
+        # beam-blocks leaves its last wave of work items mostly empty) unless
+        # the oldest pushed block has waited max_wait seconds, or no more
+        # blocks are due
+        self.min_batch = max(1, int(min_batch))
+        self.max_wait = float(max_wait)
 
     def _timed(self, fn):
         if not self.device_timing:
@@ -146,6 +154,13 @@ class ServingLoop:
         lat = np.full((nb, nk), np.nan)
         ncand = np.zeros((nb, nk), dtype=np.int64)
         inflight = deque()
+        # push times of the blocks not yet in a step (a step takes the
+        # oldest pushes first, so the front is the oldest)
+        push_time = deque()
+
+        def oldest_push():
+            return push_time[0] if push_time else float("inf")
+
         res = ServeResult(lat, ncand)
         nexta, ndone = 0, 0
         t0 = self.clock()
@@ -183,6 +198,7 @@ class ServingLoop:
                     heapq.heappop(waiting[i])
                     pushed[i] += 1
                     unstepped += 1
+                    push_time.append(self.clock() - t0)
                     busy = True
                 if not waiting[i]:
                     has_waiting.discard(i)
@@ -205,7 +221,10 @@ class ServingLoop:
             if self.max_inflight > 1:
                 self._fetch(finished, res)
                 finished = []
-            if len(inflight) < self.max_inflight and unstepped > 0:
+            full = (unstepped >= self.min_batch or nexta >= total or
+                    (unstepped > 0 and
+                     now - oldest_push() >= self.max_wait))
+            if len(inflight) < self.max_inflight and unstepped > 0 and full:
                 sid, sbeams = self._timed(lambda: self.server.step(
                     self.threshold, self.max_beams_in_step, stream=self.stream))
                 if sbeams:
@@ -215,6 +234,8 @@ class ServingLoop:
                         members.append((i, stepped[i]))
                         stepped[i] += 1
                         unstepped -= 1
+                        if push_time:
+                            push_time.popleft()
                     inflight.append((sid, members))
                     res.step_sizes.append(len(sbeams))
                     busy = True

@@ -80,14 +80,33 @@ class FakeServer:
 
 
 def _run(nbeams, nblocks, per_beam, max_beams_in_step=0, arrivals=None,
-         time_limit=None, overhead=2e-3, max_inflight=1):
+         time_limit=None, overhead=2e-3, max_inflight=1, min_batch=1,
+         max_wait=0.0):
     clock = SimClock()
     srv = FakeServer(clock, nbeams, overhead=overhead, per_beam=per_beam)
     arr = arrivals if arrivals is not None else synth.arrival_times(nbeams, nblocks, seed=5)
     loop = ServingLoop(srv, list(range(nbeams)), lambda i, k: (i, k), 7.0,
                        max_beams_in_step=max_beams_in_step, clock=clock,
-                       sleep=clock.sleep, max_inflight=max_inflight)
+                       sleep=clock.sleep, max_inflight=max_inflight,
+                       min_batch=min_batch, max_wait=max_wait)
     return loop.run(arr, time_limit=time_limit), srv
+
+
+def test_minimum_batch_waits_at_most_max_wait():
+    """Steps wait for 4 pushed blocks unless the oldest has waited 60 ms:
+    every block completes, steps are larger than without the minimum, and
+    no block waits for its step much beyond the limit."""
+    # 256 beams: about 11 blocks arrive in 60 ms
+    res, srv = _run(256, 3, per_beam=5e-4, min_batch=4, max_wait=0.06)
+    base, _ = _run(256, 3, per_beam=5e-4)
+    assert np.isfinite(res.latency).all()
+    assert sum(res.step_sizes) == 256 * 3
+    assert np.mean(res.step_sizes) > np.mean(base.step_sizes)
+    small = [n for n in res.step_sizes if n < 4]
+    assert len(small) < len(res.step_sizes) // 4
+    # a block's latency: its wait (<= 60 ms plus one step in flight) and
+    # its own step
+    assert res.latency.max() < 0.06 + 2 * (2e-3 + 64 * 5e-4) + 0.01
 
 
 def test_arrival_schedule():
