@@ -43,9 +43,10 @@ constexpr int64_t kMaxWindowSamples = 49152;
 constexpr float kMadToSigma = 1.482602218505602f;
 
 struct SpsShared {
-  uint32_t hist[kFastBins];
+  uint32_t hist[kFastBins + 4];   // + a sink for keys outside the bins
   uint32_t wred[kWarps][2];
   uint32_t hred[kWarps][2];
+  uint32_t wsx[kWarps];    // each warp's sum of x over its scan groups
   int64_t bc[4];      // broadcast slots
   float inv[kMaxWidths];
   int32_t thr_by[kMaxWidths];
@@ -250,7 +251,8 @@ __device__ bool median_mad_fast(const int32_t *__restrict__ buf, uint32_t base,
   const uint32_t AB = base + A;
   auto bin = [&](int32_t v) {
     const uint32_t d = (uint32_t)v - AB;
-    if (d < (uint32_t)kFastBins) atomicAdd(&sh.hist[d], 1u);
+    // keys outside the bins go to the sink bin kFastBins (no branch)
+    atomicAdd(&sh.hist[min(d, (uint32_t)kFastBins)], 1u);
     nb += d >> 31;
   };
   {
@@ -379,6 +381,8 @@ __device__ bool median_mad_fast(const int32_t *__restrict__ buf, uint32_t base,
 // so the screen costs a few operations per sample instead of one load, add
 // and compare per sample and width.
 constexpr int kChunk = 8;
+// prefix positions per scan group: 32 lanes x one chunk each
+constexpr int kGroup = 32 * kChunk;
 // windows up to this many buffered samples keep the chunk statistics in
 // shared memory (longer ones take every start through the exact screen)
 constexpr int64_t kStatsMaxCap = 32768;
@@ -389,9 +393,9 @@ constexpr int64_t kSeg = 8192;
 
 __host__ __device__ __forceinline__ int64_t sps_buf_cap(int64_t maxlen,
                                                         int wmax) {
-  // x[0 .. elen) then, in place, Q[0 .. elen]; rounded to whole 128-value
-  // scan groups
-  return ((maxlen + wmax + 1 + 127) / 128) * 128;
+  // x[0 .. elen) then, in place, Q[0 .. elen]; rounded to whole
+  // 256-position scan groups
+  return ((maxlen + wmax + 1 + 255) / 256) * 256;
 }
 __host__ __device__ __forceinline__ int64_t sps_chunk_cap(int64_t cap) {
   return cap / kChunk + 2;
@@ -630,9 +634,11 @@ __device__ __forceinline__ void sps_window(
   const int len = (int)(hi - lo), elen = (int)(ext - lo);
   const int32_t *x = series + (int64_t)k * n + lo;
 
-  // ---- 1. load x[0 .. elen) to buf (16-byte loads when the window starts
-  // on a 16-byte boundary, as it does when n and L are multiples of 4),
-  // min and max over the window [0, len)
+  // ---- 1. load x[0 .. elen) to buf, min and max over the window [0, len)
+  // and over the look-ahead [len, elen), and each warp's sum of x over its
+  // run of the scan's 128-position groups (so step 3 needs one pass).  A
+  // lane takes 4 consecutive samples of a group: 16-byte loads when the
+  // window starts on a 16-byte boundary (n and L multiples of 4).
   int32_t mn32 = INT32_MAX, mx32 = INT32_MIN;   // the window [0, len)
   int32_t hmn = INT32_MAX, hmx = INT32_MIN;     // look-ahead [len, elen)
   auto take = [&](int i, int32_t v) {
@@ -644,46 +650,44 @@ __device__ __forceinline__ void sps_window(
       hmx = max(hmx, v);
     }
   };
-  if ((reinterpret_cast<uintptr_t>(x) & 15) == 0) {
-    const int n4 = elen >> 2;
-    const int4 *x4 = reinterpret_cast<const int4 *>(x);
-    int4 *b4 = reinterpret_cast<int4 *>(buf);
-#pragma unroll 2
-    for (int q = tid; q < n4; q += kSpsThreads) {
-      if (!DDSP_BC(lo + 4 * q + 4 <= n, kBcSpsLoad, lo + 4 * q) ||
-          !DDSP_BC(4 * q + 4 <= bufcap, kBcSpsBuf, 4 * q))
-        continue;
-      const int4 v = __ldg(x4 + q);
-      b4[q] = v;
-      const int i = 4 * q;
-      if (i + 4 <= len) {
+  const int ntot = elen + 1;                    // prefix positions 0 .. elen
+  const int ngroups = (ntot + kGroup - 1) / kGroup;
+  const int gpw = (ngroups + kWarps - 1) / kWarps;
+  const int g0 = warp * gpw, g1 = min(ngroups, g0 + gpw);
+  const bool vec = (reinterpret_cast<uintptr_t>(x) & 15) == 0;
+  uint32_t sx = 0;                              // this lane's sum of x
+  for (int h = 2 * g0; h < 2 * g1; ++h) {       // 128-position halves
+    const int b4 = h * 128 + 4 * lane;
+    if (!DDSP_BC(b4 + 4 <= bufcap, kBcSpsBuf, b4)) continue;
+    if (vec && b4 + 4 <= elen &&
+        DDSP_BC(lo + b4 + 4 <= n, kBcSpsLoad, lo + b4)) {
+      const int4 v = __ldg(reinterpret_cast<const int4 *>(x + b4));
+      *reinterpret_cast<int4 *>(buf + b4) = v;
+      sx += (uint32_t)v.x + (uint32_t)v.y + (uint32_t)v.z + (uint32_t)v.w;
+      if (b4 + 4 <= len) {
         mn32 = min(mn32, min(min(v.x, v.y), min(v.z, v.w)));
         mx32 = max(mx32, max(max(v.x, v.y), max(v.z, v.w)));
       } else {
-        take(i, v.x);
-        take(i + 1, v.y);
-        take(i + 2, v.z);
-        take(i + 3, v.w);
+        take(b4, v.x);
+        take(b4 + 1, v.y);
+        take(b4 + 2, v.z);
+        take(b4 + 3, v.w);
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int i = b4 + e;
+        if (i < elen && DDSP_BC(lo + i < n, kBcSpsLoad, lo + i)) {
+          const int32_t v = __ldg(x + i);
+          buf[i] = v;
+          sx += (uint32_t)v;
+          take(i, v);
+        }
       }
     }
-    for (int i = 4 * n4 + tid; i < elen; i += kSpsThreads) {
-      if (!DDSP_BC(lo + i < n, kBcSpsLoad, lo + i) ||
-          !DDSP_BC(i < bufcap, kBcSpsBuf, i))
-        continue;
-      const int32_t v = __ldg(x + i);
-      buf[i] = v;
-      take(i, v);
-    }
-  } else {
-    for (int i = tid; i < elen; i += kSpsThreads) {
-      if (!DDSP_BC(lo + i < n, kBcSpsLoad, lo + i) ||
-          !DDSP_BC(i < bufcap, kBcSpsBuf, i))
-        continue;
-      const int32_t v = __ldg(x + i);
-      buf[i] = v;
-      take(i, v);
-    }
   }
+  sx = __reduce_add_sync(0xffffffffu, sx);
+  if (lane == 0) sh.wsx[warp] = sx;
   mn32 = __reduce_min_sync(0xffffffffu, mn32);
   mx32 = __reduce_max_sync(0xffffffffu, mx32);
   hmn = __reduce_min_sync(0xffffffffu, hmn);
@@ -767,10 +771,11 @@ __device__ __forceinline__ void sps_window(
 
   // ---- 3. y = x - floor(median) and the exclusive prefix sum Q, in place:
   // buf[p] = Q[p] = sum_{t < p} y[t] for p = 0 .. elen (uint32, modular, so
-  // every boxcar sum Q[t + w] - Q[t] is exact).  Groups of 128 positions, a
-  // lane taking 4 consecutive ones with a 16-byte shared load, each warp a
-  // contiguous run of groups: first the runs' totals, then the scan with
-  // every warp's offset known, recording the chunk statistics on the way.
+  // every boxcar sum Q[t + w] - Q[t] is exact).  Groups of 256 positions, a
+  // lane taking 8 consecutive ones (one chunk) with two 16-byte shared
+  // loads, each warp a contiguous run of groups: the runs' totals follow
+  // from the sums of x the load took, so one pass scans with every warp's
+  // offset known, recording each lane's chunk statistics on the way.
   // Statistics are kept only when every prefix value fits in 30 bits in
   // magnitude (|y| <= the larger distance of floor(median) to the extremes
   // of everything loaded, so that times (elen + 1) below 2^30), where
@@ -780,70 +785,67 @@ __device__ __forceinline__ void sps_window(
       !DENSE && have_stats && range_ok && MAD4 > 0 && elen > 0 &&
       ybound * (int64_t)(elen + 1) < ((int64_t)1 << 30);
   {
-    const int ntot = elen + 1;
-    const int ngroups = (ntot + 127) / 128;
-    const int gpw = (ngroups + kWarps - 1) / kWarps;
-    const int g0 = warp * gpw, g1 = min(ngroups, g0 + gpw);
     const uint32_t mf = (uint32_t)mfloor;
     auto yv = [&](int p, int32_t v) {
       return p < elen ? (uint32_t)v - mf : 0u;
     };
-    // totals of every warp's run
-    uint32_t tsum = 0;
-    for (int g = g0; g < g1; ++g) {
-      const int b4 = g * 128 + 4 * lane;
-      if (!DDSP_BC(b4 + 4 <= bufcap, kBcSpsScan, b4)) continue;
-      const int4 v = *reinterpret_cast<const int4 *>(buf + b4);
-      if (b4 + 4 <= elen)
-        tsum += (uint32_t)v.x + (uint32_t)v.y + (uint32_t)v.z + (uint32_t)v.w -
-                4u * mf;
-      else
-        tsum += yv(b4, v.x) + yv(b4 + 1, v.y) + yv(b4 + 2, v.z) +
-                yv(b4 + 3, v.w);
+    // warp runs' totals of y from the sums of x the load took: a run holds
+    // the positions [128 g0, 128 g1) and those below elen carry a sample
+    if (warp == 0 && lane < kWarps) {
+      const int r0 = lane * gpw * kGroup;
+      const int r1 = min(ngroups, (lane + 1) * gpw) * kGroup;
+      const int cnt = max(0, min(r1, elen) - r0);
+      sh.wsum[lane] = sh.wsx[lane] - (uint32_t)cnt * mf;
     }
-    tsum = __reduce_add_sync(0xffffffffu, tsum);
-    if (lane == 0) sh.wsum[warp] = tsum;
     __syncthreads();
     uint32_t carry = warp_excl_offset(sh.wsum, warp, lane);
     for (int g = g0; g < g1; ++g) {
-      const int b4 = g * 128 + 4 * lane;
-      // (a failed check leaves this lane's values out; the warp's scan and
-      // shuffles below still run with all lanes)
-      const bool in_buf = DDSP_BC(b4 + 4 <= bufcap, kBcSpsScan, b4);
-      int4 v = make_int4(0, 0, 0, 0);
-      if (in_buf) v = *reinterpret_cast<const int4 *>(buf + b4);
-      uint32_t y0, y1, y2, y3;
-      if (b4 + 4 <= elen) {
-        y0 = (uint32_t)v.x - mf;
-        y1 = (uint32_t)v.y - mf;
-        y2 = (uint32_t)v.z - mf;
-        y3 = (uint32_t)v.w - mf;
-      } else {
-        y0 = yv(b4, v.x);
-        y1 = yv(b4 + 1, v.y);
-        y2 = yv(b4 + 2, v.z);
-        y3 = yv(b4 + 3, v.w);
+      // this lane's 8 consecutive positions = one chunk of the statistics
+      const int b8 = g * kGroup + kChunk * lane;
+      // (a failed check leaves this lane's values out; the warp's scan
+      // below still runs with all lanes)
+      const bool in_buf = DDSP_BC(b8 + 8 <= bufcap, kBcSpsScan, b8);
+      int4 va = make_int4(0, 0, 0, 0), vb = va;
+      if (in_buf) {
+        va = *reinterpret_cast<const int4 *>(buf + b8);
+        vb = *reinterpret_cast<const int4 *>(buf + b8 + 4);
       }
-      const uint32_t e1 = y0, e2 = y0 + y1, e3 = e2 + y2, tot = e3 + y3;
+      const int32_t xv[8] = {va.x, va.y, va.z, va.w, vb.x, vb.y, vb.z, vb.w};
+      uint32_t y[8];
+      if (b8 + 8 <= elen) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) y[e] = (uint32_t)xv[e] - mf;
+      } else {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) y[e] = yv(b8 + e, xv[e]);
+      }
+      uint32_t ex[8];        // exclusive prefix inside the chunk
+      ex[0] = 0u;
+#pragma unroll
+      for (int e = 1; e < 8; ++e) ex[e] = ex[e - 1] + y[e - 1];
+      const uint32_t tot = ex[7] + y[7];
       const uint32_t inc = warp_incl_scan(tot, lane);
       const uint32_t pre = carry + inc - tot;
-      const uint32_t q0 = pre, q1 = pre + e1, q2 = pre + e2, q3 = pre + e3;
-      if (in_buf)
-        *reinterpret_cast<uint4 *>(buf + b4) = make_uint4(q0, q1, q2, q3);
+      if (in_buf) {
+        *reinterpret_cast<uint4 *>(buf + b8) =
+            make_uint4(pre + ex[0], pre + ex[1], pre + ex[2], pre + ex[3]);
+        *reinterpret_cast<uint4 *>(buf + b8 + 4) =
+            make_uint4(pre + ex[4], pre + ex[5], pre + ex[6], pre + ex[7]);
+      }
       carry += __shfl_sync(0xffffffffu, inc, 31);
       if (bounds) {
-        // chunk of 8 = this lane's 4 positions and its partner's
-        int32_t cn = min(min((int32_t)q0, (int32_t)q1), min((int32_t)q2, (int32_t)q3));
-        int32_t cx = max(max((int32_t)q0, (int32_t)q1), max((int32_t)q2, (int32_t)q3));
-        int32_t ym = max(max((int32_t)y0, (int32_t)y1), max((int32_t)y2, (int32_t)y3));
-        cn = min(cn, __shfl_xor_sync(0xffffffffu, cn, 1));
-        cx = max(cx, __shfl_xor_sync(0xffffffffu, cx, 1));
-        ym = max(ym, __shfl_xor_sync(0xffffffffu, ym, 1));
-        const int c = b4 / kChunk;
-        if ((lane & 1) == 0 &&
-            DDSP_BC(c < sps_chunk_cap(bufcap), kBcSpsStats, c)) {
-          cmin[c] = cn;
-          cmax[c] = cx;
+        // Q = pre + ex, exact as int32 here (|Q| < 2^30)
+        int32_t en = 0, exx = 0, ym = (int32_t)y[0];
+#pragma unroll
+        for (int e = 1; e < 8; ++e) {
+          en = min(en, (int32_t)ex[e]);
+          exx = max(exx, (int32_t)ex[e]);
+          ym = max(ym, (int32_t)y[e]);
+        }
+        const int c = b8 / kChunk;
+        if (DDSP_BC(c < sps_chunk_cap(bufcap), kBcSpsStats, c)) {
+          cmin[c] = (int32_t)pre + en;
+          cmax[c] = (int32_t)pre + exx;
           ymax[c] = ym;
         }
       }
@@ -1035,7 +1037,7 @@ size_t sps_smem_bytes(int64_t maxlen, int wmax) {
 // limit once (smem_opt_in), shared by plan, batch, server and
 // allocation-free launches and never lowered.
 constexpr size_t kSpsMaxSmem =
-    kBufOff + 4 * (size_t)(((kMaxWindowSamples + 1 + 127) / 128) * 128);
+    kBufOff + 4 * (size_t)(((kMaxWindowSamples + 1 + 255) / 256) * 256);
 
 cudaError_t launch_sps_batch(const SpsBeam *d_beams, int nbeams,
                              int64_t total_blocks, float threshold,
