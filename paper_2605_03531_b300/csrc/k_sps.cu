@@ -43,7 +43,7 @@ constexpr int64_t kMaxWindowSamples = 49152;
 constexpr float kMadToSigma = 1.482602218505602f;
 
 struct SpsShared {
-  uint32_t hist[kFastBins + 4];   // + a sink for keys outside the bins
+  uint32_t hist[kFastBins + 32];  // + a sink per lane for keys outside the bins
   uint32_t wred[kWarps][2];
   uint32_t hred[kWarps][2];
   uint32_t wsx[kWarps];    // each warp's sum of x over its scan groups
@@ -78,6 +78,13 @@ __device__ __forceinline__ float twice_minus(int32_t by, int32_t c) {
   const float hf = __int_as_float(0x4B400000 + hi) - magic;
   const float lf = __int_as_float(0x4B400000 + lo) - magic;
   return __fmaf_rn(hf, 131072.0f, lf);
+}
+
+// float(2*by - c) as twice_minus, with one integer multiply-add and one
+// conversion when the window is known to keep |2*by - c| below 2^31 (then
+// the conversion rounds the same exact integer once, to the same value).
+__device__ __forceinline__ float numer(int32_t by, int32_t c, bool small) {
+  return small ? __int2float_rn(2 * by - c) : twice_minus(by, c);
 }
 
 // Sum of wsum[0 .. warp-1] (kWarps <= 32 per-warp totals), by one warp scan.
@@ -251,8 +258,9 @@ __device__ bool median_mad_fast(const int32_t *__restrict__ buf, uint32_t base,
   const uint32_t AB = base + A;
   auto bin = [&](int32_t v) {
     const uint32_t d = (uint32_t)v - AB;
-    // keys outside the bins go to the sink bin kFastBins (no branch)
-    atomicAdd(&sh.hist[min(d, (uint32_t)kFastBins)], 1u);
+    // keys outside the bins go to the lane's own sink bin (no branch, and
+    // no two lanes of a warp collide there)
+    atomicAdd(&sh.hist[d < (uint32_t)kFastBins ? d : kFastBins + lane], 1u);
     nb += d >> 31;
   };
   {
@@ -412,37 +420,35 @@ template <bool DENSE, int NW>
 __device__ __forceinline__ int exact_start(
     const uint32_t *__restrict__ Q, int qcap, int i, int nv, int nw,
     const int32_t (&wv)[kMaxWidths], const int32_t (&tbv)[kMaxWidths],
-    const float (&iv)[kMaxWidths], int odd, int32_t mfloor, float &bs,
-    int32_t &bsum) {
+    const float (&iv)[kMaxWidths], int odd, int32_t mfloor, bool small,
+    float &bs, int32_t &bsum) {
   const uint32_t qi = Q[i];
   int bw = -1;
   bs = 0.0f;
   bsum = 0;
   if constexpr (NW > 0) {
+    // Every width that ends inside the series gets its FP32 S/N and the
+    // first maximum wins; no integer screen first.  The same best comes out
+    // as from the widths that pass the screen: a width that fails it has
+    // S/N below the threshold (the screen keeps a margin), so it can be the
+    // best only when no width reaches the threshold and there is no
+    // candidate either way.  Here most starts (those of chunks whose bound
+    // could pass) have several widths near the threshold, and the S/N of
+    // all of them costs fewer operations than screening first.
     constexpr int kWidest = 1 << (NW - 1);
-    int32_t by[NW];
-    unsigned pm = 0u;   // widths that end inside the series and pass
     const bool inner = i + kWidest <= nv &&
                        DDSP_BC(i + kWidest < qcap, kBcSpsQ, i + kWidest);
 #pragma unroll
     for (int wi = 0; wi < NW; ++wi) {
       const bool v = inner || (i + (1 << wi) <= nv &&
                                DDSP_BC(i + (1 << wi) < qcap, kBcSpsQ, i));
-      by[wi] = v ? (int32_t)(Q[i + (1 << wi)] - qi) : 0;
-      pm |= (unsigned)(v && (DENSE || by[wi] >= tbv[wi])) << wi;
-    }
-    // a width whose FP32 S/N reaches the threshold always passes the integer
-    // screen (it keeps a margin), so a width that failed can never be the
-    // best one of an emitted candidate
-    if (pm == 0u) return -1;
-#pragma unroll
-    for (int wi = 0; wi < NW; ++wi) {
-      if ((pm >> wi) & 1u) {
-        const float sn = twice_minus(by[wi], (1 << wi) * odd) * iv[wi];
+      if (v) {
+        const int32_t by = (int32_t)(Q[i + (1 << wi)] - qi);
+        const float sn = numer(by, (1 << wi) * odd, small) * iv[wi];
         if (bw < 0 || sn > bs) {
           bw = wi;
           bs = sn;
-          bsum = by[wi] + (1 << wi) * mfloor;
+          bsum = by + (1 << wi) * mfloor;
         }
       }
     }
@@ -453,7 +459,7 @@ __device__ __forceinline__ int exact_start(
           DDSP_BC(i + wv[wi] < qcap, kBcSpsQ, i + wv[wi])) {
         const int32_t by = (int32_t)(Q[i + wv[wi]] - qi);
         if (DENSE || by >= tbv[wi]) {
-          const float sn = twice_minus(by, wv[wi] * odd) * iv[wi];
+          const float sn = numer(by, wv[wi] * odd, small) * iv[wi];
           if (bw < 0 || sn > bs) {
             bw = wi;
             bs = sn;
@@ -501,6 +507,7 @@ struct SweepArgs {
   int64_t lo, n, nrep;
   int k, wmax;
   bool bounds;
+  bool small;    // every |2 B_y - w*odd| < 2^31 in this window
   const int32_t *cmin, *cmax, *ymax;
   ddsp_cand *cands;
   uint32_t *count;
@@ -523,7 +530,8 @@ __device__ __forceinline__ void sweep(const SweepArgs &g,
       float bs;
       int32_t bsum;
       const int bw = exact_start<true, NW>(g.Q, g.qcap, i, g.nv, g.nw, wv, tbv,
-                                           iv, g.odd, g.mfloor, bs, bsum);
+                                           iv, g.odd, g.mfloor, g.small, bs,
+                                           bsum);
       const int64_t o = (int64_t)g.k * g.n + g.lo + i;
       if (DDSP_BC(g.lo + i < g.n, kBcSpsDense, g.lo + i)) {
         g.best_w[o] = bw;
@@ -586,7 +594,7 @@ __device__ __forceinline__ void sweep(const SweepArgs &g,
       int bw = -1;
       if (mine)
         bw = exact_start<false, NW>(g.Q, g.qcap, i, g.nv, g.nw, wv, tbv, iv,
-                                    g.odd, g.mfloor, bs, bsum);
+                                    g.odd, g.mfloor, g.small, bs, bsum);
       const bool cand = bw >= 0 && bs >= g.thr && g.lo + i < g.nrep;
       emit(0xffffffffu, cand, g.k, g.lo + i, bw, bs, g.cands, g.count, g.cap);
     }
@@ -656,7 +664,29 @@ __device__ __forceinline__ void sps_window(
   const int g0 = warp * gpw, g1 = min(ngroups, g0 + gpw);
   const bool vec = (reinterpret_cast<uintptr_t>(x) & 15) == 0;
   uint32_t sx = 0;                              // this lane's sum of x
-  for (int h = 2 * g0; h < 2 * g1; ++h) {       // 128-position halves
+  int h = 2 * g0;                               // 128-position halves
+  if (vec) {
+    // halves wholly inside the window proper, four loads in flight a lane
+    const int hin = min(2 * g1, len / 128);
+    for (; h + 4 <= hin; h += 4) {
+      if (!DDSP_BC((h + 4) * 128 <= bufcap && lo + (h + 4) * 128 <= n,
+                   kBcSpsLoad, lo + h * 128))
+        break;
+      int4 v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        v[u] = __ldg(reinterpret_cast<const int4 *>(x + (h + u) * 128) + lane);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        reinterpret_cast<int4 *>(buf + (h + u) * 128)[lane] = v[u];
+        sx += (uint32_t)v[u].x + (uint32_t)v[u].y + (uint32_t)v[u].z +
+              (uint32_t)v[u].w;
+        mn32 = min(mn32, min(min(v[u].x, v[u].y), min(v[u].z, v[u].w)));
+        mx32 = max(mx32, max(max(v[u].x, v[u].y), max(v[u].z, v[u].w)));
+      }
+    }
+  }
+  for (; h < 2 * g1; ++h) {
     const int b4 = h * 128 + 4 * lane;
     if (!DDSP_BC(b4 + 4 <= bufcap, kBcSpsBuf, b4)) continue;
     if (vec && b4 + 4 <= elen &&
@@ -872,9 +902,11 @@ __device__ __forceinline__ void sps_window(
 #pragma unroll
   for (int wi = 0; wi < kMaxWidths; ++wi)
     pow2 = pow2 && (wi >= nw || wv[wi] == (1 << wi));
+  // |B_y| <= ybound * w, so |2 B_y - w odd| < 2^31 when ybound * wmax < 2^29
+  const bool small = range_ok && ybound * (int64_t)wmax < ((int64_t)1 << 29);
   const SweepArgs g{Q,    (int)bufcap, len,   nv,    nw,     odd,  mfloor,
                     thr,  lo,          n,     nrep,  k,      wmax, bounds,
-                    cmin, cmax,        ymax,  cands, count,  cap,  best_w,
+                    small, cmin, cmax, ymax,  cands, count,  cap,  best_w,
                     best_snr, best_sum};
   switch (pow2 ? nw : 0) {
 #define DDSP_SWEEP(N)                        \
