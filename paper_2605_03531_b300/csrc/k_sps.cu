@@ -12,17 +12,20 @@
 //      wanted order statistic is one key wide (or the two middle order
 //      statistics fall in different bins: then max of the lower bin and min
 //      of the upper bin); m2 = 2*median, mad4 = 4*MAD are exact integers;
-//   3. y = x - floor(median) and an exclusive prefix sum Q of y in uint32
-//      (modular, so every boxcar sum B_w(t) - w*floor(median) = Q[t+w]-Q[t]
-//      is exact), computed with warp-shuffle scans, recording per chunk of
-//      8 start times the extremes of Q and the largest y;
+//   3. an exclusive prefix sum Q in uint32 (modular, so every difference
+//      Q[t+w] - Q[t] is exact) of y = 2x - m2 when the window keeps every
+//      S/N numerator 2 B_y - w*odd below 2^30 in magnitude (a difference is
+//      then the numerator itself), else of y = x - floor(median) (a
+//      difference is B_y = B_w(t) - w*floor(median)), computed with
+//      warp-shuffle scans, recording per chunk of 8 start times the
+//      extremes of Q and the largest y;
 //   4. per chunk a bound of every width's boxcar sums from those extremes
 //      against the integer screen thresholds (derived from the S/N
 //      threshold with a small safety margin); only chunks that could pass
-//      go start by start through the exact integer screen, then for the
-//      survivors the FP32 S/N of the widths that passed, the best one
-//      (first maximum), and candidate emission with one atomicAdd per warp
-//      (ballot + popc).
+//      go start by start through the exact path: the FP32 S/N of every
+//      width, the best one (first maximum), and candidate emission through
+//      a per-warp stage in shared memory, one atomicAdd on the global count
+//      per stage-full (ballot + popc place the records).
 // Memory traffic is 4 bytes per series sample read once (plus the look-ahead)
 // and 16 bytes per candidate: the kernel is bounded by HBM bandwidth.
 #include <math.h>
@@ -47,7 +50,8 @@ struct SpsShared {
   uint32_t wred[kWarps][2];
   uint32_t hred[kWarps][2];
   uint32_t wsx[kWarps];    // each warp's sum of x over its scan groups
-  int64_t bc[4];      // broadcast slots
+  uint32_t nbw[kWarps];    // each warp's count of keys below the bins
+  int64_t bc[6];      // broadcast slots
   float inv[kMaxWidths];
   int32_t thr_by[kMaxWidths];
   int32_t wid[kMaxWidths];
@@ -57,13 +61,27 @@ struct SpsShared {
 // The window buffer follows the struct, 16-byte aligned (vector accesses).
 constexpr size_t kBufOff = (sizeof(SpsShared) + 15) & ~(size_t)15;
 
+// Inclusive warp scan (Hillis-Steele): the shuffle's own predicate says
+// whether lane - o exists, so each step is one shuffle and one predicated
+// add.
 __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane) {
+  (void)lane;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    uint32_t u = __shfl_up_sync(0xffffffffu, v, o);
-    if (lane >= o) v += u;
+    asm("{\n\t.reg .u32 t;\n\t.reg .pred p;\n\t"
+        "shfl.sync.up.b32 t|p, %0, %1, 0, 0xffffffff;\n\t"
+        "@p add.u32 %0, %0, t;\n\t}"
+        : "+r"(v)
+        : "r"(o));
   }
   return v;
+}
+
+// float(d) for |d| < 2^22, exact: the integer added to the bit pattern of
+// 1.5 * 2^23 (whose unit in the last place is 1) and the constant taken
+// away again, two full-rate operations instead of a conversion.
+__device__ __forceinline__ float small_int_to_float(int32_t d) {
+  return __int_as_float(0x4B400000 + d) - 12582912.0f;
 }
 
 // float(2*by - c), rounded to nearest, for any int32 by and 0 <= c < 2^16,
@@ -74,17 +92,9 @@ __device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v, int lane) {
 __device__ __forceinline__ float twice_minus(int32_t by, int32_t c) {
   const int32_t hi = by >> 16;
   const int32_t lo = 2 * (by & 0xffff) - c;
-  const float magic = 12582912.0f;  // 1.5 * 2^23, bit pattern 0x4B400000
-  const float hf = __int_as_float(0x4B400000 + hi) - magic;
-  const float lf = __int_as_float(0x4B400000 + lo) - magic;
+  const float hf = small_int_to_float(hi);
+  const float lf = small_int_to_float(lo);
   return __fmaf_rn(hf, 131072.0f, lf);
-}
-
-// float(2*by - c) as twice_minus, with one integer multiply-add and one
-// conversion when the window is known to keep |2*by - c| below 2^31 (then
-// the conversion rounds the same exact integer once, to the same value).
-__device__ __forceinline__ float numer(int32_t by, int32_t c, bool small) {
-  return small ? __int2float_rn(2 * by - c) : twice_minus(by, c);
 }
 
 // Sum of wsum[0 .. warp-1] (kWarps <= 32 per-warp totals), by one warp scan.
@@ -204,84 +214,60 @@ __device__ void select2(KeyFn key, int n, int r1, int r2, uint32_t kmax,
   }
 }
 
-// Exact median and MAD in one histogram pass, for windows whose middle half
-// is narrow: keys k = x - min, ranks r1 <= r2 = r1 or r1 + 1.
-//  * estimate: 32 evenly spaced keys sorted in one warp give the median and
-//    the quartiles; wide windows (estimated IQR > 2800) go to select2;
-//  * one pass counts every key in single-value bins [A, A + 4096) around
-//    the estimate and the keys below A; their prefix sums P give the two
-//    middle order statistics k1, k2 directly;
+// The estimate median_mad_fast starts from: 32 evenly spaced samples of the
+// window [0, n), read straight from global memory by one warp (while the
+// other warps load the window) and sorted in that warp; bc[0] = their median
+// (a sample value), bc[1] = their interquartile range, bc[2 .. 5] = -1.
+__device__ __forceinline__ void median_estimate(const int32_t *__restrict__ x,
+                                                int64_t lo, int64_t n_series,
+                                                int n, SpsShared &sh) {
+  const int lane = threadIdx.x & 31;
+  const int i = (lane * n) >> 5;   // n < 2^26
+  int32_t v = 0;
+  if (DDSP_BC(lo + i < n_series, kBcSpsLoad, lo + i)) v = __ldg(x + i);
+#pragma unroll
+  for (int kk = 2; kk <= 32; kk <<= 1) {
+#pragma unroll
+    for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+      const int32_t o = __shfl_xor_sync(0xffffffffu, v, jj);
+      const bool up = (lane & kk) == 0, low = (lane & jj) == 0;
+      v = (low == up) ? min(v, o) : max(v, o);
+    }
+  }
+  const int32_t med = __shfl_sync(0xffffffffu, v, 16);
+  const int32_t q1 = __shfl_sync(0xffffffffu, v, 8);
+  const int32_t q3 = __shfl_sync(0xffffffffu, v, 24);
+  if (lane == 0) {
+    sh.bc[0] = med;
+    sh.bc[1] = (int64_t)q3 - (int64_t)q1;
+#pragma unroll
+    for (int q = 2; q < 6; ++q) sh.bc[q] = -1;
+  }
+}
+
+// Exact median and MAD from one histogram pass, for windows whose middle
+// half is narrow: keys k = x - min, ranks r1 <= r2 = r1 or r1 + 1.
+//  * the load (step 1) counted every window sample in single-value bins of
+//    keys [A, A + 4096) around an estimate (median_estimate: 32 evenly spaced
+//    samples give the median and the quartiles; wide windows, estimated
+//    IQR > 2800, go to select2) and, per warp, the samples below A (nbw);
+//    A may be negative (bins below the window's minimum stay empty);
+//  * their prefix sums P give the two middle order statistics k1, k2
+//    directly;
 //  * with m = k1 + k2 (= M2 - 2*min), #{|2k - m| <= v} is the number of
 //    keys in [ceil((m - v)/2), floor((m + v)/2)], a difference of two prefix
-//    sums while that range lies inside the bins; the MAD order statistics
-//    are the smallest v reaching ranks r1 + 1 and r2 + 1.
+//    sums while that range lies inside the bins (or starts below them when
+//    no key is below the bins); the MAD order statistics are the smallest v
+//    reaching ranks r1 + 1 and r2 + 1.
 // Returns false (the caller then uses select2) when a rank falls outside
 // the bins.  The result, when true, equals select2's.
-__device__ bool median_mad_fast(const int32_t *__restrict__ buf, uint32_t base,
-                                int n, int r1, int r2, SpsShared &sh,
+__device__ bool median_mad_fast(int64_t A, int r1, int r2, SpsShared &sh,
                                 uint32_t &k1, uint32_t &k2, uint32_t &u1,
                                 uint32_t &u2) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  auto key = [&](int i) { return (uint32_t)buf[i] - base; };
-  // ---- estimate
-  if (warp == 0) {
-    uint32_t v = key((int)((int64_t)lane * n / 32));
-#pragma unroll
-    for (int kk = 2; kk <= 32; kk <<= 1) {
-#pragma unroll
-      for (int jj = kk >> 1; jj > 0; jj >>= 1) {
-        const uint32_t o = __shfl_xor_sync(0xffffffffu, v, jj);
-        const bool up = (lane & kk) == 0, low = (lane & jj) == 0;
-        v = (low == up) ? min(v, o) : max(v, o);
-      }
-    }
-    const uint32_t med = __shfl_sync(0xffffffffu, v, 16);
-    const uint32_t q1 = __shfl_sync(0xffffffffu, v, 8);
-    const uint32_t q3 = __shfl_sync(0xffffffffu, v, 24);
-    if (lane == 0) {
-      sh.bc[0] = med;
-      sh.bc[1] = (int64_t)q3 - (int64_t)q1;
-      sh.bc[2] = -1;
-      sh.bc[3] = -1;
-    }
-  }
-  for (int b = tid; b < kFastBins; b += kSpsThreads) sh.hist[b] = 0;
-  __syncthreads();
-  const uint32_t est = (uint32_t)sh.bc[0];
-  if (sh.bc[1] > 2800) return false;  // block-uniform
-  const uint32_t A = est > kFastBins / 2 ? est - kFastBins / 2 : 0u;
-  // ---- one pass: single-value bins [A, A + kFastBins) and the count below A
-  // d = (x - min) - A mod 2^32: below the bins (x - min < A <= 2^31) d has
-  // its top bit set, above them (x - min < 2^31) it does not, so one
-  // subtraction both bins a key and counts the keys below A
-  uint32_t nb = 0;
-  const uint32_t AB = base + A;
-  auto bin = [&](int32_t v) {
-    const uint32_t d = (uint32_t)v - AB;
-    // keys outside the bins go to the lane's own sink bin (no branch, and
-    // no two lanes of a warp collide there)
-    atomicAdd(&sh.hist[d < (uint32_t)kFastBins ? d : kFastBins + lane], 1u);
-    nb += d >> 31;
-  };
-  {
-    // 16-byte shared loads (buf is 16-byte aligned), then the ragged tail
-    const int n4 = n >> 2;
-    const int4 *b4 = reinterpret_cast<const int4 *>(buf);
-    for (int q = tid; q < n4; q += kSpsThreads) {
-      const int4 v = b4[q];
-      bin(v.x);
-      bin(v.y);
-      bin(v.z);
-      bin(v.w);
-    }
-    for (int i = 4 * n4 + tid; i < n; i += kSpsThreads) bin(buf[i]);
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) nb += __shfl_xor_sync(0xffffffffu, nb, o);
-  if (lane == 0) sh.wred[warp][0] = nb;
-  __syncthreads();
   uint32_t below = 0;
-  for (int w = 0; w < kWarps; ++w) below += sh.wred[w][0];
+#pragma unroll
+  for (int w = 0; w < kWarps; ++w) below += sh.nbw[w];
   // ---- inclusive prefix P[b] = below + #{keys in [A, A + b]}, in place.
   // Warp w owns bins [kWarpBins w, kWarpBins (w + 1)) and lane l the four
   // bins 4l .. 4l + 3 of each 128-bin segment of them, so every 16-byte
@@ -315,63 +301,63 @@ __device__ bool median_mad_fast(const int32_t *__restrict__ buf, uint32_t base,
     const uint32_t inc = warp_incl_scan(t, lane);
     const uint32_t pre = run + inc - t;
     const uint32_t p0 = pre + c.x, p1 = p0 + c.y, p2 = p1 + c.z, p3 = p2 + c.w;
-    const int b0 = kWarpBins * warp + 128 * sg + 4 * lane;
-    hit(pre, p0, b0);
-    hit(p0, p1, b0 + 1);
-    hit(p1, p2, b0 + 2);
-    hit(p2, p3, b0 + 3);
+    // a rank reached inside this lane's four bins (R1 <= R2): rare, so the
+    // bins are told apart only then
+    if (pre < R2 && R1 <= p3) {
+      const int b0 = kWarpBins * warp + 128 * sg + 4 * lane;
+      hit(pre, p0, b0);
+      hit(p0, p1, b0 + 1);
+      hit(p1, p2, b0 + 2);
+      hit(p2, p3, b0 + 3);
+    }
     *reinterpret_cast<uint4 *>(wbins + 128 * sg) = make_uint4(p0, p1, p2, p3);
     run += __shfl_sync(0xffffffffu, inc, 31);
   }
   __syncthreads();
+  // (nothing writes bc[2], bc[3] again in this window, and select2, if it
+  // follows, starts with a barrier: no barrier after these reads)
   const int64_t b1 = sh.bc[2], b2 = sh.bc[3];
-  __syncthreads();
   if (b1 < 0 || b2 < 0) return false;  // block-uniform
-  k1 = A + (uint32_t)b1;
-  k2 = A + (uint32_t)b2;
-  if (tid == 0) {
-    sh.bc[2] = -1;
-    sh.bc[3] = -1;
-  }
-  __syncthreads();
+  k1 = (uint32_t)(A + b1);
+  k2 = (uint32_t)(A + b2);
   // ---- MAD: C(v) = #{|2k - m| <= v}, -1 when its key range leaves the bins
   const int64_t m = (int64_t)k1 + (int64_t)k2;
-  const int64_t lo_ok = (int64_t)A, hi_ok = (int64_t)A + kFastBins - 1;
+  const int64_t lo_ok = A, hi_ok = A + kFastBins - 1;
   auto count_within = [&](int64_t v) -> int64_t {
     const int64_t lo = (m - v + 1) >> 1, hi = (m + v) >> 1;
-    if (lo < lo_ok || hi > hi_ok) return -1;
+    if (hi > hi_ok || (lo < lo_ok && lo_ok > 0)) return -1;
     const int64_t ph = sh.hist[hi - lo_ok];
-    const int64_t pl = lo == lo_ok ? (int64_t)below : (int64_t)sh.hist[lo - lo_ok - 1];
+    // no key lies below min (key 0), so none below lo <= A <= 0 either
+    const int64_t pl = lo <= lo_ok ? (lo == lo_ok ? (int64_t)below : 0)
+                                   : (int64_t)sh.hist[lo - lo_ok - 1];
     return ph - pl;
   };
   // C is non-decreasing in v and valid on a prefix of [0, 2 * kFastBins),
-  // so the smallest v with C(v) >= R is found by one warp in three 32-way
-  // steps of widths 256, 8 and 1, each lane testing the last v of its part.
+  // so the smallest v with C(v) >= R is found by one warp per rank (warps
+  // 0 and 1 side by side) in three 32-way steps of widths 256, 8 and 1,
+  // each lane testing the last v of its part.
   static_assert(2 * kFastBins == 32 * 256, "MAD search covers [0, 8192)");
-  if (warp == 0) {
+  if (warp < 2) {
+    const int which = warp;
+    const int64_t R = (int64_t)(which ? r2 : r1) + 1;
+    int64_t base = 0;
+    bool found = true;
 #pragma unroll
-    for (int which = 0; which < 2; ++which) {
-      const int64_t R = (int64_t)(which ? r2 : r1) + 1;
-      int64_t base = 0;
-      bool found = true;
-#pragma unroll
-      for (int st = 0; st < 3; ++st) {
-        const int64_t w = st == 0 ? 256 : (st == 1 ? 8 : 1);
-        const int nl = st == 2 ? 8 : 32;
-        const int64_t cv = lane < nl ? count_within(base + lane * w + w - 1) : -1;
-        const unsigned hit = __ballot_sync(0xffffffffu, cv >= R);
-        if (hit == 0u) {   // warp-uniform: only possible in the first step
-          found = false;
-          break;
-        }
-        base += (int64_t)(__ffs(hit) - 1) * w;
+    for (int st = 0; st < 3; ++st) {
+      const int64_t w = st == 0 ? 256 : (st == 1 ? 8 : 1);
+      const int nl = st == 2 ? 8 : 32;
+      const int64_t cv = lane < nl ? count_within(base + lane * w + w - 1) : -1;
+      const unsigned hit = __ballot_sync(0xffffffffu, cv >= R);
+      if (hit == 0u) {   // warp-uniform: only possible in the first step
+        found = false;
+        break;
       }
-      if (lane == 0) sh.bc[2 + which] = found ? base : -1;
+      base += (int64_t)(__ffs(hit) - 1) * w;
     }
+    if (lane == 0) sh.bc[4 + which] = found ? base : -1;
   }
   __syncthreads();
-  const int64_t v1 = sh.bc[2], v2 = sh.bc[3];
-  __syncthreads();
+  const int64_t v1 = sh.bc[4], v2 = sh.bc[5];
   if (v1 < 0 || v2 < 0) return false;  // block-uniform
   u1 = (uint32_t)v1;
   u2 = (uint32_t)v2;
@@ -409,32 +395,33 @@ __host__ __device__ __forceinline__ int64_t sps_chunk_cap(int64_t cap) {
   return cap / kChunk + 2;
 }
 
-// One start time through the exact screen: the boxcar sums of every width
-// from the prefix sums, the integer screen, and (for widths that pass, or
-// every width in the dense mode) the FP32 S/N; best = first maximum.
-// Returns the best width index (-1: none) with its S/N and boxcar sum.
+// One start time through the exact path: the boxcar differences of every
+// width from the prefix values, the FP32 S/N and the best width (first
+// maximum).  Q2: the prefix is of y2 = 2x - M2, so a difference is the S/N
+// numerator 2 B_y - w*odd itself, below 2^22 in magnitude, and two
+// full-rate operations convert it exactly; else the prefix is of
+// y = x - floor(median), a difference is B_y and twice_minus rounds
+// 2 B_y - w*odd (no conversion instruction either: on this GPU it issues
+// at a fraction of the integer and FP32 rate).  Returns the best
+// width index (-1: none) with its S/N and its difference.
 // NW > 0: the widths are 1, 2, 4, ..., 2^(NW-1), so the boxcar ends are
 // compile-time offsets and a start whose widest boxcar ends inside the
-// series needs no per-width check; NW = 0: any ascending width list.
-template <bool DENSE, int NW>
+// series needs no per-width check; every width's S/N is taken (the same
+// best comes out as from the widths that pass the integer screen: a width
+// that fails it has S/N below the threshold, so it can be the best only
+// when no width reaches the threshold and there is no candidate either
+// way).  NW = 0: any ascending width list, each width screened first
+// (every width in the dense mode).
+template <bool DENSE, int NW, bool Q2>
 __device__ __forceinline__ int exact_start(
     const uint32_t *__restrict__ Q, int qcap, int i, int nv, int nw,
     const int32_t (&wv)[kMaxWidths], const int32_t (&tbv)[kMaxWidths],
-    const float (&iv)[kMaxWidths], int odd, int32_t mfloor, bool small,
-    float &bs, int32_t &bsum) {
+    const float (&iv)[kMaxWidths], int odd, float &bs, int32_t &bd) {
   const uint32_t qi = Q[i];
   int bw = -1;
   bs = 0.0f;
-  bsum = 0;
+  bd = 0;
   if constexpr (NW > 0) {
-    // Every width that ends inside the series gets its FP32 S/N and the
-    // first maximum wins; no integer screen first.  The same best comes out
-    // as from the widths that pass the screen: a width that fails it has
-    // S/N below the threshold (the screen keeps a margin), so it can be the
-    // best only when no width reaches the threshold and there is no
-    // candidate either way.  Here most starts (those of chunks whose bound
-    // could pass) have several widths near the threshold, and the S/N of
-    // all of them costs fewer operations than screening first.
     constexpr int kWidest = 1 << (NW - 1);
     const bool inner = i + kWidest <= nv &&
                        DDSP_BC(i + kWidest < qcap, kBcSpsQ, i + kWidest);
@@ -443,12 +430,13 @@ __device__ __forceinline__ int exact_start(
       const bool v = inner || (i + (1 << wi) <= nv &&
                                DDSP_BC(i + (1 << wi) < qcap, kBcSpsQ, i));
       if (v) {
-        const int32_t by = (int32_t)(Q[i + (1 << wi)] - qi);
-        const float sn = numer(by, (1 << wi) * odd, small) * iv[wi];
+        const int32_t d = (int32_t)(Q[i + (1 << wi)] - qi);
+        const float sn =
+            (Q2 ? small_int_to_float(d) : twice_minus(d, odd << wi)) * iv[wi];
         if (bw < 0 || sn > bs) {
           bw = wi;
           bs = sn;
-          bsum = by + (1 << wi) * mfloor;
+          bd = d;
         }
       }
     }
@@ -457,13 +445,15 @@ __device__ __forceinline__ int exact_start(
     for (int wi = 0; wi < kMaxWidths; ++wi) {
       if (wi < nw && i + wv[wi] <= nv &&
           DDSP_BC(i + wv[wi] < qcap, kBcSpsQ, i + wv[wi])) {
-        const int32_t by = (int32_t)(Q[i + wv[wi]] - qi);
-        if (DENSE || by >= tbv[wi]) {
-          const float sn = numer(by, wv[wi] * odd, small) * iv[wi];
+        const int32_t d = (int32_t)(Q[i + wv[wi]] - qi);
+        if (DENSE || d >= tbv[wi]) {
+          const float sn =
+              (Q2 ? small_int_to_float(d) : twice_minus(d, wv[wi] * odd)) *
+              iv[wi];
           if (bw < 0 || sn > bs) {
             bw = wi;
             bs = sn;
-            bsum = by + wv[wi] * mfloor;
+            bd = d;
           }
         }
       }
@@ -472,30 +462,75 @@ __device__ __forceinline__ int exact_start(
   return bw;
 }
 
-// Candidate emission of the lanes in `mask` that execute it together: one
-// atomicAdd per warp (ballot + popc), records beyond the capacity dropped
-// (the count stays exact).
-__device__ __forceinline__ void emit(unsigned mask, bool cand, int k, int64_t t,
-                                     int bw, float bs,
+// Candidate emission.  Each warp appends its candidates to its own stage
+// in shared memory (two words a record: start << 4 | width index, S/N;
+// ballot + popc give the positions) and, when the next run might not fit
+// and at the end of the window, moves the stage to the output with one
+// atomicAdd on the global count and coalesced 16-byte stores (records
+// beyond the capacity dropped, the count stays exact).  Without room for a
+// stage of 32 records (scap == 0) every run reserves its own slots.
+struct Emitter {
+  uint32_t *stage;   // this warp's stage: 2 * scap words
+  int scap;          // records it holds (0: no stage)
+  int n;             // records staged (warp-uniform)
+};
+
+__device__ __forceinline__ void emit_flush(Emitter &e, int k, int64_t lo,
+                                           ddsp_cand *__restrict__ cands,
+                                           uint32_t *__restrict__ count,
+                                           uint32_t cap) {
+  const int lane = threadIdx.x & 31;
+  if (e.n == 0) return;                         // warp-uniform
+  __syncwarp();
+  uint32_t base = 0;
+  if (lane == 0) base = atomicAdd(count, (uint32_t)e.n);
+  base = __shfl_sync(0xffffffffu, base, 0);
+  for (int r = lane; r < e.n; r += 32) {
+    const uint2 rec = reinterpret_cast<const uint2 *>(e.stage)[r];
+    if (base + (uint32_t)r < cap) {
+      ddsp_cand c;
+      c.dm_idx = (uint32_t)k;
+      c.t = (uint32_t)(lo + (int64_t)(rec.x >> 4));
+      c.w_idx = rec.x & 15u;
+      c.snr = __uint_as_float(rec.y);
+      cands[base + (uint32_t)r] = c;
+    }
+  }
+  __syncwarp();
+  e.n = 0;
+}
+
+// The candidates of one run of 32 starts (all lanes of the warp call it).
+__device__ __forceinline__ void emit(Emitter &e, bool cand, int k, int64_t lo,
+                                     int i, int bw, float bs,
                                      ddsp_cand *__restrict__ cands,
                                      uint32_t *__restrict__ count,
                                      uint32_t cap) {
   const int lane = threadIdx.x & 31;
-  const unsigned ball = __ballot_sync(mask, cand);
-  if (!cand) return;
-  const int leader = __ffs(ball) - 1;
-  uint32_t base = 0;
-  if (lane == leader) base = atomicAdd(count, (uint32_t)__popc(ball));
-  base = __shfl_sync(ball, base, leader);
-  const uint32_t slot = base + __popc(ball & ((1u << lane) - 1u));
-  if (slot < cap) {
-    ddsp_cand c;
-    c.dm_idx = (uint32_t)k;
-    c.t = (uint32_t)t;
-    c.w_idx = (uint32_t)bw;
-    c.snr = bs;
-    cands[slot] = c;
+  const unsigned ball = __ballot_sync(0xffffffffu, cand);
+  if (ball == 0u) return;                       // warp-uniform
+  const int nb = __popc(ball);
+  const uint32_t below = __popc(ball & ((1u << lane) - 1u));
+  if (e.scap == 0) {
+    const int leader = __ffs(ball) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(count, (uint32_t)nb);
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (cand && base + below < cap) {
+      ddsp_cand c;
+      c.dm_idx = (uint32_t)k;
+      c.t = (uint32_t)(lo + i);
+      c.w_idx = (uint32_t)bw;
+      c.snr = bs;
+      cands[base + below] = c;
+    }
+    return;
   }
+  if (e.n + nb > e.scap) emit_flush(e, k, lo, cands, count, cap);
+  if (cand)
+    reinterpret_cast<uint2 *>(e.stage)[e.n + (int)below] =
+        make_uint2(((uint32_t)i << 4) | (uint32_t)bw, __float_as_uint(bs));
+  e.n += nb;
 }
 
 // What the sweep of one window needs (step 4).
@@ -503,12 +538,15 @@ struct SweepArgs {
   const uint32_t *Q;
   int qcap, len, nv, nw, odd;
   int32_t mfloor;
+  int64_t m2;
   float thr;
   int64_t lo, n, nrep;
   int k, wmax;
   bool bounds;
-  bool small;    // every |2 B_y - w*odd| < 2^31 in this window
   const int32_t *cmin, *cmax, *ymax;
+  const int32_t *wid;       // the widths (shared memory)
+  uint32_t *stage;          // the warps' stages (shared memory)
+  int scap;                 // records per warp stage (0: none)
   ddsp_cand *cands;
   uint32_t *count;
   uint32_t cap;
@@ -517,8 +555,9 @@ struct SweepArgs {
   int32_t *best_sum;
 };
 
-// Step 4: boxcars, S/N, candidates of one window (NW as in exact_start).
-template <bool DENSE, int NW>
+// Step 4: boxcars, S/N, candidates of one window (NW and Q2 as in
+// exact_start).
+template <bool DENSE, int NW, bool Q2>
 __device__ __forceinline__ void sweep(const SweepArgs &g,
                                       const int32_t (&wv)[kMaxWidths],
                                       const int32_t (&tbv)[kMaxWidths],
@@ -528,10 +567,17 @@ __device__ __forceinline__ void sweep(const SweepArgs &g,
   if (DENSE) {
     for (int i = tid; i < g.len; i += kSpsThreads) {
       float bs;
-      int32_t bsum;
-      const int bw = exact_start<true, NW>(g.Q, g.qcap, i, g.nv, g.nw, wv, tbv,
-                                           iv, g.odd, g.mfloor, g.small, bs,
-                                           bsum);
+      int32_t bd;
+      const int bw = exact_start<true, NW, Q2>(g.Q, g.qcap, i, g.nv, g.nw, wv,
+                                               tbv, iv, g.odd, bs, bd);
+      // the boxcar sum of x: (num + w*M2)/2 (Q2) or B_y + w*floor(median),
+      // modulo 2^32
+      int32_t bsum = 0;
+      if (bw >= 0) {
+        const int w = NW > 0 ? (1 << bw) : g.wid[bw];
+        bsum = Q2 ? (int32_t)(((int64_t)bd + (int64_t)w * g.m2) >> 1)
+                  : (int32_t)((uint32_t)bd + (uint32_t)w * (uint32_t)g.mfloor);
+      }
       const int64_t o = (int64_t)g.k * g.n + g.lo + i;
       if (DDSP_BC(g.lo + i < g.n, kBcSpsDense, g.lo + i)) {
         g.best_w[o] = bw;
@@ -541,9 +587,10 @@ __device__ __forceinline__ void sweep(const SweepArgs &g,
     }
     return;
   }
+  Emitter em{g.stage + 2 * g.scap * warp, g.scap, 0};
   // A warp takes 32 consecutive chunks (256 start times) at a time: lane l
   // bounds chunk l; the chunks that could pass then go through the exact
-  // screen 32 consecutive starts at a time, one per lane (consecutive
+  // path 32 consecutive starts at a time, one per lane (consecutive
   // shared-memory words: no bank conflicts), skipping the 32-start runs
   // whose four chunks all failed their bounds.
   const int nch = (g.len + kChunk - 1) / kChunk;
@@ -590,15 +637,16 @@ __device__ __forceinline__ void sweep(const SweepArgs &g,
       const int i = kChunk * cb + 32 * sb + lane;
       const bool mine = ((sub >> (lane >> 3)) & 1u) && i < g.len;
       float bs = 0.0f;
-      int32_t bsum;
+      int32_t bd;
       int bw = -1;
       if (mine)
-        bw = exact_start<false, NW>(g.Q, g.qcap, i, g.nv, g.nw, wv, tbv, iv,
-                                    g.odd, g.mfloor, g.small, bs, bsum);
+        bw = exact_start<false, NW, Q2>(g.Q, g.qcap, i, g.nv, g.nw, wv, tbv,
+                                        iv, g.odd, bs, bd);
       const bool cand = bw >= 0 && bs >= g.thr && g.lo + i < g.nrep;
-      emit(0xffffffffu, cand, g.k, g.lo + i, bw, bs, g.cands, g.count, g.cap);
+      emit(em, cand, g.k, g.lo, i, bw, bs, g.cands, g.count, g.cap);
     }
   }
+  emit_flush(em, g.k, g.lo, g.cands, g.count, g.cap);
 }
 
 // The search of one (DM trial k, window j): the body of the per-plan kernel
@@ -643,10 +691,12 @@ __device__ __forceinline__ void sps_window(
   const int32_t *x = series + (int64_t)k * n + lo;
 
   // ---- 1. load x[0 .. elen) to buf, min and max over the window [0, len)
-  // and over the look-ahead [len, elen), and each warp's sum of x over its
-  // run of the scan's 128-position groups (so step 3 needs one pass).  A
-  // lane takes 4 consecutive samples of a group: 16-byte loads when the
-  // window starts on a 16-byte boundary (n and L multiples of 4).
+  // and over the look-ahead [len, elen), each warp's sum of x over its run
+  // of the scan's 128-position groups (so step 3 needs one pass), and the
+  // median's histogram of the window (step 2's one-pass bins, filled as the
+  // samples arrive).  A lane takes 4 consecutive samples of a group: 16-byte
+  // loads when the window starts on a 16-byte boundary (n and L multiples
+  // of 4).
   int32_t mn32 = INT32_MAX, mx32 = INT32_MIN;   // the window [0, len)
   int32_t hmn = INT32_MAX, hmx = INT32_MIN;     // look-ahead [len, elen)
   auto take = [&](int i, int32_t v) {
@@ -665,25 +715,68 @@ __device__ __forceinline__ void sps_window(
   const bool vec = (reinterpret_cast<uintptr_t>(x) & 15) == 0;
   uint32_t sx = 0;                              // this lane's sum of x
   int h = 2 * g0;                               // 128-position halves
-  if (vec) {
-    // halves wholly inside the window proper, four loads in flight a lane
-    const int hin = min(2 * g1, len / 128);
-    for (; h + 4 <= hin; h += 4) {
-      if (!DDSP_BC((h + 4) * 128 <= bufcap && lo + (h + 4) * 128 <= n,
-                   kBcSpsLoad, lo + h * 128))
-        break;
-      int4 v[4];
+  // halves wholly inside the window proper go four at a time, four loads
+  // in flight a lane; the first four leave before the estimate's barrier
+  const int hin = vec ? min(2 * g1, len / 128) : h;
+  auto batch_ok = [&](int hh) {
+    return hh + 4 <= hin &&
+           DDSP_BC((hh + 4) * 128 <= bufcap && lo + (hh + 4) * 128 <= n,
+                   kBcSpsLoad, lo + hh * 128);
+  };
+  int4 v[4];
+  bool have = batch_ok(h);
+  if (have) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      v[u] = __ldg(reinterpret_cast<const int4 *>(x + (h + u) * 128) + lane);
+  }
+  // the median estimate (the last warp has the fewest load groups) and the
+  // zeroed histogram, both visible after the barrier
+  if (!given && warp == kWarps - 1) median_estimate(x, lo, n, len, sh);
+  for (int b = tid; b < (kFastBins + 32) / 4; b += kSpsThreads)
+    reinterpret_cast<uint4 *>(sh.hist)[b] = make_uint4(0u, 0u, 0u, 0u);
+  __syncthreads();
+  // Single-value bins [AB, AB + kFastBins) of x around the estimate and the
+  // count of window samples below AB, for windows whose estimated
+  // interquartile range is narrow (else step 2 goes to select2).  d = x - AB
+  // mod 2^32 bins a sample and, by its top bit, counts it below the bins;
+  // that holds while every x - AB lies in [-2^31, 2^31), which step 2
+  // checks against the window's extremes before it trusts the counts.
+  const bool binning = !given && sh.bc[1] <= 2800;   // block-uniform
+  const int64_t AB64 = max((int64_t)(int32_t)sh.bc[0] - kFastBins / 2,
+                           (int64_t)INT32_MIN);
+  const uint32_t AB = (uint32_t)(int32_t)AB64;
+  uint32_t nb = 0;
+  auto bin = [&](int32_t xv) {
+    const uint32_t d = (uint32_t)xv - AB;
+    // samples outside the bins (d >= kFastBins as unsigned: above them, or
+    // below them with the top bit set) go by one unsigned minimum to the
+    // lane's own sink bin (no branch, and no two lanes of a warp collide
+    // there)
+    atomicAdd(&sh.hist[min(d, (uint32_t)(kFastBins + lane))], 1u);
+    nb += d >> 31;
+  };
+  while (have) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      reinterpret_cast<int4 *>(buf + (h + u) * 128)[lane] = v[u];
+      sx += (uint32_t)v[u].x + (uint32_t)v[u].y + (uint32_t)v[u].z +
+            (uint32_t)v[u].w;
+      mn32 = __vimin3_s32(mn32, __vimin3_s32(v[u].x, v[u].y, v[u].z), v[u].w);
+      mx32 = __vimax3_s32(mx32, __vimax3_s32(v[u].x, v[u].y, v[u].z), v[u].w);
+      if (binning) {
+        bin(v[u].x);
+        bin(v[u].y);
+        bin(v[u].z);
+        bin(v[u].w);
+      }
+    }
+    h += 4;
+    have = batch_ok(h);
+    if (have) {
 #pragma unroll
       for (int u = 0; u < 4; ++u)
         v[u] = __ldg(reinterpret_cast<const int4 *>(x + (h + u) * 128) + lane);
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        reinterpret_cast<int4 *>(buf + (h + u) * 128)[lane] = v[u];
-        sx += (uint32_t)v[u].x + (uint32_t)v[u].y + (uint32_t)v[u].z +
-              (uint32_t)v[u].w;
-        mn32 = min(mn32, min(min(v[u].x, v[u].y), min(v[u].z, v[u].w)));
-        mx32 = max(mx32, max(max(v[u].x, v[u].y), max(v[u].z, v[u].w)));
-      }
     }
   }
   for (; h < 2 * g1; ++h) {
@@ -691,31 +784,42 @@ __device__ __forceinline__ void sps_window(
     if (!DDSP_BC(b4 + 4 <= bufcap, kBcSpsBuf, b4)) continue;
     if (vec && b4 + 4 <= elen &&
         DDSP_BC(lo + b4 + 4 <= n, kBcSpsLoad, lo + b4)) {
-      const int4 v = __ldg(reinterpret_cast<const int4 *>(x + b4));
-      *reinterpret_cast<int4 *>(buf + b4) = v;
-      sx += (uint32_t)v.x + (uint32_t)v.y + (uint32_t)v.z + (uint32_t)v.w;
+      const int4 w4 = __ldg(reinterpret_cast<const int4 *>(x + b4));
+      *reinterpret_cast<int4 *>(buf + b4) = w4;
+      sx += (uint32_t)w4.x + (uint32_t)w4.y + (uint32_t)w4.z + (uint32_t)w4.w;
       if (b4 + 4 <= len) {
-        mn32 = min(mn32, min(min(v.x, v.y), min(v.z, v.w)));
-        mx32 = max(mx32, max(max(v.x, v.y), max(v.z, v.w)));
+        mn32 = __vimin3_s32(mn32, __vimin3_s32(w4.x, w4.y, w4.z), w4.w);
+        mx32 = __vimax3_s32(mx32, __vimax3_s32(w4.x, w4.y, w4.z), w4.w);
+        if (binning) {
+          bin(w4.x);
+          bin(w4.y);
+          bin(w4.z);
+          bin(w4.w);
+        }
       } else {
-        take(b4, v.x);
-        take(b4 + 1, v.y);
-        take(b4 + 2, v.z);
-        take(b4 + 3, v.w);
+        const int32_t e4[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          take(b4 + e, e4[e]);
+          if (binning && b4 + e < len) bin(e4[e]);
+        }
       }
     } else {
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const int i = b4 + e;
         if (i < elen && DDSP_BC(lo + i < n, kBcSpsLoad, lo + i)) {
-          const int32_t v = __ldg(x + i);
-          buf[i] = v;
-          sx += (uint32_t)v;
-          take(i, v);
+          const int32_t xv = __ldg(x + i);
+          buf[i] = xv;
+          sx += (uint32_t)xv;
+          take(i, xv);
+          if (binning && i < len) bin(xv);
         }
       }
     }
   }
+  nb = __reduce_add_sync(0xffffffffu, nb);
+  if (lane == 0) sh.nbw[warp] = nb;
   sx = __reduce_add_sync(0xffffffffu, sx);
   if (lane == 0) sh.wsx[warp] = sx;
   mn32 = __reduce_min_sync(0xffffffffu, mn32);
@@ -740,7 +844,8 @@ __device__ __forceinline__ void sps_window(
   }
   fmn = min(mn, hn);    // everything loaded: window and look-ahead
   fmx = max(mx, hx);
-  __syncthreads();
+  // (no barrier: wred and hred are written again only by select2's
+  // fallback, after barriers every thread passes once it has read them)
 
   // ---- 2. median and MAD
   int64_t M2 = 0, MAD4 = 0;
@@ -754,7 +859,11 @@ __device__ __forceinline__ void sps_window(
     uint32_t k1, k2, u1, u2;
     // keys x - min in [0, 2^31)
     auto kx = [&](int i) { return (uint32_t)buf[i] - base; };
-    const bool fast = median_mad_fast(buf, base, len, r1, r2, sh, k1, k2, u1, u2);
+    // the bins' counts hold when every window sample lies within 2^31
+    // of AB (below it: top bit set; from it up: clear)
+    const bool fast = binning && mx - AB64 < ((int64_t)1 << 31) &&
+                      AB64 - mn <= ((int64_t)1 << 31) &&
+                      median_mad_fast(AB64 - mn, r1, r2, sh, k1, k2, u1, u2);
     if (!fast)
       select2(kx, len, r1, r2, (uint32_t)(mx - mn), sh, k1, k2);
     M2 = 2 * mn + (int64_t)k1 + (int64_t)k2;
@@ -779,55 +888,64 @@ __device__ __forceinline__ void sps_window(
   }
 
   // per-width FP32 scale 1/(2 sigma sqrt(w)) and integer screen thresholds
-  // on B_y = sum(y) over the width: S/N >= thr  <=>  2 B_y - w*odd >= thr *
-  // 2 sigma sqrt(w); the screen keeps a 4e-6 relative margin below that so
-  // FP32 rounding cannot hide a candidate the FP32 S/N would accept.
+  // (set in step 3 by the last warp).
+  // S/N >= thr  <=>  2 B_y - w*odd >= thr * 2 sigma sqrt(w); the screen
+  // keeps a 4e-6 relative margin below that so FP32 rounding cannot hide a
+  // candidate the FP32 S/N would accept.  Q2 (|2x - M2| <= 2 ybound + 1,
+  // ybound the larger distance of floor(median) to the extremes of
+  // everything loaded; that times elen + 1 below 2^30, so every prefix
+  // value is below 2^30 in magnitude and the chunk bounds stay exact, and
+  // times w_max below 2^22, so every numerator 2 B_y - w*odd converts
+  // exactly): the prefix holds 2x - M2 and the threshold is on the
+  // numerator itself; else on B_y.
   const int32_t mfloor = (int32_t)(M2 >> 1);  // floor(median)
   const int odd = (int)(M2 & 1);
-  if (tid < nw) {
-    const float w = (float)widths[tid];
-    const float two_sigma = kMadToSigma * (float)MAD4 * 0.5f;
-    const float denom = two_sigma * sqrtf(w);
-    sh.inv[tid] = MAD4 > 0 ? 1.0f / denom : 0.0f;
-    float tnum = thr * denom * (1.0f - 4e-6f);  // threshold on 2B_y - w*odd
-    float tby = 0.5f * (tnum + (float)(widths[tid] * odd));
-    int32_t tb;
-    if (MAD4 <= 0 || !(tby < 2.0e9f)) tb = INT32_MAX;
-    else if (tby <= -2.0e9f) tb = INT32_MIN;
-    else tb = (int32_t)floorf(tby);
-    sh.thr_by[tid] = tb;
-    sh.wid[tid] = widths[tid];
-  }
-
-  // ---- 3. y = x - floor(median) and the exclusive prefix sum Q, in place:
-  // buf[p] = Q[p] = sum_{t < p} y[t] for p = 0 .. elen (uint32, modular, so
-  // every boxcar sum Q[t + w] - Q[t] is exact).  Groups of 256 positions, a
-  // lane taking 8 consecutive ones (one chunk) with two 16-byte shared
-  // loads, each warp a contiguous run of groups: the runs' totals follow
-  // from the sums of x the load took, so one pass scans with every warp's
-  // offset known, recording each lane's chunk statistics on the way.
-  // Statistics are kept only when every prefix value fits in 30 bits in
-  // magnitude (|y| <= the larger distance of floor(median) to the extremes
-  // of everything loaded, so that times (elen + 1) below 2^30), where
-  // minima, maxima and their differences are exact.
   const int64_t ybound = max(fmx - (int64_t)mfloor, (int64_t)mfloor - fmn);
-  const bool bounds =
-      !DENSE && have_stats && range_ok && MAD4 > 0 && elen > 0 &&
-      ybound * (int64_t)(elen + 1) < ((int64_t)1 << 30);
+  const bool q2 = range_ok &&
+                  (2 * ybound + 1) * (int64_t)(elen + 1) < ((int64_t)1 << 30) &&
+                  (2 * ybound + 1) * (int64_t)wmax < ((int64_t)1 << 22);
+  // ---- 3. y (Q2: 2x - M2, else x - floor(median)) and its exclusive prefix
+  // sum Q, in place: buf[p] = Q[p] = sum_{t < p} y[t] for p = 0 .. elen
+  // (uint32, modular, so every difference Q[t + w] - Q[t] is exact).
+  // Groups of 256 positions, a lane taking 8 consecutive ones (one chunk)
+  // with two 16-byte shared loads, each warp a contiguous run of groups:
+  // the runs' totals follow from the sums of x the load took, so one pass
+  // scans with every warp's offset known, recording each lane's chunk
+  // statistics on the way.  Statistics are kept only when every prefix
+  // value fits in 30 bits in magnitude (the bound on |y| times (elen + 1)
+  // below 2^30), where minima, maxima and their differences are exact.
+  const int64_t ybnd = q2 ? 2 * ybound + 1 : ybound;
+  const bool bounds = !DENSE && have_stats && range_ok && MAD4 > 0 &&
+                      elen > 0 && ybnd * (int64_t)(elen + 1) < ((int64_t)1 << 30);
   {
-    const uint32_t mf = (uint32_t)mfloor;
-    auto yv = [&](int p, int32_t v) {
-      return p < elen ? (uint32_t)v - mf : 0u;
-    };
+    // y = x * ymul - ysub (mod 2^32)
+    const uint32_t ymul = q2 ? 2u : 1u;
+    const uint32_t ysub = q2 ? (uint32_t)M2 : (uint32_t)mfloor;
     // warp runs' totals of y from the sums of x the load took: a run holds
     // the positions [128 g0, 128 g1) and those below elen carry a sample
     if (warp == 0 && lane < kWarps) {
       const int r0 = lane * gpw * kGroup;
       const int r1 = min(ngroups, (lane + 1) * gpw) * kGroup;
       const int cnt = max(0, min(r1, elen) - r0);
-      sh.wsum[lane] = sh.wsx[lane] - (uint32_t)cnt * mf;
+      sh.wsum[lane] = sh.wsx[lane] * ymul - (uint32_t)cnt * ysub;
     }
     __syncthreads();
+    // thresholds (read by the sweep after the barrier that ends the scan)
+    // by the last warp, which has the fewest scan groups
+    if (warp == kWarps - 1 && lane < nw) {
+      const float w = (float)widths[lane];
+      const float two_sigma = kMadToSigma * (float)MAD4 * 0.5f;
+      const float denom = two_sigma * sqrtf(w);
+      sh.inv[lane] = MAD4 > 0 ? 1.0f / denom : 0.0f;
+      const float tnum = thr * denom * (1.0f - 4e-6f);
+      const float t = q2 ? tnum : 0.5f * (tnum + (float)(widths[lane] * odd));
+      int32_t tb;
+      if (MAD4 <= 0 || !(t < 2.0e9f)) tb = INT32_MAX;
+      else if (t <= -2.0e9f) tb = INT32_MIN;
+      else tb = (int32_t)floorf(t);
+      sh.thr_by[lane] = tb;
+      sh.wid[lane] = widths[lane];
+    }
     uint32_t carry = warp_excl_offset(sh.wsum, warp, lane);
     for (int g = g0; g < g1; ++g) {
       // this lane's 8 consecutive positions = one chunk of the statistics
@@ -844,10 +962,11 @@ __device__ __forceinline__ void sps_window(
       uint32_t y[8];
       if (b8 + 8 <= elen) {
 #pragma unroll
-        for (int e = 0; e < 8; ++e) y[e] = (uint32_t)xv[e] - mf;
+        for (int e = 0; e < 8; ++e) y[e] = (uint32_t)xv[e] * ymul - ysub;
       } else {
 #pragma unroll
-        for (int e = 0; e < 8; ++e) y[e] = yv(b8 + e, xv[e]);
+        for (int e = 0; e < 8; ++e)
+          y[e] = b8 + e < elen ? (uint32_t)xv[e] * ymul - ysub : 0u;
       }
       uint32_t ex[8];        // exclusive prefix inside the chunk
       ex[0] = 0u;
@@ -864,14 +983,21 @@ __device__ __forceinline__ void sps_window(
       }
       carry += __shfl_sync(0xffffffffu, inc, 31);
       if (bounds) {
-        // Q = pre + ex, exact as int32 here (|Q| < 2^30)
-        int32_t en = 0, exx = 0, ym = (int32_t)y[0];
-#pragma unroll
-        for (int e = 1; e < 8; ++e) {
-          en = min(en, (int32_t)ex[e]);
-          exx = max(exx, (int32_t)ex[e]);
-          ym = max(ym, (int32_t)y[e]);
-        }
+        // Q = pre + ex, exact as int32 here (|Q| < 2^30); ex[0] = 0
+        const int32_t e1 = (int32_t)ex[1], e2 = (int32_t)ex[2],
+                      e3 = (int32_t)ex[3], e4 = (int32_t)ex[4],
+                      e5 = (int32_t)ex[5], e6 = (int32_t)ex[6],
+                      e7 = (int32_t)ex[7];
+        const int32_t en = __vimin3_s32(__vimin3_s32(0, e1, e2),
+                                        __vimin3_s32(e3, e4, e5),
+                                        min(e6, e7));
+        const int32_t exx = __vimax3_s32(__vimax3_s32(0, e1, e2),
+                                         __vimax3_s32(e3, e4, e5),
+                                         max(e6, e7));
+        const int32_t ym = __vimax3_s32(
+            __vimax3_s32((int32_t)y[0], (int32_t)y[1], (int32_t)y[2]),
+            __vimax3_s32((int32_t)y[3], (int32_t)y[4], (int32_t)y[5]),
+            max((int32_t)y[6], (int32_t)y[7]));
         const int c = b8 / kChunk;
         if (DDSP_BC(c < sps_chunk_cap(bufcap), kBcSpsStats, c)) {
           cmin[c] = (int32_t)pre + en;
@@ -902,23 +1028,40 @@ __device__ __forceinline__ void sps_window(
 #pragma unroll
   for (int wi = 0; wi < kMaxWidths; ++wi)
     pow2 = pow2 && (wi >= nw || wv[wi] == (1 << wi));
-  // |B_y| <= ybound * w, so |2 B_y - w odd| < 2^31 when ybound * wmax < 2^29
-  const bool small = range_ok && ybound * (int64_t)wmax < ((int64_t)1 << 29);
-  const SweepArgs g{Q,    (int)bufcap, len,   nv,    nw,     odd,  mfloor,
-                    thr,  lo,          n,     nrep,  k,      wmax, bounds,
-                    small, cmin, cmax, ymax,  cands, count,  cap,  best_w,
-                    best_snr, best_sum};
-  switch (pow2 ? nw : 0) {
-#define DDSP_SWEEP(N)                        \
-  case N:                                    \
-    sweep<DENSE, N>(g, wv, tbv, iv, bufcap); \
+  // the warps' candidate stages: the histogram's space the chunk statistics
+  // leave free (16-byte aligned), when it holds 32 records a warp
+  uint32_t *stage = nullptr;
+  int scap = 0;
+  if (!DENSE) {
+    const int used = stats_in_hist ? (int)((3 * ccap + 3) & ~3) : 0;
+    const int per = ((kFastBins + 32 - used) / kWarps / 2) & ~1;
+    if (per >= 32) {
+      stage = sh.hist + used;
+      scap = per;
+    }
+  }
+  const SweepArgs g{Q,     (int)bufcap, len,  nv,    nw,       odd,
+                    mfloor, M2,         thr,  lo,    n,        nrep,
+                    k,     wmax,        bounds, cmin, cmax,    ymax,
+                    sh.wid, stage,      scap, cands, count,    cap,
+                    best_w, best_snr,   best_sum};
+  switch ((pow2 ? nw : 0) + (q2 ? 16 : 0)) {
+#define DDSP_SWEEP(N)                                 \
+  case N:                                             \
+    sweep<DENSE, N, false>(g, wv, tbv, iv, bufcap);   \
+    return;                                           \
+  case N + 16:                                        \
+    sweep<DENSE, N, true>(g, wv, tbv, iv, bufcap);    \
     return;
     DDSP_SWEEP(1) DDSP_SWEEP(2) DDSP_SWEEP(3) DDSP_SWEEP(4) DDSP_SWEEP(5)
     DDSP_SWEEP(6) DDSP_SWEEP(7) DDSP_SWEEP(8) DDSP_SWEEP(9) DDSP_SWEEP(10)
     DDSP_SWEEP(11)
 #undef DDSP_SWEEP
+    case 16:
+      sweep<DENSE, 0, true>(g, wv, tbv, iv, bufcap);
+      return;
     default:
-      sweep<DENSE, 0>(g, wv, tbv, iv, bufcap);
+      sweep<DENSE, 0, false>(g, wv, tbv, iv, bufcap);
   }
 }
 
