@@ -425,20 +425,41 @@ __device__ __forceinline__ int exact_start(
     constexpr int kWidest = 1 << (NW - 1);
     const bool inner = i + kWidest <= nv &&
                        DDSP_BC(i + kWidest < qcap, kBcSpsQ, i + kWidest);
+    // every width's S/N (-inf for a boxcar past the series end), then the
+    // first maximum by a pairwise tree: the right group (higher widths) wins
+    // only when strictly larger, so ties keep the lowest width, as a scan
+    // in width order would, with log2(NW) dependent steps instead of NW
+    float sn[NW];
+    int32_t dd[NW];
+    int id[NW];
 #pragma unroll
     for (int wi = 0; wi < NW; ++wi) {
       const bool v = inner || (i + (1 << wi) <= nv &&
                                DDSP_BC(i + (1 << wi) < qcap, kBcSpsQ, i));
+      id[wi] = wi;
+      dd[wi] = 0;
+      sn[wi] = -INFINITY;
       if (v) {
-        const int32_t d = (int32_t)(Q[i + (1 << wi)] - qi);
-        const float sn =
-            (Q2 ? small_int_to_float(d) : twice_minus(d, odd << wi)) * iv[wi];
-        if (bw < 0 || sn > bs) {
-          bw = wi;
-          bs = sn;
-          bd = d;
-        }
+        dd[wi] = (int32_t)(Q[i + (1 << wi)] - qi);
+        sn[wi] = (Q2 ? small_int_to_float(dd[wi])
+                     : twice_minus(dd[wi], odd << wi)) *
+                 iv[wi];
       }
+    }
+#pragma unroll
+    for (int st = 1; st < NW; st <<= 1) {
+#pragma unroll
+      for (int a = 0; a + st < NW; a += 2 * st) {
+        const bool right = sn[a + st] > sn[a];
+        sn[a] = right ? sn[a + st] : sn[a];
+        id[a] = right ? id[a + st] : id[a];
+        dd[a] = right ? dd[a + st] : dd[a];
+      }
+    }
+    if (sn[0] != -INFINITY) {   // (width 1 always fits: never taken here)
+      bw = id[0];
+      bs = sn[0];
+      bd = dd[0];
     }
   } else {
 #pragma unroll
@@ -463,19 +484,23 @@ __device__ __forceinline__ int exact_start(
 }
 
 // Candidate emission.  Each warp appends its candidates to its own stage
-// in shared memory (two words a record: start << 4 | width index, S/N;
-// ballot + popc give the positions) and, when the next run might not fit
-// and at the end of the window, moves the stage to the output with one
-// atomicAdd on the global count and coalesced 16-byte stores (records
-// beyond the capacity dropped, the count stays exact).  Without room for a
-// stage of 32 records (scap == 0) every run reserves its own slots.
+// in shared memory, one word a record (start << 4 | width index; ballot +
+// popc give the positions), and, when the next run might not fit and at
+// the end of the window, moves the stage to the output with one atomicAdd
+// on the global count and coalesced 16-byte stores, each record's S/N
+// recomputed from the prefix values with the operations that produced it
+// (the same bits); records beyond the capacity are dropped, the count
+// stays exact.  Without room for a stage of 32 records (scap == 0) every
+// run reserves its own slots.
 struct Emitter {
-  uint32_t *stage;   // this warp's stage: 2 * scap words
+  uint32_t *stage;   // this warp's stage: scap words
   int scap;          // records it holds (0: no stage)
   int n;             // records staged (warp-uniform)
 };
 
-__device__ __forceinline__ void emit_flush(Emitter &e, int k, int64_t lo,
+// rec(word) -> ddsp_cand rebuilds a staged record.
+template <typename RecFn>
+__device__ __forceinline__ void emit_flush(Emitter &e, RecFn rec,
                                            ddsp_cand *__restrict__ cands,
                                            uint32_t *__restrict__ count,
                                            uint32_t cap) {
@@ -485,24 +510,16 @@ __device__ __forceinline__ void emit_flush(Emitter &e, int k, int64_t lo,
   uint32_t base = 0;
   if (lane == 0) base = atomicAdd(count, (uint32_t)e.n);
   base = __shfl_sync(0xffffffffu, base, 0);
-  for (int r = lane; r < e.n; r += 32) {
-    const uint2 rec = reinterpret_cast<const uint2 *>(e.stage)[r];
-    if (base + (uint32_t)r < cap) {
-      ddsp_cand c;
-      c.dm_idx = (uint32_t)k;
-      c.t = (uint32_t)(lo + (int64_t)(rec.x >> 4));
-      c.w_idx = rec.x & 15u;
-      c.snr = __uint_as_float(rec.y);
-      cands[base + (uint32_t)r] = c;
-    }
-  }
+  for (int r = lane; r < e.n; r += 32)
+    if (base + (uint32_t)r < cap) cands[base + (uint32_t)r] = rec(e.stage[r]);
   __syncwarp();
   e.n = 0;
 }
 
 // The candidates of one run of 32 starts (all lanes of the warp call it).
+template <typename RecFn>
 __device__ __forceinline__ void emit(Emitter &e, bool cand, int k, int64_t lo,
-                                     int i, int bw, float bs,
+                                     int i, int bw, float bs, RecFn rec,
                                      ddsp_cand *__restrict__ cands,
                                      uint32_t *__restrict__ count,
                                      uint32_t cap) {
@@ -526,10 +543,8 @@ __device__ __forceinline__ void emit(Emitter &e, bool cand, int k, int64_t lo,
     }
     return;
   }
-  if (e.n + nb > e.scap) emit_flush(e, k, lo, cands, count, cap);
-  if (cand)
-    reinterpret_cast<uint2 *>(e.stage)[e.n + (int)below] =
-        make_uint2(((uint32_t)i << 4) | (uint32_t)bw, __float_as_uint(bs));
+  if (e.n + nb > e.scap) emit_flush(e, rec, cands, count, cap);
+  if (cand) e.stage[e.n + (int)below] = ((uint32_t)i << 4) | (uint32_t)bw;
   e.n += nb;
 }
 
@@ -545,6 +560,7 @@ struct SweepArgs {
   bool bounds;
   const int32_t *cmin, *cmax, *ymax;
   const int32_t *wid;       // the widths (shared memory)
+  const float *inv;         // their S/N scales (shared memory)
   uint32_t *stage;          // the warps' stages (shared memory)
   int scap;                 // records per warp stage (0: none)
   ddsp_cand *cands;
@@ -587,7 +603,21 @@ __device__ __forceinline__ void sweep(const SweepArgs &g,
     }
     return;
   }
-  Emitter em{g.stage + 2 * g.scap * warp, g.scap, 0};
+  Emitter em{g.stage + g.scap * warp, g.scap, 0};
+  // a staged record back to its output form: the S/N of width bw at start
+  // i, computed as exact_start computes it
+  auto rec = [&](uint32_t word) {
+    const int i = (int)(word >> 4), bw = (int)(word & 15u);
+    const int w = NW > 0 ? (1 << bw) : g.wid[bw];
+    const int32_t d = (int32_t)(g.Q[i + w] - g.Q[i]);
+    ddsp_cand c;
+    c.dm_idx = (uint32_t)g.k;
+    c.t = (uint32_t)(g.lo + i);
+    c.w_idx = (uint32_t)bw;
+    c.snr = (Q2 ? small_int_to_float(d) : twice_minus(d, w * g.odd)) *
+            g.inv[bw];
+    return c;
+  };
   // A warp takes 32 consecutive chunks (256 start times) at a time: lane l
   // bounds chunk l; the chunks that could pass then go through the exact
   // path 32 consecutive starts at a time, one per lane (consecutive
@@ -643,10 +673,10 @@ __device__ __forceinline__ void sweep(const SweepArgs &g,
         bw = exact_start<false, NW, Q2>(g.Q, g.qcap, i, g.nv, g.nw, wv, tbv,
                                         iv, g.odd, bs, bd);
       const bool cand = bw >= 0 && bs >= g.thr && g.lo + i < g.nrep;
-      emit(em, cand, g.k, g.lo, i, bw, bs, g.cands, g.count, g.cap);
+      emit(em, cand, g.k, g.lo, i, bw, bs, rec, g.cands, g.count, g.cap);
     }
   }
-  emit_flush(em, g.k, g.lo, g.cands, g.count, g.cap);
+  emit_flush(em, rec, g.cands, g.count, g.cap);
 }
 
 // The search of one (DM trial k, window j): the body of the per-plan kernel
@@ -1034,7 +1064,7 @@ __device__ __forceinline__ void sps_window(
   int scap = 0;
   if (!DENSE) {
     const int used = stats_in_hist ? (int)((3 * ccap + 3) & ~3) : 0;
-    const int per = ((kFastBins + 32 - used) / kWarps / 2) & ~1;
+    const int per = ((kFastBins + 32 - used) / kWarps) & ~1;
     if (per >= 32) {
       stage = sh.hist + used;
       scap = per;
@@ -1043,7 +1073,7 @@ __device__ __forceinline__ void sps_window(
   const SweepArgs g{Q,     (int)bufcap, len,  nv,    nw,       odd,
                     mfloor, M2,         thr,  lo,    n,        nrep,
                     k,     wmax,        bounds, cmin, cmax,    ymax,
-                    sh.wid, stage,      scap, cands, count,    cap,
+                    sh.wid, sh.inv,     stage, scap, cands, count, cap,
                     best_w, best_snr,   best_sum};
   switch ((pow2 ? nw : 0) + (q2 ? 16 : 0)) {
 #define DDSP_SWEEP(N)                                 \
