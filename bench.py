@@ -455,9 +455,9 @@ def serving_check(dev, blocks_per_beam=5, log=None):
     (16384-spectrum blocks every 1.342 s, Poisson-jittered arrivals) served
     by batched steps (every waiting beam-block, interleaved mode, 8 staging
     slots) and by the plain per-beam path (one beam per step, a second step
-    queued), each at the same two beam counts: the plain path's estimated
-    real-time limit and the batched one's, from an untimed calibration of
-    the step time per beam-block.  Rings are filled first (untimed), then
+    queued), each from the real-time count an untimed calibration of its
+    step time per beam-block suggests, then in steps of 16 beams up or down
+    until the runs bracket its limit.  Rings are filled first (untimed), then
     `blocks_per_beam` blocks per beam arrive in real time; p50/p99 latency
     from arrival to the host seeing the block's step complete, and the
     device time the pushes and steps took per second of stream (duty): a
@@ -517,12 +517,10 @@ def serving_check(dev, blocks_per_beam=5, log=None):
     free, _ = torch.cuda.mem_get_info(dev)
     n_mem = int((free - reserve - slots * 4 * cfg.nchan * (B + 90112)) //
                 per_beam_bytes) // 16 * 16
-    # the counts each path's step time allows (the runs decide): the plain
-    # path's, the next multiple of 16, and the batched path's
+    # the count each path's step time allows, rounded down to 16 (the
+    # runs decide)
     est_b = int(T * 1e3 / ms_b) // 16 * 16
     est_p = int(T * 1e3 / ms_p) // 16 * 16
-    counts = sorted(set(min(c, n_mem) for c in (est_p, est_p + 16,
-                                                max(est_b, est_p + 16))))
     runs = {"batched": {}, "plain_per_beam": {}}
 
     def run_at(n, per_step, inflight, min_batch=1):
@@ -565,14 +563,30 @@ def serving_check(dev, blocks_per_beam=5, log=None):
                 "device_duty": duty,
                 "real_time": bool(p99 < T and duty < 1.0)}
 
-    for n in counts:
+    # each path from its own estimate in steps of 16 beams: up while the
+    # count is real time (at most two steps), down until it is (at most
+    # three), so the runs bracket the path's limit
+    paths = {
         # batched: a step waits for 4 beam-blocks (a launch of fewer leaves
         # its last wave of work items mostly empty) or 50 ms
-        runs["batched"][str(n)] = run_at(n, 0, 1, min_batch=4)
-        runs["plain_per_beam"][str(n)] = run_at(n, 1, 2)
+        "batched": (est_b, lambda n: run_at(n, 0, 1, min_batch=4)),
+        "plain_per_beam": (est_p, lambda n: run_at(n, 1, 2)),
+    }
+    for path, (start, run) in paths.items():
+        n = max(16, min(start, n_mem))
+        r = runs[path][str(n)] = run(n)
         if log:
-            log(f"serving {n}: {runs['batched'][str(n)]} | "
-                f"{runs['plain_per_beam'][str(n)]}")
+            log(f"serving {path} {n}: {r}")
+        up = r.get("real_time", False)
+        for _ in range(2 if up else 3):
+            n = n + 16 if up else n - 16
+            if n < 16 or n > n_mem:
+                break
+            r = runs[path][str(n)] = run(n)
+            if log:
+                log(f"serving {path} {n}: {r}")
+            if r.get("real_time", False) != up:
+                break
 
     def best(path):
         ok = [int(n) for n, r in runs[path].items() if r.get("real_time")]
@@ -580,7 +594,7 @@ def serving_check(dev, blocks_per_beam=5, log=None):
     return {
         "metric": "real-time beams per B300 at p99 (of the beam counts run)",
         "unit": "beams", "deadline_s": T, "blocks_per_beam": blocks_per_beam,
-        "beams_tested": counts,
+        "beams_tested": {p: sorted(int(n) for n in runs[p]) for p in runs},
         "real_time_beams": {"batched": best("batched"),
                             "plain_per_beam": best("plain_per_beam")},
         "step_ms_per_beam_block": {"batched_8": ms_b, "plain_1": ms_p},

@@ -964,7 +964,11 @@ __device__ __forceinline__ void sps_window(
     // by the last warp, which has the fewest scan groups
     if (warp == kWarps - 1 && lane < nw) {
       const float w = (float)widths[lane];
-      const float two_sigma = kMadToSigma * (float)MAD4 * 0.5f;
+      // (a 32-bit conversion when MAD4 fits, the same rounding; the 64-bit
+      // one runs on the FP64 pipe)
+      const float mad4f = MAD4 < ((int64_t)1 << 31) ? __int2float_rn((int32_t)MAD4)
+                                                    : (float)MAD4;
+      const float two_sigma = kMadToSigma * mad4f * 0.5f;
       const float denom = two_sigma * sqrtf(w);
       sh.inv[lane] = MAD4 > 0 ? 1.0f / denom : 0.0f;
       const float tnum = thr * denom * (1.0f - 4e-6f);
