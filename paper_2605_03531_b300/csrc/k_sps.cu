@@ -6,7 +6,7 @@
 //      shared memory (the series is read from HBM once);
 //   2. exact median and MAD of the window on integer keys: in one pass of
 //      4096 single-value bins around an estimate from 32 sorted samples
-//      when the window's middle half is narrow (median_mad_fast), else by
+//      when the window's middle half is narrow (median_fast, mad_fast_warp), else by
 //      histogram selection: a 2048-bin shared histogram over the current
 //      key range narrows it by 2^11 per pass until the bin holding the
 //      wanted order statistic is one key wide (or the two middle order
@@ -214,7 +214,7 @@ __device__ void select2(KeyFn key, int n, int r1, int r2, uint32_t kmax,
   }
 }
 
-// The estimate median_mad_fast starts from: 32 evenly spaced samples of the
+// The estimate the one-pass bins start from: 32 evenly spaced samples of the
 // window [0, n), read straight from global memory by one warp (while the
 // other warps load the window) and sorted in that warp; bc[0] = their median
 // (a sample value), bc[1] = their interquartile range, bc[2 .. 5] = -1.
@@ -259,11 +259,13 @@ __device__ __forceinline__ void median_estimate(const int32_t *__restrict__ x,
 //    sums while that range lies inside the bins (or starts below them when
 //    no key is below the bins); the MAD order statistics are the smallest v
 //    reaching ranks r1 + 1 and r2 + 1.
-// Returns false (the caller then uses select2) when a rank falls outside
-// the bins.  The result, when true, equals select2's.
-__device__ bool median_mad_fast(int64_t A, int r1, int r2, SpsShared &sh,
-                                uint32_t &k1, uint32_t &k2, uint32_t &u1,
-                                uint32_t &u2) {
+// A rank outside the bins sends that part to select2 (the median at once,
+// the MAD after the scan); the results equal select2's.
+// median_fast: the median part (block-wide), true with k1, k2 and the
+// count below the bins when both middle ranks fall inside them; the prefix
+// P stays in the bins for mad_fast_warp.
+__device__ bool median_fast(int64_t A, int r1, int r2, SpsShared &sh,
+                            uint32_t &k1, uint32_t &k2, uint32_t &below_out) {
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   uint32_t below = 0;
 #pragma unroll
@@ -320,6 +322,16 @@ __device__ bool median_mad_fast(int64_t A, int r1, int r2, SpsShared &sh,
   if (b1 < 0 || b2 < 0) return false;  // block-uniform
   k1 = (uint32_t)(A + b1);
   k2 = (uint32_t)(A + b2);
+  below_out = below;
+  return true;
+}
+
+// mad_fast_warp: the MAD part, run by warps 0 and 1 only (one rank each,
+// no block barrier, so the other warps go on meanwhile): bc[4 + warp] =
+// the rank's order statistic of |2k - m|, or -1 when it leaves the bins.
+__device__ void mad_fast_warp(int64_t A, uint32_t below, uint32_t k1,
+                              uint32_t k2, int r1, int r2, SpsShared &sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   // ---- MAD: C(v) = #{|2k - m| <= v}, -1 when its key range leaves the bins
   const int64_t m = (int64_t)k1 + (int64_t)k2;
   const int64_t lo_ok = A, hi_ok = A + kFastBins - 1;
@@ -333,11 +345,11 @@ __device__ bool median_mad_fast(int64_t A, int r1, int r2, SpsShared &sh,
     return ph - pl;
   };
   // C is non-decreasing in v and valid on a prefix of [0, 2 * kFastBins),
-  // so the smallest v with C(v) >= R is found by one warp per rank (warps
-  // 0 and 1 side by side) in three 32-way steps of widths 256, 8 and 1,
-  // each lane testing the last v of its part.
+  // so the smallest v with C(v) >= R is found by one warp per rank in
+  // three 32-way steps of widths 256, 8 and 1, each lane testing the last
+  // v of its part.
   static_assert(2 * kFastBins == 32 * 256, "MAD search covers [0, 8192)");
-  if (warp < 2) {
+  {
     const int which = warp;
     const int64_t R = (int64_t)(which ? r2 : r1) + 1;
     int64_t base = 0;
@@ -356,12 +368,6 @@ __device__ bool median_mad_fast(int64_t A, int r1, int r2, SpsShared &sh,
     }
     if (lane == 0) sh.bc[4 + which] = found ? base : -1;
   }
-  __syncthreads();
-  const int64_t v1 = sh.bc[4], v2 = sh.bc[5];
-  if (v1 < 0 || v2 < 0) return false;  // block-uniform
-  u1 = (uint32_t)v1;
-  u2 = (uint32_t)v2;
-  return true;
 }
 
 // Chunk bounds of the screen.  Start times are taken in chunks of kChunk;
@@ -741,7 +747,11 @@ __device__ __forceinline__ void sps_window(
   const int ntot = elen + 1;                    // prefix positions 0 .. elen
   const int ngroups = (ntot + kGroup - 1) / kGroup;
   const int gpw = (ngroups + kWarps - 1) / kWarps;
-  const int g0 = warp * gpw, g1 = min(ngroups, g0 + gpw);
+  // warp w takes run kWarps - 1 - w of gpw groups: the runs at the end are
+  // the short ones, so warps 0 and 1, which also estimate the median and
+  // search the MAD, carry the least of the load and the scan
+  const int run = kWarps - 1 - warp;
+  const int g0 = run * gpw, g1 = min(ngroups, g0 + gpw);
   const bool vec = (reinterpret_cast<uintptr_t>(x) & 15) == 0;
   uint32_t sx = 0;                              // this lane's sum of x
   int h = 2 * g0;                               // 128-position halves
@@ -760,9 +770,9 @@ __device__ __forceinline__ void sps_window(
     for (int u = 0; u < 4; ++u)
       v[u] = __ldg(reinterpret_cast<const int4 *>(x + (h + u) * 128) + lane);
   }
-  // the median estimate (the last warp has the fewest load groups) and the
+  // the median estimate (warp 0 has the fewest load groups) and the
   // zeroed histogram, both visible after the barrier
-  if (!given && warp == kWarps - 1) median_estimate(x, lo, n, len, sh);
+  if (!given && warp == 0) median_estimate(x, lo, n, len, sh);
   for (int b = tid; b < (kFastBins + 32) / 4; b += kSpsThreads)
     reinterpret_cast<uint4 *>(sh.hist)[b] = make_uint4(0u, 0u, 0u, 0u);
   __syncthreads();
@@ -851,7 +861,7 @@ __device__ __forceinline__ void sps_window(
   nb = __reduce_add_sync(0xffffffffu, nb);
   if (lane == 0) sh.nbw[warp] = nb;
   sx = __reduce_add_sync(0xffffffffu, sx);
-  if (lane == 0) sh.wsx[warp] = sx;
+  if (lane == 0) sh.wsx[run] = sx;
   mn32 = __reduce_min_sync(0xffffffffu, mn32);
   mx32 = __reduce_max_sync(0xffffffffu, mx32);
   hmn = __reduce_min_sync(0xffffffffu, hmn);
@@ -877,7 +887,11 @@ __device__ __forceinline__ void sps_window(
   // (no barrier: wred and hred are written again only by select2's
   // fallback, after barriers every thread passes once it has read them)
 
-  // ---- 2. median and MAD
+  // ---- 2. median and MAD.  On the one-pass path the block finds the median,
+  // then warps 0 and 1 (the lightest load and scan runs) search the MAD's
+  // two ranks; the other warps wait at the barrier (the scan's chunk
+  // statistics reuse the bins' space, so it cannot start earlier).  Either
+  // part falls back to select2 when its ranks leave the bins.
   int64_t M2 = 0, MAD4 = 0;
   const bool range_ok = given || (mx - mn) < (int64_t)1 << 31;
   if (given) {
@@ -886,39 +900,44 @@ __device__ __forceinline__ void sps_window(
   } else if (range_ok) {
     const int r1 = (len - 1) / 2, r2 = len / 2;
     const uint32_t base = (uint32_t)(int32_t)mn;
-    uint32_t k1, k2, u1, u2;
+    uint32_t k1, k2, below = 0;
     // keys x - min in [0, 2^31)
     auto kx = [&](int i) { return (uint32_t)buf[i] - base; };
     // the bins' counts hold when every window sample lies within 2^31
     // of AB (below it: top bit set; from it up: clear)
     const bool fast = binning && mx - AB64 < ((int64_t)1 << 31) &&
                       AB64 - mn <= ((int64_t)1 << 31) &&
-                      median_mad_fast(AB64 - mn, r1, r2, sh, k1, k2, u1, u2);
+                      median_fast(AB64 - mn, r1, r2, sh, k1, k2, below);
     if (!fast)
       select2(kx, len, r1, r2, (uint32_t)(mx - mn), sh, k1, k2);
     M2 = 2 * mn + (int64_t)k1 + (int64_t)k2;
-    // |2x - M2| = |2(x - min) - (M2 - 2 min)|, both terms in [0, 2^32)
-    const int64_t m2c = M2;
-    const uint32_t m2r = (uint32_t)(m2c - 2 * mn);
-    uint64_t umax = (uint64_t)max(2 * mx - m2c, m2c - 2 * mn);
-    if (!fast)
+    bool mad_done = false;
+    if (fast) {
+      if (warp < 2) mad_fast_warp(AB64 - mn, below, k1, k2, r1, r2, sh);
+      __syncthreads();
+      const int64_t v1 = sh.bc[4], v2 = sh.bc[5];
+      mad_done = v1 >= 0 && v2 >= 0;   // block-uniform
+      MAD4 = v1 + v2;
+    }
+    if (!mad_done) {
+      // |2x - M2| = |2(x - min) - (M2 - 2 min)|, both terms in [0, 2^32)
+      const uint32_t m2r = (uint32_t)(M2 - 2 * mn);
+      const uint64_t umax = (uint64_t)max(2 * mx - M2, M2 - 2 * mn);
+      uint32_t u1, u2;
       select2(
           [&](int i) {
             const uint32_t t2 = 2u * ((uint32_t)buf[i] - base);
             return t2 >= m2r ? t2 - m2r : m2r - t2;
           },
           len, r1, r2, (uint32_t)umax, sh, u1, u2);
-    MAD4 = (int64_t)u1 + (int64_t)u2;
+      MAD4 = (int64_t)u1 + (int64_t)u2;
+    }
   } else if (tid == 0) {
     atomicExch(err, kErrRange);
   }
-  if (tid == 0 && !given) {
-    m2_out[(int64_t)k * nwin + j] = M2;
-    mad4_out[(int64_t)k * nwin + j] = MAD4;
-  }
 
   // per-width FP32 scale 1/(2 sigma sqrt(w)) and integer screen thresholds
-  // (set in step 3 by the last warp).
+  // (set by warp 0, the lightest scan run, before its scan).
   // S/N >= thr  <=>  2 B_y - w*odd >= thr * 2 sigma sqrt(w); the screen
   // keeps a 4e-6 relative margin below that so FP32 rounding cannot hide a
   // candidate the FP32 S/N would accept.  Q2 (|2x - M2| <= 2 ybound + 1,
@@ -934,6 +953,34 @@ __device__ __forceinline__ void sps_window(
   const bool q2 = range_ok &&
                   (2 * ybound + 1) * (int64_t)(elen + 1) < ((int64_t)1 << 30) &&
                   (2 * ybound + 1) * (int64_t)wmax < ((int64_t)1 << 22);
+  auto thresholds = [&](int64_t mad4) {
+    if (lane < nw) {
+      const float w = (float)widths[lane];
+      // (a 32-bit conversion when MAD4 fits, the same rounding; the 64-bit
+      // one runs on the FP64 pipe)
+      const float mad4f = mad4 < ((int64_t)1 << 31)
+                              ? __int2float_rn((int32_t)mad4)
+                              : (float)mad4;
+      const float two_sigma = kMadToSigma * mad4f * 0.5f;
+      const float denom = two_sigma * sqrtf(w);
+      sh.inv[lane] = mad4 > 0 ? 1.0f / denom : 0.0f;
+      const float tnum = thr * denom * (1.0f - 4e-6f);
+      const float t = q2 ? tnum : 0.5f * (tnum + (float)(widths[lane] * odd));
+      int32_t tb;
+      if (mad4 <= 0 || !(t < 2.0e9f)) tb = INT32_MAX;
+      else if (t <= -2.0e9f) tb = INT32_MIN;
+      else tb = (int32_t)floorf(t);
+      sh.thr_by[lane] = tb;
+      sh.wid[lane] = widths[lane];
+    }
+    if (lane == 0) {
+      if (!given) {
+        m2_out[(int64_t)k * nwin + j] = M2;
+        mad4_out[(int64_t)k * nwin + j] = mad4;
+      }
+    }
+  };
+  if (warp == 0) thresholds(MAD4);
   // ---- 3. y (Q2: 2x - M2, else x - floor(median)) and its exclusive prefix
   // sum Q, in place: buf[p] = Q[p] = sum_{t < p} y[t] for p = 0 .. elen
   // (uint32, modular, so every difference Q[t + w] - Q[t] is exact).
@@ -946,41 +993,23 @@ __device__ __forceinline__ void sps_window(
   // below 2^30), where minima, maxima and their differences are exact.
   const int64_t ybnd = q2 ? 2 * ybound + 1 : ybound;
   const bool bounds = !DENSE && have_stats && range_ok && MAD4 > 0 &&
-                      elen > 0 && ybnd * (int64_t)(elen + 1) < ((int64_t)1 << 30);
+                     elen > 0 && ybnd * (int64_t)(elen + 1) < ((int64_t)1 << 30);
   {
     // y = x * ymul - ysub (mod 2^32)
     const uint32_t ymul = q2 ? 2u : 1u;
     const uint32_t ysub = q2 ? (uint32_t)M2 : (uint32_t)mfloor;
-    // warp runs' totals of y from the sums of x the load took: a run holds
-    // the positions [128 g0, 128 g1) and those below elen carry a sample
-    if (warp == 0 && lane < kWarps) {
+    // this run's offset: the totals of y over the runs before it, from the
+    // sums of x the load took (a run holds the positions
+    // [256 r gpw, 256 min(ngroups, (r + 1) gpw)), those below elen carry a
+    // sample); every warp computes its own, so no barrier
+    uint32_t carry = 0;
+    if (lane < run) {
       const int r0 = lane * gpw * kGroup;
       const int r1 = min(ngroups, (lane + 1) * gpw) * kGroup;
       const int cnt = max(0, min(r1, elen) - r0);
-      sh.wsum[lane] = sh.wsx[lane] * ymul - (uint32_t)cnt * ysub;
+      carry = sh.wsx[lane] * ymul - (uint32_t)cnt * ysub;
     }
-    __syncthreads();
-    // thresholds (read by the sweep after the barrier that ends the scan)
-    // by the last warp, which has the fewest scan groups
-    if (warp == kWarps - 1 && lane < nw) {
-      const float w = (float)widths[lane];
-      // (a 32-bit conversion when MAD4 fits, the same rounding; the 64-bit
-      // one runs on the FP64 pipe)
-      const float mad4f = MAD4 < ((int64_t)1 << 31) ? __int2float_rn((int32_t)MAD4)
-                                                    : (float)MAD4;
-      const float two_sigma = kMadToSigma * mad4f * 0.5f;
-      const float denom = two_sigma * sqrtf(w);
-      sh.inv[lane] = MAD4 > 0 ? 1.0f / denom : 0.0f;
-      const float tnum = thr * denom * (1.0f - 4e-6f);
-      const float t = q2 ? tnum : 0.5f * (tnum + (float)(widths[lane] * odd));
-      int32_t tb;
-      if (MAD4 <= 0 || !(t < 2.0e9f)) tb = INT32_MAX;
-      else if (t <= -2.0e9f) tb = INT32_MIN;
-      else tb = (int32_t)floorf(t);
-      sh.thr_by[lane] = tb;
-      sh.wid[lane] = widths[lane];
-    }
-    uint32_t carry = warp_excl_offset(sh.wsum, warp, lane);
+    carry = __reduce_add_sync(0xffffffffu, carry);
     for (int g = g0; g < g1; ++g) {
       // this lane's 8 consecutive positions = one chunk of the statistics
       const int b8 = g * kGroup + kChunk * lane;
