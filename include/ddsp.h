@@ -20,7 +20,11 @@
  *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls that
  *     take a stream are asynchronous and stream-ordered: they return once the
  *     work is enqueued.  ddsp_candidates_fetch and the *_get_* calls
- *     synchronise.
+ *     synchronise: reads of a search's results wait for that search only
+ *     (an event recorded after it), not for work queued behind it on the
+ *     same stream, and copy through a plan-owned non-blocking stream, so a
+ *     pipeline can fetch block k's candidates while block k+1 is being
+ *     dedispersed.
  *   - Every call returns DDSP_OK (0) or a negative DDSP_E_* code; no C++
  *     exception crosses this boundary.  A plan is not thread-safe: use one
  *     plan per host thread / stream.
@@ -231,7 +235,7 @@ int ddsp_single_pulse_search_noalloc_check(ddsp_stream_t stream);
 
 /* Copy the per-(DM, window) statistics of the last search to the host:
  * m2[k*nwin + j] = 2*median, mad4[k*nwin + j] = 4*MAD (both exact).  *nwin
- * receives the window count.  Synchronises the last search's stream.
+ * receives the window count.  Waits for the last search.
  * host arrays may be NULL to query *nwin only. */
 int ddsp_plan_get_stats(ddsp_plan *plan, int64_t *m2, int64_t *mad4,
                         int64_t cap, int64_t *nwin);

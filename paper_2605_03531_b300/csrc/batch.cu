@@ -653,9 +653,9 @@ int ddsp_batch_run(ddsp_batch *B, float threshold, int use_graph,
     Plan &p = B->plans[b]->p;
     int64_t nwin;
     search_windows(p, B->nout[b], &nwin);
-    p.searched = true;
-    p.last_stream = s;
     p.last_nwin = nwin;
+    const int rc = mark_searched(p, s);
+    if (rc != DDSP_OK) return rc;
   }
   return DDSP_OK;
 }

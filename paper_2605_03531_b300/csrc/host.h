@@ -80,5 +80,11 @@ int search_windows(const Plan &p, int64_t n, int64_t *nwin,
                    bool allow_long = false);
 // Reads and clears the plan's device error word.
 int read_err(Plan &p);
+// after a search launch on s: records the plan's search event
+int mark_searched(Plan &p, cudaStream_t s);
+// waits for the plan's last search (its event, else its stream)
+cudaError_t wait_search(Plan &p);
+// device-to-host copy through the plan's copy stream, then waits for it
+cudaError_t copy_to_host(Plan &p, void *dst, const void *src, size_t bytes);
 
 }  // namespace ddsp

@@ -94,6 +94,12 @@ struct Plan {
   int32_t *d_widths = nullptr;
   bool searched = false;
   cudaStream_t last_stream = nullptr;
+  // recorded after every search launch: reading the results waits for the
+  // search, not for work queued behind it on the same stream; the reads go
+  // through a plan-owned non-blocking stream (a copy on the legacy default
+  // stream would wait for every blocking stream's work)
+  cudaEvent_t ev_search = nullptr;
+  cudaStream_t copy_stream = nullptr;
 
   // failure detection of the interleaved dedispersion kernel: the bound of
   // its copy/compute hand-off waits in SM cycles (0: kDefaultWaitCycles),

@@ -292,6 +292,35 @@ void release(Plan &p) {
   cudaFree(p.d_err);
   cudaFree(p.d_widths);
   cudaFree(p.d_rs);
+  if (p.ev_search) cudaEventDestroy(p.ev_search);
+  if (p.copy_stream) cudaStreamDestroy(p.copy_stream);
+  p.ev_search = nullptr;
+  p.copy_stream = nullptr;
+}
+
+int mark_searched(Plan &p, cudaStream_t s) {
+  p.searched = true;
+  p.last_stream = s;
+  cudaError_t e = cudaSuccess;
+  if (!p.ev_search)
+    e = cudaEventCreateWithFlags(&p.ev_search, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventRecord(p.ev_search, s);
+  return cuda_rc(e);
+}
+
+cudaError_t wait_search(Plan &p) {
+  return p.ev_search ? cudaEventSynchronize(p.ev_search)
+                     : cudaStreamSynchronize(p.last_stream);
+}
+
+cudaError_t copy_to_host(Plan &p, void *dst, const void *src, size_t bytes) {
+  cudaError_t e = cudaSuccess;
+  if (!p.copy_stream)
+    e = cudaStreamCreateWithFlags(&p.copy_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, p.copy_stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(p.copy_stream);
+  return e;
 }
 
 int search_windows(const Plan &p, int64_t n, int64_t *nwin, bool allow_long) {
@@ -307,9 +336,11 @@ int search_windows(const Plan &p, int64_t n, int64_t *nwin, bool allow_long) {
 
 int read_err(Plan &p) {
   int32_t e = 0;
-  if (cudaMemcpy(&e, p.d_err, 4, cudaMemcpyDeviceToHost) != cudaSuccess)
-    return DDSP_E_CUDA;
-  if (e != kErrNone) cudaMemset(p.d_err, 0, 4);
+  if (copy_to_host(p, &e, p.d_err, 4) != cudaSuccess) return DDSP_E_CUDA;
+  if (e != kErrNone) {
+    cudaMemsetAsync(p.d_err, 0, 4, p.copy_stream);
+    cudaStreamSynchronize(p.copy_stream);
+  }
   if (e == kErrTimeout) return DDSP_E_TIMEOUT;
   if (e == kErrRange) return DDSP_E_RANGE;
   return DDSP_OK;
@@ -703,9 +734,7 @@ static int run_search(ddsp_plan *h, const int32_t *d_series, int64_t n,
   e = launch_sps(p, d_series, n, threshold, dense, bw, bs, bsum, s);
   if (e != cudaSuccess) return cuda_rc(e);
   p.last_nwin = nwin;
-  p.searched = true;
-  p.last_stream = s;
-  return DDSP_OK;
+  return mark_searched(p, s);
 }
 
 int ddsp_single_pulse_search(ddsp_plan *h, const int32_t *d_series,
@@ -734,11 +763,10 @@ int ddsp_plan_get_stats(ddsp_plan *h, int64_t *m2, int64_t *mad4, int64_t cap,
   if (!m2 && !mad4) return DDSP_OK;
   const int64_t n = p.last_nwin * p.ndm;
   if (cap < n) return DDSP_E_INVALID_ARG;
-  cudaError_t e = cudaStreamSynchronize(p.last_stream);
+  cudaError_t e = wait_search(p);
   if (e != cudaSuccess) return cuda_rc(e);
-  if (m2) e = cudaMemcpy(m2, p.d_m2, n * 8, cudaMemcpyDeviceToHost);
-  if (e == cudaSuccess && mad4)
-    e = cudaMemcpy(mad4, p.d_mad4, n * 8, cudaMemcpyDeviceToHost);
+  if (m2) e = copy_to_host(p, m2, p.d_m2, n * 8);
+  if (e == cudaSuccess && mad4) e = copy_to_host(p, mad4, p.d_mad4, n * 8);
   return cuda_rc(e);
 }
 
@@ -748,17 +776,16 @@ int ddsp_candidates_fetch(ddsp_plan *h, ddsp_cand *host_buf, size_t cap,
   Plan &p = h->p;
   if (!p.searched) return DDSP_E_STATE;
   DeviceGuard g(p.device);
-  cudaError_t e = cudaStreamSynchronize(p.last_stream);
+  cudaError_t e = wait_search(p);
   if (e != cudaSuccess) return cuda_rc(e);
   uint32_t cnt = 0;
-  e = cudaMemcpy(&cnt, p.d_count, 4, cudaMemcpyDeviceToHost);
+  e = copy_to_host(p, &cnt, p.d_count, 4);
   if (e != cudaSuccess) return cuda_rc(e);
   *n_total = cnt;
   const size_t stored = std::min<size_t>(cnt, p.cand_capacity);
   const size_t ncopy = std::min(stored, cap);
   if (ncopy) {
-    e = cudaMemcpy(host_buf, p.d_cands, ncopy * sizeof(ddsp_cand),
-                   cudaMemcpyDeviceToHost);
+    e = copy_to_host(p, host_buf, p.d_cands, ncopy * sizeof(ddsp_cand));
     if (e != cudaSuccess) return cuda_rc(e);
     std::sort(host_buf, host_buf + ncopy,
               [](const ddsp_cand &a, const ddsp_cand &b) {
@@ -775,10 +802,10 @@ int ddsp_candidates_count(ddsp_plan *h, size_t *n_total) {
   Plan &p = h->p;
   if (!p.searched) return DDSP_E_STATE;
   DeviceGuard g(p.device);
-  cudaError_t e = cudaStreamSynchronize(p.last_stream);
+  cudaError_t e = wait_search(p);
   if (e != cudaSuccess) return cuda_rc(e);
   uint32_t cnt = 0;
-  e = cudaMemcpy(&cnt, p.d_count, 4, cudaMemcpyDeviceToHost);
+  e = copy_to_host(p, &cnt, p.d_count, 4);
   if (e != cudaSuccess) return cuda_rc(e);
   *n_total = cnt;
   return read_err(p);
@@ -793,10 +820,10 @@ int ddsp_candidates_fetch_dm_range(ddsp_plan *h, uint32_t dm_lo,
   Plan &p = h->p;
   if (!p.searched) return DDSP_E_STATE;
   DeviceGuard g(p.device);
-  cudaError_t e = cudaStreamSynchronize(p.last_stream);
+  cudaError_t e = wait_search(p);
   if (e != cudaSuccess) return cuda_rc(e);
   uint32_t cnt = 0;
-  e = cudaMemcpy(&cnt, p.d_count, 4, cudaMemcpyDeviceToHost);
+  e = copy_to_host(p, &cnt, p.d_count, 4);
   if (e != cudaSuccess) return cuda_rc(e);
   *n_total = cnt;
   const size_t stored = std::min<size_t>(cnt, p.cand_capacity);
@@ -806,8 +833,7 @@ int ddsp_candidates_fetch_dm_range(ddsp_plan *h, uint32_t dm_lo,
   size_t found = 0, kept = 0;
   for (size_t off = 0; off < stored; off += piece) {
     const size_t n = std::min(piece, stored - off);
-    e = cudaMemcpy(tmp.data(), p.d_cands + off, n * sizeof(ddsp_cand),
-                   cudaMemcpyDeviceToHost);
+    e = copy_to_host(p, tmp.data(), p.d_cands + off, n * sizeof(ddsp_cand));
     if (e != cudaSuccess) return cuda_rc(e);
     for (size_t i = 0; i < n; ++i) {
       if (tmp[i].dm_idx >= dm_lo && tmp[i].dm_idx < dm_hi) {

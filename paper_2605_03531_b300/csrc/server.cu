@@ -680,15 +680,16 @@ int ddsp_server_fetch(ddsp_server *S, int beam, int64_t block,
   DeviceGuard g(S->device);
   cudaError_t e = cudaEventSynchronize(step_event(*S, b.step_of[block % 4]));
   uint32_t cnt = 0;
+  // copies through the plan's non-blocking copy stream: the legacy default
+  // stream would also wait for the steps queued since
   if (e == cudaSuccess)
-    e = cudaMemcpy(&cnt, S->d_counts + 2 * beam + (block & 1), 4,
-                   cudaMemcpyDeviceToHost);
+    e = copy_to_host(S->plan->p, &cnt, S->d_counts + 2 * beam + (block & 1), 4);
   if (e != cudaSuccess) return cuda_rc(e);
   const size_t stored = std::min<size_t>(cnt, S->cap);
   const size_t ncopy = std::min(stored, cap);
   if (ncopy > 0) {
-    e = cudaMemcpy(host_buf, b.cands + (size_t)(block & 1) * S->cap,
-                   ncopy * sizeof(ddsp_cand), cudaMemcpyDeviceToHost);
+    e = copy_to_host(S->plan->p, host_buf, b.cands + (size_t)(block & 1) * S->cap,
+                     ncopy * sizeof(ddsp_cand));
     if (e != cudaSuccess) return cuda_rc(e);
     std::sort(host_buf, host_buf + ncopy,
               [](const ddsp_cand &a, const ddsp_cand &c) {
