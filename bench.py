@@ -608,6 +608,53 @@ def serving_check(dev, blocks_per_beam=5, log=None):
         "runs": runs}
 
 
+# ------------------------------------------------ one serving step (profiling)
+def run_servestep(args):
+    """One streaming server of the 4096-channel shape in the interleaved
+    mode (8 staging slots) with --nbeams beams (0 = 8), stepped --steps
+    times after --warmup steps, each step taking one fresh block of every
+    beam: the device time of a step and per beam-block, by CUDA events (the
+    workload that the serving launch list and its profile are taken on)."""
+    import torch
+    from paper_2605_03531_b300 import Plan, Server, build, synth
+    build.build()
+    dev = torch.device("cuda", 0)
+    cfg = synth.config5(1)[0]
+    B = cfg.nsamp_out
+    plan = Plan(cfg.nchan, cfg.f_top, cfg.chan_bw, cfg.tsamp, cfg.dm_list(),
+                cfg.widths, nbits=8, norm_window=cfg.norm_window,
+                cand_capacity=1 << 18)
+    nb = args.nbeams or 8
+    srv = Server(plan, B, nb, 4 << 30)
+    srv.set_mode(Server.INTERLEAVED, 8)
+    beams = [srv.admit() for _ in range(nb)]
+    blocks = [synth.noise_u8(B, cfg.nchan, 100 + i, device=dev)
+              for i in range(4)]
+    stream = torch.cuda.current_stream(dev)
+    ms = []
+    for k in range(args.warmup + args.steps):
+        for i, b in enumerate(beams):
+            srv.push(b, blocks[(i + k) % 4], stream=stream)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        srv.step(cfg.threshold, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        if k >= args.warmup:
+            ms.append(e0.elapsed_time(e1))
+    srv.check(stream)
+    srv.close()
+    step = float(np.median(ms))
+    print(json.dumps({"workload": "one serving step", "beams": nb,
+                      "block": B, "nchan": cfg.nchan, "ndm": cfg.ndm,
+                      "mode": "interleaved, 8 staging slots",
+                      "ms_per_step": step, "ms_per_beam_block": step / nb,
+                      "steps": args.steps, "warmup": args.warmup}),
+          flush=True)
+    return 0
+
+
 # ------------------------------------------------ unit peaks (measurement)
 def run_peaks(args):
     """Microbenchmarks of the on-chip units the dedispersion is bound by
@@ -1645,7 +1692,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-serving", action="store_true",
                     help="beam workload: skip the bounded serving check")
-    ap.add_argument("--workload", choices=["beam", "sps", "batch", "serve", "peaks",
+    ap.add_argument("--workload", choices=["beam", "sps", "batch", "serve",
+                                           "servestep", "peaks",
                                            "cluster", "dered", "ffa",
                                            "resample", "rfi"],
                     default="beam",
@@ -1653,6 +1701,8 @@ def main():
                          "(headline); sps: the search-only stress case; batch: "
                          "160 uneven beams in one persistent launch; serve: "
                          "real-time streaming beams (--steps blocks per beam); "
+                         "servestep: device time of one serving step of "
+                         "--nbeams beams (profiling); "
                          "cluster: peaks filter + DBSCAN of a candidate list; "
                          "dered: running-median de-reddening of the beam's "
                          "series; ffa: folding transform + profile search; "
@@ -1660,7 +1710,8 @@ def main():
                          "rfi: gptool-style RFI cleaning of a block; peaks: "
                          "microbenchmarks of the shared-memory and integer "
                          "ALU rates per SM clock")
-    ap.add_argument("--nbeams", type=int, default=0, help="batch: beams (0 = 160)")
+    ap.add_argument("--nbeams", type=int, default=0,
+                    help="batch: beams (0 = 160); servestep: beams (0 = 8)")
     ap.add_argument("--inflight", type=int, default=1,
                     help="serve: batched steps queued on the device at once")
     ap.add_argument("--plain-inflight", type=int, default=2,
@@ -1688,6 +1739,8 @@ def main():
         return run_batch(args)
     if args.workload == "serve":
         return run_serve(args)
+    if args.workload == "servestep":
+        return run_servestep(args)
     if args.workload == "cluster":
         return run_cluster(args)
     if args.workload == "dered":
