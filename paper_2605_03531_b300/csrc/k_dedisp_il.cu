@@ -127,6 +127,57 @@ interleave_kernel(const T *__restrict__ cm, int64_t pitch, int64_t nvalid,
   *reinterpret_cast<uint4 *>(y + (int64_t)c * ypitch + i) = o;
 }
 
+// The uint8 interleave with 16-byte loads, for rows, segment length S,
+// ring length and ring start that are multiples of 16 (a 16-sample group
+// then never straddles the wrap): a thread builds 16 consecutive elements
+// from four 16-byte loads (rows i + m S), four 4x4 byte transposes, four
+// 16-byte stores.
+__global__ void __launch_bounds__(256)
+interleave16_u8_kernel(const uint8_t *__restrict__ cm, int64_t pitch,
+                       int64_t nvalid, int S, uint32_t *__restrict__ y,
+                       int64_t ypitch, int64_t ring, int64_t t0) {
+  const int c = blockIdx.y;
+  const int64_t i = 16 * ((int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+  if (i >= ypitch) return;
+  const uint8_t *x = cm + (int64_t)c * pitch;
+  auto at = [&](int64_t b) {
+    if (ring <= 0) return b;
+    int64_t q = t0 + b;
+    if (q >= ring) q -= ring;
+    return q < ring ? q : q % ring;
+  };
+  uint4 w[4];
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    const int64_t b = i + (int64_t)m * S;
+    if (b + 16 <= nvalid) {
+      const int64_t a = at(b);
+      w[m] = DDSP_BC(a >= 0 && a + 16 <= pitch, kBcIntlvIn, a)
+                 ? __ldg(reinterpret_cast<const uint4 *>(x + a))
+                 : make_uint4(0u, 0u, 0u, 0u);
+    } else {
+      uint32_t v[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+      for (int k = 0; k < 16; ++k)
+        if (b + k < nvalid) v[k >> 2] |= (uint32_t)x[at(b + k)] << (8 * (k & 3));
+      w[m] = make_uint4(v[0], v[1], v[2], v[3]);
+    }
+  }
+  uint32_t *yr = y + (int64_t)c * ypitch + i;
+  const uint4 q0 = transpose4x4(w[0].x, w[1].x, w[2].x, w[3].x);
+  const uint4 q1 = transpose4x4(w[0].y, w[1].y, w[2].y, w[3].y);
+  const uint4 q2 = transpose4x4(w[0].z, w[1].z, w[2].z, w[3].z);
+  const uint4 q3 = transpose4x4(w[0].w, w[1].w, w[2].w, w[3].w);
+  if (i + 4 <= ypitch && DDSP_BC(true, kBcIntlvOut, i))
+    reinterpret_cast<uint4 *>(yr)[0] = q0;
+  if (i + 8 <= ypitch && DDSP_BC(true, kBcIntlvOut, i + 4))
+    reinterpret_cast<uint4 *>(yr)[1] = q1;
+  if (i + 12 <= ypitch && DDSP_BC(true, kBcIntlvOut, i + 8))
+    reinterpret_cast<uint4 *>(yr)[2] = q2;
+  if (i + 16 <= ypitch && DDSP_BC(true, kBcIntlvOut, i + 12))
+    reinterpret_cast<uint4 *>(yr)[3] = q3;
+}
+
 // Time-major uint8 spectra (nchan % 16 == 0) straight to interleaved rows:
 // a block takes 64 elements x 128 channels, i.e. the four 64-sample x
 // 128-channel tiles of input rows i0 + m S (m < 4), loaded as 16-byte
@@ -435,7 +486,16 @@ cudaError_t launch_interleave(const IlLaunch &p, const void *d_cm,
   const int S = dedisp_segment(p.tile);
   const dim3 grid((unsigned)((ypitch / 4 + 255) / 256), (unsigned)p.nchan);
   uint32_t *y = static_cast<uint32_t *>(ydst ? ydst : p.d_il);
-  if (p.nbits == 8)
+  const bool al16 = (reinterpret_cast<uintptr_t>(d_cm) & 15) == 0 &&
+                    pitch % 16 == 0 && S % 16 == 0 &&
+                    (ring <= 0 || (ring % 16 == 0 && t0 % 16 == 0));
+  if (p.nbits == 8 && al16) {
+    const dim3 g16((unsigned)(((ypitch + 15) / 16 + 255) / 256),
+                   (unsigned)p.nchan);
+    interleave16_u8_kernel<<<g16, 256, 0, s>>>(
+        static_cast<const uint8_t *>(d_cm), pitch, nvalid, S, y, ypitch, ring,
+        t0);
+  } else if (p.nbits == 8)
     interleave_kernel<uint8_t><<<grid, 256, 0, s>>>(
         static_cast<const uint8_t *>(d_cm), pitch, nvalid, S, y, ypitch, ring,
         t0);
