@@ -342,3 +342,39 @@ def test_c5_shape_blocks_match_oracle(mode):
                           width_check)
     srv.check()
     srv.close()
+
+
+def test_server_interleave_on_unaligned_ring_positions():
+    """Widths up to 8 make the carry 8 samples, so the ring position of a
+    block's window is a multiple of 8 but not of 16: the interleave then
+    takes its 4-sample path instead of the 16-byte one.  Every block's
+    series and candidates equal the plain path's."""
+    widths = [1, 2, 4, 8]
+
+    def plan():
+        return Plan(NCHAN, 500.0, -200.0 / NCHAN, 81.92e-6,
+                    np.linspace(0.0, 10.0, 64), widths, nbits=8,
+                    norm_window=2048, cand_capacity=1 << 16)
+
+    srv_plan, ref_plan = plan(), plan()
+    srv = Server(srv_plan, B, 2)
+    srv.set_mode(Server.INTERLEAVED, 2)
+    assert srv.carry == 8
+    beams = [srv.admit() for _ in range(2)]
+    xs = [_stream(300 + i) for i in range(2)]
+    unaligned = 0
+    for j in range(NBLK):
+        for i in range(2):
+            assert srv.push(beams[i], xs[i][j * B:(j + 1) * B])
+        sid, sb = srv.step(THR)
+        torch.cuda.synchronize()
+        assert sorted(sb) == sorted(beams)
+        for i in range(2):
+            s_ref, c_ref = _reference(ref_plan, srv, xs[i], j)
+            s_got = srv.series(beams[i])
+            assert torch.equal(s_got, s_ref), (i, j)
+            c, n, t0 = srv.fetch(beams[i], j)
+            _same(c, c_ref)
+            unaligned += (t0 % 16) != 0
+    assert unaligned > 0
+    srv.close()
