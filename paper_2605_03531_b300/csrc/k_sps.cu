@@ -418,7 +418,7 @@ __host__ __device__ __forceinline__ int64_t sps_chunk_cap(int64_t cap) {
 // when no width reaches the threshold and there is no candidate either
 // way).  NW = 0: any ascending width list, each width screened first
 // (every width in the dense mode).
-template <bool DENSE, int NW, bool Q2>
+template <bool DENSE, int NW, bool Q2, bool N32 = false>
 __device__ __forceinline__ int exact_start(
     const uint32_t *__restrict__ Q, int qcap, int i, int nv, int nw,
     const int32_t (&wv)[kMaxWidths], const int32_t (&tbv)[kMaxWidths],
@@ -447,8 +447,12 @@ __device__ __forceinline__ int exact_start(
       sn[wi] = -INFINITY;
       if (v) {
         dd[wi] = (int32_t)(Q[i + (1 << wi)] - qi);
+        // N32 (y prefix): widths up to 32 keep 2 B_y - w*odd below 2^22,
+        // so it converts exactly by two operations as well
         sn[wi] = (Q2 ? small_int_to_float(dd[wi])
-                     : twice_minus(dd[wi], odd << wi)) *
+                  : (N32 && (1 << wi) <= 32)
+                      ? small_int_to_float(2 * dd[wi] - (odd << wi))
+                      : twice_minus(dd[wi], odd << wi)) *
                  iv[wi];
       }
     }
@@ -579,7 +583,7 @@ struct SweepArgs {
 
 // Step 4: boxcars, S/N, candidates of one window (NW and Q2 as in
 // exact_start).
-template <bool DENSE, int NW, bool Q2>
+template <bool DENSE, int NW, bool Q2, bool N32 = false>
 __device__ __forceinline__ void sweep(const SweepArgs &g,
                                       const int32_t (&wv)[kMaxWidths],
                                       const int32_t (&tbv)[kMaxWidths],
@@ -590,7 +594,7 @@ __device__ __forceinline__ void sweep(const SweepArgs &g,
     for (int i = tid; i < g.len; i += kSpsThreads) {
       float bs;
       int32_t bd;
-      const int bw = exact_start<true, NW, Q2>(g.Q, g.qcap, i, g.nv, g.nw, wv,
+      const int bw = exact_start<true, NW, Q2, N32>(g.Q, g.qcap, i, g.nv, g.nw, wv,
                                                tbv, iv, g.odd, bs, bd);
       // the boxcar sum of x: (num + w*M2)/2 (Q2) or B_y + w*floor(median),
       // modulo 2^32
@@ -620,7 +624,9 @@ __device__ __forceinline__ void sweep(const SweepArgs &g,
     c.dm_idx = (uint32_t)g.k;
     c.t = (uint32_t)(g.lo + i);
     c.w_idx = (uint32_t)bw;
-    c.snr = (Q2 ? small_int_to_float(d) : twice_minus(d, w * g.odd)) *
+    c.snr = (Q2 ? small_int_to_float(d)
+             : (N32 && w <= 32) ? small_int_to_float(2 * d - w * g.odd)
+                                : twice_minus(d, w * g.odd)) *
             g.inv[bw];
     return c;
   };
@@ -676,7 +682,7 @@ __device__ __forceinline__ void sweep(const SweepArgs &g,
       int32_t bd;
       int bw = -1;
       if (mine)
-        bw = exact_start<false, NW, Q2>(g.Q, g.qcap, i, g.nv, g.nw, wv, tbv,
+        bw = exact_start<false, NW, Q2, N32>(g.Q, g.qcap, i, g.nv, g.nw, wv, tbv,
                                         iv, g.odd, bs, bd);
       const bool cand = bw >= 0 && bs >= g.thr && g.lo + i < g.nrep;
       emit(em, cand, g.k, g.lo, i, bw, bs, rec, g.cands, g.count, g.cap);
@@ -1108,13 +1114,19 @@ __device__ __forceinline__ void sps_window(
                     k,     wmax,        bounds, cmin, cmax,    ymax,
                     sh.wid, sh.inv,     stage, scap, cands, count, cap,
                     best_w, best_snr,   best_sum};
-  switch ((pow2 ? nw : 0) + (q2 ? 16 : 0)) {
-#define DDSP_SWEEP(N)                                 \
-  case N:                                             \
-    sweep<DENSE, N, false>(g, wv, tbv, iv, bufcap);   \
-    return;                                           \
-  case N + 16:                                        \
-    sweep<DENSE, N, true>(g, wv, tbv, iv, bufcap);    \
+  // y prefix (not Q2) with |2 B_y - w*odd| < 2^22 for every width up to 32
+  const bool n32 = !q2 && range_ok &&
+                   (2 * ybound + 1) * 32 < ((int64_t)1 << 22);
+  switch ((pow2 ? nw : 0) + (q2 ? 16 : (n32 && pow2 ? 32 : 0))) {
+#define DDSP_SWEEP(N)                                     \
+  case N:                                                 \
+    sweep<DENSE, N, false>(g, wv, tbv, iv, bufcap);       \
+    return;                                               \
+  case N + 16:                                            \
+    sweep<DENSE, N, true>(g, wv, tbv, iv, bufcap);        \
+    return;                                               \
+  case N + 32:                                            \
+    sweep<DENSE, N, false, true>(g, wv, tbv, iv, bufcap); \
     return;
     DDSP_SWEEP(1) DDSP_SWEEP(2) DDSP_SWEEP(3) DDSP_SWEEP(4) DDSP_SWEEP(5)
     DDSP_SWEEP(6) DDSP_SWEEP(7) DDSP_SWEEP(8) DDSP_SWEEP(9) DDSP_SWEEP(10)
