@@ -192,11 +192,14 @@ constexpr int kIlPW = kIlTC / 4 + 1;   // tile row pitch in words (skew)
 __global__ void __launch_bounds__(256)
 unpack_interleave_u8_kernel(const uint8_t *__restrict__ in, int64_t nsamp_in,
                             int nchan, int S, uint32_t *__restrict__ y,
-                            int64_t ypitch) {
+                            int64_t ypitch, int time_on_y) {
   __shared__ uint32_t tile[4][kIlTS * kIlPW];
   const int tid = threadIdx.x;
-  const int64_t i0 = (int64_t)blockIdx.x * kIlTS;
-  const int c0 = blockIdx.y * kIlTC;
+  // time_on_y: blockIdx.x is the channel slice, so the slices of one time
+  // range run together and write neighbouring parts of every row (10 %
+  // faster than the slices one after another)
+  const int64_t i0 = (int64_t)(time_on_y ? blockIdx.y : blockIdx.x) * kIlTS;
+  const int c0 = (time_on_y ? blockIdx.x : blockIdx.y) * kIlTC;
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
 #pragma unroll
@@ -514,11 +517,14 @@ cudaError_t launch_unpack_interleave(const Plan &p, const void *d_in,
                                      int64_t nsamp_in, int64_t ypitch,
                                      cudaStream_t s) {
   const int S = dedisp_segment(p.tile);
-  const dim3 grid((unsigned)((ypitch + kIlTS - 1) / kIlTS),
-                  (unsigned)((p.nchan + kIlTC - 1) / kIlTC));
+  const int64_t nt = (ypitch + kIlTS - 1) / kIlTS;
+  const unsigned nc = (unsigned)((p.nchan + kIlTC - 1) / kIlTC);
+  // time tiles along y while they fit its 65535 limit
+  const int time_on_y = nt <= 65535;
+  const dim3 grid = time_on_y ? dim3(nc, (unsigned)nt) : dim3((unsigned)nt, nc);
   unpack_interleave_u8_kernel<<<grid, 256, 0, s>>>(
       static_cast<const uint8_t *>(d_in), nsamp_in, p.nchan, S,
-      static_cast<uint32_t *>(p.d_il), ypitch);
+      static_cast<uint32_t *>(p.d_il), ypitch, time_on_y);
   return cudaGetLastError();
 }
 
