@@ -480,9 +480,9 @@ int ddsp_server_fetch(ddsp_server *server, int beam, int64_t block,
                       int64_t *t_start);
 
 /* Device pointer of the series [ndm][ncols] of a beam's last stepped block
- * (valid once its step completed, until the next step): its series slot
- * (the step's k-th beam-block uses slot k mod G), which still holds it only
- * if the block was among the latest step's last G beam-blocks;
+ * (valid once its step completed, until the next step): its series slot (a
+ * step runs its beam-blocks in groups of G, the k-th in slot k mod G), which
+ * is reported only if the block was in the latest step's last group;
  * DDSP_E_STATE otherwise. */
 int ddsp_server_series(ddsp_server *server, int beam, int32_t **d_series,
                        int64_t *ncols);
